@@ -1,0 +1,528 @@
+"""Pins of the FP64 CPU oracle against closed forms, limits, identities and brute force.
+
+Each test fixes one part of the oracle to something other than the oracle itself (a textbook
+closed form, a limit the paper's equations reduce to, an exact algebraic identity, or a
+brute-force evaluation), so that a dropped term, a wrong sign or index or a transposed operand
+in the oracle fails at least one of them. Paper references are to arXiv:2602.12011.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_12011_gb300 import workloads as W
+
+MSUN_S = 4.925490947641267e-6
+GPC_S = 1.02927125054339e17
+C_SI = 299792458.0
+
+TH = np.array([1e6, 2.0, 0.5, 0.3, 25.8, 0.4, 1.3, 1.375, -1.2108, 2.659, 0.8 * 2.0 ** 20])
+
+
+def chirp_mass_s(th):
+    M = th[0] * MSUN_S
+    eta = th[1] / (1 + th[1]) ** 2
+    return eta ** 0.6 * M
+
+
+# -------------------------------------------------------------------------------------------
+# Spin-weighted spherical harmonics
+# -------------------------------------------------------------------------------------------
+def ylm_closed(l, m, i):
+    """Closed forms of -2Y_lm(iota, 0) (Ajith et al. 2007, arXiv:0709.0093, Eq. II.9 list)."""
+    c2, s2 = math.cos(i / 2), math.sin(i / 2)
+    pi = math.pi
+    table = {
+        (2, 2): math.sqrt(5 / (64 * pi)) * (1 + math.cos(i)) ** 2,
+        (2, -2): math.sqrt(5 / (64 * pi)) * (1 - math.cos(i)) ** 2,
+        (2, 1): math.sqrt(5 / (16 * pi)) * math.sin(i) * (1 + math.cos(i)),
+        (2, -1): math.sqrt(5 / (16 * pi)) * math.sin(i) * (1 - math.cos(i)),
+        (3, 3): -math.sqrt(21 / (2 * pi)) * c2 ** 5 * s2,
+        (3, -3): math.sqrt(21 / (2 * pi)) * c2 * s2 ** 5,
+        (3, 2): math.sqrt(7 / pi) / 2 * c2 ** 4 * (3 * math.cos(i) - 2),
+        (3, -2): math.sqrt(7 / (4 * pi)) * (3 * math.cos(i) + 2) * s2 ** 4,
+        (4, 4): 3 * math.sqrt(7 / pi) * c2 ** 6 * s2 ** 2,
+        (4, -4): 3 * math.sqrt(7 / pi) * c2 ** 2 * s2 ** 6,
+    }
+    return table[(l, m)]
+
+
+LMS = [(2, 2), (2, -2), (2, 1), (2, -1), (3, 3), (3, -3), (3, 2), (3, -2), (4, 4), (4, -4)]
+
+
+@pytest.mark.parametrize("lm", LMS)
+def test_sylm_wigner_matches_closed_forms(oracle_mod, lm):
+    for i in np.linspace(0.0, math.pi, 13):
+        assert oracle_mod.sylm(lm[0], lm[1], i) == pytest.approx(ylm_closed(lm[0], lm[1], i), abs=1e-14)
+
+
+def test_sylm_orthonormal(oracle_mod):
+    # integral over the sphere of -2Y_lm -2Y*_l'm = delta_ll' (Gauss-Legendre in cos(iota)).
+    x, w = np.polynomial.legendre.leggauss(40)
+    io = np.arccos(x)
+    def integ(l1, l2, m):
+        y1 = np.array([oracle_mod.sylm(l1, m, i) for i in io])
+        y2 = np.array([oracle_mod.sylm(l2, m, i) for i in io])
+        return 2 * math.pi * np.sum(w * y1 * y2)
+    for l, m in [(2, 2), (2, -2), (2, 1), (3, 3), (3, 2), (3, -2), (4, 4), (4, -4), (4, 2), (4, 1)]:
+        assert integ(l, l, m) == pytest.approx(1.0, abs=1e-12)
+    for (l1, l2, m) in [(2, 3, 2), (2, 4, 2), (3, 4, 3), (2, 3, -2), (2, 3, 1)]:
+        assert abs(integ(l1, l2, m)) < 1e-12
+
+
+# -------------------------------------------------------------------------------------------
+# Waveform
+# -------------------------------------------------------------------------------------------
+def test_face_on_22_newtonian_amplitude(oracle_mod):
+    """|h+| of the face-on (2,2) SPA signal = sqrt(5/24) pi^(-2/3) Mc^(5/6) f^(-7/6) / D."""
+    th = TH.copy(); th[5] = 0.0
+    f = np.geomspace(1e-4, 3e-3, 9)
+    hp, hc = oracle_mod.polarizations(th, W.MODE_22, f)
+    Mc = chirp_mass_s(th)
+    D = th[4] * GPC_S
+    ref = math.sqrt(5 / 24) * math.pi ** (-2 / 3) * Mc ** (5 / 6) * f ** (-7 / 6) / D
+    np.testing.assert_allclose(np.abs(hp), ref, rtol=1e-12)
+    np.testing.assert_allclose(hc, -1j * hp, rtol=1e-13, atol=0)
+
+
+def test_tf_newtonian_limit(oracle_mod):
+    """t_c - t_f -> (5/256) Mc^(-5/3) (pi f)^(-8/3) as v -> 0 (Eq. eq_tf at Newtonian order)."""
+    th = TH.copy()
+    M = th[0] * MSUN_S
+    Mc = chirp_mass_s(th)
+    for v in (1e-3, 3e-3):
+        f = v ** 3 / (math.pi * M)
+        _, tf, _ = oracle_mod.mode(th, 2, 2, [f])
+        newt = 5.0 / 256.0 * Mc ** (-5 / 3) * (math.pi * f) ** (-8 / 3)
+        assert (th[10] - tf[0]) / newt == pytest.approx(1.0, abs=10 * v * v)
+
+
+@pytest.mark.parametrize("q", [1.0, 2.0, 7.0])
+def test_tf_matches_taylort2_to_2p5pn(oracle_mod, q):
+    """Non-spinning t_f against the published TaylorT2 time t(v) to 2.5PN (Buonanno et al. 2009):
+    t_c - t = 5M/(256 eta v^8) [1 + tau2 v^2 + tau3 v^3 + tau4 v^4 + tau5 v^5 + O(v^6)]."""
+    th = TH.copy(); th[1] = q; th[2] = th[3] = 0.0
+    M = th[0] * MSUN_S
+    eta = q / (1 + q) ** 2
+    pi = math.pi
+    tau2 = 743 / 252 + 11 * eta / 3
+    tau3 = -32 * pi / 5
+    tau4 = 3058673 / 508032 + 5429 * eta / 504 + 617 * eta ** 2 / 72
+    tau5 = -(7729 / 252 - 13 * eta / 3) * pi
+    for v in (0.01, 0.02, 0.04):
+        f = v ** 3 / (pi * M)
+        _, tf, _ = oracle_mod.mode(th, 2, 2, [f])
+        series = 1 + tau2 * v ** 2 + tau3 * v ** 3 + tau4 * v ** 4 + tau5 * v ** 5
+        ratio = (th[10] - tf[0]) / (5 * M / (256 * eta * v ** 8))
+        assert abs(ratio - series) < 2000 * v ** 6
+
+
+@pytest.mark.parametrize("lm", list(W.MODES))
+def test_tf_is_phase_derivative(oracle_mod, lm):
+    """t_f = (1/2 pi) dPsi/df (Eq. eq_tf with Phi = -Psi) against a central difference."""
+    f = np.geomspace(2e-4, 3e-3, 7)
+    _, tf, _ = oracle_mod.mode(TH, lm[0], lm[1], f)
+    h = f * 1e-6
+    _, _, pp = oracle_mod.mode(TH, lm[0], lm[1], f + h)
+    _, _, pm = oracle_mod.mode(TH, lm[0], lm[1], f - h)
+    fd = (pp - pm) / (2 * h) / (2 * math.pi)
+    np.testing.assert_allclose(tf, fd, rtol=1e-7)
+
+
+@pytest.mark.parametrize("lm", [(2, 1), (3, 3), (3, 2), (4, 4)])
+def test_mode_phase_scaling_identity(oracle_mod, lm):
+    """Psi_lm(f) = (m/2) Psi_22(2f/m) + (m-2) pi/8 and t_f^lm(f) = t_f^22(2f/m): the (l,m)
+    harmonic at frequency f is the orbit at orbital frequency f/m."""
+    l, m = lm
+    f = np.geomspace(2e-4, 2e-3, 6)
+    _, tf, ps = oracle_mod.mode(TH, l, m, f)
+    _, tf22, ps22 = oracle_mod.mode(TH, 2, 2, 2 * f / m)
+    np.testing.assert_allclose(ps - m / 2 * ps22, (m - 2) * math.pi / 8, atol=1e-9 * np.abs(ps).max())
+    np.testing.assert_allclose(tf, tf22, rtol=1e-13)
+
+
+def test_odd_m_modes_vanish_for_equal_masses(oracle_mod):
+    th = TH.copy(); th[1] = 1.0
+    f = np.geomspace(1e-4, 3e-3, 5)
+    for l, m in ((2, 1), (3, 3)):
+        h, _, _ = oracle_mod.mode(th, l, m, f)
+        assert np.all(h == 0)
+    h, _, _ = oracle_mod.mode(th, 2, 2, f)
+    assert np.all(np.abs(h) > 0)
+
+
+def test_face_on_only_m2_and_circular(oracle_mod):
+    """iota = 0: only m = 2 harmonics reach the observer and h_x = -i h_+ (circular)."""
+    th = TH.copy(); th[5] = 0.0
+    f = np.geomspace(1e-4, 3e-3, 5)
+    for bit, (l, m) in enumerate(W.MODES):
+        hp, hc = oracle_mod.polarizations(th, 1 << bit, f)
+        if m == 2:
+            assert np.all(np.abs(hp) > 0)
+            np.testing.assert_allclose(hc, -1j * hp, rtol=1e-14)
+        else:
+            assert np.all(hp == 0) and np.all(hc == 0)
+
+
+def test_22_inclination_dependence(oracle_mod):
+    """(2,2) only: h+ = sqrt(5/16pi) (1+cos^2 i)/2 H22, hx = -i sqrt(5/16pi) cos i H22."""
+    f = np.geomspace(1e-4, 3e-3, 5)
+    for inc in (0.3, 1.1, 2.0, 2.9):
+        th = TH.copy(); th[5] = inc
+        hp, hc = oracle_mod.polarizations(th, W.MODE_22, f)
+        H, _, _ = oracle_mod.mode(th, 2, 2, f)
+        k = math.sqrt(5 / (16 * math.pi))
+        np.testing.assert_allclose(hp, k * (1 + math.cos(inc) ** 2) / 2 * H, rtol=1e-13)
+        np.testing.assert_allclose(hc, -1j * k * math.cos(inc) * H, rtol=1e-13)
+
+
+def test_mode_symmetry_explicit_plus_minus_m(oracle_mod):
+    """h_{l,-m} = (-1)^l h*_lm: summing both signs of m explicitly,
+    h+ + i hx = sum_lm H~_lm Y_lm and h+ - i hx = sum_lm (-1)^l H~_lm Y_{l,-m} for f > 0."""
+    f = np.geomspace(1e-4, 3e-3, 5)
+    for inc in (0.4, 1.7, 2.8):
+        th = TH.copy(); th[5] = inc
+        hp, hc = oracle_mod.polarizations(th, W.MODE_ALL, f)
+        sp = np.zeros_like(hp); sm = np.zeros_like(hp)
+        for l, m in W.MODES:
+            H, _, _ = oracle_mod.mode(th, l, m, f)
+            sp += H * ylm_closed(l, m, inc)
+            sm += (-1) ** l * H * ylm_closed(l, -m, inc)
+        np.testing.assert_allclose(hp + 1j * hc, sp, rtol=1e-12, atol=1e-12 * np.abs(sp).max())
+        np.testing.assert_allclose(hp - 1j * hc, sm, rtol=1e-12, atol=1e-12 * np.abs(sp).max())
+
+
+def test_planck_taper_edges(oracle_mod):
+    M = TH[0] * MSUN_S
+    Fisco = 6 ** -1.5 / (2 * math.pi * M)
+    for m in (1, 2, 3, 4):
+        assert oracle_mod.taper(TH, 0.9 * Fisco * m * (1 - 1e-12), m) == 1.0
+        assert oracle_mod.taper(TH, Fisco * m, m) == 0.0
+        assert oracle_mod.taper(TH, 0.95 * Fisco * m, m) == pytest.approx(0.5, abs=1e-12)
+        fs = np.linspace(0.9, 1.0, 50) * Fisco * m
+        w = np.array([oracle_mod.taper(TH, x, m) for x in fs])
+        assert np.all(np.diff(w) <= 0)
+
+
+# -------------------------------------------------------------------------------------------
+# Geometry: sky basis and orbits
+# -------------------------------------------------------------------------------------------
+def test_sky_basis_orthonormal(oracle_mod):
+    for lam, bet, psi in ((1.375, -1.2108, 2.659), (4.0, 0.3, 0.1), (0.2, 1.4, 1.9)):
+        th = TH.copy(); th[7], th[8], th[9] = lam, bet, psi
+        k, ep, ec = oracle_mod.sky_basis(th)
+        src = np.array([math.cos(bet) * math.cos(lam), math.cos(bet) * math.sin(lam), math.sin(bet)])
+        np.testing.assert_allclose(k, -src, atol=1e-15)
+        for e in (ep, ec):
+            np.testing.assert_allclose(e, e.T, atol=1e-15)
+            assert abs(np.trace(e)) < 1e-15
+            np.testing.assert_allclose(e @ k, 0, atol=1e-15)
+        assert np.sum(ep * ep) == pytest.approx(2.0, abs=1e-14)
+        assert np.sum(ec * ec) == pytest.approx(2.0, abs=1e-14)
+        assert abs(np.sum(ep * ec)) < 1e-14
+
+
+@pytest.mark.parametrize("det", [W.LISA, W.TAIJI])
+def test_heliocentric_orbit_geometry(oracle_mod, det):
+    AU_S = 499.00478383615643
+    L = det["arm_m"] / C_SI
+    for t in (0.0, 1e6, 1.3e7, -4e8):
+        x = oracle_mod.orbit(det, t)
+        arms = [np.linalg.norm(x[i] - x[j]) for i, j in ((0, 1), (1, 2), (2, 0))]
+        np.testing.assert_allclose(arms, L, rtol=1e-2)
+        alpha = det["alpha0"] + 2 * math.pi * t / 31557600.0
+        c = x.mean(axis=0)
+        np.testing.assert_allclose(c, AU_S * np.array([math.cos(alpha), math.sin(alpha), 0.0]), atol=0.02 * L)
+        nrm = np.cross(x[1] - x[0], x[2] - x[0]); nrm /= np.linalg.norm(nrm)
+        assert abs(nrm[2]) == pytest.approx(0.5, abs=2e-2)       # plane tilted 60 deg to the ecliptic
+        x1 = oracle_mod.orbit(det, t + 31557600.0)
+        np.testing.assert_allclose(x1, x, atol=1e-9 * AU_S)
+
+
+def test_geocentric_orbit_geometry(oracle_mod):
+    det = W.TIANQIN
+    AU_S = 499.00478383615643
+    L = det["arm_m"] / C_SI
+    lon, lat = det["geo_lon"], det["geo_lat"]
+    nhat = np.array([math.cos(lat) * math.cos(lon), math.cos(lat) * math.sin(lon), math.sin(lat)])
+    for t in (0.0, 1e5, 3e6):
+        x = oracle_mod.orbit(det, t)
+        arms = [np.linalg.norm(x[i] - x[j]) for i, j in ((0, 1), (1, 2), (2, 0))]
+        np.testing.assert_allclose(arms, L, rtol=1e-12)
+        alpha = det["alpha0"] + 2 * math.pi * t / 31557600.0
+        np.testing.assert_allclose(x.mean(axis=0), AU_S * np.array([math.cos(alpha), math.sin(alpha), 0.0]),
+                                   atol=1e-11 * AU_S)
+        nrm = np.cross(x[1] - x[0], x[2] - x[0]); nrm /= np.linalg.norm(nrm)
+        np.testing.assert_allclose(nrm, nhat, atol=1e-12)
+        x1 = oracle_mod.orbit(det, t + det["geo_period_s"])
+        np.testing.assert_allclose(x1 - x1.mean(axis=0), x - x.mean(axis=0), atol=1e-9)
+
+
+# -------------------------------------------------------------------------------------------
+# Response
+# -------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("lm", [(2, 2), (3, 3)])
+@pytest.mark.parametrize("rs", [(1, 2), (2, 1), (1, 3), (3, 2)])
+def test_link_sinc_form_equals_time_shift_form(oracle_mod, lm, rs):
+    """Eq. eq_fd_resp is the Fourier transform of Eq. eq_td_resp under h(t - t0) -> e^{-2 pi i f t0}:
+    y~_rs = [e^{-2 pi i f (L + k.x_s)} - e^{-2 pi i f k.x_r}] / (2 (1 - k.n_rs)) n_rs.h~.n_rs."""
+    det = W.LISA
+    L = det["arm_m"] / C_SI
+    bit = W.MODES.index(lm)
+    f = np.geomspace(1e-4, 4e-2, 7)
+    th = TH.copy(); th[0] = 2e5
+    y = oracle_mod.link(det, th, lm[0], lm[1], f, rs[0], rs[1])
+    k, ep, ec = oracle_mod.sky_basis(th)
+    hp, hc = oracle_mod.polarizations(th, 1 << bit, f)
+    _, tf, _ = oracle_mod.mode(th, lm[0], lm[1], f)
+    for i in range(f.size):
+        x = oracle_mod.orbit(det, tf[i])
+        xr, xs = x[rs[0] - 1], x[rs[1] - 1]
+        n = (xr - xs) / np.linalg.norm(xr - xs)
+        nhn = hp[i] * (n @ ep @ n) + hc[i] * (n @ ec @ n)
+        ref = (np.exp(-2j * math.pi * f[i] * (L + k @ xs)) - np.exp(-2j * math.pi * f[i] * (k @ xr))) \
+            / (2 * (1 - k @ n)) * nhn
+        assert abs(y[i] - ref) <= 1e-11 * abs(ref)
+
+
+def test_long_wavelength_limit(oracle_mod):
+    """fL -> 0: X_1.5 -> 2 (2 pi f L)^2 [n13.h.n13 - n12.h.n12] e^{-2 pi i f k.xbar} and
+    X_2.0 -> 4 i (2 pi f L) X_1.5, with relative corrections O(f L)."""
+    det15 = dict(W.LISA, tdi_gen=15)
+    L = det15["arm_m"] / C_SI
+    th = TH.copy()
+    f = np.array([1e-6, 3e-6])
+    x15 = oracle_mod.response_xyz(det15, th, W.MODE_22, f)[0]
+    x20 = oracle_mod.response_xyz(W.LISA, th, W.MODE_22, f)[0]
+    k, ep, ec = oracle_mod.sky_basis(th)
+    hp, hc = oracle_mod.polarizations(th, W.MODE_22, f)
+    _, tf, _ = oracle_mod.mode(th, 2, 2, f)
+    for i in range(f.size):
+        x = oracle_mod.orbit(det15, tf[i])
+        def nhn(a, b):
+            n = (x[a] - x[b]) / np.linalg.norm(x[a] - x[b])
+            return hp[i] * (n @ ep @ n) + hc[i] * (n @ ec @ n)
+        xbar = x.mean(axis=0)
+        ref = 2 * (2 * math.pi * f[i] * L) ** 2 * (nhn(0, 2) - nhn(0, 1)) * np.exp(-2j * math.pi * f[i] * (k @ xbar))
+        eps = 2 * math.pi * f[i] * L
+        assert abs(x15[i] - ref) < 5 * eps * abs(ref)
+        assert abs(x20[i] - 4j * eps * x15[i]) < 5 * eps * abs(x20[i])
+
+
+def test_tdi20_is_tdi15_times_one_minus_z4(oracle_mod):
+    det15 = dict(W.LISA, tdi_gen=15)
+    L = W.LISA["arm_m"] / C_SI
+    f = np.geomspace(1e-4, 4e-2, 11)
+    th = TH.copy(); th[0] = 2e5
+    a = oracle_mod.response_xyz(det15, th, W.MODE_ALL, f)
+    b = oracle_mod.response_xyz(W.LISA, th, W.MODE_ALL, f)
+    z = np.exp(-2j * math.pi * f * L)
+    np.testing.assert_allclose(b, (1 - z ** 4) * a, rtol=1e-12, atol=1e-12 * np.abs(b).max())
+
+
+def test_cyclic_permutation_by_constellation_rotation(oracle_mod):
+    """Rotating the heliocentric constellation by 2 pi/3 relabels spacecraft i -> i+1, so
+    X(rotated) = Y and Y(rotated) = Z: the Y and Z channels are the cyclic permutations of X."""
+    f = np.geomspace(1e-4, 4e-2, 9)
+    th = TH.copy(); th[0] = 3e5
+    rot = dict(W.LISA, cartwheel0=2 * math.pi / 3)
+    a = oracle_mod.response_xyz(W.LISA, th, W.MODE_ALL, f)
+    b = oracle_mod.response_xyz(rot, th, W.MODE_ALL, f)
+    sc = np.abs(a).max()
+    np.testing.assert_allclose(b[0], a[1], atol=1e-11 * sc)
+    np.testing.assert_allclose(b[1], a[2], atol=1e-11 * sc)
+    np.testing.assert_allclose(b[2], a[0], atol=1e-11 * sc)
+
+
+def test_aet_from_xyz_and_t_suppression(oracle_mod):
+    f = np.geomspace(1e-5, 1e-3, 12)
+    th = TH.copy()
+    xyz = oracle_mod.response_xyz(W.LISA, th, W.MODE_ALL, f)
+    aet = oracle_mod.response(W.LISA, th, W.MODE_ALL, f)
+    X, Y, Z = xyz
+    np.testing.assert_allclose(aet[0], (Z - X) / math.sqrt(2), rtol=1e-13, atol=1e-13 * np.abs(X).max())
+    np.testing.assert_allclose(aet[1], (X - 2 * Y + Z) / math.sqrt(6), rtol=1e-13, atol=1e-13 * np.abs(X).max())
+    np.testing.assert_allclose(aet[2], (X + Y + Z) / math.sqrt(3), rtol=1e-13, atol=1e-13 * np.abs(X).max())
+    ratio = np.abs(aet[2]) / np.abs(aet[0])
+    slope = np.polyfit(np.log(f), np.log(ratio), 1)[0]
+    assert slope >= 1.0
+
+
+# -------------------------------------------------------------------------------------------
+# Noise and likelihood
+# -------------------------------------------------------------------------------------------
+def test_psd_aet_is_rotation_of_xyz_covariance(oracle_mod):
+    """S_A, S_E, S_T are the diagonal of the A/E/T rotation of the equal-arm XYZ noise covariance
+    (diagonal S_X = 16 sin^2 x [S_oms + (3 + cos 2x) S_acc], off-diagonal
+    -8 sin^2 x cos x [S_oms + 4 S_acc]); TDI 2.0 multiplies by |1 - z^4|^2."""
+    for det in (W.LISA, W.TIANQIN, dict(W.LISA, tdi_gen=15)):
+        f = np.geomspace(1e-4, 5e-2, 17)
+        S = oracle_mod.psd(det, f)
+        L = det["arm_m"] / C_SI
+        x = 2 * math.pi * f * L
+        Soms = (det["oms_m_rtHz"] * 2 * math.pi * f / C_SI) ** 2
+        Sacc = (det["acc_ms2_rtHz"] / (2 * math.pi * f * C_SI)) ** 2
+        if det.get("psd_shaping", 1):
+            Soms = Soms * (1 + (2e-3 / f) ** 4)
+            Sacc = Sacc * (1 + (0.4e-3 / f) ** 2) * (1 + (f / 8e-3) ** 4)
+        SX = 16 * np.sin(x) ** 2 * (Soms + (3 + np.cos(2 * x)) * Sacc)
+        CXY = -8 * np.sin(x) ** 2 * np.cos(x) * (Soms + 4 * Sacc)
+        R = np.array([[-1 / math.sqrt(2), 0, 1 / math.sqrt(2)],
+                      [1 / math.sqrt(6), -2 / math.sqrt(6), 1 / math.sqrt(6)],
+                      [1 / math.sqrt(3), 1 / math.sqrt(3), 1 / math.sqrt(3)]])
+        fac = np.abs(1 - np.exp(-2j * x) ** 2) ** 2 if det["tdi_gen"] == 20 else np.ones_like(f)
+        for i in range(f.size):
+            Cm = np.full((3, 3), CXY[i]) + np.eye(3) * (SX[i] - CXY[i])
+            Ca = R @ Cm @ R.T * fac[i]
+            # the rotation cancels to O(x^2) in T, so its rounding is relative to S_X
+            np.testing.assert_allclose(np.diag(Ca), S[:, i], rtol=1e-12, atol=1e-13 * SX[i] * fac[i])
+            assert np.abs(Ca - np.diag(np.diag(Ca))).max() < 1e-13 * SX[i] * fac[i]
+
+
+def test_parseval_brute_force_dft(oracle_mod):
+    """White noise of variance sigma^2 at cadence dt has one-sided PSD 2 sigma^2 dt; with the
+    DFT d~_k = dt sum_j n_j e^{-2 pi i jk/N}, sum_j n_j^2/sigma^2 = <d|d> exactly when the series
+    has no DC or Nyquist content (Eq. eq_inner_product, Eq. eq_diag_Sigma_to_Sn)."""
+    N, dt, sigma = 256, 10.0, 1.7e-20
+    rng = np.random.Generator(np.random.PCG64(7))
+    n = rng.standard_normal(N) * sigma
+    j = np.arange(N)
+    n = n - n.mean() - ((-1.0) ** j) * np.mean(n * (-1.0) ** j)
+    T = N * dt
+    ks = np.arange(1, N // 2)
+    dft = np.array([dt * np.sum(n * np.exp(-2j * math.pi * j * k / N)) for k in ks])
+    data = np.stack([dft, dft, dft])
+    psd = np.full((3, ks.size), 2 * sigma ** 2 * dt)
+    D = oracle_mod.Detector(W.LISA, T, 1, ks.size, data, psd)
+    r = oracle_mod.loglike([D], TH, 0)
+    ref = np.sum(n ** 2) / sigma ** 2
+    np.testing.assert_allclose(r["dd"][0], ref, rtol=1e-12)
+    assert r["logl"] == pytest.approx(-1.5 * ref, rel=1e-12)
+
+
+def _single(oracle_mod, normals_seed=None, T=2.0 ** 20, mask=W.MODE_22, det=W.LISA, th=None):
+    k0, nb = W.grid(T)
+    f = (k0 + np.arange(nb)) / T
+    th = TH if th is None else th
+    nrm = None if normals_seed is None else W.normals(nb, normals_seed)
+    d = oracle_mod.make_data(det, th, mask, T, k0, nb, nrm)
+    return oracle_mod.Detector(det, T, k0, nb, d, oracle_mod.psd(det, f))
+
+
+def test_noiseless_injection(oracle_mod):
+    D = _single(oracle_mod, None, mask=W.MODE_ALL)
+    r = oracle_mod.loglike([D], TH, W.MODE_ALL)
+    snr2 = r["hh"].sum()
+    assert snr2 > 1e4
+    assert abs(r["logl"]) < 1e-12 * snr2
+    np.testing.assert_allclose(r["dh"], r["hh"], rtol=1e-13)
+    np.testing.assert_allclose(r["dd"], r["hh"], rtol=1e-13)
+
+
+def test_noise_chi2(oracle_mod):
+    """-1/2 <n|n> per channel has mean -N_b and variance N_b (Re, Im ~ N(0, S T/4))."""
+    T = 2.0 ** 16
+    k0, nb = W.grid(T)
+    th = TH.copy(); th[4] = 1e12          # signal negligible
+    vals = []
+    for seed in range(6):
+        D = _single(oracle_mod, 100 + seed, T=T, th=th)
+        r = oracle_mod.loglike([D], th, W.MODE_22)
+        vals.extend(list(-0.5 * r["dd"][0]))
+    vals = np.array(vals)
+    assert abs(vals.mean() + nb) < 5 * math.sqrt(nb / vals.size)
+    assert vals.var() == pytest.approx(nb, rel=0.8)
+
+
+def test_residual_form_equals_component_form(oracle_mod):
+    D = _single(oracle_mod, 12011, mask=W.MODE_ALL)
+    for dq in (0.0, 1e-3, 0.1):
+        th = TH.copy(); th[1] += dq; th[7] += dq
+        r = oracle_mod.loglike([D], th, W.MODE_ALL)
+        scale = 0.5 * r["dd"].sum() + abs(r["dh"].sum()) + 0.5 * r["hh"].sum()
+        assert abs(r["logl"] - r["logl_resid"]) < 1e-13 * scale
+
+
+# -------------------------------------------------------------------------------------------
+# Gradient and Fisher (Sec. 2.2 and the AD discussion of Sec. 2.3)
+# -------------------------------------------------------------------------------------------
+def test_grad_dl_closed_form(oracle_mod):
+    D = _single(oracle_mod, 12011, mask=W.MODE_ALL)
+    th = TH.copy(); th[0] *= 1.0001; th[10] += 3.0
+    r = oracle_mod.loglike([D], th, W.MODE_ALL)
+    ll, g = oracle_mod.grad([D], th, W.MODE_ALL)
+    assert ll == pytest.approx(r["logl"], rel=1e-14)
+    ref = -(r["dh"].sum() - r["hh"].sum()) / th[4]
+    assert g[4] == pytest.approx(ref, rel=1e-10)
+
+
+def test_fisher_closed_forms(oracle_mod):
+    D = _single(oracle_mod, None, mask=W.MODE_22)
+    F = oracle_mod.fisher([D], TH, W.MODE_22)
+    r = oracle_mod.loglike([D], TH, W.MODE_22)
+    hh = r["hh"].sum()
+    assert F[4, 4] == pytest.approx(hh / TH[4] ** 2, rel=1e-10)
+    assert F[6, 6] == pytest.approx(4 * hh, rel=1e-10)
+    np.testing.assert_allclose(F, F.T, rtol=1e-13, atol=1e-13 * np.abs(F).max())
+    ev = np.linalg.eigvalsh(F / np.sqrt(np.outer(np.diag(F), np.diag(F))))
+    assert ev.min() > -1e-9
+
+
+def test_fisher_equals_jt_w_j(oracle_mod):
+    T = 2.0 ** 18
+    k0, nb = W.grid(T)
+    th = TH.copy(); th[10] = 0.8 * T
+    D = _single(oracle_mod, None, T=T, mask=W.MODE_ALL, th=th)
+    F = oracle_mod.fisher([D], th, W.MODE_ALL)
+    f = (k0 + np.arange(nb)) / T
+    J = oracle_mod.response_jac(W.LISA, th, W.MODE_ALL, f)       # [n][3][2][11]
+    w = 4.0 / (D.psd * T)                                         # [3][n]
+    Fr = np.einsum("cn,ncri,ncrj->ij", w, J, J)
+    np.testing.assert_allclose(F, Fr, rtol=1e-10, atol=1e-12 * np.abs(F).max())
+
+
+def test_drho_diota_symbolic(oracle_mod):
+    """The paper's own derivative check (Fig. fig_nerr_diota): for the (2,2) mode,
+    rho^2(iota) = a ((1+c^2)/2)^2 + b c^2 + e c (1+c^2)/2 with c = cos(iota), so d rho/d iota is
+    known symbolically once a, b, e are fitted from three inclinations; the dual-number gradient
+    must agree to near machine precision and central differences only at a good step."""
+    T = 2.0 ** 20
+    k0, nb = W.grid(T)
+    f = (k0 + np.arange(nb)) / T
+    zero = np.zeros((3, nb), dtype=np.complex128)
+    D = oracle_mod.Detector(W.LISA, T, k0, nb, zero, oracle_mod.psd(W.LISA, f))
+    def rho2(inc):
+        th = TH.copy(); th[5] = inc
+        return -2 * oracle_mod.loglike([D], th, W.MODE_22)["logl"]
+    incs = np.array([0.3, 1.2, 2.2])
+    c = np.cos(incs)
+    A = np.stack([((1 + c ** 2) / 2) ** 2, c ** 2, c * (1 + c ** 2) / 2], axis=1)
+    a, b, e = np.linalg.solve(A, [rho2(i) for i in incs])
+    inc = TH[5]
+    ci, si = math.cos(inc), math.sin(inc)
+    r2 = a * ((1 + ci ** 2) / 2) ** 2 + b * ci ** 2 + e * ci * (1 + ci ** 2) / 2
+    assert rho2(inc) == pytest.approx(r2, rel=1e-11)
+    dr2 = (a * (1 + ci ** 2) * ci + 2 * b * ci + e * ((1 + ci ** 2) / 2 + ci * ci)) * (-si)
+    drho_sd = dr2 / (2 * math.sqrt(r2))
+    ll, g = oracle_mod.grad([D], TH, W.MODE_22)
+    rho = math.sqrt(-2 * ll)
+    drho_ad = -g[5] / rho
+    assert drho_ad == pytest.approx(drho_sd, rel=1e-9)
+    h = 1e-5
+    drho_nd = (math.sqrt(rho2(inc + h)) - math.sqrt(rho2(inc - h))) / (2 * h)
+    assert drho_nd == pytest.approx(drho_sd, rel=1e-6)
+
+
+def test_grad_matches_central_differences(oracle_mod):
+    D = _single(oracle_mod, 12011, mask=W.MODE_ALL, T=2.0 ** 19,
+                th=np.r_[TH[:10], 0.8 * 2.0 ** 19])
+    th = np.r_[TH[:10], 0.8 * 2.0 ** 19]
+    th = th + np.array([1e3, 0.01, 0.02, -0.02, 0.1, 0.01, 0.05, 0.002, 0.002, 0.01, 2.0])
+    ll, g = oracle_mod.grad([D], th, W.MODE_ALL)
+    steps = np.array([1.0, 1e-5, 1e-5, 1e-5, 1e-4, 1e-6, 1e-6, 1e-7, 1e-7, 1e-6, 1e-3])
+    for i in range(11):
+        tp = th.copy(); tp[i] += steps[i]
+        tm = th.copy(); tm[i] -= steps[i]
+        fd = (oracle_mod.loglike([D], tp, W.MODE_ALL)["logl"] - oracle_mod.loglike([D], tm, W.MODE_ALL)["logl"]) \
+            / (2 * steps[i])
+        assert g[i] == pytest.approx(fd, rel=2e-4, abs=1e-6 * np.abs(g).max()), W.PARAM_NAMES[i]
