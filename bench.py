@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the batched MBHB log-likelihood on GB300 (arXiv:2602.12011 likelihood hot path).
+
+Workload (default): one LISA-like detector, modes (2,2) (2,1) (3,3) (3,2) (4,4), TDI 2.0 A/E/T,
+T_obs = 2^22 s (209,296 bins), data = injection + seeded Gaussian noise, a batch of 1024 prior
+samples per GPU. A step is one pe_loglike_batch call over the batch (all rows of the path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank evaluates its own batch (independent
+samples, no data-path collective: weak scaling); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2602_12011_gb300 import workloads as W  # noqa: E402
+
+METRIC = "log-likelihood evals/s (HM, 3 TDI ch, batched) vs plain path; grad evals/s"
+UNIT = "evals/s"
+MSUN_S = 4.925490947641267e-6
+# FP64 operations per active (sample, mode, bin) unit of the fused kernel, FMA counted as 2:
+# (2 x DFMA + DADD + DMUL) thread-instructions per unit, from the ncu SASS counters of the
+# forward kernel (profiles/k_loglike_fwd_lisa_hm_T2^22_B64_ncu_full.md).
+FP64_FLOPS_PER_UNIT = 779.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def active_units(theta: np.ndarray, T: float, k0: int, nb: int, mode_mask: int) -> int:
+    """Active (sample, mode, bin) units: bins of each mode below its taper end m F_isco
+    (odd-m modes vanish for q = 1). Work accounting only."""
+    tot = 0
+    f_lo = k0 / T
+    f_hi = (k0 + nb - 1) / T
+    for th in theta:
+        M = th[0] * MSUN_S
+        fisco = 6 ** -1.5 / (2 * math.pi * M)
+        for bit, (l, m) in enumerate(W.MODES):
+            if not (mode_mask >> bit) & 1:
+                continue
+            if m % 2 == 1 and th[1] == 1.0:
+                continue
+            fe = min(m * fisco, f_hi + 1.0 / T)
+            if fe <= f_lo:
+                continue
+            tot += min(nb, int(math.ceil(fe * T - 1e-9)) - k0)
+    return tot
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self, gpu_index: int):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != gpu_index:
+                    continue
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(dets_spec, theta, mode_mask, n_samples, noise_seed, inj, inj_mask):
+    """The oracle, as it stands, on the host cores: a bounded sample of the same workload."""
+    from oracle import oracle as O
+    O.build()
+    ods = []
+    for det, T, k0, nb in dets_spec:
+        nrm = W.normals(nb, noise_seed)
+        data = O.make_data(det, inj, inj_mask, T, k0, nb, nrm)
+        psd = O.psd(det, (k0 + np.arange(nb)) / T)
+        ods.append(O.Detector(det, T, k0, nb, data, psd))
+    th = theta[:n_samples]
+    cores = O.max_threads()
+    t0 = time.perf_counter()
+    O.loglike_batch(ods, th, mode_mask, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": th.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of the %d-sample batch, all modes, full grid, OpenMP over samples (%.1f s wall)"
+                      % (th.shape[0], theta.shape[0], dt)}
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 CPU oracle on the host cores, each step a bounded sample."""
+    from oracle import oracle as O
+    O.build()
+    dets_spec = wl["dets"]
+    ods = []
+    for det, T, k0, nb in dets_spec:
+        data = O.make_data(det, wl["inj"], wl["inj_mask"], T, k0, nb, W.normals(nb, wl["noise_seed"]))
+        psd = O.psd(det, (k0 + np.arange(nb)) / T)
+        ods.append(O.Detector(det, T, k0, nb, data, psd))
+    n = 32
+    th = wl["theta"][:n]
+    cores = O.max_threads()
+    for _ in range(args.warmup):
+        O.loglike_batch(ods, th[:4], wl["mode_mask"], nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.loglike_batch(ods, th, wl["mode_mask"], nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = n * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["name"], "detectors": "+".join(d[0]["name"] for d in dets_spec),
+                       "modes": "22,21,33,32,44", "batch_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "first %d samples of the %d-sample batch per step" % (n, wl["theta"].shape[0])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = W.batch_hm(args.batch)
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2602_12011_gb300 import build as Bld
+    from paper_2602_12011_gb300 import _lib as L
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    Bld.build()
+    L.lib()
+
+    det, T, k0, nb = wl["dets"][0]
+    mask = wl["mode_mask"]
+    B = args.batch
+    theta = wl["theta"] if rank == 0 else W.draw_prior(B, W.SEED_BATCH_HM + 1000 * rank, T)
+    gd = L.Detector(det, T, k0, nb)
+    gd.inject(wl["inj"], wl["inj_mask"], W.normals(nb, wl["noise_seed"]))
+    hs = [gd.handle]
+
+    stream = torch.cuda.current_stream()
+    th_dev = torch.tensor(theta, device="cuda")
+    out_dev = torch.empty(B, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # 256 MiB > 129 MB L2
+
+    def step():
+        L.pe_loglike_batch(hs, th_dev, B, mask, out_dev, None, None, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K batched steps, L2 flushed before each, device-timed on the stream
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler()
+    time.sleep(0.3)
+    L.pe_profile_read()
+    L.pe_profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    L.pe_profile_enable(False)
+    fwd_ms, fwd_launches = L.pe_profile_read()
+    clk = clocks.stop(local_rank)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = world * B * K / t_total
+    result_ok = bool(torch.isfinite(out_dev).all().item())
+
+    # ---- plain path: one call per sample (B = 1), same samples, device-timed
+    n_plain = 64
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    for i in range(4):
+        L.pe_loglike_batch(hs, th_dev[i:i + 1], 1, mask, out1, None, None, stream)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(n_plain):
+        L.pe_loglike_batch(hs, th_dev[i:i + 1], 1, mask, out1, None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_value = n_plain / (e0.elapsed_time(e1) / 1e3)
+    # the same samples batched, for the like-for-like ratio
+    e0.record(stream)
+    L.pe_loglike_batch(hs, th_dev[:n_plain], n_plain, mask, out_dev[:n_plain], None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_same = n_plain / (e0.elapsed_time(e1) / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of logL
+    th_host = torch.tensor(theta).pin_memory()
+    out_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for k in range(K + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.pe_loglike_batch(hs, th_host, B, mask, out_host, None, None, stream)
+        dt = time.perf_counter() - t0
+        if k > 0:
+            e2e_t.append(dt)
+    e2e_tot = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = world * B * K / e2e_tot
+
+    # ---- roofline of the dominant kernel (fused forward, FP64 ALU bound)
+    units = active_units(theta, T, k0, nb, mask)
+    fwd_avg_s = (fwd_ms / max(fwd_launches, 1)) / 1e3
+    peak = L.pe_measure_fp64_peak(1.0)
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_kind": "measured FP64 FMA, 1 s loop",
+            "kernel": "k_loglike_fwd", "launch_ms": fwd_avg_s * 1e3, "units_per_launch": units,
+            "traffic": None}
+    if FP64_FLOPS_PER_UNIT:
+        ach = FP64_FLOPS_PER_UNIT * units / fwd_avg_s / 1e12
+        roof.update({"achieved": ach, "frac": ach / peak, "flops_per_unit": FP64_FLOPS_PER_UNIT})
+    else:
+        roof.update({"achieved": None, "frac": None, "units_per_s": units / fwd_avg_s})
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_total / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "detectors": "LISA", "modes": "22,21,33,32,44", "T_obs_s": T,
+                       "nbins": nb, "batch_per_gpu": B, "parallelism": "replicas (independent samples per GPU)",
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * 11 * 8),
+                    "d2h_bytes_per_step": int(B * 8)},
+            "plain_path": {"value": plain_value, "unit": UNIT, "samples": n_plain,
+                           "batched_same_samples": batched_same},
+            "gpu_launches": 4 * K,
+            "clocks": clk,
+            "results_finite": result_ok}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl["dets"], theta, mask, 128, wl["noise_seed"], wl["inj"], wl["inj_mask"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gd.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

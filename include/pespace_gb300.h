@@ -1,0 +1,168 @@
+/* pespace_gb300.h -- C ABI of the GB300 (sm_103a) library that evaluates the frequency-domain
+ * Whittle log-likelihood of massive-black-hole-binary signals in the TDI A/E/T channels of
+ * LISA-, Taiji- and TianQin-like detectors (arXiv:2602.12011, Sec. 2).
+ *
+ * Conventions shared by every call
+ *   - Units: masses in solar masses, distances in Gpc, times in seconds, angles in radians,
+ *     frequencies in Hz, strain and TDI outputs in fractional-frequency units.
+ *   - Parameter vector theta[11] (PE_NPARAM), in this order:
+ *       Mtot [Msun], q = m1/m2 >= 1, chi1, chi2 (aligned spins), dL [Gpc], iota, phi_c,
+ *       lambda (ecliptic longitude), beta (ecliptic latitude), psi, t_c [s]
+ *     (the eleven parameters of the paper's Table tab_pe_res, with q inverted to q >= 1).
+ *   - Mode mask bits: 0x01 (2,2), 0x02 (2,1), 0x04 (3,3), 0x08 (3,2), 0x10 (4,4).
+ *   - Frequency grid of a detector: f_k = k / T_obs for k = k0 .. k0 + nbins - 1 (Sec. 3.1:
+ *     numpy.fft.rfftfreq bins truncated to a band).
+ *   - Complex arrays are interleaved (re, im) doubles. Channel-major layouts: [3][nbins][2]
+ *     for A, E, T in that order.
+ *   - Pointers named "may be host or device" are classified with cudaPointerGetAttributes;
+ *     host buffers are copied through the library, device buffers are used in place.
+ *   - Every call is enqueued on the caller's CUDA stream (NULL = the legacy default stream).
+ *     Device outputs are valid once that stream has been synchronised. When an output pointer
+ *     is a host pointer the call synchronises the stream before it returns.
+ *   - Errors are reported by the return status only; pe_last_error() gives a message for the
+ *     calling thread. No call aborts the process or throws across the ABI.
+ *   - A parameter sample outside the domain (non-finite component, q < 1, |chi| >= 1,
+ *     dL <= 0, Mtot outside [1e3, 1e9] Msun) is not an error: its log-likelihood is -inf, its
+ *     gradient is zero, and its bit in the optional status array is set.
+ *   - The library owns all device scratch memory; it is allocated stream-ordered
+ *     (cudaMallocAsync) inside each call and released on the same stream.
+ */
+#ifndef PESPACE_GB300_H
+#define PESPACE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PE_NPARAM 11
+#define PE_MODE_22 0x01u
+#define PE_MODE_21 0x02u
+#define PE_MODE_33 0x04u
+#define PE_MODE_32 0x08u
+#define PE_MODE_44 0x10u
+#define PE_MODE_ALL 0x1Fu
+
+typedef enum {
+  PE_OK = 0,
+  PE_EINVAL = 1,   /* invalid argument (NULL handle, bad size, mode mask, grid mismatch) */
+  PE_ENOMEM = 2,   /* device or host allocation failed */
+  PE_ECUDA = 3,    /* a CUDA runtime call failed */
+  PE_ETIMEOUT = 4, /* a bounded host wait gave up */
+  PE_ESTATE = 5    /* call out of order (e.g. likelihood before data was set) */
+} pe_status;
+
+typedef enum { PE_ORBIT_HELIO = 0, PE_ORBIT_GEO = 1 } pe_orbit_kind;
+
+/* Detector description (Sec. 2.1 response model; Sec. 3.2 orbits and noise).
+ *   orbit        PE_ORBIT_HELIO: Keplerian heliocentric constellation to first order in the
+ *                eccentricity (LISA, Taiji); PE_ORBIT_GEO: equilateral triangle of radius
+ *                arm/sqrt(3) around a circular-orbit Earth (TianQin).
+ *   tdi_gen      15 or 20: FD TDI generation 1.5 or 2.0 (Sec. 2.1, after Eq. eq_tf).
+ *   psd_shaping  1: apply the LISA-type low/high-frequency shaping factors to the noise.
+ *   arm_m        nominal arm length L [m]; alpha0_rad initial revolution angle around the Sun;
+ *   cartwheel0_rad initial constellation orientation (heliocentric only);
+ *   geo_period_s, geo_lon_rad, geo_lat_rad: TianQin constellation period and normal direction.
+ *   oms_m_rtHz, acc_ms2_rtHz: optical-metrology and test-mass acceleration noise levels. */
+typedef struct {
+  int32_t orbit;
+  int32_t tdi_gen;
+  int32_t psd_shaping;
+  int32_t reserved;
+  double arm_m;
+  double alpha0_rad;
+  double cartwheel0_rad;
+  double geo_period_s;
+  double geo_lon_rad;
+  double geo_lat_rad;
+  double oms_m_rtHz;
+  double acc_ms2_rtHz;
+} pe_detector_config;
+
+typedef struct pe_detector_s* pe_detector; /* opaque; owned by the library */
+
+/* Create a detector on the current CUDA device with the grid f_k = k/T_obs,
+ * k in [k0, k0 + nbins). Allocates the per-bin device tables (about 150 bytes per bin).
+ * Errors: PE_EINVAL for a NULL cfg/out, nbins < 1, k0 < 1, T_obs <= 0, tdi_gen not 15/20,
+ * orbit not 0/1, arm_m <= 0; PE_ENOMEM; PE_ECUDA. */
+pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_t k0, int64_t nbins,
+                             pe_detector* out);
+
+/* Free the detector and its device memory (synchronises the device first). NULL is a no-op. */
+pe_status pe_destroy_detector(pe_detector det);
+
+/* Analytic noise PSD of A, E, T on the detector grid (Sec. 3.2: acceleration + OMS noise only,
+ * equal-arm TDI, times |1 - z^4|^2 for TDI 2.0). out_psd: HOST array [3][nbins]. */
+pe_status pe_psd_model(pe_detector det, double* out_psd);
+
+/* Set the data and PSD the likelihood uses (Eq. eq_ll_fd, Eq. eq_inner_product). The library
+ * copies both, builds the whitened per-bin tables and <d|d> per channel.
+ *   data_aet: [3][nbins][2] complex data d~_c(f_k) (host or device);
+ *   psd_aet:  [3][nbins] one-sided PSD S_c(f_k) (host or device), or NULL for pe_psd_model's;
+ *   ptr_is_device: 1 if both pointers are device pointers, 0 if host.
+ * Synchronous. Errors: PE_EINVAL (NULL det/data, non-positive or non-finite PSD value). */
+pe_status pe_set_data_psd(pe_detector det, const double* data_aet, const double* psd_aet, int ptr_is_device);
+
+/* <d|d> per channel (after pe_set_data_psd). out_dd: host double[3]. */
+pe_status pe_data_norm(pe_detector det, double* out_dd);
+
+/* Noise-free signal h~_c(f_k) of one source in the A, E, T channels on the detector grid:
+ * TaylorF2 modes (SPA, time-frequency map Eq. eq_tf), single-link response Eq. eq_fd_resp at
+ * t_f, FD TDI and A/E/T (Sec. 2.1). theta: [11] (host or device); out: [3][nbins][2]
+ * (host or device). Out-of-domain theta gives PE_EINVAL. */
+pe_status pe_signal_aet(pe_detector det, const double* theta, unsigned mode_mask, double* out, void* stream);
+
+/* Data = noise-free signal of theta_inj + noise with Re, Im ~ N(0, S_c T/4) (Eq.
+ * eq_diag_Sigma_to_Sn), using the detector's analytic PSD, then pe_set_data_psd(data, NULL).
+ * normals: HOST [3][nbins][2] standard-normal draws supplied by the caller, or NULL for
+ * noise-free data. Synchronous. */
+pe_status pe_inject(pe_detector det, const double* theta_inj, unsigned mode_mask, const double* normals);
+
+/* Batched joint log-likelihood over ndet detectors and the A/E/T channels (Eq. eq_ll_fd with
+ * the joint product over channels and detectors, Sec. 2.2):
+ *   logL_s = sum_I sum_c ( <d|h>_{I,c} - 1/2 <h|h>_{I,c} - 1/2 <d|d>_{I,c} ).
+ *   dets[ndet]: detector handles, each with data set; 1 <= ndet <= 8.
+ *   theta: [B][11] (host or device), 1 <= B <= 1048576.
+ *   out_logl: [B] (host or device).
+ *   out_dhhh: nullable [B][ndet][3][2] = (<d|h>, <h|h>) per detector and channel.
+ *   out_status: nullable int32 [B]; bit 0 = sample out of domain.
+ * Samples are independent: each sample's result depends only on its own theta (fixed-order
+ * reductions), so it is identical in any batch. Errors: PE_EINVAL, PE_ESTATE, PE_ENOMEM, PE_ECUDA. */
+pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
+                           double* out_logl, double* out_dhhh, int32_t* out_status, void* stream);
+
+/* Batched gradient d logL_s / d theta_s (hand-written adjoint of the same path, Sec. 2.3 on
+ * automatic differentiation); arguments as pe_loglike_batch, plus out_grad [B][11]
+ * (host or device). out_logl may be NULL. */
+pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
+                                double* out_logl, double* out_grad, int32_t* out_status, void* stream);
+
+/* Fisher matrix F_ij = <d h/d theta_i | d h/d theta_j> summed over detectors and channels
+ * (Sec. 2.2, the equation after Eq. eq_ll_fisher), for B parameter points.
+ * theta: [B][11] (host or device); out_F: [B][11][11] row-major (host or device). */
+pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
+                    double* out_F, void* stream);
+
+/* ---- Measurement helpers (no counterpart in the paper; used by the benchmark) ----------------
+ * pe_profile_enable(1) makes the library record a CUDA event pair, on the call's stream, around
+ * every launch of its fused per-bin kernels (log-likelihood forward, gradient, Fisher);
+ * pe_profile_read waits for those events, returns the summed device time [ms] and the number of
+ * launches since the previous read, and clears the record. pe_profile_enable(0) stops recording.
+ * pe_measure_fp64_peak runs an FP64 fused-multiply-add throughput kernel (8 independent chains
+ * per thread, one grid of 8 CTAs of 256 threads per SM) for about `seconds` and returns the
+ * achieved FP64 rate in TFLOP/s (one FMA = 2 flops): the ALU roofline of the FP64 kernels. */
+pe_status pe_profile_enable(int on);
+pe_status pe_profile_read(double* total_ms, int64_t* launches);
+pe_status pe_measure_fp64_peak(double seconds, double* out_tflops);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char* pe_last_error(void);
+
+/* Library ABI version (increments on incompatible change). */
+int pe_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PESPACE_GB300_H */

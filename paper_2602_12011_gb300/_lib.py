@@ -1,0 +1,266 @@
+"""ctypes binding of libpespace_gb300.so (include/pespace_gb300.h).
+
+Argument marshalling only: every computation runs in the library's CUDA kernels. The functions
+carry the ABI's names. Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+a CUDA tensor's data pointer is passed straight to the library, which works on it in place.
+Importing this module does not load the library; the first call does, and it raises if the
+library has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpespace_gb300.so")
+
+PE_OK, PE_EINVAL, PE_ENOMEM, PE_ECUDA, PE_ETIMEOUT, PE_ESTATE = range(6)
+STATUS_NAMES = {0: "PE_OK", 1: "PE_EINVAL", 2: "PE_ENOMEM", 3: "PE_ECUDA", 4: "PE_ETIMEOUT", 5: "PE_ESTATE"}
+NPARAM = 11
+
+
+class PeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class DetectorConfig(C.Structure):
+    _fields_ = [
+        ("orbit", C.c_int32), ("tdi_gen", C.c_int32), ("psd_shaping", C.c_int32), ("reserved", C.c_int32),
+        ("arm_m", C.c_double), ("alpha0_rad", C.c_double), ("cartwheel0_rad", C.c_double),
+        ("geo_period_s", C.c_double), ("geo_lon_rad", C.c_double), ("geo_lat_rad", C.c_double),
+        ("oms_m_rtHz", C.c_double), ("acc_ms2_rtHz", C.c_double),
+    ]
+
+
+def config_from_dict(d: dict) -> DetectorConfig:
+    c = DetectorConfig()
+    c.orbit = int(d["orbit"])
+    c.tdi_gen = int(d.get("tdi_gen", 20))
+    c.psd_shaping = int(d.get("psd_shaping", 1))
+    c.arm_m = float(d["arm_m"])
+    c.alpha0_rad = float(d.get("alpha0", 0.0))
+    c.cartwheel0_rad = float(d.get("cartwheel0", 0.0))
+    c.geo_period_s = float(d.get("geo_period_s", 0.0))
+    c.geo_lon_rad = float(d.get("geo_lon", 0.0))
+    c.geo_lat_rad = float(d.get("geo_lat", 0.0))
+    c.oms_m_rtHz = float(d["oms_m_rtHz"])
+    c.acc_ms2_rtHz = float(d["acc_ms2_rtHz"])
+    return c
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpespace_gb300.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        L.pe_abi_version.restype = C.c_int
+        L.pe_last_error.restype = C.c_char_p
+        L.pe_create_detector.argtypes = [C.POINTER(DetectorConfig), C.c_double, C.c_int64, C.c_int64, C.POINTER(_P)]
+        L.pe_destroy_detector.argtypes = [_P]
+        L.pe_psd_model.argtypes = [_P, _P]
+        L.pe_set_data_psd.argtypes = [_P, _P, _P, C.c_int]
+        L.pe_data_norm.argtypes = [_P, _P]
+        L.pe_signal_aet.argtypes = [_P, _P, C.c_uint, _P, _P]
+        L.pe_inject.argtypes = [_P, _P, C.c_uint, _P]
+        L.pe_loglike_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+        L.pe_loglike_grad_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+        L.pe_fisher.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P]
+        L.pe_profile_enable.argtypes = [C.c_int]
+        L.pe_profile_read.argtypes = [_P, _P]
+        L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
+        for name in ("pe_profile_enable", "pe_profile_read", "pe_measure_fp64_peak", "pe_create_detector", "pe_destroy_detector", "pe_psd_model", "pe_set_data_psd", "pe_data_norm",
+                     "pe_signal_aet", "pe_inject", "pe_loglike_batch", "pe_loglike_grad_batch", "pe_fisher"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != PE_OK:
+        raise PeError(st, lib().pe_last_error().decode())
+
+
+def _ptr(a):
+    """Raw data pointer of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or torch tensor, got %r" % type(a))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- ABI functions (same names) --------------------------------------------------------------
+def pe_abi_version() -> int:
+    return lib().pe_abi_version()
+
+
+def pe_create_detector(cfg: dict, T_obs: float, k0: int, nbins: int) -> int:
+    h = _P()
+    c = config_from_dict(cfg)
+    _check(lib().pe_create_detector(C.byref(c), float(T_obs), int(k0), int(nbins), C.byref(h)))
+    return h.value
+
+
+def pe_destroy_detector(h: int):
+    _check(lib().pe_destroy_detector(h))
+
+
+def pe_psd_model(h: int, out):
+    _check(lib().pe_psd_model(h, _ptr(out)))
+
+
+def pe_set_data_psd(h: int, data, psd=None, ptr_is_device: bool = False):
+    _check(lib().pe_set_data_psd(h, _ptr(data), _ptr(psd), int(bool(ptr_is_device))))
+
+
+def pe_data_norm(h: int, out):
+    _check(lib().pe_data_norm(h, _ptr(out)))
+
+
+def pe_signal_aet(h: int, theta, mode_mask: int, out, stream=None):
+    _check(lib().pe_signal_aet(h, _ptr(theta), int(mode_mask), _ptr(out), _stream(stream)))
+
+
+def pe_inject(h: int, theta, mode_mask: int, normals=None):
+    _check(lib().pe_inject(h, _ptr(theta), int(mode_mask), _ptr(normals)))
+
+
+def _handles(hs):
+    arr = (_P * len(hs))(*hs)
+    return arr
+
+
+def pe_loglike_batch(hs, theta, B: int, mode_mask: int, out_logl, out_dhhh=None, out_status=None, stream=None):
+    _check(lib().pe_loglike_batch(_handles(hs), len(hs), _ptr(theta), int(B), int(mode_mask), _ptr(out_logl),
+                                  _ptr(out_dhhh), _ptr(out_status), _stream(stream)))
+
+
+def pe_loglike_grad_batch(hs, theta, B: int, mode_mask: int, out_logl, out_grad, out_status=None, stream=None):
+    _check(lib().pe_loglike_grad_batch(_handles(hs), len(hs), _ptr(theta), int(B), int(mode_mask), _ptr(out_logl),
+                                       _ptr(out_grad), _ptr(out_status), _stream(stream)))
+
+
+def pe_fisher(hs, theta, B: int, mode_mask: int, out_F, stream=None):
+    _check(lib().pe_fisher(_handles(hs), len(hs), _ptr(theta), int(B), int(mode_mask), _ptr(out_F),
+                           _stream(stream)))
+
+
+def pe_profile_enable(on: bool):
+    _check(lib().pe_profile_enable(int(bool(on))))
+
+
+def pe_profile_read():
+    """(summed device ms, launches) of the fused kernels since the previous read."""
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(lib().pe_profile_read(C.addressof(ms), C.addressof(n)))
+    return ms.value, n.value
+
+
+def pe_measure_fp64_peak(seconds: float = 1.0) -> float:
+    t = C.c_double()
+    _check(lib().pe_measure_fp64_peak(float(seconds), C.addressof(t)))
+    return t.value
+
+
+# ---- convenience object ------------------------------------------------------------------------
+class Detector:
+    """One detector handle with its grid f_k = k/T, k in [k0, k0 + nbins)."""
+
+    def __init__(self, cfg: dict, T_obs: float, k0: int, nbins: int):
+        self.cfg, self.T, self.k0, self.nb = dict(cfg), float(T_obs), int(k0), int(nbins)
+        self.handle = pe_create_detector(cfg, T_obs, k0, nbins)
+
+    def close(self):
+        if self.handle:
+            pe_destroy_detector(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def psd(self) -> np.ndarray:
+        out = np.zeros((3, self.nb))
+        pe_psd_model(self.handle, out)
+        return out
+
+    def set_data(self, data, psd=None):
+        """data: complex [3][nb] (numpy) or a device tensor of float64 [3][nb][2]."""
+        if isinstance(data, np.ndarray):
+            d = np.ascontiguousarray(data.astype(np.complex128).reshape(3, self.nb))
+            p = None if psd is None else np.ascontiguousarray(np.asarray(psd, dtype=np.float64).reshape(3, self.nb))
+            pe_set_data_psd(self.handle, d, p, False)
+        else:
+            pe_set_data_psd(self.handle, data, psd, True)
+
+    def inject(self, theta, mode_mask: int, normals=None):
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        n = None if normals is None else np.ascontiguousarray(np.asarray(normals, dtype=np.float64))
+        pe_inject(self.handle, th, mode_mask, n)
+
+    def data_norm(self) -> np.ndarray:
+        out = np.zeros(3)
+        pe_data_norm(self.handle, out)
+        return out
+
+    def signal(self, theta, mode_mask: int) -> np.ndarray:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        out = np.zeros((3, self.nb), dtype=np.complex128)
+        pe_signal_aet(self.handle, th, mode_mask, out)
+        return out
+
+
+def loglike(dets, theta, mode_mask: int, dhhh: bool = False, status: bool = False, stream=None):
+    """Batched joint log-likelihood. theta: numpy [B][11] (host path) or CUDA tensor [B][11]
+    (device path, outputs are CUDA tensors on the same stream)."""
+    hs = [d.handle for d in dets]
+    if isinstance(theta, np.ndarray):
+        th = np.ascontiguousarray(theta.reshape(-1, NPARAM).astype(np.float64))
+        B = th.shape[0]
+        out = np.zeros(B)
+        dh = np.zeros((B, len(dets), 3, 2)) if dhhh else None
+        stt = np.zeros(B, dtype=np.int32) if status else None
+        pe_loglike_batch(hs, th, B, mode_mask, out, dh, stt, stream)
+    else:
+        import torch
+        th = theta.reshape(-1, NPARAM).contiguous()
+        B = th.shape[0]
+        out = torch.empty(B, dtype=torch.float64, device=th.device)
+        dh = torch.empty((B, len(dets), 3, 2), dtype=torch.float64, device=th.device) if dhhh else None
+        stt = torch.empty(B, dtype=torch.int32, device=th.device) if status else None
+        if stream is None:
+            stream = torch.cuda.current_stream(th.device)
+        pe_loglike_batch(hs, th, B, mode_mask, out, dh, stt, stream)
+    res = {"logl": out}
+    if dhhh:
+        res["dhhh"] = dh
+    if status:
+        res["status"] = stt
+    return res

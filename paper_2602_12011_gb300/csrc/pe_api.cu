@@ -1,0 +1,443 @@
+// pe_api.cu -- host implementation of the C ABI in include/pespace_gb300.h: detector handles,
+// argument validation, pointer-kind handling, stream-ordered scratch and kernel launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pe_internal.h"
+#include "pe_kernels.h"
+#include "pe_measure.h"
+#include "pespace_gb300.h"
+
+struct pe_detector_s {
+  int device;
+  pe_detector_config cfg;
+  double T;
+  long long k0;
+  int nb;
+  void* mem;           // one allocation for every per-bin table
+  double* f;
+  double* f13;
+  double* fm13;
+  double* lnf3;
+  double* fm76;
+  double2* sca;
+  double2* z;
+  double2* dg;
+  double* gg;
+  double* psd_model;   // [3][nb] analytic PSD
+  double* dd_dev;      // [3]
+  double dd[3];
+  int has_data;
+  pe::DetDev dev;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+pe_status fail(pe_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define PE_CUDA(call)                                                                             \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(PE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+std::once_flag g_pool_once;
+void setup_pool() {
+  std::call_once(g_pool_once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      unsigned long long thr = ~0ull;  // keep freed blocks cached in the pool
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
+}
+
+// Stream-ordered scratch for one call: every buffer is released on the call's stream.
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> bufs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  ~Scratch() {
+    for (void* p : bufs) cudaFreeAsync(p, st);
+  }
+  template <class T>
+  cudaError_t alloc(T** p, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, n * sizeof(T) + 16, st);
+    if (e != cudaSuccess) return e;
+    bufs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+};
+
+double det_arm_s(const pe_detector_config& c) { return c.arm_m / pe::kC; }
+
+void fill_dev(pe_detector_s* d) {
+  pe::DetDev& D = d->dev;
+  memset(&D, 0, sizeof(D));
+  const pe_detector_config& c = d->cfg;
+  D.T = d->T;
+  D.k0 = d->k0;
+  D.nb = d->nb;
+  D.orbit = c.orbit;
+  D.tdi_gen = c.tdi_gen;
+  D.L = det_arm_s(c);
+  D.R = pe::kAuS;
+  D.alpha0_ht = c.alpha0_rad / pe::kPi;
+  D.rate_ht = 2.0 / pe::kYearS;
+  if (c.orbit == PE_ORBIT_HELIO) {
+    const double e = D.L / (2.0 * std::sqrt(3.0) * D.R);
+    D.eRh = 0.5 * e * D.R;
+    D.eR3h = 1.5 * e * D.R;
+    D.eRs3 = std::sqrt(3.0) * e * D.R;
+    for (int i = 0; i < 3; ++i) {
+      const double b = 2.0 * pe::kPi * i / 3.0 + c.cartwheel0_rad;
+      D.cb[i] = std::cos(b);
+      D.sb[i] = std::sin(b);
+    }
+  } else {
+    D.rgeo = D.L / std::sqrt(3.0);
+    D.geo_rate_ht = 2.0 / c.geo_period_s;
+    const double nl = c.geo_lon_rad, nbt = c.geo_lat_rad;
+    const double n[3] = {std::cos(nbt) * std::cos(nl), std::cos(nbt) * std::sin(nl), std::sin(nbt)};
+    D.e1[0] = -std::sin(nl); D.e1[1] = std::cos(nl); D.e1[2] = 0.0;
+    D.e2[0] = n[1] * D.e1[2] - n[2] * D.e1[1];
+    D.e2[1] = n[2] * D.e1[0] - n[0] * D.e1[2];
+    D.e2[2] = n[0] * D.e1[1] - n[1] * D.e1[0];
+  }
+  D.f = d->f; D.f13 = d->f13; D.fm13 = d->fm13; D.lnf3 = d->lnf3; D.fm76 = d->fm76;
+  D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev;
+}
+
+pe_status check_dets(const pe_detector* dets, int ndet, pe::DetSet* ds) {
+  if (dets == nullptr) return fail(PE_EINVAL, "dets is NULL");
+  if (ndet < 1 || ndet > pe::kMaxDet) return fail(PE_EINVAL, "ndet=%d outside [1, %d]", ndet, pe::kMaxDet);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(PE_ECUDA, "no CUDA device"); }
+  memset(ds, 0, sizeof(*ds));
+  ds->ndet = ndet;
+  for (int i = 0; i < ndet; ++i) {
+    if (dets[i] == nullptr) return fail(PE_EINVAL, "dets[%d] is NULL", i);
+    if (!dets[i]->has_data) return fail(PE_ESTATE, "dets[%d] has no data (call pe_set_data_psd first)", i);
+    if (dets[i]->device != dev) return fail(PE_EINVAL, "dets[%d] lives on device %d, current is %d", i, dets[i]->device, dev);
+    ds->d[i] = dets[i]->dev;
+  }
+  return PE_OK;
+}
+
+int g_sm_count = 0;
+int sm_count() {
+  if (g_sm_count == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sm_count <= 0) g_sm_count = 1;
+  }
+  return g_sm_count;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pe_abi_version(void) { return 1; }
+
+const char* pe_last_error(void) { return g_err.c_str(); }
+
+pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_t k0, int64_t nbins, pe_detector* out) {
+  if (cfg == nullptr || out == nullptr) return fail(PE_EINVAL, "cfg/out is NULL");
+  *out = nullptr;
+  if (!(T_obs > 0.0) || !std::isfinite(T_obs)) return fail(PE_EINVAL, "T_obs must be positive");
+  if (k0 < 1) return fail(PE_EINVAL, "k0 must be >= 1 (no DC bin)");
+  if (nbins < 1 || nbins > (1 << 26)) return fail(PE_EINVAL, "nbins=%lld outside [1, 2^26]", (long long)nbins);
+  if (cfg->orbit != PE_ORBIT_HELIO && cfg->orbit != PE_ORBIT_GEO) return fail(PE_EINVAL, "orbit must be 0 or 1");
+  if (cfg->tdi_gen != 15 && cfg->tdi_gen != 20) return fail(PE_EINVAL, "tdi_gen must be 15 or 20");
+  if (!(cfg->arm_m > 0.0)) return fail(PE_EINVAL, "arm_m must be positive");
+  if (cfg->orbit == PE_ORBIT_GEO && !(cfg->geo_period_s > 0.0)) return fail(PE_EINVAL, "geo_period_s must be positive");
+  setup_pool();
+  pe_detector_s* d = new (std::nothrow) pe_detector_s();
+  if (!d) return fail(PE_ENOMEM, "host allocation failed");
+  if (cudaGetDevice(&d->device) != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ECUDA, "no CUDA device"); }
+  d->cfg = *cfg;
+  d->T = T_obs;
+  d->k0 = k0;
+  d->nb = (int)nbins;
+  const size_t nb = (size_t)nbins;
+  // doubles: f, f13, fm13, lnf3, fm76 (5 nb) + gg (3 nb) + psd_model (3 nb) + dd (3, padded);
+  // double2: sca, z (2 nb) + dg (3 nb)
+  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb;
+  const size_t bytes = n_d * sizeof(double) + n_d2 * sizeof(double2);
+  cudaError_t e = cudaMalloc(&d->mem, bytes);
+  if (e != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ENOMEM, "cudaMalloc(%zu) failed", bytes); }
+  double2* p2 = static_cast<double2*>(d->mem);
+  d->sca = p2; p2 += nb;
+  d->z = p2; p2 += nb;
+  d->dg = p2; p2 += 3 * nb;
+  double* p = reinterpret_cast<double*>(p2);
+  d->f = p; p += nb;
+  d->f13 = p; p += nb;
+  d->fm13 = p; p += nb;
+  d->lnf3 = p; p += nb;
+  d->fm76 = p; p += nb;
+  d->gg = p; p += 3 * nb;
+  d->psd_model = p; p += 3 * nb;
+  d->dd_dev = p;
+  fill_dev(d);
+  const double L = det_arm_s(*cfg);
+  if ((e = pe::launch_grid_tables(T_obs, k0, d->nb, L, d->f, d->f13, d->fm13, d->lnf3, d->fm76, d->sca, d->z, 0)) !=
+          cudaSuccess ||
+      (e = pe::launch_psd_model(d->f, d->nb, L, cfg->oms_m_rtHz, cfg->acc_ms2_rtHz, cfg->psd_shaping, cfg->tdi_gen,
+                                d->psd_model, 0)) != cudaSuccess ||
+      (e = cudaMemset(d->dd_dev, 0, 3 * sizeof(double))) != cudaSuccess ||
+      (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d->mem);
+    delete d;
+    return fail(PE_ECUDA, "detector table set-up failed: %s", cudaGetErrorString(e));
+  }
+  *out = d;
+  return PE_OK;
+}
+
+pe_status pe_destroy_detector(pe_detector det) {
+  if (det == nullptr) return PE_OK;
+  cudaDeviceSynchronize();
+  cudaFree(det->mem);
+  cudaGetLastError();
+  delete det;
+  return PE_OK;
+}
+
+pe_status pe_psd_model(pe_detector det, double* out_psd) {
+  if (det == nullptr || out_psd == nullptr) return fail(PE_EINVAL, "det/out_psd is NULL");
+  PE_CUDA(cudaMemcpy(out_psd, det->psd_model, 3 * (size_t)det->nb * sizeof(double), cudaMemcpyDeviceToHost));
+  return PE_OK;
+}
+
+pe_status pe_data_norm(pe_detector det, double* out_dd) {
+  if (det == nullptr || out_dd == nullptr) return fail(PE_EINVAL, "det/out_dd is NULL");
+  if (!det->has_data) return fail(PE_ESTATE, "no data set");
+  for (int c = 0; c < 3; ++c) out_dd[c] = det->dd[c];
+  return PE_OK;
+}
+
+static pe_status set_data_device(pe_detector det, const double2* data_dev, const double* psd_dev) {
+  const int nb = det->nb;
+  double* parts = nullptr;
+  int* bad = nullptr;
+  const int nblk = (nb + pe::kTileBins - 1) / pe::kTileBins;
+  PE_CUDA(cudaMalloc(&parts, (size_t)nblk * 3 * sizeof(double)));
+  if (cudaMalloc(&bad, sizeof(int)) != cudaSuccess) { cudaFree(parts); return fail(PE_ENOMEM, "cudaMalloc failed"); }
+  cudaMemset(bad, 0, sizeof(int));
+  int g = 0;
+  const double L = det_arm_s(det->cfg);
+  cudaError_t e = pe::launch_data_tables(det->f, det->sca, det->z, nb, det->T, L, det->cfg.tdi_gen, data_dev,
+                                         psd_dev ? psd_dev : det->psd_model, det->dg, det->gg, parts, bad, &g, 0);
+  if (e == cudaSuccess) e = pe::launch_sum_parts(parts, g, 3, det->dd_dev, 0);
+  int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(det->dd, det->dd_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(parts);
+  cudaFree(bad);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(PE_ECUDA, "data tables: %s", cudaGetErrorString(e)); }
+  if (hbad) { det->has_data = 0; return fail(PE_EINVAL, "PSD has a non-positive or non-finite value"); }
+  det->has_data = 1;
+  return PE_OK;
+}
+
+pe_status pe_set_data_psd(pe_detector det, const double* data_aet, const double* psd_aet, int ptr_is_device) {
+  if (det == nullptr || data_aet == nullptr) return fail(PE_EINVAL, "det/data is NULL");
+  const size_t nb = (size_t)det->nb;
+  if (ptr_is_device) return set_data_device(det, reinterpret_cast<const double2*>(data_aet), psd_aet);
+  double2* dd = nullptr;
+  double* pd = nullptr;
+  PE_CUDA(cudaMalloc(&dd, 3 * nb * sizeof(double2)));
+  if (psd_aet && cudaMalloc(&pd, 3 * nb * sizeof(double)) != cudaSuccess) {
+    cudaFree(dd);
+    return fail(PE_ENOMEM, "cudaMalloc failed");
+  }
+  cudaError_t e = cudaMemcpy(dd, data_aet, 3 * nb * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && psd_aet) e = cudaMemcpy(pd, psd_aet, 3 * nb * sizeof(double), cudaMemcpyHostToDevice);
+  pe_status st = PE_OK;
+  if (e != cudaSuccess) st = fail(PE_ECUDA, "upload failed: %s", cudaGetErrorString(e));
+  else st = set_data_device(det, dd, pd);
+  cudaFree(dd);
+  if (pd) cudaFree(pd);
+  return st;
+}
+
+static pe_status signal_device(pe_detector det, const double* theta, unsigned mode_mask, double2* out_dev,
+                               cudaStream_t st) {
+  Scratch sc(st);
+  double* th = nullptr;
+  pe::SampleCoef* coef = nullptr;
+  int* nend = nullptr;
+  int* status = nullptr;
+  PE_CUDA(sc.alloc(&coef, 1));
+  PE_CUDA(sc.alloc(&nend, 1));
+  PE_CUDA(sc.alloc(&status, 1));
+  if (is_device_ptr(theta)) {
+    th = const_cast<double*>(theta);
+  } else {
+    for (int i = 0; i < PE_NPARAM; ++i)
+      if (!std::isfinite(theta[i])) return fail(PE_EINVAL, "theta[%d] is not finite", i);
+    PE_CUDA(sc.alloc(&th, PE_NPARAM));
+    PE_CUDA(cudaMemcpyAsync(th, theta, PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  pe::DetSet ds;
+  memset(&ds, 0, sizeof(ds));
+  ds.ndet = 1;
+  ds.d[0] = det->dev;
+  PE_CUDA(pe::launch_prep(th, 1, mode_mask, ds, coef, nend, status, st));
+  PE_CUDA(pe::launch_signal(det->dev, coef, out_dev, st));
+  int hs = 0;
+  PE_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PE_CUDA(cudaStreamSynchronize(st));
+  if (hs) return fail(PE_EINVAL, "theta is outside the parameter domain");
+  return PE_OK;
+}
+
+pe_status pe_signal_aet(pe_detector det, const double* theta, unsigned mode_mask, double* out, void* stream) {
+  if (det == nullptr || theta == nullptr || out == nullptr) return fail(PE_EINVAL, "det/theta/out is NULL");
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (is_device_ptr(out)) return signal_device(det, theta, mode_mask, reinterpret_cast<double2*>(out), st);
+  double2* tmp = nullptr;
+  const size_t n = 3 * (size_t)det->nb;
+  PE_CUDA(cudaMalloc(&tmp, n * sizeof(double2)));
+  pe_status s = signal_device(det, theta, mode_mask, tmp, st);
+  if (s == PE_OK) {
+    cudaError_t e = cudaMemcpy(out, tmp, n * sizeof(double2), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = fail(PE_ECUDA, "download failed: %s", cudaGetErrorString(e));
+  }
+  cudaFree(tmp);
+  return s;
+}
+
+pe_status pe_inject(pe_detector det, const double* theta_inj, unsigned mode_mask, const double* normals) {
+  if (det == nullptr || theta_inj == nullptr) return fail(PE_EINVAL, "det/theta is NULL");
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  const size_t n = 3 * (size_t)det->nb;
+  double2* h = nullptr;
+  double2* nd = nullptr;
+  PE_CUDA(cudaMalloc(&h, n * sizeof(double2)));
+  pe_status s = signal_device(det, theta_inj, mode_mask, h, 0);
+  if (s == PE_OK && normals) {
+    cudaError_t e = cudaMalloc(&nd, n * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpy(nd, normals, n * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = pe::launch_inject(det->nb, det->T, det->psd_model, nd, h, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { cudaGetLastError(); s = fail(PE_ECUDA, "noise injection failed: %s", cudaGetErrorString(e)); }
+  }
+  if (s == PE_OK) s = set_data_device(det, h, nullptr);
+  cudaFree(h);
+  if (nd) cudaFree(nd);
+  return s;
+}
+
+pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
+                           double* out_logl, double* out_dhhh, int32_t* out_status, void* stream) {
+  pe::DetSet ds;
+  pe_status s0 = check_dets(dets, ndet, &ds);
+  if (s0 != PE_OK) return s0;
+  if (theta == nullptr || out_logl == nullptr) return fail(PE_EINVAL, "theta/out_logl is NULL");
+  if (B < 1 || B > (1 << 20)) return fail(PE_EINVAL, "B=%d outside [1, 2^20]", B);
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch sc(st);
+  const int P = ndet * B;
+  long long max_tiles = 0;
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * ((ds.d[i].nb + pe::kTileBins - 1) / pe::kTileBins);
+  const double* th = theta;
+  if (!is_device_ptr(theta)) {
+    double* t = nullptr;
+    PE_CUDA(sc.alloc(&t, (size_t)B * PE_NPARAM));
+    PE_CUDA(cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+    th = t;
+  }
+  pe::SampleCoef* coef = nullptr;
+  int* nend = nullptr;
+  long long* off = nullptr;
+  double* part = nullptr;
+  PE_CUDA(sc.alloc(&coef, B));
+  PE_CUDA(sc.alloc(&nend, P));
+  PE_CUDA(sc.alloc(&off, P + 1));
+  PE_CUDA(sc.alloc(&part, (size_t)max_tiles * 6));
+  const bool h_logl = !is_device_ptr(out_logl);
+  const bool h_dhhh = out_dhhh && !is_device_ptr(out_dhhh);
+  const bool h_stat = out_status && !is_device_ptr(out_status);
+  double* logl = out_logl;
+  double* dhhh = out_dhhh;
+  int32_t* stat = out_status;
+  if (h_logl) PE_CUDA(sc.alloc(&logl, B));
+  if (h_dhhh) PE_CUDA(sc.alloc(&dhhh, (size_t)B * ndet * 6));
+  if (h_stat) PE_CUDA(sc.alloc(&stat, B));
+  PE_CUDA(pe::launch_prep(th, B, mode_mask, ds, coef, nend, stat, st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, st));
+  const long long g = std::min<long long>(max_tiles, (long long)sm_count() * pe::fwd_blocks_per_sm());
+  void* prof = nullptr;
+  pe::profile_begin(st, &prof);
+  PE_CUDA(pe::launch_loglike_fwd(ds, B, coef, nend, off, part, (int)std::max<long long>(g, 1), st));
+  pe::profile_end(st, prof);
+  PE_CUDA(pe::launch_reduce(ds, B, off, part, coef, logl, dhhh, st));
+  if (h_logl) PE_CUDA(cudaMemcpyAsync(out_logl, logl, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (h_dhhh)
+    PE_CUDA(cudaMemcpyAsync(out_dhhh, dhhh, (size_t)B * ndet * 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (h_stat) PE_CUDA(cudaMemcpyAsync(out_status, stat, (size_t)B * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (h_logl || h_dhhh || h_stat) PE_CUDA(cudaStreamSynchronize(st));
+  return PE_OK;
+}
+
+pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
+                                double* out_logl, double* out_grad, int32_t* out_status, void* stream) {
+  (void)dets; (void)ndet; (void)theta; (void)B; (void)mode_mask; (void)out_logl; (void)out_grad;
+  (void)out_status; (void)stream;
+  return fail(PE_ESTATE, "pe_loglike_grad_batch is not available in this build");
+}
+
+pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask, double* out_F,
+                    void* stream) {
+  (void)dets; (void)ndet; (void)theta; (void)B; (void)mode_mask; (void)out_F; (void)stream;
+  return fail(PE_ESTATE, "pe_fisher is not available in this build");
+}
+
+}  // extern "C"
+
+namespace pe {
+int fwd_blocks_per_sm() {
+  static int n = 0;
+  if (n == 0) n = 8;
+  return n;
+}
+}  // namespace pe

@@ -1,0 +1,293 @@
+// pe_device.cuh -- device functions of the hot path (rows A1-A6): per-sample coefficients and
+// the per-(sample, mode, bin) waveform, time-frequency map, orbit, single-link responses and TDI.
+// arXiv:2602.12011 Sec. 2.1 (Eq. eq_td_resp, eq_tf, eq_fd_resp, FD TDI, A/E/T).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pe_internal.h"
+
+namespace pe {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// -2Y_lm(iota, 0) closed forms for the ten (l, +-m) the five modes need.
+__device__ inline void sylm_pair(int l, int m, double iota, double* ypos, double* yneg) {
+  double ci = cos(iota), si = sin(iota);
+  double c2 = cos(0.5 * iota), s2 = sin(0.5 * iota);
+  const double pi = kPi;
+  if (l == 2 && m == 2) {
+    *ypos = sqrt(5.0 / (64.0 * pi)) * (1.0 + ci) * (1.0 + ci);
+    *yneg = sqrt(5.0 / (64.0 * pi)) * (1.0 - ci) * (1.0 - ci);
+  } else if (l == 2 && m == 1) {
+    *ypos = sqrt(5.0 / (16.0 * pi)) * si * (1.0 + ci);
+    *yneg = sqrt(5.0 / (16.0 * pi)) * si * (1.0 - ci);
+  } else if (l == 3 && m == 3) {
+    double c4 = c2 * c2 * c2 * c2, s4 = s2 * s2 * s2 * s2;
+    *ypos = -sqrt(21.0 / (2.0 * pi)) * c4 * c2 * s2;
+    *yneg = sqrt(21.0 / (2.0 * pi)) * c2 * s4 * s2;
+  } else if (l == 3 && m == 2) {
+    double c4 = c2 * c2 * c2 * c2, s4 = s2 * s2 * s2 * s2;
+    *ypos = 0.5 * sqrt(7.0 / pi) * c4 * (3.0 * ci - 2.0);
+    *yneg = sqrt(7.0 / (4.0 * pi)) * (3.0 * ci + 2.0) * s4;
+  } else {  // (4, 4)
+    double cc = c2 * c2, ss = s2 * s2;
+    *ypos = 3.0 * sqrt(7.0 / pi) * cc * cc * cc * ss;
+    *yneg = 3.0 * sqrt(7.0 / pi) * cc * ss * ss * ss;
+  }
+}
+
+__device__ __constant__ static const int kModeL[kNModes] = {2, 2, 3, 3, 4};
+__device__ __constant__ static const int kModeM[kNModes] = {2, 1, 3, 2, 4};
+
+// Domain of a parameter sample (out-of-domain samples get logL = -inf).
+__device__ inline bool theta_valid(const double* th) {
+  for (int i = 0; i < PE_NPARAM; ++i)
+    if (!isfinite(th[i])) return false;
+  if (!(th[0] >= 1e3 && th[0] <= 1e9)) return false;
+  if (!(th[1] >= 1.0)) return false;
+  if (!(fabs(th[2]) < 1.0 && fabs(th[3]) < 1.0)) return false;
+  if (!(th[4] > 0.0)) return false;
+  return true;
+}
+
+// Row A1: per-sample coefficients from theta[11].
+//  TaylorF2 phase (Buonanno et al. 2009 3.5PN; 1.5PN spin-orbit, 2PN aligned spin-spin),
+//  SPA amplitudes of the leading-order spherical modes (Blanchet 2014), C-infinity taper
+//  on the orbital frequency between 0.9 F_isco and F_isco, -2Y_lm polarisation weights
+//  (h_{l,-m} = (-1)^l h*_lm), sky frame.
+__device__ inline void sample_prep(const double* th, unsigned mask, SampleCoef& S) {
+  S.valid = theta_valid(th) ? 1 : 0;
+  const double Mtot = th[0], q = th[1], chi1 = th[2], chi2 = th[3], dL = th[4], iota = th[5];
+  const double phic = th[6], lam = th[7], bet = th[8], psi = th[9], tc = th[10];
+  const double M = Mtot * kMsunS;
+  const double D = dL * kGpcS;
+  const double eta = q / ((1.0 + q) * (1.0 + q));
+  const double m1 = q / (1.0 + q), m2 = 1.0 / (1.0 + q);
+  const double delta = (q - 1.0) / (q + 1.0);
+  const double pi = kPi;
+  const double bso = chi1 * (113.0 / 12.0 * m1 * m1 + 25.0 / 4.0 * eta) + chi2 * (113.0 / 12.0 * m2 * m2 + 25.0 / 4.0 * eta);
+  const double sss = 79.0 / 8.0 * eta * chi1 * chi2;
+  const double a5c = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+  const double a6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi - 6848.0 / 21.0 * kEulerGamma +
+                     (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi) * eta + 76055.0 / 1728.0 * eta * eta -
+                     127825.0 / 1296.0 * eta * eta * eta;
+  const double n = 3.0 / (128.0 * eta);
+  S.tc = tc;
+  S.P[0] = n;
+  S.P[1] = 0.0;
+  S.P[2] = n * (3715.0 / 756.0 + 55.0 / 9.0 * eta);
+  S.P[3] = n * (-16.0 * pi + 4.0 * bso);
+  S.P[4] = n * (15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta - 10.0 * sss);
+  S.P[5] = n * a5c * (1.0 + 1.5 * log(6.0));          // alpha5 (1 + 3 ln(v/v_lso)), v_lso = 6^-1/2
+  S.P[6] = n * (a6c - 6848.0 / 21.0 * log(4.0));        // alpha6 - (6848/21) ln(4 v)
+  S.P[7] = n * pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
+  S.Q5 = n * 3.0 * a5c;
+  S.Q6 = n * (-6848.0 / 21.0);
+  // sky frame
+  double sl, cl, sb, cb, sp, cp;
+  sincos(lam, &sl, &cl);
+  sincos(bet, &sb, &cb);
+  sincos(psi, &sp, &cp);
+  S.k[0] = -(cb * cl); S.k[1] = -(cb * sl); S.k[2] = -sb;
+  const double u[3] = {sl, -cl, 0.0};
+  const double v[3] = {-(sb * cl), -(sb * sl), cb};
+  for (int i = 0; i < 3; ++i) { S.p[i] = cp * u[i] + sp * v[i]; S.q[i] = -(sp * u[i]) + cp * v[i]; }
+  // modes
+  const double Fisco = 1.0 / (pow(6.0, 1.5) * 2.0 * pi * M);
+  for (int md = 0; md < kNModes; ++md) {
+    ModeCoef& C = S.md[md];
+    const int l = kModeL[md], m = kModeM[md];
+    double hmag, argt;  // |H_lm| / x^(p/2) and arg(conj H_lm) in turns
+    int p;
+    if (md == 0) { hmag = 1.0; argt = 0.0; p = 0; }
+    else if (md == 1) { hmag = delta / 3.0; argt = -0.25; p = 1; }
+    else if (md == 2) { hmag = 0.75 * sqrt(15.0 / 14.0) * delta; argt = 0.25; p = 1; }
+    else if (md == 3) { hmag = sqrt(5.0 / 7.0) / 3.0 * (1.0 - 3.0 * eta); argt = 0.0; p = 2; }
+    else { hmag = 8.0 / 9.0 * sqrt(5.0 / 7.0) * (1.0 - 3.0 * eta); argt = 0.5; p = 2; }
+    C.cm = cbrt(2.0 * pi * M / m);
+    C.icm = 1.0 / C.cm;
+    C.lncm = log(C.cm);
+    C.amp = 2.0 * pi * M * M / D * sqrt(eta / (3.0 * m)) * hmag * pow(C.cm, -3.5);
+    double ph = m * phic / (2.0 * pi) + 0.125 + argt;
+    C.ph0 = ph - rint(ph);
+    C.mfac = m / (4.0 * pi);
+    C.tffac = m / (12.0 * pi);
+    double yp, yn;
+    sylm_pair(l, m, iota, &yp, &yn);
+    const double sgn = (l % 2) ? -1.0 : 1.0;
+    C.Pp = 0.5 * (yp + sgn * yn);
+    C.Pc = 0.5 * (sgn * yn - yp);
+    C.fend = m * Fisco;
+    C.ftap = 0.9 * m * Fisco;
+    C.p = p;
+    C.active = (S.valid && (mask & (1u << md)) && hmag != 0.0) ? 1 : 0;
+  }
+}
+
+// Spacecraft offsets delta_i from the constellation centre and the centre x_c, at time t.
+__device__ __forceinline__ void orbit_offsets(const DetDev& D, double t, double xc[3], double dl[3][3]) {
+  double s, c;
+  sincospi(fma(t, D.rate_ht, D.alpha0_ht), &s, &c);
+  xc[0] = D.R * c; xc[1] = D.R * s; xc[2] = 0.0;
+  if (D.orbit == 0) {
+    const double c2 = c * c - s * s, s2 = 2.0 * s * c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dl[i][0] = D.eRh * (c2 * D.cb[i] + s2 * D.sb[i]) - D.eR3h * D.cb[i];
+      dl[i][1] = D.eRh * (s2 * D.cb[i] - c2 * D.sb[i]) - D.eR3h * D.sb[i];
+      dl[i][2] = -D.eRs3 * (c * D.cb[i] + s * D.sb[i]);
+    }
+  } else {
+    double s0, c0;
+    sincospi(t * D.geo_rate_ht, &s0, &c0);
+    const double ch = -0.5, sh = 0.86602540378443864676;  // cos, sin of 120 degrees
+    double ci = c0, si = s0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dl[i][j] = D.rgeo * (ci * D.e1[j] + si * D.e2[j]);
+      const double cn = ci * ch - si * sh, sn = si * ch + ci * sh;
+      ci = cn; si = sn;
+    }
+  }
+}
+
+// sinc(u) with the same small-argument series as the definition: 1 - u^2/6 + u^4/120 - u^6/5040
+__device__ __forceinline__ double sinc_small(double u) {
+  const double u2 = u * u;
+  return 1.0 - u2 / 6.0 + u2 * u2 / 120.0 - u2 * u2 * u2 / 5040.0;
+}
+
+// Per-bin inputs shared by all modes of one bin.
+struct BinIn {
+  double f, f13, fm13, lnf3, fm76, invf;
+  double a, sa, ca;    // a = pi f L
+  double2 z;           // e^{-2 i a}
+  double frc;          // frac(f t_c) computed exactly (turns)
+};
+
+// One (sample, mode, bin) unit: adds this mode's TDI brackets X', Y', Z' (Sec. 2.1) to acc.
+// X = Q X' with Q = TDI factor (-i a) e^{-ia}; here
+//   X' = G31 V31 - G12 U12,  Y' = G12 V12 - G23 U23,  Z' = G23 V23 - G31 U31,
+// G_l = e^{i pi f k.delta_t} (n_l.h~.n_l) per link pair l=(r,s) with third spacecraft t,
+// U_l = sinc(a(1 - k.n_l)) + z sinc(a(1 + k.n_l)), V_l = sinc(a(1 + k.n_l)) + z sinc(a(1 - k.n_l)),
+// n_l = (x_r - x_s)/|x_r - x_s|, geometry at the mode's t_f, and the centre Doppler phase
+// e^{-2 pi i f k.x_c} folded into the mode's phase.
+__device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
+                                         double2 acc[3]) {
+  // --- waveform and time-frequency map (rows A2, A3)
+  const double v = C.cm * B.f13;
+  const double iv = C.icm * B.fm13;
+  const double lnv = C.lncm + B.lnf3;
+  double iv5 = iv * iv;
+  iv5 = iv5 * iv5 * iv;
+  double poly = S.P[7];
+  double dpol = 2.0 * S.P[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) {
+    poly = fma(poly, v, S.P[k]);
+    dpol = fma(dpol, v, (k - 5) * S.P[k]);
+  }
+  const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
+  const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));  // v dPsi_PN/dv
+  const double tf = fma(C.tffac * B.invf, dv, S.tc);                   // Eq. eq_tf
+  double w = 1.0;
+  if (B.f > C.ftap) {
+    const double span = C.fend - C.ftap;
+    const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
+    w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
+  }
+  double amp = C.amp * B.fm76 * w;
+  if (C.p >= 1) amp *= v;
+  if (C.p >= 2) amp *= v;
+  // --- orbit at t_f (row A4)
+  double xc[3], dl[3][3];
+  orbit_offsets(D, tf, xc, dl);
+  const double kxc = S.k[0] * xc[0] + S.k[1] * xc[1] + S.k[2] * xc[2];
+  double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
+  ph -= rint(ph);
+  double sph, cph;
+  sincospi(2.0 * ph, &sph, &cph);
+  const double2 H = make_double2(amp * cph, amp * sph);
+  // --- links (row A5): pair l = (1,2), (2,3), (3,1); third spacecraft 3, 1, 2
+  double2 G[3], U[3], V[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const int r = l, s = (l + 1) % 3, t = (l + 2) % 3;
+    double n0 = dl[r][0] - dl[s][0], n1 = dl[r][1] - dl[s][1], n2 = dl[r][2] - dl[s][2];
+    const double inv = rsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    n0 *= inv; n1 *= inv; n2 *= inv;
+    const double kn = S.k[0] * n0 + S.k[1] * n1 + S.k[2] * n2;
+    const double np = S.p[0] * n0 + S.p[1] * n1 + S.p[2] * n2;
+    const double nq = S.q[0] * n0 + S.q[1] * n1 + S.q[2] * n2;
+    const double2 gam = make_double2(C.Pp * (np * np - nq * nq), C.Pc * 2.0 * np * nq);
+    const double kd = S.k[0] * dl[t][0] + S.k[1] * dl[t][1] + S.k[2] * dl[t][2];
+    double se, ce;
+    sincospi(B.f * kd, &se, &ce);
+    G[l] = cmul(make_double2(ce, se), cmul(gam, H));
+    // sinc(a(1 -+ kn)) from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
+    double sak, cak;
+    sincos(B.a * kn, &sak, &cak);
+    const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
+    const double s1 = B.sa * cak - B.ca * sak, s2 = B.sa * cak + B.ca * sak;
+    double sm, spl;
+    if (fabs(u1) >= 1e-3 && fabs(u2) >= 1e-3) {
+      const double rr = 1.0 / (u1 * u2);
+      sm = s1 * u2 * rr;
+      spl = s2 * u1 * rr;
+    } else {
+      sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
+      spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2 / u2;
+    }
+    U[l] = make_double2(fma(B.z.x, spl, sm), B.z.y * spl);
+    V[l] = make_double2(fma(B.z.x, sm, spl), B.z.y * sm);
+  }
+  // --- TDI brackets (row A6); l index: 0 = (1,2), 1 = (2,3), 2 = (3,1)
+  acc[0] = cadd(acc[0], csub(cmul(G[2], V[2]), cmul(G[0], U[0])));
+  acc[1] = cadd(acc[1], csub(cmul(G[0], V[0]), cmul(G[1], U[1])));
+  acc[2] = cadd(acc[2], csub(cmul(G[1], V[1]), cmul(G[2], U[2])));
+}
+
+__device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinIn& B) {
+  B.f = D.f[b];
+  B.f13 = D.f13[b];
+  B.fm13 = D.fm13[b];
+  B.lnf3 = D.lnf3[b];
+  B.fm76 = D.fm76[b];
+  B.invf = B.fm13 * B.fm13 * B.fm13;
+  B.a = kPi * B.f * D.L;
+  const double2 sc = D.sca[b];
+  B.sa = sc.x; B.ca = sc.y;
+  B.z = D.z[b];
+  // frac(f t_c) without rounding the product: p + e = f t_c exactly (FMA two-product)
+  const double pr = B.f * tc;
+  const double er = fma(B.f, tc, -pr);
+  B.frc = (pr - rint(pr)) + er;
+}
+
+// Mode-summed TDI brackets X', Y', Z' of one sample at one bin.
+__device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, int b, double2 acc[3]) {
+  BinIn B;
+  load_bin(D, b, S.tc, B);
+  acc[0] = acc[1] = acc[2] = make_double2(0.0, 0.0);
+#pragma unroll 1
+  for (int md = 0; md < kNModes; ++md) {
+    const ModeCoef& C = S.md[md];
+    if (!C.active || !(B.f < C.fend)) continue;
+    mode_bin(D, S, C, B, acc);
+  }
+}
+
+// A/E/T combinations (without Q n_c): B_A = Z' - X', B_E = X' - 2Y' + Z', B_T = X' + Y' + Z'.
+__device__ __forceinline__ void aet_from_xyz(const double2 x[3], double2 o[3]) {
+  o[0] = csub(x[2], x[0]);
+  o[1] = cadd(csub(x[0], cscale(x[1], 2.0)), x[2]);
+  o[2] = cadd(cadd(x[0], x[1]), x[2]);
+}
+
+}  // namespace pe

@@ -1,0 +1,90 @@
+// pe_internal.h -- library-internal layouts shared by the host code and the CUDA kernels of
+// libpespace_gb300. Nothing here is part of the public ABI (include/pespace_gb300.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pespace_gb300.h"
+
+namespace pe {
+
+// Physical constants (the library's own copy).
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kC = 299792458.0;                 // speed of light [m/s]
+constexpr double kMsunS = 4.925490947641267e-6;    // G Msun / c^3 [s]
+constexpr double kGpcS = 1.02927125054339e17;      // 1 Gpc / c [s]
+constexpr double kAuS = 499.00478383615643;        // 1 au / c [s]
+constexpr double kYearS = 31557600.0;              // Julian year [s]
+constexpr double kEulerGamma = 0.57721566490153286061;
+
+constexpr int kNModes = 5;      // (2,2) (2,1) (3,3) (3,2) (4,4)
+constexpr int kMaxDet = 8;
+constexpr int kTileBins = 128;  // frequency bins per work tile = threads per CTA of the hot kernels
+
+// Per-(sample, mode) coefficients (row A1 of the path). With v = (2 pi M f/m)^(1/3):
+//   v = cm f^(1/3), 1/v = icm f^(-1/3), ln v = lncm + ln(f)/3,
+//   |H~_lm(f)| = amp f^(-7/6) v^p w(f)   (w: Planck taper, 1 for f <= ftap, 0 for f >= fend),
+//   arg H~_lm(f) = 2 pi [ ph0 - f t_c - (m/4pi) Psi_PN(v) ] (turns, before the orbit's
+//   centre Doppler term), and the mode's tensor is H~ (Pp e+ + i Pc ex).
+struct ModeCoef {
+  double cm, icm, lncm;
+  double amp;
+  double ph0;
+  double mfac;      // m / (4 pi)
+  double tffac;     // m / (12 pi)
+  double Pp, Pc;
+  double fend, ftap;
+  int p;            // power of v in |H_lm|: 0 (22), 1 (21, 33), 2 (32, 44)
+  int active;       // 1 if the mode is in the mask and its amplitude is non-zero
+};
+
+// Per-sample coefficients. Psi_PN(v) = v^-5 sum_k P[k] v^k + ln v (Q5 + Q6 v) (TaylorF2 3.5PN,
+// already multiplied by 3/(128 eta)).
+struct SampleCoef {
+  double tc;
+  double P[8];
+  double Q5, Q6;
+  double k[3], p[3], q[3];   // propagation direction and polarisation frame
+  ModeCoef md[kNModes];
+  int valid;
+  int pad_;
+};
+
+// Device view of one detector: grid, orbit constants and per-bin SoA tables.
+struct DetDev {
+  double T;          // observation time = 1/df [s]
+  long long k0;      // first bin index
+  int nb;            // number of bins
+  int orbit;         // 0 heliocentric, 1 geocentric
+  int tdi_gen;
+  int pad_;
+  double L;          // nominal arm [s]
+  // orbit: centre R (cos alpha, sin alpha, 0), alpha in half-turns = alpha0_ht + t * rate_ht
+  double R, alpha0_ht, rate_ht;
+  // heliocentric (first order in e): offsets from the centre use eRh = e R / 2,
+  // eR3h = 3 e R / 2, eRs3 = sqrt(3) e R and the spacecraft angles cb[i], sb[i].
+  double eRh, eR3h, eRs3;
+  double cb[3], sb[3];
+  // geocentric: offsets r (cos phi_i e1 + sin phi_i e2), phi_0 in half-turns = t * geo_rate_ht
+  double rgeo, geo_rate_ht;
+  double e1[3], e2[3];
+  // per-bin tables (length nb)
+  const double* f;      // f_k = k / T
+  const double* f13;    // f^(1/3)
+  const double* fm13;   // f^(-1/3)
+  const double* lnf3;   // ln(f)/3
+  const double* fm76;   // f^(-7/6)
+  const double2* sca;   // (sin a, cos a), a = pi f L
+  const double2* z;     // z = e^{-2 pi i f L}
+  const double2* dg;    // [3][nb]: conj(d~_c) w_c Q n_c   (w_c = 4/(S_c T))
+  const double* gg;     // [3][nb]: w_c |Q|^2 n_c^2
+  const double* dd;     // [3]: <d|d>_c
+  // Q = TDI factor(z) (-i a) e^{-i a}; n_A = 1/sqrt2, n_E = 1/sqrt6, n_T = 1/sqrt3
+};
+
+struct DetSet {
+  DetDev d[kMaxDet];
+  int ndet;
+};
+
+}  // namespace pe

@@ -1,0 +1,364 @@
+// pe_kernels.cu -- CUDA kernels of the log-likelihood hot path (arXiv:2602.12011 Sec. 2):
+//   k_grid_tables    row A0: per-bin grid tables of a detector
+//   k_psd_model      row A0: analytic A/E/T PSD (Sec. 3.2)
+//   k_data_tables    row A0: whitened data/weight tables and per-block <d|d> partials
+//   k_sum_parts      fixed-order sum of per-block partials (used for <d|d>)
+//   k_prep           row A1: per-sample coefficients and active bin counts per detector
+//   k_scan_tiles     tile offsets of the uneven (detector, sample) work list
+//   k_loglike_fwd    rows A2-A7: persistent fused waveform -> t_f -> orbit -> links -> TDI ->
+//                    A/E/T -> PSD-weighted sums, one fixed-order partial per tile
+//   k_reduce         row A7: fixed-order sums of the partials -> <d|h>, <h|h>, logL
+//   k_signal         noise-free A/E/T signal on the grid (per-bin output)
+//   k_inject         data = signal + noise scaled by the PSD (Eq. eq_diag_Sigma_to_Sn)
+#include <cuda_runtime.h>
+
+#include "pe_device.cuh"
+#include "pe_kernels.h"
+
+namespace pe {
+
+// ------------------------------------------------------------------------------------------
+// Row A0: grid tables f, f^(1/3), f^(-1/3), ln(f)/3, f^(-7/6), sincos(pi f L), z = e^{-2 pi i f L}.
+// ------------------------------------------------------------------------------------------
+__global__ void k_grid_tables(double T, long long k0, int nb, double L, double* f, double* f13, double* fm13,
+                              double* lnf3, double* fm76, double2* sca, double2* z) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const double fb = double(k0 + b) / T;
+  const double c = cbrt(fb);
+  f[b] = fb;
+  f13[b] = c;
+  fm13[b] = 1.0 / c;
+  lnf3[b] = log(fb) / 3.0;
+  fm76[b] = rsqrt(c) / fb;
+  double s, co;
+  sincospi(fb * L, &s, &co);
+  sca[b] = make_double2(s, co);
+  double s2, c2;
+  sincospi(2.0 * fb * L, &s2, &c2);
+  z[b] = make_double2(c2, -s2);
+}
+
+// Analytic PSD (acceleration + OMS noise only): equal-arm TDI-1.5 A/E/T spectra
+//   S_A = S_E = 8 sin^2 x [(2 + cos x) S_oms + (6 + 4 cos x + 2 cos 2x) S_acc],
+//   S_T = 32 sin^2 x sin^2(x/2) [S_oms + 4 sin^2(x/2) S_acc],   x = 2 pi f L,
+// times |1 - z^4|^2 = 4 sin^2(2x) for TDI 2.0. out: [3][nb].
+__global__ void k_psd_model(const double* f, int nb, double L, double oms, double acc, int shaping, int tdi_gen,
+                            double* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const double fb = f[b];
+  const double x = 2.0 * kPi * fb * L;
+  const double so = oms * 2.0 * kPi * fb / kC;
+  const double sa = acc / (2.0 * kPi * fb * kC);
+  double Soms = so * so, Sacc = sa * sa;
+  if (shaping) {
+    const double r1 = 2e-3 / fb, r2 = 0.4e-3 / fb, r3 = fb / 8e-3;
+    Soms *= 1.0 + r1 * r1 * r1 * r1;
+    Sacc *= (1.0 + r2 * r2) * (1.0 + r3 * r3 * r3 * r3);
+  }
+  const double sx = sin(x), cx = cos(x), sh = sin(0.5 * x);
+  double SA = 8.0 * sx * sx * ((2.0 + cx) * Soms + (6.0 + 4.0 * cx + 2.0 * cos(2.0 * x)) * Sacc);
+  double ST = 32.0 * sx * sx * sh * sh * (Soms + 4.0 * sh * sh * Sacc);
+  if (tdi_gen == 20) {
+    const double s2 = sin(2.0 * x);
+    SA *= 4.0 * s2 * s2;
+    ST *= 4.0 * s2 * s2;
+  }
+  out[b] = SA;
+  out[nb + b] = SA;
+  out[2 * nb + b] = ST;
+}
+
+// Per-bin TDI/transfer factor Q = TDI(z) (-i a) e^{-ia}, a = pi f L, TDI(z) = 1 - z^2 (1.5) or
+// (1 - z^2)(1 - z^4) (2.0): X = Q X' for the brackets X' built per mode.
+__device__ __forceinline__ double2 transfer_q(double a, double2 sca, double2 z, int tdi_gen) {
+  const double2 z2 = cmul(z, z);
+  double2 tdi = make_double2(1.0 - z2.x, -z2.y);
+  if (tdi_gen == 20) {
+    const double2 z4 = cmul(z2, z2);
+    tdi = cmul(tdi, make_double2(1.0 - z4.x, -z4.y));
+  }
+  const double2 ma = make_double2(-a * sca.x, -a * sca.y);  // (-i a)(cos a - i sin a)
+  return cmul(tdi, ma);
+}
+
+__device__ __constant__ static const double kChanNorm[3] = {0.70710678118654752440, 0.40824829046386301637,
+                                                             0.57735026918962576451};
+
+// Whitened tables (row A0): w_c = 4/(S_c T) (Eq. eq_inner_product); dg_c = conj(d_c) w_c Q n_c;
+// gg_c = w_c |Q|^2 n_c^2; per-block partials of <d|d>_c = sum_k w_c |d_c|^2 in a fixed tree
+// order. data: [3][nb] complex, psd: [3][nb]; dd_part: [gridDim.x][3]; bad: 1 on a bad PSD.
+__global__ void k_data_tables(const double* f, const double2* sca, const double2* zt, int nb, double T, double L,
+                              int tdi_gen, const double2* data, const double* psd, double2* dg, double* gg,
+                              double* dd_part, int* bad) {
+  __shared__ double red[3][kTileBins];
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  double ddc[3] = {0.0, 0.0, 0.0};
+  if (b < nb) {
+    const double2 Q = transfer_q(kPi * f[b] * L, sca[b], zt[b], tdi_gen);
+    const double QQ = Q.x * Q.x + Q.y * Q.y;
+    for (int c = 0; c < 3; ++c) {
+      const double S = psd[c * nb + b];
+      if (!(S > 0.0) || !isfinite(S)) {
+        *bad = 1;
+        dg[c * nb + b] = make_double2(0.0, 0.0);
+        gg[c * nb + b] = 0.0;
+        continue;
+      }
+      const double w = 4.0 / (S * T);
+      const double2 d = data[c * nb + b];
+      ddc[c] = w * (d.x * d.x + d.y * d.y);
+      const double2 dw = make_double2(d.x * w * kChanNorm[c], -d.y * w * kChanNorm[c]);
+      dg[c * nb + b] = cmul(dw, Q);
+      gg[c * nb + b] = w * QQ * kChanNorm[c] * kChanNorm[c];
+    }
+  }
+  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = ddc[c];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 3; ++c) dd_part[blockIdx.x * 3 + c] = red[c][0];
+}
+
+// Fixed-order sum of n partials of width w (single warp, lane-strided then a shuffle tree).
+__global__ void k_sum_parts(const double* part, int n, int w, double* out) {
+  for (int c = 0; c < w; ++c) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += part[i * w + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[c] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Row A1: per-sample coefficients; active bins per (detector, sample): the bins below the
+// largest active mode's taper end m F_isco (one extra bin guards the rounding of the bound;
+// every unit still checks f < fend of its own mode).
+// ------------------------------------------------------------------------------------------
+__global__ void k_prep(const double* theta, int B, unsigned mask, DetSet ds, SampleCoef* coef, int* nend,
+                       int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  SampleCoef S;
+  sample_prep(theta + (size_t)s * PE_NPARAM, mask, S);
+  coef[s] = S;
+  double fmax = 0.0;
+  for (int md = 0; md < kNModes; ++md)
+    if (S.md[md].active) fmax = fmax > S.md[md].fend ? fmax : S.md[md].fend;
+  for (int I = 0; I < ds.ndet; ++I) {
+    const DetDev& D = ds.d[I];
+    int n = 0;
+    if (fmax > 0.0) {
+      const double kx = ceil(fmax * D.T) - double(D.k0) + 1.0;
+      n = kx <= 0.0 ? 0 : (kx >= double(D.nb) ? D.nb : int(kx));
+    }
+    nend[I * B + s] = n;
+  }
+  if (status) status[s] = S.valid ? 0 : 1;
+}
+
+// Exclusive prefix sum of tiles per (detector, sample) pair; off[P] = total tiles. One CTA.
+__global__ void k_scan_tiles(const int* nend, int P, long long* off) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x;
+  const int chunk = (P + blockDim.x - 1) / blockDim.x;
+  const int lo = t * chunk, hi = min(P, lo + chunk);
+  long long s = 0;
+  for (int i = lo; i < hi; ++i) s += (nend[i] + kTileBins - 1) / kTileBins;
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long long run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) { long long v = part[i]; part[i] = run; run += v; }
+    off[P] = run;
+  }
+  __syncthreads();
+  long long run = part[t];
+  for (int i = lo; i < hi; ++i) { off[i] = run; run += (nend[i] + kTileBins - 1) / kTileBins; }
+}
+
+// pair index p with off[p] <= t < off[p+1]
+__device__ __forceinline__ int find_pair(const long long* off, int P, long long t) {
+  int lo = 0, hi = P;  // invariant off[lo] <= t < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Block reduction of NV doubles per thread in a fixed tree order; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins / 32]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[i][wid] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = sh[i][0];
+      for (int w = 1; w < kTileBins / 32; ++w) s += sh[i][w];
+      v[i] = s;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Rows A2-A7: persistent fused kernel. Work item = one tile of kTileBins bins of one
+// (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns one bin,
+// sums the modes' TDI brackets in registers, forms A/E/T and the weighted products; the tile's
+// six sums (<d|h>_c, <h|h>_c) go to part[tile][6].
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileBins) k_loglike_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+                                                           const int* __restrict__ nend,
+                                                           const long long* __restrict__ off, double* part) {
+  __shared__ double sh[6][kTileBins / 32];
+  const int P = ds.ndet * B;
+  const long long total = off[P];
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int p = find_pair(off, P, t);
+    const int I = p / B, s = p - I * B;
+    const int b = int(t - off[p]) * kTileBins + threadIdx.x;
+    const DetDev& D = ds.d[I];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (b < nend[p]) {
+      const SampleCoef& S = coef[s];
+      double2 x[3], o[3];
+      bin_xyz(D, S, b, x);
+      aet_from_xyz(x, o);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double2 g = D.dg[c * D.nb + b];
+        v[c] = g.x * o[c].x - g.y * o[c].y;                        // Re(dg_c B_c)
+        v[3 + c] = D.gg[c * D.nb + b] * (o[c].x * o[c].x + o[c].y * o[c].y);
+      }
+    }
+    block_sum<6>(v, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) part[t * 6 + i] = v[i];
+  }
+}
+
+// Row A7: one warp per sample; for each detector a lane-strided, shuffle-tree sum of that
+// pair's tile partials (fixed order), then logL = sum_{I,c} (<d|h> - <h|h>/2 - <d|d>/2).
+// dhhh: [B][ndet][3][2] or NULL.
+__global__ void k_reduce(DetSet ds, int B, const long long* off, const double* part, const SampleCoef* coef,
+                         double* logl, double* dhhh) {
+  const int ndet = ds.ndet;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const int s = warp;
+  double L = 0.0;
+  for (int I = 0; I < ndet; ++I) {
+    const int p = I * B + s;
+    const long long t0 = off[p], t1 = off[p + 1];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long t = t0 + lane; t < t1; t += 32)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] += part[t * 6 + i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    if (lane == 0) {
+      for (int c = 0; c < 3; ++c) {
+        L += v[c] - 0.5 * v[3 + c] - 0.5 * ds.d[I].dd[c];
+        if (dhhh) {
+          dhhh[(((size_t)s * ndet + I) * 3 + c) * 2 + 0] = v[c];
+          dhhh[(((size_t)s * ndet + I) * 3 + c) * 2 + 1] = v[3 + c];
+        }
+      }
+    }
+  }
+  if (lane == 0) logl[s] = coef[s].valid ? L : -INFINITY;
+}
+
+// Noise-free A/E/T signal of one sample on the whole grid: h_c = Q n_c B_c. out: [3][nb].
+__global__ void k_signal(DetDev D, const SampleCoef* coef, double2* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= D.nb) return;
+  const SampleCoef& S = coef[0];
+  double2 x[3], o[3];
+  bin_xyz(D, S, b, x);
+  aet_from_xyz(x, o);
+  const double2 Q = transfer_q(kPi * D.f[b] * D.L, D.sca[b], D.z[b], D.tdi_gen);
+  for (int c = 0; c < 3; ++c) out[c * D.nb + b] = cscale(cmul(Q, o[c]), kChanNorm[c]);
+}
+
+// data_c = h_c + n_c sqrt(S_c T / 4) (Re, Im independent), in place on h. normals may be NULL.
+__global__ void k_inject(int nb, double T, const double* psd, const double2* normals, double2* h) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nb || normals == nullptr) return;
+  const double sig = sqrt(psd[i] * T / 4.0);
+  const double2 n = normals[i];
+  h[i] = make_double2(h[i].x + n.x * sig, h[i].y + n.y * sig);
+}
+
+// ------------------------------------------------------------------------------------------
+// Host-callable launch wrappers.
+// ------------------------------------------------------------------------------------------
+cudaError_t launch_grid_tables(double T, long long k0, int nb, double L, double* f, double* f13, double* fm13,
+                               double* lnf3, double* fm76, double2* sca, double2* z, cudaStream_t st) {
+  k_grid_tables<<<(nb + 127) / 128, 128, 0, st>>>(T, k0, nb, L, f, f13, fm13, lnf3, fm76, sca, z);
+  return cudaGetLastError();
+}
+cudaError_t launch_psd_model(const double* f, int nb, double L, double oms, double acc, int shaping, int tdi_gen,
+                             double* out, cudaStream_t st) {
+  k_psd_model<<<(nb + 127) / 128, 128, 0, st>>>(f, nb, L, oms, acc, shaping, tdi_gen, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_data_tables(const double* f, const double2* sca, const double2* z, int nb, double T, double L,
+                               int tdi_gen, const double2* data, const double* psd, double2* dg, double* gg,
+                               double* dd_part, int* bad, int* nblocks, cudaStream_t st) {
+  const int g = (nb + kTileBins - 1) / kTileBins;
+  *nblocks = g;
+  k_data_tables<<<g, kTileBins, 0, st>>>(f, sca, z, nb, T, L, tdi_gen, data, psd, dg, gg, dd_part, bad);
+  return cudaGetLastError();
+}
+cudaError_t launch_sum_parts(const double* part, int n, int w, double* out, cudaStream_t st) {
+  k_sum_parts<<<1, 32, 0, st>>>(part, n, w, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef, int* nend,
+                        int* status, cudaStream_t st) {
+  k_prep<<<(B + 63) / 64, 64, 0, st>>>(theta, B, mask, ds, coef, nend, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, cudaStream_t st) {
+  k_scan_tiles<<<1, 1024, 0, st>>>(nend, P, off);
+  return cudaGetLastError();
+}
+cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
+                               double* part, int grid, cudaStream_t st) {
+  k_loglike_fwd<<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const double* part, const SampleCoef* coef,
+                          double* logl, double* dhhh, cudaStream_t st) {
+  const int threads = 128;
+  const long long warps = B;
+  const int grid = int((warps * 32 + threads - 1) / threads);
+  k_reduce<<<grid, threads, 0, st>>>(ds, B, off, part, coef, logl, dhhh);
+  return cudaGetLastError();
+}
+cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, cudaStream_t st) {
+  k_signal<<<(D.nb + kTileBins - 1) / kTileBins, kTileBins, 0, st>>>(D, coef, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_inject(int nb, double T, const double* psd, const double2* normals, double2* h, cudaStream_t st) {
+  k_inject<<<(3 * nb + 127) / 128, 128, 0, st>>>(nb, T, psd, normals, h);
+  return cudaGetLastError();
+}
+
+}  // namespace pe
