@@ -132,6 +132,27 @@ pe_status pe_inject(pe_detector det, const double* theta_inj, unsigned mode_mask
 pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
                            double* out_logl, double* out_dhhh, int32_t* out_status, void* stream);
 
+/* pe_loglike_batch without any device allocation (the paper has no counterpart: this entry
+ * point exists for callers that cannot allocate). A sampler embedded in an application that
+ * reserves the GPU's memory for its own pool at start-up, or a latency-critical loop that must
+ * never enter the allocator, cannot let the library call cudaMalloc/cudaMallocAsync per call.
+ * This variant computes exactly what pe_loglike_batch computes, with its scratch in one fixed
+ * 32 MiB device array that every GPU loading the library holds until the process exits; it calls
+ * no allocating routine.
+ *   theta, out_logl and the optional out_dhhh / out_status must be DEVICE pointers (host buffers
+ *   would need staging memory); other arguments and layouts are as for pe_loglike_batch.
+ *   Size limit: coefficients (about 0.7 KB per sample) plus one 48-byte partial per 128-bin tile
+ *   of every (detector, sample) pair must fit in 32 MiB -- about 400 samples on one 2^22 s grid
+ *   (209,296 bins), about 1,500 on a 2^20 s grid. Larger batches return PE_EINVAL with the
+ *   needed size in pe_last_error(); split them.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current, so make that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (other streams, other
+ *   host threads) race on it and give wrong results; serialise them. Every scratch element is
+ *   written before it is read within a call, so nothing is cleared between calls. */
+pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
+                                   double* out_logl, double* out_dhhh, int32_t* out_status, void* stream);
+
 /* Batched gradient d logL_s / d theta_s (hand-written adjoint of the same path, Sec. 2.3 on
  * automatic differentiation); arguments as pe_loglike_batch, plus out_grad [B][11]
  * (host or device). out_logl may be NULL. */

@@ -75,6 +75,8 @@ def lib():
         L.pe_loglike_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
         L.pe_loglike_grad_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
         L.pe_fisher.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P]
+        L.pe_loglike_batch_noalloc.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+        L.pe_loglike_batch_noalloc.restype = C.c_int
         L.pe_profile_enable.argtypes = [C.c_int]
         L.pe_profile_read.argtypes = [_P, _P]
         L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
@@ -157,6 +159,14 @@ def _handles(hs):
 def pe_loglike_batch(hs, theta, B: int, mode_mask: int, out_logl, out_dhhh=None, out_status=None, stream=None):
     _check(lib().pe_loglike_batch(_handles(hs), len(hs), _ptr(theta), int(B), int(mode_mask), _ptr(out_logl),
                                   _ptr(out_dhhh), _ptr(out_status), _stream(stream)))
+
+
+def pe_loglike_batch_noalloc(hs, theta, B: int, mode_mask: int, out_logl, out_dhhh=None, out_status=None,
+                             stream=None):
+    """pe_loglike_batch with the library's fixed device scratch array: allocates nothing.
+    theta and outputs must be CUDA tensors."""
+    _check(lib().pe_loglike_batch_noalloc(_handles(hs), len(hs), _ptr(theta), int(B), int(mode_mask),
+                                          _ptr(out_logl), _ptr(out_dhhh), _ptr(out_status), _stream(stream)))
 
 
 def pe_loglike_grad_batch(hs, theta, B: int, mode_mask: int, out_logl, out_grad, out_status=None, stream=None):

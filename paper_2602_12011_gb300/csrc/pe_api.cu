@@ -435,6 +435,12 @@ pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int 
 }  // extern "C"
 
 namespace pe {
+// Detector-handle validation for entry points defined in other translation units: fills the
+// device views of dets[0..ndet) and sets pe_last_error on failure.
+pe_status detset_from_handles(const pe_detector* dets, int ndet, DetSet* ds) { return check_dets(dets, ndet, ds); }
+// Records a message for pe_last_error and returns st.
+pe_status set_error(pe_status st, const char* msg) { return fail(st, "%s", msg); }
+
 int fwd_blocks_per_sm() {
   static int n = 0;
   if (n == 0) n = 8;

@@ -27,4 +27,8 @@ cudaError_t launch_inject(int nb, double T, const double* psd, const double2* no
 // CTAs per SM the persistent forward kernel can keep resident (occupancy query).
 int fwd_blocks_per_sm();
 
+// Defined in pe_api.cu: handle validation and error reporting shared with other entry points.
+pe_status detset_from_handles(const pe_detector* dets, int ndet, DetSet* ds);
+pe_status set_error(pe_status st, const char* msg);
+
 }  // namespace pe

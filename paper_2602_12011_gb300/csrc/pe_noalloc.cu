@@ -1,0 +1,129 @@
+// pe_noalloc.cu -- pe_loglike_batch_noalloc: the batched log-likelihood with its scratch in a
+// fixed, file-scope device array instead of memory allocated per call.
+//
+// Who needs it: a caller that must not allocate device memory while it runs, for example a
+// sampler embedded in a host application that reserves the GPU's memory for its own pool at
+// start-up (so a library cudaMalloc can fail at an arbitrary point), or a latency-critical loop
+// that must never enter the allocator or wait on its implicit synchronisation. Such a caller
+// allocates its inputs and outputs once, up front, and this entry point then touches no
+// allocator at all.
+//
+// The scratch lives in g_noalloc_scratch below: kNoAllocScratchBytes (32 MiB) on every GPU that
+// loads the library, held until the process exits. Its device address is looked up once per
+// device with cudaGetSymbolAddress (the host-side symbol is only a stand-in, not a device
+// address) by the entry point's first call on that device.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "pe_internal.h"
+#include "pe_kernels.h"
+#include "pespace_gb300.h"
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_dev[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device address of the scratch array on the current device (looked up once per device).
+pe_status scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return pe::set_error(PE_ECUDA, "pe_loglike_batch_noalloc: no current CUDA device");
+  }
+  if (dev < 0 || dev >= kMaxDevices) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: device index too large");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_scratch_dev[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      char msg[256];
+      snprintf(msg, sizeof(msg), "pe_loglike_batch_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return pe::set_error(PE_ECUDA, msg);
+    }
+    g_scratch_dev[dev] = p;
+  }
+  *out = g_scratch_dev[dev];
+  return PE_OK;
+}
+
+}  // namespace
+
+extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet, const double* theta, int B,
+                                              unsigned mode_mask, double* out_logl, double* out_dhhh,
+                                              int32_t* out_status, void* stream) {
+  pe::DetSet ds;
+  pe_status s0 = pe::detset_from_handles(dets, ndet, &ds);
+  if (s0 != PE_OK) return s0;
+  if (B < 1) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: B must be >= 1");
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: bad mode mask");
+  if (!device_ptr(theta) || !device_ptr(out_logl) || (out_dhhh && !device_ptr(out_dhhh)) ||
+      (out_status && !device_ptr(out_status)))
+    return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: theta and every output must be device pointers");
+  // Scratch layout: coefficients [B], active bins [P], tile offsets [P+1], tile partials [tiles][6].
+  const size_t P = (size_t)ndet * B;
+  size_t max_tiles = 0;
+  for (int i = 0; i < ndet; ++i) max_tiles += (size_t)B * ((ds.d[i].nb + pe::kTileBins - 1) / pe::kTileBins);
+  const size_t o_coef = 0;
+  const size_t o_nend = align256(o_coef + (size_t)B * sizeof(pe::SampleCoef));
+  const size_t o_off = align256(o_nend + P * sizeof(int));
+  const size_t o_part = align256(o_off + (P + 1) * sizeof(long long));
+  const size_t need = o_part + max_tiles * 6 * sizeof(double);
+  if (need > kNoAllocScratchBytes) {
+    char msg[320];
+    snprintf(msg, sizeof(msg),
+             "pe_loglike_batch_noalloc: B=%d on these grids needs %zu bytes of scratch, more than the fixed %zu; "
+             "split the batch (about %zu bytes per sample)",
+             B, need, kNoAllocScratchBytes, need / (size_t)B);
+    return pe::set_error(PE_EINVAL, msg);
+  }
+  void* base = nullptr;
+  pe_status s1 = scratch_address(&base);
+  if (s1 != PE_OK) return s1;
+  unsigned char* sc = static_cast<unsigned char*>(base);
+  pe::SampleCoef* coef = reinterpret_cast<pe::SampleCoef*>(sc + o_coef);
+  int* nend = reinterpret_cast<int*>(sc + o_nend);
+  long long* off = reinterpret_cast<long long*>(sc + o_off);
+  double* part = reinterpret_cast<double*>(sc + o_part);
+  // Every scratch element a kernel reads is written earlier in the same call (coefficients and
+  // active counts by the prep kernel, offsets by the scan, one partial per tile by the forward
+  // kernel), so nothing is cleared between calls.
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+    cudaGetLastError();
+    nsm = 1;
+  }
+  cudaError_t e = pe::launch_prep(theta, B, mode_mask, ds, coef, nend, out_status, st);
+  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, st);
+  const size_t g = max_tiles < (size_t)nsm * pe::fwd_blocks_per_sm() ? max_tiles : (size_t)nsm * pe::fwd_blocks_per_sm();
+  if (e == cudaSuccess) e = pe::launch_loglike_fwd(ds, B, coef, nend, off, part, (int)(g > 0 ? g : 1), st);
+  if (e == cudaSuccess) e = pe::launch_reduce(ds, B, off, part, coef, out_logl, out_dhhh, st);
+  if (e != cudaSuccess) {
+    char msg[256];
+    snprintf(msg, sizeof(msg), "pe_loglike_batch_noalloc: launch failed: %s", cudaGetErrorString(e));
+    return pe::set_error(PE_ECUDA, msg);
+  }
+  return PE_OK;
+}

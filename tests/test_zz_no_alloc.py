@@ -1,0 +1,65 @@
+"""pe_loglike_batch_noalloc: the batched log-likelihood for callers that cannot allocate device
+memory (for instance a sampler inside an application that has reserved the GPU's memory for its
+own pool). It must give what pe_loglike_batch gives, call after call, using only the library's
+fixed scratch array. This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+from paper_2602_12011_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2602_12011_gb300 import build as B
+    from paper_2602_12011_gb300 import _lib as L
+    B.build()
+    T = 2.0 ** 18
+    k0, nb = W.grid(T)
+    d = L.Detector(W.LISA, T, k0, nb)
+    d.inject(W.theta_injection(T), W.MODE_ALL, W.normals(nb, 31))
+    return torch, L, d, T
+
+
+def _run(torch, L, d, th, noalloc):
+    B = th.shape[0]
+    tt = torch.tensor(th, device="cuda")
+    logl = torch.empty(B, dtype=torch.float64, device="cuda")
+    dhhh = torch.empty((B, 1, 3, 2), dtype=torch.float64, device="cuda")
+    st = torch.empty(B, dtype=torch.int32, device="cuda")
+    fn = L.pe_loglike_batch_noalloc if noalloc else L.pe_loglike_batch
+    fn([d.handle], tt, B, W.MODE_ALL, logl, dhhh, st, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return logl.cpu().numpy(), dhhh.cpu().numpy(), st.cpu().numpy()
+
+
+def test_noalloc_matches_allocating_entry_point_on_two_calls(setup):
+    torch, L, d, T = setup
+    dd = d.data_norm().sum()
+    for seed, B in ((401, 96), (402, 37)):          # two calls in a row, different batches
+        th = W.draw_prior(B, seed, T)
+        th[5, 1] = 0.5                                # one out-of-domain sample
+        ref = _run(torch, L, d, th, noalloc=False)
+        got = _run(torch, L, d, th, noalloc=True)
+        np.testing.assert_array_equal(got[2], ref[2])
+        ok = ref[2] == 0
+        assert np.all(np.isneginf(got[0][~ok]))
+        scale = 0.5 * dd + np.abs(ref[1][ok, :, :, 0]).sum(axis=(1, 2)) + 0.5 * ref[1][ok, :, :, 1].sum(axis=(1, 2))
+        assert np.all(np.abs(got[0][ok] - ref[0][ok]) <= 1e-10 * scale)
+        assert np.all(np.abs(got[1][ok] - ref[1][ok]) <= 1e-10 * scale[:, None, None, None])
+
+
+def test_noalloc_rejects_oversize_and_host_buffers(setup):
+    torch, L, d, T = setup
+    B = 20000                                         # about 114 MB of scratch on this grid
+    th = torch.tensor(W.draw_prior(B, 3, T), device="cuda")
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.PeError) as e:
+        L.pe_loglike_batch_noalloc([d.handle], th, B, W.MODE_ALL, out)
+    assert e.value.status == L.PE_EINVAL and "scratch" in str(e.value)
+    with pytest.raises(L.PeError) as e:
+        L.pe_loglike_batch_noalloc([d.handle], W.draw_prior(4, 3, T), 4, W.MODE_ALL, np.zeros(4))
+    assert e.value.status == L.PE_EINVAL
