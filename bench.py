@@ -260,6 +260,22 @@ def main():
     torch.cuda.synchronize()
     batched_same = n_plain / (e0.elapsed_time(e1) / 1e3)
 
+    # ---- gradient evals/s: hand-written adjoint over the same batch, device-timed
+    grad_dev = torch.empty((B, 11), dtype=torch.float64, device="cuda")
+    ll_dev = torch.empty(B, dtype=torch.float64, device="cuda")
+    L.pe_loglike_grad_batch(hs, th_dev, B, mask, ll_dev, grad_dev, None, stream)
+    Kg = max(2, K // 2)
+    gms = []
+    for k in range(Kg):
+        flush.zero_()
+        e0.record(stream)
+        L.pe_loglike_grad_batch(hs, th_dev, B, mask, ll_dev, grad_dev, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gms.append(e0.elapsed_time(e1))
+    grad_value = world * B * Kg / (sum(gms) / 1e3)
+    grad_ok = bool(torch.isfinite(grad_dev).all().item())
+
     # ---- end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of logL
     th_host = torch.tensor(theta).pin_memory()
     out_host = torch.empty(B, dtype=torch.float64).pin_memory()
@@ -303,6 +319,8 @@ def main():
                     "d2h_bytes_per_step": int(B * 8)},
             "plain_path": {"value": plain_value, "unit": UNIT, "samples": n_plain,
                            "batched_same_samples": batched_same},
+            "grad": {"value": grad_value, "unit": "grad evals/s", "ms_per_step": sum(gms) / Kg, "steps": Kg,
+                     "finite": grad_ok},
             "gpu_launches": 4 * K,
             "clocks": clk,
             "results_finite": result_ok}

@@ -274,3 +274,47 @@ def loglike(dets, theta, mode_mask: int, dhhh: bool = False, status: bool = Fals
     if status:
         res["status"] = stt
     return res
+
+
+def loglike_grad(dets, theta, mode_mask: int, status: bool = False, stream=None):
+    """Batched log-likelihood and its gradient d logL/d theta [B][11] (hand-written adjoint).
+    theta: numpy [B][11] (host path) or CUDA tensor (device path, outputs on the same stream)."""
+    hs = [d.handle for d in dets]
+    if isinstance(theta, np.ndarray):
+        th = np.ascontiguousarray(theta.reshape(-1, NPARAM).astype(np.float64))
+        B = th.shape[0]
+        ll = np.zeros(B)
+        g = np.zeros((B, NPARAM))
+        stt = np.zeros(B, dtype=np.int32) if status else None
+    else:
+        import torch
+        th = theta.reshape(-1, NPARAM).contiguous()
+        B = th.shape[0]
+        ll = torch.empty(B, dtype=torch.float64, device=th.device)
+        g = torch.empty((B, NPARAM), dtype=torch.float64, device=th.device)
+        stt = torch.empty(B, dtype=torch.int32, device=th.device) if status else None
+        if stream is None:
+            stream = torch.cuda.current_stream(th.device)
+    pe_loglike_grad_batch(hs, th, B, mode_mask, ll, g, stt, stream)
+    res = {"logl": ll, "grad": g}
+    if status:
+        res["status"] = stt
+    return res
+
+
+def fisher(dets, theta, mode_mask: int, stream=None):
+    """Fisher matrices F[B][11][11] = <dh/dtheta_i | dh/dtheta_j> (summed over detectors, channels)."""
+    hs = [d.handle for d in dets]
+    if isinstance(theta, np.ndarray):
+        th = np.ascontiguousarray(theta.reshape(-1, NPARAM).astype(np.float64))
+        B = th.shape[0]
+        F = np.zeros((B, NPARAM, NPARAM))
+    else:
+        import torch
+        th = theta.reshape(-1, NPARAM).contiguous()
+        B = th.shape[0]
+        F = torch.empty((B, NPARAM, NPARAM), dtype=torch.float64, device=th.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(th.device)
+    pe_fisher(hs, th, B, mode_mask, F, stream)
+    return F

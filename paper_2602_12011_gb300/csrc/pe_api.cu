@@ -5,12 +5,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "pe_internal.h"
+#include "pe_grad.h"
 #include "pe_kernels.h"
 #include "pe_measure.h"
 #include "pespace_gb300.h"
@@ -421,15 +423,107 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
 
 pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
                                 double* out_logl, double* out_grad, int32_t* out_status, void* stream) {
-  (void)dets; (void)ndet; (void)theta; (void)B; (void)mode_mask; (void)out_logl; (void)out_grad;
-  (void)out_status; (void)stream;
-  return fail(PE_ESTATE, "pe_loglike_grad_batch is not available in this build");
+  pe::DetSet ds;
+  pe_status s0 = check_dets(dets, ndet, &ds);
+  if (s0 != PE_OK) return s0;
+  if (theta == nullptr || out_grad == nullptr) return fail(PE_EINVAL, "theta/out_grad is NULL");
+  if (B < 1 || B > (1 << 20)) return fail(PE_EINVAL, "B=%d outside [1, 2^20]", B);
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch sc(st);
+  const int P = ndet * B;
+  long long max_tiles = 0;
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * ((ds.d[i].nb + pe::kTileBins - 1) / pe::kTileBins);
+  const double* th = theta;
+  if (!is_device_ptr(theta)) {
+    double* t = nullptr;
+    PE_CUDA(sc.alloc(&t, (size_t)B * PE_NPARAM));
+    PE_CUDA(cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+    th = t;
+  }
+  pe::SampleCoef* coef = nullptr;
+  pe::SampleGrad* sg = nullptr;
+  int* nend = nullptr;
+  long long* off = nullptr;
+  double* part = nullptr;
+  const int W = pe::grad_partial_width();
+  PE_CUDA(sc.alloc(&coef, B));
+  PE_CUDA(sc.alloc(&sg, B));
+  PE_CUDA(sc.alloc(&nend, P));
+  PE_CUDA(sc.alloc(&off, P + 1));
+  PE_CUDA(sc.alloc(&part, (size_t)max_tiles * W));
+  const bool h_logl = out_logl && !is_device_ptr(out_logl);
+  const bool h_grad = !is_device_ptr(out_grad);
+  const bool h_stat = out_status && !is_device_ptr(out_status);
+  double* logl = out_logl;
+  double* grad = out_grad;
+  int32_t* stat = out_status;
+  if (h_logl) PE_CUDA(sc.alloc(&logl, B));
+  if (h_grad) PE_CUDA(sc.alloc(&grad, (size_t)B * PE_NPARAM));
+  if (h_stat) PE_CUDA(sc.alloc(&stat, B));
+  PE_CUDA(pe::launch_prep_grad(th, B, mode_mask, ds, coef, sg, nend, stat, st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, st));
+  const long long g = std::min<long long>(max_tiles, (long long)sm_count() * pe::fwd_blocks_per_sm());
+  void* prof = nullptr;
+  pe::profile_begin(st, &prof);
+  PE_CUDA(pe::launch_grad_fwd(ds, B, coef, sg, nend, off, part, (int)std::max<long long>(g, 1), st));
+  pe::profile_end(st, prof);
+  PE_CUDA(pe::launch_grad_reduce(ds, B, off, part, coef, sg, logl, grad, st));
+  if (h_logl) PE_CUDA(cudaMemcpyAsync(out_logl, logl, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (h_grad)
+    PE_CUDA(cudaMemcpyAsync(out_grad, grad, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (h_stat) PE_CUDA(cudaMemcpyAsync(out_status, stat, (size_t)B * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (h_logl || h_grad || h_stat) PE_CUDA(cudaStreamSynchronize(st));
+  return PE_OK;
 }
 
 pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask, double* out_F,
                     void* stream) {
-  (void)dets; (void)ndet; (void)theta; (void)B; (void)mode_mask; (void)out_F; (void)stream;
-  return fail(PE_ESTATE, "pe_fisher is not available in this build");
+  pe::DetSet ds;
+  pe_status s0 = check_dets(dets, ndet, &ds);
+  if (s0 != PE_OK) return s0;
+  if (theta == nullptr || out_F == nullptr) return fail(PE_EINVAL, "theta/out_F is NULL");
+  if (B < 1 || B > (1 << 16)) return fail(PE_EINVAL, "B=%d outside [1, 2^16]", B);
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch sc(st);
+  const int P = ndet * B;
+  long long max_tiles = 0;
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * ((ds.d[i].nb + pe::kTileBins - 1) / pe::kTileBins);
+  const double* th = theta;
+  if (!is_device_ptr(theta)) {
+    double* t = nullptr;
+    PE_CUDA(sc.alloc(&t, (size_t)B * PE_NPARAM));
+    PE_CUDA(cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+    th = t;
+  }
+  pe::SampleCoef* coef = nullptr;
+  pe::SampleGrad* sg = nullptr;
+  int* nend = nullptr;
+  long long* off = nullptr;
+  double* part = nullptr;
+  const int W = pe::fisher_partial_width();
+  PE_CUDA(sc.alloc(&coef, B));
+  PE_CUDA(sc.alloc(&sg, B));
+  PE_CUDA(sc.alloc(&nend, P));
+  PE_CUDA(sc.alloc(&off, P + 1));
+  PE_CUDA(sc.alloc(&part, (size_t)max_tiles * W));
+  const bool h_F = !is_device_ptr(out_F);
+  double* F = out_F;
+  if (h_F) PE_CUDA(sc.alloc(&F, (size_t)B * 121));
+  PE_CUDA(pe::launch_prep_grad(th, B, mode_mask, ds, coef, sg, nend, nullptr, st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, st));
+  const long long g = std::min<long long>(max_tiles, (long long)sm_count() * 16);
+  void* prof = nullptr;
+  pe::profile_begin(st, &prof);
+  PE_CUDA(pe::launch_fisher_fwd(ds, B, coef, sg, nend, off, part, (int)std::max<long long>(g, 1), st));
+  pe::profile_end(st, prof);
+  PE_CUDA(pe::launch_fisher_reduce(ds, B, off, part, coef, F, st));
+  if (h_F) {
+    PE_CUDA(cudaMemcpyAsync(out_F, F, (size_t)B * 121 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PE_CUDA(cudaStreamSynchronize(st));
+  }
+  return PE_OK;
 }
 
 }  // extern "C"

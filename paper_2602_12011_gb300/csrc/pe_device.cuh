@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "pe_dual.cuh"
 #include "pe_internal.h"
 
 namespace pe {
@@ -16,9 +17,10 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
 // -2Y_lm(iota, 0) closed forms for the ten (l, +-m) the five modes need.
-__device__ inline void sylm_pair(int l, int m, double iota, double* ypos, double* yneg) {
-  double ci = cos(iota), si = sin(iota);
-  double c2 = cos(0.5 * iota), s2 = sin(0.5 * iota);
+template <class T>
+__device__ inline void sylm_pair(int l, int m, const T& iota, T* ypos, T* yneg) {
+  const T ci = cos(iota), si = sin(iota);
+  const T c2 = cos(0.5 * iota), s2 = sin(0.5 * iota);
   const double pi = kPi;
   if (l == 2 && m == 2) {
     *ypos = sqrt(5.0 / (64.0 * pi)) * (1.0 + ci) * (1.0 + ci);
@@ -27,15 +29,15 @@ __device__ inline void sylm_pair(int l, int m, double iota, double* ypos, double
     *ypos = sqrt(5.0 / (16.0 * pi)) * si * (1.0 + ci);
     *yneg = sqrt(5.0 / (16.0 * pi)) * si * (1.0 - ci);
   } else if (l == 3 && m == 3) {
-    double c4 = c2 * c2 * c2 * c2, s4 = s2 * s2 * s2 * s2;
+    const T c4 = c2 * c2 * c2 * c2, s4 = s2 * s2 * s2 * s2;
     *ypos = -sqrt(21.0 / (2.0 * pi)) * c4 * c2 * s2;
     *yneg = sqrt(21.0 / (2.0 * pi)) * c2 * s4 * s2;
   } else if (l == 3 && m == 2) {
-    double c4 = c2 * c2 * c2 * c2, s4 = s2 * s2 * s2 * s2;
+    const T c4 = c2 * c2 * c2 * c2, s4 = s2 * s2 * s2 * s2;
     *ypos = 0.5 * sqrt(7.0 / pi) * c4 * (3.0 * ci - 2.0);
     *yneg = sqrt(7.0 / (4.0 * pi)) * (3.0 * ci + 2.0) * s4;
   } else {  // (4, 4)
-    double cc = c2 * c2, ss = s2 * s2;
+    const T cc = c2 * c2, ss = s2 * s2;
     *ypos = 3.0 * sqrt(7.0 / pi) * cc * cc * cc * ss;
     *yneg = 3.0 * sqrt(7.0 / pi) * cc * ss * ss * ss;
   }
@@ -59,74 +61,80 @@ __device__ inline bool theta_valid(const double* th) {
 //  TaylorF2 phase (Buonanno et al. 2009 3.5PN; 1.5PN spin-orbit, 2PN aligned spin-spin),
 //  SPA amplitudes of the leading-order spherical modes (Blanchet 2014), C-infinity taper
 //  on the orbital frequency between 0.9 F_isco and F_isco, -2Y_lm polarisation weights
-//  (h_{l,-m} = (-1)^l h*_lm), sky frame.
-__device__ inline void sample_prep(const double* th, unsigned mask, SampleCoef& S) {
-  S.valid = theta_valid(th) ? 1 : 0;
-  const double Mtot = th[0], q = th[1], chi1 = th[2], chi2 = th[3], dL = th[4], iota = th[5];
-  const double phic = th[6], lam = th[7], bet = th[8], psi = th[9], tc = th[10];
-  const double M = Mtot * kMsunS;
-  const double D = dL * kGpcS;
-  const double eta = q / ((1.0 + q) * (1.0 + q));
-  const double m1 = q / (1.0 + q), m2 = 1.0 / (1.0 + q);
-  const double delta = (q - 1.0) / (q + 1.0);
+//  (h_{l,-m} = (-1)^l h*_lm), sky frame. T = double, or Dn for derivatives with respect to theta.
+template <class T>
+__device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, SampleCoefT<T>& S) {
+  S.valid = valid ? 1 : 0;
+  const T Mtot = th[0], q = th[1], chi1 = th[2], chi2 = th[3], dL = th[4], iota = th[5];
+  const T phic = th[6], lam = th[7], bet = th[8], psi = th[9], tc = th[10];
+  const T M = Mtot * kMsunS;
+  const T D = dL * kGpcS;
+  const T eta = q / ((1.0 + q) * (1.0 + q));
+  const T m1 = q / (1.0 + q), m2 = 1.0 / (1.0 + q);
+  const T delta = (q - 1.0) / (q + 1.0);
   const double pi = kPi;
-  const double bso = chi1 * (113.0 / 12.0 * m1 * m1 + 25.0 / 4.0 * eta) + chi2 * (113.0 / 12.0 * m2 * m2 + 25.0 / 4.0 * eta);
-  const double sss = 79.0 / 8.0 * eta * chi1 * chi2;
-  const double a5c = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
-  const double a6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi - 6848.0 / 21.0 * kEulerGamma +
-                     (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi) * eta + 76055.0 / 1728.0 * eta * eta -
-                     127825.0 / 1296.0 * eta * eta * eta;
-  const double n = 3.0 / (128.0 * eta);
+  const T bso = chi1 * (113.0 / 12.0 * m1 * m1 + 25.0 / 4.0 * eta) + chi2 * (113.0 / 12.0 * m2 * m2 + 25.0 / 4.0 * eta);
+  const T sss = 79.0 / 8.0 * eta * chi1 * chi2;
+  const T a5c = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+  const T a6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi - 6848.0 / 21.0 * kEulerGamma +
+                (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi) * eta + 76055.0 / 1728.0 * eta * eta -
+                127825.0 / 1296.0 * eta * eta * eta;
+  const T n = 3.0 / (128.0 * eta);
   S.tc = tc;
   S.P[0] = n;
-  S.P[1] = 0.0;
+  S.P[1] = 0.0 * n;
   S.P[2] = n * (3715.0 / 756.0 + 55.0 / 9.0 * eta);
   S.P[3] = n * (-16.0 * pi + 4.0 * bso);
   S.P[4] = n * (15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta - 10.0 * sss);
-  S.P[5] = n * a5c * (1.0 + 1.5 * log(6.0));          // alpha5 (1 + 3 ln(v/v_lso)), v_lso = 6^-1/2
-  S.P[6] = n * (a6c - 6848.0 / 21.0 * log(4.0));        // alpha6 - (6848/21) ln(4 v)
+  S.P[5] = n * a5c * (1.0 + 1.5 * ::log(6.0));          // alpha5 (1 + 3 ln(v/v_lso)), v_lso = 6^-1/2
+  S.P[6] = n * (a6c - 6848.0 / 21.0 * ::log(4.0));       // alpha6 - (6848/21) ln(4 v)
   S.P[7] = n * pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
   S.Q5 = n * 3.0 * a5c;
   S.Q6 = n * (-6848.0 / 21.0);
   // sky frame
-  double sl, cl, sb, cb, sp, cp;
+  T sl, cl, sb, cb, sp, cp;
   sincos(lam, &sl, &cl);
   sincos(bet, &sb, &cb);
   sincos(psi, &sp, &cp);
   S.k[0] = -(cb * cl); S.k[1] = -(cb * sl); S.k[2] = -sb;
-  const double u[3] = {sl, -cl, 0.0};
-  const double v[3] = {-(sb * cl), -(sb * sl), cb};
+  const T u[3] = {sl, -cl, 0.0 * sl};
+  const T v[3] = {-(sb * cl), -(sb * sl), cb};
   for (int i = 0; i < 3; ++i) { S.p[i] = cp * u[i] + sp * v[i]; S.q[i] = -(sp * u[i]) + cp * v[i]; }
   // modes
-  const double Fisco = 1.0 / (pow(6.0, 1.5) * 2.0 * pi * M);
+  const T Fisco = 1.0 / (::pow(6.0, 1.5) * 2.0 * pi * M);
   for (int md = 0; md < kNModes; ++md) {
-    ModeCoef& C = S.md[md];
+    ModeCoefT<T>& C = S.md[md];
     const int l = kModeL[md], m = kModeM[md];
-    double hmag, argt;  // |H_lm| / x^(p/2) and arg(conj H_lm) in turns
+    T hmag;          // |H_lm| / x^(p/2)
+    double argt;     // arg(conj H_lm) in turns
     int p;
-    if (md == 0) { hmag = 1.0; argt = 0.0; p = 0; }
+    if (md == 0) { hmag = 1.0 + 0.0 * q; argt = 0.0; p = 0; }
     else if (md == 1) { hmag = delta / 3.0; argt = -0.25; p = 1; }
-    else if (md == 2) { hmag = 0.75 * sqrt(15.0 / 14.0) * delta; argt = 0.25; p = 1; }
-    else if (md == 3) { hmag = sqrt(5.0 / 7.0) / 3.0 * (1.0 - 3.0 * eta); argt = 0.0; p = 2; }
-    else { hmag = 8.0 / 9.0 * sqrt(5.0 / 7.0) * (1.0 - 3.0 * eta); argt = 0.5; p = 2; }
-    C.cm = cbrt(2.0 * pi * M / m);
+    else if (md == 2) { hmag = 0.75 * ::sqrt(15.0 / 14.0) * delta; argt = 0.25; p = 1; }
+    else if (md == 3) { hmag = ::sqrt(5.0 / 7.0) / 3.0 * (1.0 - 3.0 * eta); argt = 0.0; p = 2; }
+    else { hmag = 8.0 / 9.0 * ::sqrt(5.0 / 7.0) * (1.0 - 3.0 * eta); argt = 0.5; p = 2; }
+    C.cm = cbrt(2.0 * pi * M / double(m));
     C.icm = 1.0 / C.cm;
     C.lncm = log(C.cm);
     C.amp = 2.0 * pi * M * M / D * sqrt(eta / (3.0 * m)) * hmag * pow(C.cm, -3.5);
-    double ph = m * phic / (2.0 * pi) + 0.125 + argt;
+    const T ph = m * phic / (2.0 * pi) + (0.125 + argt);
     C.ph0 = ph - rint(ph);
-    C.mfac = m / (4.0 * pi);
-    C.tffac = m / (12.0 * pi);
-    double yp, yn;
+    C.mfac = 0.0 * q + m / (4.0 * pi);
+    C.tffac = 0.0 * q + m / (12.0 * pi);
+    T yp, yn;
     sylm_pair(l, m, iota, &yp, &yn);
     const double sgn = (l % 2) ? -1.0 : 1.0;
     C.Pp = 0.5 * (yp + sgn * yn);
     C.Pc = 0.5 * (sgn * yn - yp);
-    C.fend = m * Fisco;
-    C.ftap = 0.9 * m * Fisco;
+    C.fend = double(m) * Fisco;
+    C.ftap = 0.9 * double(m) * Fisco;
     C.p = p;
-    C.active = (S.valid && (mask & (1u << md)) && hmag != 0.0) ? 1 : 0;
+    C.active = (valid && (mask & (1u << md)) && val(hmag) != 0.0) ? 1 : 0;
   }
+}
+
+__device__ inline void sample_prep(const double* th, unsigned mask, SampleCoef& S) {
+  sample_prep_t<double>(th, theta_valid(th), mask, S);
 }
 
 // Spacecraft offsets delta_i from the constellation centre and the centre x_c, at time t.

@@ -1,0 +1,23 @@
+// pe_grad.h -- launch wrappers of the gradient and Fisher kernels (pe_grad.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pe_internal.h"
+
+namespace pe {
+
+cudaError_t launch_prep_grad(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef,
+                             SampleGrad* sgrad, int* nend, int* status, cudaStream_t st);
+cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad, const int* nend,
+                            const long long* off, double* part, int grid, cudaStream_t st);
+cudaError_t launch_grad_reduce(const DetSet& ds, int B, const long long* off, const double* part,
+                               const SampleCoef* coef, const SampleGrad* sgrad, double* logl, double* grad,
+                               cudaStream_t st);
+cudaError_t launch_fisher_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad,
+                              const int* nend, const long long* off, double* part, int grid, cudaStream_t st);
+cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, const double* part,
+                                 const SampleCoef* coef, double* F, cudaStream_t st);
+int grad_partial_width();
+int fisher_partial_width();
+
+}  // namespace pe

@@ -26,28 +26,53 @@ constexpr int kTileBins = 128;  // frequency bins per work tile = threads per CT
 //   |H~_lm(f)| = amp f^(-7/6) v^p w(f)   (w: Planck taper, 1 for f <= ftap, 0 for f >= fend),
 //   arg H~_lm(f) = 2 pi [ ph0 - f t_c - (m/4pi) Psi_PN(v) ] (turns, before the orbit's
 //   centre Doppler term), and the mode's tensor is H~ (Pp e+ + i Pc ex).
-struct ModeCoef {
-  double cm, icm, lncm;
-  double amp;
-  double ph0;
-  double mfac;      // m / (4 pi)
-  double tffac;     // m / (12 pi)
-  double Pp, Pc;
-  double fend, ftap;
-  int p;            // power of v in |H_lm|: 0 (22), 1 (21, 33), 2 (32, 44)
-  int active;       // 1 if the mode is in the mask and its amplitude is non-zero
+// Templated on the scalar so that the same code gives values (double) and, with device dual
+// numbers, their derivatives with respect to theta.
+template <class T>
+struct ModeCoefT {
+  T cm, icm, lncm;
+  T amp;
+  T ph0;
+  T mfac;       // m / (4 pi)
+  T tffac;      // m / (12 pi)
+  T Pp, Pc;
+  T fend, ftap;
+  int p;        // power of v in |H_lm|: 0 (22), 1 (21, 33), 2 (32, 44)
+  int active;   // 1 if the mode is in the mask and its amplitude is non-zero
 };
 
 // Per-sample coefficients. Psi_PN(v) = v^-5 sum_k P[k] v^k + ln v (Q5 + Q6 v) (TaylorF2 3.5PN,
 // already multiplied by 3/(128 eta)).
-struct SampleCoef {
-  double tc;
-  double P[8];
-  double Q5, Q6;
-  double k[3], p[3], q[3];   // propagation direction and polarisation frame
-  ModeCoef md[kNModes];
+template <class T>
+struct SampleCoefT {
+  T tc;
+  T P[8];
+  T Q5, Q6;
+  T k[3], p[3], q[3];   // propagation direction and polarisation frame
+  ModeCoefT<T> md[kNModes];
   int valid;
   int pad_;
+};
+
+using ModeCoef = ModeCoefT<double>;
+using SampleCoef = SampleCoefT<double>;
+
+// Derivatives of the per-sample coefficients with respect to theta that the adjoint needs
+// (the sparsity of the map theta -> coefficients is built in: P and Q depend on q, chi1, chi2;
+// amp on Mtot, q, dL; cm and the taper on Mtot; the polarisation weights on iota; the sky
+// frame on lambda, beta, psi).
+struct ModeGrad {
+  double dlnA_dM, dlnA_dq;   // d ln(amp)/d Mtot, d ln(amp)/d q
+  double dcm_dM;             // d cm / d Mtot
+  double dfend_dM;           // d fend / d Mtot (ftap = 0.9 fend)
+  double dPp_di, dPc_di;     // d Pp/d iota, d Pc/d iota
+};
+struct SampleGrad {
+  double dP_dq[8], dQ5_dq, dQ6_dq;
+  double dP3_dc1, dP4_dc1, dP3_dc2, dP4_dc2;
+  double dlnA_ddL;           // -1/dL
+  double dk[3][3], dp[3][3], dq[3][3];   // [component][lambda, beta, psi]
+  ModeGrad md[kNModes];
 };
 
 // Device view of one detector: grid, orbit constants and per-bin SoA tables.

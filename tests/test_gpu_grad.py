@@ -1,0 +1,167 @@
+"""GPU parity of the hand-written adjoint (gradient) and of the Fisher matrix against the oracle's
+dual-number derivatives, plus closed forms, central differences of the GPU log L itself, and the
+torch.autograd.Function wrapper (Sec. 2.2, Sec. 2.3 of arXiv:2602.12011)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_12011_gb300 import workloads as W
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Lb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2602_12011_gb300 import build as B
+    from paper_2602_12011_gb300 import _lib
+    B.build()
+    return _lib
+
+
+def _inj(T):
+    return np.array([1e6, 2.0, 0.5, 0.3, 25.8, 0.4, 1.3, 1.375, -1.2108, 2.659, 0.8 * T])
+
+
+def _setup(O, Lb, dets_T, inj, seed=12011):
+    ods, gds = [], []
+    for det, T in dets_T:
+        k0, nb = W.grid(T)
+        od = H.oracle_detector(O, det, T, k0, nb, inj, W.MODE_ALL, seed)
+        ods.append(od)
+        gds.append(H.library_detector(Lb, od))
+    return ods, gds
+
+
+def _check_grad(O, Lb, ods, gds, th, mask, rel=1e-8):
+    g = Lb.loglike_grad(gds, th, mask)
+    for s in range(th.shape[0]):
+        r = O.loglike(ods, th[s], mask)
+        scale = H.scale_of(r["dh"], r["hh"], r["dd"])
+        ll, gref = O.grad(ods, th[s], mask)
+        F = O.fisher(ods, th[s], mask)
+        assert abs(g["logl"][s] - ll) <= 1e-10 * scale
+        for i in range(11):
+            tol = rel * (abs(gref[i]) + math.sqrt(scale * max(F[i, i], 0.0)))
+            assert abs(g["grad"][s, i] - gref[i]) <= tol, (s, W.PARAM_NAMES[i], g["grad"][s, i], gref[i], tol)
+
+
+def test_grad_parity_lisa_hm(oracle_mod, Lb):
+    T = 2.0 ** 17
+    inj = _inj(T)
+    ods, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
+    th = np.vstack([inj + np.array([2e3, 0.01, 0.01, -0.02, 0.3, 0.02, 0.05, 1e-3, 1e-3, 0.02, 3.0]),
+                    W.draw_prior(5, 51, T)])
+    th[2, 0] = 1.5e7          # heavy: the taper region lies inside the band
+    _check_grad(oracle_mod, Lb, ods, gds, th, W.MODE_ALL)
+
+
+def test_grad_parity_tianqin_and_network(oracle_mod, Lb):
+    Ts = [(W.LISA, 2.0 ** 17), (W.TAIJI, 2.0 ** 16), (W.TIANQIN, 2.0 ** 16)]
+    inj = _inj(2.0 ** 16)
+    ods, gds = _setup(oracle_mod, Lb, Ts, inj, seed=7)
+    th = np.vstack([inj, W.draw_prior(2, 61, 2.0 ** 16)])
+    _check_grad(oracle_mod, Lb, ods[2:], gds[2:], th, W.MODE_ALL)     # TianQin alone (geocentric orbit)
+    _check_grad(oracle_mod, Lb, ods, gds, th, W.MODE_ALL)             # network
+
+
+def test_grad_single_modes_and_tdi15(oracle_mod, Lb):
+    T = 2.0 ** 16
+    inj = _inj(T)
+    det15 = dict(W.LISA, tdi_gen=15)
+    ods, gds = _setup(oracle_mod, Lb, [(det15, T)], inj, seed=3)
+    th = np.vstack([inj, W.draw_prior(2, 71, T)])
+    for mask in (0x01, 0x02, 0x04, 0x08, 0x10):
+        _check_grad(oracle_mod, Lb, ods, gds, th, mask)
+
+
+def test_grad_matches_central_differences_of_gpu_loglike(oracle_mod, Lb):
+    T = 2.0 ** 17
+    inj = _inj(T)
+    _, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
+    th = inj + np.array([1e3, 0.01, 0.02, -0.02, 0.1, 0.01, 0.05, 0.002, 0.002, 0.01, 2.0])
+    g = Lb.loglike_grad(gds, th[None, :], W.MODE_ALL)["grad"][0]
+    steps = np.array([1.0, 1e-5, 1e-5, 1e-5, 1e-4, 1e-6, 1e-6, 1e-7, 1e-7, 1e-6, 1e-3])
+    for i in range(11):
+        tp, tm = th.copy(), th.copy()
+        tp[i] += steps[i]
+        tm[i] -= steps[i]
+        ll = Lb.loglike(gds, np.vstack([tp, tm]), W.MODE_ALL)["logl"]
+        fd = (ll[0] - ll[1]) / (2 * steps[i])
+        assert g[i] == pytest.approx(fd, rel=2e-4, abs=1e-6 * np.abs(g).max()), W.PARAM_NAMES[i]
+
+
+def test_grad_out_of_domain_and_bitwise_logl(oracle_mod, Lb):
+    T = 2.0 ** 16
+    inj = _inj(T)
+    _, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
+    th = W.draw_prior(6, 81, T)
+    th[2, 1] = 0.3
+    g = Lb.loglike_grad(gds, th, W.MODE_ALL, status=True)
+    assert g["status"][2] == 1 and np.isneginf(g["logl"][2]) and np.all(g["grad"][2] == 0)
+    ll = Lb.loglike(gds, th, W.MODE_ALL)["logl"]
+    ok = g["status"] == 0
+    assert np.all(np.abs(g["logl"][ok] - ll[ok]) <= 1e-12 * np.abs(ll[ok]))
+
+
+def test_fisher_parity(oracle_mod, Lb):
+    T = 2.0 ** 17
+    inj = _inj(T)
+    ods, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
+    th = np.vstack([inj, W.draw_prior(1, 91, T)])
+    F = Lb.fisher(gds, th, W.MODE_ALL)
+    for s in range(th.shape[0]):
+        Fr = oracle_mod.fisher(ods, th[s], W.MODE_ALL)
+        d = np.sqrt(np.abs(np.outer(np.diag(Fr), np.diag(Fr))))
+        assert np.all(np.abs(F[s] - Fr) <= 1e-8 * d + 1e-300), np.max(np.abs(F[s] - Fr) / d)
+        np.testing.assert_array_equal(F[s], F[s].T)
+
+
+def test_fisher_closed_forms_on_gpu(oracle_mod, Lb):
+    """F_dLdL = <h|h>/dL^2 and, for (2,2) alone, F_phi_phi = 4 <h|h> (d h/d phi_c = 2 i h)."""
+    T = 2.0 ** 18
+    inj = _inj(T)
+    _, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
+    F = Lb.fisher(gds, inj[None, :], W.MODE_22)[0]
+    hh = Lb.loglike(gds, inj[None, :], W.MODE_22, dhhh=True)["dhhh"][0, :, :, 1].sum()
+    assert F[4, 4] == pytest.approx(hh / inj[4] ** 2, rel=1e-10)
+    assert F[6, 6] == pytest.approx(4 * hh, rel=1e-10)
+
+
+def test_autograd_function(oracle_mod, Lb):
+    import torch
+    from paper_2602_12011_gb300 import autograd as AG
+    T = 2.0 ** 16
+    inj = _inj(T)
+    _, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
+    th = torch.tensor(W.draw_prior(4, 5, T), device="cuda", requires_grad=True)
+    ll = AG.loglike(th, gds, W.MODE_ALL)
+    w = torch.tensor([1.0, -2.0, 0.5, 3.0], dtype=torch.float64, device="cuda")
+    (ll * w).sum().backward()
+    ref = Lb.loglike_grad(gds, th.detach(), W.MODE_ALL)
+    torch.testing.assert_close(th.grad, w[:, None] * ref["grad"], rtol=0, atol=0)
+    torch.testing.assert_close(ll.detach(), ref["logl"], rtol=0, atol=0)
+
+
+def test_grad_full_size_sampled(oracle_mod, Lb):
+    """The gradient over the benchmark batch (T = 2^22 s, B = 1024, 5 modes) in one call; the
+    four heaviest samples are checked against the oracle's dual-number gradient."""
+    wl = W.batch_hm(1024)
+    det, T, k0, nb = wl["dets"][0]
+    od = H.oracle_detector(oracle_mod, det, T, k0, nb, wl["inj"], wl["inj_mask"], wl["noise_seed"])
+    gd = H.library_detector(Lb, od)
+    th = wl["theta"]
+    g = Lb.loglike_grad([gd], th, wl["mode_mask"])
+    assert np.all(np.isfinite(g["grad"]))
+    pick = np.argsort(th[:, 0])[-4:]
+    for s in pick:
+        r = oracle_mod.loglike([od], th[s], wl["mode_mask"])
+        scale = H.scale_of(r["dh"], r["hh"], r["dd"])
+        ll, gref = oracle_mod.grad([od], th[s], wl["mode_mask"])
+        F = oracle_mod.fisher([od], th[s], wl["mode_mask"])
+        for i in range(11):
+            tol = 1e-8 * (abs(gref[i]) + math.sqrt(scale * max(F[i, i], 0.0)))
+            assert abs(g["grad"][s, i] - gref[i]) <= tol, (s, W.PARAM_NAMES[i])
