@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-network", action="store_true")
     return ap.parse_args()
 
 
@@ -205,6 +206,10 @@ def main():
     def step():
         L.pe_loglike_batch(hs, th_dev, B, mask, out_dev, None, None, stream)
 
+    # project autotuner (set-up, untimed): register-budget variant and persistent grid size of the
+    # fused kernel for this workload; pe_loglike_batch then uses the cached choice
+    tuned = L.pe_autotune(hs, th_dev, B, mask)
+
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -260,6 +265,21 @@ def main():
     torch.cuda.synchronize()
     batched_same = n_plain / (e0.elapsed_time(e1) / 1e3)
 
+    # the plain path again through a B = 1 CUDA-graph plan (no per-call host work)
+    plan1 = L.Plan([gd], 1, mask, theta=th_dev[:1].clone(), autotune=False)
+    for i in range(4):
+        plan1.launch(stream)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(n_plain):
+        plan1.theta.copy_(th_dev[i:i + 1])
+        plan1.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_graph_value = n_plain / (e0.elapsed_time(e1) / 1e3)
+    plan1.close()
+
     # ---- gradient evals/s: hand-written adjoint over the same batch, device-timed
     grad_dev = torch.empty((B, 11), dtype=torch.float64, device="cuda")
     ll_dev = torch.empty(B, dtype=torch.float64, device="cuda")
@@ -275,6 +295,37 @@ def main():
         gms.append(e0.elapsed_time(e1))
     grad_value = world * B * Kg / (sum(gms) / 1e3)
     grad_ok = bool(torch.isfinite(grad_dev).all().item())
+
+    # ---- detector network (LISA 2^22 s + Taiji 2^21 s + TianQin 2^20 s), B = 4096, one CUDA-graph
+    # plan with autotuned launch parameters
+    net = None
+    if not args.no_network:
+        wn = W.network_hm(4096)
+        nds = []
+        for det_n, T_n, k0_n, nb_n in wn["dets"]:
+            dn = L.Detector(det_n, T_n, k0_n, nb_n)
+            dn.inject(wn["inj"], wn["inj_mask"], W.normals(nb_n, wn["noise_seed"]))
+            nds.append(dn)
+        thn = torch.tensor(wn["theta"] if rank == 0 else W.draw_prior(4096, W.SEED_BATCH_NET + 1000 * rank, 2.0 ** 20),
+                           device="cuda")
+        pn = L.Plan(nds, 4096, wn["mode_mask"], theta=thn, autotune=True)
+        for _ in range(3):
+            pn.launch(stream)
+        nms = []
+        for k in range(max(2, K // 2)):
+            flush.zero_()
+            e0.record(stream)
+            pn.launch(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nms.append(e0.elapsed_time(e1))
+        net = {"value": world * 4096 * len(nms) / (sum(nms) / 1e3), "unit": UNIT, "ms_per_step": sum(nms) / len(nms),
+               "workload": wn["name"], "detectors": "LISA(2^22 s)+Taiji(2^21 s)+TianQin(2^20 s)",
+               "launch": "one CUDA graph per step", "tuned": pn.info(),
+               "finite": bool(torch.isfinite(pn.logl).all().item())}
+        pn.close()
+        for dn in nds:
+            dn.close()
 
     # ---- end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of logL
     th_host = torch.tensor(theta).pin_memory()
@@ -318,7 +369,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * 11 * 8),
                     "d2h_bytes_per_step": int(B * 8)},
             "plain_path": {"value": plain_value, "unit": UNIT, "samples": n_plain,
-                           "batched_same_samples": batched_same},
+                           "graph_plan_value": plain_graph_value, "batched_same_samples": batched_same},
+            "network": net,
+            "tuning": tuned,
             "grad": {"value": grad_value, "unit": "grad evals/s", "ms_per_step": sum(gms) / Kg, "steps": Kg,
                      "finite": grad_ok},
             "gpu_launches": 4 * K,

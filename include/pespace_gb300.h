@@ -153,6 +153,30 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
 pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
                                    double* out_logl, double* out_dhhh, int32_t* out_status, void* stream);
 
+/* ---- Uneven-batch plans and the autotuner (spec growth: batched uneven launches) -------
+ * A plan is the whole pe_loglike_batch computation for fixed detectors, batch size, mode mask
+ * and fixed DEVICE buffers (theta [B][11], out_logl [B], optional out_dhhh [B][ndet][3][2] and
+ * out_status [B]), captured once into a CUDA graph with its scratch allocated at creation. Every
+ * (detector, sample) pair brings its own grid length and active bin range; all pairs run in one
+ * persistent launch over their 128-bin tiles. Refill theta in place and call pe_plan_launch on
+ * any stream; results equal pe_loglike_batch's bit for bit.
+ *   autotune = 1: if the tuning cache has no entry for this workload (GPU, SM count, batch size,
+ *   mode mask, grids), time the forward kernel's launch variants on the theta present at
+ *   creation and store the fastest. The cache is a JSON file at $PE_TUNE_CACHE, else
+ *   $XDG_CACHE_HOME/pespace_gb300/tune.json, else ~/.cache/pespace_gb300/tune.json.
+ *   Tuning picks only the kernel's register-budget variant and its persistent grid size, never
+ *   the tile, so it never changes a result. pe_loglike_batch also uses a cached choice.
+ * pe_autotune tunes (and caches) the same choice without building a plan (theta: device). */
+typedef struct pe_plan_s* pe_plan;
+pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode_mask, const double* theta_dev,
+                         double* out_logl_dev, double* out_dhhh_dev, int32_t* out_status_dev, int autotune,
+                         pe_plan* out);
+pe_status pe_plan_launch(pe_plan plan, void* stream);
+pe_status pe_plan_info(pe_plan plan, int* fwd_variant, int* ctas_per_sm, double* tuned_ms);
+pe_status pe_plan_destroy(pe_plan plan);
+pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev, int B, unsigned mode_mask,
+                      int* out_variant, int* out_ctas_per_sm, double* out_ms);
+
 /* Batched gradient d logL_s / d theta_s (hand-written adjoint of the same path, Sec. 2.3 on
  * automatic differentiation); arguments as pe_loglike_batch, plus out_grad [B][11]
  * (host or device). out_logl may be NULL. */

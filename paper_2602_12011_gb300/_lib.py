@@ -77,6 +77,13 @@ def lib():
         L.pe_fisher.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P]
         L.pe_loglike_batch_noalloc.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
         L.pe_loglike_batch_noalloc.restype = C.c_int
+        L.pe_plan_create.argtypes = [_P, C.c_int, C.c_int, C.c_uint, _P, _P, _P, _P, C.c_int, C.POINTER(_P)]
+        L.pe_plan_launch.argtypes = [_P, _P]
+        L.pe_plan_info.argtypes = [_P, _P, _P, _P]
+        L.pe_plan_destroy.argtypes = [_P]
+        L.pe_autotune.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P]
+        for name in ("pe_plan_create", "pe_plan_launch", "pe_plan_info", "pe_plan_destroy", "pe_autotune"):
+            getattr(L, name).restype = C.c_int
         L.pe_profile_enable.argtypes = [C.c_int]
         L.pe_profile_read.argtypes = [_P, _P]
         L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
@@ -318,3 +325,66 @@ def fisher(dets, theta, mode_mask: int, stream=None):
             stream = torch.cuda.current_stream(th.device)
     pe_fisher(hs, th, B, mode_mask, F, stream)
     return F
+
+
+def pe_plan_create(hs, theta, B: int, mode_mask: int, out_logl, out_dhhh=None, out_status=None,
+                   autotune: bool = True) -> int:
+    h = _P()
+    _check(lib().pe_plan_create(_handles(hs), len(hs), int(B), int(mode_mask), _ptr(theta), _ptr(out_logl),
+                                _ptr(out_dhhh), _ptr(out_status), int(bool(autotune)), C.byref(h)))
+    return h.value
+
+
+def pe_plan_launch(plan: int, stream=None):
+    _check(lib().pe_plan_launch(plan, _stream(stream)))
+
+
+def pe_plan_info(plan: int):
+    v, c, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(lib().pe_plan_info(plan, C.addressof(v), C.addressof(c), C.addressof(ms)))
+    return {"fwd_variant": v.value, "ctas_per_sm": c.value, "tuned_ms": ms.value}
+
+
+def pe_plan_destroy(plan: int):
+    _check(lib().pe_plan_destroy(plan))
+
+
+def pe_autotune(hs, theta, B: int, mode_mask: int):
+    v, c, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(lib().pe_autotune(_handles(hs), len(hs), _ptr(theta), int(B), int(mode_mask), C.addressof(v),
+                             C.addressof(c), C.addressof(ms)))
+    return {"fwd_variant": v.value, "ctas_per_sm": c.value, "tuned_ms": ms.value}
+
+
+class Plan:
+    """A CUDA-graph plan of the batched log-likelihood over fixed device buffers: refill
+    ``theta`` in place, then ``launch()``; ``logl`` (and ``dhhh``) hold the results."""
+
+    def __init__(self, dets, B: int, mode_mask: int, theta=None, dhhh: bool = False, autotune: bool = True):
+        import torch
+        self.dets = list(dets)
+        self.B = int(B)
+        self.theta = theta if theta is not None else torch.zeros((B, NPARAM), dtype=torch.float64, device="cuda")
+        self.logl = torch.empty(B, dtype=torch.float64, device=self.theta.device)
+        self.dhhh = torch.empty((B, len(dets), 3, 2), dtype=torch.float64, device=self.theta.device) if dhhh else None
+        self.status = torch.empty(B, dtype=torch.int32, device=self.theta.device)
+        self.handle = pe_plan_create([d.handle for d in self.dets], self.theta, B, mode_mask, self.logl, self.dhhh,
+                                     self.status, autotune)
+
+    def launch(self, stream=None):
+        import torch
+        pe_plan_launch(self.handle, stream if stream is not None else torch.cuda.current_stream(self.theta.device))
+
+    def info(self):
+        return pe_plan_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pe_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

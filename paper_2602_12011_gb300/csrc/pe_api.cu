@@ -15,6 +15,7 @@
 #include "pe_grad.h"
 #include "pe_kernels.h"
 #include "pe_measure.h"
+#include "pe_plan.h"
 #include "pespace_gb300.h"
 
 struct pe_detector_s {
@@ -407,10 +408,11 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep(th, B, mode_mask, ds, coef, nend, stat, st));
   PE_CUDA(pe::launch_scan_tiles(nend, P, off, st));
-  const long long g = std::min<long long>(max_tiles, (long long)sm_count() * pe::fwd_blocks_per_sm());
+  pe::TuneChoice tc = pe::default_choice();
+  pe::lookup_tuned(ds, B, mode_mask, &tc);
   void* prof = nullptr;
   pe::profile_begin(st, &prof);
-  PE_CUDA(pe::launch_loglike_fwd(ds, B, coef, nend, off, part, (int)std::max<long long>(g, 1), st));
+  PE_CUDA(pe::launch_loglike_fwd_variant(tc.variant, ds, B, coef, nend, off, part, pe::grid_for(tc, max_tiles), st));
   pe::profile_end(st, prof);
   PE_CUDA(pe::launch_reduce(ds, B, off, part, coef, logl, dhhh, st));
   if (h_logl) PE_CUDA(cudaMemcpyAsync(out_logl, logl, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st));

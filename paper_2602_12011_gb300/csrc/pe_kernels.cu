@@ -217,11 +217,14 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins /
 // Rows A2-A7: persistent fused kernel. Work item = one tile of kTileBins bins of one
 // (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns one bin,
 // sums the modes' TDI brackets in registers, forms A/E/T and the weighted products; the tile's
-// six sums (<d|h>_c, <h|h>_c) go to part[tile][6].
+// six sums (<d|h>_c, <h|h>_c) go to part[tile][6]. MINB (resident CTAs per SM requested from
+// the compiler) sets the register budget only; every variant does the same arithmetic in the
+// same order, so the autotuner's choice never changes a result.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTileBins) k_loglike_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
-                                                           const int* __restrict__ nend,
-                                                           const long long* __restrict__ off, double* part) {
+template <int MINB>
+__global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+                                                                 const int* __restrict__ nend,
+                                                                 const long long* __restrict__ off, double* part) {
   __shared__ double sh[6][kTileBins / 32];
   const int P = ds.ndet * B;
   const long long total = off[P];
@@ -341,8 +344,30 @@ cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, cudaStream
 }
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
                                double* part, int grid, cudaStream_t st) {
-  k_loglike_fwd<<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part);
+  return launch_loglike_fwd_variant(kFwdDefaultVariant, ds, B, coef, nend, off, part, grid, st);
+}
+cudaError_t launch_loglike_fwd_variant(int variant, const DetSet& ds, int B, const SampleCoef* coef, const int* nend,
+                                       const long long* off, double* part, int grid, cudaStream_t st) {
+  switch (variant) {
+    case 0: k_loglike_fwd<2><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    case 1: k_loglike_fwd<3><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    case 2: k_loglike_fwd<4><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
+}
+int fwd_variant_min_blocks(int variant) { return variant == 0 ? 2 : variant == 1 ? 3 : 4; }
+int fwd_variant_max_blocks_per_sm(int variant) {
+  int n = 0;
+  cudaError_t e = cudaSuccess;
+  switch (variant) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<2>, kTileBins, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<3>, kTileBins, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<4>, kTileBins, 0); break;
+    default: return 0;
+  }
+  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+  return n;
 }
 cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const double* part, const SampleCoef* coef,
                           double* logl, double* dhhh, cudaStream_t st) {

@@ -19,6 +19,13 @@ cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet&
 cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, cudaStream_t st);
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
                                double* part, int grid, cudaStream_t st);
+// Register-budget variants of the forward kernel (min resident CTAs per SM 2, 3, 4).
+constexpr int kFwdVariants = 3;
+constexpr int kFwdDefaultVariant = 1;
+cudaError_t launch_loglike_fwd_variant(int variant, const DetSet& ds, int B, const SampleCoef* coef, const int* nend,
+                                       const long long* off, double* part, int grid, cudaStream_t st);
+int fwd_variant_min_blocks(int variant);
+int fwd_variant_max_blocks_per_sm(int variant);
 cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const double* part, const SampleCoef* coef,
                           double* logl, double* dhhh, cudaStream_t st);
 cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, cudaStream_t st);
