@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-network", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -327,6 +328,43 @@ def main():
         for dn in nds:
             dn.close()
 
+    # ---- learned surrogate: trained on the GPU (set-up, untimed) on 2^20 prior samples, then the
+    # surrogate path against the plain path on one 16384-sample inference batch
+    sur = None
+    if not args.no_surrogate:
+        srg = L.Surrogate(seed=2605)
+        t_tr = time.perf_counter()
+        sl, _ = srg.train(torch.tensor(W.draw_prior(1 << 20, 2605, T), device="cuda"), 60, batch=1024, lr=2e-3)
+        torch.cuda.synchronize()
+        t_tr = time.perf_counter() - t_tr
+        Bs = 16384
+        ths = W.draw_prior(Bs, 2609 + rank, T)
+        tts = torch.tensor(ths, device="cuda")
+        outs = torch.empty(Bs, dtype=torch.float64, device="cuda")
+        srg.loglike([gd], tts, mask)
+        L.pe_loglike_batch(hs, tts, Bs, mask, outs, None, None, stream)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0.record(stream)
+        _, used = srg.loglike([gd], tts, mask)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1)
+        flush.zero_()
+        e0.record(stream)
+        L.pe_loglike_batch(hs, tts, Bs, mask, outs, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        tho = W.draw_prior(2048, 2606, T)
+        mm = srg.mismatch(gd, torch.tensor(tho, device="cuda"), mask).cpu().numpy()
+        inbox = (tho[:, 0] >= 3e5) & (tho[:, 1] <= 8.0)
+        sur = {"value": world * Bs / (ms_s / 1e3), "unit": UNIT, "plain_same_batch": world * Bs / (ms_p / 1e3),
+               "gain": ms_p / ms_s, "batch": Bs, "used_fraction": float(used.float().mean().item()),
+               "train_s": t_tr, "train_loss": sl, "heldout_pass_1e-3": float(np.mean(mm[inbox] <= 1e-3)),
+               "heldout_in_box": int(inbox.sum())}
+        srg.close()
+
     # ---- end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of logL
     th_host = torch.tensor(theta).pin_memory()
     out_host = torch.empty(B, dtype=torch.float64).pin_memory()
@@ -371,6 +409,7 @@ def main():
             "plain_path": {"value": plain_value, "unit": UNIT, "samples": n_plain,
                            "graph_plan_value": plain_graph_value, "batched_same_samples": batched_same},
             "network": net,
+            "surrogate": sur,
             "tuning": tuned,
             "grad": {"value": grad_value, "unit": "grad evals/s", "ms_per_step": sum(gms) / Kg, "steps": Kg,
                      "finite": grad_ok},

@@ -177,6 +177,53 @@ pe_status pe_plan_destroy(pe_plan plan);
 pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev, int B, unsigned mode_mask,
                       int* out_variant, int* out_ctas_per_sm, double* out_ms);
 
+/* ---- Learned waveform surrogate (spec growth: MLP on BF16 tensor cores + node spline) ----
+ * An MLP 11 -> 256 -> 256 -> 256 -> 2560 (BF16 weights and activations on tensor cores, FP32
+ * accumulation, SiLU) maps theta to, per mode, a phase residual and an amplitude ratio at 256
+ * frequency nodes log-spaced from 1e-4 Hz to the mode's taper end m F_isco. The phase residual is
+ * the plain generator's 3PN and 3.5PN phase terms (the series through 2.5PN, spins included, is
+ * evaluated exactly at the nodes as the baseline), the
+ * amplitude ratio its |H_lm| relative to the Newtonian power law. At the nodes the full response
+ * (t_f, orbit, links, TDI) is evaluated in FP64 and not-a-knot cubic splines in ln f carry the
+ * mode phase and the A/E/T transfer functions to every bin (the sparse-node interpolation idea the
+ * paper cites for lisabeta, Sec. 1). Samples outside the training box take the plain path.
+ *   pe_surrogate_create: random initial weights (seed); the library owns all device memory.
+ *   pe_surrogate_train: trains on the plain generator's node values of theta_train_dev
+ *     [n_train][11] (device) with Adam, MSE on standardised outputs, cosine learning rate, batch
+ *     % 64 == 0; out_loss_curve (host, nullable) receives the last minibatch loss of each epoch.
+ *   pe_surrogate_set_node_source: 0 (default) the network's node values; 1 the plain generator's
+ *     own node values (the same spline path without the network, for comparison).
+ *   pe_surrogate_set_box: the training box (defaults 3e5-1e7 Msun, q <= 8, |chi| <= 0.99: where
+ *     the held-out mismatch of the trained network stays <= 1e-3).
+ *   pe_surrogate_targets / pe_surrogate_predict: plain-generator / network node values
+ *     [B][5][2][256] (fp32, device) for theta [B][11] (device).
+ *   pe_surrogate_loglike_batch: log L per sample through the surrogate path (device pointers);
+ *     out_used_dev (nullable) = 1 where the surrogate was used, 0 where the plain path was.
+ *   pe_surrogate_mismatch: 1 - <h_s|h_p>/sqrt(<h_s|h_s><h_p|h_p>) between the surrogate and the
+ *     plain A/E/T signals on one detector (noise-weighted inner product, Eq. eq_inner_product;
+ *     App. A's mismatch without the maximisation over t_c and phi_c); 0 for fallback samples.
+ *   pe_surrogate_mlp_debug / pe_surrogate_get_weights: forward + backward of the network on given
+ *     inputs and output cotangents, and its weights, for gradient checks.
+ *   pe_surrogate_save / pe_surrogate_load: versioned binary checkpoint (weights, Adam state,
+ *     output standardisation, box, seed) with an FNV-1a checksum; PE_EINVAL on a bad file. */
+typedef struct pe_surrogate_s* pe_surrogate;
+pe_status pe_surrogate_create(uint64_t seed, pe_surrogate* out);
+pe_status pe_surrogate_destroy(pe_surrogate s);
+pe_status pe_surrogate_train(pe_surrogate s, const double* theta_train_dev, int n_train, int epochs, int batch,
+                             double lr, double* out_final_loss, float* out_loss_curve);
+pe_status pe_surrogate_set_box(pe_surrogate s, double mtot_lo, double mtot_hi, double q_max, double chi_max);
+pe_status pe_surrogate_set_node_source(pe_surrogate s, int source);
+pe_status pe_surrogate_targets(const double* theta_dev, int B, float* out_dev);
+pe_status pe_surrogate_predict(pe_surrogate s, const double* theta_dev, int B, float* out_dev);
+pe_status pe_surrogate_loglike_batch(pe_surrogate s, const pe_detector* dets, int ndet, const double* theta_dev, int B,
+                                     unsigned mode_mask, double* out_logl_dev, int32_t* out_used_dev, void* stream);
+pe_status pe_surrogate_mismatch(pe_surrogate s, pe_detector det, const double* theta_dev, int B, unsigned mode_mask,
+                                double* out_mismatch_dev, void* stream);
+pe_status pe_surrogate_mlp_debug(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads);
+pe_status pe_surrogate_get_weights(pe_surrogate s, float* out, int64_t* count);
+pe_status pe_surrogate_save(pe_surrogate s, const char* path);
+pe_status pe_surrogate_load(pe_surrogate s, const char* path);
+
 /* Batched gradient d logL_s / d theta_s (hand-written adjoint of the same path, Sec. 2.3 on
  * automatic differentiation); arguments as pe_loglike_batch, plus out_grad [B][11]
  * (host or device). out_logl may be NULL. */

@@ -84,6 +84,25 @@ def lib():
         L.pe_autotune.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P]
         for name in ("pe_plan_create", "pe_plan_launch", "pe_plan_info", "pe_plan_destroy", "pe_autotune"):
             getattr(L, name).restype = C.c_int
+        L.pe_surrogate_create.argtypes = [C.c_uint64, C.POINTER(_P)]
+        L.pe_surrogate_destroy.argtypes = [_P]
+        L.pe_surrogate_train.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]
+        L.pe_surrogate_set_box.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.pe_surrogate_set_node_source.argtypes = [_P, C.c_int]
+        L.pe_surrogate_set_node_source.restype = C.c_int
+        L.pe_surrogate_targets.argtypes = [_P, C.c_int, _P]
+        L.pe_surrogate_predict.argtypes = [_P, _P, C.c_int, _P]
+        L.pe_surrogate_loglike_batch.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P]
+        L.pe_surrogate_mismatch.argtypes = [_P, _P, _P, C.c_int, C.c_uint, _P, _P]
+        L.pe_surrogate_mlp_debug.argtypes = [_P, _P, C.c_int, _P, _P, _P]
+        L.pe_surrogate_get_weights.argtypes = [_P, _P, _P]
+        L.pe_surrogate_save.argtypes = [_P, C.c_char_p]
+        L.pe_surrogate_load.argtypes = [_P, C.c_char_p]
+        for name in ("pe_surrogate_create", "pe_surrogate_destroy", "pe_surrogate_train", "pe_surrogate_set_box",
+                     "pe_surrogate_targets", "pe_surrogate_predict", "pe_surrogate_loglike_batch",
+                     "pe_surrogate_mismatch", "pe_surrogate_mlp_debug", "pe_surrogate_get_weights",
+                     "pe_surrogate_save", "pe_surrogate_load"):
+            getattr(L, name).restype = C.c_int
         L.pe_profile_enable.argtypes = [C.c_int]
         L.pe_profile_read.argtypes = [_P, _P]
         L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
@@ -388,3 +407,101 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ---- learned surrogate ---------------------------------------------------------------------------
+SUR_NODES = 256
+SUR_NOUT = 5 * 2 * SUR_NODES
+SUR_NIN = 64
+
+
+class Surrogate:
+    """The BF16 tensor-core MLP surrogate with its node-spline likelihood path (device tensors)."""
+
+    def __init__(self, seed: int = 2605):
+        h = _P()
+        _check(lib().pe_surrogate_create(int(seed), C.byref(h)))
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().pe_surrogate_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_box(self, mtot_lo: float, mtot_hi: float, q_max: float = 10.0, chi_max: float = 0.99):
+        _check(lib().pe_surrogate_set_box(self.handle, float(mtot_lo), float(mtot_hi), float(q_max), float(chi_max)))
+
+    def set_node_source(self, source: int):
+        """0: network node values (default); 1: plain generator's node values (no network)."""
+        _check(lib().pe_surrogate_set_node_source(self.handle, int(source)))
+
+    def train(self, theta, epochs: int, batch: int = 1024, lr: float = 1e-3):
+        """theta: CUDA float64 tensor [n][11]. Returns (final loss, per-epoch loss curve)."""
+        n = int(theta.shape[0])
+        loss = C.c_double()
+        curve = np.zeros(epochs, dtype=np.float32)
+        _check(lib().pe_surrogate_train(self.handle, _ptr(theta.contiguous()), n, int(epochs), int(batch), float(lr),
+                                        C.addressof(loss), curve.ctypes.data))
+        return loss.value, curve
+
+    def predict(self, theta):
+        import torch
+        out = torch.empty((theta.shape[0], SUR_NOUT), dtype=torch.float32, device=theta.device)
+        _check(lib().pe_surrogate_predict(self.handle, _ptr(theta.contiguous()), int(theta.shape[0]), _ptr(out)))
+        return out
+
+    @staticmethod
+    def targets(theta):
+        import torch
+        out = torch.empty((theta.shape[0], SUR_NOUT), dtype=torch.float32, device=theta.device)
+        _check(lib().pe_surrogate_targets(_ptr(theta.contiguous()), int(theta.shape[0]), _ptr(out)))
+        return out
+
+    def loglike(self, dets, theta, mode_mask: int, stream=None):
+        import torch
+        B = int(theta.shape[0])
+        out = torch.empty(B, dtype=torch.float64, device=theta.device)
+        used = torch.empty(B, dtype=torch.int32, device=theta.device)
+        st = stream if stream is not None else torch.cuda.current_stream(theta.device)
+        _check(lib().pe_surrogate_loglike_batch(self.handle, _handles([d.handle for d in dets]), len(dets),
+                                                _ptr(theta.contiguous()), B, int(mode_mask), _ptr(out), _ptr(used),
+                                                _stream(st)))
+        return out, used
+
+    def mismatch(self, det, theta, mode_mask: int, stream=None):
+        import torch
+        B = int(theta.shape[0])
+        out = torch.empty(B, dtype=torch.float64, device=theta.device)
+        st = stream if stream is not None else torch.cuda.current_stream(theta.device)
+        _check(lib().pe_surrogate_mismatch(self.handle, det.handle, _ptr(theta.contiguous()), B, int(mode_mask),
+                                           _ptr(out), _stream(st)))
+        return out
+
+    def weights(self) -> np.ndarray:
+        n = C.c_int64()
+        _check(lib().pe_surrogate_get_weights(self.handle, None, C.addressof(n)))
+        w = np.zeros(n.value, dtype=np.float32)
+        _check(lib().pe_surrogate_get_weights(self.handle, w.ctypes.data, C.addressof(n)))
+        return w
+
+    def mlp_debug(self, x: np.ndarray, dy: np.ndarray):
+        """Forward + backward on host inputs x [B][64] and cotangents dy [B][2560] (fp32)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        dy = np.ascontiguousarray(dy, dtype=np.float32)
+        B = x.shape[0]
+        y = np.zeros((B, SUR_NOUT), dtype=np.float32)
+        g = np.zeros_like(self.weights())
+        _check(lib().pe_surrogate_mlp_debug(self.handle, x.ctypes.data, B, dy.ctypes.data, y.ctypes.data, g.ctypes.data))
+        return y, g
+
+    def save(self, path: str):
+        _check(lib().pe_surrogate_save(self.handle, path.encode()))
+
+    def load(self, path: str):
+        _check(lib().pe_surrogate_load(self.handle, path.encode()))

@@ -1,0 +1,1057 @@
+// pe_surrogate.cu -- the learned waveform surrogate (spec growth 4): an MLP
+// 11 -> 256 -> 256 -> 256 -> 2560 on BF16 tensor cores (pe_mlp.cu) predicts, per mode, a phase
+// residual and an amplitude ratio at 256 log-spaced frequency nodes; at those nodes the full
+// response is evaluated in FP64 and spline-interpolated onto the grid (the sparse-node idea the
+// paper cites for lisabeta, Sec. 1), feeding the same A/E/T weighted sums.
+//
+// Per mode m, nodes f_j = f_min exp(j h), j = 0..255, from f_min = 1e-4 Hz to the taper end
+// m F_isco(M) (detector independent). Targets come from the plain generator at the nodes:
+//   phase residual r_j = (m/2) [Psi_PN(v_j) - Psi_PN^{<=2.5PN}(v_j)]  (the 3PN and 3.5PN terms;
+//                        the series through 2.5PN, spins included, is evaluated exactly at the nodes)
+//   amplitude ratio a_j = |H_lm(x_j)|  (to the Newtonian power law (2 pi M^2/D) sqrt(eta/3m) x^-7/4)
+// At each node: t_f from the analytic derivative of the baseline plus the node-differenced
+// residual, the orbit at t_f, the six links and TDI give the transfer functions T_X, T_Y, T_Z per
+// unit mode amplitude, scaled by a_j, and the mode phase phi_nl (turns, centre Doppler included,
+// -f t_c excluded). Per bin: natural-knot-free (not-a-knot) cubic splines in u = ln f of these 7
+// quantities, H = A_N(f) w(f) e^{2 pi i (phi_nl - frac(f t_c))}, X' += H T_X ... The taper w and
+// frac(f t_c) stay exact per bin. Samples outside the training box take the plain path.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "pe_device.cuh"
+#include "pe_kernels.h"
+#include "pe_mlp.h"
+#include "pe_surrogate.h"
+
+namespace pe {
+
+constexpr int kNodes = 256;
+constexpr int kNout = kNModes * 2 * kNodes;   // [mode][kind][node], kind 0 phase residual, 1 amplitude ratio
+constexpr int kNin = 64;                      // 11 features, zero padded
+constexpr int kHid = 256;
+constexpr int kQ = 7;                         // spline quantities per (detector, sample, mode)
+constexpr double kFmin = 1e-4;                // lowest node frequency [Hz]
+
+// ---- features, targets ------------------------------------------------------------------------
+// Normalised inputs: the 11 parameters, each affinely scaled to order one (log10 for the mass).
+__global__ void k_features(const double* theta, int B, int Bpad, __nv_bfloat16* X) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Bpad) return;
+  float f[kNin];
+  for (int i = 0; i < kNin; ++i) f[i] = 0.f;
+  if (s < B) {
+    const double* t = theta + (size_t)s * PE_NPARAM;
+    f[0] = (float)((log10(fmax(t[0], 1.0)) - 6.5) / 0.5);
+    f[1] = (float)((t[1] - 5.5) / 2.6);
+    f[2] = (float)(t[2] / 0.57);
+    f[3] = (float)(t[3] / 0.57);
+    f[4] = (float)((t[4] - 25.5) / 14.1);
+    f[5] = (float)(t[5] - 1.5708);
+    f[6] = (float)((t[6] - 3.1416) / 1.81);
+    f[7] = (float)((t[7] - 3.1416) / 1.81);
+    f[8] = (float)(t[8] / 0.9);
+    f[9] = (float)((t[9] - 1.5708) / 0.91);
+    f[10] = (float)((t[10] - 3.4e6) / 1.2e6);
+  }
+  for (int i = 0; i < kNin; ++i) X[(size_t)s * kNin + i] = __float2bfloat16_rn(f[i]);
+}
+
+// node frequency of mode m for a sample with mass M [s]: f_j = f_min exp(j h)
+__device__ __forceinline__ double node_h(double M, int m) {
+  const double fend = m / (pow(6.0, 1.5) * 2.0 * kPi * M);
+  return log(fend / kFmin) / (kNodes - 1);
+}
+
+__device__ __forceinline__ double hmag_of(int md, double q) {
+  const double eta = q / ((1.0 + q) * (1.0 + q)), delta = (q - 1.0) / (q + 1.0);
+  if (md == 0) return 1.0;
+  if (md == 1) return delta / 3.0;
+  if (md == 2) return 0.75 * sqrt(15.0 / 14.0) * delta;
+  if (md == 3) return sqrt(5.0 / 7.0) / 3.0 * (1.0 - 3.0 * eta);
+  return 8.0 / 9.0 * sqrt(5.0 / 7.0) * (1.0 - 3.0 * eta);
+}
+
+// Per-sample coefficients of the plain generator and of its analytic baseline.
+__global__ void k_sur_prep(const double* theta, int B, unsigned mask, SampleCoef* S, SampleCoef* S0) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const double* t = theta + (size_t)s * PE_NPARAM;
+  SampleCoef a;
+  sample_prep(t, mask, a);
+  S[s] = a;
+  // baseline: the same phase series truncated after 2.5PN (the 3PN and 3.5PN terms, with the
+  // 3PN logarithm, are what the network learns)
+  SampleCoef b = a;
+  b.P[6] = 0.0;
+  b.P[7] = 0.0;
+  b.Q6 = 0.0;
+  // the surrogate's per-bin amplitude is the Newtonian power law (2 pi M^2/D) sqrt(eta/3m) x^-7/4;
+  // the mode factor |H_lm| travels with the transfer functions, so store amp / |H_lm| here
+  for (int md = 0; md < kNModes; ++md) {
+    const double hm = hmag_of(md, t[1]);
+    b.md[md].amp = (hm != 0.0) ? a.md[md].amp / hm : 0.0;
+  }
+  S0[s] = b;
+}
+
+__device__ __forceinline__ double psi_of(const SampleCoef& S, double v, double lnv, double* dv_out) {
+  const double iv = 1.0 / v;
+  double iv5 = iv * iv;
+  iv5 = iv5 * iv5 * iv;
+  double poly = S.P[7], dpol = 2.0 * S.P[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) {
+    poly = fma(poly, v, S.P[k]);
+    dpol = fma(dpol, v, (k - 5) * S.P[k]);
+  }
+  if (dv_out) *dv_out = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
+  return fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
+}
+
+// Plain-generator node values (raw): out[s][(md*2 + kind)*kNodes + j].
+__global__ void k_targets(const double* theta, int B, const SampleCoef* S, const SampleCoef* S0, float* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * kNModes * kNodes) return;
+  const int j = (int)(i % kNodes);
+  const int md = (int)((i / kNodes) % kNModes);
+  const int s = (int)(i / ((long long)kNodes * kNModes));
+  const double* t = theta + (size_t)s * PE_NPARAM;
+  const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
+  const double M = t[0] * kMsunS;
+  const double f = kFmin * exp(j * node_h(M, mm));
+  const double v = cbrt(2.0 * kPi * M * f / mm);
+  const double lnv = log(v);
+  const double r = 0.5 * mm * (psi_of(S[s], v, lnv, nullptr) - psi_of(S0[s], v, lnv, nullptr));
+  const int p = S[s].md[md].p;
+  const double a = hmag_of(md, t[1]) * (p >= 1 ? v : 1.0) * (p >= 2 ? v : 1.0);
+  out[(size_t)s * kNout + (md * 2 + 0) * kNodes + j] = (float)r;
+  out[(size_t)s * kNout + (md * 2 + 1) * kNodes + j] = (float)a;
+}
+
+// column mean/std over n rows (fixed order, FP64)
+__global__ void k_colstats(const float* T, long long n, float* mean, float* stdv) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= kNout) return;
+  double s = 0.0, s2 = 0.0;
+  for (long long r = 0; r < n; ++r) {
+    const double x = T[r * kNout + c];
+    s += x;
+    s2 += x * x;
+  }
+  const double mu = s / n;
+  const double var = fmax(s2 / n - mu * mu, 0.0);
+  const double sd = sqrt(var);
+  mean[c] = (float)mu;
+  stdv[c] = (float)(sd > 1e-6 * (fabs(mu) + 1e-30) && sd > 1e-30 ? sd : 1.0);
+}
+
+// The phase outputs of one mode share one scale (the largest per-node std of that mode), so the
+// standardised loss weighs phase errors in radians, as the mismatch does; amplitude ratios keep
+// their per-node scale.
+__global__ void k_group_phase_scale(float* stdv) {
+  const int md = threadIdx.x;
+  if (md >= kNModes) return;
+  float mx = 0.f;
+  for (int j = 0; j < kNodes; ++j) mx = fmaxf(mx, stdv[(md * 2) * kNodes + j]);
+  for (int j = 0; j < kNodes; ++j) stdv[(md * 2) * kNodes + j] = mx > 0.f ? mx : 1.f;
+}
+
+__global__ void k_standardize(float* T, long long n, const float* mean, const float* stdv) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * kNout) return;
+  const int c = (int)(i % kNout);
+  T[i] = (T[i] - mean[c]) / stdv[c];
+}
+
+__global__ void k_gather_rows(const __nv_bfloat16* X, const float* T, const int* idx, int b, __nv_bfloat16* Xb,
+                              float* Tb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (long long)b * kNin) {
+    const int r = (int)(i / kNin), c = (int)(i % kNin);
+    Xb[i] = X[(size_t)idx[r] * kNin + c];
+  }
+  if (i < (long long)b * kNout) {
+    const int r = (int)(i / kNout), c = (int)(i % kNout);
+    Tb[i] = T[(size_t)idx[r] * kNout + c];
+  }
+}
+
+// ---- node response and splines ---------------------------------------------------------------
+__device__ __forceinline__ bool in_box(const double* t, const SurBox& bx) {
+  return t[0] >= bx.mlo && t[0] <= bx.mhi && t[1] <= bx.qmax && fabs(t[2]) <= bx.chimax && fabs(t[3]) <= bx.chimax;
+}
+
+// Per (detector I, sample s, mode md, node j): the 7 spline quantities.
+// Y: de-standardised MLP outputs [Bpad][kNout]; nodes out: [I][s][md][q][j].
+__global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleCoef* S0, const float* Y,
+                            const double* theta, SurBox bx, double* nodes) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)ds.ndet * B * kNModes * kNodes;
+  if (i >= total) return;
+  const int j = (int)(i % kNodes);
+  const int md = (int)((i / kNodes) % kNModes);
+  const int s = (int)((i / ((long long)kNodes * kNModes)) % B);
+  const int I = (int)(i / ((long long)kNodes * kNModes * B));
+  double* q = nodes + ((((size_t)I * B + s) * kNModes + md) * kQ) * kNodes + j;
+  const SampleCoef& Sa = S[s];
+  const ModeCoef& C = Sa.md[md];
+  if (!C.active || !in_box(theta + (size_t)s * PE_NPARAM, bx)) {
+    for (int k = 0; k < kQ; ++k) q[k * kNodes] = 0.0;
+    return;
+  }
+  const DetDev& D = ds.d[I];
+  const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
+  const double M = theta[(size_t)s * PE_NPARAM] * kMsunS;
+  const double h = node_h(M, mm);
+  const double f = kFmin * exp(j * h);
+  const double v = cbrt(2.0 * kPi * M * f / mm);
+  const double lnv = log(v);
+  double D0;
+  const double psi0 = psi_of(S0[s], v, lnv, &D0);
+  const float* y = Y + (size_t)s * kNout;
+  const double r = y[(md * 2 + 0) * kNodes + j];
+  const double amp_ratio = y[(md * 2 + 1) * kNodes + j];
+  // residual derivative in u = ln f by node differences (one-sided at the ends)
+  double drdu;
+  if (j == 0) drdu = (-3.0 * r + 4.0 * y[(md * 2) * kNodes + 1] - y[(md * 2) * kNodes + 2]) / (2.0 * h);
+  else if (j == kNodes - 1)
+    drdu = (3.0 * r - 4.0 * y[(md * 2) * kNodes + kNodes - 2] + y[(md * 2) * kNodes + kNodes - 3]) / (2.0 * h);
+  else drdu = (y[(md * 2) * kNodes + j + 1] - y[(md * 2) * kNodes + j - 1]) / (2.0 * h);
+  const double tf = Sa.tc + C.tffac / f * D0 + drdu / (2.0 * kPi * f);
+  double xc[3], dl[3][3];
+  orbit_offsets(D, tf, xc, dl);
+  const double kxc = Sa.k[0] * xc[0] + Sa.k[1] * xc[1] + Sa.k[2] * xc[2];
+  const double phi = C.ph0 - (0.5 * mm * psi0 + r) / (2.0 * kPi) - f * kxc;
+  // link transfer functions per unit mode amplitude at the node frequency
+  double sa, ca;
+  sincospi(f * D.L, &sa, &ca);
+  double s2, c2;
+  sincospi(2.0 * f * D.L, &s2, &c2);
+  const double2 z = make_double2(c2, -s2);
+  const double a = kPi * f * D.L;
+  double2 G[3], U[3], V[3];
+  for (int l = 0; l < 3; ++l) {
+    const int rr = l, ss = (l + 1) % 3, tt = (l + 2) % 3;
+    double n0 = dl[rr][0] - dl[ss][0], n1 = dl[rr][1] - dl[ss][1], n2 = dl[rr][2] - dl[ss][2];
+    const double inv = rsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    n0 *= inv; n1 *= inv; n2 *= inv;
+    const double kn = Sa.k[0] * n0 + Sa.k[1] * n1 + Sa.k[2] * n2;
+    const double np = Sa.p[0] * n0 + Sa.p[1] * n1 + Sa.p[2] * n2;
+    const double nq = Sa.q[0] * n0 + Sa.q[1] * n1 + Sa.q[2] * n2;
+    const double2 gam = make_double2(C.Pp * (np * np - nq * nq), C.Pc * 2.0 * np * nq);
+    const double kd = Sa.k[0] * dl[tt][0] + Sa.k[1] * dl[tt][1] + Sa.k[2] * dl[tt][2];
+    double se, ce;
+    sincospi(f * kd, &se, &ce);
+    G[l] = cmul(make_double2(ce, se), gam);
+    const double u1 = a * (1.0 - kn), u2 = a * (1.0 + kn);
+    const double sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : sin(u1) / u1;
+    const double spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : sin(u2) / u2;
+    U[l] = make_double2(fma(z.x, spl, sm), z.y * spl);
+    V[l] = make_double2(fma(z.x, sm, spl), z.y * sm);
+  }
+  const double2 TX = csub(cmul(G[2], V[2]), cmul(G[0], U[0]));
+  const double2 TY = csub(cmul(G[0], V[0]), cmul(G[1], U[1]));
+  const double2 TZ = csub(cmul(G[1], V[1]), cmul(G[2], U[2]));
+  q[0 * kNodes] = phi;
+  q[1 * kNodes] = TX.x * amp_ratio;
+  q[2 * kNodes] = TX.y * amp_ratio;
+  q[3 * kNodes] = TY.x * amp_ratio;
+  q[4 * kNodes] = TY.y * amp_ratio;
+  q[5 * kNodes] = TZ.x * amp_ratio;
+  q[6 * kNodes] = TZ.y * amp_ratio;
+}
+
+// Not-a-knot cubic spline on the uniform nodes u_j = u_0 + j h of one quantity; writes, per
+// interval j, (a, b, c, d) of y(u_j + t) = a + b t + c t^2 + d t^3 in place over coef[j][4].
+// With uniform spacing the not-a-knot conditions give M_1 = r_1/6, M_{N-2} = r_{N-2}/6
+// (r_j = 6 (y_{j+1} - 2 y_j + y_{j-1})/h^2); the interior (1, 4, 1) system is solved by Thomas.
+__global__ void k_spline(const double* nodes, long long nsys, const double* hs, double* coef) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsys) return;
+  const double* y = nodes + i * kNodes;
+  double* cf = coef + i * (kNodes - 1) * 4;
+  const double h = hs[i / kQ];
+  if (!(h > 0.0)) {
+    for (int j = 0; j < kNodes - 1; ++j) cf[4 * j] = cf[4 * j + 1] = cf[4 * j + 2] = cf[4 * j + 3] = 0.0;
+    return;
+  }
+  constexpr int N = kNodes;
+  double Mv[N];
+  double cp[N];
+  const double ih2 = 6.0 / (h * h);
+  Mv[1] = ih2 * (y[2] - 2.0 * y[1] + y[0]) / 6.0;
+  Mv[N - 2] = ih2 * (y[N - 1] - 2.0 * y[N - 2] + y[N - 3]) / 6.0;
+  // interior rows j = 2 .. N-3: M_{j-1} + 4 M_j + M_{j+1} = r_j, with M_1, M_{N-2} known
+  const int lo = 2, hi = N - 3;
+  double dprev = 0.0;
+  for (int j = lo; j <= hi; ++j) {
+    double rj = ih2 * (y[j + 1] - 2.0 * y[j] + y[j - 1]);
+    if (j == lo) rj -= Mv[1];
+    if (j == hi) rj -= Mv[N - 2];
+    const double denom = 4.0 - (j == lo ? 0.0 : cp[j - 1]);
+    cp[j] = 1.0 / denom;
+    dprev = (rj - (j == lo ? 0.0 : dprev)) / denom;
+    Mv[j] = dprev;  // holds d'_j for now
+  }
+  for (int j = hi - 1; j >= lo; --j) Mv[j] -= cp[j] * Mv[j + 1];
+  Mv[0] = 2.0 * Mv[1] - Mv[2];
+  Mv[N - 1] = 2.0 * Mv[N - 2] - Mv[N - 3];
+  for (int j = 0; j < N - 1; ++j) {
+    cf[4 * j + 0] = y[j];
+    cf[4 * j + 1] = (y[j + 1] - y[j]) / h - h * (2.0 * Mv[j] + Mv[j + 1]) / 6.0;
+    cf[4 * j + 2] = 0.5 * Mv[j];
+    cf[4 * j + 3] = (Mv[j + 1] - Mv[j]) / (6.0 * h);
+  }
+}
+
+__global__ void k_node_h(const double* theta, int B, double* hs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * kNModes) return;
+  const int s = i / kNModes, md = i % kNModes;
+  const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
+  hs[i] = node_h(theta[(size_t)s * PE_NPARAM] * kMsunS, mm);
+}
+
+// Spline evaluation of one mode at one bin: adds H T_X, H T_Y, H T_Z to acc.
+__device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, const BinIn& B, double u,
+                                             const double* cf, double h, double2 acc[3]) {
+  const double uj = (u - log(kFmin)) / h;
+  int j = (int)floor(uj);
+  j = j < 0 ? 0 : (j > kNodes - 2 ? kNodes - 2 : j);
+  const double t = (uj - j) * h;
+  double val[kQ];
+#pragma unroll
+  for (int k = 0; k < kQ; ++k) {
+    const double* c = cf + ((size_t)k * (kNodes - 1) + j) * 4;
+    val[k] = fma(fma(fma(c[3], t, c[2]), t, c[1]), t, c[0]);
+  }
+  double w = 1.0;
+  if (B.f > C.ftap) {
+    const double span = C.fend - C.ftap;
+    const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
+    w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
+  }
+  double ph = val[0] - B.frc;
+  ph -= rint(ph);
+  double sph, cph;
+  sincospi(2.0 * ph, &sph, &cph);
+  const double amp = ampN * B.fm76 * w;  // Newtonian power law; the mode factor |H_lm| is in T
+  const double2 H = make_double2(amp * cph, amp * sph);
+  acc[0] = cadd(acc[0], cmul(H, make_double2(val[1], val[2])));
+  acc[1] = cadd(acc[1], cmul(H, make_double2(val[3], val[4])));
+  acc[2] = cadd(acc[2], cmul(H, make_double2(val[5], val[6])));
+}
+
+__device__ __forceinline__ int find_pair_s(const long long* off, int P, long long t) {
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Persistent kernel over the same tile list as k_loglike_fwd. mode 0: surrogate path (in-box
+// samples) or plain path (others), partials [tile][6] as the plain kernel. mode 1: mismatch sums
+// of the surrogate against the plain signal, partials [tile][6] = (<s|p>, <s|s>, <p|p>, 0, 0, 0).
+__global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+                                                       const SampleCoef* __restrict__ coefN,
+                                                       const double* __restrict__ theta, SurBox bx,
+                                                       const double* __restrict__ spl, const double* __restrict__ hs,
+                                                       const int* __restrict__ nend, const long long* __restrict__ off,
+                                                       double* part, int mode) {
+  __shared__ double sh[6][kTileBins / 32];
+  const int P = ds.ndet * B;
+  const long long total = off[P];
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int p = find_pair_s(off, P, t);
+    const int I = p / B, s = p - I * B;
+    const int b = int(t - off[p]) * kTileBins + threadIdx.x;
+    const DetDev& D = ds.d[I];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (b < nend[p]) {
+      const SampleCoef& S = coef[s];
+      const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
+      BinIn Bn;
+      load_bin(D, b, S.tc, Bn);
+      double2 xs[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+      double2 xp[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+      const double u = 3.0 * Bn.lnf3;
+#pragma unroll 1
+      for (int md = 0; md < kNModes; ++md) {
+        const ModeCoef& C = S.md[md];
+        if (!C.active || !(Bn.f < C.fend)) continue;
+        const size_t sys = ((size_t)I * B + s) * kNModes + md;
+        if (sur)
+          mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], xs);
+        if (!sur || mode == 1) mode_bin(D, S, C, Bn, xp);
+      }
+      double2 os[3], op[3];
+      aet_from_xyz(sur ? xs : xp, os);
+      if (mode == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double2 g = D.dg[c * D.nb + b];
+          v[c] = g.x * os[c].x - g.y * os[c].y;
+          v[3 + c] = D.gg[c * D.nb + b] * (os[c].x * os[c].x + os[c].y * os[c].y);
+        }
+      } else {
+        aet_from_xyz(xp, op);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double w = D.gg[c * D.nb + b];
+          v[0] += w * (os[c].x * op[c].x + os[c].y * op[c].y);
+          v[1] += w * (os[c].x * os[c].x + os[c].y * os[c].y);
+          v[2] += w * (op[c].x * op[c].x + op[c].y * op[c].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+      for (int i = 0; i < 6; ++i) sh[i][wid] = v[i];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      double a = sh[threadIdx.x][0];
+      for (int w = 1; w < kTileBins / 32; ++w) a += sh[threadIdx.x][w];
+      part[t * 6 + threadIdx.x] = a;
+    }
+  }
+}
+
+__global__ void k_mismatch_reduce(int ndet, int B, const long long* off, const double* part, const SampleCoef* coef,
+                                  double* mm) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int I = 0; I < ndet; ++I) {
+    const int p = I * B + s;
+    for (long long t = off[p]; t < off[p + 1]; ++t) {
+      a += part[t * 6 + 0];
+      b += part[t * 6 + 1];
+      c += part[t * 6 + 2];
+    }
+  }
+  mm[s] = (coef[s].valid && b > 0.0 && c > 0.0) ? 1.0 - a / sqrt(b * c) : NAN;
+}
+
+__global__ void k_used(const double* theta, int B, SurBox bx, const SampleCoef* coef, int32_t* used) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < B) used[s] = (coef[s].valid && in_box(theta + (size_t)s * PE_NPARAM, bx)) ? 1 : 0;
+}
+
+__global__ void k_destd(const float* Y, int B, const float* mean, const float* stdv, float* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * kNout) return;
+  const int c = (int)(i % kNout);
+  out[i] = Y[i] * stdv[c] + mean[c];
+}
+
+}  // namespace pe
+
+// =============================================================================================
+// Host side
+// =============================================================================================
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+struct Layer {
+  int in = 0, out = 0;
+  float *W = nullptr, *b = nullptr, *mW = nullptr, *vW = nullptr, *mb = nullptr, *vb = nullptr, *gW = nullptr,
+        *gb = nullptr;
+  bf16 *Wb = nullptr, *WTb = nullptr;
+};
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T) + 16);
+}
+
+}  // namespace
+
+struct pe_surrogate_s {
+  Layer L[4];
+  float* mean = nullptr;
+  float* stdv = nullptr;
+  pe::SurBox box{3e5, 1e7, 8.0, 0.99};
+  int node_source = 0;   // 0: the network; 1: the plain generator at the nodes (no network)
+  int trained = 0;
+  int adam_t = 0;
+  uint64_t seed = 0;
+  std::vector<void*> owned;
+  // batch work buffers
+  int cap = 0;
+  bf16 *X = nullptr, *H[3] = {nullptr, nullptr, nullptr}, *HT[3] = {nullptr, nullptr, nullptr}, *XT = nullptr;
+  bf16 *dY = nullptr, *dYT = nullptr, *dZ = nullptr, *dZT = nullptr;
+  float *Z[3] = {nullptr, nullptr, nullptr}, *Y = nullptr, *dYf = nullptr, *dH = nullptr, *dZf = nullptr, *Tb = nullptr;
+  double* part = nullptr;
+};
+
+namespace {
+
+pe_status sfail(pe_status st, const char* msg) { return pe::set_error(st, msg); }
+
+void free_batch(pe_surrogate_s* s) {
+  void* ptrs[] = {s->X, s->H[0], s->H[1], s->H[2], s->HT[0], s->HT[1], s->HT[2], s->XT, s->dY, s->dYT, s->dZ,
+                  s->dZT, s->Z[0], s->Z[1], s->Z[2], s->Y, s->dYf, s->dH, s->dZf, s->Tb, s->part};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  s->X = s->XT = s->dY = s->dYT = s->dZ = s->dZT = nullptr;
+  for (int i = 0; i < 3; ++i) { s->H[i] = s->HT[i] = nullptr; s->Z[i] = nullptr; }
+  s->Y = s->dYf = s->dH = s->dZf = s->Tb = nullptr;
+  s->part = nullptr;
+  s->cap = 0;
+}
+
+cudaError_t ensure_batch(pe_surrogate_s* s, int cap) {
+  if (cap <= s->cap) return cudaSuccess;
+  free_batch(s);
+  cudaError_t e = cudaSuccess;
+  const size_t c = (size_t)cap;
+  if (e == cudaSuccess) e = dalloc(&s->X, c * pe::kNin);
+  if (e == cudaSuccess) e = dalloc(&s->XT, c * pe::kNin);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = dalloc(&s->H[i], c * pe::kHid);
+    if (e == cudaSuccess) e = dalloc(&s->HT[i], c * pe::kHid);
+    if (e == cudaSuccess) e = dalloc(&s->Z[i], c * pe::kHid);
+  }
+  if (e == cudaSuccess) e = dalloc(&s->Y, c * pe::kNout);
+  if (e == cudaSuccess) e = dalloc(&s->Tb, c * pe::kNout);
+  if (e == cudaSuccess) e = dalloc(&s->dYf, c * pe::kNout);
+  if (e == cudaSuccess) e = dalloc(&s->dY, c * pe::kNout);
+  if (e == cudaSuccess) e = dalloc(&s->dYT, c * pe::kNout);
+  if (e == cudaSuccess) e = dalloc(&s->dH, c * pe::kHid);
+  if (e == cudaSuccess) e = dalloc(&s->dZ, c * pe::kHid);
+  if (e == cudaSuccess) e = dalloc(&s->dZT, c * pe::kHid);
+  if (e == cudaSuccess) e = dalloc(&s->dZf, c * pe::kHid);
+  if (e == cudaSuccess) e = dalloc(&s->part, (c * pe::kNout + 255) / 256 + 1);
+  if (e == cudaSuccess) s->cap = cap;
+  return e;
+}
+
+// refresh the bf16 copies (and transposed copies) of every weight matrix
+cudaError_t refresh_bf16(pe_surrogate_s* s, cudaStream_t st) {
+  for (int l = 0; l < 4; ++l) {
+    Layer& L = s->L[l];
+    cudaError_t e = pe::f32_to_bf16(L.W, L.Wb, (size_t)L.out * L.in, st);
+    if (e == cudaSuccess) e = pe::transpose_bf16(L.Wb, L.WTb, L.out, L.in, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// forward of Bp rows (Bp % 64 == 0) from s->X; output Y (standardised) in s->Y
+cudaError_t mlp_forward(pe_surrogate_s* s, int Bp, cudaStream_t st) {
+  cudaError_t e = pe::gemm_tn(s->X, s->L[0].Wb, s->Z[0], Bp, pe::kHid, pe::kNin, 1, s->L[0].b, s->H[0], st);
+  if (e == cudaSuccess) e = pe::gemm_tn(s->H[0], s->L[1].Wb, s->Z[1], Bp, pe::kHid, pe::kHid, 1, s->L[1].b, s->H[1], st);
+  if (e == cudaSuccess) e = pe::gemm_tn(s->H[1], s->L[2].Wb, s->Z[2], Bp, pe::kHid, pe::kHid, 1, s->L[2].b, s->H[2], st);
+  if (e == cudaSuccess) e = pe::gemm_tn(s->H[2], s->L[3].Wb, s->Y, Bp, pe::kNout, pe::kHid, 2, s->L[3].b, nullptr, st);
+  return e;
+}
+
+// backward from dY (bf16 + fp32 in s->dY, s->dYf) into every layer's gW, gb
+cudaError_t mlp_backward(pe_surrogate_s* s, int Bp, cudaStream_t st) {
+  cudaError_t e = pe::transpose_bf16(s->dY, s->dYT, Bp, pe::kNout, st);
+  if (e == cudaSuccess) e = pe::transpose_bf16(s->H[2], s->HT[2], Bp, pe::kHid, st);
+  // layer 3: gW3 [2560][256] = dY^T H2; gb3 = colsum dY; dH2 = dY W3
+  if (e == cudaSuccess) e = pe::gemm_tn(s->dYT, s->HT[2], s->L[3].gW, pe::kNout, pe::kHid, Bp, 0, nullptr, nullptr, st);
+  if (e == cudaSuccess) e = pe::colsum(s->dYf, s->L[3].gb, Bp, pe::kNout, st);
+  if (e == cudaSuccess) e = pe::gemm_tn(s->dY, s->L[3].WTb, s->dH, Bp, pe::kHid, pe::kNout, 0, nullptr, nullptr, st);
+  for (int l = 2; l >= 0 && e == cudaSuccess; --l) {
+    const bf16* Hin = (l == 0) ? s->X : s->H[l - 1];
+    bf16* HinT = (l == 0) ? s->XT : s->HT[l - 1];
+    const int nin = (l == 0) ? pe::kNin : pe::kHid;
+    e = pe::silu_bwd(s->dH, s->Z[l], s->dZ, s->dZf, (size_t)Bp * pe::kHid, st);
+    if (e == cudaSuccess) e = pe::transpose_bf16(s->dZ, s->dZT, Bp, pe::kHid, st);
+    if (e == cudaSuccess) e = pe::transpose_bf16(Hin, HinT, Bp, nin, st);
+    if (e == cudaSuccess) e = pe::gemm_tn(s->dZT, HinT, s->L[l].gW, pe::kHid, nin, Bp, 0, nullptr, nullptr, st);
+    if (e == cudaSuccess) e = pe::colsum(s->dZf, s->L[l].gb, Bp, pe::kHid, st);
+    if (e == cudaSuccess && l > 0)
+      e = pe::gemm_tn(s->dZ, s->L[l].WTb, s->dH, Bp, pe::kHid, pe::kHid, 0, nullptr, nullptr, st);
+  }
+  return e;
+}
+
+int pad64(int b) { return (b + 63) / 64 * 64; }
+
+}  // namespace
+
+extern "C" {
+
+pe_status pe_surrogate_create(uint64_t seed, pe_surrogate* out) {
+  if (out == nullptr) return sfail(PE_EINVAL, "pe_surrogate_create: out is NULL");
+  *out = nullptr;
+  pe_surrogate_s* s = new (std::nothrow) pe_surrogate_s();
+  if (!s) return sfail(PE_ENOMEM, "pe_surrogate_create: host allocation failed");
+  s->seed = seed;
+  const int dims[5] = {pe::kNin, pe::kHid, pe::kHid, pe::kHid, pe::kNout};
+  std::mt19937_64 rng(seed);
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    Layer& L = s->L[l];
+    L.in = dims[l];
+    L.out = dims[l + 1];
+    const size_t nw = (size_t)L.in * L.out;
+    e = dalloc(&L.W, nw);
+    if (e == cudaSuccess) e = dalloc(&L.b, L.out);
+    if (e == cudaSuccess) e = dalloc(&L.mW, nw);
+    if (e == cudaSuccess) e = dalloc(&L.vW, nw);
+    if (e == cudaSuccess) e = dalloc(&L.mb, L.out);
+    if (e == cudaSuccess) e = dalloc(&L.vb, L.out);
+    if (e == cudaSuccess) e = dalloc(&L.gW, nw);
+    if (e == cudaSuccess) e = dalloc(&L.gb, L.out);
+    if (e == cudaSuccess) e = dalloc(&L.Wb, nw);
+    if (e == cudaSuccess) e = dalloc(&L.WTb, nw);
+    if (e != cudaSuccess) break;
+    // He-uniform initialisation (the input layer only sees its 11 used features)
+    const int fan = (l == 0) ? PE_NPARAM : L.in;
+    const double lim = std::sqrt(6.0 / fan) * (l == 3 ? 0.1 : 1.0);
+    std::uniform_real_distribution<double> U(-lim, lim);
+    std::vector<float> w(nw), z(nw, 0.f), zb(L.out, 0.f);
+    for (size_t i = 0; i < nw; ++i) w[i] = (l == 0 && (int)(i % L.in) >= PE_NPARAM) ? 0.f : (float)U(rng);
+    e = cudaMemcpy(L.W, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.mW, z.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.vW, z.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.b, zb.data(), L.out * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.mb, zb.data(), L.out * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.vb, zb.data(), L.out * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = dalloc(&s->mean, pe::kNout);
+  if (e == cudaSuccess) e = dalloc(&s->stdv, pe::kNout);
+  if (e == cudaSuccess) {
+    std::vector<float> zero(pe::kNout, 0.f), one(pe::kNout, 1.f);
+    e = cudaMemcpy(s->mean, zero.data(), pe::kNout * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->stdv, one.data(), pe::kNout * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = refresh_bf16(s, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pe_surrogate_destroy(s);
+    return sfail(PE_ENOMEM, "pe_surrogate_create: device allocation failed");
+  }
+  *out = s;
+  return PE_OK;
+}
+
+pe_status pe_surrogate_destroy(pe_surrogate s) {
+  if (!s) return PE_OK;
+  cudaDeviceSynchronize();
+  free_batch(s);
+  for (int l = 0; l < 4; ++l) {
+    Layer& L = s->L[l];
+    void* ptrs[] = {L.W, L.b, L.mW, L.vW, L.mb, L.vb, L.gW, L.gb, L.Wb, L.WTb};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+  if (s->mean) cudaFree(s->mean);
+  if (s->stdv) cudaFree(s->stdv);
+  cudaGetLastError();
+  delete s;
+  return PE_OK;
+}
+
+pe_status pe_surrogate_set_node_source(pe_surrogate s, int source) {
+  if (!s || (source != 0 && source != 1)) return sfail(PE_EINVAL, "pe_surrogate_set_node_source: bad arguments");
+  s->node_source = source;
+  return PE_OK;
+}
+
+pe_status pe_surrogate_set_box(pe_surrogate s, double mtot_lo, double mtot_hi, double q_max, double chi_max) {
+  if (!s) return sfail(PE_EINVAL, "pe_surrogate_set_box: NULL handle");
+  if (!(mtot_lo > 0.0 && mtot_hi >= mtot_lo && q_max >= 1.0 && chi_max >= 0.0 && chi_max < 1.0))
+    return sfail(PE_EINVAL, "pe_surrogate_set_box: bad box");
+  s->box = pe::SurBox{mtot_lo, mtot_hi, q_max, chi_max};
+  return PE_OK;
+}
+
+pe_status pe_surrogate_targets(const double* theta_dev, int B, float* out_dev) {
+  if (!theta_dev || !out_dev || B < 1) return sfail(PE_EINVAL, "pe_surrogate_targets: bad arguments");
+  pe::SampleCoef *S = nullptr, *S0 = nullptr;
+  cudaError_t e = dalloc(&S, B);
+  if (e == cudaSuccess) e = dalloc(&S0, B);
+  if (e == cudaSuccess) {
+    pe::k_sur_prep<<<(B + 63) / 64, 64>>>(theta_dev, B, PE_MODE_ALL, S, S0);
+    const long long n = (long long)B * pe::kNModes * pe::kNodes;
+    pe::k_targets<<<(unsigned)((n + 255) / 256), 256>>>(theta_dev, B, S, S0, out_dev);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (S) cudaFree(S);
+  if (S0) cudaFree(S0);
+  if (e != cudaSuccess) { cudaGetLastError(); return sfail(PE_ECUDA, "pe_surrogate_targets failed"); }
+  return PE_OK;
+}
+
+pe_status pe_surrogate_train(pe_surrogate s, const double* theta_train_dev, int n_train, int epochs, int batch, double lr,
+                             double* out_final_loss, float* out_loss_curve) {
+  if (!s || !theta_train_dev || n_train < 64 || epochs < 1 || batch < 64 || batch % 64 || !(lr > 0.0))
+    return sfail(PE_EINVAL, "pe_surrogate_train: bad arguments (n_train >= 64, batch % 64 == 0)");
+  const size_t nt = (size_t)n_train;
+  float* T = nullptr;
+  bf16* Xall = nullptr;
+  int* idx_d = nullptr;
+  cudaError_t e = dalloc(&T, nt * pe::kNout);
+  if (e == cudaSuccess) e = dalloc(&Xall, nt * pe::kNin);
+  if (e == cudaSuccess) e = dalloc(&idx_d, (size_t)batch);
+  if (e == cudaSuccess) e = ensure_batch(s, batch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (T) cudaFree(T);
+    if (Xall) cudaFree(Xall);
+    if (idx_d) cudaFree(idx_d);
+    return sfail(PE_ENOMEM, "pe_surrogate_train: allocation failed");
+  }
+  pe_status st = PE_OK;
+  // targets from the plain generator (chunks of 32768 samples), standardised per output
+  for (size_t c0 = 0; c0 < nt && st == PE_OK; c0 += 32768) {
+    const int nb = (int)std::min<size_t>(32768, nt - c0);
+    st = pe_surrogate_targets(theta_train_dev + c0 * PE_NPARAM, nb, T + c0 * pe::kNout);
+  }
+  if (st == PE_OK) {
+    pe::k_colstats<<<(pe::kNout + 127) / 128, 128>>>(T, (long long)nt, s->mean, s->stdv);
+    pe::k_group_phase_scale<<<1, 32>>>(s->stdv);
+    const long long n = (long long)nt * pe::kNout;
+    pe::k_standardize<<<(unsigned)((n + 255) / 256), 256>>>(T, (long long)nt, s->mean, s->stdv);
+    pe::k_features<<<(n_train + 127) / 128, 128>>>(theta_train_dev, n_train, n_train, Xall);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = sfail(PE_ECUDA, "pe_surrogate_train: target preparation failed");
+  }
+  std::mt19937_64 rng(s->seed ^ 0x9e3779b97f4a7c15ull);
+  std::vector<int> perm(nt);
+  for (size_t i = 0; i < nt; ++i) perm[i] = (int)i;
+  const int steps = n_train / batch;
+  const int total_steps = steps * epochs;
+  std::vector<double> hpart;
+  double last = 0.0;
+  int gstep = 0;
+  for (int ep = 0; ep < epochs && st == PE_OK; ++ep) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    double ep_loss = 0.0;
+    for (int k = 0; k < steps && st == PE_OK; ++k, ++gstep) {
+      e = cudaMemcpy(idx_d, perm.data() + (size_t)k * batch, batch * sizeof(int), cudaMemcpyHostToDevice);
+      const long long ng = (long long)batch * pe::kNout;
+      if (e == cudaSuccess) {
+        pe::k_gather_rows<<<(unsigned)((ng + 255) / 256), 256>>>(Xall, T, idx_d, batch, s->X, s->Tb);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = mlp_forward(s, batch, 0);
+      int nblk = 0;
+      if (e == cudaSuccess)
+        e = pe::mse(s->Y, s->Tb, s->dYf, s->dY, s->part, (size_t)ng, 1.0f / (float)ng, &nblk, 0);
+      if (e == cudaSuccess) e = mlp_backward(s, batch, 0);
+      // cosine learning-rate schedule
+      const double frac = (double)gstep / (double)std::max(1, total_steps - 1);
+      const float lr_t = (float)(lr * (0.02 + 0.98 * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))));
+      ++s->adam_t;
+      for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+        Layer& L = s->L[l];
+        e = pe::adam(L.W, L.gW, L.mW, L.vW, nullptr, (size_t)L.in * L.out, lr_t, 0.9f, 0.999f, 1e-8f, s->adam_t, 0);
+        if (e == cudaSuccess) e = pe::adam(L.b, L.gb, L.mb, L.vb, nullptr, L.out, lr_t, 0.9f, 0.999f, 1e-8f, s->adam_t, 0);
+      }
+      if (e == cudaSuccess) e = refresh_bf16(s, 0);
+      if (e == cudaSuccess && k == steps - 1) {
+        hpart.resize(nblk);
+        e = cudaMemcpy(hpart.data(), s->part, nblk * sizeof(double), cudaMemcpyDeviceToHost);
+        double sum = 0.0;
+        for (double x : hpart) sum += x;
+        ep_loss = sum / (double)ng;
+      }
+      if (e != cudaSuccess) st = sfail(PE_ECUDA, "pe_surrogate_train: training step failed");
+    }
+    last = ep_loss;
+    if (out_loss_curve) out_loss_curve[ep] = (float)ep_loss;
+  }
+  cudaFree(T);
+  cudaFree(Xall);
+  cudaFree(idx_d);
+  if (st != PE_OK) { cudaGetLastError(); return st; }
+  s->trained = 1;
+  if (out_final_loss) *out_final_loss = last;
+  return PE_OK;
+}
+
+// De-standardised node values [B][2560] of theta (device), written to out_dev (device).
+pe_status pe_surrogate_predict(pe_surrogate s, const double* theta_dev, int B, float* out_dev) {
+  if (!s || !theta_dev || !out_dev || B < 1) return sfail(PE_EINVAL, "pe_surrogate_predict: bad arguments");
+  const int Bp = pad64(B);
+  cudaError_t e = ensure_batch(s, Bp);
+  if (e == cudaSuccess) {
+    pe::k_features<<<(Bp + 127) / 128, 128>>>(theta_dev, B, Bp, s->X);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = mlp_forward(s, Bp, 0);
+  if (e == cudaSuccess) {
+    const long long n = (long long)B * pe::kNout;
+    pe::k_destd<<<(unsigned)((n + 255) / 256), 256>>>(s->Y, B, s->mean, s->stdv, out_dev);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { cudaGetLastError(); return sfail(PE_ECUDA, "pe_surrogate_predict failed"); }
+  return PE_OK;
+}
+
+// Shared driver of the surrogate log-likelihood (mode 0) and the mismatch study (mode 1).
+static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, const double* theta_dev, int B,
+                         unsigned mode_mask, int mode, double* out0, int32_t* used, cudaStream_t st) {
+  pe::DetSet ds;
+  pe_status s0 = pe::detset_from_handles(dets, ndet, &ds);
+  if (s0 != PE_OK) return s0;
+  if (B < 1 || B > (1 << 20) || !theta_dev || !out0) return sfail(PE_EINVAL, "surrogate: bad arguments");
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return sfail(PE_EINVAL, "surrogate: bad mode mask");
+  const int P = ndet * B;
+  long long max_tiles = 0;
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * ((ds.d[i].nb + pe::kTileBins - 1) / pe::kTileBins);
+  const int Bp = pad64(B);
+  cudaError_t e = ensure_batch(s, Bp);
+  std::vector<void*> bufs;
+  auto aalloc = [&](auto** p, size_t n) {
+    if (e != cudaSuccess) return;
+    void* q = nullptr;
+    e = cudaMallocAsync(&q, n * sizeof(**p) + 16, st);
+    if (e == cudaSuccess) { bufs.push_back(q); *p = static_cast<std::remove_pointer_t<decltype(p)>>(q); }
+  };
+  pe::SampleCoef *S = nullptr, *S0 = nullptr;
+  int* nend = nullptr;
+  long long* off = nullptr;
+  double *part = nullptr, *nodes = nullptr, *spl = nullptr, *hs = nullptr, *hs_sys = nullptr;
+  float* Yd = nullptr;
+  const size_t nsys = (size_t)ndet * B * pe::kNModes;
+  aalloc(&S, B);
+  aalloc(&S0, B);
+  aalloc(&nend, P);
+  aalloc(&off, P + 1);
+  aalloc(&part, (size_t)max_tiles * 6);
+  aalloc(&nodes, nsys * pe::kQ * pe::kNodes);
+  aalloc(&spl, nsys * pe::kQ * (pe::kNodes - 1) * 4);
+  aalloc(&hs, (size_t)B * pe::kNModes);
+  aalloc(&hs_sys, nsys);
+  aalloc(&Yd, (size_t)B * pe::kNout);
+  if (e == cudaSuccess) {
+    // MLP inference (BF16 tensor cores) -> de-standardised node values
+    pe::k_features<<<(Bp + 127) / 128, 128, 0, st>>>(theta_dev, B, Bp, s->X);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && s->node_source == 0) e = mlp_forward(s, Bp, st);
+  }
+  if (e == cudaSuccess) {
+    const long long n = (long long)B * pe::kNout;
+    pe::k_sur_prep<<<(B + 63) / 64, 64, 0, st>>>(theta_dev, B, mode_mask, S, S0);
+    if (s->node_source == 0) {
+      pe::k_destd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->Y, B, s->mean, s->stdv, Yd);
+    } else {
+      const long long nt = (long long)B * pe::kNModes * pe::kNodes;
+      pe::k_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(theta_dev, B, S, S0, Yd);
+    }
+    pe::k_node_h<<<(B * pe::kNModes + 127) / 128, 128, 0, st>>>(theta_dev, B, hs);
+    const long long nn = (long long)nsys * pe::kNodes;
+    pe::k_sur_nodes<<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(ds, B, S, S0, Yd, theta_dev, s->box, nodes);
+    e = cudaGetLastError();
+    // the spline kernel reads the node spacing per system (I, s, md): replicate per detector
+    for (int I = 0; I < ndet && e == cudaSuccess; ++I)
+      e = cudaMemcpyAsync(hs_sys + (size_t)I * B * pe::kNModes, hs, (size_t)B * pe::kNModes * sizeof(double),
+                          cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+      const long long ns = (long long)nsys * pe::kQ;
+      pe::k_spline<<<(unsigned)((ns + 63) / 64), 64, 0, st>>>(nodes, ns, hs_sys, spl);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = pe::launch_prep(theta_dev, B, mode_mask, ds, S, nend, nullptr, st);
+  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, P, off, st);
+  if (e == cudaSuccess) {
+    int nsm = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long g = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * 8));
+    pe::k_sur_fwd<<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, hs, nend, off, part,
+                                                          mode);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    if (mode == 0) {
+      e = pe::launch_reduce(ds, B, off, part, S, out0, nullptr, st);
+      if (e == cudaSuccess && used) {
+        pe::k_used<<<(B + 127) / 128, 128, 0, st>>>(theta_dev, B, s->box, S, used);
+        e = cudaGetLastError();
+      }
+    } else {
+      pe::k_mismatch_reduce<<<(B + 127) / 128, 128, 0, st>>>(ndet, B, off, part, S, out0);
+      e = cudaGetLastError();
+    }
+  }
+  for (void* p : bufs) cudaFreeAsync(p, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char msg[256];
+    snprintf(msg, sizeof(msg), "surrogate path failed: %s", cudaGetErrorString(e));
+    return sfail(PE_ECUDA, msg);
+  }
+  return PE_OK;
+}
+
+pe_status pe_surrogate_loglike_batch(pe_surrogate s, const pe_detector* dets, int ndet, const double* theta_dev, int B,
+                                     unsigned mode_mask, double* out_logl_dev, int32_t* out_used_dev, void* stream) {
+  if (!s) return sfail(PE_EINVAL, "pe_surrogate_loglike_batch: NULL handle");
+  return sur_run(s, dets, ndet, theta_dev, B, mode_mask, 0, out_logl_dev, out_used_dev, static_cast<cudaStream_t>(stream));
+}
+
+pe_status pe_surrogate_mismatch(pe_surrogate s, pe_detector det, const double* theta_dev, int B, unsigned mode_mask,
+                                double* out_mismatch_dev, void* stream) {
+  if (!s) return sfail(PE_EINVAL, "pe_surrogate_mismatch: NULL handle");
+  return sur_run(s, &det, 1, theta_dev, B, mode_mask, 1, out_mismatch_dev, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+// Forward and backward of the network on given inputs and output cotangents (host arrays), for
+// gradient checks: x [B][64] (fp32, rounded to bf16 on the device), dy [B][2560]; returns the raw
+// (standardised-space) outputs y [B][2560] and the gradients of every layer, concatenated as
+// gW0, gb0, gW1, gb1, gW2, gb2, gW3, gb3 (weights [out][in]). B must be a multiple of 64.
+pe_status pe_surrogate_mlp_debug(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads) {
+  if (!s || !x || !dy || !y || !grads || B < 64 || B % 64) return sfail(PE_EINVAL, "pe_surrogate_mlp_debug: bad arguments");
+  cudaError_t e = ensure_batch(s, B);
+  float* tmp = nullptr;
+  const size_t nx = (size_t)B * pe::kNin, ny = (size_t)B * pe::kNout;
+  if (e == cudaSuccess) e = dalloc(&tmp, std::max(nx, ny));
+  if (e == cudaSuccess) e = cudaMemcpy(tmp, x, nx * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pe::f32_to_bf16(tmp, s->X, nx, 0);
+  if (e == cudaSuccess) e = mlp_forward(s, B, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(y, s->Y, ny * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(s->dYf, dy, ny * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pe::f32_to_bf16(s->dYf, s->dY, ny, 0);
+  if (e == cudaSuccess) e = mlp_backward(s, B, 0);
+  size_t o = 0;
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    const size_t nw = (size_t)s->L[l].in * s->L[l].out;
+    e = cudaMemcpy(grads + o, s->L[l].gW, nw * sizeof(float), cudaMemcpyDeviceToHost);
+    o += nw;
+    if (e == cudaSuccess) e = cudaMemcpy(grads + o, s->L[l].gb, s->L[l].out * sizeof(float), cudaMemcpyDeviceToHost);
+    o += s->L[l].out;
+  }
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) { cudaGetLastError(); return sfail(PE_ECUDA, "pe_surrogate_mlp_debug failed"); }
+  return PE_OK;
+}
+
+// Weights and biases as fp32 host arrays, concatenated W0, b0, W1, b1, W2, b2, W3, b3 ([out][in]).
+pe_status pe_surrogate_get_weights(pe_surrogate s, float* out, int64_t* count) {
+  if (!s || !count) return sfail(PE_EINVAL, "pe_surrogate_get_weights: bad arguments");
+  size_t n = 0;
+  for (int l = 0; l < 4; ++l) n += (size_t)s->L[l].in * s->L[l].out + s->L[l].out;
+  *count = (int64_t)n;
+  if (!out) return PE_OK;
+  size_t o = 0;
+  for (int l = 0; l < 4; ++l) {
+    const size_t nw = (size_t)s->L[l].in * s->L[l].out;
+    if (cudaMemcpy(out + o, s->L[l].W, nw * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(out + o + nw, s->L[l].b, s->L[l].out * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return sfail(PE_ECUDA, "pe_surrogate_get_weights: copy failed");
+    }
+    o += nw + s->L[l].out;
+  }
+  return PE_OK;
+}
+
+// ---- checkpoint: "PESURR01" | u32 version | u32 dims[5] | SurBox | i32 adam_t | u64 seed |
+//      per layer W, b, mW, vW, mb, vb (fp32) | mean, std (fp32) | u64 FNV-1a of all preceding bytes
+static uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+pe_status pe_surrogate_save(pe_surrogate s, const char* path) {
+  if (!s || !path) return sfail(PE_EINVAL, "pe_surrogate_save: bad arguments");
+  std::vector<unsigned char> buf;
+  auto put = [&](const void* p, size_t n) { buf.insert(buf.end(), (const unsigned char*)p, (const unsigned char*)p + n); };
+  put("PESURR01", 8);
+  const uint32_t ver = 1, dims[5] = {pe::kNin, pe::kHid, pe::kHid, pe::kHid, pe::kNout};
+  put(&ver, 4);
+  put(dims, sizeof(dims));
+  put(&s->box, sizeof(s->box));
+  put(&s->adam_t, 4);
+  put(&s->seed, 8);
+  std::vector<float> h;
+  auto dget = [&](const float* d, size_t n) -> bool {
+    h.resize(n);
+    if (cudaMemcpy(h.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    put(h.data(), n * sizeof(float));
+    return true;
+  };
+  bool ok = true;
+  for (int l = 0; l < 4 && ok; ++l) {
+    const Layer& L = s->L[l];
+    const size_t nw = (size_t)L.in * L.out;
+    ok = dget(L.W, nw) && dget(L.b, L.out) && dget(L.mW, nw) && dget(L.vW, nw) && dget(L.mb, L.out) && dget(L.vb, L.out);
+  }
+  ok = ok && dget(s->mean, pe::kNout) && dget(s->stdv, pe::kNout);
+  if (!ok) { cudaGetLastError(); return sfail(PE_ECUDA, "pe_surrogate_save: device copy failed"); }
+  const uint64_t cs = fnv1a(buf.data(), buf.size());
+  put(&cs, 8);
+  FILE* f = fopen(path, "wb");
+  if (!f) return sfail(PE_EINVAL, "pe_surrogate_save: cannot open file");
+  const size_t w = fwrite(buf.data(), 1, buf.size(), f);
+  fclose(f);
+  if (w != buf.size()) return sfail(PE_EINVAL, "pe_surrogate_save: short write");
+  return PE_OK;
+}
+
+pe_status pe_surrogate_load(pe_surrogate s, const char* path) {
+  if (!s || !path) return sfail(PE_EINVAL, "pe_surrogate_load: bad arguments");
+  FILE* f = fopen(path, "rb");
+  if (!f) return sfail(PE_EINVAL, "pe_surrogate_load: cannot open file");
+  std::vector<unsigned char> buf;
+  unsigned char tmp[65536];
+  size_t r;
+  while ((r = fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + r);
+  fclose(f);
+  if (buf.size() < 8 + 4 + 20 + sizeof(pe::SurBox) + 12 + 8 || memcmp(buf.data(), "PESURR01", 8) != 0)
+    return sfail(PE_EINVAL, "pe_surrogate_load: not a surrogate checkpoint");
+  uint64_t cs;
+  memcpy(&cs, buf.data() + buf.size() - 8, 8);
+  if (fnv1a(buf.data(), buf.size() - 8) != cs) return sfail(PE_EINVAL, "pe_surrogate_load: checksum mismatch");
+  size_t o = 8;
+  uint32_t ver, dims[5];
+  memcpy(&ver, buf.data() + o, 4); o += 4;
+  memcpy(dims, buf.data() + o, sizeof(dims)); o += sizeof(dims);
+  const uint32_t want[5] = {pe::kNin, pe::kHid, pe::kHid, pe::kHid, pe::kNout};
+  if (ver != 1 || memcmp(dims, want, sizeof(dims)) != 0) return sfail(PE_EINVAL, "pe_surrogate_load: version/shape mismatch");
+  memcpy(&s->box, buf.data() + o, sizeof(s->box)); o += sizeof(s->box);
+  memcpy(&s->adam_t, buf.data() + o, 4); o += 4;
+  memcpy(&s->seed, buf.data() + o, 8); o += 8;
+  auto dput = [&](float* d, size_t n) -> bool {
+    if (o + n * sizeof(float) > buf.size() - 8) return false;
+    const bool ok = cudaMemcpy(d, buf.data() + o, n * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    o += n * sizeof(float);
+    return ok;
+  };
+  bool ok = true;
+  for (int l = 0; l < 4 && ok; ++l) {
+    Layer& L = s->L[l];
+    const size_t nw = (size_t)L.in * L.out;
+    ok = dput(L.W, nw) && dput(L.b, L.out) && dput(L.mW, nw) && dput(L.vW, nw) && dput(L.mb, L.out) && dput(L.vb, L.out);
+  }
+  ok = ok && dput(s->mean, pe::kNout) && dput(s->stdv, pe::kNout);
+  if (!ok || o != buf.size() - 8) { cudaGetLastError(); return sfail(PE_EINVAL, "pe_surrogate_load: truncated checkpoint"); }
+  if (refresh_bf16(s, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return sfail(PE_ECUDA, "pe_surrogate_load: device refresh failed");
+  }
+  s->trained = 1;
+  return PE_OK;
+}
+
+}  // extern "C"
