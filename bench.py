@@ -32,10 +32,11 @@ from paper_2602_12011_gb300 import workloads as W  # noqa: E402
 METRIC = "log-likelihood evals/s (HM, 3 TDI ch, batched) vs plain path; grad evals/s"
 UNIT = "evals/s"
 MSUN_S = 4.925490947641267e-6
-# FP64 operations per active (sample, mode, bin) unit of the fused kernel, FMA counted as 2:
-# (2 x DFMA + DADD + DMUL) thread-instructions per unit, from the ncu SASS counters of the
-# forward kernel (profiles/k_loglike_fwd_lisa_hm_T2^22_B64_ncu_full.md).
-FP64_FLOPS_PER_UNIT = 779.5
+# FP64 work per active (sample, mode, bin) unit of the fused kernel, from the ncu SASS counters
+# of the forward kernel (profiles/k_loglike_fwd_lisa_hm_T2^22_B64_ncu_full.md): flops with an FMA
+# counted as 2 (2 DFMA + DADD + DMUL), and FP64 pipe instructions (every FP64 instruction).
+FP64_FLOPS_PER_UNIT = 616.0
+FP64_INST_PER_UNIT = 425.7
 
 
 def parse():
@@ -391,11 +392,14 @@ def main():
     roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_kind": "measured FP64 FMA, 1 s loop",
             "kernel": "k_loglike_fwd", "launch_ms": fwd_avg_s * 1e3, "units_per_launch": units,
             "traffic": None}
-    if FP64_FLOPS_PER_UNIT:
-        ach = FP64_FLOPS_PER_UNIT * units / fwd_avg_s / 1e12
-        roof.update({"achieved": ach, "frac": ach / peak, "flops_per_unit": FP64_FLOPS_PER_UNIT})
-    else:
-        roof.update({"achieved": None, "frac": None, "units_per_s": units / fwd_avg_s})
+    ach = FP64_FLOPS_PER_UNIT * units / fwd_avg_s / 1e12
+    roof.update({"achieved": ach, "frac": ach / peak, "flops_per_unit": FP64_FLOPS_PER_UNIT,
+                 "units_per_s": units / fwd_avg_s,
+                 # the same launch in FP64-pipe slots: every FP64 instruction against the FMA loop's rate
+                 "fp64_pipe": {"inst_per_unit": FP64_INST_PER_UNIT,
+                               "achieved_ginst_s": FP64_INST_PER_UNIT * units / fwd_avg_s / 1e9,
+                               "peak_ginst_s": peak * 1e3 / 2.0,
+                               "frac": (FP64_INST_PER_UNIT * units / fwd_avg_s / 1e9) / (peak * 1e3 / 2.0)}})
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_total / K, "higher_is_better": True,

@@ -40,7 +40,8 @@ __device__ __forceinline__ double dsinc(double u, double cosu, double sincu) {
 
 // Reverse sweep of one unit. sX, sY, sZ: cotangents of this bin's brackets X', Y', Z'.
 __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, const SampleGrad& SG, int md,
-                                         const BinIn& B, double2 sX, double2 sY, double2 sZ, GradAcc& g) {
+                                         const BinIn& B, double2 sX, double2 sY, double2 sZ, GradAcc& g,
+                                         const double2* __restrict__ tab) {
   const ModeCoef& C = S.md[md];
   const ModeGrad& CG = SG.md[md];
   // ---------------- forward recompute: waveform, t_f, amplitude, orbit, phase
@@ -55,8 +56,8 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);
-    dpol = fma(dpol, v, (k - 5) * S.P[k]);
-    ddpol = fma(ddpol, v, double((k - 5) * (k - 5)) * S.P[k]);
+    dpol = fma(dpol, v, S.Pd[k]);
+    ddpol = fma(ddpol, v, double(k - 5) * S.Pd[k]);
   }
   const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
@@ -75,7 +76,7 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
   const double amp = amp0 * w;
   // orbit
   double so, co;
-  sincospi(fma(tf, D.rate_ht, D.alpha0_ht), &so, &co);
+  sincos_turns(fma(tf, D.rate_t, D.alpha0_t), tab, &so, &co);
   double xc[3] = {D.R * co, D.R * so, 0.0};
   double dl[3][3];
   double s0 = 0.0, c0 = 0.0, c2 = 0.0, s2 = 0.0;
@@ -89,7 +90,7 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
       dl[i][2] = -D.eRs3 * (co * D.cb[i] + so * D.sb[i]);
     }
   } else {
-    sincospi(tf * D.geo_rate_ht, &s0, &c0);
+    sincos_turns(tf * D.geo_rate_t, tab, &s0, &c0);
     const double ch = -0.5, sh = 0.86602540378443864676;
     double ci = c0, si = s0;
 #pragma unroll
@@ -101,11 +102,21 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     }
   }
   const double kxc = S.k[0] * xc[0] + S.k[1] * xc[1] + S.k[2] * xc[2];
-  double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
-  ph -= rint(ph);
+  const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
   double sph, cph;
-  sincospi(2.0 * ph, &sph, &cph);
+  sincos_turns(ph, tab, &sph, &cph);
   const double2 H = make_double2(amp * cph, amp * sph);
+  // third-spacecraft phases e^{i pi f k.delta_t}: E_2 = conj(E_0 E_1) since the offsets sum to zero
+  double2 Et[3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double kd = S.k[0] * dl[i][0] + S.k[1] * dl[i][1] + S.k[2] * dl[i][2];
+    sincos_turns(0.5 * B.f * kd, tab, &Et[i].y, &Et[i].x);
+  }
+  {
+    const double2 e01 = cmul(Et[0], Et[1]);
+    Et[2] = make_double2(e01.x, -e01.y);
+  }
   // ---------------- links: forward and reverse, one pair at a time
   // seeds: pair 0 = (1,2): X' has -G U, Y' has +G V; pair 1 = (2,3): Y' -G U, Z' +G V;
   //        pair 2 = (3,1): Z' -G U, X' +G V.
@@ -129,14 +140,12 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double nq = S.q[0] * n[0] + S.q[1] * n[1] + S.q[2] * n[2];
     const double Fp = np * np - nq * nq, Fc = 2.0 * np * nq;
     const double2 gam = make_double2(C.Pp * Fp, C.Pc * Fc);
-    const double kd = S.k[0] * dl[t][0] + S.k[1] * dl[t][1] + S.k[2] * dl[t][2];
-    double se, ce;
-    sincospi(B.f * kd, &se, &ce);
-    const double2 E = make_double2(ce, se);
+    const double2 E = Et[t];
+    const double se = E.y, ce = E.x;
     const double2 K = cmul(gam, H);
     const double2 G = cmul(E, K);
     double sak, cak;
-    sincos(B.a * kn, &sak, &cak);
+    sincos_turns(B.aturn * kn, tab, &sak, &cak);
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
     const double s1 = B.sa * cak - B.ca * sak, s2u = B.sa * cak + B.ca * sak;
     const double c1u = B.ca * cak + B.sa * sak, c2u = B.ca * cak - B.sa * sak;

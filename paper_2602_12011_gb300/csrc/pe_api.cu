@@ -36,6 +36,7 @@ struct pe_detector_s {
   double* gg;
   double* psd_model;   // [3][nb] analytic PSD
   double* dd_dev;      // [3]
+  double2* sct;        // [kSinTab] sincos table
   double dd[3];
   int has_data;
   pe::DetDev dev;
@@ -119,6 +120,8 @@ void fill_dev(pe_detector_s* d) {
   D.R = pe::kAuS;
   D.alpha0_ht = c.alpha0_rad / pe::kPi;
   D.rate_ht = 2.0 / pe::kYearS;
+  D.alpha0_t = 0.5 * D.alpha0_ht;
+  D.rate_t = 1.0 / pe::kYearS;
   if (c.orbit == PE_ORBIT_HELIO) {
     const double e = D.L / (2.0 * std::sqrt(3.0) * D.R);
     D.eRh = 0.5 * e * D.R;
@@ -132,6 +135,7 @@ void fill_dev(pe_detector_s* d) {
   } else {
     D.rgeo = D.L / std::sqrt(3.0);
     D.geo_rate_ht = 2.0 / c.geo_period_s;
+    D.geo_rate_t = 1.0 / c.geo_period_s;
     const double nl = c.geo_lon_rad, nbt = c.geo_lat_rad;
     const double n[3] = {std::cos(nbt) * std::cos(nl), std::cos(nbt) * std::sin(nl), std::sin(nbt)};
     D.e1[0] = -std::sin(nl); D.e1[1] = std::cos(nl); D.e1[2] = 0.0;
@@ -140,7 +144,7 @@ void fill_dev(pe_detector_s* d) {
     D.e2[2] = n[0] * D.e1[1] - n[1] * D.e1[0];
   }
   D.f = d->f; D.f13 = d->f13; D.fm13 = d->fm13; D.lnf3 = d->lnf3; D.fm76 = d->fm76;
-  D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev;
+  D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev; D.sct = d->sct;
 }
 
 pe_status check_dets(const pe_detector* dets, int ndet, pe::DetSet* ds) {
@@ -199,11 +203,12 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   const size_t nb = (size_t)nbins;
   // doubles: f, f13, fm13, lnf3, fm76 (5 nb) + gg (3 nb) + psd_model (3 nb) + dd (3, padded);
   // double2: sca, z (2 nb) + dg (3 nb)
-  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb;
+  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab;
   const size_t bytes = n_d * sizeof(double) + n_d2 * sizeof(double2);
   cudaError_t e = cudaMalloc(&d->mem, bytes);
   if (e != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ENOMEM, "cudaMalloc(%zu) failed", bytes); }
   double2* p2 = static_cast<double2*>(d->mem);
+  d->sct = p2; p2 += pe::kSinTab;
   d->sca = p2; p2 += nb;
   d->z = p2; p2 += nb;
   d->dg = p2; p2 += 3 * nb;
@@ -218,7 +223,8 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->dd_dev = p;
   fill_dev(d);
   const double L = det_arm_s(*cfg);
-  if ((e = pe::launch_grid_tables(T_obs, k0, d->nb, L, d->f, d->f13, d->fm13, d->lnf3, d->fm76, d->sca, d->z, 0)) !=
+  if ((e = pe::launch_sincos_table(d->sct, 0)) != cudaSuccess ||
+      (e = pe::launch_grid_tables(T_obs, k0, d->nb, L, d->f, d->f13, d->fm13, d->lnf3, d->fm76, d->sca, d->z, 0)) !=
           cudaSuccess ||
       (e = pe::launch_psd_model(d->f, d->nb, L, cfg->oms_m_rtHz, cfg->acc_ms2_rtHz, cfg->psd_shaping, cfg->tdi_gen,
                                 d->psd_model, 0)) != cudaSuccess ||

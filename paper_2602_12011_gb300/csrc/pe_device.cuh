@@ -16,6 +16,23 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
+// sin and cos of 2 pi x for x in turns: exact reduction x - rint(x), nearest table angle
+// 2 pi j/kSinTab, and the remainder t (|t| <= pi/kSinTab) through the angle-addition formulas with
+// sin t = t - t^3/6 + t^5/120, cos t = 1 - t^2/2 + t^4/24 (truncation below 1e-18).
+// tab[j] = (cos, sin)(2 pi j/kSinTab).
+__device__ __forceinline__ void sincos_turns(double x, const double2* __restrict__ tab, double* s, double* c) {
+  const double r = x - rint(x);
+  const double jf = rint(r * kSinTab);
+  const double d = fma(jf, -1.0 / kSinTab, r);
+  const double2 cs = tab[(int)jf & (kSinTab - 1)];
+  const double t = d * (2.0 * kPi);
+  const double t2 = t * t;
+  const double st = fma(t, t2 * fma(t2, 1.0 / 120.0, -1.0 / 6.0), t);
+  const double ct = fma(t2, fma(t2, 1.0 / 24.0, -0.5), 1.0);
+  *s = fma(cs.y, ct, cs.x * st);
+  *c = fma(cs.x, ct, -(cs.y * st));
+}
+
 // -2Y_lm(iota, 0) closed forms for the ten (l, +-m) the five modes need.
 template <class T>
 __device__ inline void sylm_pair(int l, int m, const T& iota, T* ypos, T* yneg) {
@@ -89,6 +106,7 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   S.P[5] = n * a5c * (1.0 + 1.5 * ::log(6.0));          // alpha5 (1 + 3 ln(v/v_lso)), v_lso = 6^-1/2
   S.P[6] = n * (a6c - 6848.0 / 21.0 * ::log(4.0));       // alpha6 - (6848/21) ln(4 v)
   S.P[7] = n * pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
+  for (int k = 0; k < 8; ++k) S.Pd[k] = double(k - 5) * S.P[k];
   S.Q5 = n * 3.0 * a5c;
   S.Q6 = n * (-6848.0 / 21.0);
   // sky frame
@@ -138,9 +156,10 @@ __device__ inline void sample_prep(const double* th, unsigned mask, SampleCoef& 
 }
 
 // Spacecraft offsets delta_i from the constellation centre and the centre x_c, at time t.
-__device__ __forceinline__ void orbit_offsets(const DetDev& D, double t, double xc[3], double dl[3][3]) {
+__device__ __forceinline__ void orbit_offsets(const DetDev& D, double t, double xc[3], double dl[3][3],
+                                              const double2* __restrict__ tab) {
   double s, c;
-  sincospi(fma(t, D.rate_ht, D.alpha0_ht), &s, &c);
+  sincos_turns(fma(t, D.rate_t, D.alpha0_t), tab, &s, &c);
   xc[0] = D.R * c; xc[1] = D.R * s; xc[2] = 0.0;
   if (D.orbit == 0) {
     const double c2 = c * c - s * s, s2 = 2.0 * s * c;
@@ -152,7 +171,7 @@ __device__ __forceinline__ void orbit_offsets(const DetDev& D, double t, double 
     }
   } else {
     double s0, c0;
-    sincospi(t * D.geo_rate_ht, &s0, &c0);
+    sincos_turns(t * D.geo_rate_t, tab, &s0, &c0);
     const double ch = -0.5, sh = 0.86602540378443864676;  // cos, sin of 120 degrees
     double ci = c0, si = s0;
 #pragma unroll
@@ -171,10 +190,25 @@ __device__ __forceinline__ double sinc_small(double u) {
   return 1.0 - u2 / 6.0 + u2 * u2 / 120.0 - u2 * u2 * u2 / 5040.0;
 }
 
+// Mode-summed TDI brackets of one bin, kept as X' = P_X + z Q_X (and Y', Z' alike): z depends on
+// the bin only, so it is applied once after the mode sum (xyz_final).
+struct XYZAcc {
+  double2 P[3], Q[3];
+};
+__device__ __forceinline__ void xyz_zero(XYZAcc& a) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) a.P[i] = a.Q[i] = make_double2(0.0, 0.0);
+}
+__device__ __forceinline__ void xyz_final(const XYZAcc& a, double2 z, double2 x[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x[i] = cadd(a.P[i], cmul(z, a.Q[i]));
+}
+
 // Per-bin inputs shared by all modes of one bin.
 struct BinIn {
   double f, f13, fm13, lnf3, fm76, invf;
   double a, sa, ca;    // a = pi f L
+  double aturn;        // a / (2 pi) = f L / 2
   double2 z;           // e^{-2 i a}
   double frc;          // frac(f t_c) computed exactly (turns)
 };
@@ -183,11 +217,12 @@ struct BinIn {
 // X = Q X' with Q = TDI factor (-i a) e^{-ia}; here
 //   X' = G31 V31 - G12 U12,  Y' = G12 V12 - G23 U23,  Z' = G23 V23 - G31 U31,
 // G_l = e^{i pi f k.delta_t} (n_l.h~.n_l) per link pair l=(r,s) with third spacecraft t,
-// U_l = sinc(a(1 - k.n_l)) + z sinc(a(1 + k.n_l)), V_l = sinc(a(1 + k.n_l)) + z sinc(a(1 - k.n_l)),
+// U_l = s-_l + z s+_l, V_l = s+_l + z s-_l, s-+_l = sinc(a(1 -+ k.n_l)),
 // n_l = (x_r - x_s)/|x_r - x_s|, geometry at the mode's t_f, and the centre Doppler phase
-// e^{-2 pi i f k.x_c} folded into the mode's phase.
+// e^{-2 pi i f k.x_c} folded into the mode's phase. Written as X' = P_X + z Q_X with
+// P_X = G31 s+31 - G12 s-12, Q_X = G31 s-31 - G12 s+12 (and cyclically for Y', Z').
 __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
-                                         double2 acc[3]) {
+                                         XYZAcc& acc, const double2* __restrict__ tab) {
   // --- waveform and time-frequency map (rows A2, A3)
   const double v = C.cm * B.f13;
   const double iv = C.icm * B.fm13;
@@ -199,7 +234,7 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);
-    dpol = fma(dpol, v, (k - 5) * S.P[k]);
+    dpol = fma(dpol, v, S.Pd[k]);
   }
   const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));  // v dPsi_PN/dv
@@ -215,15 +250,26 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   if (C.p >= 2) amp *= v;
   // --- orbit at t_f (row A4)
   double xc[3], dl[3][3];
-  orbit_offsets(D, tf, xc, dl);
+  orbit_offsets(D, tf, xc, dl, tab);
   const double kxc = S.k[0] * xc[0] + S.k[1] * xc[1] + S.k[2] * xc[2];
-  double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
-  ph -= rint(ph);
+  const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
   double sph, cph;
-  sincospi(2.0 * ph, &sph, &cph);
+  sincos_turns(ph, tab, &sph, &cph);
   const double2 H = make_double2(amp * cph, amp * sph);
+  // third-spacecraft phases e^{i pi f k.delta_t}; the offsets sum to zero, so E_2 = conj(E_0 E_1)
+  double2 E[3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double kd = S.k[0] * dl[i][0] + S.k[1] * dl[i][1] + S.k[2] * dl[i][2];
+    sincos_turns(0.5 * B.f * kd, tab, &E[i].y, &E[i].x);
+  }
+  {
+    const double2 e01 = cmul(E[0], E[1]);
+    E[2] = make_double2(e01.x, -e01.y);
+  }
   // --- links (row A5): pair l = (1,2), (2,3), (3,1); third spacecraft 3, 1, 2
-  double2 G[3], U[3], V[3];
+  double2 G[3];
+  double smv[3], spv[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int r = l, s = (l + 1) % 3, t = (l + 2) % 3;
@@ -234,13 +280,10 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     const double np = S.p[0] * n0 + S.p[1] * n1 + S.p[2] * n2;
     const double nq = S.q[0] * n0 + S.q[1] * n1 + S.q[2] * n2;
     const double2 gam = make_double2(C.Pp * (np * np - nq * nq), C.Pc * 2.0 * np * nq);
-    const double kd = S.k[0] * dl[t][0] + S.k[1] * dl[t][1] + S.k[2] * dl[t][2];
-    double se, ce;
-    sincospi(B.f * kd, &se, &ce);
-    G[l] = cmul(make_double2(ce, se), cmul(gam, H));
+    G[l] = cmul(E[t], cmul(gam, H));
     // sinc(a(1 -+ kn)) from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     double sak, cak;
-    sincos(B.a * kn, &sak, &cak);
+    sincos_turns(B.aturn * kn, tab, &sak, &cak);
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
     const double s1 = B.sa * cak - B.ca * sak, s2 = B.sa * cak + B.ca * sak;
     double sm, spl;
@@ -252,13 +295,19 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
       sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
       spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2 / u2;
     }
-    U[l] = make_double2(fma(B.z.x, spl, sm), B.z.y * spl);
-    V[l] = make_double2(fma(B.z.x, sm, spl), B.z.y * sm);
+    smv[l] = sm;
+    spv[l] = spl;
   }
-  // --- TDI brackets (row A6); l index: 0 = (1,2), 1 = (2,3), 2 = (3,1)
-  acc[0] = cadd(acc[0], csub(cmul(G[2], V[2]), cmul(G[0], U[0])));
-  acc[1] = cadd(acc[1], csub(cmul(G[0], V[0]), cmul(G[1], U[1])));
-  acc[2] = cadd(acc[2], csub(cmul(G[1], V[1]), cmul(G[2], U[2])));
+  // --- TDI brackets (row A6); l index: 0 = (1,2), 1 = (2,3), 2 = (3,1); bracket c uses
+  // links lp = (c + 2) % 3 (V term) and lu = c (U term)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lp = (c + 2) % 3, lu = c;
+    acc.P[c].x = fma(G[lp].x, spv[lp], fma(-G[lu].x, smv[lu], acc.P[c].x));
+    acc.P[c].y = fma(G[lp].y, spv[lp], fma(-G[lu].y, smv[lu], acc.P[c].y));
+    acc.Q[c].x = fma(G[lp].x, smv[lp], fma(-G[lu].x, spv[lu], acc.Q[c].x));
+    acc.Q[c].y = fma(G[lp].y, smv[lp], fma(-G[lu].y, spv[lu], acc.Q[c].y));
+  }
 }
 
 __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinIn& B) {
@@ -269,6 +318,7 @@ __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinI
   B.fm76 = D.fm76[b];
   B.invf = B.fm13 * B.fm13 * B.fm13;
   B.a = kPi * B.f * D.L;
+  B.aturn = 0.5 * B.f * D.L;
   const double2 sc = D.sca[b];
   B.sa = sc.x; B.ca = sc.y;
   B.z = D.z[b];
@@ -279,16 +329,19 @@ __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinI
 }
 
 // Mode-summed TDI brackets X', Y', Z' of one sample at one bin.
-__device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, int b, double2 acc[3]) {
+__device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, int b, double2 acc[3],
+                                        const double2* __restrict__ tab) {
   BinIn B;
   load_bin(D, b, S.tc, B);
-  acc[0] = acc[1] = acc[2] = make_double2(0.0, 0.0);
+  XYZAcc a;
+  xyz_zero(a);
 #pragma unroll 1
   for (int md = 0; md < kNModes; ++md) {
     const ModeCoef& C = S.md[md];
     if (!C.active || !(B.f < C.fend)) continue;
-    mode_bin(D, S, C, B, acc);
+    mode_bin(D, S, C, B, a, tab);
   }
+  xyz_final(a, B.z, acc);
 }
 
 // A/E/T combinations (without Q n_c): B_A = Z' - X', B_E = X' - 2Y' + Z', B_T = X' + Y' + Z'.

@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
                                                         const int* __restrict__ nend,
                                                         const long long* __restrict__ off, double* part) {
   __shared__ double sh[kGradW][kTileBins / 32];
+  __shared__ double2 stab[kSinTab];
+  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -125,11 +128,13 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
       const SampleGrad& SG = sgrad[s];
       BinIn Bn;
       load_bin(D, b, S.tc, Bn);
-      double2 x[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+      XYZAcc xa;
+      xyz_zero(xa);
 #pragma unroll 1
       for (int md = 0; md < kNModes; ++md)
-        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bin(D, S, S.md[md], Bn, x);
-      double2 o[3];
+        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bin(D, S, S.md[md], Bn, xa, stab);
+      double2 x[3], o[3];
+      xyz_final(xa, Bn.z, x);
       aet_from_xyz(x, o);
       double2 sX, sY, sZ;
       bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
       gacc_zero(g);
 #pragma unroll 1
       for (int md = 0; md < kNModes; ++md)
-        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g);
+        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, stab);
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
 #pragma unroll
       for (int i = 0; i < 3; ++i) { v[14 + i] = g.k[i]; v[17 + i] = g.p[i]; v[20 + i] = g.qv[i]; }
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(kFisherThreads) k_fisher_fwd(DetSet ds, int B,
         gacc_zero(g);
 #pragma unroll 1
         for (int md = 0; md < kNModes; ++md)
-          if (S.md[md].active && Bn.f < S.md[md].fend) mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g);
+          if (S.md[md].active && Bn.f < S.md[md].fend) mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, D.sct);
         double row[PE_NPARAM];
         gacc_to_theta(g, SG, row);
         for (int i = 0; i < PE_NPARAM; ++i) Js[j][i][tid] = row[i];

@@ -19,7 +19,8 @@ constexpr double kEulerGamma = 0.57721566490153286061;
 
 constexpr int kNModes = 5;      // (2,2) (2,1) (3,3) (3,2) (4,4)
 constexpr int kMaxDet = 8;
-constexpr int kTileBins = 128;  // frequency bins per work tile = threads per CTA of the hot kernels
+constexpr int kTileBins = 128;
+constexpr int kSinTab = 1024;   // entries of the (cos, sin) table used by sincos_turns  // frequency bins per work tile = threads per CTA of the hot kernels
 
 // Per-(sample, mode) coefficients (row A1 of the path). With v = (2 pi M f/m)^(1/3):
 //   v = cm f^(1/3), 1/v = icm f^(-1/3), ln v = lncm + ln(f)/3,
@@ -47,6 +48,7 @@ template <class T>
 struct SampleCoefT {
   T tc;
   T P[8];
+  T Pd[8];              // (k - 5) P[k]: coefficients of v dPsi_PN/dv
   T Q5, Q6;
   T k[3], p[3], q[3];   // propagation direction and polarisation frame
   ModeCoefT<T> md[kNModes];
@@ -85,13 +87,14 @@ struct DetDev {
   int pad_;
   double L;          // nominal arm [s]
   // orbit: centre R (cos alpha, sin alpha, 0), alpha in half-turns = alpha0_ht + t * rate_ht
-  double R, alpha0_ht, rate_ht;
+  // (alpha0_t, rate_t: the same in turns)
+  double R, alpha0_ht, rate_ht, alpha0_t, rate_t;
   // heliocentric (first order in e): offsets from the centre use eRh = e R / 2,
   // eR3h = 3 e R / 2, eRs3 = sqrt(3) e R and the spacecraft angles cb[i], sb[i].
   double eRh, eR3h, eRs3;
   double cb[3], sb[3];
   // geocentric: offsets r (cos phi_i e1 + sin phi_i e2), phi_0 in half-turns = t * geo_rate_ht
-  double rgeo, geo_rate_ht;
+  double rgeo, geo_rate_ht, geo_rate_t;
   double e1[3], e2[3];
   // per-bin tables (length nb)
   const double* f;      // f_k = k / T
@@ -104,6 +107,7 @@ struct DetDev {
   const double2* dg;    // [3][nb]: conj(d~_c) w_c Q n_c   (w_c = 4/(S_c T))
   const double* gg;     // [3][nb]: w_c |Q|^2 n_c^2
   const double* dd;     // [3]: <d|d>_c
+  const double2* sct;   // [kSinTab]: (cos, sin)(2 pi j / kSinTab), the sincos table
   // Q = TDI factor(z) (-i a) e^{-i a}; n_A = 1/sqrt2, n_E = 1/sqrt6, n_T = 1/sqrt3
 };
 

@@ -39,6 +39,15 @@ __global__ void k_grid_tables(double T, long long k0, int nb, double L, double* 
   z[b] = make_double2(c2, -s2);
 }
 
+// The (cos, sin)(2 pi j / kSinTab) table of sincos_turns (exact arguments j/(kSinTab/2) half-turns).
+__global__ void k_sincos_table(double2* tab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kSinTab) return;
+  double s, c;
+  sincospi(double(j) / (kSinTab / 2), &s, &c);
+  tab[j] = make_double2(c, s);
+}
+
 // Analytic PSD (acceleration + OMS noise only): equal-arm TDI-1.5 A/E/T spectra
 //   S_A = S_E = 8 sin^2 x [(2 + cos x) S_oms + (6 + 4 cos x + 2 cos 2x) S_acc],
 //   S_T = 32 sin^2 x sin^2(x/2) [S_oms + 4 sin^2(x/2) S_acc],   x = 2 pi f L,
@@ -226,6 +235,9 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
                                                                  const int* __restrict__ nend,
                                                                  const long long* __restrict__ off, double* part) {
   __shared__ double sh[6][kTileBins / 32];
+  __shared__ double2 stab[kSinTab];
+  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
     if (b < nend[p]) {
       const SampleCoef& S = coef[s];
       double2 x[3], o[3];
-      bin_xyz(D, S, b, x);
+      bin_xyz(D, S, b, x, stab);
       aet_from_xyz(x, o);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -293,7 +305,7 @@ __global__ void k_signal(DetDev D, const SampleCoef* coef, double2* out) {
   if (b >= D.nb) return;
   const SampleCoef& S = coef[0];
   double2 x[3], o[3];
-  bin_xyz(D, S, b, x);
+  bin_xyz(D, S, b, x, D.sct);
   aet_from_xyz(x, o);
   const double2 Q = transfer_q(kPi * D.f[b] * D.L, D.sca[b], D.z[b], D.tdi_gen);
   for (int c = 0; c < 3; ++c) out[c * D.nb + b] = cscale(cmul(Q, o[c]), kChanNorm[c]);
@@ -314,6 +326,10 @@ __global__ void k_inject(int nb, double T, const double* psd, const double2* nor
 cudaError_t launch_grid_tables(double T, long long k0, int nb, double L, double* f, double* f13, double* fm13,
                                double* lnf3, double* fm76, double2* sca, double2* z, cudaStream_t st) {
   k_grid_tables<<<(nb + 127) / 128, 128, 0, st>>>(T, k0, nb, L, f, f13, fm13, lnf3, fm76, sca, z);
+  return cudaGetLastError();
+}
+cudaError_t launch_sincos_table(double2* tab, cudaStream_t st) {
+  k_sincos_table<<<(kSinTab + 127) / 128, 128, 0, st>>>(tab);
   return cudaGetLastError();
 }
 cudaError_t launch_psd_model(const double* f, int nb, double L, double oms, double acc, int shaping, int tdi_gen,

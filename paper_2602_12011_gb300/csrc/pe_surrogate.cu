@@ -229,7 +229,7 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
   else drdu = (y[(md * 2) * kNodes + j + 1] - y[(md * 2) * kNodes + j - 1]) / (2.0 * h);
   const double tf = Sa.tc + C.tffac / f * D0 + drdu / (2.0 * kPi * f);
   double xc[3], dl[3][3];
-  orbit_offsets(D, tf, xc, dl);
+  orbit_offsets(D, tf, xc, dl, D.sct);
   const double kxc = Sa.k[0] * xc[0] + Sa.k[1] * xc[1] + Sa.k[2] * xc[2];
   const double phi = C.ph0 - (0.5 * mm * psi0 + r) / (2.0 * kPi) - f * kxc;
   // link transfer functions per unit mode amplitude at the node frequency
@@ -324,7 +324,8 @@ __global__ void k_node_h(const double* theta, int B, double* hs) {
 
 // Spline evaluation of one mode at one bin: adds H T_X, H T_Y, H T_Z to acc.
 __device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, const BinIn& B, double u,
-                                             const double* cf, double h, double2 acc[3]) {
+                                             const double* cf, double h, double2 acc[3],
+                                             const double2* __restrict__ tab) {
   const double uj = (u - log(kFmin)) / h;
   int j = (int)floor(uj);
   j = j < 0 ? 0 : (j > kNodes - 2 ? kNodes - 2 : j);
@@ -341,10 +342,8 @@ __device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, con
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
     w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
   }
-  double ph = val[0] - B.frc;
-  ph -= rint(ph);
   double sph, cph;
-  sincospi(2.0 * ph, &sph, &cph);
+  sincos_turns(val[0] - B.frc, tab, &sph, &cph);
   const double amp = ampN * B.fm76 * w;  // Newtonian power law; the mode factor |H_lm| is in T
   const double2 H = make_double2(amp * cph, amp * sph);
   acc[0] = cadd(acc[0], cmul(H, make_double2(val[1], val[2])));
@@ -371,6 +370,9 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
                                                        const int* __restrict__ nend, const long long* __restrict__ off,
                                                        double* part, int mode) {
   __shared__ double sh[6][kTileBins / 32];
+  __shared__ double2 stab[kSinTab];
+  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -385,7 +387,8 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
       BinIn Bn;
       load_bin(D, b, S.tc, Bn);
       double2 xs[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-      double2 xp[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+      XYZAcc xpa;
+      xyz_zero(xpa);
       const double u = 3.0 * Bn.lnf3;
 #pragma unroll 1
       for (int md = 0; md < kNModes; ++md) {
@@ -393,9 +396,12 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
         if (!C.active || !(Bn.f < C.fend)) continue;
         const size_t sys = ((size_t)I * B + s) * kNModes + md;
         if (sur)
-          mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], xs);
-        if (!sur || mode == 1) mode_bin(D, S, C, Bn, xp);
+          mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], xs,
+                       stab);
+        if (!sur || mode == 1) mode_bin(D, S, C, Bn, xpa, stab);
       }
+      double2 xp[3];
+      xyz_final(xpa, Bn.z, xp);
       double2 os[3], op[3];
       aet_from_xyz(sur ? xs : xp, os);
       if (mode == 0) {
