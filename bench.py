@@ -185,6 +185,7 @@ def main():
     import torch.distributed as dist
     from paper_2602_12011_gb300 import build as Bld
     from paper_2602_12011_gb300 import _lib as L
+    from paper_2602_12011_gb300 import shard
 
     torch.cuda.set_device(local_rank)
     if world > 1:
@@ -238,11 +239,7 @@ def main():
     fwd_ms, fwd_launches = L.pe_profile_read()
     clk = clocks.stop(local_rank)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = shard.max_over_ranks(sum(step_ms) / 1e3, device="cuda")
     value = world * B * K / t_total
     result_ok = bool(torch.isfinite(out_dev).all().item())
 
@@ -378,11 +375,7 @@ def main():
         dt = time.perf_counter() - t0
         if k > 0:
             e2e_t.append(dt)
-    e2e_tot = sum(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
+    e2e_tot = shard.max_over_ranks(sum(e2e_t), device="cuda")
     e2e_value = world * B * K / e2e_tot
 
     # ---- roofline of the dominant kernel (fused forward, FP64 ALU bound)
