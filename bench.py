@@ -295,6 +295,16 @@ def main():
     grad_value = world * B * Kg / (sum(gms) / 1e3)
     grad_ok = bool(torch.isfinite(grad_dev).all().item())
 
+    # ---- Fisher matrix at the injected source (5 modes, all 11 parameters), device-timed
+    thf = torch.tensor(wl["inj"][None, :], device="cuda")
+    Fd = torch.empty((1, 11, 11), dtype=torch.float64, device="cuda")
+    L.pe_fisher(hs, thf, 1, mask, Fd, stream)
+    e0.record(stream)
+    L.pe_fisher(hs, thf, 1, mask, Fd, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fisher = {"ms": e0.elapsed_time(e1), "theta": "injection", "finite": bool(torch.isfinite(Fd).all().item())}
+
     # ---- detector network (LISA 2^22 s + Taiji 2^21 s + TianQin 2^20 s), B = 4096, one CUDA-graph
     # plan with autotuned launch parameters
     net = None
@@ -405,6 +415,7 @@ def main():
                     "d2h_bytes_per_step": int(B * 8)},
             "plain_path": {"value": plain_value, "unit": UNIT, "samples": n_plain,
                            "graph_plan_value": plain_graph_value, "batched_same_samples": batched_same},
+            "fisher": fisher,
             "network": net,
             "surrogate": sur,
             "tuning": tuned,

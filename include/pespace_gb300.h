@@ -248,6 +248,18 @@ pe_status pe_profile_enable(int on);
 pe_status pe_profile_read(double* total_ms, int64_t* launches);
 pe_status pe_measure_fp64_peak(double seconds, double* out_tflops);
 
+/* Fisher-Gaussian approximation of the posterior on a subset of the parameters (Sec. 2.2: the
+ * high-SNR likelihood Eq. eq_ll_fisher with covariance C = F^-1; Sec. 3.3 applies it to lambda,
+ * beta, psi, t_c with the other parameters held at their fiducial values). Computes the full
+ * Fisher matrix at theta0 (host [11]) with pe_fisher, takes the sub-block on idx[k] (host, distinct
+ * indices in [0, 11)), inverts it by Cholesky, and maps the caller's standard normals
+ * normals[n][k] (host) to samples out_samples[n][11] (host) = theta0 + L z with C = L L^T (other
+ * components equal theta0). out_cov: host [k][k]. n may be 0 (then normals/out_samples may be
+ * NULL). PE_EINVAL if the sub-block is not positive definite. Synchronous. */
+pe_status pe_fisher_gaussian(const pe_detector* dets, int ndet, const double* theta0, unsigned mode_mask,
+                             const int32_t* idx, int k, const double* normals, int n, double* out_cov,
+                             double* out_samples);
+
 /* Message describing the last failing call on this thread ("" if none). */
 const char* pe_last_error(void);
 

@@ -103,6 +103,8 @@ def lib():
                      "pe_surrogate_mismatch", "pe_surrogate_mlp_debug", "pe_surrogate_get_weights",
                      "pe_surrogate_save", "pe_surrogate_load"):
             getattr(L, name).restype = C.c_int
+        L.pe_fisher_gaussian.argtypes = [_P, C.c_int, _P, C.c_uint, _P, C.c_int, _P, C.c_int, _P, _P]
+        L.pe_fisher_gaussian.restype = C.c_int
         L.pe_profile_enable.argtypes = [C.c_int]
         L.pe_profile_read.argtypes = [_P, _P]
         L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
@@ -505,3 +507,21 @@ class Surrogate:
 
     def load(self, path: str):
         _check(lib().pe_surrogate_load(self.handle, path.encode()))
+
+
+def fisher_gaussian(dets, theta0, mode_mask: int, idx, normals=None):
+    """Fisher-Gaussian posterior on the parameters idx (others fixed at theta0): returns
+    (cov [k][k], samples [n][11]) with samples = theta0 + L z for the given standard normals z [n][k]."""
+    th = np.ascontiguousarray(np.asarray(theta0, dtype=np.float64).reshape(NPARAM))
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    k = ix.size
+    cov = np.zeros((k, k))
+    if normals is None:
+        n, z, out = 0, None, None
+    else:
+        z = np.ascontiguousarray(np.asarray(normals, dtype=np.float64).reshape(-1, k))
+        n = z.shape[0]
+        out = np.zeros((n, NPARAM))
+    _check(lib().pe_fisher_gaussian(_handles([d.handle for d in dets]), len(dets), _ptr(th), int(mode_mask), _ptr(ix),
+                                    k, _ptr(z), n, _ptr(cov), _ptr(out)))
+    return cov, out

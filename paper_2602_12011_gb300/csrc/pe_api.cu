@@ -534,6 +534,67 @@ pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int 
   return PE_OK;
 }
 
+// Fisher-Gaussian approximation of the posterior on a parameter subset (Sec. 2.2: C = F^-1 of
+// Eq. eq_ll_fisher, the other parameters held at theta0 as in Sec. 3.3): F on the subset is the
+// sub-block of the full Fisher matrix; C = F_sub^-1 by Cholesky; samples theta0 + L z with
+// C = L L^T and z the caller's standard normals.
+pe_status pe_fisher_gaussian(const pe_detector* dets, int ndet, const double* theta0, unsigned mode_mask,
+                             const int32_t* idx, int k, const double* normals, int n, double* out_cov,
+                             double* out_samples) {
+  if (theta0 == nullptr || idx == nullptr || out_cov == nullptr) return fail(PE_EINVAL, "theta0/idx/out_cov is NULL");
+  if (k < 1 || k > PE_NPARAM) return fail(PE_EINVAL, "k=%d outside [1, 11]", k);
+  if (n < 0 || (n > 0 && (normals == nullptr || out_samples == nullptr)))
+    return fail(PE_EINVAL, "normals/out_samples required for n > 0");
+  for (int i = 0; i < k; ++i) {
+    if (idx[i] < 0 || idx[i] >= PE_NPARAM) return fail(PE_EINVAL, "idx[%d]=%d out of range", i, idx[i]);
+    for (int j = 0; j < i; ++j)
+      if (idx[j] == idx[i]) return fail(PE_EINVAL, "idx has a repeated parameter");
+  }
+  double F[PE_NPARAM * PE_NPARAM];
+  pe_status st = pe_fisher(dets, ndet, theta0, 1, mode_mask, F, nullptr);
+  if (st != PE_OK) return st;
+  // sub-block and its Cholesky factor F_sub = R R^T
+  double A[PE_NPARAM][PE_NPARAM], R[PE_NPARAM][PE_NPARAM] = {};
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) A[i][j] = F[idx[i] * PE_NPARAM + idx[j]];
+  for (int j = 0; j < k; ++j) {
+    double d = A[j][j];
+    for (int m = 0; m < j; ++m) d -= R[j][m] * R[j][m];
+    if (!(d > 0.0)) return fail(PE_EINVAL, "Fisher sub-block is not positive definite");
+    R[j][j] = std::sqrt(d);
+    for (int i = j + 1; i < k; ++i) {
+      double v = A[i][j];
+      for (int m = 0; m < j; ++m) v -= R[i][m] * R[j][m];
+      R[i][j] = v / R[j][j];
+    }
+  }
+  // C = F_sub^-1 = R^-T R^-1: invert the lower-triangular R column by column
+  double Ri[PE_NPARAM][PE_NPARAM] = {};
+  for (int c = 0; c < k; ++c) {
+    for (int i = 0; i < k; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int m = 0; m < i; ++m) v -= R[i][m] * Ri[m][c];
+      Ri[i][c] = v / R[i][i];
+    }
+  }
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      double v = 0.0;
+      for (int m = 0; m < k; ++m) v += Ri[m][i] * Ri[m][j];
+      out_cov[i * k + j] = v;
+    }
+  // samples: delta = L z with L = R^-T (lower factor of C), so C = L L^T
+  for (int sidx = 0; sidx < n; ++sidx) {
+    for (int p = 0; p < PE_NPARAM; ++p) out_samples[(size_t)sidx * PE_NPARAM + p] = theta0[p];
+    for (int i = 0; i < k; ++i) {
+      double v = 0.0;
+      for (int m = 0; m < k; ++m) v += Ri[m][i] * normals[(size_t)sidx * k + m];
+      out_samples[(size_t)sidx * PE_NPARAM + idx[i]] += v;
+    }
+  }
+  return PE_OK;
+}
+
 }  // extern "C"
 
 namespace pe {
