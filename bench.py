@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-network", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="forward path: all FP64, or FP64 phase/t_f/sums with double-word geometry")
     return ap.parse_args()
 
 
@@ -194,7 +196,8 @@ def main():
     L.lib()
 
     det, T, k0, nb = wl["dets"][0]
-    mask = wl["mode_mask"]
+    mask64 = wl["mode_mask"]                       # gradient and Fisher: FP64 only
+    mask = mask64 | (L.PE_PREC_MIXED if args.precision == "mixed" else 0)
     B = args.batch
     theta = wl["theta"] if rank == 0 else W.draw_prior(B, W.SEED_BATCH_HM + 1000 * rank, T)
     gd = L.Detector(det, T, k0, nb)
@@ -282,13 +285,13 @@ def main():
     # ---- gradient evals/s: hand-written adjoint over the same batch, device-timed
     grad_dev = torch.empty((B, 11), dtype=torch.float64, device="cuda")
     ll_dev = torch.empty(B, dtype=torch.float64, device="cuda")
-    L.pe_loglike_grad_batch(hs, th_dev, B, mask, ll_dev, grad_dev, None, stream)
+    L.pe_loglike_grad_batch(hs, th_dev, B, mask64, ll_dev, grad_dev, None, stream)
     Kg = max(2, K // 2)
     gms = []
     for k in range(Kg):
         flush.zero_()
         e0.record(stream)
-        L.pe_loglike_grad_batch(hs, th_dev, B, mask, ll_dev, grad_dev, None, stream)
+        L.pe_loglike_grad_batch(hs, th_dev, B, mask64, ll_dev, grad_dev, None, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         gms.append(e0.elapsed_time(e1))
@@ -298,9 +301,9 @@ def main():
     # ---- Fisher matrix at the injected source (5 modes, all 11 parameters), device-timed
     thf = torch.tensor(wl["inj"][None, :], device="cuda")
     Fd = torch.empty((1, 11, 11), dtype=torch.float64, device="cuda")
-    L.pe_fisher(hs, thf, 1, mask, Fd, stream)
+    L.pe_fisher(hs, thf, 1, mask64, Fd, stream)
     e0.record(stream)
-    L.pe_fisher(hs, thf, 1, mask, Fd, stream)
+    L.pe_fisher(hs, thf, 1, mask64, Fd, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     fisher = {"ms": e0.elapsed_time(e1), "theta": "injection", "finite": bool(torch.isfinite(Fd).all().item())}
@@ -317,7 +320,7 @@ def main():
             nds.append(dn)
         thn = torch.tensor(wn["theta"] if rank == 0 else W.draw_prior(4096, W.SEED_BATCH_NET + 1000 * rank, 2.0 ** 20),
                            device="cuda")
-        pn = L.Plan(nds, 4096, wn["mode_mask"], theta=thn, autotune=True)
+        pn = L.Plan(nds, 4096, wn["mode_mask"] | (mask & L.PE_PREC_MIXED), theta=thn, autotune=True)
         for _ in range(3):
             pn.launch(stream)
         nms = []
@@ -349,12 +352,12 @@ def main():
         ths = W.draw_prior(Bs, 2609 + rank, T)
         tts = torch.tensor(ths, device="cuda")
         outs = torch.empty(Bs, dtype=torch.float64, device="cuda")
-        srg.loglike([gd], tts, mask)
+        srg.loglike([gd], tts, mask64)
         L.pe_loglike_batch(hs, tts, Bs, mask, outs, None, None, stream)
         torch.cuda.synchronize()
         flush.zero_()
         e0.record(stream)
-        _, used = srg.loglike([gd], tts, mask)
+        _, used = srg.loglike([gd], tts, mask64)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_s = e0.elapsed_time(e1)
@@ -365,7 +368,7 @@ def main():
         torch.cuda.synchronize()
         ms_p = e0.elapsed_time(e1)
         tho = W.draw_prior(2048, 2606, T)
-        mm = srg.mismatch(gd, torch.tensor(tho, device="cuda"), mask).cpu().numpy()
+        mm = srg.mismatch(gd, torch.tensor(tho, device="cuda"), mask64).cpu().numpy()
         inbox = (tho[:, 0] >= 3e5) & (tho[:, 1] <= 8.0)
         sur = {"value": world * Bs / (ms_s / 1e3), "unit": UNIT, "plain_same_batch": world * Bs / (ms_p / 1e3),
                "gain": ms_p / ms_s, "batch": Bs, "used_fraction": float(used.float().mean().item()),

@@ -43,6 +43,16 @@ extern "C" {
 #define PE_MODE_32 0x08u
 #define PE_MODE_44 0x10u
 #define PE_MODE_ALL 0x1Fu
+/* Precision flag, OR-ed into the mode_mask of the forward entry points (pe_loglike_batch,
+ * pe_loglike_batch_noalloc, pe_plan_create, pe_autotune, pe_signal_aet). Without it every step
+ * runs in FP64. With it the TaylorF2 phase, t_f, the reduction of the phase and orbital angles
+ * to a fraction of a turn and every sum stay FP64, while the response geometry (orbit offsets,
+ * link vectors, projections, sincs, third-spacecraft phases, TDI brackets) runs on the FP32 pipe
+ * in double-word arithmetic (~48-bit significands, ~1e-14 relative). It agrees with the FP64 path
+ * to far below the 1e-10 parity bar but not bit for bit; each precision is bitwise
+ * batch-invariant by itself. The gradient, Fisher and surrogate entry points are FP64 only and
+ * reject the flag. */
+#define PE_PREC_MIXED 0x100u
 
 typedef enum {
   PE_OK = 0,
@@ -110,7 +120,7 @@ pe_status pe_data_norm(pe_detector det, double* out_dd);
 /* Noise-free signal h~_c(f_k) of one source in the A, E, T channels on the detector grid:
  * TaylorF2 modes (SPA, time-frequency map Eq. eq_tf), single-link response Eq. eq_fd_resp at
  * t_f, FD TDI and A/E/T (Sec. 2.1). theta: [11] (host or device); out: [3][nbins][2]
- * (host or device). Out-of-domain theta gives PE_EINVAL. */
+ * (host or device). Out-of-domain theta gives PE_EINVAL. mode_mask may carry PE_PREC_MIXED. */
 pe_status pe_signal_aet(pe_detector det, const double* theta, unsigned mode_mask, double* out, void* stream);
 
 /* Data = noise-free signal of theta_inj + noise with Re, Im ~ N(0, S_c T/4) (Eq.
@@ -127,6 +137,7 @@ pe_status pe_inject(pe_detector det, const double* theta_inj, unsigned mode_mask
  *   out_logl: [B] (host or device).
  *   out_dhhh: nullable [B][ndet][3][2] = (<d|h>, <h|h>) per detector and channel.
  *   out_status: nullable int32 [B]; bit 0 = sample out of domain.
+ *   mode_mask: PE_MODE_* bits (at least one), optionally | PE_PREC_MIXED.
  * Samples are independent: each sample's result depends only on its own theta (fixed-order
  * reductions), so it is identical in any batch. Errors: PE_EINVAL, PE_ESTATE, PE_ENOMEM, PE_ECUDA. */
 pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
@@ -141,9 +152,9 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
  * no allocating routine.
  *   theta, out_logl and the optional out_dhhh / out_status must be DEVICE pointers (host buffers
  *   would need staging memory); other arguments and layouts are as for pe_loglike_batch.
- *   Size limit: coefficients (about 0.7 KB per sample) plus one 48-byte partial per 128-bin tile
- *   of every (detector, sample) pair must fit in 32 MiB -- about 400 samples on one 2^22 s grid
- *   (209,296 bins), about 1,500 on a 2^20 s grid. Larger batches return PE_EINVAL with the
+ *   Size limit: coefficients (880 bytes per sample) plus one 48-byte partial per 512-bin tile
+ *   of every (detector, sample) pair must fit in 32 MiB -- about 1,600 samples on one 2^22 s grid
+ *   (209,296 bins), about 5,700 on a 2^20 s grid. Larger batches return PE_EINVAL with the
  *   needed size in pe_last_error(); split them.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  *   that device current, so make that first call before any stream capture.
@@ -158,7 +169,7 @@ pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet, const doub
  * and fixed DEVICE buffers (theta [B][11], out_logl [B], optional out_dhhh [B][ndet][3][2] and
  * out_status [B]), captured once into a CUDA graph with its scratch allocated at creation. Every
  * (detector, sample) pair brings its own grid length and active bin range; all pairs run in one
- * persistent launch over their 128-bin tiles. Refill theta in place and call pe_plan_launch on
+ * persistent launch over their 512-bin tiles. Refill theta in place and call pe_plan_launch on
  * any stream; results equal pe_loglike_batch's bit for bit.
  *   autotune = 1: if the tuning cache has no entry for this workload (GPU, SM count, batch size,
  *   mode mask, grids), time the forward kernel's launch variants on the theta present at

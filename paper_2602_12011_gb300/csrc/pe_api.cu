@@ -37,6 +37,15 @@ struct pe_detector_s {
   double* psd_model;   // [3][nb] analytic PSD
   double* dd_dev;      // [3]
   double2* sct;        // [kSinTab] sincos table
+  float4* sctw;        // [kSinTab] the same as double words
+  float2* fw;          // [nb] double words of f, pi f L, f L / 2, sin(pi f L), cos(pi f L)
+  float2* aw;
+  float2* atw;
+  float2* saw;
+  float2* caw;
+  float4* zw;          // [nb] z as a double-word pair
+  float4* dgw;         // [3][nb] dg / dg_scale as double words
+  float2* ggw;         // [3][nb] gg / gg_scale as double words
   double dd[3];
   int has_data;
   pe::DetDev dev;
@@ -107,6 +116,12 @@ struct Scratch {
 
 double det_arm_s(const pe_detector_config& c) { return c.arm_m / pe::kC; }
 
+// double -> double word (hi = nearest float, lo = nearest float of the remainder)
+float2 host_dw(double a) {
+  const float h = static_cast<float>(a);
+  return make_float2(h, static_cast<float>(a - static_cast<double>(h)));
+}
+
 void fill_dev(pe_detector_s* d) {
   pe::DetDev& D = d->dev;
   memset(&D, 0, sizeof(D));
@@ -132,6 +147,13 @@ void fill_dev(pe_detector_s* d) {
       D.cb[i] = std::cos(b);
       D.sb[i] = std::sin(b);
     }
+    // offsets as linear forms in (cos 2a, sin 2a) for x, y and (cos a, sin a) for z:
+    //   x = eRh (c2 cb + s2 sb) - eR3h cb,  y = eRh (s2 cb - c2 sb) - eR3h sb,  z = -eRs3 (c cb + s sb)
+    for (int i = 0; i < 3; ++i) {
+      D.oA[i][0] = host_dw(D.eRh * D.cb[i]);   D.oB[i][0] = host_dw(D.eRh * D.sb[i]);  D.oC[i][0] = host_dw(-D.eR3h * D.cb[i]);
+      D.oA[i][1] = host_dw(-D.eRh * D.sb[i]);  D.oB[i][1] = host_dw(D.eRh * D.cb[i]);  D.oC[i][1] = host_dw(-D.eR3h * D.sb[i]);
+      D.oA[i][2] = host_dw(-D.eRs3 * D.cb[i]); D.oB[i][2] = host_dw(-D.eRs3 * D.sb[i]); D.oC[i][2] = host_dw(0.0);
+    }
   } else {
     D.rgeo = D.L / std::sqrt(3.0);
     D.geo_rate_ht = 2.0 / c.geo_period_s;
@@ -142,9 +164,30 @@ void fill_dev(pe_detector_s* d) {
     D.e2[0] = n[1] * D.e1[2] - n[2] * D.e1[1];
     D.e2[1] = n[2] * D.e1[0] - n[0] * D.e1[2];
     D.e2[2] = n[0] * D.e1[1] - n[1] * D.e1[0];
+    // spacecraft i at phase phi_0 + 2 pi i/3: r (cos(phi_0 + b_i) e1 + sin(phi_0 + b_i) e2)
+    //   = cos phi_0 r (cos b_i e1 + sin b_i e2) + sin phi_0 r (-sin b_i e1 + cos b_i e2)
+    for (int i = 0; i < 3; ++i) {
+      const double cbi = std::cos(2.0 * pe::kPi * i / 3.0), sbi = std::sin(2.0 * pe::kPi * i / 3.0);
+      for (int j = 0; j < 3; ++j) {
+        D.oA[i][j] = host_dw(D.rgeo * (cbi * D.e1[j] + sbi * D.e2[j]));
+        D.oB[i][j] = host_dw(D.rgeo * (-sbi * D.e1[j] + cbi * D.e2[j]));
+        D.oC[i][j] = host_dw(0.0);
+      }
+    }
   }
+  D.Rw = host_dw(D.R);
   D.f = d->f; D.f13 = d->f13; D.fm13 = d->fm13; D.lnf3 = d->lnf3; D.fm76 = d->fm76;
   D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev; D.sct = d->sct;
+  D.sctw = d->sctw; D.fw = d->fw; D.aw = d->aw; D.atw = d->atw; D.saw = d->saw; D.caw = d->caw;
+  D.zw = d->zw; D.dgw = d->dgw; D.ggw = d->ggw;
+  D.dg_scale = 1.0;
+  D.gg_scale = 1.0;
+}
+
+// Power of two above |x| (1 for zero or non-finite x): the double-word tables hold x / scale < 1.
+double pow2_above(double x) {
+  if (!(x > 0.0) || !std::isfinite(x)) return 1.0;
+  return std::ldexp(1.0, std::ilogb(x) + 1);
 }
 
 pe_status check_dets(const pe_detector* dets, int ndet, pe::DetSet* ds) {
@@ -201,10 +244,11 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->k0 = k0;
   d->nb = (int)nbins;
   const size_t nb = (size_t)nbins;
-  // doubles: f, f13, fm13, lnf3, fm76 (5 nb) + gg (3 nb) + psd_model (3 nb) + dd (3, padded);
-  // double2: sca, z (2 nb) + dg (3 nb)
-  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab;
-  const size_t bytes = n_d * sizeof(double) + n_d2 * sizeof(double2);
+  // double2: sincos table + sca, z (2 nb) + dg (3 nb); float4: double-word sincos table, zw (nb),
+  // dgw (3 nb); doubles: f, f13, fm13, lnf3, fm76 (5 nb) + gg (3 nb) + psd_model (3 nb) + dd (3,
+  // padded); float2: fw, aw, atw, saw, caw (5 nb) + ggw (3 nb)
+  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab, n_f4 = pe::kSinTab + 4 * nb, n_f2 = 8 * nb;
+  const size_t bytes = n_d2 * sizeof(double2) + n_f4 * sizeof(float4) + n_d * sizeof(double) + n_f2 * sizeof(float2);
   cudaError_t e = cudaMalloc(&d->mem, bytes);
   if (e != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ENOMEM, "cudaMalloc(%zu) failed", bytes); }
   double2* p2 = static_cast<double2*>(d->mem);
@@ -212,7 +256,11 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->sca = p2; p2 += nb;
   d->z = p2; p2 += nb;
   d->dg = p2; p2 += 3 * nb;
-  double* p = reinterpret_cast<double*>(p2);
+  float4* p4 = reinterpret_cast<float4*>(p2);
+  d->sctw = p4; p4 += pe::kSinTab;
+  d->zw = p4; p4 += nb;
+  d->dgw = p4; p4 += 3 * nb;
+  double* p = reinterpret_cast<double*>(p4);
   d->f = p; p += nb;
   d->f13 = p; p += nb;
   d->fm13 = p; p += nb;
@@ -220,7 +268,14 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->fm76 = p; p += nb;
   d->gg = p; p += 3 * nb;
   d->psd_model = p; p += 3 * nb;
-  d->dd_dev = p;
+  d->dd_dev = p; p += 8;
+  float2* pf = reinterpret_cast<float2*>(p);
+  d->fw = pf; pf += nb;
+  d->aw = pf; pf += nb;
+  d->atw = pf; pf += nb;
+  d->saw = pf; pf += nb;
+  d->caw = pf; pf += nb;
+  d->ggw = pf;
   fill_dev(d);
   const double L = det_arm_s(*cfg);
   if ((e = pe::launch_sincos_table(d->sct, 0)) != cudaSuccess ||
@@ -228,6 +283,8 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
           cudaSuccess ||
       (e = pe::launch_psd_model(d->f, d->nb, L, cfg->oms_m_rtHz, cfg->acc_ms2_rtHz, cfg->psd_shaping, cfg->tdi_gen,
                                 d->psd_model, 0)) != cudaSuccess ||
+      (e = pe::launch_dw_tables(d->f, d->sca, d->z, d->sct, d->nb, L, d->fw, d->aw, d->atw, d->saw, d->caw, d->zw,
+                                d->sctw, 0)) != cudaSuccess ||
       (e = cudaMemset(d->dd_dev, 0, 3 * sizeof(double))) != cudaSuccess ||
       (e = cudaDeviceSynchronize()) != cudaSuccess) {
     cudaGetLastError();
@@ -277,6 +334,25 @@ static pe_status set_data_device(pe_detector det, const double2* data_dev, const
   int hbad = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(det->dd, det->dd_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+  // double-word copies of the whitened tables for the mixed-precision path, scaled by powers of two
+  // near their maxima
+  double* mxp = nullptr;
+  const int n3 = 3 * nb;
+  if (e == cudaSuccess) e = cudaMalloc(&mxp, ((size_t)(n3 + pe::kTileBins - 1) / pe::kTileBins * 2 + 2) * sizeof(double));
+  double mx[2] = {0.0, 0.0};
+  if (e == cudaSuccess) {
+    double* out = mxp;
+    e = pe::launch_table_max(det->dg, det->gg, n3, mxp + 2, out, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(mx, out, 2 * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) {
+    det->dev.dg_scale = pow2_above(mx[0]);
+    det->dev.gg_scale = pow2_above(mx[1]);
+    e = pe::launch_dw_data(det->dg, det->gg, n3, 1.0 / det->dev.dg_scale, 1.0 / det->dev.gg_scale, det->dgw, det->ggw,
+                           0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (mxp) cudaFree(mxp);
   cudaFree(parts);
   cudaFree(bad);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(PE_ECUDA, "data tables: %s", cudaGetErrorString(e)); }
@@ -329,7 +405,7 @@ static pe_status signal_device(pe_detector det, const double* theta, unsigned mo
   ds.ndet = 1;
   ds.d[0] = det->dev;
   PE_CUDA(pe::launch_prep(th, 1, mode_mask, ds, coef, nend, status, st));
-  PE_CUDA(pe::launch_signal(det->dev, coef, out_dev, st));
+  PE_CUDA(pe::launch_signal(det->dev, coef, out_dev, pe::mask_mixed(mode_mask), st));
   int hs = 0;
   PE_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   PE_CUDA(cudaStreamSynchronize(st));
@@ -339,7 +415,7 @@ static pe_status signal_device(pe_detector det, const double* theta, unsigned mo
 
 pe_status pe_signal_aet(pe_detector det, const double* theta, unsigned mode_mask, double* out, void* stream) {
   if (det == nullptr || theta == nullptr || out == nullptr) return fail(PE_EINVAL, "det/theta/out is NULL");
-  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  if (!pe::fwd_mask_ok(mode_mask)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (is_device_ptr(out)) return signal_device(det, theta, mode_mask, reinterpret_cast<double2*>(out), st);
   double2* tmp = nullptr;
@@ -382,12 +458,12 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (s0 != PE_OK) return s0;
   if (theta == nullptr || out_logl == nullptr) return fail(PE_EINVAL, "theta/out_logl is NULL");
   if (B < 1 || B > (1 << 20)) return fail(PE_EINVAL, "B=%d outside [1, 2^20]", B);
-  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  if (!pe::fwd_mask_ok(mode_mask)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch sc(st);
   const int P = ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * ((ds.d[i].nb + pe::kTileBins - 1) / pe::kTileBins);
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kFwdTileBins);
   const double* th = theta;
   if (!is_device_ptr(theta)) {
     double* t = nullptr;
@@ -413,12 +489,13 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (h_dhhh) PE_CUDA(sc.alloc(&dhhh, (size_t)B * ndet * 6));
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep(th, B, mode_mask, ds, coef, nend, stat, st));
-  PE_CUDA(pe::launch_scan_tiles(nend, P, off, st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::kFwdTileBins, st));
   pe::TuneChoice tc = pe::default_choice();
   pe::lookup_tuned(ds, B, mode_mask, &tc);
   void* prof = nullptr;
   pe::profile_begin(st, &prof);
-  PE_CUDA(pe::launch_loglike_fwd_variant(tc.variant, ds, B, coef, nend, off, part, pe::grid_for(tc, max_tiles), st));
+  PE_CUDA(pe::launch_loglike_fwd_variant(tc.variant, pe::mask_mixed(mode_mask), ds, B, coef, nend, off, part,
+                                         pe::grid_for(tc, max_tiles), st));
   pe::profile_end(st, prof);
   PE_CUDA(pe::launch_reduce(ds, B, off, part, coef, logl, dhhh, st));
   if (h_logl) PE_CUDA(cudaMemcpyAsync(out_logl, logl, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -436,7 +513,8 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   if (s0 != PE_OK) return s0;
   if (theta == nullptr || out_grad == nullptr) return fail(PE_EINVAL, "theta/out_grad is NULL");
   if (B < 1 || B > (1 << 20)) return fail(PE_EINVAL, "B=%d outside [1, 2^20]", B);
-  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL))
+    return fail(PE_EINVAL, "bad mode mask 0x%x (the gradient is FP64 only)", mode_mask);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch sc(st);
   const int P = ndet * B;
@@ -470,7 +548,7 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   if (h_grad) PE_CUDA(sc.alloc(&grad, (size_t)B * PE_NPARAM));
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep_grad(th, B, mode_mask, ds, coef, sg, nend, stat, st));
-  PE_CUDA(pe::launch_scan_tiles(nend, P, off, st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::kTileBins, st));
   const long long g = std::min<long long>(max_tiles, (long long)sm_count() * pe::fwd_blocks_per_sm());
   void* prof = nullptr;
   pe::profile_begin(st, &prof);
@@ -520,7 +598,7 @@ pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int 
   double* F = out_F;
   if (h_F) PE_CUDA(sc.alloc(&F, (size_t)B * 121));
   PE_CUDA(pe::launch_prep_grad(th, B, mode_mask, ds, coef, sg, nend, nullptr, st));
-  PE_CUDA(pe::launch_scan_tiles(nend, P, off, st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::kTileBins, st));
   const long long g = std::min<long long>(max_tiles, (long long)sm_count() * 16);
   void* prof = nullptr;
   pe::profile_begin(st, &prof);

@@ -60,6 +60,12 @@ __device__ inline void sylm_pair(int l, int m, const T& iota, T* ypos, T* yneg) 
   }
 }
 
+// double -> double word (FP32 pair)
+__device__ __forceinline__ float2 to_dw(double a) {
+  const float h = __double2float_rn(a);
+  return make_float2(h, __double2float_rn(a - (double)h));
+}
+
 __device__ __constant__ static const int kModeL[kNModes] = {2, 2, 3, 3, 4};
 __device__ __constant__ static const int kModeM[kNModes] = {2, 1, 3, 2, 4};
 
@@ -118,6 +124,7 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   const T u[3] = {sl, -cl, 0.0 * sl};
   const T v[3] = {-(sb * cl), -(sb * sl), cb};
   for (int i = 0; i < 3; ++i) { S.p[i] = cp * u[i] + sp * v[i]; S.q[i] = -(sp * u[i]) + cp * v[i]; }
+  for (int i = 0; i < 3; ++i) { S.kw[i] = to_dw(val(S.k[i])); S.pw[i] = to_dw(val(S.p[i])); S.qw[i] = to_dw(val(S.q[i])); }
   // modes
   const T Fisco = 1.0 / (::pow(6.0, 1.5) * 2.0 * pi * M);
   for (int md = 0; md < kNModes; ++md) {
@@ -146,9 +153,15 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
     C.Pc = 0.5 * (sgn * yn - yp);
     C.fend = double(m) * Fisco;
     C.ftap = 0.9 * double(m) * Fisco;
+    C.Ppw = to_dw(val(C.Pp));
+    C.Pcw = to_dw(val(C.Pc));
     C.p = p;
     C.active = (valid && (mask & (1u << md)) && val(hmag) != 0.0) ? 1 : 0;
   }
+  const double a0 = val(S.md[0].amp);
+  const int e0 = (a0 > 0.0 && isfinite(a0)) ? ilogb(a0) : 0;
+  S.hsc = scalbn(1.0, -e0);
+  S.ihsc = scalbn(1.0, e0);
 }
 
 __device__ inline void sample_prep(const double* th, unsigned mask, SampleCoef& S) {
@@ -342,6 +355,17 @@ __device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, in
     mode_bin(D, S, C, B, a, tab);
   }
   xyz_final(a, B.z, acc);
+}
+
+// Adds one bin's PSD-weighted products to the running sums: v[c] += Re(dg_c B_c),
+// v[3+c] += gg_c |B_c|^2 (explicitly rounded, so every kernel that uses it adds identically).
+__device__ __forceinline__ void accum_bin(const DetDev& D, int b, const double2 o[3], double v[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double2 g = D.dg[c * D.nb + b];
+    v[c] = __dadd_rn(v[c], __fma_rn(g.x, o[c].x, -__dmul_rn(g.y, o[c].y)));
+    v[3 + c] = __dadd_rn(v[3 + c], __dmul_rn(D.gg[c * D.nb + b], __fma_rn(o[c].x, o[c].x, __dmul_rn(o[c].y, o[c].y))));
+  }
 }
 
 // A/E/T combinations (without Q n_c): B_A = Z' - X', B_E = X' - 2Y' + Z', B_T = X' + Y' + Z'.

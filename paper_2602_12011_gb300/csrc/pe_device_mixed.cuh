@@ -1,0 +1,207 @@
+// pe_device_mixed.cuh -- the (sample, mode, bin) unit of mode_bin (pe_device.cuh) with the
+// response geometry on the FP32 pipe in double-word arithmetic (pe_df.cuh, ~1e-14 relative).
+// GB300 issues FP32 at 64x its FP64 rate, so the FP64 pipe keeps only what needs FP64's range
+// and 53-bit precision: the TaylorF2 phase (up to ~1e6 rad) and t_f, the exact reduction of the
+// phase and the orbital angle to a fraction of a turn, and the likelihood accumulation across tiles.
+// Everything else -- the sines and cosines of the orbit, phase, third-spacecraft and sinc
+// arguments, the spacecraft offsets, unit link vectors, the projections k.n, n.e+.n, n.ex.n, the
+// sincs, the mode tensor factors, the TDI brackets, the A/E/T combinations and the PSD-weighted
+// per-bin products -- is double-word. Amplitudes enter multiplied by the sample's power of two hsc
+// (near 1/amp of the (2,2) mode) and the whitened data tables divided by powers of two near their
+// maxima, keeping every double word far from the FP32 overflow and underflow limits; the tile sums
+// are scaled back when they are converted to FP64.
+// Same definitions as mode_bin: arXiv:2602.12011 Sec. 2.1 (Eq. eq_tf, eq_fd_resp, FD TDI).
+#pragma once
+#include "pe_device.cuh"
+#include "pe_df.cuh"
+
+namespace pe {
+
+struct MixAcc {
+  df Pr[3], Pi[3], Qr[3], Qi[3];
+};
+__device__ __forceinline__ void mix_zero(MixAcc& a) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) a.Pr[i] = a.Pi[i] = a.Qr[i] = a.Qi[i] = df_make(0.f, 0.f);
+}
+// X' = P + z Q (times hsc), double words
+__device__ __forceinline__ void mix_final(const MixAcc& a, const cdf& z, cdf x[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const cdf zq = cdf_mul(z, cdf{a.Qr[i], a.Qi[i]});
+    x[i].re = df_add_s(a.Pr[i], zq.re);
+    x[i].im = df_add_s(a.Pi[i], zq.im);
+  }
+}
+
+// Per-bin double words: f, a = pi f L, a / (2 pi), sin a, cos a.
+struct BinW {
+  df f, a, at, sa, ca;
+};
+__device__ __forceinline__ void load_bin_w(const DetDev& D, int b, BinW& W) {
+  W.f = D.fw[b];
+  W.a = D.aw[b];
+  W.at = D.atw[b];
+  W.sa = D.saw[b];
+  W.ca = D.caw[b];
+}
+
+// sinc(u) for |u| < 1e-3: 1 + u^2 (-1/6 + u^2/120) (the u^2/120 term enters the low word of -1/6;
+// the dropped u^6/5040 is below 2e-22)
+__device__ __forceinline__ df df_sinc_small(df u) {
+  const df u2 = df_mul(u, u);
+  const df p = df_make(-0.166666672f, __fmaf_rn(u2.x, 1.0f / 120.0f, 4.96705388e-09f));
+  return df_add_s(df_make(1.f, 0.f), df_mul(u2, p));
+}
+
+__device__ __forceinline__ df dw_dot3(const df a[3], const df b[3]) {
+  return df_add_s(df_add_s(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+}
+
+// double -> double word of the fraction x - rint(x) (exact in FP64), for the sincos of a turn count
+__device__ __forceinline__ df frac_dw(double x) { return df_from(x - rint(x)); }
+
+__device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
+                                               const BinW& W, MixAcc& acc, const float4* __restrict__ tab) {
+  // --- waveform and time-frequency map (FP64; rows A2, A3)
+  const double v = C.cm * B.f13;
+  const double iv = C.icm * B.fm13;
+  const double lnv = C.lncm + B.lnf3;
+  double iv5 = iv * iv;
+  iv5 = iv5 * iv5 * iv;
+  double poly = S.P[7];
+  double dpol = 2.0 * S.P[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) {
+    poly = fma(poly, v, S.P[k]);
+    dpol = fma(dpol, v, S.Pd[k]);
+  }
+  const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
+  const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
+  const double tf = fma(C.tffac * B.invf, dv, S.tc);
+  double w = 1.0;
+  if (B.f > C.ftap) {
+    const double span = C.fend - C.ftap;
+    const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
+    w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
+  }
+  double amp = C.amp * S.hsc * B.fm76 * w;
+  if (C.p >= 1) amp *= v;
+  if (C.p >= 2) amp *= v;
+  // --- orbital angle alpha(t_f) (row A4), centre Doppler f k.x_c, x_c = R (cos a, sin a, 0)
+  const cdf eo = df_cis_turns(frac_dw(fma(tf, D.rate_t, D.alpha0_t)), tab);
+  const df co = eo.re, so = eo.im;
+  const df kxc = df_mul(D.Rw, df_add_s(df_mul(S.kw[0], co), df_mul(S.kw[1], so)));
+  const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - df_to(df_mul(W.f, kxc));
+  const cdf eph = df_cis_turns(frac_dw(ph), tab);
+  const df A = df_from(amp);
+  const cdf H = {df_mul(A, eph.re), df_mul(A, eph.im)};
+  // --- spacecraft offsets: dl[i][j] = oA U_j + oB V_j + oC
+  df Uc[3], Vc[3];
+  if (D.orbit == 0) {
+    Uc[0] = Uc[1] = df_sub_s(df_mul(co, co), df_mul(so, so));
+    Vc[0] = Vc[1] = df_scale2(df_mul(so, co), 2.0f);
+    Uc[2] = co;
+    Vc[2] = so;
+  } else {
+    const cdf e0 = df_cis_turns(frac_dw(tf * D.geo_rate_t), tab);
+    Uc[0] = Uc[1] = Uc[2] = e0.re;
+    Vc[0] = Vc[1] = Vc[2] = e0.im;
+  }
+  df dl[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      dl[i][j] = df_add_s(df_add_s(df_mul(D.oA[i][j], Uc[j]), df_mul(D.oB[i][j], Vc[j])), D.oC[i][j]);
+  // --- third-spacecraft phases e^{i pi f k.delta_t} (E_2 = conj(E_0 E_1))
+  cdf E[3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const df kd = dw_dot3(S.kw, dl[i]);
+    E[i] = df_cis_turns(df_scale2(df_mul(W.f, kd), 0.5f), tab);
+  }
+  {
+    const cdf e01 = cdf_mul(E[0], E[1]);
+    E[2].re = e01.re;
+    E[2].im = df_make(-e01.im.x, -e01.im.y);
+  }
+  // --- links (row A5); the loop stays rolled (one copy of its body) for the instruction cache
+  cdf G[3];
+  df smv[3], spv[3];
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    const int r = l, s = (l + 1) % 3, t = (l + 2) % 3;
+    df n[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n[j] = df_sub_s(dl[r][j], dl[s][j]);
+    const df inv = df_rsqrt(dw_dot3(n, n));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n[j] = df_mul(n[j], inv);
+    const df kn = dw_dot3(S.kw, n);
+    const df np = dw_dot3(S.pw, n);
+    const df nq = dw_dot3(S.qw, n);
+    const df Fp = df_sub_s(df_mul(np, np), df_mul(nq, nq));
+    const df Fc = df_scale2(df_mul(np, nq), 2.0f);
+    const cdf gam = {df_mul(C.Ppw, Fp), df_mul(C.Pcw, Fc)};
+    G[l] = cdf_mul(E[t], cdf_mul(gam, H));
+    // sinc(a(1 -+ kn)) from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
+    const cdf ea = df_cis_turns(df_mul(W.at, kn), tab);
+    const df sak = ea.im, cak = ea.re;
+    const df akn = df_mul(W.a, kn);
+    const df u1 = df_sub_s(W.a, akn), u2 = df_add_s(W.a, akn);
+    const df x1 = df_mul(W.sa, cak), x2 = df_mul(W.ca, sak);
+    const df s1 = df_sub_s(x1, x2), s2 = df_add_s(x1, x2);
+    const bool small1 = fabsf(u1.x) < 1e-3f, small2 = fabsf(u2.x) < 1e-3f;
+    if (!small1 && !small2) {
+      const df rr = df_rcp(df_mul(u1, u2));
+      smv[l] = df_mul(df_mul(s1, u2), rr);
+      spv[l] = df_mul(df_mul(s2, u1), rr);
+    } else {
+      smv[l] = small1 ? df_sinc_small(u1) : df_mul(s1, df_rcp(u1));
+      spv[l] = small2 ? df_sinc_small(u2) : df_mul(s2, df_rcp(u2));
+    }
+  }
+  // --- TDI brackets (row A6): P_c += G_lp s+_lp - G_lu s-_lu, Q_c += G_lp s-_lp - G_lu s+_lu
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lp = (c + 2) % 3, lu = c;
+    acc.Pr[c] = df_add_s(acc.Pr[c], df_sub_s(df_mul(G[lp].re, spv[lp]), df_mul(G[lu].re, smv[lu])));
+    acc.Pi[c] = df_add_s(acc.Pi[c], df_sub_s(df_mul(G[lp].im, spv[lp]), df_mul(G[lu].im, smv[lu])));
+    acc.Qr[c] = df_add_s(acc.Qr[c], df_sub_s(df_mul(G[lp].re, smv[lp]), df_mul(G[lu].re, spv[lu])));
+    acc.Qi[c] = df_add_s(acc.Qi[c], df_sub_s(df_mul(G[lp].im, smv[lp]), df_mul(G[lu].im, spv[lu])));
+  }
+}
+
+// Mode-summed TDI brackets X', Y', Z' of one sample at one bin times the sample's hsc, mixed
+// precision.
+__device__ __forceinline__ void bin_xyz_mixed(const DetDev& D, const SampleCoef& S, int b, cdf x[3],
+                                              const float4* __restrict__ tab) {
+  BinIn B;
+  load_bin(D, b, S.tc, B);
+  BinW W;
+  load_bin_w(D, b, W);
+  MixAcc a;
+  mix_zero(a);
+#pragma unroll 1
+  for (int md = 0; md < kNModes; ++md) {
+    const ModeCoef& C = S.md[md];
+    if (!C.active || !(B.f < C.fend)) continue;
+    mode_bin_mixed(D, S, C, B, W, a, tab);
+  }
+  const float4 zz = D.zw[b];
+  mix_final(a, cdf{df_make(zz.x, zz.y), df_make(zz.z, zz.w)}, x);
+}
+
+// A/E/T combinations (without Q n_c) in double words: B_A = Z' - X', B_E = X' - 2Y' + Z',
+// B_T = X' + Y' + Z'.
+__device__ __forceinline__ void aet_from_xyz_dw(const cdf x[3], cdf o[3]) {
+  o[0].re = df_sub_s(x[2].re, x[0].re);
+  o[0].im = df_sub_s(x[2].im, x[0].im);
+  o[1].re = df_sub_s(df_add_s(x[0].re, x[2].re), df_scale2(x[1].re, 2.0f));
+  o[1].im = df_sub_s(df_add_s(x[0].im, x[2].im), df_scale2(x[1].im, 2.0f));
+  o[2].re = df_add_s(df_add_s(x[0].re, x[1].re), x[2].re);
+  o[2].im = df_add_s(df_add_s(x[0].im, x[1].im), x[2].im);
+}
+
+}  // namespace pe

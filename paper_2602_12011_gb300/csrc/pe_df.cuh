@@ -1,0 +1,141 @@
+// pe_df.cuh -- double-word ("double-float") arithmetic on the FP32 pipe: a value is the unevaluated
+// sum hi + lo of two floats with |lo| <= ulp(hi)/2, about 48 significant bits (relative error of the
+// operations below ~1e-14). Error-free transformations: TwoSum (Knuth, TAOCP 4.2.2), Fast2Sum
+// (Dekker 1971), TwoProd by FMA; double-word addition and multiplication after Joldes, Muller and
+// Popescu, "Tight and rigorous error bounds for basic building blocks of double-word arithmetic"
+// (ACM TOMS 2017), Algorithms 6 (accurate DW + DW) and 12 (DW x DW with FMA). Every float operation
+// of the transformations is an explicitly rounded intrinsic, so the compiler cannot contract them.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pe_internal.h"
+
+namespace pe {
+
+using df = float2;  // (hi, lo)
+
+__device__ __forceinline__ df df_make(float h, float l) { return make_float2(h, l); }
+
+// s + e = a + b exactly
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+  return df_make(s, e);
+}
+// s + e = a + b exactly when |a| >= |b| (or a == 0)
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return df_make(s, e);
+}
+
+// accurate DW + DW (Alg. 6): relative error <= 3 u^2 + 13 u^3
+__device__ __forceinline__ df df_add(df x, df y) {
+  const df s = two_sum(x.x, y.x);
+  const df t = two_sum(x.y, y.y);
+  const float c = __fadd_rn(s.y, t.x);
+  const df v = fast_two_sum(s.x, c);
+  const float w = __fadd_rn(t.y, v.y);
+  return fast_two_sum(v.x, w);
+}
+// "sloppy" DW + DW (the same paper's Alg. 5): only x.lo + y.lo and the carry are rounded, so the
+// absolute error stays below ~2 u^2 (|x| + |y|). Its relative error is unbounded under
+// cancellation, but there the operands' own rounding errors (~u^2 of their size) are as large; it
+// is the add of the hot loops, where every operand is itself a rounded result.
+__device__ __forceinline__ df df_add_s(df x, df y) {
+  const df s = two_sum(x.x, y.x);
+  const float v = __fadd_rn(x.y, y.y);
+  const float w = __fadd_rn(s.y, v);
+  return fast_two_sum(s.x, w);
+}
+__device__ __forceinline__ df df_sub_s(df x, df y) { return df_add_s(x, make_float2(-y.x, -y.y)); }
+__device__ __forceinline__ df df_neg(df x) { return df_make(-x.x, -x.y); }
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+
+// DW x DW with FMA (Alg. 12): relative error <= 4 u^2
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float ch = __fmul_rn(x.x, y.x);
+  const float cl1 = __fmaf_rn(x.x, y.x, -ch);
+  const float tl0 = __fmul_rn(x.y, y.y);
+  const float tl1 = __fmaf_rn(x.x, y.y, tl0);
+  const float cl2 = __fmaf_rn(x.y, y.x, tl1);
+  const float cl3 = __fadd_rn(cl1, cl2);
+  return fast_two_sum(ch, cl3);
+}
+// DW x float
+__device__ __forceinline__ df df_mulf(df x, float y) {
+  const float ch = __fmul_rn(x.x, y);
+  const float cl1 = __fmaf_rn(x.x, y, -ch);
+  const float cl3 = __fmaf_rn(x.y, y, cl1);
+  return fast_two_sum(ch, cl3);
+}
+// multiplication by a power of two is exact
+__device__ __forceinline__ df df_scale2(df x, float p2) { return df_make(x.x * p2, x.y * p2); }
+
+__device__ __forceinline__ df df_from(double a) {
+  const float h = __double2float_rn(a);
+  return df_make(h, __double2float_rn(a - (double)h));
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.x + (double)a.y; }
+
+// 1/x: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0) (error delta^2)
+__device__ __forceinline__ df df_rcp(df x) {
+  const float y0 = __frcp_rn(x.x);
+  const df e = df_sub(df_make(1.f, 0.f), df_mulf(x, y0));
+  return df_add(df_make(y0, 0.f), df_mulf(e, y0));
+}
+// 1/sqrt(x), x > 0: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0^2)/2
+// (relative error (3/2) delta^2 for a seed error delta <= u, plus the DW rounding)
+__device__ __forceinline__ df df_rsqrt(df x) {
+  const float y0 = __frsqrt_rn(x.x);
+  const df xy2 = df_mulf(df_mulf(x, y0), y0);
+  const df e = df_sub(df_make(1.f, 0.f), xy2);
+  return df_add(df_make(y0, 0.f), df_mulf(df_scale2(e, 0.5f), y0));
+}
+
+// complex DW numbers as pairs (re, im)
+struct cdf {
+  df re, im;
+};
+__device__ __forceinline__ cdf cdf_mul(const cdf& a, const cdf& b) {
+  cdf r;
+  r.re = df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im));
+  r.im = df_add(df_mul(a.re, b.im), df_mul(a.im, b.re));
+  return r;
+}
+
+// e^{2 pi i x} = (cos, sin)(2 pi x) for x in turns (|x| < 2^20). The reduction is exact: x.hi - rint(x.hi) and
+// the step to the nearest table angle 2 pi j/kSinTab are Sterbenz subtractions, and the low word
+// joins by Fast2Sum (the reduced high word is a multiple of ulp(x.hi) or zero). The remainder
+// t = 2 pi d (|t| <= pi/kSinTab) goes through sin t = t + t t^2 (-1/6 + t^2/120) and
+// cos t = 1 + t^2 (-1/2 + t^2/24); the t^2/120 and t^2/24 corrections enter the low words of the
+// double-word coefficients (their rounding is below 1e-18 of the result, the dropped t^7 and t^6
+// terms below 2e-18). tab[j] = (cos hi, cos lo, sin hi, sin lo) of 2 pi j/kSinTab. Not inlined: the
+// mixed unit calls it from five places, and one copy keeps the kernel's hot loop in the
+// instruction cache.
+__device__ __noinline__ cdf df_cis_turns(df x, const float4* __restrict__ tab) {
+  // round to nearest integer by adding and subtracting 1.5 * 2^23 (exact for |v| < 2^22), on the
+  // FP32 pipe; the table index is read from the biased sum's bits
+  const float kR = 12582912.0f;
+  const float rh = __fsub_rn(x.x, __fsub_rn(__fadd_rn(x.x, kR), kR));
+  const float y = __fmul_rn(rh, (float)kSinTab);
+  const float yb = __fadd_rn(y, kR);
+  const int j = __float_as_int(yb) - __float_as_int(kR);
+  const df d = fast_two_sum(__fsub_rn(rh, __fmul_rn(__fsub_rn(yb, kR), 1.0f / kSinTab)), x.y);
+  const float4 e = tab[j & (kSinTab - 1)];
+  const df cj = df_make(e.x, e.y), sj = df_make(e.z, e.w);
+  const df t = df_mul(d, df_make(6.28318548202514648f, -1.74845553e-07f));   // 2 pi as a double word
+  const df t2 = df_mul(t, t);
+  // -1/6 = -0.166666672 + 4.96705388e-09 and -1/2, with the next Taylor terms folded into the lows
+  const df ps = df_make(-0.166666672f, __fmaf_rn(t2.x, 1.0f / 120.0f, 4.96705388e-09f));
+  const df pc = df_make(-0.5f, __fmul_rn(t2.x, 1.0f / 24.0f));
+  const df st = df_add_s(t, df_mul(t, df_mul(t2, ps)));
+  const df ct = df_add_s(df_make(1.f, 0.f), df_mul(t2, pc));
+  cdf r;
+  r.re = df_sub_s(df_mul(cj, ct), df_mul(sj, st));
+  r.im = df_add_s(df_mul(sj, ct), df_mul(cj, st));
+  return r;
+}
+
+}  // namespace pe

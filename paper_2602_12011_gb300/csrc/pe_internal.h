@@ -19,8 +19,9 @@ constexpr double kEulerGamma = 0.57721566490153286061;
 
 constexpr int kNModes = 5;      // (2,2) (2,1) (3,3) (3,2) (4,4)
 constexpr int kMaxDet = 8;
-constexpr int kTileBins = 128;
-constexpr int kSinTab = 1024;   // entries of the (cos, sin) table used by sincos_turns  // frequency bins per work tile = threads per CTA of the hot kernels
+constexpr int kTileBins = 128;  // frequency bins per work tile = threads per CTA of the hot kernels
+constexpr int kFwdTileBins = 512;  // bins per work tile of the log-likelihood kernels (4 per thread)
+constexpr int kSinTab = 1024;   // entries of the (cos, sin) table used by sincos_turns
 
 // Per-(sample, mode) coefficients (row A1 of the path). With v = (2 pi M f/m)^(1/3):
 //   v = cm f^(1/3), 1/v = icm f^(-1/3), ln v = lncm + ln(f)/3,
@@ -38,6 +39,7 @@ struct ModeCoefT {
   T tffac;      // m / (12 pi)
   T Pp, Pc;
   T fend, ftap;
+  float2 Ppw, Pcw;   // Pp, Pc as double words (FP32 pairs) for the mixed-precision path
   int p;        // power of v in |H_lm|: 0 (22), 1 (21, 33), 2 (32, 44)
   int active;   // 1 if the mode is in the mask and its amplitude is non-zero
 };
@@ -51,6 +53,10 @@ struct SampleCoefT {
   T Pd[8];              // (k - 5) P[k]: coefficients of v dPsi_PN/dv
   T Q5, Q6;
   T k[3], p[3], q[3];   // propagation direction and polarisation frame
+  float2 kw[3], pw[3], qw[3];   // the same as double words
+  double hsc, ihsc;     // power of two near 1/amp of the (2,2) mode and its inverse: the mixed-
+                        // precision path carries amplitudes times hsc, keeping them far from the
+                        // FP32 range limits
   ModeCoefT<T> md[kNModes];
   int valid;
   int pad_;
@@ -108,6 +114,22 @@ struct DetDev {
   const double* gg;     // [3][nb]: w_c |Q|^2 n_c^2
   const double* dd;     // [3]: <d|d>_c
   const double2* sct;   // [kSinTab]: (cos, sin)(2 pi j / kSinTab), the sincos table
+  const float4* sctw;   // [kSinTab]: the same as double words (cos hi, cos lo, sin hi, sin lo)
+  // mixed-precision path: per-bin double words of f, a = pi f L, a/(2 pi), sin a, cos a
+  const float2* fw;
+  const float2* aw;
+  const float2* atw;
+  const float2* saw;
+  const float2* caw;
+  const float4* zw;     // z as (re hi, re lo, im hi, im lo)
+  const float4* dgw;    // [3][nb]: dg / dg_scale as (re hi, re lo, im hi, im lo)
+  const float2* ggw;    // [3][nb]: gg / gg_scale
+  double dg_scale, gg_scale;   // powers of two near max|dg|, max gg (keep the double words in range)
+  // orbit offsets as double words: dl[i][j] = oA[i][j] U_j + oB[i][j] V_j + oC[i][j], with
+  // (U, V) = (cos 2alpha, sin 2alpha) for j = 0, 1 and (cos alpha, sin alpha) for j = 2
+  // (heliocentric), (cos phi_0, sin phi_0) for every j (geocentric, oC = 0)
+  float2 oA[3][3], oB[3][3], oC[3][3];
+  float2 Rw;            // R as a double word
   // Q = TDI factor(z) (-i a) e^{-i a}; n_A = 1/sqrt2, n_E = 1/sqrt6, n_T = 1/sqrt3
 };
 

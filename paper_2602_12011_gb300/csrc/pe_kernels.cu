@@ -5,14 +5,17 @@
 //   k_sum_parts      fixed-order sum of per-block partials (used for <d|d>)
 //   k_prep           row A1: per-sample coefficients and active bin counts per detector
 //   k_scan_tiles     tile offsets of the uneven (detector, sample) work list
+//   k_dw_tables      row A0: double-word copies of the per-bin and sincos tables (mixed path)
 //   k_loglike_fwd    rows A2-A7: persistent fused waveform -> t_f -> orbit -> links -> TDI ->
-//                    A/E/T -> PSD-weighted sums, one fixed-order partial per tile
+//                    A/E/T -> PSD-weighted sums, one fixed-order partial per tile (FP64 or
+//                    mixed FP64/double-word precision)
 //   k_reduce         row A7: fixed-order sums of the partials -> <d|h>, <h|h>, logL
 //   k_signal         noise-free A/E/T signal on the grid (per-bin output)
 //   k_inject         data = signal + noise scaled by the PSD (Eq. eq_diag_Sigma_to_Sn)
 #include <cuda_runtime.h>
 
 #include "pe_device.cuh"
+#include "pe_device_mixed.cuh"
 #include "pe_kernels.h"
 
 namespace pe {
@@ -46,6 +49,74 @@ __global__ void k_sincos_table(double2* tab) {
   double s, c;
   sincospi(double(j) / (kSinTab / 2), &s, &c);
   tab[j] = make_double2(c, s);
+}
+
+// Double words of the mixed-precision path: per bin f, a = pi f L, a/(2 pi), sin a, cos a (from
+// the FP64 tables), and the sincos table as (cos hi, cos lo, sin hi, sin lo).
+__device__ __forceinline__ float2 dw_of(double a) {
+  const float h = __double2float_rn(a);
+  return make_float2(h, __double2float_rn(a - (double)h));
+}
+__global__ void k_dw_tables(const double* f, const double2* sca, const double2* z, const double2* tab, int nb, double L,
+                            float2* fw, float2* aw, float2* atw, float2* saw, float2* caw, float4* zw, float4* tabw) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < kSinTab) {
+    const float2 c = dw_of(tab[b].x), s = dw_of(tab[b].y);
+    tabw[b] = make_float4(c.x, c.y, s.x, s.y);
+  }
+  if (b >= nb) return;
+  fw[b] = dw_of(f[b]);
+  aw[b] = dw_of(kPi * f[b] * L);
+  atw[b] = dw_of(0.5 * f[b] * L);
+  saw[b] = dw_of(sca[b].x);
+  caw[b] = dw_of(sca[b].y);
+  const float2 zr = dw_of(z[b].x), zi = dw_of(z[b].y);
+  zw[b] = make_float4(zr.x, zr.y, zi.x, zi.y);
+}
+
+// Largest |Re dg|, |Im dg| and gg of the whitened tables: per-block maxima (mx_part[block][2]),
+// then one warp over the blocks (out[2]).
+__global__ void k_table_max(const double2* dg, const double* gg, int n, double* mx_part) {
+  __shared__ double red[2][kTileBins];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double a = 0.0, g = 0.0;
+  if (i < n) {
+    a = fmax(fabs(dg[i].x), fabs(dg[i].y));
+    g = fabs(gg[i]);
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = g;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + s]);
+      red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    mx_part[blockIdx.x * 2 + 0] = red[0][0];
+    mx_part[blockIdx.x * 2 + 1] = red[1][0];
+  }
+}
+__global__ void k_max_parts(const double* part, int n, double* out) {
+  for (int c = 0; c < 2; ++c) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) m = fmax(m, part[i * 2 + c]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) out[c] = m;
+  }
+}
+
+// Double-word copies of the whitened tables divided by the power-of-two scales: dgw [3][nb] as
+// (re hi, re lo, im hi, im lo), ggw [3][nb].
+__global__ void k_dw_data(const double2* dg, const double* gg, int n, double inv_dgs, double inv_ggs, float4* dgw,
+                          float2* ggw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 r = dw_of(dg[i].x * inv_dgs), m = dw_of(dg[i].y * inv_dgs);
+  dgw[i] = make_float4(r.x, r.y, m.x, m.y);
+  ggw[i] = dw_of(gg[i] * inv_ggs);
 }
 
 // Analytic PSD (acceleration + OMS noise only): equal-arm TDI-1.5 A/E/T spectra
@@ -171,14 +242,16 @@ __global__ void k_prep(const double* theta, int B, unsigned mask, DetSet ds, Sam
   if (status) status[s] = S.valid ? 0 : 1;
 }
 
-// Exclusive prefix sum of tiles per (detector, sample) pair; off[P] = total tiles. One CTA.
+// Exclusive prefix sum of tiles (TILE bins each) per (detector, sample) pair; off[P] = total tiles.
+// One CTA.
+template <int TILE>
 __global__ void k_scan_tiles(const int* nend, int P, long long* off) {
   __shared__ long long part[1024];
   const int t = threadIdx.x;
   const int chunk = (P + blockDim.x - 1) / blockDim.x;
   const int lo = t * chunk, hi = min(P, lo + chunk);
   long long s = 0;
-  for (int i = lo; i < hi; ++i) s += (nend[i] + kTileBins - 1) / kTileBins;
+  for (int i = lo; i < hi; ++i) s += (nend[i] + TILE - 1) / TILE;
   part[t] = s;
   __syncthreads();
   if (t == 0) {
@@ -188,7 +261,7 @@ __global__ void k_scan_tiles(const int* nend, int P, long long* off) {
   }
   __syncthreads();
   long long run = part[t];
-  for (int i = lo; i < hi; ++i) { off[i] = run; run += (nend[i] + kTileBins - 1) / kTileBins; }
+  for (int i = lo; i < hi; ++i) { off[i] = run; run += (nend[i] + TILE - 1) / TILE; }
 }
 
 // pair index p with off[p] <= t < off[p+1]
@@ -223,45 +296,105 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins /
 }
 
 // ------------------------------------------------------------------------------------------
-// Rows A2-A7: persistent fused kernel. Work item = one tile of kTileBins bins of one
-// (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns one bin,
-// sums the modes' TDI brackets in registers, forms A/E/T and the weighted products; the tile's
-// six sums (<d|h>_c, <h|h>_c) go to part[tile][6]. MINB (resident CTAs per SM requested from
-// the compiler) sets the register budget only; every variant does the same arithmetic in the
-// same order, so the autotuner's choice never changes a result.
+// Rows A2-A7: persistent fused kernel. Work item = one tile of kFwdTileBins bins of one
+// (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns every
+// kTileBins-th bin of the tile (coalesced), sums the modes' TDI brackets in registers, forms A/E/T
+// and the weighted products and adds them up; the tile's six sums (<d|h>_c, <h|h>_c) go to
+// part[tile][6]. MINB (resident CTAs per SM requested from
+// the compiler) sets the register budget only; every variant of one precision does the same
+// arithmetic in the same order, so the autotuner's choice never changes a result. MIXED selects
+// the mixed FP64/double-word unit (pe_device_mixed.cuh) over the all-FP64 one.
 // ------------------------------------------------------------------------------------------
-template <int MINB>
+// Block reduction of NV double words per thread (accurate double-word adds, fixed tree order);
+// result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_dw(df v[NV], float2 (*sh)[kTileBins / 32]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o > 0; o >>= 1) {
+      const df u = df_make(__shfl_down_sync(0xffffffffu, v[i].x, o), __shfl_down_sync(0xffffffffu, v[i].y, o));
+      v[i] = df_add(v[i], u);
+    }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[i][wid] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      df s = sh[i][0];
+      for (int w = 1; w < kTileBins / 32; ++w) s = df_add(s, sh[i][w]);
+      v[i] = s;
+    }
+}
+
+template <int MINB, bool MIXED>
 __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                                  const int* __restrict__ nend,
                                                                  const long long* __restrict__ off, double* part) {
   __shared__ double sh[6][kTileBins / 32];
-  __shared__ double2 stab[kSinTab];
-  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  __shared__ double2 stab[kSinTab];   // the detector set's sincos table (as float4 double words if MIXED)
+  if (MIXED) {
+    float4* t4 = reinterpret_cast<float4*>(stab);
+    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) t4[i] = ds.d[0].sctw[i];
+  } else {
+    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  }
   __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair(off, P, t);
     const int I = p / B, s = p - I * B;
-    const int b = int(t - off[p]) * kTileBins + threadIdx.x;
+    const int b0 = int(t - off[p]) * kFwdTileBins + threadIdx.x;
+    const int ne = nend[p];
     const DetDev& D = ds.d[I];
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (b < nend[p]) {
-      const SampleCoef& S = coef[s];
-      double2 x[3], o[3];
-      bin_xyz(D, S, b, x, stab);
-      aet_from_xyz(x, o);
+    const SampleCoef& S = coef[s];
+    if (MIXED) {
+      // per bin in double words, times hsc (h) and 1/dg_scale, 1/gg_scale (tables); the tile sums
+      // are scaled back in FP64
+      df v[6];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double2 g = D.dg[c * D.nb + b];
-        v[c] = g.x * o[c].x - g.y * o[c].y;                        // Re(dg_c B_c)
-        v[3 + c] = D.gg[c * D.nb + b] * (o[c].x * o[c].x + o[c].y * o[c].y);
+      for (int i = 0; i < 6; ++i) v[i] = df_make(0.f, 0.f);
+#pragma unroll 1
+      for (int b = b0; b < b0 + kFwdTileBins && b < ne; b += kTileBins) {
+        cdf x[3], o[3];
+        bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab));
+        aet_from_xyz_dw(x, o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float4 g = D.dgw[c * D.nb + b];
+          v[c] = df_add_s(v[c], df_sub_s(df_mul(df_make(g.x, g.y), o[c].re), df_mul(df_make(g.z, g.w), o[c].im)));
+          const df m2 = df_add_s(df_mul(o[c].re, o[c].re), df_mul(o[c].im, o[c].im));
+          v[3 + c] = df_add_s(v[3 + c], df_mul(D.ggw[c * D.nb + b], m2));
+        }
       }
-    }
-    block_sum<6>(v, sh);
-    if (threadIdx.x == 0)
+      block_sum_dw<6>(v, reinterpret_cast<float2(*)[kTileBins / 32]>(sh));
+      if (threadIdx.x == 0) {
+        const double ih = S.ihsc;
+        const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) part[t * 6 + i] = v[i];
+        for (int c = 0; c < 3; ++c) {
+          part[t * 6 + c] = df_to(v[c]) * sd;
+          part[t * 6 + 3 + c] = df_to(v[3 + c]) * sg;
+        }
+      }
+    } else {
+      double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 1
+      for (int b = b0; b < b0 + kFwdTileBins && b < ne; b += kTileBins) {
+        double2 x[3], o[3];
+        bin_xyz(D, S, b, x, stab);
+        aet_from_xyz(x, o);
+        accum_bin(D, b, o, v);
+      }
+      block_sum<6>(v, sh);
+      if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) part[t * 6 + i] = v[i];
+    }
   }
 }
 
@@ -300,12 +433,19 @@ __global__ void k_reduce(DetSet ds, int B, const long long* off, const double* p
 }
 
 // Noise-free A/E/T signal of one sample on the whole grid: h_c = Q n_c B_c. out: [3][nb].
+template <bool MIXED>
 __global__ void k_signal(DetDev D, const SampleCoef* coef, double2* out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= D.nb) return;
   const SampleCoef& S = coef[0];
   double2 x[3], o[3];
-  bin_xyz(D, S, b, x, D.sct);
+  if (MIXED) {
+    cdf xw[3];
+    bin_xyz_mixed(D, S, b, xw, D.sctw);
+    for (int i = 0; i < 3; ++i) x[i] = make_double2(df_to(xw[i].re) * S.ihsc, df_to(xw[i].im) * S.ihsc);
+  } else {
+    bin_xyz(D, S, b, x, D.sct);
+  }
   aet_from_xyz(x, o);
   const double2 Q = transfer_q(kPi * D.f[b] * D.L, D.sca[b], D.z[b], D.tdi_gen);
   for (int c = 0; c < 3; ++c) out[c * D.nb + b] = cscale(cmul(Q, o[c]), kChanNorm[c]);
@@ -354,32 +494,61 @@ cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet&
   k_prep<<<(B + 63) / 64, 64, 0, st>>>(theta, B, mask, ds, coef, nend, status);
   return cudaGetLastError();
 }
-cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, cudaStream_t st) {
-  k_scan_tiles<<<1, 1024, 0, st>>>(nend, P, off);
+cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st) {
+  if (tile_bins == kTileBins)
+    k_scan_tiles<kTileBins><<<1, 1024, 0, st>>>(nend, P, off);
+  else if (tile_bins == kFwdTileBins)
+    k_scan_tiles<kFwdTileBins><<<1, 1024, 0, st>>>(nend, P, off);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_tables(const double* f, const double2* sca, const double2* z, const double2* tab, int nb,
+                             double L, float2* fw, float2* aw, float2* atw, float2* saw, float2* caw, float4* zw,
+                             float4* tabw, cudaStream_t st) {
+  const int n = nb > kSinTab ? nb : kSinTab;
+  k_dw_tables<<<(n + 127) / 128, 128, 0, st>>>(f, sca, z, tab, nb, L, fw, aw, atw, saw, caw, zw, tabw);
+  return cudaGetLastError();
+}
+cudaError_t launch_table_max(const double2* dg, const double* gg, int n, double* mx_part, double* out, cudaStream_t st) {
+  const int g = (n + kTileBins - 1) / kTileBins;
+  k_table_max<<<g, kTileBins, 0, st>>>(dg, gg, n, mx_part);
+  k_max_parts<<<1, 32, 0, st>>>(mx_part, g, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_data(const double2* dg, const double* gg, int n, double inv_dgs, double inv_ggs, float4* dgw,
+                           float2* ggw, cudaStream_t st) {
+  k_dw_data<<<(n + 127) / 128, 128, 0, st>>>(dg, gg, n, inv_dgs, inv_ggs, dgw, ggw);
   return cudaGetLastError();
 }
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
-                               double* part, int grid, cudaStream_t st) {
-  return launch_loglike_fwd_variant(kFwdDefaultVariant, ds, B, coef, nend, off, part, grid, st);
+                               double* part, int grid, bool mixed, cudaStream_t st) {
+  return launch_loglike_fwd_variant(kFwdDefaultVariant, mixed, ds, B, coef, nend, off, part, grid, st);
 }
-cudaError_t launch_loglike_fwd_variant(int variant, const DetSet& ds, int B, const SampleCoef* coef, const int* nend,
-                                       const long long* off, double* part, int grid, cudaStream_t st) {
-  switch (variant) {
-    case 0: k_loglike_fwd<2><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    case 1: k_loglike_fwd<3><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    case 2: k_loglike_fwd<4><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+cudaError_t launch_loglike_fwd_variant(int variant, bool mixed, const DetSet& ds, int B, const SampleCoef* coef,
+                                       const int* nend, const long long* off, double* part, int grid, cudaStream_t st) {
+  switch (variant * 2 + (mixed ? 1 : 0)) {
+    case 0: k_loglike_fwd<2, false><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    case 1: k_loglike_fwd<2, true><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    case 2: k_loglike_fwd<3, false><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    case 3: k_loglike_fwd<3, true><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    case 4: k_loglike_fwd<4, false><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
+    case 5: k_loglike_fwd<4, true><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 int fwd_variant_min_blocks(int variant) { return variant == 0 ? 2 : variant == 1 ? 3 : 4; }
-int fwd_variant_max_blocks_per_sm(int variant) {
+int fwd_variant_max_blocks_per_sm(int variant, bool mixed) {
   int n = 0;
   cudaError_t e = cudaSuccess;
-  switch (variant) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<2>, kTileBins, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<3>, kTileBins, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<4>, kTileBins, 0); break;
+  switch (variant * 2 + (mixed ? 1 : 0)) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<2, false>, kTileBins, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<2, true>, kTileBins, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<3, false>, kTileBins, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<3, true>, kTileBins, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<4, false>, kTileBins, 0); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<4, true>, kTileBins, 0); break;
     default: return 0;
   }
   if (e != cudaSuccess) { cudaGetLastError(); return 0; }
@@ -393,8 +562,11 @@ cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const d
   k_reduce<<<grid, threads, 0, st>>>(ds, B, off, part, coef, logl, dhhh);
   return cudaGetLastError();
 }
-cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, cudaStream_t st) {
-  k_signal<<<(D.nb + kTileBins - 1) / kTileBins, kTileBins, 0, st>>>(D, coef, out);
+cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, bool mixed, cudaStream_t st) {
+  if (mixed)
+    k_signal<true><<<(D.nb + kTileBins - 1) / kTileBins, kTileBins, 0, st>>>(D, coef, out);
+  else
+    k_signal<false><<<(D.nb + kTileBins - 1) / kTileBins, kTileBins, 0, st>>>(D, coef, out);
   return cudaGetLastError();
 }
 cudaError_t launch_inject(int nb, double T, const double* psd, const double2* normals, double2* h, cudaStream_t st) {

@@ -17,20 +17,34 @@ cudaError_t launch_data_tables(const double* f, const double2* sca, const double
 cudaError_t launch_sum_parts(const double* part, int n, int w, double* out, cudaStream_t st);
 cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef, int* nend,
                         int* status, cudaStream_t st);
-cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, cudaStream_t st);
+// tile_bins: kTileBins (gradient, Fisher, surrogate kernels) or kFwdTileBins (log-likelihood kernels)
+cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st);
+inline long long tiles_of(int nb, int tile_bins) { return (nb + tile_bins - 1) / tile_bins; }
+cudaError_t launch_dw_tables(const double* f, const double2* sca, const double2* z, const double2* tab, int nb,
+                             double L, float2* fw, float2* aw, float2* atw, float2* saw, float2* caw, float4* zw,
+                             float4* tabw, cudaStream_t st);
+// max over n entries of max(|Re dg|, |Im dg|) and gg -> out[2]; mx_part: [ceil(n/128)][2] scratch
+cudaError_t launch_table_max(const double2* dg, const double* gg, int n, double* mx_part, double* out, cudaStream_t st);
+cudaError_t launch_dw_data(const double2* dg, const double* gg, int n, double inv_dgs, double inv_ggs, float4* dgw,
+                           float2* ggw, cudaStream_t st);
+// mixed: the mixed FP64/double-word forward kernel instead of the all-FP64 one
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
-                               double* part, int grid, cudaStream_t st);
-// Register-budget variants of the forward kernel (min resident CTAs per SM 2, 3, 4).
+                               double* part, int grid, bool mixed, cudaStream_t st);
+// Register-budget variants of the forward kernel (min resident CTAs per SM 2, 3, 4), per precision.
 constexpr int kFwdVariants = 3;
 constexpr int kFwdDefaultVariant = 1;
-cudaError_t launch_loglike_fwd_variant(int variant, const DetSet& ds, int B, const SampleCoef* coef, const int* nend,
-                                       const long long* off, double* part, int grid, cudaStream_t st);
+cudaError_t launch_loglike_fwd_variant(int variant, bool mixed, const DetSet& ds, int B, const SampleCoef* coef,
+                                       const int* nend, const long long* off, double* part, int grid, cudaStream_t st);
 int fwd_variant_min_blocks(int variant);
-int fwd_variant_max_blocks_per_sm(int variant);
+int fwd_variant_max_blocks_per_sm(int variant, bool mixed);
 cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const double* part, const SampleCoef* coef,
                           double* logl, double* dhhh, cudaStream_t st);
-cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, cudaStream_t st);
+cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, bool mixed, cudaStream_t st);
 cudaError_t launch_inject(int nb, double T, const double* psd, const double2* normals, double2* h, cudaStream_t st);
+
+// Mode mask of the forward entry points: at least one PE_MODE_* bit, optionally PE_PREC_MIXED.
+inline bool fwd_mask_ok(unsigned m) { return (m & PE_MODE_ALL) != 0u && (m & ~(PE_MODE_ALL | PE_PREC_MIXED)) == 0u; }
+inline bool mask_mixed(unsigned m) { return (m & PE_PREC_MIXED) != 0u; }
 
 // CTAs per SM the persistent forward kernel can keep resident (occupancy query).
 int fwd_blocks_per_sm();

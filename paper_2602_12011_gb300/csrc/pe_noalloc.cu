@@ -76,14 +76,14 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
   pe_status s0 = pe::detset_from_handles(dets, ndet, &ds);
   if (s0 != PE_OK) return s0;
   if (B < 1) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: B must be >= 1");
-  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: bad mode mask");
+  if (!pe::fwd_mask_ok(mode_mask)) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: bad mode mask");
   if (!device_ptr(theta) || !device_ptr(out_logl) || (out_dhhh && !device_ptr(out_dhhh)) ||
       (out_status && !device_ptr(out_status)))
     return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: theta and every output must be device pointers");
   // Scratch layout: coefficients [B], active bins [P], tile offsets [P+1], tile partials [tiles][6].
   const size_t P = (size_t)ndet * B;
   size_t max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (size_t)B * ((ds.d[i].nb + pe::kTileBins - 1) / pe::kTileBins);
+  for (int i = 0; i < ndet; ++i) max_tiles += (size_t)B * pe::tiles_of(ds.d[i].nb, pe::kFwdTileBins);
   const size_t o_coef = 0;
   const size_t o_nend = align256(o_coef + (size_t)B * sizeof(pe::SampleCoef));
   const size_t o_off = align256(o_nend + P * sizeof(int));
@@ -116,9 +116,10 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
     nsm = 1;
   }
   cudaError_t e = pe::launch_prep(theta, B, mode_mask, ds, coef, nend, out_status, st);
-  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, st);
+  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::kFwdTileBins, st);
   const size_t g = max_tiles < (size_t)nsm * pe::fwd_blocks_per_sm() ? max_tiles : (size_t)nsm * pe::fwd_blocks_per_sm();
-  if (e == cudaSuccess) e = pe::launch_loglike_fwd(ds, B, coef, nend, off, part, (int)(g > 0 ? g : 1), st);
+  if (e == cudaSuccess) e = pe::launch_loglike_fwd(ds, B, coef, nend, off, part, (int)(g > 0 ? g : 1),
+                                                     pe::mask_mixed(mode_mask), st);
   if (e == cudaSuccess) e = pe::launch_reduce(ds, B, off, part, coef, out_logl, out_dhhh, st);
   if (e != cudaSuccess) {
     char msg[256];

@@ -54,7 +54,7 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls(setup):
 
 def test_noalloc_rejects_oversize_and_host_buffers(setup):
     torch, L, d, T = setup
-    B = 20000                                         # about 114 MB of scratch on this grid
+    B = 20000                                         # about 43 MB of scratch on this grid
     th = torch.tensor(W.draw_prior(B, 3, T), device="cuda")
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     with pytest.raises(L.PeError) as e:
@@ -63,3 +63,18 @@ def test_noalloc_rejects_oversize_and_host_buffers(setup):
     with pytest.raises(L.PeError) as e:
         L.pe_loglike_batch_noalloc([d.handle], W.draw_prior(4, 3, T), 4, W.MODE_ALL, np.zeros(4))
     assert e.value.status == L.PE_EINVAL
+
+
+def test_noalloc_mixed_precision_matches_direct_call(setup):
+    """The precision flag reaches the no-allocation entry point: same bits as pe_loglike_batch."""
+    torch, L, d, T = setup
+    th = W.draw_prior(50, 403, T)
+    tt = torch.tensor(th, device="cuda")
+    m = W.MODE_ALL | L.PE_PREC_MIXED
+    outs = []
+    for fn in (L.pe_loglike_batch, L.pe_loglike_batch_noalloc):
+        logl = torch.empty(50, dtype=torch.float64, device="cuda")
+        fn([d.handle], tt, 50, m, logl, None, None, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        outs.append(logl.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
