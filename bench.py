@@ -32,11 +32,18 @@ from paper_2602_12011_gb300 import workloads as W  # noqa: E402
 METRIC = "log-likelihood evals/s (HM, 3 TDI ch, batched) vs plain path; grad evals/s"
 UNIT = "evals/s"
 MSUN_S = 4.925490947641267e-6
-# FP64 work per active (sample, mode, bin) unit of the fused kernel, from the ncu SASS counters
-# of the forward kernel (profiles/k_loglike_fwd_lisa_hm_T2^22_B64_ncu_full.md): flops with an FMA
-# counted as 2 (2 DFMA + DADD + DMUL), and FP64 pipe instructions (every FP64 instruction).
-FP64_FLOPS_PER_UNIT = 616.0
-FP64_INST_PER_UNIT = 425.7
+# Work per active (sample, mode, bin) unit of the fused forward kernel, from the ncu SASS counters
+# of one launch on the 64-sample case of this workload (profiles/k_loglike_fwd_*_ncu.md):
+#   fp64_flops  DFMA x 2 + DMUL + DADD
+#   fp64_inst   every FP64-pipe instruction (DFMA, DMUL, DADD, DSETP, F2F, FRND)
+#   fp32_inst   FFMA + FMUL + FADD (the double-word arithmetic of the mixed path)
+UNIT_COUNTS = {
+    "fp64": {"fp64_flops": 610.3, "fp64_inst": 434.4, "fp32_inst": 0.8},
+    "mixed": {"fp64_flops": 77.5, "fp64_inst": 69.1, "fp32_inst": 4422.5},
+}
+# DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum
+# (profiles/k_loglike_fwd_dram_lisa_hm_T2^22_B1024.md): the per-bin tables, read once per launch
+TRAFFIC = {"fp64": 31.23e6, "mixed": 37.53e6 + 7.22e6}
 
 
 def parse():
@@ -50,7 +57,8 @@ def parse():
     ap.add_argument("--no-network", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
-                    help="forward path: all FP64, or FP64 phase/t_f/sums with double-word geometry")
+                    help="headline forward path: all FP64, or FP64 phase/t_f/sums with double-word geometry")
+    ap.add_argument("--no-precision-study", action="store_true")
     return ap.parse_args()
 
 
@@ -172,6 +180,27 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def roofline(prec: str, units: int, launch_s: float, fp64_tflops: float, fp32_tflops: float) -> dict:
+    """ALU roofline of the fused forward kernel: per pipe, the instructions one launch issues
+    (per-unit count x active units) per second against the pipe's measured FMA-loop rate; the
+    binding pipe is the busier one."""
+    c = UNIT_COUNTS[prec]
+    ups = units / launch_s
+    pipes = {}
+    for name, inst, tf in (("fp64", c["fp64_inst"], fp64_tflops), ("fp32", c["fp32_inst"], fp32_tflops)):
+        peak = tf * 1e3 / 2.0   # G FMA instructions/s of the measured loop
+        ach = inst * ups / 1e9
+        pipes[name] = {"inst_per_unit": inst, "achieved_ginst_s": ach, "peak_ginst_s": peak, "frac": ach / peak}
+    bind = max(pipes, key=lambda k: pipes[k]["frac"])
+    return {"bound": "alu", "pipe": bind, "unit": "Ginst/s", "achieved": pipes[bind]["achieved_ginst_s"],
+            "peak": pipes[bind]["peak_ginst_s"], "frac": pipes[bind]["frac"],
+            "peak_kind": "measured FMA loops (FP64 and FP32, 1 s each)", "kernel": "k_loglike_fwd",
+            "launch_ms": launch_s * 1e3, "units_per_launch": units, "units_per_s": ups,
+            "fp64_tflops": c["fp64_flops"] * ups / 1e12, "fp64_tflops_peak": fp64_tflops,
+            "fp64_flops_frac": c["fp64_flops"] * ups / 1e12 / fp64_tflops, "pipes": pipes,
+            "traffic": TRAFFIC[prec], "traffic_gbs": TRAFFIC[prec] / launch_s / 1e9}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -245,6 +274,51 @@ def main():
     t_total = shard.max_over_ranks(sum(step_ms) / 1e3, device="cuda")
     value = world * B * K / t_total
     result_ok = bool(torch.isfinite(out_dev).all().item())
+
+    units = active_units(theta, T, k0, nb, mask)
+    fwd_avg_s = (fwd_ms / max(fwd_launches, 1)) / 1e3
+    peak64 = L.pe_measure_fp64_peak(1.0)
+    peak32 = L.pe_measure_fp32_peak(1.0)
+
+    # ---- precision study (the paper's low-precision option against FP64): the same batch through
+    # the other forward path, device-timed the same way; accuracy of its log L against the FP64
+    # result on the likelihood's scale 1/2 <d|d> + |<d|h>| + 1/2 <h|h>
+    study = None
+    if not args.no_precision_study:
+        dh64 = torch.empty((B, 1, 3, 2), dtype=torch.float64, device="cuda")
+        ll64 = torch.empty(B, dtype=torch.float64, device="cuda")
+        L.pe_loglike_batch(hs, th_dev, B, mask64, ll64, dh64, None, stream)
+        torch.cuda.synchronize()
+        dd = float(gd.data_norm().sum())
+        scale = 0.5 * dd + dh64[:, :, :, 0].sum(dim=(1, 2)).abs() + 0.5 * dh64[:, :, :, 1].sum(dim=(1, 2))
+        study = {args.precision: {"value": value, "ms_per_step": 1e3 * t_total / K,
+                                  "roofline_frac": roofline(args.precision, units, fwd_avg_s, peak64, peak32)["frac"]}}
+        for other in ("fp64", "mixed"):
+            if other == args.precision:
+                continue
+            m = mask64 | (L.PE_PREC_MIXED if other == "mixed" else 0)
+            tuned_o = L.pe_autotune(hs, th_dev, B, m)
+            llo = torch.empty(B, dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                L.pe_loglike_batch(hs, th_dev, B, m, llo, None, None, stream)
+            torch.cuda.synchronize()
+            L.pe_profile_read()
+            L.pe_profile_enable(True)
+            for k in range(K):
+                flush.zero_()
+                ev[k][0].record(stream)
+                L.pe_loglike_batch(hs, th_dev, B, m, llo, None, None, stream)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            L.pe_profile_enable(False)
+            o_ms, o_n = L.pe_profile_read()
+            ems = [a.elapsed_time(b) for a, b in ev]
+            rel = ((llo - ll64).abs() / scale).max().item()
+            study[other] = {"value": B * K / (sum(ems) / 1e3), "ms_per_step": sum(ems) / K, "tuning": tuned_o,
+                            "max_rel_dlogl_vs_fp64": rel, "parity_bar": 1e-10,
+                            "roofline": roofline(other, units, (o_ms / max(o_n, 1)) / 1e3, peak64, peak32)}
+        study["note"] = ("mixed: FP64 TaylorF2 phase, t_f, turn reductions and tile sums; response "
+                         "geometry, TDI, A/E/T and per-bin products in double-word FP32 arithmetic")
 
     # ---- plain path: one call per sample (B = 1), same samples, device-timed
     n_plain = 64
@@ -391,29 +465,18 @@ def main():
     e2e_tot = shard.max_over_ranks(sum(e2e_t), device="cuda")
     e2e_value = world * B * K / e2e_tot
 
-    # ---- roofline of the dominant kernel (fused forward, FP64 ALU bound)
-    units = active_units(theta, T, k0, nb, mask)
-    fwd_avg_s = (fwd_ms / max(fwd_launches, 1)) / 1e3
-    peak = L.pe_measure_fp64_peak(1.0)
-    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_kind": "measured FP64 FMA, 1 s loop",
-            "kernel": "k_loglike_fwd", "launch_ms": fwd_avg_s * 1e3, "units_per_launch": units,
-            "traffic": None}
-    ach = FP64_FLOPS_PER_UNIT * units / fwd_avg_s / 1e12
-    roof.update({"achieved": ach, "frac": ach / peak, "flops_per_unit": FP64_FLOPS_PER_UNIT,
-                 "units_per_s": units / fwd_avg_s,
-                 # the same launch in FP64-pipe slots: every FP64 instruction against the FMA loop's rate
-                 "fp64_pipe": {"inst_per_unit": FP64_INST_PER_UNIT,
-                               "achieved_ginst_s": FP64_INST_PER_UNIT * units / fwd_avg_s / 1e9,
-                               "peak_ginst_s": peak * 1e3 / 2.0,
-                               "frac": (FP64_INST_PER_UNIT * units / fwd_avg_s / 1e9) / (peak * 1e3 / 2.0)}})
+    # ---- roofline of the dominant kernel (fused forward, ALU bound)
+    roof = roofline(args.precision, units, fwd_avg_s, peak64, peak32)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_total / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32x2 (double-word)", "data": "synthetic",
             "config": {"workload": wl["name"], "detectors": "LISA", "modes": "22,21,33,32,44", "T_obs_s": T,
                        "nbins": nb, "batch_per_gpu": B, "parallelism": "replicas (independent samples per GPU)",
                        "l2": "flushed before every timed step (256 MiB write)"},
             "roofline": roof,
+            "precision_study": study,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * 11 * 8),
                     "d2h_bytes_per_step": int(B * 8)},
             "plain_path": {"value": plain_value, "unit": UNIT, "samples": n_plain,

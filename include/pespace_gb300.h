@@ -152,9 +152,10 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
  * no allocating routine.
  *   theta, out_logl and the optional out_dhhh / out_status must be DEVICE pointers (host buffers
  *   would need staging memory); other arguments and layouts are as for pe_loglike_batch.
- *   Size limit: coefficients (880 bytes per sample) plus one 48-byte partial per 512-bin tile
- *   of every (detector, sample) pair must fit in 32 MiB -- about 1,600 samples on one 2^22 s grid
- *   (209,296 bins), about 5,700 on a 2^20 s grid. Larger batches return PE_EINVAL with the
+ *   Size limit: coefficients (880 bytes per sample) plus one 48-byte partial per tile (128 bins in
+ *   FP64, 512 with PE_PREC_MIXED) of every (detector, sample) pair must fit in 32 MiB -- in FP64
+ *   about 400 samples on one 2^22 s grid (209,296 bins), about 1,500 on a 2^20 s grid (four times
+ *   as many with PE_PREC_MIXED). Larger batches return PE_EINVAL with the
  *   needed size in pe_last_error(); split them.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  *   that device current, so make that first call before any stream capture.
@@ -169,7 +170,7 @@ pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet, const doub
  * and fixed DEVICE buffers (theta [B][11], out_logl [B], optional out_dhhh [B][ndet][3][2] and
  * out_status [B]), captured once into a CUDA graph with its scratch allocated at creation. Every
  * (detector, sample) pair brings its own grid length and active bin range; all pairs run in one
- * persistent launch over their 512-bin tiles. Refill theta in place and call pe_plan_launch on
+ * persistent launch over their bin tiles. Refill theta in place and call pe_plan_launch on
  * any stream; results equal pe_loglike_batch's bit for bit.
  *   autotune = 1: if the tuning cache has no entry for this workload (GPU, SM count, batch size,
  *   mode mask, grids), time the forward kernel's launch variants on the theta present at
@@ -254,10 +255,13 @@ pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int 
  * launches since the previous read, and clears the record. pe_profile_enable(0) stops recording.
  * pe_measure_fp64_peak runs an FP64 fused-multiply-add throughput kernel (8 independent chains
  * per thread, one grid of 8 CTAs of 256 threads per SM) for about `seconds` and returns the
- * achieved FP64 rate in TFLOP/s (one FMA = 2 flops): the ALU roofline of the FP64 kernels. */
+ * achieved FP64 rate in TFLOP/s (one FMA = 2 flops): the ALU roofline of the FP64 kernels.
+ * pe_measure_fp32_peak does the same with FP32 FMAs: the FP32-pipe roofline of the double-word
+ * arithmetic of the mixed-precision path (PE_PREC_MIXED). */
 pe_status pe_profile_enable(int on);
 pe_status pe_profile_read(double* total_ms, int64_t* launches);
 pe_status pe_measure_fp64_peak(double seconds, double* out_tflops);
+pe_status pe_measure_fp32_peak(double seconds, double* out_tflops);
 
 /* Fisher-Gaussian approximation of the posterior on a subset of the parameters (Sec. 2.2: the
  * high-SNR likelihood Eq. eq_ll_fisher with covariance C = F^-1; Sec. 3.3 applies it to lambda,

@@ -110,7 +110,8 @@ def lib():
         L.pe_profile_enable.argtypes = [C.c_int]
         L.pe_profile_read.argtypes = [_P, _P]
         L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
-        for name in ("pe_profile_enable", "pe_profile_read", "pe_measure_fp64_peak", "pe_create_detector", "pe_destroy_detector", "pe_psd_model", "pe_set_data_psd", "pe_data_norm",
+        L.pe_measure_fp32_peak.argtypes = [C.c_double, _P]
+        for name in ("pe_profile_enable", "pe_profile_read", "pe_measure_fp64_peak", "pe_measure_fp32_peak", "pe_create_detector", "pe_destroy_detector", "pe_psd_model", "pe_set_data_psd", "pe_data_norm",
                      "pe_signal_aet", "pe_inject", "pe_loglike_batch", "pe_loglike_grad_batch", "pe_fisher"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -224,6 +225,12 @@ def pe_profile_read():
 def pe_measure_fp64_peak(seconds: float = 1.0) -> float:
     t = C.c_double()
     _check(lib().pe_measure_fp64_peak(float(seconds), C.addressof(t)))
+    return t.value
+
+
+def pe_measure_fp32_peak(seconds: float = 1.0) -> float:
+    t = C.c_double()
+    _check(lib().pe_measure_fp32_peak(float(seconds), C.addressof(t)))
     return t.value
 
 

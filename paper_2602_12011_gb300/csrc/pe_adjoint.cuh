@@ -144,19 +144,26 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double se = E.y, ce = E.x;
     const double2 K = cmul(gam, H);
     const double2 G = cmul(E, K);
-    double sak, cak;
-    sincos_turns(B.aturn * kn, tab, &sak, &cak);
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
-    const double s1 = B.sa * cak - B.ca * sak, s2u = B.sa * cak + B.ca * sak;
-    const double c1u = B.ca * cak + B.sa * sak, c2u = B.ca * cak - B.sa * sak;
-    double sm, spl;
-    if (fabs(u1) >= 1e-3 && fabs(u2) >= 1e-3) {
-      const double rr = 1.0 / (u1 * u2);
-      sm = s1 * u2 * rr;
-      spl = s2u * u1 * rr;
+    double sm, spl, dsm, dspl;   // sinc(u1), sinc(u2) and their derivatives
+    if (B.a < kSincPolyA) {
+      sinc_poly_d(u1, &sm, &dsm);
+      sinc_poly_d(u2, &spl, &dspl);
     } else {
-      sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
-      spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2u / u2;
+      double sak, cak;
+      sincos_turns(B.aturn * kn, tab, &sak, &cak);
+      const double s1 = B.sa * cak - B.ca * sak, s2u = B.sa * cak + B.ca * sak;
+      const double c1u = B.ca * cak + B.sa * sak, c2u = B.ca * cak - B.sa * sak;
+      if (fabs(u1) >= 1e-3 && fabs(u2) >= 1e-3) {
+        const double rr = 1.0 / (u1 * u2);
+        sm = s1 * u2 * rr;
+        spl = s2u * u1 * rr;
+      } else {
+        sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
+        spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2u / u2;
+      }
+      dsm = dsinc(u1, c1u, sm);
+      dspl = dsinc(u2, c2u, spl);
     }
     const double2 U = make_double2(fma(B.z.x, spl, sm), B.z.y * spl);
     const double2 V = make_double2(fma(B.z.x, sm, spl), B.z.y * sm);
@@ -166,8 +173,8 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double2 Vb = cconjmul(Sv, G);
     const double smb = Ub.x + Vb.x * B.z.x + Vb.y * B.z.y;
     const double splb = Ub.x * B.z.x + Ub.y * B.z.y + Vb.x;
-    const double u1b = smb * dsinc(u1, c1u, sm);
-    const double u2b = splb * dsinc(u2, c2u, spl);
+    const double u1b = smb * dsm;
+    const double u2b = splb * dspl;
     const double knb = B.a * (u2b - u1b);
     const double2 Eb = cconjmul(Gb, K);
     const double2 Kb = cconjmul(Gb, E);

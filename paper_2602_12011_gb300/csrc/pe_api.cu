@@ -463,7 +463,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   Scratch sc(st);
   const int P = ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kFwdTileBins);
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)));
   const double* th = theta;
   if (!is_device_ptr(theta)) {
     double* t = nullptr;
@@ -489,7 +489,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (h_dhhh) PE_CUDA(sc.alloc(&dhhh, (size_t)B * ndet * 6));
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep(th, B, mode_mask, ds, coef, nend, stat, st));
-  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::kFwdTileBins, st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)), st));
   pe::TuneChoice tc = pe::default_choice();
   pe::lookup_tuned(ds, B, mode_mask, &tc);
   void* prof = nullptr;

@@ -203,6 +203,36 @@ __device__ __forceinline__ double sinc_small(double u) {
   return 1.0 - u2 / 6.0 + u2 * u2 / 120.0 - u2 * u2 * u2 / 5040.0;
 }
 
+// sinc(u) = sum_k (-1)^k u^(2k) / (2k+1)! through u^16 (Horner in u^2), for |u| <= 1: the first
+// dropped term is below 1/19! = 8.2e-18, under half an ulp of sinc(u) >= sin 1.
+constexpr double kSincPolyA = 0.5;   // bins with a = pi f L below this take the polynomial (|u| <= 2a)
+__device__ __forceinline__ double sinc_poly(double u) {
+  const double x = u * u;
+  double p = 1.0 / 355687428096000.0;             // 1/17!
+  p = fma(p, x, -1.0 / 1307674368000.0);          // 1/15!
+  p = fma(p, x, 1.0 / 6227020800.0);              // 1/13!
+  p = fma(p, x, -1.0 / 39916800.0);               // 1/11!
+  p = fma(p, x, 1.0 / 362880.0);                  // 1/9!
+  p = fma(p, x, -1.0 / 5040.0);                   // 1/7!
+  p = fma(p, x, 1.0 / 120.0);                     // 1/5!
+  p = fma(p, x, -1.0 / 6.0);                      // 1/3!
+  return fma(p, x, 1.0);
+}
+// sinc(u) and d sinc/du = u sum_{k>=1} 2k (-1)^k u^(2k-2) / (2k+1)! through the same order, |u| <= 1
+__device__ __forceinline__ void sinc_poly_d(double u, double* sv, double* dv) {
+  const double x = u * u;
+  *sv = sinc_poly(u);
+  double q = 1.0 / 22230464256000.0;              // 16/17!
+  q = fma(q, x, -1.0 / 93405312000.0);            // 14/15!
+  q = fma(q, x, 1.0 / 518918400.0);               // 12/13!
+  q = fma(q, x, -1.0 / 3991680.0);                // 10/11!
+  q = fma(q, x, 1.0 / 45360.0);                   // 8/9!
+  q = fma(q, x, -1.0 / 840.0);                    // 6/7!
+  q = fma(q, x, 1.0 / 30.0);                      // 4/5!
+  q = fma(q, x, -1.0 / 3.0);                      // 2/3!
+  *dv = u * q;
+}
+
 // Mode-summed TDI brackets of one bin, kept as X' = P_X + z Q_X (and Y', Z' alike): z depends on
 // the bin only, so it is applied once after the mode sum (xyz_final).
 struct XYZAcc {
@@ -294,19 +324,25 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     const double nq = S.q[0] * n0 + S.q[1] * n1 + S.q[2] * n2;
     const double2 gam = make_double2(C.Pp * (np * np - nq * nq), C.Pc * 2.0 * np * nq);
     G[l] = cmul(E[t], cmul(gam, H));
-    // sinc(a(1 -+ kn)) from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
-    double sak, cak;
-    sincos_turns(B.aturn * kn, tab, &sak, &cak);
+    // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (most bins of a massive-binary
+    // signal), else from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
-    const double s1 = B.sa * cak - B.ca * sak, s2 = B.sa * cak + B.ca * sak;
     double sm, spl;
-    if (fabs(u1) >= 1e-3 && fabs(u2) >= 1e-3) {
-      const double rr = 1.0 / (u1 * u2);
-      sm = s1 * u2 * rr;
-      spl = s2 * u1 * rr;
+    if (B.a < kSincPolyA) {
+      sm = sinc_poly(u1);
+      spl = sinc_poly(u2);
     } else {
-      sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
-      spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2 / u2;
+      double sak, cak;
+      sincos_turns(B.aturn * kn, tab, &sak, &cak);
+      const double s1 = B.sa * cak - B.ca * sak, s2 = B.sa * cak + B.ca * sak;
+      if (fabs(u1) >= 1e-3 && fabs(u2) >= 1e-3) {
+        const double rr = 1.0 / (u1 * u2);
+        sm = s1 * u2 * rr;
+        spl = s2 * u1 * rr;
+      } else {
+        sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
+        spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2 / u2;
+      }
     }
     smv[l] = sm;
     spv[l] = spl;

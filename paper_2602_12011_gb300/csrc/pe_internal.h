@@ -20,7 +20,10 @@ constexpr double kEulerGamma = 0.57721566490153286061;
 constexpr int kNModes = 5;      // (2,2) (2,1) (3,3) (3,2) (4,4)
 constexpr int kMaxDet = 8;
 constexpr int kTileBins = 128;  // frequency bins per work tile = threads per CTA of the hot kernels
-constexpr int kFwdTileBins = 512;  // bins per work tile of the log-likelihood kernels (4 per thread)
+constexpr int kMixTileBins = 512;  // bins per work tile of the mixed-precision likelihood kernel (4 per thread)
+// Bins per work tile of the log-likelihood kernels: the FP64 path keeps one bin per thread (most
+// CTAs for small batches); the mixed path amortises its double-word reduction over four bins.
+constexpr int fwd_tile_bins(bool mixed) { return mixed ? kMixTileBins : kTileBins; }
 constexpr int kSinTab = 1024;   // entries of the (cos, sin) table used by sincos_turns
 
 // Per-(sample, mode) coefficients (row A1 of the path). With v = (2 pi M f/m)^(1/3):

@@ -296,11 +296,11 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins /
 }
 
 // ------------------------------------------------------------------------------------------
-// Rows A2-A7: persistent fused kernel. Work item = one tile of kFwdTileBins bins of one
+// Rows A2-A7: persistent fused kernel. Work item = one tile of fwd_tile_bins(MIXED) bins of one
 // (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns every
-// kTileBins-th bin of the tile (coalesced), sums the modes' TDI brackets in registers, forms A/E/T
-// and the weighted products and adds them up; the tile's six sums (<d|h>_c, <h|h>_c) go to
-// part[tile][6]. MINB (resident CTAs per SM requested from
+// kTileBins-th bin of the tile (one bin in FP64, four in mixed precision; coalesced), sums the
+// modes' TDI brackets in registers, forms A/E/T and the weighted products and adds them up; the
+// tile's six sums (<d|h>_c, <h|h>_c) go to part[tile][6]. MINB (resident CTAs per SM requested from
 // the compiler) sets the register budget only; every variant of one precision does the same
 // arithmetic in the same order, so the autotuner's choice never changes a result. MIXED selects
 // the mixed FP64/double-word unit (pe_device_mixed.cuh) over the all-FP64 one.
@@ -334,6 +334,7 @@ template <int MINB, bool MIXED>
 __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                                  const int* __restrict__ nend,
                                                                  const long long* __restrict__ off, double* part) {
+  constexpr int TILE = MIXED ? kMixTileBins : kTileBins;
   __shared__ double sh[6][kTileBins / 32];
   __shared__ double2 stab[kSinTab];   // the detector set's sincos table (as float4 double words if MIXED)
   if (MIXED) {
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair(off, P, t);
     const int I = p / B, s = p - I * B;
-    const int b0 = int(t - off[p]) * kFwdTileBins + threadIdx.x;
+    const int b0 = int(t - off[p]) * TILE + threadIdx.x;
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
 #pragma unroll
       for (int i = 0; i < 6; ++i) v[i] = df_make(0.f, 0.f);
 #pragma unroll 1
-      for (int b = b0; b < b0 + kFwdTileBins && b < ne; b += kTileBins) {
+      for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
         cdf x[3], o[3];
         bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab));
         aet_from_xyz_dw(x, o);
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
     } else {
       double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
-      for (int b = b0; b < b0 + kFwdTileBins && b < ne; b += kTileBins) {
+      for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
         double2 x[3], o[3];
         bin_xyz(D, S, b, x, stab);
         aet_from_xyz(x, o);
@@ -497,8 +498,8 @@ cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet&
 cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st) {
   if (tile_bins == kTileBins)
     k_scan_tiles<kTileBins><<<1, 1024, 0, st>>>(nend, P, off);
-  else if (tile_bins == kFwdTileBins)
-    k_scan_tiles<kFwdTileBins><<<1, 1024, 0, st>>>(nend, P, off);
+  else if (tile_bins == kMixTileBins)
+    k_scan_tiles<kMixTileBins><<<1, 1024, 0, st>>>(nend, P, off);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -17,7 +17,8 @@ cudaError_t launch_data_tables(const double* f, const double2* sca, const double
 cudaError_t launch_sum_parts(const double* part, int n, int w, double* out, cudaStream_t st);
 cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef, int* nend,
                         int* status, cudaStream_t st);
-// tile_bins: kTileBins (gradient, Fisher, surrogate kernels) or kFwdTileBins (log-likelihood kernels)
+// tile_bins: kTileBins (FP64 log-likelihood, gradient, Fisher, surrogate kernels) or kMixTileBins
+// (mixed-precision log-likelihood kernel)
 cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st);
 inline long long tiles_of(int nb, int tile_bins) { return (nb + tile_bins - 1) / tile_bins; }
 cudaError_t launch_dw_tables(const double* f, const double2* sca, const double2* z, const double2* tab, int nb,

@@ -1,5 +1,5 @@
 // pe_measure.cu -- measurement helpers of the benchmark: CUDA-event timing of the fused
-// kernels on their own stream, and the FP64 FMA throughput that bounds them.
+// kernels on their own stream, and the FP64 and FP32 FMA throughputs that bound them.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -40,13 +40,49 @@ void profile_end(cudaStream_t st, void* token) {
 }
 
 // 8 independent FMA chains per thread; the result is stored so nothing is dead code.
-__global__ void k_dfma_peak(double* out, double a, double b, int iters) {
-  double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+template <class T>
+__global__ void k_fma_peak(T* out, T a, T b, int iters) {
+  T x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
   for (int i = 0; i < iters; ++i) {
     x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
     x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+// FMA throughput of type T over about `seconds` of back-to-back launches, in TFLOP/s (FMA = 2).
+template <class T>
+pe_status fma_peak(double seconds, int iters, double* out_tflops) {
+  if (out_tflops == nullptr || !(seconds > 0.0)) return PE_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PE_ECUDA;
+  }
+  const int blocks = nsm * 8, threads = 256;
+  T* d = nullptr;
+  if (cudaMalloc(&d, (size_t)blocks * threads * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return PE_ENOMEM; }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_peak<T><<<blocks, threads>>>(d, T(0.999999), T(1e-7), iters);  // warm-up
+  double total_ms = 0.0, flops = 0.0;
+  pe_status st = PE_OK;
+  while (total_ms < seconds * 1e3) {
+    cudaEventRecord(e0);
+    k_fma_peak<T><<<blocks, threads>>>(d, T(0.999999), T(1e-7), iters);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = PE_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    total_ms += ms;
+    flops += 2.0 * 8.0 * iters * (double)blocks * threads;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (st == PE_OK) *out_tflops = flops / (total_ms * 1e-3) / 1e12;
+  return st;
 }
 
 }  // namespace pe
@@ -84,36 +120,11 @@ pe_status pe_profile_read(double* total_ms, int64_t* launches) {
 }
 
 pe_status pe_measure_fp64_peak(double seconds, double* out_tflops) {
-  if (out_tflops == nullptr || !(seconds > 0.0)) return PE_EINVAL;
-  int dev = 0, nsm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return PE_ECUDA;
-  }
-  const int blocks = nsm * 8, threads = 256, iters = 4096;
-  double* d = nullptr;
-  if (cudaMalloc(&d, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return PE_ENOMEM; }
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  pe::k_dfma_peak<<<blocks, threads>>>(d, 0.999999, 1e-7, iters);  // warm-up
-  double total_ms = 0.0, flops = 0.0;
-  pe_status st = PE_OK;
-  while (total_ms < seconds * 1e3) {
-    cudaEventRecord(e0);
-    pe::k_dfma_peak<<<blocks, threads>>>(d, 0.999999, 1e-7, iters);
-    cudaEventRecord(e1);
-    if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = PE_ECUDA; break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    total_ms += ms;
-    flops += 2.0 * 8.0 * iters * (double)blocks * threads;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(d);
-  if (st == PE_OK) *out_tflops = flops / (total_ms * 1e-3) / 1e12;
-  return st;
+  return pe::fma_peak<double>(seconds, 4096, out_tflops);
+}
+
+pe_status pe_measure_fp32_peak(double seconds, double* out_tflops) {
+  return pe::fma_peak<float>(seconds, 65536, out_tflops);
 }
 
 }  // extern "C"

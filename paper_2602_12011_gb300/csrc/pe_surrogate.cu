@@ -360,8 +360,8 @@ __device__ __forceinline__ int find_pair_s(const long long* off, int P, long lon
   return lo;
 }
 
-// Persistent kernel over the same tile list as k_loglike_fwd (kFwdTileBins bins per tile, every
-// kTileBins-th bin per thread, the same per-thread order of the sums). mode 0: surrogate path (in-box
+// Persistent kernel over the same tile list as the FP64 k_loglike_fwd (kTileBins bins per tile,
+// one bin per thread, the same order of the sums). mode 0: surrogate path (in-box
 // samples) or plain path (others), partials [tile][6] as the plain kernel. mode 1: mismatch sums
 // of the surrogate against the plain signal, partials [tile][6] = (<s|p>, <s|s>, <p|p>, 0, 0, 0).
 __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
@@ -379,14 +379,14 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair_s(off, P, t);
     const int I = p / B, s = p - I * B;
-    const int b0 = int(t - off[p]) * kFwdTileBins + threadIdx.x;
+    const int b0 = int(t - off[p]) * kTileBins + threadIdx.x;
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
     const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
-    for (int b = b0; b < b0 + kFwdTileBins && b < ne; b += kTileBins) {
+    for (int b = b0; b < b0 + kTileBins && b < ne; b += kTileBins) {
       BinIn Bn;
       load_bin(D, b, S.tc, Bn);
       double2 xs[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
@@ -820,7 +820,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return sfail(PE_EINVAL, "surrogate: bad mode mask");
   const int P = ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kFwdTileBins);
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kTileBins);
   const int Bp = pad64(B);
   cudaError_t e = ensure_batch(s, Bp);
   std::vector<void*> bufs;
@@ -876,7 +876,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     }
   }
   if (e == cudaSuccess) e = pe::launch_prep(theta_dev, B, mode_mask, ds, S, nend, nullptr, st);
-  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, P, off, pe::kFwdTileBins, st);
+  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, P, off, pe::kTileBins, st);
   if (e == cudaSuccess) {
     int nsm = 1, dev = 0;
     cudaGetDevice(&dev);

@@ -54,7 +54,7 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls(setup):
 
 def test_noalloc_rejects_oversize_and_host_buffers(setup):
     torch, L, d, T = setup
-    B = 20000                                         # about 43 MB of scratch on this grid
+    B = 20000                                         # about 116 MB of scratch on this grid
     th = torch.tensor(W.draw_prior(B, 3, T), device="cuda")
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     with pytest.raises(L.PeError) as e:
