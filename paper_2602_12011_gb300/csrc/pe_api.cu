@@ -147,12 +147,15 @@ void fill_dev(pe_detector_s* d) {
       D.cb[i] = std::cos(b);
       D.sb[i] = std::sin(b);
     }
-    // offsets as linear forms in (cos 2a, sin 2a) for x, y and (cos a, sin a) for z:
+    // offsets as linear forms in the basis (cos 2a, sin 2a, cos a, sin a) plus a constant:
     //   x = eRh (c2 cb + s2 sb) - eR3h cb,  y = eRh (s2 cb - c2 sb) - eR3h sb,  z = -eRs3 (c cb + s sb)
     for (int i = 0; i < 3; ++i) {
-      D.oA[i][0] = host_dw(D.eRh * D.cb[i]);   D.oB[i][0] = host_dw(D.eRh * D.sb[i]);  D.oC[i][0] = host_dw(-D.eR3h * D.cb[i]);
-      D.oA[i][1] = host_dw(-D.eRh * D.sb[i]);  D.oB[i][1] = host_dw(D.eRh * D.cb[i]);  D.oC[i][1] = host_dw(-D.eR3h * D.sb[i]);
-      D.oA[i][2] = host_dw(-D.eRs3 * D.cb[i]); D.oB[i][2] = host_dw(-D.eRs3 * D.sb[i]); D.oC[i][2] = host_dw(0.0);
+      const double cb = D.cb[i], sb = D.sb[i];
+      const double row[3][5] = {{D.eRh * cb, D.eRh * sb, 0.0, 0.0, -D.eR3h * cb},
+                                {-D.eRh * sb, D.eRh * cb, 0.0, 0.0, -D.eR3h * sb},
+                                {0.0, 0.0, -D.eRs3 * cb, -D.eRs3 * sb, 0.0}};
+      for (int j = 0; j < 3; ++j)
+        for (int m = 0; m < 5; ++m) D.Mo[i][j][m] = row[j][m];
     }
   } else {
     D.rgeo = D.L / std::sqrt(3.0);
@@ -169,9 +172,9 @@ void fill_dev(pe_detector_s* d) {
     for (int i = 0; i < 3; ++i) {
       const double cbi = std::cos(2.0 * pe::kPi * i / 3.0), sbi = std::sin(2.0 * pe::kPi * i / 3.0);
       for (int j = 0; j < 3; ++j) {
-        D.oA[i][j] = host_dw(D.rgeo * (cbi * D.e1[j] + sbi * D.e2[j]));
-        D.oB[i][j] = host_dw(D.rgeo * (-sbi * D.e1[j] + cbi * D.e2[j]));
-        D.oC[i][j] = host_dw(0.0);
+        D.Mo[i][j][0] = D.rgeo * (cbi * D.e1[j] + sbi * D.e2[j]);
+        D.Mo[i][j][1] = D.rgeo * (-sbi * D.e1[j] + cbi * D.e2[j]);
+        D.Mo[i][j][2] = D.Mo[i][j][3] = D.Mo[i][j][4] = 0.0;
       }
     }
   }

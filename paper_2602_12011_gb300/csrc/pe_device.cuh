@@ -233,6 +233,52 @@ __device__ __forceinline__ void sinc_poly_d(double u, double* sv, double* dv) {
   *dv = u * q;
 }
 
+// Projections of the geometry on the sample's frame as linear forms in the orbit basis b
+// (DetDev::Mo), formed once per (detector, sample) tile into shared memory (kProj doubles):
+//   pc[15 l + 5 v + m]: v-component (v = k, p, q) of the unnormalised link vector
+//                       n'_l = delta_r - delta_s, link l = (r, s) = (0,1), (1,2), (2,0);
+//   pc[45 + 5 i + m]:   k.delta_i, spacecraft i = 0, 1 (the third-spacecraft phases).
+// Since (k, p, q) is orthonormal, |n'|^2 = (k.n')^2 + (p.n')^2 + (q.n')^2.
+constexpr int kProj = 55;
+__device__ __forceinline__ double proj_coef(const DetDev& D, const SampleCoef& S, int i) {
+  const int m = i % 5;
+  if (i < 45) {
+    const int l = i / 15, v = (i / 5) % 3, r = l, s = (l + 1) % 3;
+    const double* w = v == 0 ? S.k : (v == 1 ? S.p : S.q);
+    return w[0] * (D.Mo[r][0][m] - D.Mo[s][0][m]) + w[1] * (D.Mo[r][1][m] - D.Mo[s][1][m]) +
+           w[2] * (D.Mo[r][2][m] - D.Mo[s][2][m]);
+  }
+  const int e = (i - 45) / 5;
+  return S.k[0] * D.Mo[e][0][m] + S.k[1] * D.Mo[e][1][m] + S.k[2] * D.Mo[e][2][m];
+}
+// Every thread of the CTA calls this at the start of a tile (a barrier on both sides).
+__device__ __forceinline__ void proj_prologue(const DetDev& D, const SampleCoef& S, double* pc) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < kProj; i += blockDim.x) pc[i] = proj_coef(D, S, i);
+  __syncthreads();
+}
+// p[0..3] . b + p[4]. p points to shared memory, read through a volatile pointer so that the 55
+// forms are loaded where they are used (broadcast loads) instead of being held in registers
+// across the mode loop.
+__device__ __forceinline__ double dot5(const volatile double* p, const double b[4]) {
+  return fma(p[0], b[0], fma(p[1], b[1], fma(p[2], b[2], fma(p[3], b[3], p[4]))));
+}
+// Orbit at time t: (cos, sin) of the centre's angle alpha and the offsets' basis b.
+__device__ __forceinline__ void orbit_basis(const DetDev& D, double t, const double2* __restrict__ tab, double* c,
+                                            double* s, double b[4]) {
+  sincos_turns(fma(t, D.rate_t, D.alpha0_t), tab, s, c);
+  if (D.orbit == 0) {
+    b[0] = *c * *c - *s * *s;
+    b[1] = 2.0 * *s * *c;
+    b[2] = *c;
+    b[3] = *s;
+  } else {
+    sincos_turns(t * D.geo_rate_t, tab, &b[1], &b[0]);
+    b[2] = 0.0;
+    b[3] = 0.0;
+  }
+}
+
 // Mode-summed TDI brackets of one bin, kept as X' = P_X + z Q_X (and Y', Z' alike): z depends on
 // the bin only, so it is applied once after the mode sum (xyz_final).
 struct XYZAcc {
@@ -265,7 +311,7 @@ struct BinIn {
 // e^{-2 pi i f k.x_c} folded into the mode's phase. Written as X' = P_X + z Q_X with
 // P_X = G31 s+31 - G12 s-12, Q_X = G31 s-31 - G12 s+12 (and cyclically for Y', Z').
 __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
-                                         XYZAcc& acc, const double2* __restrict__ tab) {
+                                         XYZAcc& acc, const double2* __restrict__ tab, const double* __restrict__ pc) {
   // --- waveform and time-frequency map (rows A2, A3)
   const double v = C.cm * B.f13;
   const double iv = C.icm * B.fm13;
@@ -291,10 +337,10 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   double amp = C.amp * B.fm76 * w;
   if (C.p >= 1) amp *= v;
   if (C.p >= 2) amp *= v;
-  // --- orbit at t_f (row A4)
-  double xc[3], dl[3][3];
-  orbit_offsets(D, tf, xc, dl, tab);
-  const double kxc = S.k[0] * xc[0] + S.k[1] * xc[1] + S.k[2] * xc[2];
+  // --- orbit at t_f (row A4): centre angle and the offsets' basis
+  double co, so, ob[4];
+  orbit_basis(D, tf, tab, &co, &so, ob);
+  const double kxc = D.R * (S.k[0] * co + S.k[1] * so);
   const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
   double sph, cph;
   sincos_turns(ph, tab, &sph, &cph);
@@ -302,10 +348,7 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   // third-spacecraft phases e^{i pi f k.delta_t}; the offsets sum to zero, so E_2 = conj(E_0 E_1)
   double2 E[3];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const double kd = S.k[0] * dl[i][0] + S.k[1] * dl[i][1] + S.k[2] * dl[i][2];
-    sincos_turns(0.5 * B.f * kd, tab, &E[i].y, &E[i].x);
-  }
+  for (int i = 0; i < 2; ++i) sincos_turns(0.5 * B.f * dot5(pc + 45 + 5 * i, ob), tab, &E[i].y, &E[i].x);
   {
     const double2 e01 = cmul(E[0], E[1]);
     E[2] = make_double2(e01.x, -e01.y);
@@ -315,13 +358,12 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   double smv[3], spv[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const int r = l, s = (l + 1) % 3, t = (l + 2) % 3;
-    double n0 = dl[r][0] - dl[s][0], n1 = dl[r][1] - dl[s][1], n2 = dl[r][2] - dl[s][2];
-    const double inv = rsqrt(n0 * n0 + n1 * n1 + n2 * n2);
-    n0 *= inv; n1 *= inv; n2 *= inv;
-    const double kn = S.k[0] * n0 + S.k[1] * n1 + S.k[2] * n2;
-    const double np = S.p[0] * n0 + S.p[1] * n1 + S.p[2] * n2;
-    const double nq = S.q[0] * n0 + S.q[1] * n1 + S.q[2] * n2;
+    const int t = (l + 2) % 3;
+    // projections of the unnormalised link vector, then k.n, n.e+.n, n.ex.n of the unit vector
+    const double knr = dot5(pc + 15 * l, ob), npr = dot5(pc + 15 * l + 5, ob), nqr = dot5(pc + 15 * l + 10, ob);
+    const double inv = rsqrt(fma(knr, knr, fma(npr, npr, nqr * nqr)));
+    const double kn = knr * inv;
+    const double np = npr * inv, nq = nqr * inv;
     const double2 gam = make_double2(C.Pp * (np * np - nq * nq), C.Pc * 2.0 * np * nq);
     G[l] = cmul(E[t], cmul(gam, H));
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (most bins of a massive-binary
@@ -379,7 +421,7 @@ __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinI
 
 // Mode-summed TDI brackets X', Y', Z' of one sample at one bin.
 __device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, int b, double2 acc[3],
-                                        const double2* __restrict__ tab) {
+                                        const double2* __restrict__ tab, const double* __restrict__ pc) {
   BinIn B;
   load_bin(D, b, S.tc, B);
   XYZAcc a;
@@ -388,7 +430,7 @@ __device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, in
   for (int md = 0; md < kNModes; ++md) {
     const ModeCoef& C = S.md[md];
     if (!C.active || !(B.f < C.fend)) continue;
-    mode_bin(D, S, C, B, a, tab);
+    mode_bin(D, S, C, B, a, tab, pc);
   }
   xyz_final(a, B.z, acc);
 }

@@ -4,7 +4,8 @@
 // and 53-bit precision: the TaylorF2 phase (up to ~1e6 rad) and t_f, the exact reduction of the
 // phase and the orbital angle to a fraction of a turn, and the likelihood accumulation across tiles.
 // Everything else -- the sines and cosines of the orbit, phase, third-spacecraft and sinc
-// arguments, the spacecraft offsets, unit link vectors, the projections k.n, n.e+.n, n.ex.n, the
+// arguments, the projections k.n, n.e+.n, n.ex.n of the link vectors (per-tile linear forms in the
+// orbit basis, converted to double words once per tile), the
 // sincs, the mode tensor factors, the TDI brackets, the A/E/T combinations and the PSD-weighted
 // per-bin products -- is double-word. Amplitudes enter multiplied by the sample's power of two hsc
 // (near 1/amp of the (2,2) mode) and the whitened data tables divided by powers of two near their
@@ -54,15 +55,18 @@ __device__ __forceinline__ df df_sinc_small(df u) {
   return df_add_s(df_make(1.f, 0.f), df_mul(u2, p));
 }
 
-__device__ __forceinline__ df dw_dot3(const df a[3], const df b[3]) {
-  return df_add_s(df_add_s(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+// p[0..3] . b + p[4] in double words (the projection forms of DetDev::Mo, see proj_coef)
+__device__ __forceinline__ df dw_dot5(const float2* p, const df b[4]) {
+  return df_add_s(df_add_s(df_mul(p[0], b[0]), df_mul(p[1], b[1])),
+                  df_add_s(df_add_s(df_mul(p[2], b[2]), df_mul(p[3], b[3])), p[4]));
 }
 
 // double -> double word of the fraction x - rint(x) (exact in FP64), for the sincos of a turn count
 __device__ __forceinline__ df frac_dw(double x) { return df_from(x - rint(x)); }
 
 __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
-                                               const BinW& W, MixAcc& acc, const float4* __restrict__ tab) {
+                                               const BinW& W, MixAcc& acc, const float4* __restrict__ tab,
+                                               const float2* __restrict__ pcw) {
   // --- waveform and time-frequency map (FP64; rows A2, A3)
   const double v = C.cm * B.f13;
   const double iv = C.icm * B.fm13;
@@ -96,31 +100,23 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   const cdf eph = df_cis_turns(frac_dw(ph), tab);
   const df A = df_from(amp);
   const cdf H = {df_mul(A, eph.re), df_mul(A, eph.im)};
-  // --- spacecraft offsets: dl[i][j] = oA U_j + oB V_j + oC
-  df Uc[3], Vc[3];
+  // --- the offsets' basis (DetDev::Mo)
+  df ob[4];
   if (D.orbit == 0) {
-    Uc[0] = Uc[1] = df_sub_s(df_mul(co, co), df_mul(so, so));
-    Vc[0] = Vc[1] = df_scale2(df_mul(so, co), 2.0f);
-    Uc[2] = co;
-    Vc[2] = so;
+    ob[0] = df_sub_s(df_mul(co, co), df_mul(so, so));
+    ob[1] = df_scale2(df_mul(so, co), 2.0f);
+    ob[2] = co;
+    ob[3] = so;
   } else {
     const cdf e0 = df_cis_turns(frac_dw(tf * D.geo_rate_t), tab);
-    Uc[0] = Uc[1] = Uc[2] = e0.re;
-    Vc[0] = Vc[1] = Vc[2] = e0.im;
+    ob[0] = e0.re;
+    ob[1] = e0.im;
+    ob[2] = ob[3] = df_make(0.f, 0.f);
   }
-  df dl[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      dl[i][j] = df_add_s(df_add_s(df_mul(D.oA[i][j], Uc[j]), df_mul(D.oB[i][j], Vc[j])), D.oC[i][j]);
   // --- third-spacecraft phases e^{i pi f k.delta_t} (E_2 = conj(E_0 E_1))
   cdf E[3];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const df kd = dw_dot3(S.kw, dl[i]);
-    E[i] = df_cis_turns(df_scale2(df_mul(W.f, kd), 0.5f), tab);
-  }
+  for (int i = 0; i < 2; ++i) E[i] = df_cis_turns(df_scale2(df_mul(W.f, dw_dot5(pcw + 45 + 5 * i, ob)), 0.5f), tab);
   {
     const cdf e01 = cdf_mul(E[0], E[1]);
     E[2].re = e01.re;
@@ -131,16 +127,12 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   df smv[3], spv[3];
 #pragma unroll 1
   for (int l = 0; l < 3; ++l) {
-    const int r = l, s = (l + 1) % 3, t = (l + 2) % 3;
-    df n[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) n[j] = df_sub_s(dl[r][j], dl[s][j]);
-    const df inv = df_rsqrt(dw_dot3(n, n));
-#pragma unroll
-    for (int j = 0; j < 3; ++j) n[j] = df_mul(n[j], inv);
-    const df kn = dw_dot3(S.kw, n);
-    const df np = dw_dot3(S.pw, n);
-    const df nq = dw_dot3(S.qw, n);
+    const int t = (l + 2) % 3;
+    const df knr = dw_dot5(pcw + 15 * l, ob), npr = dw_dot5(pcw + 15 * l + 5, ob), nqr = dw_dot5(pcw + 15 * l + 10, ob);
+    const df inv = df_rsqrt(df_add_s(df_mul(knr, knr), df_add_s(df_mul(npr, npr), df_mul(nqr, nqr))));
+    const df kn = df_mul(knr, inv);
+    const df np = df_mul(npr, inv);
+    const df nq = df_mul(nqr, inv);
     const df Fp = df_sub_s(df_mul(np, np), df_mul(nq, nq));
     const df Fc = df_scale2(df_mul(np, nq), 2.0f);
     const cdf gam = {df_mul(C.Ppw, Fp), df_mul(C.Pcw, Fc)};
@@ -176,7 +168,7 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
 // Mode-summed TDI brackets X', Y', Z' of one sample at one bin times the sample's hsc, mixed
 // precision.
 __device__ __forceinline__ void bin_xyz_mixed(const DetDev& D, const SampleCoef& S, int b, cdf x[3],
-                                              const float4* __restrict__ tab) {
+                                              const float4* __restrict__ tab, const float2* __restrict__ pcw) {
   BinIn B;
   load_bin(D, b, S.tc, B);
   BinW W;
@@ -187,7 +179,7 @@ __device__ __forceinline__ void bin_xyz_mixed(const DetDev& D, const SampleCoef&
   for (int md = 0; md < kNModes; ++md) {
     const ModeCoef& C = S.md[md];
     if (!C.active || !(B.f < C.fend)) continue;
-    mode_bin_mixed(D, S, C, B, W, a, tab);
+    mode_bin_mixed(D, S, C, B, W, a, tab, pcw);
   }
   const float4 zz = D.zw[b];
   mix_final(a, cdf{df_make(zz.x, zz.y), df_make(zz.z, zz.w)}, x);

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
                                                         const long long* __restrict__ off, double* part) {
   __shared__ double sh[kGradW][kTileBins / 32];
   __shared__ double2 stab[kSinTab];
+  __shared__ double pc[kProj];
   for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
   __syncthreads();
   const int P = ds.ndet * B;
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
     const int I = p / B, s = p - I * B;
     const int b = int(t - off[p]) * kTileBins + threadIdx.x;
     const DetDev& D = ds.d[I];
+    proj_prologue(D, coef[s], pc);
     double v[kGradW];
 #pragma unroll
     for (int i = 0; i < kGradW; ++i) v[i] = 0.0;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
       xyz_zero(xa);
 #pragma unroll 1
       for (int md = 0; md < kNModes; ++md)
-        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bin(D, S, S.md[md], Bn, xa, stab);
+        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bin(D, S, S.md[md], Bn, xa, stab, pc);
       double2 x[3], o[3];
       xyz_final(xa, Bn.z, x);
       aet_from_xyz(x, o);

@@ -128,10 +128,10 @@ struct DetDev {
   const float4* dgw;    // [3][nb]: dg / dg_scale as (re hi, re lo, im hi, im lo)
   const float2* ggw;    // [3][nb]: gg / gg_scale
   double dg_scale, gg_scale;   // powers of two near max|dg|, max gg (keep the double words in range)
-  // orbit offsets as double words: dl[i][j] = oA[i][j] U_j + oB[i][j] V_j + oC[i][j], with
-  // (U, V) = (cos 2alpha, sin 2alpha) for j = 0, 1 and (cos alpha, sin alpha) for j = 2
-  // (heliocentric), (cos phi_0, sin phi_0) for every j (geocentric, oC = 0)
-  float2 oA[3][3], oB[3][3], oC[3][3];
+  // spacecraft offsets as linear forms: delta_i[j] = sum_m Mo[i][j][m] b_m + Mo[i][j][4] over the
+  // orbit basis b = (cos 2alpha, sin 2alpha, cos alpha, sin alpha) (heliocentric) or
+  // (cos phi_0, sin phi_0, 0, 0) (geocentric, constant term 0)
+  double Mo[3][3][5];
   float2 Rw;            // R as a double word
   // Q = TDI factor(z) (-i a) e^{-i a}; n_A = 1/sqrt2, n_E = 1/sqrt6, n_T = 1/sqrt3
 };

@@ -336,6 +336,8 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
                                                                  const long long* __restrict__ off, double* part) {
   constexpr int TILE = MIXED ? kMixTileBins : kTileBins;
   __shared__ double sh[6][kTileBins / 32];
+  __shared__ double pc[kProj];    // the tile's projection forms (proj_coef)
+  __shared__ float2 pcw[kProj];   // the same as double words (MIXED)
   __shared__ double2 stab[kSinTab];   // the detector set's sincos table (as float4 double words if MIXED)
   if (MIXED) {
     float4* t4 = reinterpret_cast<float4*>(stab);
@@ -353,7 +355,10 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
+    proj_prologue(D, S, pc);
     if (MIXED) {
+      if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+      __syncthreads();
       // per bin in double words, times hsc (h) and 1/dg_scale, 1/gg_scale (tables); the tile sums
       // are scaled back in FP64
       df v[6];
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
 #pragma unroll 1
       for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
         cdf x[3], o[3];
-        bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab));
+        bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab), pcw);
         aet_from_xyz_dw(x, o);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
 #pragma unroll 1
       for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
         double2 x[3], o[3];
-        bin_xyz(D, S, b, x, stab);
+        bin_xyz(D, S, b, x, stab, pc);
         aet_from_xyz(x, o);
         accum_bin(D, b, o, v);
       }
@@ -436,16 +441,23 @@ __global__ void k_reduce(DetSet ds, int B, const long long* off, const double* p
 // Noise-free A/E/T signal of one sample on the whole grid: h_c = Q n_c B_c. out: [3][nb].
 template <bool MIXED>
 __global__ void k_signal(DetDev D, const SampleCoef* coef, double2* out) {
+  __shared__ double pc[kProj];
+  __shared__ float2 pcw[kProj];
+  const SampleCoef& S = coef[0];
+  proj_prologue(D, S, pc);
+  if (MIXED) {
+    if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+    __syncthreads();
+  }
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= D.nb) return;
-  const SampleCoef& S = coef[0];
   double2 x[3], o[3];
   if (MIXED) {
     cdf xw[3];
-    bin_xyz_mixed(D, S, b, xw, D.sctw);
+    bin_xyz_mixed(D, S, b, xw, D.sctw, pcw);
     for (int i = 0; i < 3; ++i) x[i] = make_double2(df_to(xw[i].re) * S.ihsc, df_to(xw[i].im) * S.ihsc);
   } else {
-    bin_xyz(D, S, b, x, D.sct);
+    bin_xyz(D, S, b, x, D.sct, pc);
   }
   aet_from_xyz(x, o);
   const double2 Q = transfer_q(kPi * D.f[b] * D.L, D.sca[b], D.z[b], D.tdi_gen);

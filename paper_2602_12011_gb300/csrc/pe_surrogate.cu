@@ -371,6 +371,7 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
                                                        const int* __restrict__ nend, const long long* __restrict__ off,
                                                        double* part, int mode) {
   __shared__ double sh[6][kTileBins / 32];
+  __shared__ double pc[kProj];
   __shared__ double2 stab[kSinTab];
   for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
   __syncthreads();
@@ -383,6 +384,7 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
+    proj_prologue(D, S, pc);
     const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
         if (sur)
           mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], xs,
                        stab);
-        if (!sur || mode == 1) mode_bin(D, S, C, Bn, xpa, stab);
+        if (!sur || mode == 1) mode_bin(D, S, C, Bn, xpa, stab, pc);
       }
       double2 xp[3];
       xyz_final(xpa, Bn.z, xp);
