@@ -38,12 +38,12 @@ MSUN_S = 4.925490947641267e-6
 #   fp64_inst   every FP64-pipe instruction (DFMA, DMUL, DADD, DSETP, F2F, FRND)
 #   fp32_inst   FFMA + FMUL + FADD (the double-word arithmetic of the mixed path)
 UNIT_COUNTS = {
-    "fp64": {"fp64_flops": 610.3, "fp64_inst": 434.4, "fp32_inst": 0.8},
-    "mixed": {"fp64_flops": 77.5, "fp64_inst": 69.1, "fp32_inst": 4422.5},
+    "fp64": {"fp64_flops": 561.0, "fp64_inst": 367.4, "fp32_inst": 0.2},
+    "mixed": {"fp64_flops": 69.3, "fp64_inst": 52.9, "fp32_inst": 4144.3},
 }
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum
 # (profiles/k_loglike_fwd_dram_lisa_hm_T2^22_B1024.md): the per-bin tables, read once per launch
-TRAFFIC = {"fp64": 31.23e6, "mixed": 37.53e6 + 7.22e6}
+TRAFFIC = {"fp64": 31.54e6 + 0.01e6, "mixed": 37.93e6 + 0.50e6}
 
 
 def parse():

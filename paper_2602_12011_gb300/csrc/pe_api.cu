@@ -43,6 +43,8 @@ struct pe_detector_s {
   float2* atw;
   float2* saw;
   float2* caw;
+  float2* f13w;        // [nb] f^(1/3), f^(-7/6) as double words
+  float2* fm76w;
   float4* zw;          // [nb] z as a double-word pair
   float4* dgw;         // [3][nb] dg / dg_scale as double words
   float2* ggw;         // [3][nb] gg / gg_scale as double words
@@ -182,7 +184,7 @@ void fill_dev(pe_detector_s* d) {
   D.f = d->f; D.f13 = d->f13; D.fm13 = d->fm13; D.lnf3 = d->lnf3; D.fm76 = d->fm76;
   D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev; D.sct = d->sct;
   D.sctw = d->sctw; D.fw = d->fw; D.aw = d->aw; D.atw = d->atw; D.saw = d->saw; D.caw = d->caw;
-  D.zw = d->zw; D.dgw = d->dgw; D.ggw = d->ggw;
+  D.zw = d->zw; D.dgw = d->dgw; D.ggw = d->ggw; D.f13w = d->f13w; D.fm76w = d->fm76w;
   D.dg_scale = 1.0;
   D.gg_scale = 1.0;
 }
@@ -249,8 +251,8 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   const size_t nb = (size_t)nbins;
   // double2: sincos table + sca, z (2 nb) + dg (3 nb); float4: double-word sincos table, zw (nb),
   // dgw (3 nb); doubles: f, f13, fm13, lnf3, fm76 (5 nb) + gg (3 nb) + psd_model (3 nb) + dd (3,
-  // padded); float2: fw, aw, atw, saw, caw (5 nb) + ggw (3 nb)
-  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab, n_f4 = pe::kSinTab + 4 * nb, n_f2 = 8 * nb;
+  // padded); float2: fw, aw, atw, saw, caw, f13w, fm76w (7 nb) + ggw (3 nb)
+  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab, n_f4 = pe::kSinTab + 4 * nb, n_f2 = 10 * nb;
   const size_t bytes = n_d2 * sizeof(double2) + n_f4 * sizeof(float4) + n_d * sizeof(double) + n_f2 * sizeof(float2);
   cudaError_t e = cudaMalloc(&d->mem, bytes);
   if (e != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ENOMEM, "cudaMalloc(%zu) failed", bytes); }
@@ -278,6 +280,8 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->atw = pf; pf += nb;
   d->saw = pf; pf += nb;
   d->caw = pf; pf += nb;
+  d->f13w = pf; pf += nb;
+  d->fm76w = pf; pf += nb;
   d->ggw = pf;
   fill_dev(d);
   const double L = det_arm_s(*cfg);
@@ -286,8 +290,8 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
           cudaSuccess ||
       (e = pe::launch_psd_model(d->f, d->nb, L, cfg->oms_m_rtHz, cfg->acc_ms2_rtHz, cfg->psd_shaping, cfg->tdi_gen,
                                 d->psd_model, 0)) != cudaSuccess ||
-      (e = pe::launch_dw_tables(d->f, d->sca, d->z, d->sct, d->nb, L, d->fw, d->aw, d->atw, d->saw, d->caw, d->zw,
-                                d->sctw, 0)) != cudaSuccess ||
+      (e = pe::launch_dw_tables(d->f, d->f13, d->fm76, d->sca, d->z, d->sct, d->nb, L, d->fw, d->aw, d->atw, d->saw,
+                                d->caw, d->f13w, d->fm76w, d->zw, d->sctw, 0)) != cudaSuccess ||
       (e = cudaMemset(d->dd_dev, 0, 3 * sizeof(double))) != cudaSuccess ||
       (e = cudaDeviceSynchronize()) != cudaSuccess) {
     cudaGetLastError();

@@ -124,7 +124,7 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   const T u[3] = {sl, -cl, 0.0 * sl};
   const T v[3] = {-(sb * cl), -(sb * sl), cb};
   for (int i = 0; i < 3; ++i) { S.p[i] = cp * u[i] + sp * v[i]; S.q[i] = -(sp * u[i]) + cp * v[i]; }
-  for (int i = 0; i < 3; ++i) { S.kw[i] = to_dw(val(S.k[i])); S.pw[i] = to_dw(val(S.p[i])); S.qw[i] = to_dw(val(S.q[i])); }
+  for (int i = 0; i < 3; ++i) S.kw[i] = to_dw(val(S.k[i]));
   // modes
   const T Fisco = 1.0 / (::pow(6.0, 1.5) * 2.0 * pi * M);
   for (int md = 0; md < kNModes; ++md) {
@@ -162,6 +162,10 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   const int e0 = (a0 > 0.0 && isfinite(a0)) ? ilogb(a0) : 0;
   S.hsc = scalbn(1.0, -e0);
   S.ihsc = scalbn(1.0, e0);
+  for (int md = 0; md < kNModes; ++md) {
+    S.md[md].cmw = to_dw(val(S.md[md].cm));
+    S.md[md].ampw = to_dw(val(S.md[md].amp) * S.hsc);
+  }
 }
 
 __device__ inline void sample_prep(const double* th, unsigned mask, SampleCoef& S) {

@@ -35,12 +35,14 @@ __device__ __forceinline__ void mix_final(const MixAcc& a, const cdf& z, cdf x[3
   }
 }
 
-// Per-bin double words: f, a = pi f L, a / (2 pi), sin a, cos a.
+// Per-bin double words: f, a = pi f L, a / (2 pi), sin a, cos a, f^(1/3), f^(-7/6).
 struct BinW {
-  df f, a, at, sa, ca;
+  df f, a, at, sa, ca, f13, fm76;
 };
 __device__ __forceinline__ void load_bin_w(const DetDev& D, int b, BinW& W) {
   W.f = D.fw[b];
+  W.f13 = D.f13w[b];
+  W.fm76 = D.fm76w[b];
   W.a = D.aw[b];
   W.at = D.atw[b];
   W.sa = D.saw[b];
@@ -56,13 +58,29 @@ __device__ __forceinline__ df df_sinc_small(df u) {
 }
 
 // p[0..3] . b + p[4] in double words (the projection forms of DetDev::Mo, see proj_coef)
+// sinc(u) for |u| <= 1 in double words: 1 + x (c1 + x (c2 + x (c3 + x (c4 + x T)))), x = u^2,
+// c_k = (-1)^k / (2k+1)! as double words; the tail T = c5 + x (c6 + x (c7 + x c8)) is below
+// 2.5e-8 and is evaluated in float (its rounding stays below 1e-14 of the result); the first
+// dropped term is below 1/19! = 8.2e-18.
+__device__ __forceinline__ df df_sinc_poly(df u) {
+  const df x = df_mul(u, u);
+  float T = __fmaf_rn(x.x, 1.0f / 355687428096000.0f, -1.0f / 1307674368000.0f);
+  T = __fmaf_rn(T, x.x, 1.0f / 6227020800.0f);
+  T = __fmaf_rn(T, x.x, -1.0f / 39916800.0f);
+  df p = df_add_s(df_make(2.75573188e-06f, 3.79357122e-14f), df_mulf(x, T));       // 1/9!
+  p = df_add_s(df_make(-0.000198412701f, 2.72559687e-12f), df_mul(x, p));           // -1/7!
+  p = df_add_s(df_make(0.00833333377f, -4.34617203e-10f), df_mul(x, p));            // 1/5!
+  p = df_add_s(df_make(-0.166666672f, 4.96705388e-09f), df_mul(x, p));              // -1/3!
+  return df_add_s(df_make(1.f, 0.f), df_mul(x, p));
+}
+
 __device__ __forceinline__ df dw_dot5(const float2* p, const df b[4]) {
   return df_add_s(df_add_s(df_mul(p[0], b[0]), df_mul(p[1], b[1])),
                   df_add_s(df_add_s(df_mul(p[2], b[2]), df_mul(p[3], b[3])), p[4]));
 }
 
 // double -> double word of the fraction x - rint(x) (exact in FP64), for the sincos of a turn count
-__device__ __forceinline__ df frac_dw(double x) { return df_from(x - rint(x)); }
+__device__ __forceinline__ df frac_dw(double x) { return df_from_bits(x - rint(x)); }
 
 __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
                                                const BinW& W, MixAcc& acc, const float4* __restrict__ tab,
@@ -83,22 +101,24 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
   const double tf = fma(C.tffac * B.invf, dv, S.tc);
-  double w = 1.0;
+  // amplitude (times hsc) in double words: ampw f^(-7/6) v^p, times the taper where it is below 1
+  df A = df_mul(C.ampw, W.fm76);
+  if (C.p >= 1) {
+    const df vw = df_mul(C.cmw, W.f13);
+    A = df_mul(A, vw);
+    if (C.p >= 2) A = df_mul(A, vw);
+  }
   if (B.f > C.ftap) {
     const double span = C.fend - C.ftap;
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
-    w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
+    A = df_mul(A, df_from_bits((zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt))));
   }
-  double amp = C.amp * S.hsc * B.fm76 * w;
-  if (C.p >= 1) amp *= v;
-  if (C.p >= 2) amp *= v;
   // --- orbital angle alpha(t_f) (row A4), centre Doppler f k.x_c, x_c = R (cos a, sin a, 0)
   const cdf eo = df_cis_turns(frac_dw(fma(tf, D.rate_t, D.alpha0_t)), tab);
   const df co = eo.re, so = eo.im;
   const df kxc = df_mul(D.Rw, df_add_s(df_mul(S.kw[0], co), df_mul(S.kw[1], so)));
-  const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - df_to(df_mul(W.f, kxc));
-  const cdf eph = df_cis_turns(frac_dw(ph), tab);
-  const df A = df_from(amp);
+  // mode phase: the FP64 part reduced to a fraction of a turn, minus f k.x_c in double words
+  const cdf eph = df_cis_turns(df_sub_s(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), df_mul(W.f, kxc)), tab);
   const cdf H = {df_mul(A, eph.re), df_mul(A, eph.im)};
   // --- the offsets' basis (DetDev::Mo)
   df ob[4];
@@ -137,21 +157,27 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     const df Fc = df_scale2(df_mul(np, nq), 2.0f);
     const cdf gam = {df_mul(C.Ppw, Fp), df_mul(C.Pcw, Fc)};
     G[l] = cdf_mul(E[t], cdf_mul(gam, H));
-    // sinc(a(1 -+ kn)) from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
-    const cdf ea = df_cis_turns(df_mul(W.at, kn), tab);
-    const df sak = ea.im, cak = ea.re;
+    // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (|u| <= 2a < 1), else from
+    // sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     const df akn = df_mul(W.a, kn);
     const df u1 = df_sub_s(W.a, akn), u2 = df_add_s(W.a, akn);
-    const df x1 = df_mul(W.sa, cak), x2 = df_mul(W.ca, sak);
-    const df s1 = df_sub_s(x1, x2), s2 = df_add_s(x1, x2);
-    const bool small1 = fabsf(u1.x) < 1e-3f, small2 = fabsf(u2.x) < 1e-3f;
-    if (!small1 && !small2) {
-      const df rr = df_rcp(df_mul(u1, u2));
-      smv[l] = df_mul(df_mul(s1, u2), rr);
-      spv[l] = df_mul(df_mul(s2, u1), rr);
+    if (B.a < kSincPolyA) {
+      smv[l] = df_sinc_poly(u1);
+      spv[l] = df_sinc_poly(u2);
     } else {
-      smv[l] = small1 ? df_sinc_small(u1) : df_mul(s1, df_rcp(u1));
-      spv[l] = small2 ? df_sinc_small(u2) : df_mul(s2, df_rcp(u2));
+      const cdf ea = df_cis_turns(df_mul(W.at, kn), tab);
+      const df sak = ea.im, cak = ea.re;
+      const df x1 = df_mul(W.sa, cak), x2 = df_mul(W.ca, sak);
+      const df s1 = df_sub_s(x1, x2), s2 = df_add_s(x1, x2);
+      const bool small1 = fabsf(u1.x) < 1e-3f, small2 = fabsf(u2.x) < 1e-3f;
+      if (!small1 && !small2) {
+        const df rr = df_rcp(df_mul(u1, u2));
+        smv[l] = df_mul(df_mul(s1, u2), rr);
+        spv[l] = df_mul(df_mul(s2, u1), rr);
+      } else {
+        smv[l] = small1 ? df_sinc_small(u1) : df_mul(s1, df_rcp(u1));
+        spv[l] = small2 ? df_sinc_small(u2) : df_mul(s2, df_rcp(u2));
+      }
     }
   }
   // --- TDI brackets (row A6): P_c += G_lp s+_lp - G_lu s-_lu, Q_c += G_lp s-_lp - G_lu s+_lu

@@ -79,6 +79,24 @@ __device__ __forceinline__ df df_from(double a) {
 }
 __device__ __forceinline__ double df_to(df a) { return (double)a.x + (double)a.y; }
 
+// double -> float by truncation to 24 significant bits on the integer pipe (GB300 runs the F2F
+// conversions on its narrow FP64 pipe). Magnitudes below 2^-126, and zero, give 0; the values
+// converted here stay far below the float overflow.
+__device__ __forceinline__ float trunc_to_float(unsigned long long u) {
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const int e = (int)((hi32 >> 20) & 0x7FFu);
+  if (e < 897) return 0.0f;
+  return __uint_as_float((hi32 & 0x80000000u) | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+}
+// double -> double word by truncation: hi = the top 24 significant bits of a (exactly a float), lo =
+// the top 24 of the exact remainder a - hi. |a - (hi + lo)| < 2^-46 |a|; one FP64 subtraction.
+__device__ __forceinline__ df df_from_bits(double a) {
+  const unsigned long long u = __double_as_longlong(a);
+  const float h = trunc_to_float(u);
+  const double hd = (h == 0.0f) ? 0.0 : __longlong_as_double((long long)(u & 0xFFFFFFFFE0000000ull));
+  return df_make(h, trunc_to_float(__double_as_longlong(a - hd)));
+}
+
 // 1/x: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0) (error delta^2)
 __device__ __forceinline__ df df_rcp(df x) {
   const float y0 = __frcp_rn(x.x);

@@ -43,6 +43,8 @@ struct ModeCoefT {
   T Pp, Pc;
   T fend, ftap;
   float2 Ppw, Pcw;   // Pp, Pc as double words (FP32 pairs) for the mixed-precision path
+  float2 cmw;        // cm as a double word
+  float2 ampw;       // amp times the sample's hsc as a double word
   int p;        // power of v in |H_lm|: 0 (22), 1 (21, 33), 2 (32, 44)
   int active;   // 1 if the mode is in the mask and its amplitude is non-zero
 };
@@ -56,7 +58,7 @@ struct SampleCoefT {
   T Pd[8];              // (k - 5) P[k]: coefficients of v dPsi_PN/dv
   T Q5, Q6;
   T k[3], p[3], q[3];   // propagation direction and polarisation frame
-  float2 kw[3], pw[3], qw[3];   // the same as double words
+  float2 kw[3];         // k as double words
   double hsc, ihsc;     // power of two near 1/amp of the (2,2) mode and its inverse: the mixed-
                         // precision path carries amplitudes times hsc, keeping them far from the
                         // FP32 range limits
@@ -124,6 +126,8 @@ struct DetDev {
   const float2* atw;
   const float2* saw;
   const float2* caw;
+  const float2* f13w;   // f^(1/3) and f^(-7/6) as double words
+  const float2* fm76w;
   const float4* zw;     // z as (re hi, re lo, im hi, im lo)
   const float4* dgw;    // [3][nb]: dg / dg_scale as (re hi, re lo, im hi, im lo)
   const float2* ggw;    // [3][nb]: gg / gg_scale

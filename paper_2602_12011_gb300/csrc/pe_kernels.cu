@@ -51,14 +51,16 @@ __global__ void k_sincos_table(double2* tab) {
   tab[j] = make_double2(c, s);
 }
 
-// Double words of the mixed-precision path: per bin f, a = pi f L, a/(2 pi), sin a, cos a (from
-// the FP64 tables), and the sincos table as (cos hi, cos lo, sin hi, sin lo).
+// Double words of the mixed-precision path: per bin f, a = pi f L, a/(2 pi), sin a, cos a,
+// f^(1/3), f^(-7/6) and z (from the FP64 tables), and the sincos table as (cos hi, cos lo, sin hi,
+// sin lo).
 __device__ __forceinline__ float2 dw_of(double a) {
   const float h = __double2float_rn(a);
   return make_float2(h, __double2float_rn(a - (double)h));
 }
-__global__ void k_dw_tables(const double* f, const double2* sca, const double2* z, const double2* tab, int nb, double L,
-                            float2* fw, float2* aw, float2* atw, float2* saw, float2* caw, float4* zw, float4* tabw) {
+__global__ void k_dw_tables(const double* f, const double* f13, const double* fm76, const double2* sca, const double2* z,
+                            const double2* tab, int nb, double L, float2* fw, float2* aw, float2* atw, float2* saw,
+                            float2* caw, float2* f13w, float2* fm76w, float4* zw, float4* tabw) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < kSinTab) {
     const float2 c = dw_of(tab[b].x), s = dw_of(tab[b].y);
@@ -70,6 +72,8 @@ __global__ void k_dw_tables(const double* f, const double2* sca, const double2* 
   atw[b] = dw_of(0.5 * f[b] * L);
   saw[b] = dw_of(sca[b].x);
   caw[b] = dw_of(sca[b].y);
+  f13w[b] = dw_of(f13[b]);
+  fm76w[b] = dw_of(fm76[b]);
   const float2 zr = dw_of(z[b].x), zi = dw_of(z[b].y);
   zw[b] = make_float4(zr.x, zr.y, zi.x, zi.y);
 }
@@ -516,11 +520,13 @@ cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_b
     return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
-cudaError_t launch_dw_tables(const double* f, const double2* sca, const double2* z, const double2* tab, int nb,
-                             double L, float2* fw, float2* aw, float2* atw, float2* saw, float2* caw, float4* zw,
+cudaError_t launch_dw_tables(const double* f, const double* f13, const double* fm76, const double2* sca,
+                             const double2* z, const double2* tab, int nb, double L, float2* fw, float2* aw,
+                             float2* atw, float2* saw, float2* caw, float2* f13w, float2* fm76w, float4* zw,
                              float4* tabw, cudaStream_t st) {
   const int n = nb > kSinTab ? nb : kSinTab;
-  k_dw_tables<<<(n + 127) / 128, 128, 0, st>>>(f, sca, z, tab, nb, L, fw, aw, atw, saw, caw, zw, tabw);
+  k_dw_tables<<<(n + 127) / 128, 128, 0, st>>>(f, f13, fm76, sca, z, tab, nb, L, fw, aw, atw, saw, caw, f13w, fm76w, zw,
+                                               tabw);
   return cudaGetLastError();
 }
 cudaError_t launch_table_max(const double2* dg, const double* gg, int n, double* mx_part, double* out, cudaStream_t st) {

@@ -21,8 +21,9 @@ cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet&
 // (mixed-precision log-likelihood kernel)
 cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st);
 inline long long tiles_of(int nb, int tile_bins) { return (nb + tile_bins - 1) / tile_bins; }
-cudaError_t launch_dw_tables(const double* f, const double2* sca, const double2* z, const double2* tab, int nb,
-                             double L, float2* fw, float2* aw, float2* atw, float2* saw, float2* caw, float4* zw,
+cudaError_t launch_dw_tables(const double* f, const double* f13, const double* fm76, const double2* sca,
+                             const double2* z, const double2* tab, int nb, double L, float2* fw, float2* aw,
+                             float2* atw, float2* saw, float2* caw, float2* f13w, float2* fm76w, float4* zw,
                              float4* tabw, cudaStream_t st);
 // max over n entries of max(|Re dg|, |Im dg|) and gg -> out[2]; mx_part: [ceil(n/128)][2] scratch
 cudaError_t launch_table_max(const double2* dg, const double* gg, int n, double* mx_part, double* out, cudaStream_t st);
