@@ -285,6 +285,60 @@ def test_link_sinc_form_equals_time_shift_form(oracle_mod, lm, rs):
         assert abs(y[i] - ref) <= 1e-11 * abs(ref)
 
 
+def test_fd_link_response_against_time_domain_dft(oracle_mod):
+    """R6, a sanity check of the SPA response, not a parity pin: the single-link response of
+    Eq. eq_td_resp, evaluated sample by sample in the time domain with the moving orbit, then
+    Fourier transformed, agrees with the frequency-domain form Eq. eq_fd_resp (geometry at t_f,
+    Eq. eq_tf) to the accuracy of the stationary-phase treatment of the orbit.
+
+    The time-domain (2,2) polarisations are the inverse DFT of the oracle's band-limited
+    frequency-domain ones (10 s sampling, 2^16 samples, 3.5e-4 Hz to the taper end, t_c inside the
+    window). Delayed samples h(t - L - k.x_s(t)) and h(t - k.x_r(t)) come from cubic splines of the
+    sampled signal; the orbit comes from the oracle every 100 s, splined."""
+    from scipy.interpolate import CubicSpline
+    det = W.LISA
+    L = det["arm_m"] / C_SI
+    dt, N = 10.0, 2 ** 16
+    Tw = N * dt
+    th = np.array([1e6, 2.0, 0.3, 0.1, 10.0, 0.6, 0.7, 1.2, 0.4, 0.9, 6.0e5])
+    fk = np.arange(N // 2 + 1) / Tw
+    flo, fend = 3.5e-4, 2.0 * 6 ** -1.5 / (2 * math.pi * th[0] * MSUN_S)
+    band = (fk >= flo) & (fk < fend)
+    hp = np.zeros(fk.size, complex)
+    hc = np.zeros(fk.size, complex)
+    hp[band], hc[band] = oracle_mod.polarizations(th, W.MODE_22, fk[band])
+    # smooth turn-on over [flo, 1.5 flo] so the time-domain signal starts without ringing
+    ramp = np.clip((fk - flo) / (0.5 * flo), 0.0, 1.0)
+    win = np.where(band, np.sin(0.5 * math.pi * ramp) ** 2, 0.0)
+    hp *= win
+    hc *= win
+    t = np.arange(N) * dt
+    sp = CubicSpline(t, np.fft.irfft(hp, n=N) / dt)
+    sc = CubicSpline(t, np.fft.irfft(hc, n=N) / dt)
+    tc = np.arange(-100.0, Tw + 200.0, 100.0)
+    xs_all = np.array([oracle_mod.orbit(det, ti) for ti in tc])          # [time][spacecraft][xyz]
+    xfun = CubicSpline(tc, xs_all, axis=0)
+    x = xfun(t)
+    k, ep, ec = oracle_mod.sky_basis(th)
+    for (r, s_) in ((1, 2), (3, 1)):
+        xr, xs = x[:, r - 1], x[:, s_ - 1]
+        n = (xr - xs) / np.linalg.norm(xr - xs, axis=1)[:, None]
+        fp = np.einsum("ti,ij,tj->t", n, ep, n)
+        fc = np.einsum("ti,ij,tj->t", n, ec, n)
+        t1 = t - L - xs @ k
+        t2 = t - xr @ k
+        y = (fp * (sp(t1) - sp(t2)) + fc * (sc(t1) - sc(t2))) / (2.0 * (1.0 - n @ k))
+        ytd = np.fft.rfft(y) * dt
+        sel = (fk > 2.0 * flo) & (fk < 0.6 * fend)
+        yfd = oracle_mod.link(det, th, 2, 2, fk[sel], r, s_)
+        err = np.abs(ytd[sel] - yfd)
+        ref = np.abs(yfd)
+        # measured: 2.7e-4 of the maximum and 2.4e-4 median; with the geometry frozen at t_c
+        # instead of t_f the same comparison gives 4.4e-2 and 6.5e-3
+        assert np.max(err) < 2e-3 * ref.max()
+        assert np.median(err / ref) < 1e-3
+
+
 def test_long_wavelength_limit(oracle_mod):
     """fL -> 0: X_1.5 -> 2 (2 pi f L)^2 [n13.h.n13 - n12.h.n12] e^{-2 pi i f k.xbar} and
     X_2.0 -> 4 i (2 pi f L) X_1.5, with relative corrections O(f L)."""
@@ -432,6 +486,29 @@ def test_noise_chi2(oracle_mod):
     vals = np.array(vals)
     assert abs(vals.mean() + nb) < 5 * math.sqrt(nb / vals.size)
     assert vals.var() == pytest.approx(nb, rel=0.8)
+
+
+def test_tdi15_and_tdi20_whitened_products_agree(oracle_mod):
+    """TDI 2.0 multiplies every channel's signal by (1 - z^4) and its PSD by |1 - z^4|^2 (Sec. 2.1,
+    Sec. 3.2), so with noise-free data every whitened product, hence log L, <d|h>, <h|h> and the
+    SNR, is the same for the two generations; only bins with 1 - z^4 = 0 would differ, and none
+    lies on the grid."""
+    T = 2.0 ** 14
+    k0, nb = W.grid(T)
+    f = (k0 + np.arange(nb)) / T
+    inj = TH.copy(); inj[0] = 3e5; inj[10] = 0.8 * T
+    res = []
+    for det in (dict(W.LISA, tdi_gen=15), W.LISA):
+        d = oracle_mod.make_data(det, inj, W.MODE_ALL, T, k0, nb, None)
+        D = oracle_mod.Detector(det, T, k0, nb, d, oracle_mod.psd(det, f))
+        ths = np.vstack([inj, inj + np.array([2e3, 0.05, 0.1, -0.1, 1.0, 0.05, 0.3, 0.01, 0.02, 0.1, 3.0])])
+        res.append([oracle_mod.loglike([D], th, W.MODE_ALL) for th in ths])
+    for a, b in zip(*res):
+        scale = 0.5 * a["dd"].sum() + abs(a["dh"].sum()) + 0.5 * a["hh"].sum()
+        assert scale > 1e3
+        assert abs(a["logl"] - b["logl"]) < 1e-11 * scale
+        np.testing.assert_allclose(b["hh"], a["hh"], rtol=1e-11)
+        np.testing.assert_allclose(b["dh"], a["dh"], rtol=1e-11, atol=1e-11 * scale)
 
 
 def test_residual_form_equals_component_form(oracle_mod):
