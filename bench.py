@@ -40,10 +40,12 @@ MSUN_S = 4.925490947641267e-6
 UNIT_COUNTS = {
     "fp64": {"fp64_flops": 561.0, "fp64_inst": 367.4, "fp32_inst": 0.2},
     "mixed": {"fp64_flops": 69.3, "fp64_inst": 52.9, "fp32_inst": 4144.3},
+    # FP32 path: fp64_inst counts the FRND and F2F of CUDA's FP32 sincospif/sinf and conversions
+    "fp32": {"fp64_flops": 0.3, "fp64_inst": 10.1, "fp32_inst": 355.8},
 }
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum
 # (profiles/k_loglike_fwd_dram_lisa_hm_T2^22_B1024.md): the per-bin tables, read once per launch
-TRAFFIC = {"fp64": 31.54e6 + 0.01e6, "mixed": 37.93e6 + 0.50e6}
+TRAFFIC = {"fp64": 31.54e6 + 0.01e6, "mixed": 37.93e6 + 0.50e6, "fp32": None}
 
 
 def parse():
@@ -184,6 +186,8 @@ def roofline(prec: str, units: int, launch_s: float, fp64_tflops: float, fp32_tf
     """ALU roofline of the fused forward kernel: per pipe, the instructions one launch issues
     (per-unit count x active units) per second against the pipe's measured FMA-loop rate; the
     binding pipe is the busier one."""
+    if prec not in UNIT_COUNTS:
+        return None
     c = UNIT_COUNTS[prec]
     ups = units / launch_s
     pipes = {}
@@ -198,7 +202,7 @@ def roofline(prec: str, units: int, launch_s: float, fp64_tflops: float, fp32_tf
             "launch_ms": launch_s * 1e3, "units_per_launch": units, "units_per_s": ups,
             "fp64_tflops": c["fp64_flops"] * ups / 1e12, "fp64_tflops_peak": fp64_tflops,
             "fp64_flops_frac": c["fp64_flops"] * ups / 1e12 / fp64_tflops, "pipes": pipes,
-            "traffic": TRAFFIC[prec], "traffic_gbs": TRAFFIC[prec] / launch_s / 1e9}
+            "traffic": TRAFFIC[prec], "traffic_gbs": TRAFFIC[prec] / launch_s / 1e9 if TRAFFIC[prec] else None}
 
 
 def main():
@@ -279,6 +283,7 @@ def main():
     fwd_avg_s = (fwd_ms / max(fwd_launches, 1)) / 1e3
     peak64 = L.pe_measure_fp64_peak(1.0)
     peak32 = L.pe_measure_fp32_peak(1.0)
+    roof = roofline(args.precision, units, fwd_avg_s, peak64, peak32)
 
     # ---- precision study (the paper's low-precision option against FP64): the same batch through
     # the other forward path, device-timed the same way; accuracy of its log L against the FP64
@@ -292,11 +297,11 @@ def main():
         dd = float(gd.data_norm().sum())
         scale = 0.5 * dd + dh64[:, :, :, 0].sum(dim=(1, 2)).abs() + 0.5 * dh64[:, :, :, 1].sum(dim=(1, 2))
         study = {args.precision: {"value": value, "ms_per_step": 1e3 * t_total / K,
-                                  "roofline_frac": roofline(args.precision, units, fwd_avg_s, peak64, peak32)["frac"]}}
-        for other in ("fp64", "mixed"):
+                                  "roofline_frac": roof["frac"] if roof else None}}
+        for other in ("fp64", "mixed", "fp32"):
             if other == args.precision:
                 continue
-            m = mask64 | (L.PE_PREC_MIXED if other == "mixed" else 0)
+            m = mask64 | {"fp64": 0, "mixed": L.PE_PREC_MIXED, "fp32": L.PE_PREC_FP32}[other]
             tuned_o = L.pe_autotune(hs, th_dev, B, m)
             llo = torch.empty(B, dtype=torch.float64, device="cuda")
             for _ in range(3):
@@ -314,11 +319,13 @@ def main():
             o_ms, o_n = L.pe_profile_read()
             ems = [a.elapsed_time(b) for a, b in ev]
             rel = ((llo - ll64).abs() / scale).max().item()
+            absmax = (llo - ll64).abs().max().item()
             study[other] = {"value": B * K / (sum(ems) / 1e3), "ms_per_step": sum(ems) / K, "tuning": tuned_o,
-                            "max_rel_dlogl_vs_fp64": rel, "parity_bar": 1e-10,
+                            "max_rel_dlogl_vs_fp64": rel, "max_abs_dlogl_vs_fp64": absmax, "parity_bar": 1e-10,
                             "roofline": roofline(other, units, (o_ms / max(o_n, 1)) / 1e3, peak64, peak32)}
         study["note"] = ("mixed: FP64 TaylorF2 phase, t_f, turn reductions and tile sums; response "
-                         "geometry, TDI, A/E/T and per-bin products in double-word FP32 arithmetic")
+                         "geometry, TDI, A/E/T and per-bin products in double-word FP32 arithmetic. "
+                         "fp32: every step in FP32 (the paper's float32 option); misses the 1e-10 bar")
 
     # ---- plain path: one call per sample (B = 1), same samples, device-timed
     n_plain = 64
@@ -464,9 +471,6 @@ def main():
             e2e_t.append(dt)
     e2e_tot = shard.max_over_ranks(sum(e2e_t), device="cuda")
     e2e_value = world * B * K / e2e_tot
-
-    # ---- roofline of the dominant kernel (fused forward, ALU bound)
-    roof = roofline(args.precision, units, fwd_avg_s, peak64, peak32)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_total / K, "higher_is_better": True,

@@ -53,6 +53,11 @@ extern "C" {
  * batch-invariant by itself. The gradient, Fisher and surrogate entry points are FP64 only and
  * reject the flag. */
 #define PE_PREC_MIXED 0x100u
+/* Precision flag for the precision study, OR-ed into the same mode masks (not with PE_PREC_MIXED):
+ * every step in FP32, including the TaylorF2 phase, t_f and frac(f t_c) -- the paper's float32
+ * option for coarse work (Sec. 3.1, Fig. fig_cost). Its log L misses the 1e-10 parity bar by
+ * orders of magnitude; it exists to measure that trade, not for inference. */
+#define PE_PREC_FP32 0x200u
 
 typedef enum {
   PE_OK = 0,

@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpespace_gb300.so")
 PE_OK, PE_EINVAL, PE_ENOMEM, PE_ECUDA, PE_ETIMEOUT, PE_ESTATE = range(6)
 STATUS_NAMES = {0: "PE_OK", 1: "PE_EINVAL", 2: "PE_ENOMEM", 3: "PE_ECUDA", 4: "PE_ETIMEOUT", 5: "PE_ESTATE"}
 NPARAM = 11
-# precision flag OR-ed into the mode mask of the forward entry points (see the C header)
+# precision flags OR-ed into the mode mask of the forward entry points (see the C header)
 PE_PREC_MIXED = 0x100
+PE_PREC_FP32 = 0x200
 
 
 class PeError(RuntimeError):

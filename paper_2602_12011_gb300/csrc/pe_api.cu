@@ -48,6 +48,11 @@ struct pe_detector_s {
   float4* zw;          // [nb] z as a double-word pair
   float4* dgw;         // [3][nb] dg / dg_scale as double words
   float2* ggw;         // [3][nb] gg / gg_scale as double words
+  float* f32;          // [5][nb] FP32 f, f^(1/3), f^(-1/3), ln f/3, f^(-7/6) (precision study)
+  float2* scaf;        // [nb] FP32 (sin a, cos a), z, then dg / dg_scale [3][nb]
+  float2* zf;
+  float2* dgf;
+  float* ggf;          // [3][nb] FP32 gg / gg_scale
   double dd[3];
   int has_data;
   pe::DetDev dev;
@@ -185,6 +190,11 @@ void fill_dev(pe_detector_s* d) {
   D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev; D.sct = d->sct;
   D.sctw = d->sctw; D.fw = d->fw; D.aw = d->aw; D.atw = d->atw; D.saw = d->saw; D.caw = d->caw;
   D.zw = d->zw; D.dgw = d->dgw; D.ggw = d->ggw; D.f13w = d->f13w; D.fm76w = d->fm76w;
+  const size_t nbz = (size_t)d->nb;
+  D.ff = d->f32; D.f13f = d->f32 + nbz; D.fm13f = d->f32 + 2 * nbz; D.lnf3f = d->f32 + 3 * nbz; D.fm76f = d->f32 + 4 * nbz;
+  D.scaf = d->scaf; D.zf = d->zf; D.dgf = d->dgf; D.ggf = d->ggf;
+  D.rate_tf = (float)D.rate_t; D.alpha0_tf = (float)D.alpha0_t; D.geo_rate_tf = (float)D.geo_rate_t;
+  D.Rf = (float)D.R; D.Lf = (float)D.L;
   D.dg_scale = 1.0;
   D.gg_scale = 1.0;
 }
@@ -251,9 +261,12 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   const size_t nb = (size_t)nbins;
   // double2: sincos table + sca, z (2 nb) + dg (3 nb); float4: double-word sincos table, zw (nb),
   // dgw (3 nb); doubles: f, f13, fm13, lnf3, fm76 (5 nb) + gg (3 nb) + psd_model (3 nb) + dd (3,
-  // padded); float2: fw, aw, atw, saw, caw, f13w, fm76w (7 nb) + ggw (3 nb)
-  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab, n_f4 = pe::kSinTab + 4 * nb, n_f2 = 10 * nb;
-  const size_t bytes = n_d2 * sizeof(double2) + n_f4 * sizeof(float4) + n_d * sizeof(double) + n_f2 * sizeof(float2);
+  // padded); float2: fw, aw, atw, saw, caw, f13w, fm76w (7 nb) + ggw (3 nb) + scaf, zf (2 nb) +
+  // dgf (3 nb); float: five FP32 grid tables (5 nb) + ggf (3 nb)
+  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab, n_f4 = pe::kSinTab + 4 * nb, n_f2 = 15 * nb,
+               n_f = 8 * nb;
+  const size_t bytes = n_d2 * sizeof(double2) + n_f4 * sizeof(float4) + n_d * sizeof(double) +
+                       n_f2 * sizeof(float2) + n_f * sizeof(float);
   cudaError_t e = cudaMalloc(&d->mem, bytes);
   if (e != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ENOMEM, "cudaMalloc(%zu) failed", bytes); }
   double2* p2 = static_cast<double2*>(d->mem);
@@ -282,7 +295,13 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->caw = pf; pf += nb;
   d->f13w = pf; pf += nb;
   d->fm76w = pf; pf += nb;
-  d->ggw = pf;
+  d->ggw = pf; pf += 3 * nb;
+  d->scaf = pf; pf += nb;
+  d->zf = pf; pf += nb;
+  d->dgf = pf; pf += 3 * nb;
+  float* pff = reinterpret_cast<float*>(pf);
+  d->f32 = pff; pff += 5 * nb;
+  d->ggf = pff;
   fill_dev(d);
   const double L = det_arm_s(*cfg);
   if ((e = pe::launch_sincos_table(d->sct, 0)) != cudaSuccess ||
@@ -292,6 +311,9 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
                                 d->psd_model, 0)) != cudaSuccess ||
       (e = pe::launch_dw_tables(d->f, d->f13, d->fm76, d->sca, d->z, d->sct, d->nb, L, d->fw, d->aw, d->atw, d->saw,
                                 d->caw, d->f13w, d->fm76w, d->zw, d->sctw, 0)) != cudaSuccess ||
+      (e = pe::launch_f32_tables(d->f, d->f13, d->fm13, d->lnf3, d->fm76, d->sca, d->z, d->nb, d->f32,
+                                 d->f32 + nb, d->f32 + 2 * nb, d->f32 + 3 * nb, d->f32 + 4 * nb, d->scaf, d->zf, 0)) !=
+          cudaSuccess ||
       (e = cudaMemset(d->dd_dev, 0, 3 * sizeof(double))) != cudaSuccess ||
       (e = cudaDeviceSynchronize()) != cudaSuccess) {
     cudaGetLastError();
@@ -356,7 +378,7 @@ static pe_status set_data_device(pe_detector det, const double2* data_dev, const
     det->dev.dg_scale = pow2_above(mx[0]);
     det->dev.gg_scale = pow2_above(mx[1]);
     e = pe::launch_dw_data(det->dg, det->gg, n3, 1.0 / det->dev.dg_scale, 1.0 / det->dev.gg_scale, det->dgw, det->ggw,
-                           0);
+                           det->dgf, det->ggf, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (mxp) cudaFree(mxp);
@@ -412,7 +434,7 @@ static pe_status signal_device(pe_detector det, const double* theta, unsigned mo
   ds.ndet = 1;
   ds.d[0] = det->dev;
   PE_CUDA(pe::launch_prep(th, 1, mode_mask, ds, coef, nend, status, st));
-  PE_CUDA(pe::launch_signal(det->dev, coef, out_dev, pe::mask_mixed(mode_mask), st));
+  PE_CUDA(pe::launch_signal(det->dev, coef, out_dev, pe::mask_prec(mode_mask), st));
   int hs = 0;
   PE_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   PE_CUDA(cudaStreamSynchronize(st));
@@ -470,7 +492,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   Scratch sc(st);
   const int P = ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
   const double* th = theta;
   if (!is_device_ptr(theta)) {
     double* t = nullptr;
@@ -496,12 +518,12 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (h_dhhh) PE_CUDA(sc.alloc(&dhhh, (size_t)B * ndet * 6));
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep(th, B, mode_mask, ds, coef, nend, stat, st));
-  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)), st));
+  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), st));
   pe::TuneChoice tc = pe::default_choice();
   pe::lookup_tuned(ds, B, mode_mask, &tc);
   void* prof = nullptr;
   pe::profile_begin(st, &prof);
-  PE_CUDA(pe::launch_loglike_fwd_variant(tc.variant, pe::mask_mixed(mode_mask), ds, B, coef, nend, off, part,
+  PE_CUDA(pe::launch_loglike_fwd_variant(tc.variant, pe::mask_prec(mode_mask), ds, B, coef, nend, off, part,
                                          pe::grid_for(tc, max_tiles), st));
   pe::profile_end(st, prof);
   PE_CUDA(pe::launch_reduce(ds, B, off, part, coef, logl, dhhh, st));

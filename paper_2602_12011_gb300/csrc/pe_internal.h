@@ -20,10 +20,12 @@ constexpr double kEulerGamma = 0.57721566490153286061;
 constexpr int kNModes = 5;      // (2,2) (2,1) (3,3) (3,2) (4,4)
 constexpr int kMaxDet = 8;
 constexpr int kTileBins = 128;  // frequency bins per work tile = threads per CTA of the hot kernels
-constexpr int kMixTileBins = 512;  // bins per work tile of the mixed-precision likelihood kernel (4 per thread)
+constexpr int kMixTileBins = 512;  // bins per work tile of the mixed and FP32 likelihood kernels (4 per thread)
+// Arithmetic of the forward path (mode-mask flags PE_PREC_MIXED, PE_PREC_FP32).
+constexpr int kPrecFP64 = 0, kPrecMixed = 1, kPrecFP32 = 2;
 // Bins per work tile of the log-likelihood kernels: the FP64 path keeps one bin per thread (most
-// CTAs for small batches); the mixed path amortises its double-word reduction over four bins.
-constexpr int fwd_tile_bins(bool mixed) { return mixed ? kMixTileBins : kTileBins; }
+// CTAs for small batches); the others amortise their block reduction over four bins.
+__host__ __device__ constexpr int fwd_tile_bins(int prec) { return prec == kPrecFP64 ? kTileBins : kMixTileBins; }
 constexpr int kSinTab = 1024;   // entries of the (cos, sin) table used by sincos_turns
 
 // Per-(sample, mode) coefficients (row A1 of the path). With v = (2 pi M f/m)^(1/3):
@@ -132,6 +134,18 @@ struct DetDev {
   const float4* dgw;    // [3][nb]: dg / dg_scale as (re hi, re lo, im hi, im lo)
   const float2* ggw;    // [3][nb]: gg / gg_scale
   double dg_scale, gg_scale;   // powers of two near max|dg|, max gg (keep the double words in range)
+  // FP32 copies for the precision study (PE_PREC_FP32): f, f^(1/3), f^(-1/3), ln f/3, f^(-7/6),
+  // (sin a, cos a), z, dg / dg_scale [3][nb], gg / gg_scale [3][nb]
+  const float* ff;
+  const float* f13f;
+  const float* fm13f;
+  const float* lnf3f;
+  const float* fm76f;
+  const float2* scaf;
+  const float2* zf;
+  const float2* dgf;
+  const float* ggf;
+  float rate_tf, alpha0_tf, geo_rate_tf, Rf, Lf;   // orbit constants and arm in FP32
   // spacecraft offsets as linear forms: delta_i[j] = sum_m Mo[i][j][m] b_m + Mo[i][j][4] over the
   // orbit basis b = (cos 2alpha, sin 2alpha, cos alpha, sin alpha) (heliocentric) or
   // (cos phi_0, sin phi_0, 0, 0) (geocentric, constant term 0)

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "pe_device.cuh"
+#include "pe_device_f32.cuh"
 #include "pe_device_mixed.cuh"
 #include "pe_kernels.h"
 
@@ -115,12 +116,29 @@ __global__ void k_max_parts(const double* part, int n, double* out) {
 // Double-word copies of the whitened tables divided by the power-of-two scales: dgw [3][nb] as
 // (re hi, re lo, im hi, im lo), ggw [3][nb].
 __global__ void k_dw_data(const double2* dg, const double* gg, int n, double inv_dgs, double inv_ggs, float4* dgw,
-                          float2* ggw) {
+                          float2* ggw, float2* dgf, float* ggf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float2 r = dw_of(dg[i].x * inv_dgs), m = dw_of(dg[i].y * inv_dgs);
   dgw[i] = make_float4(r.x, r.y, m.x, m.y);
   ggw[i] = dw_of(gg[i] * inv_ggs);
+  dgf[i] = make_float2(r.x, m.x);
+  ggf[i] = (float)(gg[i] * inv_ggs);
+}
+
+// FP32 copies of the grid tables for the precision study (PE_PREC_FP32).
+__global__ void k_f32_tables(const double* f, const double* f13, const double* fm13, const double* lnf3,
+                             const double* fm76, const double2* sca, const double2* z, int nb, float* ff, float* f13f,
+                             float* fm13f, float* lnf3f, float* fm76f, float2* scaf, float2* zf) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  ff[b] = (float)f[b];
+  f13f[b] = (float)f13[b];
+  fm13f[b] = (float)fm13[b];
+  lnf3f[b] = (float)lnf3[b];
+  fm76f[b] = (float)fm76[b];
+  scaf[b] = make_float2((float)sca[b].x, (float)sca[b].y);
+  zf[b] = make_float2((float)z[b].x, (float)z[b].y);
 }
 
 // Analytic PSD (acceleration + OMS noise only): equal-arm TDI-1.5 A/E/T spectra
@@ -300,14 +318,15 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins /
 }
 
 // ------------------------------------------------------------------------------------------
-// Rows A2-A7: persistent fused kernel. Work item = one tile of fwd_tile_bins(MIXED) bins of one
+// Rows A2-A7: persistent fused kernel. Work item = one tile of fwd_tile_bins(PREC) bins of one
 // (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns every
-// kTileBins-th bin of the tile (one bin in FP64, four in mixed precision; coalesced), sums the
-// modes' TDI brackets in registers, forms A/E/T and the weighted products and adds them up; the
-// tile's six sums (<d|h>_c, <h|h>_c) go to part[tile][6]. MINB (resident CTAs per SM requested from
+// kTileBins-th bin of the tile (one bin in FP64, four in the mixed and FP32 paths; coalesced),
+// sums the modes' TDI brackets in registers, forms A/E/T and the weighted products and adds them
+// up; the tile's six sums (<d|h>_c, <h|h>_c) go to part[tile][6]. MINB (resident CTAs per SM requested from
 // the compiler) sets the register budget only; every variant of one precision does the same
-// arithmetic in the same order, so the autotuner's choice never changes a result. MIXED selects
-// the mixed FP64/double-word unit (pe_device_mixed.cuh) over the all-FP64 one.
+// arithmetic in the same order, so the autotuner's choice never changes a result. PREC selects the
+// all-FP64 unit, the mixed FP64/double-word one (pe_device_mixed.cuh) or the all-FP32 one of the
+// precision study (pe_device_f32.cuh).
 // ------------------------------------------------------------------------------------------
 // Block reduction of NV double words per thread (accurate double-word adds, fixed tree order);
 // result valid in thread 0.
@@ -334,19 +353,20 @@ __device__ __forceinline__ void block_sum_dw(df v[NV], float2 (*sh)[kTileBins / 
     }
 }
 
-template <int MINB, bool MIXED>
+template <int MINB, int PREC>
 __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                                  const int* __restrict__ nend,
                                                                  const long long* __restrict__ off, double* part) {
-  constexpr int TILE = MIXED ? kMixTileBins : kTileBins;
+  constexpr int TILE = fwd_tile_bins(PREC);
   __shared__ double sh[6][kTileBins / 32];
   __shared__ double pc[kProj];    // the tile's projection forms (proj_coef)
-  __shared__ float2 pcw[kProj];   // the same as double words (MIXED)
-  __shared__ double2 stab[kSinTab];   // the detector set's sincos table (as float4 double words if MIXED)
-  if (MIXED) {
+  __shared__ float2 pcw[kProj];   // the same as double words (mixed) or floats (.x, FP32)
+  __shared__ SampleF sf;          // the tile's sample coefficients in FP32 (FP32 path)
+  __shared__ double2 stab[kSinTab];   // the sincos table (as float4 double words in the mixed path)
+  if (PREC == kPrecMixed) {
     float4* t4 = reinterpret_cast<float4*>(stab);
     for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) t4[i] = ds.d[0].sctw[i];
-  } else {
+  } else if (PREC == kPrecFP64) {
     for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
   }
   __syncthreads();
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
     proj_prologue(D, S, pc);
-    if (MIXED) {
+    if constexpr (PREC == kPrecMixed) {
       if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
       __syncthreads();
       // per bin in double words, times hsc (h) and 1/dg_scale, 1/gg_scale (tables); the tile sums
@@ -389,6 +409,42 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
         for (int c = 0; c < 3; ++c) {
           part[t * 6 + c] = df_to(v[c]) * sd;
           part[t * 6 + 3 + c] = df_to(v[3 + c]) * sg;
+        }
+      }
+    } else if constexpr (PREC == kPrecFP32) {
+      float* pcf = reinterpret_cast<float*>(pcw);
+      if (threadIdx.x < kProj) pcf[threadIdx.x] = (float)pc[threadIdx.x];
+      if (threadIdx.x == 0) sample_to_f32(S, sf);
+      __syncthreads();
+      float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+      for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
+        float2 o[3];
+        bin_aet_f32(D, sf, b, o, pcf);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 g = D.dgf[c * D.nb + b];
+          v[c] += g.x * o[c].x - g.y * o[c].y;
+          v[3 + c] += D.ggf[c * D.nb + b] * (o[c].x * o[c].x + o[c].y * o[c].y);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+      float* shf = reinterpret_cast<float*>(sh);
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      __syncthreads();
+      if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) shf[i * 4 + wid] = v[i];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double ih = S.ihsc;
+        const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const float a = ((shf[i * 4] + shf[i * 4 + 1]) + shf[i * 4 + 2]) + shf[i * 4 + 3];
+          part[t * 6 + i] = (double)a * (i < 3 ? sd : sg);
         }
       }
     } else {
@@ -443,27 +499,35 @@ __global__ void k_reduce(DetSet ds, int B, const long long* off, const double* p
 }
 
 // Noise-free A/E/T signal of one sample on the whole grid: h_c = Q n_c B_c. out: [3][nb].
-template <bool MIXED>
+template <int PREC>
 __global__ void k_signal(DetDev D, const SampleCoef* coef, double2* out) {
   __shared__ double pc[kProj];
   __shared__ float2 pcw[kProj];
+  __shared__ SampleF sf;
   const SampleCoef& S = coef[0];
   proj_prologue(D, S, pc);
-  if (MIXED) {
-    if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
-    __syncthreads();
+  if (PREC == kPrecMixed && threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+  if (PREC == kPrecFP32) {
+    if (threadIdx.x < kProj) reinterpret_cast<float*>(pcw)[threadIdx.x] = (float)pc[threadIdx.x];
+    if (threadIdx.x == 0) sample_to_f32(S, sf);
   }
+  __syncthreads();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= D.nb) return;
   double2 x[3], o[3];
-  if (MIXED) {
+  if (PREC == kPrecMixed) {
     cdf xw[3];
     bin_xyz_mixed(D, S, b, xw, D.sctw, pcw);
     for (int i = 0; i < 3; ++i) x[i] = make_double2(df_to(xw[i].re) * S.ihsc, df_to(xw[i].im) * S.ihsc);
+    aet_from_xyz(x, o);
+  } else if (PREC == kPrecFP32) {
+    float2 of[3];
+    bin_aet_f32(D, sf, b, of, reinterpret_cast<const float*>(pcw));
+    for (int i = 0; i < 3; ++i) o[i] = make_double2((double)of[i].x * S.ihsc, (double)of[i].y * S.ihsc);
   } else {
     bin_xyz(D, S, b, x, D.sct, pc);
+    aet_from_xyz(x, o);
   }
-  aet_from_xyz(x, o);
   const double2 Q = transfer_q(kPi * D.f[b] * D.L, D.sca[b], D.z[b], D.tdi_gen);
   for (int c = 0; c < 3; ++c) out[c * D.nb + b] = cscale(cmul(Q, o[c]), kChanNorm[c]);
 }
@@ -536,42 +600,69 @@ cudaError_t launch_table_max(const double2* dg, const double* gg, int n, double*
   return cudaGetLastError();
 }
 cudaError_t launch_dw_data(const double2* dg, const double* gg, int n, double inv_dgs, double inv_ggs, float4* dgw,
-                           float2* ggw, cudaStream_t st) {
-  k_dw_data<<<(n + 127) / 128, 128, 0, st>>>(dg, gg, n, inv_dgs, inv_ggs, dgw, ggw);
+                           float2* ggw, float2* dgf, float* ggf, cudaStream_t st) {
+  k_dw_data<<<(n + 127) / 128, 128, 0, st>>>(dg, gg, n, inv_dgs, inv_ggs, dgw, ggw, dgf, ggf);
+  return cudaGetLastError();
+}
+cudaError_t launch_f32_tables(const double* f, const double* f13, const double* fm13, const double* lnf3,
+                              const double* fm76, const double2* sca, const double2* z, int nb, float* ff, float* f13f,
+                              float* fm13f, float* lnf3f, float* fm76f, float2* scaf, float2* zf, cudaStream_t st) {
+  k_f32_tables<<<(nb + 127) / 128, 128, 0, st>>>(f, f13, fm13, lnf3, fm76, sca, z, nb, ff, f13f, fm13f, lnf3f, fm76f,
+                                                 scaf, zf);
   return cudaGetLastError();
 }
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
-                               double* part, int grid, bool mixed, cudaStream_t st) {
-  return launch_loglike_fwd_variant(kFwdDefaultVariant, mixed, ds, B, coef, nend, off, part, grid, st);
+                               double* part, int grid, int prec, cudaStream_t st) {
+  return launch_loglike_fwd_variant(kFwdDefaultVariant, prec, ds, B, coef, nend, off, part, grid, st);
 }
-cudaError_t launch_loglike_fwd_variant(int variant, bool mixed, const DetSet& ds, int B, const SampleCoef* coef,
-                                       const int* nend, const long long* off, double* part, int grid, cudaStream_t st) {
-  switch (variant * 2 + (mixed ? 1 : 0)) {
-    case 0: k_loglike_fwd<2, false><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    case 1: k_loglike_fwd<2, true><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    case 2: k_loglike_fwd<3, false><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    case 3: k_loglike_fwd<3, true><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    case 4: k_loglike_fwd<4, false><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    case 5: k_loglike_fwd<4, true><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part); break;
-    default: return cudaErrorInvalidValue;
-  }
+
+namespace {
+template <int MINB, int PREC>
+cudaError_t fwd_one(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
+                    double* part, int grid, cudaStream_t st) {
+  k_loglike_fwd<MINB, PREC><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part);
   return cudaGetLastError();
 }
-int fwd_variant_min_blocks(int variant) { return variant == 0 ? 2 : variant == 1 ? 3 : 4; }
-int fwd_variant_max_blocks_per_sm(int variant, bool mixed) {
+template <int MINB, int PREC>
+int fwd_occ() {
   int n = 0;
-  cudaError_t e = cudaSuccess;
-  switch (variant * 2 + (mixed ? 1 : 0)) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<2, false>, kTileBins, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<2, true>, kTileBins, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<3, false>, kTileBins, 0); break;
-    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<3, true>, kTileBins, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<4, false>, kTileBins, 0); break;
-    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<4, true>, kTileBins, 0); break;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_loglike_fwd<MINB, PREC>, kTileBins, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+}  // namespace
+
+cudaError_t launch_loglike_fwd_variant(int variant, int prec, const DetSet& ds, int B, const SampleCoef* coef,
+                                       const int* nend, const long long* off, double* part, int grid, cudaStream_t st) {
+  switch (variant * 3 + prec) {
+    case 0: return fwd_one<2, kPrecFP64>(ds, B, coef, nend, off, part, grid, st);
+    case 1: return fwd_one<2, kPrecMixed>(ds, B, coef, nend, off, part, grid, st);
+    case 2: return fwd_one<2, kPrecFP32>(ds, B, coef, nend, off, part, grid, st);
+    case 3: return fwd_one<3, kPrecFP64>(ds, B, coef, nend, off, part, grid, st);
+    case 4: return fwd_one<3, kPrecMixed>(ds, B, coef, nend, off, part, grid, st);
+    case 5: return fwd_one<3, kPrecFP32>(ds, B, coef, nend, off, part, grid, st);
+    case 6: return fwd_one<4, kPrecFP64>(ds, B, coef, nend, off, part, grid, st);
+    case 7: return fwd_one<4, kPrecMixed>(ds, B, coef, nend, off, part, grid, st);
+    case 8: return fwd_one<4, kPrecFP32>(ds, B, coef, nend, off, part, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+int fwd_variant_min_blocks(int variant) { return variant == 0 ? 2 : variant == 1 ? 3 : 4; }
+int fwd_variant_max_blocks_per_sm(int variant, int prec) {
+  switch (variant * 3 + prec) {
+    case 0: return fwd_occ<2, kPrecFP64>();
+    case 1: return fwd_occ<2, kPrecMixed>();
+    case 2: return fwd_occ<2, kPrecFP32>();
+    case 3: return fwd_occ<3, kPrecFP64>();
+    case 4: return fwd_occ<3, kPrecMixed>();
+    case 5: return fwd_occ<3, kPrecFP32>();
+    case 6: return fwd_occ<4, kPrecFP64>();
+    case 7: return fwd_occ<4, kPrecMixed>();
+    case 8: return fwd_occ<4, kPrecFP32>();
     default: return 0;
   }
-  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
-  return n;
 }
 cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const double* part, const SampleCoef* coef,
                           double* logl, double* dhhh, cudaStream_t st) {
@@ -581,11 +672,14 @@ cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const d
   k_reduce<<<grid, threads, 0, st>>>(ds, B, off, part, coef, logl, dhhh);
   return cudaGetLastError();
 }
-cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, bool mixed, cudaStream_t st) {
-  if (mixed)
-    k_signal<true><<<(D.nb + kTileBins - 1) / kTileBins, kTileBins, 0, st>>>(D, coef, out);
+cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, int prec, cudaStream_t st) {
+  const int g = (D.nb + kTileBins - 1) / kTileBins;
+  if (prec == kPrecMixed)
+    k_signal<kPrecMixed><<<g, kTileBins, 0, st>>>(D, coef, out);
+  else if (prec == kPrecFP32)
+    k_signal<kPrecFP32><<<g, kTileBins, 0, st>>>(D, coef, out);
   else
-    k_signal<false><<<(D.nb + kTileBins - 1) / kTileBins, kTileBins, 0, st>>>(D, coef, out);
+    k_signal<kPrecFP64><<<g, kTileBins, 0, st>>>(D, coef, out);
   return cudaGetLastError();
 }
 cudaError_t launch_inject(int nb, double T, const double* psd, const double2* normals, double2* h, cudaStream_t st) {

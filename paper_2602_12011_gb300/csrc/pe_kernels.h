@@ -28,25 +28,34 @@ cudaError_t launch_dw_tables(const double* f, const double* f13, const double* f
 // max over n entries of max(|Re dg|, |Im dg|) and gg -> out[2]; mx_part: [ceil(n/128)][2] scratch
 cudaError_t launch_table_max(const double2* dg, const double* gg, int n, double* mx_part, double* out, cudaStream_t st);
 cudaError_t launch_dw_data(const double2* dg, const double* gg, int n, double inv_dgs, double inv_ggs, float4* dgw,
-                           float2* ggw, cudaStream_t st);
-// mixed: the mixed FP64/double-word forward kernel instead of the all-FP64 one
+                           float2* ggw, float2* dgf, float* ggf, cudaStream_t st);
+// FP32 copies of the grid tables (precision study)
+cudaError_t launch_f32_tables(const double* f, const double* f13, const double* fm13, const double* lnf3,
+                              const double* fm76, const double2* sca, const double2* z, int nb, float* ff, float* f13f,
+                              float* fm13f, float* lnf3f, float* fm76f, float2* scaf, float2* zf, cudaStream_t st);
+// prec: kPrecFP64, kPrecMixed or kPrecFP32 forward kernel
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
-                               double* part, int grid, bool mixed, cudaStream_t st);
+                               double* part, int grid, int prec, cudaStream_t st);
 // Register-budget variants of the forward kernel (min resident CTAs per SM 2, 3, 4), per precision.
 constexpr int kFwdVariants = 3;
 constexpr int kFwdDefaultVariant = 1;
-cudaError_t launch_loglike_fwd_variant(int variant, bool mixed, const DetSet& ds, int B, const SampleCoef* coef,
+cudaError_t launch_loglike_fwd_variant(int variant, int prec, const DetSet& ds, int B, const SampleCoef* coef,
                                        const int* nend, const long long* off, double* part, int grid, cudaStream_t st);
 int fwd_variant_min_blocks(int variant);
-int fwd_variant_max_blocks_per_sm(int variant, bool mixed);
+int fwd_variant_max_blocks_per_sm(int variant, int prec);
 cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const double* part, const SampleCoef* coef,
                           double* logl, double* dhhh, cudaStream_t st);
-cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, bool mixed, cudaStream_t st);
+cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, int prec, cudaStream_t st);
 cudaError_t launch_inject(int nb, double T, const double* psd, const double2* normals, double2* h, cudaStream_t st);
 
-// Mode mask of the forward entry points: at least one PE_MODE_* bit, optionally PE_PREC_MIXED.
-inline bool fwd_mask_ok(unsigned m) { return (m & PE_MODE_ALL) != 0u && (m & ~(PE_MODE_ALL | PE_PREC_MIXED)) == 0u; }
-inline bool mask_mixed(unsigned m) { return (m & PE_PREC_MIXED) != 0u; }
+// Mode mask of the forward entry points: at least one PE_MODE_* bit, optionally one precision flag.
+inline bool fwd_mask_ok(unsigned m) {
+  return (m & PE_MODE_ALL) != 0u && (m & ~(PE_MODE_ALL | PE_PREC_MIXED | PE_PREC_FP32)) == 0u &&
+         (m & (PE_PREC_MIXED | PE_PREC_FP32)) != (PE_PREC_MIXED | PE_PREC_FP32);
+}
+inline int mask_prec(unsigned m) {
+  return (m & PE_PREC_MIXED) ? kPrecMixed : ((m & PE_PREC_FP32) ? kPrecFP32 : kPrecFP64);
+}
 
 // CTAs per SM the persistent forward kernel can keep resident (occupancy query).
 int fwd_blocks_per_sm();

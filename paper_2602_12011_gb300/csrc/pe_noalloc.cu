@@ -83,7 +83,7 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
   // Scratch layout: coefficients [B], active bins [P], tile offsets [P+1], tile partials [tiles][6].
   const size_t P = (size_t)ndet * B;
   size_t max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (size_t)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (size_t)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
   const size_t o_coef = 0;
   const size_t o_nend = align256(o_coef + (size_t)B * sizeof(pe::SampleCoef));
   const size_t o_off = align256(o_nend + P * sizeof(int));
@@ -116,10 +116,10 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
     nsm = 1;
   }
   cudaError_t e = pe::launch_prep(theta, B, mode_mask, ds, coef, nend, out_status, st);
-  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)), st);
+  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), st);
   const size_t g = max_tiles < (size_t)nsm * pe::fwd_blocks_per_sm() ? max_tiles : (size_t)nsm * pe::fwd_blocks_per_sm();
   if (e == cudaSuccess) e = pe::launch_loglike_fwd(ds, B, coef, nend, off, part, (int)(g > 0 ? g : 1),
-                                                     pe::mask_mixed(mode_mask), st);
+                                                     pe::mask_prec(mode_mask), st);
   if (e == cudaSuccess) e = pe::launch_reduce(ds, B, off, part, coef, out_logl, out_dhhh, st);
   if (e != cudaSuccess) {
     char msg[256];

@@ -137,7 +137,7 @@ int grid_for(const TuneChoice& c, long long max_tiles) {
 cudaError_t autotune_fwd(const DetSet& ds, int B, unsigned mask, const SampleCoef* coef, const int* nend,
                          const long long* off, double* part, long long max_tiles, cudaStream_t st, TuneChoice* best) {
   static const int kCtas[] = {2, 4, 8, 16};
-  const bool mixed = mask_mixed(mask);
+  const int prec = mask_prec(mask);
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
   if (e != cudaSuccess) return e;
@@ -147,11 +147,11 @@ cudaError_t autotune_fwd(const DetSet& ds, int B, unsigned mask, const SampleCoe
     for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
       TuneChoice c{v, kCtas[ci], 0.0};
       const int grid = grid_for(c, max_tiles);
-      if ((e = launch_loglike_fwd_variant(v, mixed, ds, B, coef, nend, off, part, grid, st)) != cudaSuccess) break;  // warm
+      if ((e = launch_loglike_fwd_variant(v, prec, ds, B, coef, nend, off, part, grid, st)) != cudaSuccess) break;  // warm
       float best_ms = 1e30f;
       for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
         cudaEventRecord(e0, st);
-        e = launch_loglike_fwd_variant(v, mixed, ds, B, coef, nend, off, part, grid, st);
+        e = launch_loglike_fwd_variant(v, prec, ds, B, coef, nend, off, part, grid, st);
         cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -218,7 +218,7 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
     return pe::set_error(PE_EINVAL, "pe_plan_create: theta and outputs must be device pointers");
   const size_t P = (size_t)ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
   const size_t o_nend = a256((size_t)B * sizeof(pe::SampleCoef));
   const size_t o_off = a256(o_nend + P * sizeof(int));
   const size_t o_part = a256(o_off + (P + 1) * sizeof(long long));
@@ -243,7 +243,7 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
   pl->choice = pe::default_choice();
   if (e == cudaSuccess && !pe::lookup_tuned(ds, B, mode_mask, &pl->choice) && autotune) {
     e = pe::launch_prep(theta_dev, B, mode_mask, ds, coef, nend, nullptr, cs);
-    if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)), cs);
+    if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), cs);
     pe::TuneChoice best;
     if (e == cudaSuccess) e = pe::autotune_fwd(ds, B, mode_mask, coef, nend, off, part, max_tiles, cs, &best);
     if (e == cudaSuccess) {
@@ -254,9 +254,9 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t e1 = pe::launch_prep(theta_dev, B, mode_mask, ds, coef, nend, out_status_dev, cs);
-    if (e1 == cudaSuccess) e1 = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)), cs);
+    if (e1 == cudaSuccess) e1 = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), cs);
     if (e1 == cudaSuccess)
-      e1 = pe::launch_loglike_fwd_variant(pl->choice.variant, pe::mask_mixed(mode_mask), ds, B, coef, nend, off, part,
+      e1 = pe::launch_loglike_fwd_variant(pl->choice.variant, pe::mask_prec(mode_mask), ds, B, coef, nend, off, part,
                                           pe::grid_for(pl->choice, max_tiles), cs);
     if (e1 == cudaSuccess) e1 = pe::launch_reduce(ds, B, off, part, coef, out_logl_dev, out_dhhh_dev, cs);
     e = cudaStreamEndCapture(cs, &pl->graph);
@@ -307,7 +307,7 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
   if (!dev_ptr(theta_dev)) return pe::set_error(PE_EINVAL, "pe_autotune: theta must be a device pointer");
   const size_t P = (size_t)ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
   const size_t o_nend = a256((size_t)B * sizeof(pe::SampleCoef));
   const size_t o_off = a256(o_nend + P * sizeof(int));
   const size_t o_part = a256(o_off + (P + 1) * sizeof(long long));
@@ -326,7 +326,7 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   pe::TuneChoice best = pe::default_choice();
   if (e == cudaSuccess) e = pe::launch_prep(theta_dev, B, mode_mask, ds, coef, nend, nullptr, cs);
-  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_mixed(mode_mask)), cs);
+  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), cs);
   if (e == cudaSuccess) e = pe::autotune_fwd(ds, B, mode_mask, coef, nend, off, part, max_tiles, cs, &best);
   if (cs) cudaStreamDestroy(cs);
   cudaFree(scratch);
