@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="headline forward path: all FP64, or FP64 phase/t_f/sums with double-word geometry")
     ap.add_argument("--no-precision-study", action="store_true")
+    ap.add_argument("--no-hetero", action="store_true")
     return ap.parse_args()
 
 
@@ -457,6 +458,49 @@ def main():
                "heldout_in_box": int(inbox.sum())}
         srg.close()
 
+    # ---- heterodyned (relative-binning) likelihood, the second workload: 1024 draws in the posterior's
+    # bulk around the injection (the all-parameter Fisher-Gaussian at 0.1 of its width), evaluated
+    # through 256 coarse bins against the exact path on the same draws
+    het = None
+    if not args.no_hetero:
+        idx = np.arange(11, dtype=np.int32)
+        nrm = 0.1 * np.random.Generator(np.random.PCG64(2607 + rank)).standard_normal((1400, 11))
+        _, draws = L.fisher_gaussian([gd], wl["inj"], mask64, idx, nrm)
+        ok = (draws[:, 1] >= 1.0) & (np.abs(draws[:, 2]) < 1) & (np.abs(draws[:, 3]) < 1) & (draws[:, 4] > 0)
+        thh = torch.tensor(draws[ok][:1024], device="cuda")
+        Bh = thh.shape[0]
+        t_c = time.perf_counter()
+        hobj = L.Hetero(gd, wl["inj"], mask64, nbins_coarse=256)
+        t_c = time.perf_counter() - t_c
+        llh = torch.empty(Bh, dtype=torch.float64, device="cuda")
+        lle = torch.empty(Bh, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            L.pe_hetero_loglike_batch([hobj.handle], thh, Bh, llh, None, None, stream)
+        L.pe_loglike_batch(hs, thh, Bh, mask64, lle, None, None, stream)
+        torch.cuda.synchronize()
+        hms, ems = [], []
+        for k in range(max(3, K // 2)):
+            flush.zero_()
+            e0.record(stream)
+            L.pe_hetero_loglike_batch([hobj.handle], thh, Bh, llh, None, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            hms.append(e0.elapsed_time(e1))
+            flush.zero_()
+            e0.record(stream)
+            L.pe_loglike_batch(hs, thh, Bh, mask64, lle, None, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ems.append(e0.elapsed_time(e1))
+        dl = (llh - lle).abs()
+        het = {"value": world * Bh / (sum(hms) / len(hms) / 1e3), "unit": UNIT, "ms_per_step": sum(hms) / len(hms),
+               "exact_same_samples": world * Bh / (sum(ems) / len(ems) / 1e3), "gain": sum(ems) / sum(hms),
+               "batch": Bh, "coarse_edges": int(hobj.edges.size), "create_s": t_c,
+               "max_abs_dlogl_vs_exact": dl.max().item(), "median_abs_dlogl_vs_exact": dl.median().item(),
+               "samples": "Fisher-Gaussian draws at 0.1 of its width around the injection (posterior bulk)",
+               "dtype": "f64"}
+        hobj.close()
+
     # ---- end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of logL
     th_host = torch.tensor(theta).pin_memory()
     out_host = torch.empty(B, dtype=torch.float64).pin_memory()
@@ -488,6 +532,7 @@ def main():
             "fisher": fisher,
             "network": net,
             "surrogate": sur,
+            "heterodyne": het,
             "tuning": tuned,
             "grad": {"value": grad_value, "unit": "grad evals/s", "ms_per_step": sum(gms) / Kg, "steps": Kg,
                      "finite": grad_ok},

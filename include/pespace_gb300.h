@@ -280,6 +280,42 @@ pe_status pe_fisher_gaussian(const pe_detector* dets, int ndet, const double* th
                              const int32_t* idx, int k, const double* normals, int n, double* out_cov,
                              double* out_samples);
 
+/* ---- Heterodyned (relative-binning) likelihood (Sec. 1: heterodyning about a reference signal) ----
+ * Relative to a reference theta0 near the truth, each mode's channel signal is h0 times a ratio
+ * r = h(theta)/h0 that varies slowly with frequency. Inside coarse bin b = [f_b, f_b+1) the ratio is
+ * linear, r0 + r1 (f - f_b), from its values at the edges. Data and reference enter through
+ * per-bin summary sums over the fine grid, formed once at creation:
+ *   A_o = sum_k w conj(d) h0_lm (f - f_b)^o,           o = 0, 1
+ *   B_o = sum_k w h0_lm conj(h0_l'm') (f - f_b)^o,     o = 0, 1, 2
+ * per mode (pair) and channel. A sample then needs the response only at the NE edges, not at
+ * every bin: <d|h> = sum Re[A0 r0 + A1 r1] and
+ * <h|h> = sum Re[B0 r0 r0'* + B1 (r1 r0'* + r0 r1'*) + B2 r1 r1'*], with <d|d> exact.
+ * Ratio rule: past a mode's last taper mark (1 - 0.1 * 0.7^10 of m F_isco, weight ~1e-15) and
+ * wherever h0 is exactly zero, the previous edge's ratio is carried forward.
+ *   pe_hetero_default_edges: host only, no GPU. Coarse edges (fine-bin indices, 0 .. kmax, kmax = the
+ *     last bin below the reference's band end) for a grid (T_obs, k0, nbins) and theta0 [11] (host):
+ *     nbins_coarse steps uniform in the relative-binning phase metric
+ *     sum_g sgn(g) (f/f*_g)^g, g in {-5/3, -2/3, 1, 5/3, 7/3}, snapped to the grid, plus 11
+ *     geometric marks 1 - 0.1 * 0.7^j (j = 0..10) of each mode's taper end; none past a mode's last
+ *     mark inside its band. *inout_n: capacity of out_edges on entry, count on return (PE_EINVAL
+ *     if too small).
+ *   pe_hetero_create: summary data for detector det (with data set), reference theta0 [11] (host),
+ *     mode_mask (no precision flag) and edges [nedges] (host, strictly increasing, 2 <= nedges <=
+ *     640, within the grid). The library owns the result; det must outlive it. Synchronous.
+ *   pe_hetero_loglike_batch: log L per sample for hets[ndet] (1..8 detectors sharing one mode mask),
+ *     theta [B][11], out_logl [B], out_dhhh nullable [B][ndet][3][2], out_status nullable [B] (host or
+ *     device each, as pe_loglike_batch). One CTA per sample evaluates all NE edges of every detector.
+ *   The heterodyned log L equals the exact one at theta0 and for changes of d_L or phi_c; elsewhere
+ *   its error shrinks as the bins do (tests/test_gpu_hetero.py measures it). */
+typedef struct pe_hetero_s* pe_hetero;
+pe_status pe_hetero_default_edges(double T_obs, int64_t k0, int64_t nbins, const double* theta0, unsigned mode_mask,
+                                  int nbins_coarse, int64_t* out_edges, int* inout_n);
+pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_mask, const int64_t* edges,
+                           int nedges, pe_hetero* out);
+pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double* theta, int B, double* out_logl,
+                                  double* out_dhhh, int32_t* out_status, void* stream);
+pe_status pe_hetero_destroy(pe_hetero h);
+
 /* Message describing the last failing call on this thread ("" if none). */
 const char* pe_last_error(void);
 

@@ -108,6 +108,12 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.pe_fisher_gaussian.argtypes = [_P, C.c_int, _P, C.c_uint, _P, C.c_int, _P, C.c_int, _P, _P]
         L.pe_fisher_gaussian.restype = C.c_int
+        L.pe_hetero_default_edges.argtypes = [C.c_double, C.c_int64, C.c_int64, _P, C.c_uint, C.c_int, _P, _P]
+        L.pe_hetero_create.argtypes = [_P, _P, C.c_uint, _P, C.c_int, C.POINTER(_P)]
+        L.pe_hetero_loglike_batch.argtypes = [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P]
+        L.pe_hetero_destroy.argtypes = [_P]
+        for name in ("pe_hetero_default_edges", "pe_hetero_create", "pe_hetero_loglike_batch", "pe_hetero_destroy"):
+            getattr(L, name).restype = C.c_int
         L.pe_profile_enable.argtypes = [C.c_int]
         L.pe_profile_read.argtypes = [_P, _P]
         L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
@@ -535,3 +541,74 @@ def fisher_gaussian(dets, theta0, mode_mask: int, idx, normals=None):
     _check(lib().pe_fisher_gaussian(_handles([d.handle for d in dets]), len(dets), _ptr(th), int(mode_mask), _ptr(ix),
                                     k, _ptr(z), n, _ptr(cov), _ptr(out)))
     return cov, out
+
+
+# ---- heterodyned (relative-binning) likelihood ------------------------------------------------------
+def pe_hetero_default_edges(T_obs: float, k0: int, nbins: int, theta0, mode_mask: int, nbins_coarse: int) -> np.ndarray:
+    """Coarse-bin edges (fine-bin indices) for reference theta0; host computation, no GPU needed."""
+    th = np.ascontiguousarray(np.asarray(theta0, dtype=np.float64))
+    cap = nbins_coarse + 64
+    out = np.zeros(cap, dtype=np.int64)
+    n = C.c_int(cap)
+    _check(lib().pe_hetero_default_edges(float(T_obs), int(k0), int(nbins), _ptr(th), int(mode_mask),
+                                         int(nbins_coarse), _ptr(out), C.byref(n)))
+    return out[:n.value].copy()
+
+
+class Hetero:
+    """Summary data of one detector (with data set) for a reference theta0 and coarse edges (fine-bin
+    indices; default: pe_hetero_default_edges with nbins_coarse bins). The detector must stay open."""
+
+    def __init__(self, det, theta0, mode_mask: int, edges=None, nbins_coarse: int = 256):
+        th = np.ascontiguousarray(np.asarray(theta0, dtype=np.float64))
+        if edges is None:
+            edges = pe_hetero_default_edges(det.T, det.k0, det.nb, th, mode_mask, nbins_coarse)
+        self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int64))
+        self.det = det
+        h = _P()
+        _check(lib().pe_hetero_create(det.handle, _ptr(th), int(mode_mask), _ptr(self.edges), int(self.edges.size),
+                                      C.byref(h)))
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pe_hetero_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pe_hetero_loglike_batch(hs, theta, B: int, out_logl, out_dhhh=None, out_status=None, stream=None):
+    _check(lib().pe_hetero_loglike_batch(_handles(hs), len(hs), _ptr(theta), int(B), _ptr(out_logl), _ptr(out_dhhh),
+                                         _ptr(out_status), _stream(stream)))
+
+
+def hetero_loglike(hets, theta, dhhh: bool = False, status: bool = False, stream=None):
+    """Heterodyned log L of a batch (numpy host path or CUDA tensors, as loglike)."""
+    hs = [h.handle for h in hets]
+    if isinstance(theta, np.ndarray):
+        th = np.ascontiguousarray(theta.reshape(-1, NPARAM).astype(np.float64))
+        B = th.shape[0]
+        ll = np.zeros(B)
+        dh = np.zeros((B, len(hs), 3, 2)) if dhhh else None
+        st = np.zeros(B, dtype=np.int32) if status else None
+    else:
+        import torch
+        th = theta.reshape(-1, NPARAM).contiguous()
+        B = th.shape[0]
+        ll = torch.empty(B, dtype=torch.float64, device=th.device)
+        dh = torch.empty((B, len(hs), 3, 2), dtype=torch.float64, device=th.device) if dhhh else None
+        st = torch.empty(B, dtype=torch.int32, device=th.device) if status else None
+        if stream is None:
+            stream = torch.cuda.current_stream(th.device)
+    pe_hetero_loglike_batch(hs, th, B, ll, dh, st, stream)
+    res = {"logl": ll}
+    if dhhh:
+        res["dhhh"] = dh
+    if status:
+        res["status"] = st
+    return res

@@ -450,6 +450,27 @@ __device__ __forceinline__ void accum_bin(const DetDev& D, int b, const double2 
   }
 }
 
+// Block reduction of NV doubles per thread in a fixed tree order; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins / 32]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[i][wid] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = sh[i][0];
+      for (int w = 1; w < kTileBins / 32; ++w) s += sh[i][w];
+      v[i] = s;
+    }
+}
+
 // A/E/T combinations (without Q n_c): B_A = Z' - X', B_E = X' - 2Y' + Z', B_T = X' + Y' + Z'.
 __device__ __forceinline__ void aet_from_xyz(const double2 x[3], double2 o[3]) {
   o[0] = csub(x[2], x[0]);

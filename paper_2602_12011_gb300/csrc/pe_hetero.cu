@@ -1,0 +1,507 @@
+// pe_hetero.cu -- heterodyned (relative-binning) log-likelihood (the heterodyning idea of Sec. 1,
+// in the per-mode relative-binning form of Zackay, Dai & Venumadhav 2018 / Leslie, Dai & Pratten
+// 2021): host edge construction, summary-data kernels and the per-sample kernel, plus the C ABI.
+//
+//   k_mode_brackets  reference per-mode A/E/T brackets on the fine bins [0, K) (creation)
+//   k_het_summary    per coarse bin: A_o (o = 0, 1) and B_o (o = 0, 1, 2) by sequential sums
+//   k_het_loglike    one CTA per sample: ratios at every edge of every detector (shared memory),
+//                    then the per-bin contraction and a fixed-order block reduction
+//
+// The brackets B_c (A/E/T combinations of X', Y', Z' before the factor Q n_c) stand for the channel
+// signals: ratios are the same, and dg = conj(d) w Q n_c, gg = w |Q|^2 n_c^2 supply the rest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "pe_device.cuh"
+#include "pe_internal.h"
+#include "pe_kernels.h"
+#include "pespace_gb300.h"
+
+namespace pe {
+
+constexpr int kHetMaxEdges = 640;
+constexpr int kPairs = kNModes * (kNModes + 1) / 2;   // unordered mode pairs (md <= md2)
+
+__host__ __device__ constexpr int pair_index(int a, int b) {   // a <= b
+  return a * kNModes - a * (a - 1) / 2 + (b - a);
+}
+
+struct HetDev {
+  DetDev det;
+  const int* edge;       // [ne] fine-bin indices
+  const double* fe;      // [ne] edge frequencies
+  const double2* h0e;    // [ne][5][3] reference brackets at the edges
+  const int* src;        // [ne][5][3] edge whose ratio applies (carry-forward), -1 for none
+  const double2* A;      // [ne-1][5][3][2]
+  const double2* Bs;     // [ne-1][kPairs][3][3]
+  int ne;
+  unsigned mask;
+};
+struct HetSet {
+  HetDev h[kMaxDet];
+  int n;
+};
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// Per-mode brackets of one sample at bin b (zero for inactive modes or bins past a mode's end).
+__device__ __forceinline__ void mode_brackets(const DetDev& D, const SampleCoef& S, int b, unsigned mask,
+                                              double2 o[kNModes][3], const double2* __restrict__ tab,
+                                              const double* __restrict__ pc) {
+  BinIn Bn;
+  load_bin(D, b, S.tc, Bn);
+#pragma unroll 1
+  for (int md = 0; md < kNModes; ++md) {
+    const ModeCoef& C = S.md[md];
+    XYZAcc a;
+    xyz_zero(a);
+    if ((mask >> md) & 1u && C.active && Bn.f < C.fend) mode_bin(D, S, C, Bn, a, tab, pc);
+    double2 x[3];
+    xyz_final(a, Bn.z, x);
+    aet_from_xyz(x, o[md]);
+  }
+}
+
+// Reference per-mode brackets on bins [0, K): out[(md*3 + c)*K + k].
+__global__ void k_mode_brackets(DetDev D, const SampleCoef* coef, int K, unsigned mask, double2* out) {
+  __shared__ double pc[kProj];
+  const SampleCoef& S = coef[0];
+  proj_prologue(D, S, pc);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double2 o[kNModes][3];
+  mode_brackets(D, S, k, mask, o, D.sct, pc);
+  for (int md = 0; md < kNModes; ++md)
+    for (int c = 0; c < 3; ++c) out[((size_t)md * 3 + c) * K + k] = o[md][c];
+}
+
+// h0e[(i*5 + md)*3 + c] = reference bracket (md, c) at edge i
+__global__ void k_gather_edges(const double2* hb, int K, const int* edge, int ne, double2* h0e) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ne * kNModes * 3) return;
+  const int i = j / (kNModes * 3), mc = j % (kNModes * 3);
+  h0e[j] = hb[(size_t)mc * K + edge[i]];
+}
+
+// Summary data: one thread per (coarse bin, quantity); a sequential sum over the bin's fine bins.
+// Quantities per bin: A: 5 modes x 3 channels x 2 orders; B: kPairs x 3 x 3 orders.
+__global__ void k_het_summary(DetDev D, const int* edge, const double* fe, int ne, const double2* h0, int K,
+                              double2* A, double2* Bs) {
+  constexpr int nA = kNModes * 3 * 2, nB = kPairs * 3 * 3;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nbin = ne - 1;
+  if (id >= (long long)nbin * (nA + nB)) return;
+  const int b = (int)(id / (nA + nB)), q = (int)(id % (nA + nB));
+  const int lo = edge[b], hi = edge[b + 1] + (b == nbin - 1 ? 1 : 0);
+  double2 acc = make_double2(0.0, 0.0);
+  if (q < nA) {
+    const int md = q / 6, c = (q / 2) % 3, o = q % 2;
+    const double2* h = h0 + ((size_t)md * 3 + c) * K;
+    for (int k = lo; k < hi; ++k) {
+      const double df = D.f[k] - fe[b];
+      const double2 t = cmul(D.dg[c * D.nb + k], h[k]);   // conj(d) w Q n_c B0
+      const double s = (o == 0) ? 1.0 : df;
+      acc.x = fma(t.x, s, acc.x);
+      acc.y = fma(t.y, s, acc.y);
+    }
+    A[(((size_t)b * kNModes + md) * 3 + c) * 2 + o] = acc;
+  } else {
+    const int r = q - nA;
+    const int p = r / 9, c = (r / 3) % 3, o = r % 3;
+    int m1 = 0, m2 = 0;
+    for (int a = 0; a < kNModes; ++a)
+      for (int bb = a; bb < kNModes; ++bb)
+        if (pair_index(a, bb) == p) { m1 = a; m2 = bb; }
+    const double2* h1 = h0 + ((size_t)m1 * 3 + c) * K;
+    const double2* h2 = h0 + ((size_t)m2 * 3 + c) * K;
+    for (int k = lo; k < hi; ++k) {
+      const double df = D.f[k] - fe[b];
+      const double s = D.gg[c * D.nb + k] * (o == 0 ? 1.0 : (o == 1 ? df : df * df));
+      const double2 t = cmul(h1[k], cconj(h2[k]));
+      acc.x = fma(t.x, s, acc.x);
+      acc.y = fma(t.y, s, acc.y);
+    }
+    Bs[(((size_t)b * kPairs + p) * 3 + c) * 3 + o] = acc;
+  }
+}
+
+// One CTA of kTileBins threads per sample. Dynamic shared memory: [max ne][5][3] double2 ratios.
+__global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, const SampleCoef* __restrict__ coef,
+                                                           double* logl, double* dhhh) {
+  extern __shared__ double2 rsh[];
+  __shared__ double pc[kProj];
+  __shared__ double sh[6][kTileBins / 32];
+  __shared__ double2 stab[kSinTab];
+  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = hs.h[0].det.sct[i];
+  const int s = blockIdx.x;
+  const SampleCoef& S = coef[s];
+  double L = 0.0;
+  for (int I = 0; I < hs.n; ++I) {
+    const HetDev& H = hs.h[I];
+    const DetDev& D = H.det;
+    proj_prologue(D, S, pc);   // its barriers also order the table staging and the previous detector
+    for (int e = threadIdx.x; e < H.ne; e += blockDim.x) {
+      bool need = false;
+      for (int j = 0; j < kNModes * 3; ++j) need |= (H.src[e * kNModes * 3 + j] == e);
+      if (!need) continue;
+      double2 o[kNModes][3];
+      mode_brackets(D, S, H.edge[e], H.mask, o, stab, pc);
+      for (int md = 0; md < kNModes; ++md)
+        for (int c = 0; c < 3; ++c) {
+          const int j = (e * kNModes + md) * 3 + c;
+          if (H.src[j] == e) rsh[j] = cdiv(o[md][c], H.h0e[j]);
+        }
+    }
+    __syncthreads();
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < H.ne - 1; b += blockDim.x) {
+      const double idf = 1.0 / (H.fe[b + 1] - H.fe[b]);
+#pragma unroll 1
+      for (int c = 0; c < 3; ++c) {
+        double2 r0[kNModes], r1[kNModes];
+        for (int md = 0; md < kNModes; ++md) {
+          const int s0 = H.src[(b * kNModes + md) * 3 + c], s1 = H.src[((b + 1) * kNModes + md) * 3 + c];
+          const double2 ra = s0 >= 0 ? rsh[(s0 * kNModes + md) * 3 + c] : make_double2(0.0, 0.0);
+          const double2 rb = s1 >= 0 ? rsh[(s1 * kNModes + md) * 3 + c] : make_double2(0.0, 0.0);
+          r0[md] = ra;
+          r1[md] = make_double2((rb.x - ra.x) * idf, (rb.y - ra.y) * idf);
+        }
+        double dh = 0.0, hh = 0.0;
+        for (int md = 0; md < kNModes; ++md) {
+          const double2 a0 = H.A[(((size_t)b * kNModes + md) * 3 + c) * 2 + 0];
+          const double2 a1 = H.A[(((size_t)b * kNModes + md) * 3 + c) * 2 + 1];
+          dh += cmul(a0, r0[md]).x + cmul(a1, r1[md]).x;
+          for (int m2 = md; m2 < kNModes; ++m2) {
+            const double2* q = H.Bs + (((size_t)b * kPairs + pair_index(md, m2)) * 3 + c) * 3;
+            const double2 t0 = cmul(r0[md], cconj(r0[m2]));
+            const double2 t1 = cadd(cmul(r1[md], cconj(r0[m2])), cmul(r0[md], cconj(r1[m2])));
+            const double2 t2 = cmul(r1[md], cconj(r1[m2]));
+            const double x = cmul(q[0], t0).x + cmul(q[1], t1).x + cmul(q[2], t2).x;
+            hh += (md == m2) ? x : 2.0 * x;
+          }
+        }
+        v[c] += dh;
+        v[3 + c] += hh;
+      }
+    }
+    block_sum<6>(v, sh);
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < 3; ++c) {
+        L += v[c] - 0.5 * v[3 + c] - 0.5 * D.dd[c];
+        if (dhhh) {
+          dhhh[(((size_t)s * hs.n + I) * 3 + c) * 2 + 0] = v[c];
+          dhhh[(((size_t)s * hs.n + I) * 3 + c) * 2 + 1] = v[3 + c];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) logl[s] = S.valid ? L : -INFINITY;
+}
+
+}  // namespace pe
+
+// ------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------
+struct pe_hetero_s {
+  pe::HetDev dev;
+  void* mem;
+  int device;
+};
+
+namespace {
+
+constexpr double kMsunSh = 4.925490947641267e-6;
+const double kGam[5] = {-5.0 / 3.0, -2.0 / 3.0, 1.0, 5.0 / 3.0, 7.0 / 3.0};
+const int kModeMh[pe::kNModes] = {2, 1, 3, 2, 4};
+
+double phase_metric(double f, double flo, double fhi) {
+  double s = 0.0;
+  for (double g : kGam) s += (g < 0 ? -1.0 : 1.0) * std::pow(f / (g < 0 ? flo : fhi), g);
+  return s;
+}
+double fisco_of(const double* th) { return std::pow(6.0, -1.5) / (2.0 * pe::kPi * th[0] * kMsunSh); }
+
+// Taper marks 1 - 0.1 * 0.7^j (j = 0..10) of m F_isco, as grid indices; kend: last bin below it.
+void taper_marks(double T, long long k0, double fisco, int m, long long ks[11], long long* kend) {
+  const double fe = m * fisco;
+  for (int j = 0; j < 11; ++j) ks[j] = (long long)std::ceil((1.0 - 0.1 * std::pow(0.7, j)) * fe * T) - k0;
+  *kend = (long long)std::ceil(fe * T) - k0 - 1;
+}
+
+bool mask_ok(unsigned m) { return m != 0u && (m & ~PE_MODE_ALL) == 0u; }
+
+pe_status herr(pe_status st, const char* msg) { return pe::set_error(st, msg); }
+
+}  // namespace
+
+extern "C" {
+
+pe_status pe_hetero_default_edges(double T_obs, int64_t k0, int64_t nbins, const double* theta0, unsigned mode_mask,
+                                  int nbins_coarse, int64_t* out_edges, int* inout_n) {
+  if (theta0 == nullptr || out_edges == nullptr || inout_n == nullptr)
+    return herr(PE_EINVAL, "pe_hetero_default_edges: NULL argument");
+  if (!(T_obs > 0.0) || k0 < 1 || nbins < 2 || nbins_coarse < 1 || !mask_ok(mode_mask) || !(theta0[0] > 0.0))
+    return herr(PE_EINVAL, "pe_hetero_default_edges: bad grid, mask, theta0 or bin count");
+  const double fisco = fisco_of(theta0);
+  double fend = 0.0;
+  for (int md = 0; md < pe::kNModes; ++md)
+    if ((mode_mask >> md) & 1u) fend = std::max(fend, kModeMh[md] * fisco);
+  const long long kmax = std::min<long long>(nbins - 1, (long long)std::ceil(fend * T_obs) - k0 - 1);
+  if (kmax < 1) return herr(PE_EINVAL, "pe_hetero_default_edges: the reference's band ends below the grid");
+  const double flo = k0 / T_obs, fhi = (k0 + kmax) / T_obs;
+  const double p0 = phase_metric(flo, flo, fhi), p1 = phase_metric(fhi, flo, fhi);
+  std::set<long long> cand = {0, kmax};
+  for (int j = 1; j < nbins_coarse; ++j) {
+    const double target = p0 + (p1 - p0) * j / nbins_coarse;
+    double a = flo, b = fhi;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (phase_metric(mid, flo, fhi) < target) a = mid; else b = mid;
+    }
+    cand.insert((long long)std::llround(0.5 * (a + b) * T_obs) - k0);
+  }
+  std::vector<std::pair<long long, long long>> forbid;   // (last mark, kend) per mode
+  for (int md = 0; md < pe::kNModes; ++md) {
+    if (!((mode_mask >> md) & 1u)) continue;
+    long long ks[11], kend;
+    taper_marks(T_obs, k0, fisco, kModeMh[md], ks, &kend);
+    for (long long k : ks) cand.insert(k);
+    forbid.push_back({ks[10], kend});
+  }
+  std::vector<int64_t> keep;
+  for (long long k : cand) {
+    if (k < 0 || k > kmax) continue;
+    bool bad = false;
+    if (k != kmax)
+      for (auto& fb : forbid) bad |= (k > fb.first && k <= fb.second);
+    if (!bad) keep.push_back(k);
+  }
+  if ((int)keep.size() > *inout_n) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "pe_hetero_default_edges: %zu edges do not fit in %d", keep.size(), *inout_n);
+    return herr(PE_EINVAL, msg);
+  }
+  std::copy(keep.begin(), keep.end(), out_edges);
+  *inout_n = (int)keep.size();
+  return PE_OK;
+}
+
+pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_mask, const int64_t* edges,
+                           int nedges, pe_hetero* out) {
+  if (out == nullptr || theta0 == nullptr || edges == nullptr) return herr(PE_EINVAL, "pe_hetero_create: NULL argument");
+  *out = nullptr;
+  if (!mask_ok(mode_mask)) return herr(PE_EINVAL, "pe_hetero_create: bad mode mask (no precision flag)");
+  pe::DetSet ds;
+  pe_status s0 = pe::detset_from_handles(&det, 1, &ds);
+  if (s0 != PE_OK) return s0;
+  const pe::DetDev& D = ds.d[0];
+  const int ne = nedges;
+  if (ne < 2 || ne > pe::kHetMaxEdges) return herr(PE_EINVAL, "pe_hetero_create: nedges outside [2, 640]");
+  for (int i = 0; i < ne; ++i) {
+    if (edges[i] < 0 || edges[i] >= D.nb || (i > 0 && edges[i] <= edges[i - 1]))
+      return herr(PE_EINVAL, "pe_hetero_create: edges must increase strictly inside the grid");
+  }
+  for (int i = 0; i < PE_NPARAM; ++i)
+    if (!std::isfinite(theta0[i])) return herr(PE_EINVAL, "pe_hetero_create: theta0 is not finite");
+  const int K = (int)edges[ne - 1] + 1;
+  const int nb = ne - 1;
+  // one allocation: edge [ne] int, src [ne][5][3] int, fe [ne] double, h0e [ne][15], A [nb][30], Bs [nb][kPairs*9]
+  auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_edge = 0;
+  const size_t o_src = a256(o_edge + ne * sizeof(int));
+  const size_t o_fe = a256(o_src + (size_t)ne * 15 * sizeof(int));
+  const size_t o_h0e = a256(o_fe + ne * sizeof(double));
+  const size_t o_A = a256(o_h0e + (size_t)ne * 15 * sizeof(double2));
+  const size_t o_B = a256(o_A + (size_t)nb * 30 * sizeof(double2));
+  const size_t bytes = o_B + (size_t)nb * pe::kPairs * 9 * sizeof(double2);
+  pe_hetero_s* h = new (std::nothrow) pe_hetero_s();
+  if (!h) return herr(PE_ENOMEM, "pe_hetero_create: host allocation failed");
+  cudaGetDevice(&h->device);
+  if (cudaMalloc(&h->mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return herr(PE_ENOMEM, "pe_hetero_create: device allocation failed");
+  }
+  unsigned char* base = static_cast<unsigned char*>(h->mem);
+  int* d_edge = reinterpret_cast<int*>(base + o_edge);
+  int* d_src = reinterpret_cast<int*>(base + o_src);
+  double* d_fe = reinterpret_cast<double*>(base + o_fe);
+  double2* d_h0e = reinterpret_cast<double2*>(base + o_h0e);
+  double2* d_A = reinterpret_cast<double2*>(base + o_A);
+  double2* d_B = reinterpret_cast<double2*>(base + o_B);
+  std::vector<int> he(ne);
+  std::vector<double> hfe(ne);
+  for (int i = 0; i < ne; ++i) {
+    he[i] = (int)edges[i];
+    hfe[i] = double(D.k0 + edges[i]) / D.T;
+  }
+  double* th0 = nullptr;
+  pe::SampleCoef* coef = nullptr;
+  int* nend = nullptr;
+  double2* hb = nullptr;
+  cudaError_t e = cudaMalloc(&th0, PE_NPARAM * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&coef, sizeof(pe::SampleCoef));
+  if (e == cudaSuccess) e = cudaMalloc(&nend, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&hb, (size_t)pe::kNModes * 3 * K * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemcpy(th0, theta0, PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_edge, he.data(), ne * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_fe, hfe.data(), ne * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pe::launch_prep(th0, 1, mode_mask, ds, coef, nend, nullptr, 0);
+  if (e == cudaSuccess) {
+    pe::k_mode_brackets<<<(K + pe::kTileBins - 1) / pe::kTileBins, pe::kTileBins>>>(D, coef, K, mode_mask, hb);
+    e = cudaGetLastError();
+  }
+  // reference brackets at the edges, and the carry-forward sources
+  std::vector<double2> h0e((size_t)ne * 15);
+  if (e == cudaSuccess) {
+    pe::k_gather_edges<<<(ne * 15 + 127) / 128, 128>>>(hb, K, d_edge, ne, d_h0e);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h0e.data(), d_h0e, h0e.size() * sizeof(double2), cudaMemcpyDeviceToHost);
+  std::vector<int> src((size_t)ne * 15, -1);
+  if (e == cudaSuccess) {
+    const double fisco = fisco_of(theta0);
+    for (int md = 0; md < pe::kNModes; ++md) {
+      long long klast = -1;
+      if ((mode_mask >> md) & 1u) {
+        long long ks[11], kend;
+        taper_marks(D.T, D.k0, fisco, kModeMh[md], ks, &kend);
+        klast = ks[10];
+      }
+      for (int c = 0; c < 3; ++c)
+        for (int i = 0; i < ne; ++i) {
+          const size_t j = ((size_t)i * pe::kNModes + md) * 3 + c;
+          const bool ok = he[i] <= klast && (h0e[j].x != 0.0 || h0e[j].y != 0.0);
+          src[j] = ok ? i : (i > 0 ? src[j - 15] : -1);
+        }
+    }
+    e = cudaMemcpy(d_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    const long long n = (long long)nb * (30 + pe::kPairs * 9);
+    pe::k_het_summary<<<(unsigned)((n + 127) / 128), 128>>>(D, d_edge, d_fe, ne, hb, K, d_A, d_B);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(th0);
+  cudaFree(coef);
+  cudaFree(nend);
+  cudaFree(hb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->mem);
+    delete h;
+    char msg[200];
+    snprintf(msg, sizeof(msg), "pe_hetero_create: %s", cudaGetErrorString(e));
+    return herr(PE_ECUDA, msg);
+  }
+  h->dev.det = D;
+  h->dev.edge = d_edge;
+  h->dev.fe = d_fe;
+  h->dev.h0e = d_h0e;
+  h->dev.src = d_src;
+  h->dev.A = d_A;
+  h->dev.Bs = d_B;
+  h->dev.ne = ne;
+  h->dev.mask = mode_mask;
+  *out = h;
+  return PE_OK;
+}
+
+pe_status pe_hetero_destroy(pe_hetero h) {
+  if (h == nullptr) return PE_OK;
+  cudaDeviceSynchronize();
+  cudaFree(h->mem);
+  cudaGetLastError();
+  delete h;
+  return PE_OK;
+}
+
+pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double* theta, int B, double* out_logl,
+                                  double* out_dhhh, int32_t* out_status, void* stream) {
+  if (hets == nullptr || theta == nullptr || out_logl == nullptr) return herr(PE_EINVAL, "pe_hetero_loglike_batch: NULL");
+  if (ndet < 1 || ndet > pe::kMaxDet) return herr(PE_EINVAL, "pe_hetero_loglike_batch: ndet outside [1, 8]");
+  if (B < 1 || B > (1 << 20)) return herr(PE_EINVAL, "pe_hetero_loglike_batch: B outside [1, 2^20]");
+  pe::HetSet hs;
+  memset(&hs, 0, sizeof(hs));
+  pe::DetSet ds;
+  memset(&ds, 0, sizeof(ds));
+  hs.n = ndet;
+  ds.ndet = ndet;
+  int dev = 0, nemax = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < ndet; ++i) {
+    if (hets[i] == nullptr) return herr(PE_EINVAL, "pe_hetero_loglike_batch: NULL handle");
+    if (hets[i]->device != dev) return herr(PE_EINVAL, "pe_hetero_loglike_batch: handle on another device");
+    if (hets[i]->dev.mask != hets[0]->dev.mask) return herr(PE_EINVAL, "pe_hetero_loglike_batch: mode masks differ");
+    hs.h[i] = hets[i]->dev;
+    ds.d[i] = hets[i]->dev.det;
+    nemax = std::max(nemax, hets[i]->dev.ne);
+  }
+  auto is_dev = [](const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  };
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<void*> bufs;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t n) {
+    if (e != cudaSuccess) return;
+    e = cudaMallocAsync(p, n + 16, st);
+    if (e == cudaSuccess) bufs.push_back(*p);
+  };
+  const double* th = theta;
+  if (!is_dev(theta)) {
+    void* t = nullptr;
+    alloc(&t, (size_t)B * PE_NPARAM * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st);
+    th = static_cast<const double*>(t);
+  }
+  void *coef = nullptr, *nend = nullptr, *ll = out_logl, *dh = out_dhhh, *stt = out_status;
+  alloc(&coef, (size_t)B * sizeof(pe::SampleCoef));
+  alloc(&nend, (size_t)B * ndet * sizeof(int));
+  const bool hl = !is_dev(out_logl), hd = out_dhhh && !is_dev(out_dhhh), hsx = out_status && !is_dev(out_status);
+  if (hl) alloc(&ll, (size_t)B * sizeof(double));
+  if (hd) alloc(&dh, (size_t)B * ndet * 6 * sizeof(double));
+  if (hsx) alloc(&stt, (size_t)B * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = pe::launch_prep(th, B, hets[0]->dev.mask, ds, static_cast<pe::SampleCoef*>(coef), static_cast<int*>(nend),
+                        static_cast<int*>(stt), st);
+  const size_t smem = (size_t)nemax * pe::kNModes * 3 * sizeof(double2);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pe::k_het_loglike, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    pe::k_het_loglike<<<B, pe::kTileBins, smem, st>>>(hs, B, static_cast<const pe::SampleCoef*>(coef),
+                                                      static_cast<double*>(ll), static_cast<double*>(dh));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && hl) e = cudaMemcpyAsync(out_logl, ll, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && hd)
+    e = cudaMemcpyAsync(out_dhhh, dh, (size_t)B * ndet * 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && hsx) e = cudaMemcpyAsync(out_status, stt, (size_t)B * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  for (void* p : bufs) cudaFreeAsync(p, st);
+  if (e == cudaSuccess && (hl || hd || hsx)) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char msg[200];
+    snprintf(msg, sizeof(msg), "pe_hetero_loglike_batch: %s", cudaGetErrorString(e));
+    return herr(PE_ECUDA, msg);
+  }
+  return PE_OK;
+}
+
+}  // extern "C"

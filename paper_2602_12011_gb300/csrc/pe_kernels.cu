@@ -296,27 +296,6 @@ __device__ __forceinline__ int find_pair(const long long* off, int P, long long 
   return lo;
 }
 
-// Block reduction of NV doubles per thread in a fixed tree order; result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins / 32]) {
-#pragma unroll
-  for (int i = 0; i < NV; ++i)
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh[i][wid] = v[i];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double s = sh[i][0];
-      for (int w = 1; w < kTileBins / 32; ++w) s += sh[i][w];
-      v[i] = s;
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // Rows A2-A7: persistent fused kernel. Work item = one tile of fwd_tile_bins(PREC) bins of one
 // (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns every

@@ -63,3 +63,32 @@ def test_product_binding_never_imports_the_oracle():
         if path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
             src = open(path).read()
             assert "oracle" not in re.sub(r"#.*|//.*", "", src).lower() or path.endswith("workloads.py"), path
+
+
+@pytest.mark.parametrize("T,mask,nbins", [(2.0 ** 17, 0x1F, 64), (2.0 ** 22, 0x1F, 256), (2.0 ** 20, 0x01, 128)])
+def test_hetero_default_edges_match_the_oracle(lib, oracle_mod, T, mask, nbins):
+    """pe_hetero_default_edges is host code (no GPU): the same edges as the oracle's construction."""
+    import numpy as np
+    from oracle import hetero as HT
+    from paper_2602_12011_gb300 import workloads as W
+    k0, nb = W.grid(T)
+    th0 = W.theta_injection(T)
+    mine = L.pe_hetero_default_edges(T, k0, nb, th0, mask, nbins)
+    ref = HT.default_edges(T, k0, nb, th0, mask, nbins)
+    assert np.array_equal(mine, ref)
+
+
+def test_hetero_argument_errors_without_cuda(lib):
+    import numpy as np
+    th = np.array([1e6, 2, 0, 0, 1, 0, 0, 0, 0, 0, 0.0])
+    with pytest.raises(L.PeError) as e:
+        L.pe_hetero_default_edges(2.0 ** 16, 7, 3000, th, 0x40, 32)
+    assert e.value.status == L.PE_EINVAL
+    out = np.zeros(2, dtype=np.int64)
+    n = C.c_int(2)
+    assert lib.pe_hetero_default_edges(2.0 ** 16, 7, 3000, L._ptr(th), 0x1F, 32, L._ptr(out), C.byref(n)) == L.PE_EINVAL
+    assert b"do not fit" in lib.pe_last_error()
+    h = C.c_void_p()
+    assert lib.pe_hetero_create(None, None, 0x1F, None, 0, C.byref(h)) == L.PE_EINVAL
+    assert lib.pe_hetero_loglike_batch(None, 1, None, 1, None, None, None, None) == L.PE_EINVAL
+    assert lib.pe_hetero_destroy(None) == L.PE_OK
