@@ -166,6 +166,16 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
     S.md[md].cmw = to_dw(val(S.md[md].cm));
     S.md[md].ampw = to_dw(val(S.md[md].amp) * S.hsc);
   }
+  S.pair32 = (S.md[0].active && S.md[3].active) ? 1 : 0;
+  S.k32 = make_double2(0.0, 0.0);
+  if (S.pair32) {
+    double sd, cd;
+    sincospi(2.0 * (val(S.md[3].ph0) - val(S.md[0].ph0)), &sd, &cd);
+    const double r = val(S.md[3].amp) / val(S.md[0].amp);
+    S.k32 = make_double2(r * cd, r * sd);
+  }
+  S.k32w[0] = to_dw(S.k32.x);
+  S.k32w[1] = to_dw(S.k32.y);
 }
 
 __device__ inline void sample_prep(const double* th, unsigned mask, SampleCoef& S) {
@@ -314,8 +324,10 @@ struct BinIn {
 // n_l = (x_r - x_s)/|x_r - x_s|, geometry at the mode's t_f, and the centre Doppler phase
 // e^{-2 pi i f k.x_c} folded into the mode's phase. Written as X' = P_X + z Q_X with
 // P_X = G31 s+31 - G12 s-12, Q_X = G31 s-31 - G12 s+12 (and cyclically for Y', Z').
+// C2 (nullable): a second mode with the same m, evaluated with this one's geometry (see k32).
 __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
-                                         XYZAcc& acc, const double2* __restrict__ tab, const double* __restrict__ pc) {
+                                         XYZAcc& acc, const double2* __restrict__ tab, const double* __restrict__ pc,
+                                         const ModeCoef* C2 = nullptr) {
   // --- waveform and time-frequency map (rows A2, A3)
   const double v = C.cm * B.f13;
   const double iv = C.icm * B.fm13;
@@ -349,6 +361,14 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   double sph, cph;
   sincos_turns(ph, tab, &sph, &cph);
   const double2 H = make_double2(amp * cph, amp * sph);
+  // paired second mode: complex polarisation weights Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
+  double2 Ap = make_double2(C.Pp, 0.0), Ac = make_double2(C.Pc, 0.0);
+  if (C2) {
+    const double v2 = v * v;
+    const double kr = S.k32.x * v2, ki = S.k32.y * v2;
+    Ap = make_double2(fma(kr, C2->Pp, C.Pp), ki * C2->Pp);
+    Ac = make_double2(fma(kr, C2->Pc, C.Pc), ki * C2->Pc);
+  }
   // third-spacecraft phases e^{i pi f k.delta_t}; the offsets sum to zero, so E_2 = conj(E_0 E_1)
   double2 E[3];
 #pragma unroll
@@ -368,7 +388,9 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     const double inv = rsqrt(fma(knr, knr, fma(npr, npr, nqr * nqr)));
     const double kn = knr * inv;
     const double np = npr * inv, nq = nqr * inv;
-    const double2 gam = make_double2(C.Pp * (np * np - nq * nq), C.Pc * 2.0 * np * nq);
+    const double Fp = np * np - nq * nq, Fc = 2.0 * np * nq;
+    const double2 gam = C2 ? make_double2(fma(Ap.x, Fp, -Ac.y * Fc), fma(Ap.y, Fp, Ac.x * Fc))
+                           : make_double2(C.Pp * Fp, C.Pc * Fc);
     G[l] = cmul(E[t], cmul(gam, H));
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (most bins of a massive-binary
     // signal), else from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
@@ -423,6 +445,19 @@ __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinI
   B.frc = (pr - rint(pr)) + er;
 }
 
+// Adds every active mode of one sample at one bin to a; (2,2) and (3,2) go through one unit when
+// both are active (pair32).
+__device__ __forceinline__ void bin_modes(const DetDev& D, const SampleCoef& S, const BinIn& B, XYZAcc& a,
+                                          const double2* __restrict__ tab, const double* __restrict__ pc) {
+#pragma unroll 1
+  for (int md = 0; md < kNModes; ++md) {
+    if (md == 3 && S.pair32) continue;
+    const ModeCoef& C = S.md[md];
+    if (!C.active || !(B.f < C.fend)) continue;
+    mode_bin(D, S, C, B, a, tab, pc, (md == 0 && S.pair32) ? &S.md[3] : nullptr);
+  }
+}
+
 // Mode-summed TDI brackets X', Y', Z' of one sample at one bin.
 __device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, int b, double2 acc[3],
                                         const double2* __restrict__ tab, const double* __restrict__ pc) {
@@ -430,12 +465,7 @@ __device__ __forceinline__ void bin_xyz(const DetDev& D, const SampleCoef& S, in
   load_bin(D, b, S.tc, B);
   XYZAcc a;
   xyz_zero(a);
-#pragma unroll 1
-  for (int md = 0; md < kNModes; ++md) {
-    const ModeCoef& C = S.md[md];
-    if (!C.active || !(B.f < C.fend)) continue;
-    mode_bin(D, S, C, B, a, tab, pc);
-  }
+  bin_modes(D, S, B, a, tab, pc);
   xyz_final(a, B.z, acc);
 }
 

@@ -82,9 +82,10 @@ __device__ __forceinline__ df dw_dot5(const float2* p, const df b[4]) {
 // double -> double word of the fraction x - rint(x) (exact in FP64), for the sincos of a turn count
 __device__ __forceinline__ df frac_dw(double x) { return df_from_bits(x - rint(x)); }
 
+// C2 (nullable): a second mode with the same m, evaluated with this one's geometry (see k32).
 __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
                                                const BinW& W, MixAcc& acc, const float4* __restrict__ tab,
-                                               const float2* __restrict__ pcw) {
+                                               const float2* __restrict__ pcw, const ModeCoef* C2 = nullptr) {
   // --- waveform and time-frequency map (FP64; rows A2, A3)
   const double v = C.cm * B.f13;
   const double iv = C.icm * B.fm13;
@@ -103,6 +104,15 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   const double tf = fma(C.tffac * B.invf, dv, S.tc);
   // amplitude (times hsc) in double words: ampw f^(-7/6) v^p, times the taper where it is below 1
   df A = df_mul(C.ampw, W.fm76);
+  // paired second mode: complex polarisation weights Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
+  cdf Ap = {C.Ppw, df_make(0.f, 0.f)}, Ac = {C.Pcw, df_make(0.f, 0.f)};
+  if (C2) {
+    const df vw = df_mul(C.cmw, W.f13);
+    const df v2 = df_mul(vw, vw);
+    const df kr = df_mul(S.k32w[0], v2), ki = df_mul(S.k32w[1], v2);
+    Ap = cdf{df_add_s(C.Ppw, df_mul(kr, C2->Ppw)), df_mul(ki, C2->Ppw)};
+    Ac = cdf{df_add_s(C.Pcw, df_mul(kr, C2->Pcw)), df_mul(ki, C2->Pcw)};
+  }
   if (C.p >= 1) {
     const df vw = df_mul(C.cmw, W.f13);
     A = df_mul(A, vw);
@@ -155,7 +165,8 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     const df nq = df_mul(nqr, inv);
     const df Fp = df_sub_s(df_mul(np, np), df_mul(nq, nq));
     const df Fc = df_scale2(df_mul(np, nq), 2.0f);
-    const cdf gam = {df_mul(C.Ppw, Fp), df_mul(C.Pcw, Fc)};
+    const cdf gam = C2 ? cdf{df_sub_s(df_mul(Ap.re, Fp), df_mul(Ac.im, Fc)), df_add_s(df_mul(Ap.im, Fp), df_mul(Ac.re, Fc))}
+                       : cdf{df_mul(C.Ppw, Fp), df_mul(C.Pcw, Fc)};
     G[l] = cdf_mul(E[t], cdf_mul(gam, H));
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (|u| <= 2a < 1), else from
     // sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
@@ -203,9 +214,10 @@ __device__ __forceinline__ void bin_xyz_mixed(const DetDev& D, const SampleCoef&
   mix_zero(a);
 #pragma unroll 1
   for (int md = 0; md < kNModes; ++md) {
+    if (md == 3 && S.pair32) continue;
     const ModeCoef& C = S.md[md];
     if (!C.active || !(B.f < C.fend)) continue;
-    mode_bin_mixed(D, S, C, B, W, a, tab, pcw);
+    mode_bin_mixed(D, S, C, B, W, a, tab, pcw, (md == 0 && S.pair32) ? &S.md[3] : nullptr);
   }
   const float4 zz = D.zw[b];
   mix_final(a, cdf{df_make(zz.x, zz.y), df_make(zz.z, zz.w)}, x);

@@ -132,9 +132,7 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
       load_bin(D, b, S.tc, Bn);
       XYZAcc xa;
       xyz_zero(xa);
-#pragma unroll 1
-      for (int md = 0; md < kNModes; ++md)
-        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bin(D, S, S.md[md], Bn, xa, stab, pc);
+      bin_modes(D, S, Bn, xa, stab, pc);
       double2 x[3], o[3];
       xyz_final(xa, Bn.z, x);
       aet_from_xyz(x, o);

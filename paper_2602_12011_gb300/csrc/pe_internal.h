@@ -65,8 +65,14 @@ struct SampleCoefT {
                         // precision path carries amplitudes times hsc, keeping them far from the
                         // FP32 range limits
   ModeCoefT<T> md[kNModes];
+  // (3,2) shares m = 2 with (2,2), hence v, t_f, the taper and every geometric factor; its signal
+  // is k32 v^2 times that of (2,2) with its own polarisation weights, k32 = (amp_32 / amp_22)
+  // e^{2 pi i (ph0_32 - ph0_22)}. pair32 = 1 when both are active, and the units evaluate them
+  // together.
+  double2 k32;
+  float2 k32w[2];       // k32 (re, im) as double words
   int valid;
-  int pad_;
+  int pair32;
 };
 
 using ModeCoef = ModeCoefT<double>;

@@ -395,16 +395,17 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
       XYZAcc xpa;
       xyz_zero(xpa);
       const double u = 3.0 * Bn.lnf3;
+      if (sur) {
 #pragma unroll 1
-      for (int md = 0; md < kNModes; ++md) {
-        const ModeCoef& C = S.md[md];
-        if (!C.active || !(Bn.f < C.fend)) continue;
-        const size_t sys = ((size_t)I * B + s) * kNModes + md;
-        if (sur)
+        for (int md = 0; md < kNModes; ++md) {
+          const ModeCoef& C = S.md[md];
+          if (!C.active || !(Bn.f < C.fend)) continue;
+          const size_t sys = ((size_t)I * B + s) * kNModes + md;
           mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], xs,
                        stab);
-        if (!sur || mode == 1) mode_bin(D, S, C, Bn, xpa, stab, pc);
+        }
       }
+      if (!sur || mode == 1) bin_modes(D, S, Bn, xpa, stab, pc);   // the plain path, as k_loglike_fwd
       double2 xp[3];
       xyz_final(xpa, Bn.z, xp);
       double2 os[3], op[3];
