@@ -38,10 +38,12 @@ __device__ __forceinline__ double dsinc(double u, double cosu, double sincu) {
   return (cosu - sincu) / u;
 }
 
-// Reverse sweep of one unit. sX, sY, sZ: cotangents of this bin's brackets X', Y', Z'.
+// Reverse sweep of one unit. sX, sY, sZ: cotangents of this bin's brackets X', Y', Z'. md2 >= 0
+// adds a second mode with the same m through this unit (complex polarisation weights
+// Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2; see SampleCoefT::k32), as the forward unit does.
 __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, const SampleGrad& SG, int md,
                                          const BinIn& B, double2 sX, double2 sY, double2 sZ, GradAcc& g,
-                                         const double2* __restrict__ tab) {
+                                         const double2* __restrict__ tab, int md2 = -1) {
   const ModeCoef& C = S.md[md];
   const ModeGrad& CG = SG.md[md];
   // ---------------- forward recompute: waveform, t_f, amplitude, orbit, phase
@@ -124,7 +126,17 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
   double dlb[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) dlb[i][0] = dlb[i][1] = dlb[i][2] = 0.0;
-  double Ppb = 0.0, Pcb = 0.0;
+  // polarisation weights: Ap = Pp + kappa Pp2, Ac = Pc + kappa Pc2 (complex; kappa = 0 unpaired)
+  double2 kap = make_double2(0.0, 0.0);
+  double Pp2 = 0.0, Pc2 = 0.0;
+  if (md2 >= 0) {
+    kap = make_double2(S.k32.x * v * v, S.k32.y * v * v);
+    Pp2 = S.md[md2].Pp;
+    Pc2 = S.md[md2].Pc;
+  }
+  const double2 Ap = make_double2(fma(kap.x, Pp2, C.Pp), kap.y * Pp2);
+  const double2 Ac = make_double2(fma(kap.x, Pc2, C.Pc), kap.y * Pc2);
+  double2 Apb = make_double2(0.0, 0.0), Acb = make_double2(0.0, 0.0);
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int r = l, s = (l + 1) % 3, t = (l + 2) % 3;
@@ -139,7 +151,7 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double np = S.p[0] * n[0] + S.p[1] * n[1] + S.p[2] * n[2];
     const double nq = S.q[0] * n[0] + S.q[1] * n[1] + S.q[2] * n[2];
     const double Fp = np * np - nq * nq, Fc = 2.0 * np * nq;
-    const double2 gam = make_double2(C.Pp * Fp, C.Pc * Fc);
+    const double2 gam = make_double2(fma(Ap.x, Fp, -Ac.y * Fc), fma(Ap.y, Fp, Ac.x * Fc));
     const double2 E = Et[t];
     const double se = E.y, ce = E.x;
     const double2 K = cmul(gam, H);
@@ -182,9 +194,9 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double kdb = kPi * B.f * thb;
     const double2 gamb = cconjmul(Kb, H);
     Hb = cadd(Hb, cconjmul(Kb, gam));
-    Ppb += gamb.x * Fp;
-    Pcb += gamb.y * Fc;
-    const double Fpb = gamb.x * C.Pp, Fcb = gamb.y * C.Pc;
+    Apb = make_double2(fma(gamb.x, Fp, Apb.x), fma(gamb.y, Fp, Apb.y));
+    Acb = make_double2(fma(gamb.y, Fc, Acb.x), fma(-gamb.x, Fc, Acb.y));
+    const double Fpb = fma(gamb.x, Ap.x, gamb.y * Ap.y), Fcb = fma(gamb.y, Ac.x, -gamb.x * Ac.y);
     const double npb = 2.0 * (np * Fpb + nq * Fcb);
     const double nqb = 2.0 * (np * Fcb - nq * Fpb);
     double nb[3];
@@ -280,8 +292,20 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
   const double iv2 = iv * iv;
   g.c1 += psib * (SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv) - Db * (2.0 * SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv);
   g.c2 += psib * (SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv) - Db * (2.0 * SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv);
-  // polarisation weights
-  g.io += Ppb * CG.dPp_di + Pcb * CG.dPc_di;
+  // polarisation weights, and the paired mode: Ap = Pp + kappa Pp2, Ac = Pc + kappa Pc2
+  g.io += Apb.x * CG.dPp_di + Acb.x * CG.dPc_di;
+  if (md2 >= 0) {
+    const ModeGrad& CG2 = SG.md[md2];
+    g.io += (Apb.x * kap.x + Apb.y * kap.y) * CG2.dPp_di + (Acb.x * kap.x + Acb.y * kap.y) * CG2.dPc_di;
+    const double2 kb = make_double2(Apb.x * Pp2 + Acb.x * Pc2, Apb.y * Pp2 + Acb.y * Pc2);   // kappa-bar
+    // kappa = k32 v^2, k32 = (amp2 / amp1) e^{2 pi i (ph0_2 - ph0_1)}; the same m makes the phase
+    // difference and the v-scale independent of theta, so only ln(amp2 / amp1) varies (M, q)
+    const double lnrb = v * v * (kb.x * S.k32.x + kb.y * S.k32.y);
+    g.M = fma(lnrb, CG2.dlnA_dM - CG.dlnA_dM, g.M);
+    g.q = fma(lnrb, CG2.dlnA_dq - CG.dlnA_dq, g.q);
+    const double vkb = 2.0 * lnrb / v;   // d kappa / d v = 2 kappa / v
+    g.M = fma(vkb * B.f13, CG.dcm_dM, g.M);
+  }
 }
 
 // Contract one thread's accumulators with the sample's sky-frame derivatives into grad[11].

@@ -141,8 +141,11 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
       GradAcc g;
       gacc_zero(g);
 #pragma unroll 1
-      for (int md = 0; md < kNModes; ++md)
-        if (S.md[md].active && Bn.f < S.md[md].fend) mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, stab);
+      for (int md = 0; md < kNModes; ++md) {
+        if (md == 3 && S.pair32) continue;
+        if (S.md[md].active && Bn.f < S.md[md].fend)
+          mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, stab, (md == 0 && S.pair32) ? 3 : -1);
+      }
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
 #pragma unroll
       for (int i = 0; i < 3; ++i) { v[14 + i] = g.k[i]; v[17 + i] = g.p[i]; v[20 + i] = g.qv[i]; }
@@ -233,8 +236,11 @@ __global__ void __launch_bounds__(kFisherThreads) k_fisher_fwd(DetSet ds, int B,
         GradAcc g;
         gacc_zero(g);
 #pragma unroll 1
-        for (int md = 0; md < kNModes; ++md)
-          if (S.md[md].active && Bn.f < S.md[md].fend) mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, D.sct);
+        for (int md = 0; md < kNModes; ++md) {
+          if (md == 3 && S.pair32) continue;
+          if (S.md[md].active && Bn.f < S.md[md].fend)
+            mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, D.sct, (md == 0 && S.pair32) ? 3 : -1);
+        }
         double row[PE_NPARAM];
         gacc_to_theta(g, SG, row);
         for (int i = 0; i < PE_NPARAM; ++i) Js[j][i][tid] = row[i];
