@@ -158,7 +158,13 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double2 G = cmul(E, K);
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
     double sm, spl, dsm, dspl;   // sinc(u1), sinc(u2) and their derivatives
-    if (B.a < kSincPolyA) {
+    if (B.a < kSincPolyA8) {
+      sinc_poly_d_n<4>(u1, &sm, &dsm);
+      sinc_poly_d_n<4>(u2, &spl, &dspl);
+    } else if (B.a < kSincPolyA12) {
+      sinc_poly_d_n<6>(u1, &sm, &dsm);
+      sinc_poly_d_n<6>(u2, &spl, &dspl);
+    } else if (B.a < kSincPolyA) {
       sinc_poly_d(u1, &sm, &dsm);
       sinc_poly_d(u2, &spl, &dspl);
     } else {

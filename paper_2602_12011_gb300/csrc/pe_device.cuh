@@ -217,35 +217,52 @@ __device__ __forceinline__ double sinc_small(double u) {
   return 1.0 - u2 / 6.0 + u2 * u2 / 120.0 - u2 * u2 * u2 / 5040.0;
 }
 
-// sinc(u) = sum_k (-1)^k u^(2k) / (2k+1)! through u^16 (Horner in u^2), for |u| <= 1: the first
-// dropped term is below 1/19! = 8.2e-18, under half an ulp of sinc(u) >= sin 1.
-constexpr double kSincPolyA = 0.5;   // bins with a = pi f L below this take the polynomial (|u| <= 2a)
-__device__ __forceinline__ double sinc_poly(double u) {
+// sinc(u) = sum_k (-1)^k u^(2k) / (2k+1)! (Horner in x = u^2), for |u| <= 1: through u^16, where
+// the first dropped term is below 1/19! = 8.2e-18, under half an ulp of sinc(u) >= sin 1. Shorter
+// sums serve smaller |u|: through u^12 for |u| <= 0.4 (dropped term < 2e-18) and through u^8 for
+// |u| <= 0.1 (< 3e-18). The caller picks the length from the bin (|u| <= 2a, a = pi f L).
+constexpr double kSincPolyA = 0.5;   // bins with a below this take a polynomial
+constexpr double kSincPolyA12 = 0.2;
+constexpr double kSincPolyA8 = 0.05;
+template <int DEG>   // highest power of x kept: 8, 6 or 4
+__device__ __forceinline__ double sinc_poly_n(double u) {
   const double x = u * u;
-  double p = 1.0 / 355687428096000.0;             // 1/17!
-  p = fma(p, x, -1.0 / 1307674368000.0);          // 1/15!
-  p = fma(p, x, 1.0 / 6227020800.0);              // 1/13!
-  p = fma(p, x, -1.0 / 39916800.0);               // 1/11!
-  p = fma(p, x, 1.0 / 362880.0);                  // 1/9!
+  double p = DEG >= 8 ? 1.0 / 355687428096000.0 : (DEG >= 6 ? 1.0 / 6227020800.0 : 1.0 / 362880.0);
+  if (DEG >= 8) {
+    p = fma(p, x, -1.0 / 1307674368000.0);        // 1/15!
+    p = fma(p, x, 1.0 / 6227020800.0);            // 1/13!
+  }
+  if (DEG >= 6) {
+    p = fma(p, x, -1.0 / 39916800.0);             // 1/11!
+    p = fma(p, x, 1.0 / 362880.0);                // 1/9!
+  }
   p = fma(p, x, -1.0 / 5040.0);                   // 1/7!
   p = fma(p, x, 1.0 / 120.0);                     // 1/5!
   p = fma(p, x, -1.0 / 6.0);                      // 1/3!
   return fma(p, x, 1.0);
 }
-// sinc(u) and d sinc/du = u sum_{k>=1} 2k (-1)^k u^(2k-2) / (2k+1)! through the same order, |u| <= 1
-__device__ __forceinline__ void sinc_poly_d(double u, double* sv, double* dv) {
+__device__ __forceinline__ double sinc_poly(double u) { return sinc_poly_n<8>(u); }
+// sinc(u) and d sinc/du = u sum_{k>=1} 2k (-1)^k u^(2k-2) / (2k+1)! through the same order as
+// sinc_poly_n<DEG>
+template <int DEG>
+__device__ __forceinline__ void sinc_poly_d_n(double u, double* sv, double* dv) {
   const double x = u * u;
-  *sv = sinc_poly(u);
-  double q = 1.0 / 22230464256000.0;              // 16/17!
-  q = fma(q, x, -1.0 / 93405312000.0);            // 14/15!
-  q = fma(q, x, 1.0 / 518918400.0);               // 12/13!
-  q = fma(q, x, -1.0 / 3991680.0);                // 10/11!
-  q = fma(q, x, 1.0 / 45360.0);                   // 8/9!
+  *sv = sinc_poly_n<DEG>(u);
+  double q = DEG >= 8 ? 1.0 / 22230464256000.0 : (DEG >= 6 ? 1.0 / 518918400.0 : 1.0 / 45360.0);
+  if (DEG >= 8) {
+    q = fma(q, x, -1.0 / 93405312000.0);          // 14/15!
+    q = fma(q, x, 1.0 / 518918400.0);             // 12/13!
+  }
+  if (DEG >= 6) {
+    q = fma(q, x, -1.0 / 3991680.0);              // 10/11!
+    q = fma(q, x, 1.0 / 45360.0);                 // 8/9!
+  }
   q = fma(q, x, -1.0 / 840.0);                    // 6/7!
   q = fma(q, x, 1.0 / 30.0);                      // 4/5!
   q = fma(q, x, -1.0 / 3.0);                      // 2/3!
   *dv = u * q;
 }
+__device__ __forceinline__ void sinc_poly_d(double u, double* sv, double* dv) { sinc_poly_d_n<8>(u, sv, dv); }
 
 // Projections of the geometry on the sample's frame as linear forms in the orbit basis b
 // (DetDev::Mo), formed once per (detector, sample) tile into shared memory (kProj doubles):
@@ -396,7 +413,13 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     // signal), else from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
     double sm, spl;
-    if (B.a < kSincPolyA) {
+    if (B.a < kSincPolyA8) {
+      sm = sinc_poly_n<4>(u1);
+      spl = sinc_poly_n<4>(u2);
+    } else if (B.a < kSincPolyA12) {
+      sm = sinc_poly_n<6>(u1);
+      spl = sinc_poly_n<6>(u2);
+    } else if (B.a < kSincPolyA) {
       sm = sinc_poly(u1);
       spl = sinc_poly(u2);
     } else {
