@@ -41,6 +41,7 @@ constexpr int kNin = 64;                      // 11 features, zero padded
 constexpr int kHid = 256;
 constexpr int kQ = 7;                         // spline quantities per (detector, sample, mode)
 constexpr double kFmin = 1e-4;                // lowest node frequency [Hz]
+constexpr double kLnFmin = -9.210340371976182;  // ln(kFmin), the nodes' origin in u = ln f
 
 // ---- features, targets ------------------------------------------------------------------------
 // Normalised inputs: the 11 parameters, each affinely scaled to order one (log10 for the mass).
@@ -323,10 +324,11 @@ __global__ void k_node_h(const double* theta, int B, double* hs) {
 }
 
 // Spline evaluation of one mode at one bin: adds H T_X, H T_Y, H T_Z to acc.
+// h, ih: the mode's node spacing in ln f and its inverse (formed once per tile).
 __device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, const BinIn& B, double u,
-                                             const double* cf, double h, double2 acc[3],
+                                             const double* cf, double h, double ih, double2 acc[3],
                                              const double2* __restrict__ tab) {
-  const double uj = (u - log(kFmin)) / h;
+  const double uj = (u - kLnFmin) * ih;
   int j = (int)floor(uj);
   j = j < 0 ? 0 : (j > kNodes - 2 ? kNodes - 2 : j);
   const double t = (uj - j) * h;
@@ -372,6 +374,7 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
                                                        double* part, int mode) {
   __shared__ double sh[6][kTileBins / 32];
   __shared__ double pc[kProj];
+  __shared__ double ihs[kNModes];
   __shared__ double2 stab[kSinTab];
   for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
   __syncthreads();
@@ -385,6 +388,8 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
     proj_prologue(D, S, pc);
+    if (threadIdx.x < kNModes) ihs[threadIdx.x] = 1.0 / hs[(size_t)s * kNModes + threadIdx.x];
+    __syncthreads();
     const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
@@ -401,8 +406,8 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
           const ModeCoef& C = S.md[md];
           if (!C.active || !(Bn.f < C.fend)) continue;
           const size_t sys = ((size_t)I * B + s) * kNModes + md;
-          mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], xs,
-                       stab);
+          mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md],
+                       ihs[md], xs, stab);
         }
       }
       if (!sur || mode == 1) bin_modes(D, S, Bn, xpa, stab, pc);   // the plain path, as k_loglike_fwd
