@@ -20,8 +20,9 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_dou
 // 2 pi j/kSinTab, and the remainder t (|t| <= pi/kSinTab) through the angle-addition formulas with
 // sin t = t - t^3/6 + t^5/120, cos t = 1 - t^2/2 + t^4/24 (truncation below 1e-18).
 // tab[j] = (cos, sin)(2 pi j/kSinTab).
-__device__ __forceinline__ void sincos_turns(double x, const double2* __restrict__ tab, double* s, double* c) {
-  const double r = x - rint(x);
+// sincos(2 pi r) for |r| < 2^20 turns without the reduction to a fraction: the table index wraps
+// modulo kSinTab, and r - jf / kSinTab is exact (Sterbenz), so the result equals sincos_turns(r).
+__device__ __forceinline__ void sincos_turns_r(double r, const double2* __restrict__ tab, double* s, double* c) {
   const double jf = rint(r * kSinTab);
   const double d = fma(jf, -1.0 / kSinTab, r);
   const double2 cs = tab[(int)jf & (kSinTab - 1)];
@@ -31,6 +32,9 @@ __device__ __forceinline__ void sincos_turns(double x, const double2* __restrict
   const double ct = fma(t2, fma(t2, 1.0 / 24.0, -0.5), 1.0);
   *s = fma(cs.y, ct, cs.x * st);
   *c = fma(cs.x, ct, -(cs.y * st));
+}
+__device__ __forceinline__ void sincos_turns(double x, const double2* __restrict__ tab, double* s, double* c) {
+  sincos_turns_r(x - rint(x), tab, s, c);
 }
 
 // -2Y_lm(iota, 0) closed forms for the ten (l, +-m) the five modes need.
@@ -375,40 +379,51 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   orbit_basis(D, tf, tab, &co, &so, ob);
   const double kxc = D.R * (S.k[0] * co + S.k[1] * so);
   const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
-  double sph, cph;
-  sincos_turns(ph, tab, &sph, &cph);
-  const double2 H = make_double2(amp * cph, amp * sph);
-  // paired second mode: complex polarisation weights Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
-  double2 Ap = make_double2(C.Pp, 0.0), Ac = make_double2(C.Pc, 0.0);
+  const double phr = ph - rint(ph);
+  // polarisation weights times the amplitude; a paired second mode makes them complex:
+  // Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
+  double2 Ap = make_double2(amp * C.Pp, 0.0), Ac = make_double2(amp * C.Pc, 0.0);
   if (C2) {
     const double v2 = v * v;
     const double kr = S.k32.x * v2, ki = S.k32.y * v2;
-    Ap = make_double2(fma(kr, C2->Pp, C.Pp), ki * C2->Pp);
-    Ac = make_double2(fma(kr, C2->Pc, C.Pc), ki * C2->Pc);
+    Ap = make_double2(amp * fma(kr, C2->Pp, C.Pp), amp * (ki * C2->Pp));
+    Ac = make_double2(amp * fma(kr, C2->Pc, C.Pc), amp * (ki * C2->Pc));
   }
-  // third-spacecraft phases e^{i pi f k.delta_t}; the offsets sum to zero, so E_2 = conj(E_0 E_1)
+  // mode phase times the third spacecraft's phase e^{i pi f k.delta_t}, one sincos per spacecraft;
+  // the offsets sum to zero, so delta_2's phase is minus the other two
   double2 E[3];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) sincos_turns(0.5 * B.f * dot5(pc + 45 + 5 * i, ob), tab, &E[i].y, &E[i].x);
   {
-    const double2 e01 = cmul(E[0], E[1]);
-    E[2] = make_double2(e01.x, -e01.y);
+    const double e0 = 0.5 * B.f * dot5(pc + 45, ob), e1 = 0.5 * B.f * dot5(pc + 50, ob);
+    sincos_turns_r(phr + e0, tab, &E[0].y, &E[0].x);
+    sincos_turns_r(phr + e1, tab, &E[1].y, &E[1].x);
+    sincos_turns_r(phr - (e0 + e1), tab, &E[2].y, &E[2].x);
   }
-  // --- links (row A5): pair l = (1,2), (2,3), (3,1); third spacecraft 3, 1, 2
+  // --- links (row A5): pair l = (1,2), (2,3), (3,1); third spacecraft 3, 1, 2. Projections of
+  // the unnormalised link vectors x_r - x_s: the three sum to zero, so the third is minus the
+  // other two
+  double knr[3], npr[3], nqr[3];
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    knr[l] = dot5(pc + 15 * l, ob);
+    npr[l] = dot5(pc + 15 * l + 5, ob);
+    nqr[l] = dot5(pc + 15 * l + 10, ob);
+  }
+  knr[2] = -(knr[0] + knr[1]);
+  npr[2] = -(npr[0] + npr[1]);
+  nqr[2] = -(nqr[0] + nqr[1]);
   double2 G[3];
   double smv[3], spv[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int t = (l + 2) % 3;
-    // projections of the unnormalised link vector, then k.n, n.e+.n, n.ex.n of the unit vector
-    const double knr = dot5(pc + 15 * l, ob), npr = dot5(pc + 15 * l + 5, ob), nqr = dot5(pc + 15 * l + 10, ob);
-    const double inv = rsqrt(fma(knr, knr, fma(npr, npr, nqr * nqr)));
-    const double kn = knr * inv;
-    const double np = npr * inv, nq = nqr * inv;
+    // k.n, n.e+.n, n.ex.n of the unit link vector
+    const double inv = rsqrt(fma(knr[l], knr[l], fma(npr[l], npr[l], nqr[l] * nqr[l])));
+    const double kn = knr[l] * inv;
+    const double np = npr[l] * inv, nq = nqr[l] * inv;
     const double Fp = np * np - nq * nq, Fc = 2.0 * np * nq;
     const double2 gam = C2 ? make_double2(fma(Ap.x, Fp, -Ac.y * Fc), fma(Ap.y, Fp, Ac.x * Fc))
-                           : make_double2(C.Pp * Fp, C.Pc * Fc);
-    G[l] = cmul(E[t], cmul(gam, H));
+                           : make_double2(Ap.x * Fp, Ac.x * Fc);
+    G[l] = cmul(gam, E[t]);
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (most bins of a massive-binary
     // signal), else from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);

@@ -104,15 +104,6 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   const double tf = fma(C.tffac * B.invf, dv, S.tc);
   // amplitude (times hsc) in double words: ampw f^(-7/6) v^p, times the taper where it is below 1
   df A = df_mul(C.ampw, W.fm76);
-  // paired second mode: complex polarisation weights Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
-  cdf Ap = {C.Ppw, df_make(0.f, 0.f)}, Ac = {C.Pcw, df_make(0.f, 0.f)};
-  if (C2) {
-    const df vw = df_mul(C.cmw, W.f13);
-    const df v2 = df_mul(vw, vw);
-    const df kr = df_mul(S.k32w[0], v2), ki = df_mul(S.k32w[1], v2);
-    Ap = cdf{df_add_s(C.Ppw, df_mul(kr, C2->Ppw)), df_mul(ki, C2->Ppw)};
-    Ac = cdf{df_add_s(C.Pcw, df_mul(kr, C2->Pcw)), df_mul(ki, C2->Pcw)};
-  }
   if (C.p >= 1) {
     const df vw = df_mul(C.cmw, W.f13);
     A = df_mul(A, vw);
@@ -123,13 +114,22 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
     A = df_mul(A, df_from_bits((zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt))));
   }
+  // polarisation weights times the amplitude; a paired second mode makes them complex:
+  // Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
+  cdf Ap = {df_mul(A, C.Ppw), df_make(0.f, 0.f)}, Ac = {df_mul(A, C.Pcw), df_make(0.f, 0.f)};
+  if (C2) {
+    const df vw = df_mul(C.cmw, W.f13);
+    const df v2 = df_mul(vw, vw);
+    const df kr = df_mul(S.k32w[0], v2), ki = df_mul(S.k32w[1], v2);
+    Ap = cdf{df_mul(A, df_add_s(C.Ppw, df_mul(kr, C2->Ppw))), df_mul(A, df_mul(ki, C2->Ppw))};
+    Ac = cdf{df_mul(A, df_add_s(C.Pcw, df_mul(kr, C2->Pcw))), df_mul(A, df_mul(ki, C2->Pcw))};
+  }
   // --- orbital angle alpha(t_f) (row A4), centre Doppler f k.x_c, x_c = R (cos a, sin a, 0)
   const cdf eo = df_cis_turns(frac_dw(fma(tf, D.rate_t, D.alpha0_t)), tab);
   const df co = eo.re, so = eo.im;
   const df kxc = df_mul(D.Rw, df_add_s(df_mul(S.kw[0], co), df_mul(S.kw[1], so)));
   // mode phase: the FP64 part reduced to a fraction of a turn, minus f k.x_c in double words
-  const cdf eph = df_cis_turns(df_sub_s(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), df_mul(W.f, kxc)), tab);
-  const cdf H = {df_mul(A, eph.re), df_mul(A, eph.im)};
+  const df pf = df_sub_s(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), df_mul(W.f, kxc));
   // --- the offsets' basis (DetDev::Mo)
   df ob[4];
   if (D.orbit == 0) {
@@ -143,22 +143,32 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     ob[1] = e0.im;
     ob[2] = ob[3] = df_make(0.f, 0.f);
   }
-  // --- third-spacecraft phases e^{i pi f k.delta_t} (E_2 = conj(E_0 E_1))
-  cdf E[3];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) E[i] = df_cis_turns(df_scale2(df_mul(W.f, dw_dot5(pcw + 45 + 5 * i, ob)), 0.5f), tab);
-  {
-    const cdf e01 = cdf_mul(E[0], E[1]);
-    E[2].re = e01.re;
-    E[2].im = df_make(-e01.im.x, -e01.im.y);
-  }
-  // --- links (row A5); the loop stays rolled (one copy of its body) for the instruction cache
+  // --- third-spacecraft phases pi f k.delta_t (the offsets sum to zero, so delta_2's phase is
+  // minus the other two); each link takes the mode phase plus its third spacecraft's phase
+  const df e0 = df_scale2(df_mul(W.f, dw_dot5(pcw + 45, ob)), 0.5f);
+  const df e1 = df_scale2(df_mul(W.f, dw_dot5(pcw + 50, ob)), 0.5f);
+  const df e01 = df_add_s(e0, e1);
+  // --- links (row A5); the loop stays rolled (one copy of its body) for the instruction cache.
+  // Projections of the unnormalised link vectors x_r - x_s: the three sum to zero, so the third
+  // is minus the sum of the other two
   cdf G[3];
   df smv[3], spv[3];
+  df sk = df_make(0.f, 0.f), sp = sk, sq = sk;
 #pragma unroll 1
   for (int l = 0; l < 3; ++l) {
-    const int t = (l + 2) % 3;
-    const df knr = dw_dot5(pcw + 15 * l, ob), npr = dw_dot5(pcw + 15 * l + 5, ob), nqr = dw_dot5(pcw + 15 * l + 10, ob);
+    df knr, npr, nqr;
+    if (l < 2) {
+      knr = dw_dot5(pcw + 15 * l, ob);
+      npr = dw_dot5(pcw + 15 * l + 5, ob);
+      nqr = dw_dot5(pcw + 15 * l + 10, ob);
+      sk = df_add_s(sk, knr);
+      sp = df_add_s(sp, npr);
+      sq = df_add_s(sq, nqr);
+    } else {
+      knr = df_make(-sk.x, -sk.y);
+      npr = df_make(-sp.x, -sp.y);
+      nqr = df_make(-sq.x, -sq.y);
+    }
     const df inv = df_rsqrt(df_add_s(df_mul(knr, knr), df_add_s(df_mul(npr, npr), df_mul(nqr, nqr))));
     const df kn = df_mul(knr, inv);
     const df np = df_mul(npr, inv);
@@ -166,8 +176,10 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     const df Fp = df_sub_s(df_mul(np, np), df_mul(nq, nq));
     const df Fc = df_scale2(df_mul(np, nq), 2.0f);
     const cdf gam = C2 ? cdf{df_sub_s(df_mul(Ap.re, Fp), df_mul(Ac.im, Fc)), df_add_s(df_mul(Ap.im, Fp), df_mul(Ac.re, Fc))}
-                       : cdf{df_mul(C.Ppw, Fp), df_mul(C.Pcw, Fc)};
-    G[l] = cdf_mul(E[t], cdf_mul(gam, H));
+                       : cdf{df_mul(Ap.re, Fp), df_mul(Ac.re, Fc)};
+    // third spacecraft t = (l + 2) % 3
+    const cdf Et = df_cis_turns(l == 0 ? df_sub_s(pf, e01) : df_add_s(pf, l == 1 ? e0 : e1), tab);
+    G[l] = cdf_mul(gam, Et);
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (|u| <= 2a < 1), else from
     // sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     const df akn = df_mul(W.a, kn);
