@@ -105,24 +105,21 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
   }
   const double kxc = S.k[0] * xc[0] + S.k[1] * xc[1] + S.k[2] * xc[2];
   const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
-  double sph, cph;
-  sincos_turns(ph, tab, &sph, &cph);
-  const double2 H = make_double2(amp * cph, amp * sph);
-  // third-spacecraft phases e^{i pi f k.delta_t}: E_2 = conj(E_0 E_1) since the offsets sum to zero
+  const double phr = ph - rint(ph);
+  // e^{2 pi i (ph + theta_t)}: the mode phase times the third spacecraft's phase
+  // theta_t = f k.delta_t / 2 (turns); the offsets sum to zero, so theta_2 = -(theta_0 + theta_1)
   double2 Et[3];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const double kd = S.k[0] * dl[i][0] + S.k[1] * dl[i][1] + S.k[2] * dl[i][2];
-    sincos_turns(0.5 * B.f * kd, tab, &Et[i].y, &Et[i].x);
-  }
   {
-    const double2 e01 = cmul(Et[0], Et[1]);
-    Et[2] = make_double2(e01.x, -e01.y);
+    const double th0 = 0.5 * B.f * (S.k[0] * dl[0][0] + S.k[1] * dl[0][1] + S.k[2] * dl[0][2]);
+    const double th1 = 0.5 * B.f * (S.k[0] * dl[1][0] + S.k[1] * dl[1][1] + S.k[2] * dl[1][2]);
+    sincos_turns_r(phr + th0, tab, &Et[0].y, &Et[0].x);
+    sincos_turns_r(phr + th1, tab, &Et[1].y, &Et[1].x);
+    sincos_turns_r(phr - (th0 + th1), tab, &Et[2].y, &Et[2].x);
   }
   // ---------------- links: forward and reverse, one pair at a time
   // seeds: pair 0 = (1,2): X' has -G U, Y' has +G V; pair 1 = (2,3): Y' -G U, Z' +G V;
   //        pair 2 = (3,1): Z' -G U, X' +G V.
-  double2 Hb = make_double2(0.0, 0.0);
+  double ampb = 0.0, phtb = 0.0;   // cotangents of amp and of the summed angle 2 pi (ph + theta_t)
   double dlb[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) dlb[i][0] = dlb[i][1] = dlb[i][2] = 0.0;
@@ -154,8 +151,8 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double2 gam = make_double2(fma(Ap.x, Fp, -Ac.y * Fc), fma(Ap.y, Fp, Ac.x * Fc));
     const double2 E = Et[t];
     const double se = E.y, ce = E.x;
-    const double2 K = cmul(gam, H);
-    const double2 G = cmul(E, K);
+    const double2 K = make_double2(amp * gam.x, amp * gam.y);
+    const double2 G = cmul(K, E);
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
     double sm, spl, dsm, dspl;   // sinc(u1), sinc(u2) and their derivatives
     if (B.a < kSincPolyA8) {
@@ -197,9 +194,10 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double2 Eb = cconjmul(Gb, K);
     const double2 Kb = cconjmul(Gb, E);
     const double thb = ce * Eb.y - se * Eb.x;
+    phtb += thb;
     const double kdb = kPi * B.f * thb;
-    const double2 gamb = cconjmul(Kb, H);
-    Hb = cadd(Hb, cconjmul(Kb, gam));
+    const double2 gamb = make_double2(amp * Kb.x, amp * Kb.y);
+    ampb = fma(Kb.x, gam.x, fma(Kb.y, gam.y, ampb));
     Apb = make_double2(fma(gamb.x, Fp, Apb.x), fma(gamb.y, Fp, Apb.y));
     Acb = make_double2(fma(gamb.y, Fc, Acb.x), fma(-gamb.x, Fc, Acb.y));
     const double Fpb = fma(gamb.x, Ap.x, gamb.y * Ap.y), Fcb = fma(gamb.y, Ac.x, -gamb.x * Ac.y);
@@ -222,9 +220,8 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
       dlb[t][i] = fma(kdb, S.k[i], dlb[t][i]);
     }
   }
-  // ---------------- mode level: H = amp e^{2 pi i ph}
-  const double ampb = Hb.x * cph + Hb.y * sph;
-  const double phb = 2.0 * kPi * (Hb.y * H.x - Hb.x * H.y);
+  // ---------------- mode level: every link's angle holds 2 pi ph
+  const double phb = 2.0 * kPi * phtb;
   g.ph = fma(phb, 2.0 * C.mfac, g.ph);          // d ph0/d phi_c = m/(2 pi)
   g.tc = fma(-B.f, phb, g.tc);                   // frac(f t_c)
   double psib = -C.mfac * phb;
