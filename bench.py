@@ -183,10 +183,17 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def roofline(prec: str, units: int, launch_s: float, fp64_tflops: float, fp32_tflops: float) -> dict:
+# Issue rate of each pipe per SM and clock: FP64 2 DFMA (the nominal 1.25 TFLOP/s FP64 of a
+# 152-SM part at 2070 MHz), FP32 128 FFMA. Nominal peak = rate x SMs x maximum SM clock.
+PIPE_PER_CLK = {"fp64": 2.0, "fp32": 128.0}
+
+
+def roofline(prec: str, units: int, launch_s: float, fp64_tflops: float, fp32_tflops: float,
+             n_sm: int = 152, sm_max_mhz: float = 2070.0) -> dict:
     """ALU roofline of the fused forward kernel: per pipe, the instructions one launch issues
-    (per-unit count x active units) per second against the pipe's measured FMA-loop rate; the
-    binding pipe is the busier one."""
+    (per-unit count x active units) per second against the pipe's measured FMA-loop rate (and,
+    beside it, the nominal rate from the unit counts and the maximum clock); the binding pipe is
+    the busier one."""
     if prec not in UNIT_COUNTS:
         return None
     c = UNIT_COUNTS[prec]
@@ -194,12 +201,17 @@ def roofline(prec: str, units: int, launch_s: float, fp64_tflops: float, fp32_tf
     pipes = {}
     for name, inst, tf in (("fp64", c["fp64_inst"], fp64_tflops), ("fp32", c["fp32_inst"], fp32_tflops)):
         peak = tf * 1e3 / 2.0   # G FMA instructions/s of the measured loop
+        nominal = PIPE_PER_CLK[name] * n_sm * sm_max_mhz / 1e3
         ach = inst * ups / 1e9
-        pipes[name] = {"inst_per_unit": inst, "achieved_ginst_s": ach, "peak_ginst_s": peak, "frac": ach / peak}
+        pipes[name] = {"inst_per_unit": inst, "achieved_ginst_s": ach, "peak_ginst_s": peak, "frac": ach / peak,
+                       "peak_nominal_ginst_s": nominal, "frac_nominal": ach / nominal}
     bind = max(pipes, key=lambda k: pipes[k]["frac"])
     return {"bound": "alu", "pipe": bind, "unit": "Ginst/s", "achieved": pipes[bind]["achieved_ginst_s"],
             "peak": pipes[bind]["peak_ginst_s"], "frac": pipes[bind]["frac"],
-            "peak_kind": "measured FMA loops (FP64 and FP32, 1 s each)", "kernel": "k_loglike_fwd",
+            "peak_kind": "measured FMA loops (FP64 and FP32, 1 s each)",
+            "peak_nominal": pipes[bind]["peak_nominal_ginst_s"], "frac_nominal": pipes[bind]["frac_nominal"],
+            "peak_nominal_kind": "%g inst/clk/SM x %d SMs x %g MHz" % (PIPE_PER_CLK[bind], n_sm, sm_max_mhz),
+            "kernel": "k_loglike_fwd",
             "launch_ms": launch_s * 1e3, "units_per_launch": units, "units_per_s": ups,
             "fp64_tflops": c["fp64_flops"] * ups / 1e12, "fp64_tflops_peak": fp64_tflops,
             "fp64_flops_frac": c["fp64_flops"] * ups / 1e12 / fp64_tflops, "pipes": pipes,
@@ -284,7 +296,9 @@ def main():
     fwd_avg_s = (fwd_ms / max(fwd_launches, 1)) / 1e3
     peak64 = L.pe_measure_fp64_peak(1.0)
     peak32 = L.pe_measure_fp32_peak(1.0)
-    roof = roofline(args.precision, units, fwd_avg_s, peak64, peak32)
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    roof = roofline(args.precision, units, fwd_avg_s, peak64, peak32, n_sm, sm_max)
 
     # ---- precision study (the paper's low-precision option against FP64): the same batch through
     # the other forward path, device-timed the same way; accuracy of its log L against the FP64
@@ -323,7 +337,8 @@ def main():
             absmax = (llo - ll64).abs().max().item()
             study[other] = {"value": B * K / (sum(ems) / 1e3), "ms_per_step": sum(ems) / K, "tuning": tuned_o,
                             "max_rel_dlogl_vs_fp64": rel, "max_abs_dlogl_vs_fp64": absmax, "parity_bar": 1e-10,
-                            "roofline": roofline(other, units, (o_ms / max(o_n, 1)) / 1e3, peak64, peak32)}
+                            "roofline": roofline(other, units, (o_ms / max(o_n, 1)) / 1e3, peak64, peak32,
+                                                 n_sm, sm_max)}
         study["note"] = ("mixed: FP64 TaylorF2 phase, t_f, turn reductions and tile sums; response "
                          "geometry, TDI, A/E/T and per-bin products in double-word FP32 arithmetic. "
                          "fp32: every step in FP32 (the paper's float32 option); misses the 1e-10 bar")
