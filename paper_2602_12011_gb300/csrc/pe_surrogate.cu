@@ -276,14 +276,19 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
 // interval j, (a, b, c, d) of y(u_j + t) = a + b t + c t^2 + d t^3 in place over coef[j][4].
 // With uniform spacing the not-a-knot conditions give M_1 = r_1/6, M_{N-2} = r_{N-2}/6
 // (r_j = 6 (y_{j+1} - 2 y_j + y_{j-1})/h^2); the interior (1, 4, 1) system is solved by Thomas.
-__global__ void k_spline(const double* nodes, long long nsys, const double* hs, double* coef) {
+// coef_t: FP32 copies of quantities 1..6 (the transfer functions), [system][6][kNodes - 1][4].
+__global__ void k_spline(const double* nodes, long long nsys, const double* hs, double* coef, float* coef_t) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsys) return;
   const double* y = nodes + i * kNodes;
   double* cf = coef + i * (kNodes - 1) * 4;
+  const int q = (int)(i % kQ);
+  float* ct = q > 0 ? coef_t + ((i / kQ) * (kQ - 1) + (q - 1)) * (kNodes - 1) * 4 : nullptr;
   const double h = hs[i / kQ];
   if (!(h > 0.0)) {
     for (int j = 0; j < kNodes - 1; ++j) cf[4 * j] = cf[4 * j + 1] = cf[4 * j + 2] = cf[4 * j + 3] = 0.0;
+    if (ct)
+      for (int j = 0; j < 4 * (kNodes - 1); ++j) ct[j] = 0.f;
     return;
   }
   constexpr int N = kNodes;
@@ -312,6 +317,8 @@ __global__ void k_spline(const double* nodes, long long nsys, const double* hs, 
     cf[4 * j + 1] = (y[j + 1] - y[j]) / h - h * (2.0 * Mv[j] + Mv[j + 1]) / 6.0;
     cf[4 * j + 2] = 0.5 * Mv[j];
     cf[4 * j + 3] = (Mv[j + 1] - Mv[j]) / (6.0 * h);
+    if (ct)
+      for (int k = 0; k < 4; ++k) ct[4 * j + k] = (float)cf[4 * j + k];
   }
 }
 
@@ -323,20 +330,26 @@ __global__ void k_node_h(const double* theta, int B, double* hs) {
   hs[i] = node_h(theta[(size_t)s * PE_NPARAM] * kMsunS, mm);
 }
 
-// Spline evaluation of one mode at one bin: adds H T_X, H T_Y, H T_Z to acc.
+// Spline evaluation of one mode at one bin: adds hsc H T_X, hsc H T_Y, hsc H T_Z to acc. The phase
+// spline (cf, quantity 0; ~1e5 turns) is evaluated in FP64; the transfer functions T (cft, FP32
+// copies of quantities 1..6, smooth and of order one relative to their own scale) and their
+// products with H in FP32, with H carried times the sample's power of two hsc.
 // h, ih: the mode's node spacing in ln f and its inverse (formed once per tile).
-__device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, const BinIn& B, double u,
-                                             const double* cf, double h, double ih, double2 acc[3],
+__device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, double hsc, const BinIn& B, double u,
+                                             const double* cf, const float* cft, double h, double ih, float2 acc[3],
                                              const double2* __restrict__ tab) {
   const double uj = (u - kLnFmin) * ih;
   int j = (int)floor(uj);
   j = j < 0 ? 0 : (j > kNodes - 2 ? kNodes - 2 : j);
   const double t = (uj - j) * h;
-  double val[kQ];
+  const double* c0 = cf + (size_t)j * 4;
+  const double ph = fma(fma(fma(c0[3], t, c0[2]), t, c0[1]), t, c0[0]);
+  const float tf = (float)t;
+  float val[kQ - 1];
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) {
-    const double* c = cf + ((size_t)k * (kNodes - 1) + j) * 4;
-    val[k] = fma(fma(fma(c[3], t, c[2]), t, c[1]), t, c[0]);
+  for (int k = 0; k < kQ - 1; ++k) {
+    const float4 c = *reinterpret_cast<const float4*>(cft + ((size_t)k * (kNodes - 1) + j) * 4);
+    val[k] = fmaf(fmaf(fmaf(c.w, tf, c.z), tf, c.y), tf, c.x);
   }
   double w = 1.0;
   if (B.f > C.ftap) {
@@ -345,12 +358,14 @@ __device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, con
     w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
   }
   double sph, cph;
-  sincos_turns(val[0] - B.frc, tab, &sph, &cph);
-  const double amp = ampN * B.fm76 * w;  // Newtonian power law; the mode factor |H_lm| is in T
-  const double2 H = make_double2(amp * cph, amp * sph);
-  acc[0] = cadd(acc[0], cmul(H, make_double2(val[1], val[2])));
-  acc[1] = cadd(acc[1], cmul(H, make_double2(val[3], val[4])));
-  acc[2] = cadd(acc[2], cmul(H, make_double2(val[5], val[6])));
+  sincos_turns(ph - B.frc, tab, &sph, &cph);
+  const double amp = ampN * hsc * B.fm76 * w;  // Newtonian power law; the mode factor |H_lm| is in T
+  const float hr = (float)(amp * cph), hi = (float)(amp * sph);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c].x = fmaf(hr, val[2 * c], fmaf(-hi, val[2 * c + 1], acc[c].x));
+    acc[c].y = fmaf(hr, val[2 * c + 1], fmaf(hi, val[2 * c], acc[c].y));
+  }
 }
 
 __device__ __forceinline__ int find_pair_s(const long long* off, int P, long long t) {
@@ -369,7 +384,8 @@ __device__ __forceinline__ int find_pair_s(const long long* off, int P, long lon
 __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                        const SampleCoef* __restrict__ coefN,
                                                        const double* __restrict__ theta, SurBox bx,
-                                                       const double* __restrict__ spl, const double* __restrict__ hs,
+                                                       const double* __restrict__ spl, const float* __restrict__ splt,
+                                                       const double* __restrict__ hs,
                                                        const int* __restrict__ nend, const long long* __restrict__ off,
                                                        double* part, int mode) {
   __shared__ double sh[6][kTileBins / 32];
@@ -396,7 +412,7 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
     for (int b = b0; b < b0 + kTileBins && b < ne; b += kTileBins) {
       BinIn Bn;
       load_bin(D, b, S.tc, Bn);
-      double2 xs[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+      float2 xs[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       XYZAcc xpa;
       xyz_zero(xpa);
       const double u = 3.0 * Bn.lnf3;
@@ -406,15 +422,17 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
           const ModeCoef& C = S.md[md];
           if (!C.active || !(Bn.f < C.fend)) continue;
           const size_t sys = ((size_t)I * B + s) * kNModes + md;
-          mode_bin_sur(C, coefN[s].md[md].amp, Bn, u, spl + sys * kQ * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md],
-                       ihs[md], xs, stab);
+          mode_bin_sur(C, coefN[s].md[md].amp, S.hsc, Bn, u, spl + sys * kQ * (kNodes - 1) * 4,
+                       splt + sys * (kQ - 1) * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], ihs[md], xs, stab);
         }
       }
       if (!sur || mode == 1) bin_modes(D, S, Bn, xpa, stab, pc);   // the plain path, as k_loglike_fwd
-      double2 xp[3];
+      double2 xp[3], xsd[3];
       xyz_final(xpa, Bn.z, xp);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xsd[c] = make_double2((double)xs[c].x * S.ihsc, (double)xs[c].y * S.ihsc);
       double2 os[3], op[3];
-      aet_from_xyz(sur ? xs : xp, os);
+      aet_from_xyz(sur ? xsd : xp, os);
       if (mode == 0) {
         accum_bin(D, b, os, v);
       } else {
@@ -842,7 +860,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   int* nend = nullptr;
   long long* off = nullptr;
   double *part = nullptr, *nodes = nullptr, *spl = nullptr, *hs = nullptr, *hs_sys = nullptr;
-  float* Yd = nullptr;
+  float *Yd = nullptr, *splt = nullptr;
   const size_t nsys = (size_t)ndet * B * pe::kNModes;
   aalloc(&S, B);
   aalloc(&S0, B);
@@ -851,6 +869,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   aalloc(&part, (size_t)max_tiles * 6);
   aalloc(&nodes, nsys * pe::kQ * pe::kNodes);
   aalloc(&spl, nsys * pe::kQ * (pe::kNodes - 1) * 4);
+  aalloc(&splt, nsys * (pe::kQ - 1) * (pe::kNodes - 1) * 4);
   aalloc(&hs, (size_t)B * pe::kNModes);
   aalloc(&hs_sys, nsys);
   aalloc(&Yd, (size_t)B * pe::kNout);
@@ -879,7 +898,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
                           cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) {
       const long long ns = (long long)nsys * pe::kQ;
-      pe::k_spline<<<(unsigned)((ns + 63) / 64), 64, 0, st>>>(nodes, ns, hs_sys, spl);
+      pe::k_spline<<<(unsigned)((ns + 63) / 64), 64, 0, st>>>(nodes, ns, hs_sys, spl, splt);
       e = cudaGetLastError();
     }
   }
@@ -890,8 +909,8 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long g = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * 8));
-    pe::k_sur_fwd<<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, hs, nend, off, part,
-                                                          mode);
+    pe::k_sur_fwd<<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
+                                                          part, mode);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
