@@ -542,8 +542,10 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   if (s0 != PE_OK) return s0;
   if (theta == nullptr || out_grad == nullptr) return fail(PE_EINVAL, "theta/out_grad is NULL");
   if (B < 1 || B > (1 << 20)) return fail(PE_EINVAL, "B=%d outside [1, 2^20]", B);
-  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL))
-    return fail(PE_EINVAL, "bad mode mask 0x%x (the gradient is FP64 only)", mode_mask);
+  if ((mode_mask & PE_MODE_ALL) == 0 || (mode_mask & ~(PE_MODE_ALL | PE_PREC_MIXED)))
+    return fail(PE_EINVAL, "bad mode mask 0x%x (the gradient takes PE_PREC_MIXED, not PE_PREC_FP32)", mode_mask);
+  const bool mixed = (mode_mask & PE_PREC_MIXED) != 0;
+  mode_mask &= PE_MODE_ALL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch sc(st);
   const int P = ndet * B;
@@ -581,7 +583,7 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   const long long g = std::min<long long>(max_tiles, (long long)sm_count() * pe::fwd_blocks_per_sm());
   void* prof = nullptr;
   pe::profile_begin(st, &prof);
-  PE_CUDA(pe::launch_grad_fwd(ds, B, coef, sg, nend, off, part, (int)std::max<long long>(g, 1), st));
+  PE_CUDA(pe::launch_grad_fwd(ds, B, coef, sg, nend, off, part, (int)std::max<long long>(g, 1), mixed, st));
   pe::profile_end(st, prof);
   PE_CUDA(pe::launch_grad_reduce(ds, B, off, part, coef, sg, logl, grad, st));
   if (h_logl) PE_CUDA(cudaMemcpyAsync(out_logl, logl, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -132,7 +132,7 @@ __device__ __forceinline__ cdf cdf_mul(const cdf& a, const cdf& b) {
 // terms below 2e-18). tab[j] = (cos hi, cos lo, sin hi, sin lo) of 2 pi j/kSinTab. Not inlined: the
 // mixed unit calls it from five places, and one copy keeps the kernel's hot loop in the
 // instruction cache.
-__device__ __noinline__ cdf df_cis_turns(df x, const float4* __restrict__ tab) {
+static __device__ __noinline__ cdf df_cis_turns(df x, const float4* __restrict__ tab) {
   // round to nearest integer by adding and subtracting 1.5 * 2^23 (exact for |v| < 2^22), on the
   // FP32 pipe; the table index is read from the biased sum's bits
   const float kR = 12582912.0f;

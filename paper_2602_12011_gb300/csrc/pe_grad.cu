@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "pe_adjoint.cuh"
+#include "pe_device_mixed.cuh"
 #include "pe_grad.h"
 
 namespace pe {
@@ -105,14 +106,22 @@ __device__ __forceinline__ void bracket_cotangents(const DetDev& D, int b, const
   *sZ = make_double2(bb[0].x + bb[1].x + bb[2].x, bb[0].y + bb[1].y + bb[2].y);
 }
 
+// MIX: the bin's forward mode sum (the brackets the cotangents need) by the mixed-precision unit
+// (FP64 phase, t_f and turn reductions; double-word geometry), returned to FP64; the reverse
+// sweeps are FP64 either way.
+template <bool MIX>
 __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                         const SampleGrad* __restrict__ sgrad,
                                                         const int* __restrict__ nend,
                                                         const long long* __restrict__ off, double* part) {
   __shared__ double sh[kGradW][kTileBins / 32];
   __shared__ double2 stab[kSinTab];
+  __shared__ float4 stabw[MIX ? kSinTab : 1];
   __shared__ double pc[kProj];
+  __shared__ float2 pcw[MIX ? kProj : 1];
   for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  if constexpr (MIX)
+    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stabw[i] = ds.d[0].sctw[i];
   __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
@@ -122,6 +131,10 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
     const int b = int(t - off[p]) * kTileBins + threadIdx.x;
     const DetDev& D = ds.d[I];
     proj_prologue(D, coef[s], pc);
+    if constexpr (MIX) {
+      if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+      __syncthreads();
+    }
     double v[kGradW];
 #pragma unroll
     for (int i = 0; i < kGradW; ++i) v[i] = 0.0;
@@ -130,12 +143,21 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
       const SampleGrad& SG = sgrad[s];
       BinIn Bn;
       load_bin(D, b, S.tc, Bn);
-      XYZAcc xa;
-      xyz_zero(xa);
-      bin_modes(D, S, Bn, xa, stab, pc);
-      double2 x[3], o[3];
-      xyz_final(xa, Bn.z, x);
-      aet_from_xyz(x, o);
+      double2 o[3];
+      if constexpr (MIX) {
+        cdf x[3], od[3];
+        bin_xyz_mixed(D, S, b, x, stabw, pcw);
+        aet_from_xyz_dw(x, od);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[c] = make_double2(df_to(od[c].re) * S.ihsc, df_to(od[c].im) * S.ihsc);
+      } else {
+        XYZAcc xa;
+        xyz_zero(xa);
+        bin_modes(D, S, Bn, xa, stab, pc);
+        double2 x[3];
+        xyz_final(xa, Bn.z, x);
+        aet_from_xyz(x, o);
+      }
       double2 sX, sY, sZ;
       bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
       GradAcc g;
@@ -295,8 +317,11 @@ cudaError_t launch_prep_grad(const double* theta, int B, unsigned mask, const De
   return cudaGetLastError();
 }
 cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad, const int* nend,
-                            const long long* off, double* part, int grid, cudaStream_t st) {
-  k_grad_fwd<<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
+                            const long long* off, double* part, int grid, bool mixed, cudaStream_t st) {
+  if (mixed)
+    k_grad_fwd<true><<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
+  else
+    k_grad_fwd<false><<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
   return cudaGetLastError();
 }
 cudaError_t launch_grad_reduce(const DetSet& ds, int B, const long long* off, const double* part,

@@ -9,7 +9,7 @@ namespace pe {
 cudaError_t launch_prep_grad(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef,
                              SampleGrad* sgrad, int* nend, int* status, cudaStream_t st);
 cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad, const int* nend,
-                            const long long* off, double* part, int grid, cudaStream_t st);
+                            const long long* off, double* part, int grid, bool mixed, cudaStream_t st);
 cudaError_t launch_grad_reduce(const DetSet& ds, int B, const long long* off, const double* part,
                                const SampleCoef* coef, const SampleGrad* sgrad, double* logl, double* grad,
                                cudaStream_t st);

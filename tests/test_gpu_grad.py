@@ -36,8 +36,8 @@ def _setup(O, Lb, dets_T, inj, seed=12011):
     return ods, gds
 
 
-def _check_grad(O, Lb, ods, gds, th, mask, rel=1e-8):
-    g = Lb.loglike_grad(gds, th, mask)
+def _check_grad(O, Lb, ods, gds, th, mask, rel=1e-8, flags=0):
+    g = Lb.loglike_grad(gds, th, mask | flags)
     for s in range(th.shape[0]):
         r = O.loglike(ods, th[s], mask)
         scale = H.scale_of(r["dh"], r["hh"], r["dd"])
@@ -76,6 +76,38 @@ def test_grad_single_modes_and_tdi15(oracle_mod, Lb):
     th = np.vstack([inj, W.draw_prior(2, 71, T)])
     for mask in (0x01, 0x02, 0x04, 0x08, 0x10):
         _check_grad(oracle_mod, Lb, ods, gds, th, mask)
+
+
+def test_grad_mixed_precision_forward_pass(oracle_mod, Lb):
+    """PE_PREC_MIXED on the gradient: each bin's forward mode sum (log L and the cotangents) comes
+    from the mixed-precision unit, the reverse sweeps stay FP64. The oracle bars are the FP64
+    gradient's, on LISA (taper region included) and TianQin (geocentric orbit); the result also
+    stays within 1e-11 of the scale of the FP64 call's log L and gradient. PE_PREC_FP32 is refused."""
+    T = 2.0 ** 17
+    inj = _inj(T)
+    ods, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
+    th = np.vstack([inj + np.array([2e3, 0.01, 0.01, -0.02, 0.3, 0.02, 0.05, 1e-3, 1e-3, 0.02, 3.0]),
+                    W.draw_prior(5, 51, T)])
+    th[2, 0] = 1.5e7
+    _check_grad(oracle_mod, Lb, ods, gds, th, W.MODE_ALL, flags=Lb.PE_PREC_MIXED)
+    g64 = Lb.loglike_grad(gds, th, W.MODE_ALL)
+    gmx = Lb.loglike_grad(gds, th, W.MODE_ALL | Lb.PE_PREC_MIXED)
+    for s in range(th.shape[0]):
+        r = oracle_mod.loglike(ods, th[s], W.MODE_ALL)
+        scale = H.scale_of(r["dh"], r["hh"], r["dd"])
+        F = oracle_mod.fisher(ods, th[s], W.MODE_ALL)
+        assert abs(gmx["logl"][s] - g64["logl"][s]) <= 1e-11 * scale
+        for i in range(11):
+            tol = 1e-11 * (abs(g64["grad"][s, i]) + math.sqrt(scale * max(F[i, i], 0.0)))
+            assert abs(gmx["grad"][s, i] - g64["grad"][s, i]) <= tol, (s, W.PARAM_NAMES[i])
+    Ts = [(W.TIANQIN, 2.0 ** 16)]
+    inj16 = _inj(2.0 ** 16)
+    ods, gds = _setup(oracle_mod, Lb, Ts, inj16, seed=7)
+    _check_grad(oracle_mod, Lb, ods, gds, np.vstack([inj16, W.draw_prior(2, 61, 2.0 ** 16)]), W.MODE_ALL,
+                flags=Lb.PE_PREC_MIXED)
+    with pytest.raises(Lb.PeError) as e:
+        Lb.loglike_grad(gds, inj16[None, :], W.MODE_ALL | Lb.PE_PREC_FP32)
+    assert e.value.status == Lb.PE_EINVAL
 
 
 def test_grad_matches_central_differences_of_gpu_loglike(oracle_mod, Lb):
@@ -155,7 +187,8 @@ def test_grad_full_size_sampled(oracle_mod, Lb):
     gd = H.library_detector(Lb, od)
     th = wl["theta"]
     g = Lb.loglike_grad([gd], th, wl["mode_mask"])
-    assert np.all(np.isfinite(g["grad"]))
+    gm = Lb.loglike_grad([gd], th, wl["mode_mask"] | Lb.PE_PREC_MIXED)   # mixed forward pass
+    assert np.all(np.isfinite(g["grad"])) and np.all(np.isfinite(gm["grad"]))
     pick = np.argsort(th[:, 0])[-4:]
     for s in pick:
         r = oracle_mod.loglike([od], th[s], wl["mode_mask"])
@@ -165,3 +198,4 @@ def test_grad_full_size_sampled(oracle_mod, Lb):
         for i in range(11):
             tol = 1e-8 * (abs(gref[i]) + math.sqrt(scale * max(F[i, i], 0.0)))
             assert abs(g["grad"][s, i] - gref[i]) <= tol, (s, W.PARAM_NAMES[i])
+            assert abs(gm["grad"][s, i] - gref[i]) <= tol, (s, W.PARAM_NAMES[i], "mixed")
