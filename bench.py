@@ -394,9 +394,9 @@ def main():
         gms.append(e0.elapsed_time(e1))
     grad_value = world * B * Kg / (sum(gms) / 1e3)
     grad_ok = bool(torch.isfinite(grad_dev).all().item())
-    # the same gradient with the forward mode sum in the mixed-precision unit (PE_PREC_MIXED): the
-    # reverse sweeps stay FP64. Its deviation from the FP64 gradient: per component, the largest
-    # |g_mixed - g_fp64| over the batch divided by the largest |g_fp64|
+    # the same gradient in mixed precision (PE_PREC_MIXED): the forward mode sum and the reverse
+    # sweeps with double-word geometry. Its deviation from the FP64 gradient: per component, the
+    # largest |g_mixed - g_fp64| over the batch divided by the largest |g_fp64|
     grad_mx = torch.empty_like(grad_dev)
     ll_mx = torch.empty_like(ll_dev)
     L.pe_loglike_grad_batch(hs, th_dev, B, mask64 | L.PE_PREC_MIXED, ll_mx, grad_mx, None, stream)
@@ -412,7 +412,8 @@ def main():
                   "ms_per_step": sum(gms_mx) / Kg, "steps": Kg,
                   "max_rel_dgrad_vs_fp64": float(((grad_mx - grad_dev).abs().amax(dim=0)
                                                   / grad_dev.abs().amax(dim=0).clamp_min(1e-300)).max().item()),
-                  "note": "forward mode sum in the mixed-precision unit, reverse sweeps FP64"}
+                  "note": ("FP64 TaylorF2 phase, t_f, turn reductions, PN chain rule and sums; "
+                           "double-word geometry, link factors and their cotangents")}
 
     # ---- Fisher matrix at the injected source (5 modes, all 11 parameters), device-timed
     thf = torch.tensor(wl["inj"][None, :], device="cuda")
@@ -569,7 +570,7 @@ def main():
             "heterodyne": het,
             "tuning": tuned,
             "grad": {"value": grad_value, "unit": "grad evals/s", "ms_per_step": sum(gms) / Kg, "steps": Kg,
-                     "finite": grad_ok, "mixed_forward": grad_mixed},
+                     "finite": grad_ok, "mixed": grad_mixed},
             "gpu_launches": 4 * K,
             "clocks": clk,
             "results_finite": result_ok}

@@ -245,7 +245,9 @@ pe_status pe_surrogate_load(pe_surrogate s, const char* path);
  * automatic differentiation); arguments as pe_loglike_batch, plus out_grad [B][11]
  * (host or device). out_logl may be NULL. mode_mask may carry PE_PREC_MIXED: the per-bin
  * forward mode sum (which out_logl and the cotangents come from) then runs in the mixed-precision
- * unit of pe_loglike_batch; the reverse sweeps stay FP64. PE_PREC_FP32 gives PE_EINVAL. */
+ * unit of pe_loglike_batch, and the reverse sweeps keep FP64 for the phase, t_f, the turn
+ * reductions, the PN-coefficient chain rule and the sums, with the geometry, link factors and
+ * their cotangents in double words. PE_PREC_FP32 gives PE_EINVAL. */
 pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
                                 double* out_logl, double* out_grad, int32_t* out_status, void* stream);
 

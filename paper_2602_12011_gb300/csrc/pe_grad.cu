@@ -12,7 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "pe_adjoint.cuh"
-#include "pe_device_mixed.cuh"
+#include "pe_adjoint_mixed.cuh"
 #include "pe_grad.h"
 
 namespace pe {
@@ -107,10 +107,10 @@ __device__ __forceinline__ void bracket_cotangents(const DetDev& D, int b, const
 }
 
 // MIX: the bin's forward mode sum (the brackets the cotangents need) by the mixed-precision unit
-// (FP64 phase, t_f and turn reductions; double-word geometry), returned to FP64; the reverse
-// sweeps are FP64 either way.
+// (FP64 phase, t_f and turn reductions; double-word geometry), returned to FP64, and the reverse
+// sweeps by mode_bwd_mixed; the cotangents of the A/E/T sums and every accumulation are FP64.
 template <bool MIX>
-__global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+__global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                         const SampleGrad* __restrict__ sgrad,
                                                         const int* __restrict__ nend,
                                                         const long long* __restrict__ off, double* part) {
@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
   __shared__ float4 stabw[MIX ? kSinTab : 1];
   __shared__ double pc[kProj];
   __shared__ float2 pcw[MIX ? kProj : 1];
+  __shared__ float2 mow[MIX ? 30 : 1];   // DetDev::Mo[0..1] as double words
+  __shared__ float2 kpq[MIX ? 9 : 1];    // the sample's k, p, q as double words
   for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
   if constexpr (MIX)
     for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stabw[i] = ds.d[0].sctw[i];
@@ -133,6 +135,15 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
     proj_prologue(D, coef[s], pc);
     if constexpr (MIX) {
       if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+      if (threadIdx.x >= kProj && threadIdx.x < kProj + 30) {
+        const int i = threadIdx.x - kProj;
+        mow[i] = to_dw(D.Mo[i / 15][(i / 5) % 3][i % 5]);
+      }
+      if (threadIdx.x >= kProj + 30 && threadIdx.x < kProj + 39) {
+        const int i = threadIdx.x - kProj - 30;
+        const SampleCoef& S = coef[s];
+        kpq[i] = to_dw(i < 3 ? S.k[i] : (i < 6 ? S.p[i - 3] : S.q[i - 6]));
+      }
       __syncthreads();
     }
     double v[kGradW];
@@ -162,11 +173,32 @@ __global__ void __launch_bounds__(kTileBins) k_grad_fwd(DetSet ds, int B, const 
       bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
       GradAcc g;
       gacc_zero(g);
+      if constexpr (MIX) {
+        BinW W;
+        load_bin_w(D, b, W);
+        const float4 zz = D.zw[b];
+        const cdf zw = {df_make(zz.x, zz.y), df_make(zz.z, zz.w)};
+        const double ih = S.ihsc;
+        const cdf wX = {df_from_bits(sX.x * ih), df_from_bits(sX.y * ih)};
+        const cdf wY = {df_from_bits(sY.x * ih), df_from_bits(sY.y * ih)};
+        const cdf wZ = {df_from_bits(sZ.x * ih), df_from_bits(sZ.y * ih)};
+        GradAccW gw;
+        gaccw_zero(gw);
 #pragma unroll 1
-      for (int md = 0; md < kNModes; ++md) {
-        if (md == 3 && S.pair32) continue;
-        if (S.md[md].active && Bn.f < S.md[md].fend)
-          mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, stab, (md == 0 && S.pair32) ? 3 : -1);
+        for (int md = 0; md < kNModes; ++md) {
+          if (md == 3 && S.pair32) continue;
+          if (S.md[md].active && Bn.f < S.md[md].fend)
+            mode_bwd_mixed(D, S, SG, md, Bn, W, zw, wX, wY, wZ, g, gw, stabw, kpq, mow,
+                           (md == 0 && S.pair32) ? 3 : -1);
+        }
+        gaccw_flush(gw, g);
+      } else {
+#pragma unroll 1
+        for (int md = 0; md < kNModes; ++md) {
+          if (md == 3 && S.pair32) continue;
+          if (S.md[md].active && Bn.f < S.md[md].fend)
+            mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, stab, (md == 0 && S.pair32) ? 3 : -1);
+        }
       }
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
 #pragma unroll

@@ -144,7 +144,8 @@ def test_mixed_full_size_sampled(oracle_mod, Lb):
 
 def test_mixed_batch_invariance_and_entry_points(oracle_mod, Lb):
     """Bitwise batch invariance in mixed precision; a plan gives the direct call's bits; the
-    FP64-only entry points reject the flag."""
+    gradient's log L agrees with the mixed forward's; the FP64-only Fisher entry point rejects
+    the flag."""
     import torch
     T = 2.0 ** 17
     k0, nb = W.grid(T)
@@ -163,9 +164,10 @@ def test_mixed_batch_invariance_and_entry_points(oracle_mod, Lb):
     torch.cuda.synchronize()
     assert np.array_equal(pl.logl.cpu().numpy(), full["logl"])
     pl.close()
-    with pytest.raises(Lb.PeError) as e:
-        Lb.loglike_grad([gd], th[:2], m)
-    assert e.value.status == Lb.PE_EINVAL
+    # the gradient takes the flag (tests/test_gpu_grad.py); its log L (per-bin sums in FP64 over
+    # 128-bin tiles) agrees with the mixed forward's (double-word sums over 512-bin tiles)
+    g = Lb.loglike_grad([gd], th[:2], m)
+    np.testing.assert_allclose(g["logl"], full["logl"][:2], rtol=1e-12, atol=0)
     with pytest.raises(Lb.PeError) as e:
         Lb.fisher([gd], th[:2], m)
     assert e.value.status == Lb.PE_EINVAL
