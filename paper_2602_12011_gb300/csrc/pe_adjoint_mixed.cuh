@@ -39,18 +39,18 @@ __device__ __forceinline__ void gaccw_flush(const GradAccW& a, GradAcc& g) {
 }
 
 __device__ __forceinline__ cdf cdf_add_s(const cdf& a, const cdf& b) {
-  return cdf{df_add_s(a.re, b.re), df_add_s(a.im, b.im)};
+  return cdf{dfl_add(a.re, b.re), dfl_add(a.im, b.im)};
 }
 // a * conj(b). Not inlined (six calls per link), like df_sinc_poly_d (two): the sweep's link loop
 // is long, and one copy of each keeps more of it in the instruction cache.
 static __device__ __noinline__ cdf cdf_mul_conj(const cdf& a, const cdf& b) {
-  return cdf{df_add_s(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_sub_s(df_mul(a.im, b.re), df_mul(a.re, b.im))};
+  return cdf{dfl_add(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_sub(dfl_mul(a.im, b.re), dfl_mul(a.re, b.im))};
 }
 __device__ __forceinline__ cdf cdf_mul_s(const cdf& a, const cdf& b) {
-  return cdf{df_sub_s(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add_s(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+  return cdf{dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_add(dfl_mul(a.re, b.im), dfl_mul(a.im, b.re))};
 }
 __device__ __forceinline__ df dw_dot3(const float2* a, const df b[3]) {
-  return df_add_s(df_add_s(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+  return dfl_add(dfl_add(dfl_mul(a[0], b[0]), dfl_mul(a[1], b[1])), dfl_mul(a[2], b[2]));
 }
 
 // sinc(u) and d sinc/du for |u| <= 1 in double words. With x = u^2: sinc = 1 + x P(x) (the series of
@@ -63,22 +63,22 @@ struct df2 {
 static __device__ __noinline__ df2 df_sinc_poly_d(df u) {
   df2 r;
   r.v = df_sinc_poly(u);
-  const df x = df_mul(u, u);
+  const df x = dfl_mul(u, u);
   float T = __fmaf_rn(x.x, 2.2491659e-14f, -5.3530145e-12f);
   T = __fmaf_rn(T, x.x, 9.635426e-10f);
   T = __fmaf_rn(T, x.x, -1.2526054e-07f);
-  df q = df_add_s(df_make(1.10229275e-05f, 1.5174285e-13f), df_mulf(x, T));   // 4 c4
-  q = df_add_s(df_make(-0.0005952381f, 2.2728706e-11f), df_mul(x, q));          // 3 c3
-  q = df_add_s(df_make(0.016666668f, -8.692344e-10f), df_mul(x, q));            // 2 c2
-  q = df_add_s(df_make(-0.16666667f, 4.967054e-09f), df_mul(x, q));             // c1
-  r.d = df_scale2(df_mul(u, q), 2.0f);
+  df q = dfl_add(df_make(1.10229275e-05f, 1.5174285e-13f), dfl_mulf(x, T));   // 4 c4
+  q = dfl_add(df_make(-0.0005952381f, 2.2728706e-11f), dfl_mul(x, q));          // 3 c3
+  q = dfl_add(df_make(0.016666668f, -8.692344e-10f), dfl_mul(x, q));            // 2 c2
+  q = dfl_add(df_make(-0.16666667f, 4.967054e-09f), dfl_mul(x, q));             // c1
+  r.d = df_scale2(dfl_mul(u, q), 2.0f);
   return r;
 }
 // d sinc/du for |u| < 1e-3: u (-1/3 + u^2/30) (the dropped u^5/840 is below 1.2e-15 of the result)
 __device__ __forceinline__ df df_dsinc_small(df u) {
-  const df u2 = df_mul(u, u);
+  const df u2 = dfl_mul(u, u);
   const df p = df_make(-0.33333334f, __fmaf_rn(u2.x, 0.033333335f, 9.934108e-09f));
-  return df_mul(u, p);
+  return dfl_mul(u, p);
 }
 
 // Reverse sweep of one unit in double words; arguments as mode_bwd, plus: W, zw: the bin's
@@ -118,19 +118,19 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
     w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
   }
   // ---------------- double words: amplitude times hsc (A0 before the taper, A after it)
-  const df vw = df_mul(C.cmw, W.f13);
-  df A0 = df_mul(C.ampw, W.fm76);
-  if (C.p >= 1) A0 = df_mul(A0, vw);
-  if (C.p >= 2) A0 = df_mul(A0, vw);
-  const df A = tap ? df_mul(A0, df_from_bits(w)) : A0;
+  const df vw = dfl_mul(C.cmw, W.f13);
+  df A0 = dfl_mul(C.ampw, W.fm76);
+  if (C.p >= 1) A0 = dfl_mul(A0, vw);
+  if (C.p >= 2) A0 = dfl_mul(A0, vw);
+  const df A = tap ? dfl_mul(A0, df_from_bits(w)) : A0;
   // orbit (row A4): centre angle, the offsets' basis, spacecraft offsets d_0, d_1
   const cdf eo = df_cis_turns(frac_dw(fma(tf, D.rate_t, D.alpha0_t)), tab);
   const df co = eo.re, so = eo.im;
   df ob[4];
   cdf eg = {df_make(0.f, 0.f), df_make(0.f, 0.f)};
   if (D.orbit == 0) {
-    ob[0] = df_sub_s(df_mul(co, co), df_mul(so, so));
-    ob[1] = df_scale2(df_mul(so, co), 2.0f);
+    ob[0] = dfl_sub(dfl_mul(co, co), dfl_mul(so, so));
+    ob[1] = df_scale2(dfl_mul(so, co), 2.0f);
     ob[2] = co;
     ob[3] = so;
   } else {
@@ -147,20 +147,20 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
   }
   // mode phase (FP64 part reduced to a fraction of a turn) minus f k.x_c; third-spacecraft phases
   // theta_t = f k.d_t / 2 in turns
-  const df kxc = df_mul(D.Rw, df_add_s(df_mul(kpq[0], co), df_mul(kpq[1], so)));
-  const df pf = df_sub_s(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), df_mul(W.f, kxc));
+  const df kxc = dfl_mul(D.Rw, dfl_add(dfl_mul(kpq[0], co), dfl_mul(kpq[1], so)));
+  const df pf = dfl_sub(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), dfl_mul(W.f, kxc));
   const df hf = df_scale2(W.f, 0.5f);
-  const df th0 = df_mul(hf, dw_dot3(kpq, d0)), th1 = df_mul(hf, dw_dot3(kpq, d1));
-  const df th01 = df_add_s(th0, th1);
-  const df pif = df_mul(W.f, df_make(3.1415927f, -8.742278e-08f));   // pi f
+  const df th0 = dfl_mul(hf, dw_dot3(kpq, d0)), th1 = dfl_mul(hf, dw_dot3(kpq, d1));
+  const df th01 = dfl_add(th0, th1);
+  const df pif = dfl_mul(W.f, df_make(3.1415927f, -8.742278e-08f));   // pi f
   // polarisation weights Ap = Pp + kappa Pp2, Ac = Pc + kappa Pc2 (kappa = k32 v^2; 0 unpaired)
   cdf Ap = {C.Ppw, df_make(0.f, 0.f)}, Ac = {C.Pcw, df_make(0.f, 0.f)};
   if (md2 >= 0) {
-    const df v2 = df_mul(vw, vw);
-    const df kr = df_mul(S.k32w[0], v2), ki = df_mul(S.k32w[1], v2);
+    const df v2 = dfl_mul(vw, vw);
+    const df kr = dfl_mul(S.k32w[0], v2), ki = dfl_mul(S.k32w[1], v2);
     const ModeCoef& C2 = S.md[md2];
-    Ap = cdf{df_add_s(C.Ppw, df_mul(kr, C2.Ppw)), df_mul(ki, C2.Ppw)};
-    Ac = cdf{df_add_s(C.Pcw, df_mul(kr, C2.Pcw)), df_mul(ki, C2.Pcw)};
+    Ap = cdf{dfl_add(C.Ppw, dfl_mul(kr, C2.Ppw)), dfl_mul(ki, C2.Ppw)};
+    Ac = cdf{dfl_add(C.Pcw, dfl_mul(kr, C2.Pcw)), dfl_mul(ki, C2.Pcw)};
   }
   // ---------------- links: forward and reverse, one pair at a time (seeds as in mode_bwd)
   const df zero = df_make(0.f, 0.f);
@@ -180,23 +180,23 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
     df n[3], dt[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      n[j] = df_add_s(df_scale2(d0[j], al), df_scale2(d1[j], be));
-      dt[j] = df_add_s(df_scale2(d0[j], ga), df_scale2(d1[j], de));
+      n[j] = dfl_add(df_scale2(d0[j], al), df_scale2(d1[j], be));
+      dt[j] = dfl_add(df_scale2(d0[j], ga), df_scale2(d1[j], de));
     }
-    const df inv = df_rsqrt(df_add_s(df_add_s(df_mul(n[0], n[0]), df_mul(n[1], n[1])), df_mul(n[2], n[2])));
+    const df inv = df_rsqrt(dfl_add(dfl_add(dfl_mul(n[0], n[0]), dfl_mul(n[1], n[1])), dfl_mul(n[2], n[2])));
 #pragma unroll
-    for (int j = 0; j < 3; ++j) n[j] = df_mul(n[j], inv);
+    for (int j = 0; j < 3; ++j) n[j] = dfl_mul(n[j], inv);
     const df kn = dw_dot3(kpq, n), np = dw_dot3(kpq + 3, n), nq = dw_dot3(kpq + 6, n);
-    const df Fp = df_sub_s(df_mul(np, np), df_mul(nq, nq));
-    const df Fc = df_scale2(df_mul(np, nq), 2.0f);
-    const cdf gam = (md2 >= 0) ? cdf{df_sub_s(df_mul(Ap.re, Fp), df_mul(Ac.im, Fc)),
-                                     df_add_s(df_mul(Ap.im, Fp), df_mul(Ac.re, Fc))}
-                               : cdf{df_mul(Ap.re, Fp), df_mul(Ac.re, Fc)};
-    const cdf E = df_cis_turns(l == 0 ? df_sub_s(pf, th01) : df_add_s(pf, l == 1 ? th0 : th1), tab);
-    const cdf K = {df_mul(A, gam.re), df_mul(A, gam.im)};
+    const df Fp = dfl_sub(dfl_mul(np, np), dfl_mul(nq, nq));
+    const df Fc = df_scale2(dfl_mul(np, nq), 2.0f);
+    const cdf gam = (md2 >= 0) ? cdf{dfl_sub(dfl_mul(Ap.re, Fp), dfl_mul(Ac.im, Fc)),
+                                     dfl_add(dfl_mul(Ap.im, Fp), dfl_mul(Ac.re, Fc))}
+                               : cdf{dfl_mul(Ap.re, Fp), dfl_mul(Ac.re, Fc)};
+    const cdf E = df_cis_turns(l == 0 ? dfl_sub(pf, th01) : dfl_add(pf, l == 1 ? th0 : th1), tab);
+    const cdf K = {dfl_mul(A, gam.re), dfl_mul(A, gam.im)};
     const cdf G = cdf_mul_s(K, E);
-    const df akn = df_mul(W.a, kn);
-    const df u1 = df_sub_s(W.a, akn), u2 = df_add_s(W.a, akn);
+    const df akn = dfl_mul(W.a, kn);
+    const df u1 = dfl_sub(W.a, akn), u2 = dfl_add(W.a, akn);
     df sm, spl, dsm, dspl;   // sinc(u1), sinc(u2) and their derivatives
     if (B.a < kSincPolyA) {
       const df2 r1 = df_sinc_poly_d(u1), r2 = df_sinc_poly_d(u2);
@@ -205,63 +205,63 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
       spl = r2.v;
       dspl = r2.d;
     } else {
-      const cdf ea = df_cis_turns(df_mul(W.at, kn), tab);
-      const df x1 = df_mul(W.sa, ea.re), x2 = df_mul(W.ca, ea.im);
-      const df y1 = df_mul(W.ca, ea.re), y2 = df_mul(W.sa, ea.im);
-      const df s1 = df_sub_s(x1, x2), s2 = df_add_s(x1, x2);   // sin u1, sin u2
-      const df c1 = df_add_s(y1, y2), c2 = df_sub_s(y1, y2);   // cos u1, cos u2
+      const cdf ea = df_cis_turns(dfl_mul(W.at, kn), tab);
+      const df x1 = dfl_mul(W.sa, ea.re), x2 = dfl_mul(W.ca, ea.im);
+      const df y1 = dfl_mul(W.ca, ea.re), y2 = dfl_mul(W.sa, ea.im);
+      const df s1 = dfl_sub(x1, x2), s2 = dfl_add(x1, x2);   // sin u1, sin u2
+      const df c1 = dfl_add(y1, y2), c2 = dfl_sub(y1, y2);   // cos u1, cos u2
       if (fabsf(u1.x) < 1e-3f) {
         sm = df_sinc_small(u1);
         dsm = df_dsinc_small(u1);
       } else {
         const df r1 = df_rcp(u1);
-        sm = df_mul(s1, r1);
-        dsm = df_mul(df_sub_s(c1, sm), r1);
+        sm = dfl_mul(s1, r1);
+        dsm = dfl_mul(dfl_sub(c1, sm), r1);
       }
       if (fabsf(u2.x) < 1e-3f) {
         spl = df_sinc_small(u2);
         dspl = df_dsinc_small(u2);
       } else {
         const df r2 = df_rcp(u2);
-        spl = df_mul(s2, r2);
-        dspl = df_mul(df_sub_s(c2, spl), r2);
+        spl = dfl_mul(s2, r2);
+        dspl = dfl_mul(dfl_sub(c2, spl), r2);
       }
     }
-    const cdf U = {df_add_s(df_mul(zw.re, spl), sm), df_mul(zw.im, spl)};
-    const cdf V = {df_add_s(df_mul(zw.re, sm), spl), df_mul(zw.im, sm)};
+    const cdf U = {dfl_add(dfl_mul(zw.re, spl), sm), dfl_mul(zw.im, spl)};
+    const cdf V = {dfl_add(dfl_mul(zw.re, sm), spl), dfl_mul(zw.im, sm)};
     // reverse
     const cdf Gb = cdf_add_s(cdf_mul_conj(Su, U), cdf_mul_conj(Sv, V));
     const cdf Ub = cdf_mul_conj(Su, G), Vb = cdf_mul_conj(Sv, G);
-    const df smb = df_add_s(Ub.re, df_add_s(df_mul(Vb.re, zw.re), df_mul(Vb.im, zw.im)));
-    const df splb = df_add_s(df_add_s(df_mul(Ub.re, zw.re), df_mul(Ub.im, zw.im)), Vb.re);
-    const df knb = df_mul(W.a, df_sub_s(df_mul(splb, dspl), df_mul(smb, dsm)));
+    const df smb = dfl_add(Ub.re, dfl_add(dfl_mul(Vb.re, zw.re), dfl_mul(Vb.im, zw.im)));
+    const df splb = dfl_add(dfl_add(dfl_mul(Ub.re, zw.re), dfl_mul(Ub.im, zw.im)), Vb.re);
+    const df knb = dfl_mul(W.a, dfl_sub(dfl_mul(splb, dspl), dfl_mul(smb, dsm)));
     const cdf Eb = cdf_mul_conj(Gb, K), Kb = cdf_mul_conj(Gb, E);
-    const df thb = df_sub_s(df_mul(E.re, Eb.im), df_mul(E.im, Eb.re));
-    phtb = df_add_s(phtb, thb);
-    const df kdb = df_mul(pif, thb);
-    const cdf gamb = {df_mul(A, Kb.re), df_mul(A, Kb.im)};
-    ampb = df_add_s(ampb, df_add_s(df_mul(Kb.re, gam.re), df_mul(Kb.im, gam.im)));
-    Apb = cdf{df_add_s(Apb.re, df_mul(gamb.re, Fp)), df_add_s(Apb.im, df_mul(gamb.im, Fp))};
-    Acb = cdf{df_add_s(Acb.re, df_mul(gamb.im, Fc)), df_sub_s(Acb.im, df_mul(gamb.re, Fc))};
-    const df Fpb = df_add_s(df_mul(gamb.re, Ap.re), df_mul(gamb.im, Ap.im));
-    const df Fcb = df_sub_s(df_mul(gamb.im, Ac.re), df_mul(gamb.re, Ac.im));
-    const df npb = df_scale2(df_add_s(df_mul(np, Fpb), df_mul(nq, Fcb)), 2.0f);
-    const df nqb = df_scale2(df_sub_s(df_mul(np, Fcb), df_mul(nq, Fpb)), 2.0f);
+    const df thb = dfl_sub(dfl_mul(E.re, Eb.im), dfl_mul(E.im, Eb.re));
+    phtb = dfl_add(phtb, thb);
+    const df kdb = dfl_mul(pif, thb);
+    const cdf gamb = {dfl_mul(A, Kb.re), dfl_mul(A, Kb.im)};
+    ampb = dfl_add(ampb, dfl_add(dfl_mul(Kb.re, gam.re), dfl_mul(Kb.im, gam.im)));
+    Apb = cdf{dfl_add(Apb.re, dfl_mul(gamb.re, Fp)), dfl_add(Apb.im, dfl_mul(gamb.im, Fp))};
+    Acb = cdf{dfl_add(Acb.re, dfl_mul(gamb.im, Fc)), dfl_sub(Acb.im, dfl_mul(gamb.re, Fc))};
+    const df Fpb = dfl_add(dfl_mul(gamb.re, Ap.re), dfl_mul(gamb.im, Ap.im));
+    const df Fcb = dfl_sub(dfl_mul(gamb.im, Ac.re), dfl_mul(gamb.re, Ac.im));
+    const df npb = df_scale2(dfl_add(dfl_mul(np, Fpb), dfl_mul(nq, Fcb)), 2.0f);
+    const df nqb = df_scale2(dfl_sub(dfl_mul(np, Fcb), dfl_mul(nq, Fpb)), 2.0f);
     df nb[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      gw.k[j] = df_add_s(gw.k[j], df_add_s(df_mul(knb, n[j]), df_mul(kdb, dt[j])));
-      gw.p[j] = df_add_s(gw.p[j], df_mul(npb, n[j]));
-      gw.q[j] = df_add_s(gw.q[j], df_mul(nqb, n[j]));
-      nb[j] = df_add_s(df_add_s(df_mul(knb, kpq[j]), df_mul(npb, kpq[3 + j])), df_mul(nqb, kpq[6 + j]));
+      gw.k[j] = dfl_add(gw.k[j], dfl_add(dfl_mul(knb, n[j]), dfl_mul(kdb, dt[j])));
+      gw.p[j] = dfl_add(gw.p[j], dfl_mul(npb, n[j]));
+      gw.q[j] = dfl_add(gw.q[j], dfl_mul(nqb, n[j]));
+      nb[j] = dfl_add(dfl_add(dfl_mul(knb, kpq[j]), dfl_mul(npb, kpq[3 + j])), dfl_mul(nqb, kpq[6 + j]));
     }
-    const df dot = df_add_s(df_add_s(df_mul(nb[0], n[0]), df_mul(nb[1], n[1])), df_mul(nb[2], n[2]));
+    const df dot = dfl_add(dfl_add(dfl_mul(nb[0], n[0]), dfl_mul(nb[1], n[1])), dfl_mul(nb[2], n[2]));
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const df db = df_mul(df_sub_s(nb[j], df_mul(dot, n[j])), inv);   // cotangent of x_r - x_s
-      const df kk = df_mul(kdb, kpq[j]);                                // of the third spacecraft's offset
-      d0b[j] = df_add_s(d0b[j], df_add_s(df_scale2(db, al), df_scale2(kk, ga)));
-      d1b[j] = df_add_s(d1b[j], df_add_s(df_scale2(db, be), df_scale2(kk, de)));
+      const df db = dfl_mul(dfl_sub(nb[j], dfl_mul(dot, n[j])), inv);   // cotangent of x_r - x_s
+      const df kk = dfl_mul(kdb, kpq[j]);                                // of the third spacecraft's offset
+      d0b[j] = dfl_add(d0b[j], dfl_add(df_scale2(db, al), df_scale2(kk, ga)));
+      d1b[j] = dfl_add(d1b[j], dfl_add(df_scale2(db, be), df_scale2(kk, de)));
     }
   }
   // ---------------- the offsets' basis: obb[m] = sum_j d0b_j Mo[0][j][m] + d1b_j Mo[1][j][m]
@@ -270,7 +270,7 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
   for (int m = 0; m < 4; ++m) {
     df a = zero;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) a = df_add_s(a, df_add_s(df_mul(d0b[j], mow[5 * j + m]), df_mul(d1b[j], mow[15 + 5 * j + m])));
+    for (int j = 0; j < 3; ++j) a = dfl_add(a, dfl_add(dfl_mul(d0b[j], mow[5 * j + m]), dfl_mul(d1b[j], mow[15 + 5 * j + m])));
     obb[m] = df_to(a);
   }
   // ---------------- FP64: mode level (as mode_bwd from here)
@@ -296,13 +296,13 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
   const double Db = tfb * C.tffac * B.invf;
   double vb = 0.0;
   if (C.amp != 0.0 && w != 0.0) {
-    const double lnAb = df_to(df_mul(ampb, A));
+    const double lnAb = df_to(dfl_mul(ampb, A));
     g.M = fma(lnAb, CG.dlnA_dM, g.M);
     g.q = fma(lnAb, CG.dlnA_dq, g.q);
     g.dL = fma(lnAb, SG.dlnA_ddL, g.dL);
     vb = lnAb * double(C.p) / v;
     if (tap) {
-      const double wb = df_to(df_mul(ampb, A0));
+      const double wb = df_to(dfl_mul(ampb, A0));
       const double zb = -wb * w * (1.0 - w);
       const double fe = C.fend, ft = C.ftap, As = fe - ft;
       const double dz = 0.1 / (fe - B.f) - As / ((fe - B.f) * (fe - B.f)) - 0.1 / (B.f - ft) -

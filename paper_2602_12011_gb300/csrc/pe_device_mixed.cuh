@@ -29,9 +29,9 @@ __device__ __forceinline__ void mix_zero(MixAcc& a) {
 __device__ __forceinline__ void mix_final(const MixAcc& a, const cdf& z, cdf x[3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const cdf zq = cdf_mul(z, cdf{a.Qr[i], a.Qi[i]});
-    x[i].re = df_add_s(a.Pr[i], zq.re);
-    x[i].im = df_add_s(a.Pi[i], zq.im);
+    const cdf zq = cdfl_mul(z, cdf{a.Qr[i], a.Qi[i]});
+    x[i].re = dfl_add(a.Pr[i], zq.re);
+    x[i].im = dfl_add(a.Pi[i], zq.im);
   }
 }
 
@@ -52,9 +52,9 @@ __device__ __forceinline__ void load_bin_w(const DetDev& D, int b, BinW& W) {
 // sinc(u) for |u| < 1e-3: 1 + u^2 (-1/6 + u^2/120) (the u^2/120 term enters the low word of -1/6;
 // the dropped u^6/5040 is below 2e-22)
 __device__ __forceinline__ df df_sinc_small(df u) {
-  const df u2 = df_mul(u, u);
+  const df u2 = dfl_mul(u, u);
   const df p = df_make(-0.166666672f, __fmaf_rn(u2.x, 1.0f / 120.0f, 4.96705388e-09f));
-  return df_add_s(df_make(1.f, 0.f), df_mul(u2, p));
+  return dfl_add(df_make(1.f, 0.f), dfl_mul(u2, p));
 }
 
 // p[0..3] . b + p[4] in double words (the projection forms of DetDev::Mo, see proj_coef)
@@ -63,20 +63,20 @@ __device__ __forceinline__ df df_sinc_small(df u) {
 // 2.5e-8 and is evaluated in float (its rounding stays below 1e-14 of the result); the first
 // dropped term is below 1/19! = 8.2e-18.
 __device__ __forceinline__ df df_sinc_poly(df u) {
-  const df x = df_mul(u, u);
+  const df x = dfl_mul(u, u);
   float T = __fmaf_rn(x.x, 1.0f / 355687428096000.0f, -1.0f / 1307674368000.0f);
   T = __fmaf_rn(T, x.x, 1.0f / 6227020800.0f);
   T = __fmaf_rn(T, x.x, -1.0f / 39916800.0f);
-  df p = df_add_s(df_make(2.75573188e-06f, 3.79357122e-14f), df_mulf(x, T));       // 1/9!
-  p = df_add_s(df_make(-0.000198412701f, 2.72559687e-12f), df_mul(x, p));           // -1/7!
-  p = df_add_s(df_make(0.00833333377f, -4.34617203e-10f), df_mul(x, p));            // 1/5!
-  p = df_add_s(df_make(-0.166666672f, 4.96705388e-09f), df_mul(x, p));              // -1/3!
-  return df_add_s(df_make(1.f, 0.f), df_mul(x, p));
+  df p = dfl_add(df_make(2.75573188e-06f, 3.79357122e-14f), dfl_mulf(x, T));       // 1/9!
+  p = dfl_add(df_make(-0.000198412701f, 2.72559687e-12f), dfl_mul(x, p));           // -1/7!
+  p = dfl_add(df_make(0.00833333377f, -4.34617203e-10f), dfl_mul(x, p));            // 1/5!
+  p = dfl_add(df_make(-0.166666672f, 4.96705388e-09f), dfl_mul(x, p));              // -1/3!
+  return dfl_add(df_make(1.f, 0.f), dfl_mul(x, p));
 }
 
 __device__ __forceinline__ df dw_dot5(const float2* p, const df b[4]) {
-  return df_add_s(df_add_s(df_mul(p[0], b[0]), df_mul(p[1], b[1])),
-                  df_add_s(df_add_s(df_mul(p[2], b[2]), df_mul(p[3], b[3])), p[4]));
+  return dfl_add(dfl_add(dfl_mul(p[0], b[0]), dfl_mul(p[1], b[1])),
+                  dfl_add(dfl_add(dfl_mul(p[2], b[2]), dfl_mul(p[3], b[3])), p[4]));
 }
 
 // double -> double word of the fraction x - rint(x) (exact in FP64), for the sincos of a turn count
@@ -103,38 +103,38 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
   const double tf = fma(C.tffac * B.invf, dv, S.tc);
   // amplitude (times hsc) in double words: ampw f^(-7/6) v^p, times the taper where it is below 1
-  df A = df_mul(C.ampw, W.fm76);
+  df A = dfl_mul(C.ampw, W.fm76);
   if (C.p >= 1) {
-    const df vw = df_mul(C.cmw, W.f13);
-    A = df_mul(A, vw);
-    if (C.p >= 2) A = df_mul(A, vw);
+    const df vw = dfl_mul(C.cmw, W.f13);
+    A = dfl_mul(A, vw);
+    if (C.p >= 2) A = dfl_mul(A, vw);
   }
   if (B.f > C.ftap) {
     const double span = C.fend - C.ftap;
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
-    A = df_mul(A, df_from_bits((zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt))));
+    A = dfl_mul(A, df_from_bits((zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt))));
   }
   // polarisation weights times the amplitude; a paired second mode makes them complex:
   // Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
-  cdf Ap = {df_mul(A, C.Ppw), df_make(0.f, 0.f)}, Ac = {df_mul(A, C.Pcw), df_make(0.f, 0.f)};
+  cdf Ap = {dfl_mul(A, C.Ppw), df_make(0.f, 0.f)}, Ac = {dfl_mul(A, C.Pcw), df_make(0.f, 0.f)};
   if (C2) {
-    const df vw = df_mul(C.cmw, W.f13);
-    const df v2 = df_mul(vw, vw);
-    const df kr = df_mul(S.k32w[0], v2), ki = df_mul(S.k32w[1], v2);
-    Ap = cdf{df_mul(A, df_add_s(C.Ppw, df_mul(kr, C2->Ppw))), df_mul(A, df_mul(ki, C2->Ppw))};
-    Ac = cdf{df_mul(A, df_add_s(C.Pcw, df_mul(kr, C2->Pcw))), df_mul(A, df_mul(ki, C2->Pcw))};
+    const df vw = dfl_mul(C.cmw, W.f13);
+    const df v2 = dfl_mul(vw, vw);
+    const df kr = dfl_mul(S.k32w[0], v2), ki = dfl_mul(S.k32w[1], v2);
+    Ap = cdf{dfl_mul(A, dfl_add(C.Ppw, dfl_mul(kr, C2->Ppw))), dfl_mul(A, dfl_mul(ki, C2->Ppw))};
+    Ac = cdf{dfl_mul(A, dfl_add(C.Pcw, dfl_mul(kr, C2->Pcw))), dfl_mul(A, dfl_mul(ki, C2->Pcw))};
   }
   // --- orbital angle alpha(t_f) (row A4), centre Doppler f k.x_c, x_c = R (cos a, sin a, 0)
   const cdf eo = df_cis_turns(frac_dw(fma(tf, D.rate_t, D.alpha0_t)), tab);
   const df co = eo.re, so = eo.im;
-  const df kxc = df_mul(D.Rw, df_add_s(df_mul(S.kw[0], co), df_mul(S.kw[1], so)));
+  const df kxc = dfl_mul(D.Rw, dfl_add(dfl_mul(S.kw[0], co), dfl_mul(S.kw[1], so)));
   // mode phase: the FP64 part reduced to a fraction of a turn, minus f k.x_c in double words
-  const df pf = df_sub_s(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), df_mul(W.f, kxc));
+  const df pf = dfl_sub(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), dfl_mul(W.f, kxc));
   // --- the offsets' basis (DetDev::Mo)
   df ob[4];
   if (D.orbit == 0) {
-    ob[0] = df_sub_s(df_mul(co, co), df_mul(so, so));
-    ob[1] = df_scale2(df_mul(so, co), 2.0f);
+    ob[0] = dfl_sub(dfl_mul(co, co), dfl_mul(so, so));
+    ob[1] = df_scale2(dfl_mul(so, co), 2.0f);
     ob[2] = co;
     ob[3] = so;
   } else {
@@ -145,9 +145,9 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   }
   // --- third-spacecraft phases pi f k.delta_t (the offsets sum to zero, so delta_2's phase is
   // minus the other two); each link takes the mode phase plus its third spacecraft's phase
-  const df e0 = df_scale2(df_mul(W.f, dw_dot5(pcw + 45, ob)), 0.5f);
-  const df e1 = df_scale2(df_mul(W.f, dw_dot5(pcw + 50, ob)), 0.5f);
-  const df e01 = df_add_s(e0, e1);
+  const df e0 = df_scale2(dfl_mul(W.f, dw_dot5(pcw + 45, ob)), 0.5f);
+  const df e1 = df_scale2(dfl_mul(W.f, dw_dot5(pcw + 50, ob)), 0.5f);
+  const df e01 = dfl_add(e0, e1);
   // --- links (row A5); the loop stays rolled (one copy of its body) for the instruction cache.
   // Projections of the unnormalised link vectors x_r - x_s: the three sum to zero, so the third
   // is minus the sum of the other two
@@ -161,45 +161,45 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
       knr = dw_dot5(pcw + 15 * l, ob);
       npr = dw_dot5(pcw + 15 * l + 5, ob);
       nqr = dw_dot5(pcw + 15 * l + 10, ob);
-      sk = df_add_s(sk, knr);
-      sp = df_add_s(sp, npr);
-      sq = df_add_s(sq, nqr);
+      sk = dfl_add(sk, knr);
+      sp = dfl_add(sp, npr);
+      sq = dfl_add(sq, nqr);
     } else {
       knr = df_make(-sk.x, -sk.y);
       npr = df_make(-sp.x, -sp.y);
       nqr = df_make(-sq.x, -sq.y);
     }
-    const df inv = df_rsqrt(df_add_s(df_mul(knr, knr), df_add_s(df_mul(npr, npr), df_mul(nqr, nqr))));
-    const df kn = df_mul(knr, inv);
-    const df np = df_mul(npr, inv);
-    const df nq = df_mul(nqr, inv);
-    const df Fp = df_sub_s(df_mul(np, np), df_mul(nq, nq));
-    const df Fc = df_scale2(df_mul(np, nq), 2.0f);
-    const cdf gam = C2 ? cdf{df_sub_s(df_mul(Ap.re, Fp), df_mul(Ac.im, Fc)), df_add_s(df_mul(Ap.im, Fp), df_mul(Ac.re, Fc))}
-                       : cdf{df_mul(Ap.re, Fp), df_mul(Ac.re, Fc)};
+    const df inv = df_rsqrt(dfl_add(dfl_mul(knr, knr), dfl_add(dfl_mul(npr, npr), dfl_mul(nqr, nqr))));
+    const df kn = dfl_mul(knr, inv);
+    const df np = dfl_mul(npr, inv);
+    const df nq = dfl_mul(nqr, inv);
+    const df Fp = dfl_sub(dfl_mul(np, np), dfl_mul(nq, nq));
+    const df Fc = df_scale2(dfl_mul(np, nq), 2.0f);
+    const cdf gam = C2 ? cdf{dfl_sub(dfl_mul(Ap.re, Fp), dfl_mul(Ac.im, Fc)), dfl_add(dfl_mul(Ap.im, Fp), dfl_mul(Ac.re, Fc))}
+                       : cdf{dfl_mul(Ap.re, Fp), dfl_mul(Ac.re, Fc)};
     // third spacecraft t = (l + 2) % 3
-    const cdf Et = df_cis_turns(l == 0 ? df_sub_s(pf, e01) : df_add_s(pf, l == 1 ? e0 : e1), tab);
-    G[l] = cdf_mul(gam, Et);
+    const cdf Et = df_cis_turns(l == 0 ? dfl_sub(pf, e01) : dfl_add(pf, l == 1 ? e0 : e1), tab);
+    G[l] = cdfl_mul(gam, Et);
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (|u| <= 2a < 1), else from
     // sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
-    const df akn = df_mul(W.a, kn);
-    const df u1 = df_sub_s(W.a, akn), u2 = df_add_s(W.a, akn);
+    const df akn = dfl_mul(W.a, kn);
+    const df u1 = dfl_sub(W.a, akn), u2 = dfl_add(W.a, akn);
     if (B.a < kSincPolyA) {
       smv[l] = df_sinc_poly(u1);
       spv[l] = df_sinc_poly(u2);
     } else {
-      const cdf ea = df_cis_turns(df_mul(W.at, kn), tab);
+      const cdf ea = df_cis_turns(dfl_mul(W.at, kn), tab);
       const df sak = ea.im, cak = ea.re;
-      const df x1 = df_mul(W.sa, cak), x2 = df_mul(W.ca, sak);
-      const df s1 = df_sub_s(x1, x2), s2 = df_add_s(x1, x2);
+      const df x1 = dfl_mul(W.sa, cak), x2 = dfl_mul(W.ca, sak);
+      const df s1 = dfl_sub(x1, x2), s2 = dfl_add(x1, x2);
       const bool small1 = fabsf(u1.x) < 1e-3f, small2 = fabsf(u2.x) < 1e-3f;
       if (!small1 && !small2) {
-        const df rr = df_rcp(df_mul(u1, u2));
-        smv[l] = df_mul(df_mul(s1, u2), rr);
-        spv[l] = df_mul(df_mul(s2, u1), rr);
+        const df rr = df_rcp(dfl_mul(u1, u2));
+        smv[l] = dfl_mul(dfl_mul(s1, u2), rr);
+        spv[l] = dfl_mul(dfl_mul(s2, u1), rr);
       } else {
-        smv[l] = small1 ? df_sinc_small(u1) : df_mul(s1, df_rcp(u1));
-        spv[l] = small2 ? df_sinc_small(u2) : df_mul(s2, df_rcp(u2));
+        smv[l] = small1 ? df_sinc_small(u1) : dfl_mul(s1, df_rcp(u1));
+        spv[l] = small2 ? df_sinc_small(u2) : dfl_mul(s2, df_rcp(u2));
       }
     }
   }
@@ -207,10 +207,10 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int lp = (c + 2) % 3, lu = c;
-    acc.Pr[c] = df_add_s(acc.Pr[c], df_sub_s(df_mul(G[lp].re, spv[lp]), df_mul(G[lu].re, smv[lu])));
-    acc.Pi[c] = df_add_s(acc.Pi[c], df_sub_s(df_mul(G[lp].im, spv[lp]), df_mul(G[lu].im, smv[lu])));
-    acc.Qr[c] = df_add_s(acc.Qr[c], df_sub_s(df_mul(G[lp].re, smv[lp]), df_mul(G[lu].re, spv[lu])));
-    acc.Qi[c] = df_add_s(acc.Qi[c], df_sub_s(df_mul(G[lp].im, smv[lp]), df_mul(G[lu].im, spv[lu])));
+    acc.Pr[c] = dfl_add(acc.Pr[c], dfl_sub(dfl_mul(G[lp].re, spv[lp]), dfl_mul(G[lu].re, smv[lu])));
+    acc.Pi[c] = dfl_add(acc.Pi[c], dfl_sub(dfl_mul(G[lp].im, spv[lp]), dfl_mul(G[lu].im, smv[lu])));
+    acc.Qr[c] = dfl_add(acc.Qr[c], dfl_sub(dfl_mul(G[lp].re, smv[lp]), dfl_mul(G[lu].re, spv[lu])));
+    acc.Qi[c] = dfl_add(acc.Qi[c], dfl_sub(dfl_mul(G[lp].im, smv[lp]), dfl_mul(G[lu].im, spv[lu])));
   }
 }
 
@@ -238,12 +238,12 @@ __device__ __forceinline__ void bin_xyz_mixed(const DetDev& D, const SampleCoef&
 // A/E/T combinations (without Q n_c) in double words: B_A = Z' - X', B_E = X' - 2Y' + Z',
 // B_T = X' + Y' + Z'.
 __device__ __forceinline__ void aet_from_xyz_dw(const cdf x[3], cdf o[3]) {
-  o[0].re = df_sub_s(x[2].re, x[0].re);
-  o[0].im = df_sub_s(x[2].im, x[0].im);
-  o[1].re = df_sub_s(df_add_s(x[0].re, x[2].re), df_scale2(x[1].re, 2.0f));
-  o[1].im = df_sub_s(df_add_s(x[0].im, x[2].im), df_scale2(x[1].im, 2.0f));
-  o[2].re = df_add_s(df_add_s(x[0].re, x[1].re), x[2].re);
-  o[2].im = df_add_s(df_add_s(x[0].im, x[1].im), x[2].im);
+  o[0].re = dfl_sub(x[2].re, x[0].re);
+  o[0].im = dfl_sub(x[2].im, x[0].im);
+  o[1].re = dfl_sub(dfl_add(x[0].re, x[2].re), df_scale2(x[1].re, 2.0f));
+  o[1].im = dfl_sub(dfl_add(x[0].im, x[2].im), df_scale2(x[1].im, 2.0f));
+  o[2].re = dfl_add(dfl_add(x[0].re, x[1].re), x[2].re);
+  o[2].im = dfl_add(dfl_add(x[0].im, x[1].im), x[2].im);
 }
 
 }  // namespace pe

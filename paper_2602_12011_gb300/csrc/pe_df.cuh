@@ -112,6 +112,28 @@ __device__ __forceinline__ df df_rsqrt(df x) {
   return df_add(df_make(y0, 0.f), df_mulf(df_scale2(e, 0.5f), y0));
 }
 
+// Unnormalised ("lazy") variants for the long chains of the mixed-precision units. dfl_add is
+// df_add_s without its closing Fast2Sum: the same rounded quantities, so the same absolute error
+// (~2 u^2 (|x| + |y|)), but |lo| may exceed ulp(hi)/2 by a few ulps. dfl_mul is Alg. 12 without
+// the lo x lo product (below u^2 |x y|) and without the closing Fast2Sum. Pairs from them are
+// fine operands for every operation here; df_cis_turns renormalises its argument, the one place
+// that needs |lo| <= ulp(hi)/2.
+__device__ __forceinline__ df dfl_add(df x, df y) {
+  const df s = two_sum(x.x, y.x);
+  return df_make(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
+__device__ __forceinline__ df dfl_sub(df x, df y) { return dfl_add(x, make_float2(-y.x, -y.y)); }
+__device__ __forceinline__ df dfl_mul(df x, df y) {
+  const float ch = __fmul_rn(x.x, y.x);
+  const float cl1 = __fmaf_rn(x.x, y.x, -ch);
+  const float cl2 = __fmaf_rn(x.y, y.x, __fmul_rn(x.x, y.y));
+  return df_make(ch, __fadd_rn(cl1, cl2));
+}
+__device__ __forceinline__ df dfl_mulf(df x, float y) {
+  const float ch = __fmul_rn(x.x, y);
+  return df_make(ch, __fmaf_rn(x.y, y, __fmaf_rn(x.x, y, -ch)));
+}
+
 // complex DW numbers as pairs (re, im)
 struct cdf {
   df re, im;
@@ -121,6 +143,9 @@ __device__ __forceinline__ cdf cdf_mul(const cdf& a, const cdf& b) {
   r.re = df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im));
   r.im = df_add(df_mul(a.re, b.im), df_mul(a.im, b.re));
   return r;
+}
+__device__ __forceinline__ cdf cdfl_mul(const cdf& a, const cdf& b) {
+  return cdf{dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_add(dfl_mul(a.re, b.im), dfl_mul(a.im, b.re))};
 }
 
 // e^{2 pi i x} = (cos, sin)(2 pi x) for x in turns (|x| < 2^20). The reduction is exact: x.hi - rint(x.hi) and
@@ -133,6 +158,7 @@ __device__ __forceinline__ cdf cdf_mul(const cdf& a, const cdf& b) {
 // mixed unit calls it from five places, and one copy keeps the kernel's hot loop in the
 // instruction cache.
 static __device__ __noinline__ cdf df_cis_turns(df x, const float4* __restrict__ tab) {
+  x = fast_two_sum(x.x, x.y);   // |lo| <= ulp(hi)/2 for the exact reduction below
   // round to nearest integer by adding and subtracting 1.5 * 2^23 (exact for |v| < 2^22), on the
   // FP32 pipe; the table index is read from the biased sum's bits
   const float kR = 12582912.0f;
