@@ -268,7 +268,7 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     g.M = fma(lnAb, CG.dlnA_dM, g.M);
     g.q = fma(lnAb, CG.dlnA_dq, g.q);
     g.dL = fma(lnAb, SG.dlnA_ddL, g.dL);
-    vb = lnAb * double(C.p) / v;
+    vb = lnAb * double(C.p) * iv;
     if (tap) {
       const double wb = ampb * amp0;
       const double zb = -wb * w * (1.0 - w);

@@ -300,7 +300,7 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
     g.M = fma(lnAb, CG.dlnA_dM, g.M);
     g.q = fma(lnAb, CG.dlnA_dq, g.q);
     g.dL = fma(lnAb, SG.dlnA_ddL, g.dL);
-    vb = lnAb * double(C.p) / v;
+    vb = lnAb * double(C.p) * iv;
     if (tap) {
       const double wb = df_to(dfl_mul(ampb, A0));
       const double zb = -wb * w * (1.0 - w);
