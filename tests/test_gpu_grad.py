@@ -64,18 +64,22 @@ def test_grad_parity_tianqin_and_network(oracle_mod, Lb):
     inj = _inj(2.0 ** 16)
     ods, gds = _setup(oracle_mod, Lb, Ts, inj, seed=7)
     th = np.vstack([inj, W.draw_prior(2, 61, 2.0 ** 16)])
-    _check_grad(oracle_mod, Lb, ods[2:], gds[2:], th, W.MODE_ALL)     # TianQin alone (geocentric orbit)
-    _check_grad(oracle_mod, Lb, ods, gds, th, W.MODE_ALL)             # network
+    for fl in (0, Lb.PE_PREC_MIXED):
+        _check_grad(oracle_mod, Lb, ods[2:], gds[2:], th, W.MODE_ALL, flags=fl)   # TianQin alone (geocentric)
+        _check_grad(oracle_mod, Lb, ods, gds, th, W.MODE_ALL, flags=fl)           # network
 
 
 def test_grad_single_modes_and_tdi15(oracle_mod, Lb):
+    """Each mode alone, and (2,2) with (3,2) (one paired unit), on a TDI 1.5 detector; FP64 and
+    PE_PREC_MIXED."""
     T = 2.0 ** 16
     inj = _inj(T)
     det15 = dict(W.LISA, tdi_gen=15)
     ods, gds = _setup(oracle_mod, Lb, [(det15, T)], inj, seed=3)
     th = np.vstack([inj, W.draw_prior(2, 71, T)])
-    for mask in (0x01, 0x02, 0x04, 0x08, 0x10):
-        _check_grad(oracle_mod, Lb, ods, gds, th, mask)
+    for mask in (0x01, 0x02, 0x04, 0x08, 0x10, 0x09):
+        for fl in (0, Lb.PE_PREC_MIXED):
+            _check_grad(oracle_mod, Lb, ods, gds, th, mask, flags=fl)
 
 
 def test_grad_mixed_precision_forward_pass(oracle_mod, Lb):
