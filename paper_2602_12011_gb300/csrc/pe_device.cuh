@@ -37,11 +37,10 @@ __device__ __forceinline__ void sincos_turns(double x, const double2* __restrict
   sincos_turns_r(x - rint(x), tab, s, c);
 }
 
-// -2Y_lm(iota, 0) closed forms for the ten (l, +-m) the five modes need.
+// -2Y_lm(iota, 0) closed forms for the ten (l, +-m) the five modes need; ci, si: cos, sin of iota;
+// c2, s2: cos, sin of iota/2.
 template <class T>
-__device__ inline void sylm_pair(int l, int m, const T& iota, T* ypos, T* yneg) {
-  const T ci = cos(iota), si = sin(iota);
-  const T c2 = cos(0.5 * iota), s2 = sin(0.5 * iota);
+__device__ inline void sylm_pair(int l, int m, const T& ci, const T& si, const T& c2, const T& s2, T* ypos, T* yneg) {
   const double pi = kPi;
   if (l == 2 && m == 2) {
     *ypos = sqrt(5.0 / (64.0 * pi)) * (1.0 + ci) * (1.0 + ci);
@@ -89,6 +88,11 @@ __device__ inline bool theta_valid(const double* th) {
 //  SPA amplitudes of the leading-order spherical modes (Blanchet 2014), C-infinity taper
 //  on the orbital frequency between 0.9 F_isco and F_isco, -2Y_lm polarisation weights
 //  (h_{l,-m} = (-1)^l h*_lm), sky frame. T = double, or Dn for derivatives with respect to theta.
+// ln 6, ln 4, 6^(3/2); m^(-1/3) and ln(m)/3 for m = 0..4 (index m)
+constexpr double kLn6 = 1.791759469228055, kLn4 = 1.3862943611198906, k6Pow15 = 14.696938456699069;
+__device__ constexpr double kCbrtInv[5] = {0.0, 1.0, 0.7937005259840998, 0.6933612743506348, 0.6299605249474366};
+__device__ constexpr double kLnM3[5] = {0.0, 0.0, 0.23104906018664842, 0.3662040962227033, 0.46209812037329684};
+
 template <class T>
 __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, SampleCoefT<T>& S) {
   S.valid = valid ? 1 : 0;
@@ -113,8 +117,8 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   S.P[2] = n * (3715.0 / 756.0 + 55.0 / 9.0 * eta);
   S.P[3] = n * (-16.0 * pi + 4.0 * bso);
   S.P[4] = n * (15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta - 10.0 * sss);
-  S.P[5] = n * a5c * (1.0 + 1.5 * ::log(6.0));          // alpha5 (1 + 3 ln(v/v_lso)), v_lso = 6^-1/2
-  S.P[6] = n * (a6c - 6848.0 / 21.0 * ::log(4.0));       // alpha6 - (6848/21) ln(4 v)
+  S.P[5] = n * a5c * (1.0 + 1.5 * kLn6);                // alpha5 (1 + 3 ln(v/v_lso)), v_lso = 6^-1/2
+  S.P[6] = n * (a6c - 6848.0 / 21.0 * kLn4);             // alpha6 - (6848/21) ln(4 v)
   S.P[7] = n * pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
   for (int k = 0; k < 8; ++k) S.Pd[k] = double(k - 5) * S.P[k];
   S.Q5 = n * 3.0 * a5c;
@@ -129,8 +133,14 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   const T v[3] = {-(sb * cl), -(sb * sl), cb};
   for (int i = 0; i < 3; ++i) { S.p[i] = cp * u[i] + sp * v[i]; S.q[i] = -(sp * u[i]) + cp * v[i]; }
   for (int i = 0; i < 3; ++i) S.kw[i] = to_dw(val(S.k[i]));
-  // modes
-  const T Fisco = 1.0 / (::pow(6.0, 1.5) * 2.0 * pi * M);
+  // modes: (2 pi M / m)^(1/3) = (2 pi M)^(1/3) m^(-1/3) and its log from one cube root and one
+  // log per sample; the spin-weighted harmonics share the sines and cosines of iota and iota/2
+  const T Fisco = 1.0 / (k6Pow15 * 2.0 * pi * M);
+  const T cm1 = cbrt(2.0 * pi * M);
+  const T lncm1 = log(cm1);
+  T ci, si, c2h, s2h;
+  sincos(iota, &si, &ci);
+  sincos(0.5 * iota, &s2h, &c2h);
   for (int md = 0; md < kNModes; ++md) {
     ModeCoefT<T>& C = S.md[md];
     const int l = kModeL[md], m = kModeM[md];
@@ -142,16 +152,16 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
     else if (md == 2) { hmag = 0.75 * ::sqrt(15.0 / 14.0) * delta; argt = 0.25; p = 1; }
     else if (md == 3) { hmag = ::sqrt(5.0 / 7.0) / 3.0 * (1.0 - 3.0 * eta); argt = 0.0; p = 2; }
     else { hmag = 8.0 / 9.0 * ::sqrt(5.0 / 7.0) * (1.0 - 3.0 * eta); argt = 0.5; p = 2; }
-    C.cm = cbrt(2.0 * pi * M / double(m));
+    C.cm = cm1 * kCbrtInv[m];
     C.icm = 1.0 / C.cm;
-    C.lncm = log(C.cm);
-    C.amp = 2.0 * pi * M * M / D * sqrt(eta / (3.0 * m)) * hmag * pow(C.cm, -3.5);
+    C.lncm = lncm1 - kLnM3[m];
+    C.amp = 2.0 * pi * M * M / D * sqrt(eta / (3.0 * m)) * hmag * (C.icm * C.icm * C.icm / sqrt(C.cm));
     const T ph = m * phic / (2.0 * pi) + (0.125 + argt);
     C.ph0 = ph - rint(ph);
     C.mfac = 0.0 * q + m / (4.0 * pi);
     C.tffac = 0.0 * q + m / (12.0 * pi);
     T yp, yn;
-    sylm_pair(l, m, iota, &yp, &yn);
+    sylm_pair(l, m, ci, si, c2h, s2h, &yp, &yn);
     const double sgn = (l % 2) ? -1.0 : 1.0;
     C.Pp = 0.5 * (yp + sgn * yn);
     C.Pc = 0.5 * (sgn * yn - yp);
