@@ -534,6 +534,25 @@ def main():
                "max_abs_dlogl_vs_exact": dl.max().item(), "median_abs_dlogl_vs_exact": dl.median().item(),
                "samples": "Fisher-Gaussian draws at 0.1 of its width around the injection (posterior bulk)",
                "dtype": "f64"}
+        # the same summary data with the signal at the edges from the mixed-precision unit
+        hmix = L.Hetero(gd, wl["inj"], mask64 | L.PE_PREC_MIXED, edges=hobj.edges)
+        llm = torch.empty_like(llh)
+        for _ in range(3):
+            L.pe_hetero_loglike_batch([hmix.handle], thh, Bh, llm, None, None, stream)
+        torch.cuda.synchronize()
+        mms = []
+        for k in range(max(3, K // 2)):
+            flush.zero_()
+            e0.record(stream)
+            L.pe_hetero_loglike_batch([hmix.handle], thh, Bh, llm, None, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mms.append(e0.elapsed_time(e1))
+        het["mixed"] = {"value": world * Bh / (sum(mms) / len(mms) / 1e3), "unit": UNIT,
+                        "ms_per_step": sum(mms) / len(mms),
+                        "max_abs_dlogl_vs_fp64_heterodyned": (llm - llh).abs().max().item(),
+                        "note": "signal at the edges from the mixed-precision unit; ratios and sums FP64"}
+        hmix.close()
         hobj.close()
 
     # ---- end to end through the C ABI with host buffers (pinned): H2D of theta, D2H of logL

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "pe_device.cuh"
+#include "pe_device_mixed.cuh"
 #include "pe_internal.h"
 #include "pe_kernels.h"
 #include "pespace_gb300.h"
@@ -70,6 +71,30 @@ __device__ __forceinline__ void mode_brackets(const DetDev& D, const SampleCoef&
     double2 x[3];
     xyz_final(a, Bn.z, x);
     aet_from_xyz(x, o[md]);
+  }
+}
+
+// The same with the mixed-precision unit (FP64 phase, t_f and turn reductions; double-word
+// geometry), each mode's brackets returned to FP64.
+__device__ __forceinline__ void mode_brackets_mixed(const DetDev& D, const SampleCoef& S, int b, unsigned mask,
+                                                    double2 o[kNModes][3], const float4* __restrict__ tab,
+                                                    const float2* __restrict__ pcw) {
+  BinIn Bn;
+  load_bin(D, b, S.tc, Bn);
+  BinW W;
+  load_bin_w(D, b, W);
+  const float4 zz = D.zw[b];
+  const cdf z = {df_make(zz.x, zz.y), df_make(zz.z, zz.w)};
+#pragma unroll 1
+  for (int md = 0; md < kNModes; ++md) {
+    const ModeCoef& C = S.md[md];
+    MixAcc a;
+    mix_zero(a);
+    if ((mask >> md) & 1u && C.active && Bn.f < C.fend) mode_bin_mixed(D, S, C, Bn, W, a, tab, pcw);
+    cdf x[3], od[3];
+    mix_final(a, z, x);
+    aet_from_xyz_dw(x, od);
+    for (int c = 0; c < 3; ++c) o[md][c] = make_double2(df_to(od[c].re) * S.ihsc, df_to(od[c].im) * S.ihsc);
   }
 }
 
@@ -137,13 +162,22 @@ __global__ void k_het_summary(DetDev D, const int* edge, const double* fe, int n
 }
 
 // One CTA of kTileBins threads per sample. Dynamic shared memory: [max ne][5][3] double2 ratios.
+// MIX: the signal at the edges by the mixed-precision unit (the ratios and the contraction stay
+// FP64).
+template <bool MIX>
 __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, const SampleCoef* __restrict__ coef,
                                                            double* logl, double* dhhh) {
   extern __shared__ double2 rsh[];
   __shared__ double pc[kProj];
+  __shared__ float2 pcw[MIX ? kProj : 1];
   __shared__ double sh[6][kTileBins / 32];
-  __shared__ double2 stab[kSinTab];
-  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = hs.h[0].det.sct[i];
+  __shared__ double2 stab[MIX ? 1 : kSinTab];
+  __shared__ float4 stabw[MIX ? kSinTab : 1];
+  if constexpr (MIX) {
+    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stabw[i] = hs.h[0].det.sctw[i];
+  } else {
+    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = hs.h[0].det.sct[i];
+  }
   const int s = blockIdx.x;
   const SampleCoef& S = coef[s];
   double L = 0.0;
@@ -151,12 +185,19 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
     const HetDev& H = hs.h[I];
     const DetDev& D = H.det;
     proj_prologue(D, S, pc);   // its barriers also order the table staging and the previous detector
+    if constexpr (MIX) {
+      if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+      __syncthreads();
+    }
     for (int e = threadIdx.x; e < H.ne; e += blockDim.x) {
       bool need = false;
       for (int j = 0; j < kNModes * 3; ++j) need |= (H.src[e * kNModes * 3 + j] == e);
       if (!need) continue;
       double2 o[kNModes][3];
-      mode_brackets(D, S, H.edge[e], H.mask, o, stab, pc);
+      if constexpr (MIX)
+        mode_brackets_mixed(D, S, H.edge[e], H.mask, o, stabw, pcw);
+      else
+        mode_brackets(D, S, H.edge[e], H.mask, o, stab, pc);
       for (int md = 0; md < kNModes; ++md)
         for (int c = 0; c < 3; ++c) {
           const int j = (e * kNModes + md) * 3 + c;
@@ -241,7 +282,7 @@ void taper_marks(double T, long long k0, double fisco, int m, long long ks[11], 
   *kend = (long long)std::ceil(fe * T) - k0 - 1;
 }
 
-bool mask_ok(unsigned m) { return m != 0u && (m & ~PE_MODE_ALL) == 0u; }
+bool mask_ok(unsigned m) { return (m & PE_MODE_ALL) != 0u && (m & ~(PE_MODE_ALL | PE_PREC_MIXED)) == 0u; }
 
 pe_status herr(pe_status st, const char* msg) { return pe::set_error(st, msg); }
 
@@ -303,7 +344,7 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
                            int nedges, pe_hetero* out) {
   if (out == nullptr || theta0 == nullptr || edges == nullptr) return herr(PE_EINVAL, "pe_hetero_create: NULL argument");
   *out = nullptr;
-  if (!mask_ok(mode_mask)) return herr(PE_EINVAL, "pe_hetero_create: bad mode mask (no precision flag)");
+  if (!mask_ok(mode_mask)) return herr(PE_EINVAL, "pe_hetero_create: bad mode mask (PE_PREC_FP32 is not taken)");
   pe::DetSet ds;
   pe_status s0 = pe::detset_from_handles(&det, 1, &ds);
   if (s0 != PE_OK) return s0;
@@ -483,10 +524,12 @@ pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double*
     e = pe::launch_prep(th, B, hets[0]->dev.mask, ds, static_cast<pe::SampleCoef*>(coef), static_cast<int*>(nend),
                         static_cast<int*>(stt), st);
   const size_t smem = (size_t)nemax * pe::kNModes * 3 * sizeof(double2);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pe::k_het_loglike, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool mix = (hets[0]->dev.mask & PE_PREC_MIXED) != 0u;
+  auto kern = mix ? pe::k_het_loglike<true> : pe::k_het_loglike<false>;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
-    pe::k_het_loglike<<<B, pe::kTileBins, smem, st>>>(hs, B, static_cast<const pe::SampleCoef*>(coef),
-                                                      static_cast<double*>(ll), static_cast<double*>(dh));
+    kern<<<B, pe::kTileBins, smem, st>>>(hs, B, static_cast<const pe::SampleCoef*>(coef), static_cast<double*>(ll),
+                                         static_cast<double*>(dh));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && hl) e = cudaMemcpyAsync(out_logl, ll, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st);

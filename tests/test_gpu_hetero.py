@@ -31,8 +31,9 @@ def _near(th0, n, seed, scale):
     return th
 
 
+@pytest.mark.parametrize("mix", [False, True], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("det", [W.LISA, W.TIANQIN], ids=["lisa", "tianqin"])
-def test_hetero_parity_with_oracle(oracle_mod, Lb, det):
+def test_hetero_parity_with_oracle(oracle_mod, Lb, det, mix):
     from oracle import hetero as HT
     T = 2.0 ** 18
     k0, nb = W.grid(T)
@@ -41,7 +42,7 @@ def test_hetero_parity_with_oracle(oracle_mod, Lb, det):
     gd = H.library_detector(Lb, od)
     edges = HT.default_edges(T, k0, nb, th0, W.MODE_ALL, 64)
     oh = HT.Hetero(od, th0, W.MODE_ALL, edges)
-    gh = Lb.Hetero(gd, th0, W.MODE_ALL, edges=edges)
+    gh = Lb.Hetero(gd, th0, W.MODE_ALL | (Lb.PE_PREC_MIXED if mix else 0), edges=edges)
     th = np.vstack([th0, _near(th0, 12, 5, 1.0)])
     g = Lb.hetero_loglike([gh], th, dhhh=True)
     for s in range(th.shape[0]):
@@ -85,6 +86,7 @@ def test_hetero_against_exact_likelihood(Lb):
     g.inject(wl["inj"], wl["inj_mask"], W.normals(nb, wl["noise_seed"]))
     th0 = wl["inj"]
     het = Lb.Hetero(g, th0, W.MODE_ALL, nbins_coarse=256)
+    hetm = Lb.Hetero(g, th0, W.MODE_ALL | Lb.PE_PREC_MIXED, nbins_coarse=256)
     cases = np.vstack([th0, th0 * np.r_[1, 1, 1, 1, 1.2, 1, 1, 1, 1, 1, 1], th0 + np.r_[0, 0, 0, 0, 0, 0, 0.4, 0, 0, 0, 0]])
     ex = Lb.loglike([g], cases, W.MODE_ALL, dhhh=True)
     ht = Lb.hetero_loglike([het], cases)
@@ -107,7 +109,11 @@ def test_hetero_against_exact_likelihood(Lb):
         assert near.sum() > 100
         # measured at 256 bins: 6.5e-3 (0.1-scaled), 3.0e-2 (0.3-scaled, within 50 of the peak)
         assert np.abs(ht - ex)[near].max() < bound, np.abs(ht - ex)[near].max()
+        # the mixed-precision edge evaluation changes the heterodyned log L by rounding only
+        hm = Lb.hetero_loglike([hetm], tt)["logl"].cpu().numpy()
+        assert np.all(np.abs(hm - ht) <= 1e-11 * (np.abs(ht) + 0.5 * g.data_norm().sum()))
     het.close()
+    hetm.close()
 
 
 def test_hetero_errors(Lb):
@@ -124,6 +130,9 @@ def test_hetero_errors(Lb):
     assert e.value.status == Lb.PE_EINVAL
     with pytest.raises(Lb.PeError) as e:
         Lb.Hetero(d, th0, W.MODE_ALL, edges=np.arange(700))
+    assert e.value.status == Lb.PE_EINVAL
+    with pytest.raises(Lb.PeError) as e:
+        Lb.Hetero(d, th0, W.MODE_ALL | Lb.PE_PREC_FP32, edges=np.array([0, 40, 90]))
     assert e.value.status == Lb.PE_EINVAL
     a = Lb.Hetero(d, th0, W.MODE_ALL, edges=np.array([0, 40, 90]))
     b = Lb.Hetero(d, th0, W.MODE_22, edges=np.array([0, 40, 90]))
