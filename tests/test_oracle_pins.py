@@ -117,6 +117,102 @@ def test_tf_matches_taylort2_to_2p5pn(oracle_mod, q):
         assert abs(ratio - series) < 2000 * v ** 6
 
 
+def _taylorf2_from_energy_and_flux():
+    """TaylorF2 coefficients alpha_k(eta) re-derived by energy balance, independently of their
+    published form: dt/dv = -(dE/dv)/F with the circular-orbit binding energy E (3PN) and the
+    gravitational-wave flux F (3.5PN, with its ln(16 x) tail term) of comparable-mass binaries
+    (Blanchet, Living Rev. Relativ. 17, 2 (2014), the non-spinning circular-orbit energy and
+    flux). Writing dt/dv = (5M/(32 eta)) v^-9 g(v), g = 1 + sum_k g_k v^k, the stationary-phase
+    phase 2 pi f t(v) - 2 phi(v) with phi' = v^3 t'/M is (3/(128 eta v^5)) sum_k alpha_k v^k up
+    to terms constant or linear in f, with alpha_k = 40 g_k / ((k-8)(k-5)) for k != 5, 8. The
+    v^5 term integrates to a logarithm (alpha_5's ln v coefficient: -(40/3) g_5); at v^6 the
+    flux's ln v term gives alpha_6 = -20 g_6c + 10 g_6l plus -20 g_6l ln v, for g_6 = g_6c +
+    g_6l ln v. Returns sympy expressions in eta."""
+    sp = pytest.importorskip("sympy")
+    et, L = sp.symbols("eta L")
+    R, pi, gE = sp.Rational, sp.pi, sp.EulerGamma
+    N = 8
+    # E / mu in powers of v (x = v^2) and F / ((32/5) eta^2 x^5); L stands for ln(16 x)
+    Ek = {2: -R(1, 2), 4: -R(1, 2) * (-R(3, 4) - et / 12), 6: -R(1, 2) * (-R(27, 8) + R(19, 8) * et - et ** 2 / 24),
+          8: -R(1, 2) * (-R(675, 64) + (R(34445, 576) - R(205, 96) * pi ** 2) * et - R(155, 96) * et ** 2
+                         - R(35, 5184) * et ** 3)}
+    Fk = {0: 1, 2: -R(1247, 336) - R(35, 12) * et, 3: 4 * pi,
+          4: -R(44711, 9072) + R(9271, 504) * et + R(65, 18) * et ** 2,
+          5: (-R(8191, 672) - R(583, 24) * et) * pi,
+          6: (R(6643739519, 69854400) + R(16, 3) * pi ** 2 - R(1712, 105) * gE - R(856, 105) * L
+              + (-R(134543, 7776) + R(41, 48) * pi ** 2) * et - R(94403, 3024) * et ** 2 - R(775, 324) * et ** 3),
+          7: (-R(16285, 504) + R(214745, 1728) * et + R(193385, 3024) * et ** 2) * pi}
+    F = [sp.sympify(Fk.get(k, 0)) for k in range(N)]
+    num = [sp.sympify(0)] * N                     # -(dE/dv) / v
+    for k, c in Ek.items():
+        num[k - 2] += -k * c
+    inv = [sp.sympify(1)] + [sp.sympify(0)] * (N - 1)   # 1/F as a series (F_0 = 1)
+    for n in range(1, N):
+        inv[n] = sp.expand(-sum(F[j] * inv[n - j] for j in range(1, n + 1)))
+    g = [sp.expand(sum(num[j] * inv[n - j] for j in range(n + 1))) for n in range(N)]
+    assert g[0] == 1 and g[1] == 0
+    out = {k: 40 * g[k] / ((k - 8) * (k - 5)) for k in (2, 3, 4, 7)}
+    d6 = sp.diff(g[6], L)                          # L = ln 16 + 2 ln v
+    c6 = g[6].subs(L, 0) + d6 * sp.log(16)
+    out["6c"] = -20 * c6 + 20 * d6
+    out["6l"] = -40 * d6
+    out["5l"] = -R(40, 3) * g[5]
+    return et, out
+
+
+@pytest.mark.parametrize("q", [1.0, 3.0, 1e9])
+def test_taylorf2_coefficients_from_energy_balance(oracle_mod, q):
+    """The oracle's non-spinning PN phase coefficients, alpha_2 ... alpha_7 with their eta
+    dependence (3PN and 3.5PN included) and the ln v terms of alpha_5 and alpha_6, against the
+    energy-balance derivation above. The oracle's coefficients are read off its Psi_PN(v) by a
+    least-squares fit on the basis v^0..v^7, v^5 ln v, v^6 ln v (Psi_PN has exactly that form).
+    Only alpha_5's constant, which joins phi_c, is convention and not compared."""
+    et, ref = _taylorf2_from_energy_and_flux()
+    eta = q / (1 + q) ** 2
+    th = TH.copy()
+    th[1] = q
+    th[2] = th[3] = 0.0
+    vs = np.linspace(0.03, 0.3, 80)
+    y = np.array([oracle_mod.psi_pn(th, v) for v in vs]) * 128 * eta * vs ** 5 / 3
+    B = np.column_stack([vs ** k for k in range(8)] + [vs ** 5 * np.log(vs), vs ** 6 * np.log(vs)])
+    sc = np.abs(B).max(axis=0)
+    c = np.linalg.lstsq(B / sc, y, rcond=None)[0] / sc
+    got = {2: c[2], 3: c[3], 4: c[4], 7: c[7], "6c": c[6], "6l": c[9], "5l": c[8]}
+    assert abs(c[0] - 1.0) < 1e-12 and abs(c[1]) < 1e-9
+    for k, expr in ref.items():
+        want = float(expr.subs(et, eta).evalf(30))
+        assert got[k] == pytest.approx(want, rel=1e-7), (k, got[k], want)
+
+
+def test_spin_orbit_coefficient_in_the_test_mass_limit(oracle_mod):
+    """The 1.5PN spin-orbit term of alpha_3, -16 pi + 4 beta with beta -> (113/12) chi_1 as
+    eta -> 0, against the same energy-balance derivation for a test mass on a prograde circular
+    equatorial orbit of a Kerr black hole of spin chi_1: the exact Bardeen-Press-Teukolsky
+    energy E/mu = (1 - 2 w^2 + a w^3) / sqrt(1 - 3 w^2 + 2 a w^3) - 1 (w^2 = M/r), written in
+    u = (M Omega)^(1/3) through w^3 = u^3 / (1 - a u^3), and the test-mass flux to 1.5PN,
+    1 - (1247/336) u^2 + (4 pi - (11/4) a) u^3 (Tagoshi, Shibata, Tanaka & Sasaki 1996)."""
+    sp = pytest.importorskip("sympy")
+    u, a = sp.symbols("u a")
+    w = u * (1 - a * u ** 3) ** sp.Rational(-1, 3)
+    E = (1 - 2 * w ** 2 + a * w ** 3) / sp.sqrt(1 - 3 * w ** 2 + 2 * a * w ** 3) - 1
+    Es = sp.expand(sp.series(E, u, 0, 6).removeO())
+    f = 1 - sp.Rational(1247, 336) * u ** 2 + (4 * sp.pi - sp.Rational(11, 4) * a) * u ** 3
+    g = sp.expand(sp.series(-sp.diff(Es, u) / (u * f), u, 0, 4).removeO())
+    alpha3 = sp.expand(40 * g.coeff(u, 3) / ((3 - 8) * (3 - 5)))
+    chi1 = 0.6
+    th = TH.copy()
+    th[1] = 1e9
+    th[2], th[3] = chi1, 0.0
+    eta = th[1] / (1 + th[1]) ** 2
+    vs = np.linspace(0.03, 0.3, 80)
+    y = np.array([oracle_mod.psi_pn(th, v) for v in vs]) * 128 * eta * vs ** 5 / 3
+    B = np.column_stack([vs ** k for k in range(8)] + [vs ** 5 * np.log(vs), vs ** 6 * np.log(vs)])
+    sc = np.abs(B).max(axis=0)
+    c = np.linalg.lstsq(B / sc, y, rcond=None)[0] / sc
+    want = float(alpha3.subs(a, chi1))
+    assert c[3] == pytest.approx(want, rel=1e-7), (c[3], want)
+
+
 @pytest.mark.parametrize("lm", list(W.MODES))
 def test_tf_is_phase_derivative(oracle_mod, lm):
     """t_f = (1/2 pi) dPsi/df (Eq. eq_tf with Phi = -Psi) against a central difference."""
