@@ -213,6 +213,83 @@ def test_spin_orbit_coefficient_in_the_test_mass_limit(oracle_mod):
     assert c[3] == pytest.approx(want, rel=1e-7), (c[3], want)
 
 
+def _newtonian_multipole_flux(m1, m2, r, n=64):
+    """Energy flux of a Newtonian circular binary (masses m1, m2, separation r; G = c = M = 1),
+    split by multipole and by harmonic of the orbital frequency, from the multipole expansion of
+    the flux (Thorne, Rev. Mod. Phys. 52, 299 (1980)):
+      F = sum_l (l+1)(l+2) / ((l-1) l l! (2l+1)!!) <(d^(l+1) I_L)^2>
+          + 4 l (l+2) / ((l-1) (l+1)! (2l+1)!!) <(d^(l+1) J_L)^2>,
+    with the symmetric trace-free mass moments I_L = sum_A m_A x_A^<L> and current moments
+    J_L = sum_A m_A [x_A^(L-1) (x_A x v_A)]^STF. The moments are sampled over one orbit; their time
+    derivatives and averages are taken harmonic by harmonic from a discrete Fourier transform
+    (the moments are trigonometric polynomials). Returns {(kind, l): {harmonic k: flux}}."""
+    M = m1 + m2
+    w = math.sqrt(M / r ** 3)
+    t = np.arange(n) * 2 * math.pi / (w * n)
+    d = np.eye(3)
+    bodies = []
+    for mA, s in ((m1, m2 / M), (m2, -m1 / M)):
+        x = np.stack([s * r * np.cos(w * t), s * r * np.sin(w * t), 0 * t], axis=1)
+        v = np.stack([-s * r * w * np.sin(w * t), s * r * w * np.cos(w * t), 0 * t], axis=1)
+        bodies.append((mA, x, v, (x * x).sum(1), np.cross(x, v)))
+    I2 = sum(mA * (np.einsum("ti,tj->tij", x, x) - r2[:, None, None] * d / 3) for mA, x, v, r2, Lv in bodies)
+    I3 = sum(mA * (np.einsum("ti,tj,tk->tijk", x, x, x) - r2[:, None, None, None] / 5 * (
+        np.einsum("ti,jk->tijk", x, d) + np.einsum("tj,ik->tijk", x, d) + np.einsum("tk,ij->tijk", x, d)))
+        for mA, x, v, r2, Lv in bodies)
+    dd = np.einsum("ij,kl->ijkl", d, d) + np.einsum("ik,jl->ijkl", d, d) + np.einsum("il,jk->ijkl", d, d)
+    I4 = sum(mA * (np.einsum("ti,tj,tk,tl->tijkl", x, x, x, x)
+                   - r2[:, None, None, None, None] / 7 * sum(np.einsum(e, d, x, x) for e in (
+                       "ij,tk,tl->tijkl", "ik,tj,tl->tijkl", "il,tj,tk->tijkl", "jk,ti,tl->tijkl",
+                       "jl,ti,tk->tijkl", "kl,ti,tj->tijkl"))
+                   + (r2 ** 2)[:, None, None, None, None] / 35 * dd) for mA, x, v, r2, Lv in bodies)
+    # x . (x x v) = 0, so only the traces named here survive
+    J2 = sum(mA * 0.5 * (np.einsum("ti,tj->tij", x, Lv) + np.einsum("ti,tj->tij", Lv, x)) for mA, x, v, r2, Lv in bodies)
+    J3 = sum(mA * ((np.einsum("ti,tj,tk->tijk", x, x, Lv) + np.einsum("ti,tj,tk->tijk", x, Lv, x)
+                    + np.einsum("ti,tj,tk->tijk", Lv, x, x)) / 3
+                   - r2[:, None, None, None] / 15 * (np.einsum("ij,tk->tijk", d, Lv) + np.einsum("ik,tj->tijk", d, Lv)
+                                                    + np.einsum("jk,ti->tijk", d, Lv)))
+             for mA, x, v, r2, Lv in bodies)
+
+    def split(T, l, kind):
+        if kind == "I":
+            coef = (l + 1) * (l + 2) / ((l - 1) * l * math.factorial(l) * _dfact(2 * l + 1))
+        else:
+            coef = 4 * l * (l + 2) / ((l - 1) * math.factorial(l + 1) * _dfact(2 * l + 1))
+        c = np.fft.fft(T, axis=0) / n
+        return {k: coef * 2 * np.sum(np.abs(c[k]) ** 2) * (k * w) ** (2 * (l + 1)) for k in range(1, n // 2)}
+
+    return {("I", 2): split(I2, 2, "I"), ("I", 3): split(I3, 3, "I"), ("I", 4): split(I4, 4, "I"),
+            ("J", 2): split(J2, 2, "J"), ("J", 3): split(J3, 3, "J")}, w
+
+
+def _dfact(n):
+    return math.prod(range(n, 0, -2))
+
+
+@pytest.mark.parametrize("q", [1.5, 3.0, 8.0])
+def test_higher_mode_amplitudes_match_multipole_flux(oracle_mod, q):
+    """|H_lm| of the four higher modes (mass octupole 33, current quadrupole 21, current octupole
+    32, mass hexadecapole 44) against the flux each multipole of a Newtonian binary radiates at
+    harmonic m, relative to the (2,2) flux (_newtonian_multipole_flux). The flux of mode (l,m) and
+    (l,-m) together is (R^2/8 pi) (m omega)^2 |h_lm|^2; the oracle's stationary-phase amplitudes
+    at the same orbital frequency F give |h_lm / h_22| = |h~_lm(mF) / h~_22(2F)| sqrt(m/2). The
+    (2,2) flux itself is pinned to the quadrupole formula here too."""
+    m1, m2 = q / (1 + q), 1 / (1 + q)
+    r = 1e4                                   # M/r = v^2 = 1e-4
+    fl, w = _newtonian_multipole_flux(m1, m2, r)
+    F22 = fl[("I", 2)][2]
+    assert F22 == pytest.approx(32 / 5 * (m1 * m2) ** 2 * w ** (10 / 3), rel=1e-12)
+    th = TH.copy()
+    th[1] = q
+    th[2] = th[3] = 0.0
+    F = (1 / r) ** 1.5 / (2 * math.pi * th[0] * MSUN_S)   # orbital frequency: M omega = v^3
+    h22 = abs(oracle_mod.mode(th, 2, 2, [2 * F])[0][0])
+    for (l, m), key in (((3, 3), ("I", 3)), ((2, 1), ("J", 2)), ((4, 4), ("I", 4)), ((3, 2), ("J", 3))):
+        hlm = abs(oracle_mod.mode(th, l, m, [m * F])[0][0])
+        ratio_oracle = (m / 2) ** 2 * (hlm / h22 * math.sqrt(m / 2)) ** 2
+        assert ratio_oracle == pytest.approx(fl[key][m] / F22, rel=1e-9), ((l, m), ratio_oracle, fl[key][m] / F22)
+
+
 @pytest.mark.parametrize("lm", list(W.MODES))
 def test_tf_is_phase_derivative(oracle_mod, lm):
     """t_f = (1/2 pi) dPsi/df (Eq. eq_tf with Phi = -Psi) against a central difference."""
