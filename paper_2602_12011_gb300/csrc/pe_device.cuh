@@ -16,16 +16,20 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
-// sin and cos of 2 pi x for x in turns: exact reduction x - rint(x), nearest table angle
-// 2 pi j/kSinTab, and the remainder t (|t| <= pi/kSinTab) through the angle-addition formulas with
+// sin and cos of 2 pi x for x in turns (|x| < 2^40): the nearest table angle 2 pi j/kSinTab and the
+// remainder t = 2 pi (x - j/kSinTab) (|t| <= pi/kSinTab) through the angle-addition formulas with
 // sin t = t - t^3/6 + t^5/120, cos t = 1 - t^2/2 + t^4/24 (truncation below 1e-18).
-// tab[j] = (cos, sin)(2 pi j/kSinTab).
-// sincos(2 pi r) for |r| < 2^20 turns without the reduction to a fraction: the table index wraps
-// modulo kSinTab, and r - jf / kSinTab is exact (Sterbenz), so the result equals sincos_turns(r).
-__device__ __forceinline__ void sincos_turns_r(double r, const double2* __restrict__ tab, double* s, double* c) {
-  const double jf = rint(r * kSinTab);
-  const double d = fma(jf, -1.0 / kSinTab, r);
-  const double2 cs = tab[(int)jf & (kSinTab - 1)];
+// tab[j] = (cos, sin)(2 pi j/kSinTab). Adding 1.5 * 2^42 rounds x to the nearest multiple of
+// 2^-10 = 1/kSinTab (round to nearest even, as rint); subtracting it again gives that multiple
+// exactly, x minus it is exact (Sterbenz), and the low ten bits of the sum's significand are j
+// modulo kSinTab. So the turn reduction and the index need three FP64 additions and no FRND or
+// conversion; the table's period absorbs the integer part of x.
+static_assert(kSinTab == 1024, "the rounding constant below assumes kSinTab = 2^10");
+__device__ __forceinline__ void sincos_turns(double x, const double2* __restrict__ tab, double* s, double* c) {
+  constexpr double kRound = 6597069766656.0;   // 1.5 * 2^42
+  const double sx = __dadd_rn(x, kRound);
+  const double d = __dsub_rn(x, __dsub_rn(sx, kRound));
+  const double2 cs = tab[__double2loint(sx) & (kSinTab - 1)];
   const double t = d * (2.0 * kPi);
   const double t2 = t * t;
   const double st = fma(t, t2 * fma(t2, 1.0 / 120.0, -1.0 / 6.0), t);
@@ -33,8 +37,9 @@ __device__ __forceinline__ void sincos_turns_r(double r, const double2* __restri
   *s = fma(cs.y, ct, cs.x * st);
   *c = fma(cs.x, ct, -(cs.y * st));
 }
-__device__ __forceinline__ void sincos_turns(double x, const double2* __restrict__ tab, double* s, double* c) {
-  sincos_turns_r(x - rint(x), tab, s, c);
+// the same for an argument already reduced to a few turns (kept as a name for those call sites)
+__device__ __forceinline__ void sincos_turns_r(double r, const double2* __restrict__ tab, double* s, double* c) {
+  sincos_turns(r, tab, s, c);
 }
 
 // -2Y_lm(iota, 0) closed forms for the ten (l, +-m) the five modes need; ci, si: cos, sin of iota;
