@@ -130,6 +130,50 @@ def test_loglike_edge_grids(oracle_mod, Lb):
         H.assert_loglike_parity(g, ll, dhhh, od_dd(oracle_mod, od))
 
 
+def test_maximum_batch_and_detector_count(oracle_mod, Lb):
+    """The largest batch the entry points take (B = 2^20, on a small ragged grid) and the largest
+    detector count (8 handles): sampled outputs against the oracle, bitwise equality with a small
+    batch of the same samples, and PE_EINVAL one past each limit."""
+    import torch
+    T = 2.0 ** 14
+    k0, nb = W.grid(T)
+    od = H.oracle_detector(oracle_mod, W.LISA, T, k0, nb, _th_small(T), W.MODE_ALL, 5)
+    gd = H.library_detector(Lb, od)
+    B = 1 << 20
+    th = W.draw_prior(B, 91, T)
+    tt = torch.tensor(th, device="cuda")
+    g = Lb.loglike([gd], tt, W.MODE_ALL, dhhh=True)
+    out, dh = g["logl"].cpu().numpy(), g["dhhh"].cpu().numpy()
+    del g, tt
+    assert np.all(np.isfinite(out))
+    pick = np.r_[0, 1, B // 2, B - 1, np.random.Generator(np.random.PCG64(3)).choice(B, 6, replace=False)]
+    ll, dhhh = oracle_mod.loglike_batch([od], th[pick], W.MODE_ALL)
+    H.assert_loglike_parity({"logl": out[pick], "dhhh": dh[pick]}, ll, dhhh, od_dd(oracle_mod, od))
+    small = Lb.loglike([gd], th[pick], W.MODE_ALL)
+    assert np.array_equal(small["logl"], out[pick])
+    with pytest.raises(Lb.PeError) as e:
+        Lb.loglike([gd], np.vstack([th[:1]] * (B + 1)), W.MODE_ALL)
+    assert e.value.status == Lb.PE_EINVAL
+    del th
+    # eight detectors: LISA, Taiji and TianQin-like grids, repeated with other noise draws
+    dets = [(W.LISA, 2.0 ** 14), (W.TAIJI, 2.0 ** 14), (W.TIANQIN, 2.0 ** 14), (W.LISA, 2.0 ** 13),
+            (W.TAIJI, 2.0 ** 13), (W.TIANQIN, 2.0 ** 13), (dict(W.LISA, tdi_gen=15), 2.0 ** 14), (W.LISA, 2.0 ** 15)]
+    ods, gds = [], []
+    for i, (det, Ti) in enumerate(dets):
+        k0i, nbi = W.grid(Ti)
+        o = H.oracle_detector(oracle_mod, det, Ti, k0i, nbi, _th_small(2.0 ** 13), W.MODE_ALL, 40 + i)
+        ods.append(o)
+        gds.append(H.library_detector(Lb, o))
+    th8 = np.vstack([_th_small(2.0 ** 13), W.draw_prior(7, 92, 2.0 ** 13)])
+    g8 = Lb.loglike(gds, th8, W.MODE_ALL, dhhh=True)
+    ll8, dhhh8 = oracle_mod.loglike_batch(ods, th8, W.MODE_ALL)
+    dd8 = np.array([od_dd(oracle_mod, o) for o in ods])
+    H.assert_loglike_parity(g8, ll8, dhhh8, dd8)
+    with pytest.raises(Lb.PeError) as e:
+        Lb.loglike(gds + gds[:1], th8, W.MODE_ALL)
+    assert e.value.status == Lb.PE_EINVAL
+
+
 def test_network_parity(oracle_mod, Lb):
     """LISA + Taiji + TianQin with uneven grids (smaller spans for the oracle's speed)."""
     Ts = (2.0 ** 19, 2.0 ** 18, 2.0 ** 17)
