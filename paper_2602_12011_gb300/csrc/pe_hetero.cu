@@ -42,6 +42,8 @@ struct HetDev {
   const int* src;        // [ne][5][3] edge whose ratio applies (carry-forward), -1 for none
   const double2* A;      // [ne-1][5][3][2]
   const double2* Bs;     // [ne-1][kPairs][3][3]
+  const float4* Aw;      // A and Bs as double words (re hi, re lo, im hi, im lo), for the mixed kernel
+  const float4* Bw;
   int ne;
   unsigned mask;
 };
@@ -161,9 +163,25 @@ __global__ void k_het_summary(DetDev D, const int* edge, const double* fe, int n
   }
 }
 
+// double2 -> double-word complex (re hi, re lo, im hi, im lo)
+__global__ void k_to_dw4(const double2* in, long long n, float4* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 re = to_dw(in[i].x), im = to_dw(in[i].y);
+  out[i] = make_float4(re.x, re.y, im.x, im.y);
+}
+
+__device__ __forceinline__ cdf unpack4(float4 q) { return cdf{df_make(q.x, q.y), df_make(q.z, q.w)}; }
+// Re(a b) and Re(a conj(b)) in double words
+__device__ __forceinline__ df re_mul(const cdf& a, const cdf& b) { return dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)); }
+__device__ __forceinline__ cdf mul_conj(const cdf& a, const cdf& b) {
+  return cdf{dfl_add(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_sub(dfl_mul(a.im, b.re), dfl_mul(a.re, b.im))};
+}
+
 // One CTA of kTileBins threads per sample. Dynamic shared memory: [max ne][5][3] double2 ratios.
-// MIX: the signal at the edges by the mixed-precision unit (the ratios and the contraction stay
-// FP64).
+// MIX: the signal at the edges by the mixed-precision unit, the ratios kept as double words and
+// the contraction in double words (Aw, Bw); the sums across bins and the block reduction stay
+// FP64.
 template <bool MIX>
 __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, const SampleCoef* __restrict__ coef,
                                                            double* logl, double* dhhh) {
@@ -201,11 +219,56 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
       for (int md = 0; md < kNModes; ++md)
         for (int c = 0; c < 3; ++c) {
           const int j = (e * kNModes + md) * 3 + c;
-          if (H.src[j] == e) rsh[j] = cdiv(o[md][c], H.h0e[j]);
+          if (H.src[j] != e) continue;
+          const double2 r = cdiv(o[md][c], H.h0e[j]);
+          if constexpr (MIX) {
+            const float2 re = to_dw(r.x), im = to_dw(r.y);
+            reinterpret_cast<float4*>(rsh)[j] = make_float4(re.x, re.y, im.x, im.y);
+          } else {
+            rsh[j] = r;
+          }
         }
     }
     __syncthreads();
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if constexpr (MIX) {
+      const float4* rw = reinterpret_cast<const float4*>(rsh);
+      const cdf zc = {df_make(0.f, 0.f), df_make(0.f, 0.f)};
+      for (int b = threadIdx.x; b < H.ne - 1; b += blockDim.x) {
+        const df idf = to_dw(1.0 / (H.fe[b + 1] - H.fe[b]));
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+          cdf r0[kNModes], r1[kNModes];
+#pragma unroll
+          for (int md = 0; md < kNModes; ++md) {
+            const int s0 = H.src[(b * kNModes + md) * 3 + c], s1 = H.src[((b + 1) * kNModes + md) * 3 + c];
+            const cdf ra = s0 >= 0 ? unpack4(rw[(s0 * kNModes + md) * 3 + c]) : zc;
+            const cdf rb = s1 >= 0 ? unpack4(rw[(s1 * kNModes + md) * 3 + c]) : zc;
+            r0[md] = ra;
+            r1[md] = cdf{dfl_mul(dfl_sub(rb.re, ra.re), idf), dfl_mul(dfl_sub(rb.im, ra.im), idf)};
+          }
+          df dh = df_make(0.f, 0.f), hh = df_make(0.f, 0.f);
+#pragma unroll
+          for (int md = 0; md < kNModes; ++md) {
+            const float4* a = H.Aw + (((size_t)b * kNModes + md) * 3 + c) * 2;
+            dh = dfl_add(dh, dfl_add(re_mul(unpack4(a[0]), r0[md]), re_mul(unpack4(a[1]), r1[md])));
+#pragma unroll
+            for (int m2 = md; m2 < kNModes; ++m2) {
+              const float4* q = H.Bw + (((size_t)b * kPairs + pair_index(md, m2)) * 3 + c) * 3;
+              const cdf t0 = mul_conj(r0[md], r0[m2]);
+              const cdf ta = mul_conj(r1[md], r0[m2]), tb = mul_conj(r0[md], r1[m2]);
+              const cdf t1 = {dfl_add(ta.re, tb.re), dfl_add(ta.im, tb.im)};
+              const cdf t2 = mul_conj(r1[md], r1[m2]);
+              df x = dfl_add(dfl_add(re_mul(unpack4(q[0]), t0), re_mul(unpack4(q[1]), t1)), re_mul(unpack4(q[2]), t2));
+              if (md != m2) x = df_scale2(x, 2.0f);
+              hh = dfl_add(hh, x);
+            }
+          }
+          v[c] += df_to(dh);
+          v[3 + c] += df_to(hh);
+        }
+      }
+    } else
     for (int b = threadIdx.x; b < H.ne - 1; b += blockDim.x) {
       const double idf = 1.0 / (H.fe[b + 1] - H.fe[b]);
 #pragma unroll 1
@@ -367,7 +430,9 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
   const size_t o_h0e = a256(o_fe + ne * sizeof(double));
   const size_t o_A = a256(o_h0e + (size_t)ne * 15 * sizeof(double2));
   const size_t o_B = a256(o_A + (size_t)nb * 30 * sizeof(double2));
-  const size_t bytes = o_B + (size_t)nb * pe::kPairs * 9 * sizeof(double2);
+  const size_t o_Aw = a256(o_B + (size_t)nb * pe::kPairs * 9 * sizeof(double2));
+  const size_t o_Bw = a256(o_Aw + (size_t)nb * 30 * sizeof(float4));
+  const size_t bytes = o_Bw + (size_t)nb * pe::kPairs * 9 * sizeof(float4);
   pe_hetero_s* h = new (std::nothrow) pe_hetero_s();
   if (!h) return herr(PE_ENOMEM, "pe_hetero_create: host allocation failed");
   cudaGetDevice(&h->device);
@@ -383,6 +448,8 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
   double2* d_h0e = reinterpret_cast<double2*>(base + o_h0e);
   double2* d_A = reinterpret_cast<double2*>(base + o_A);
   double2* d_B = reinterpret_cast<double2*>(base + o_B);
+  float4* d_Aw = reinterpret_cast<float4*>(base + o_Aw);
+  float4* d_Bw = reinterpret_cast<float4*>(base + o_Bw);
   std::vector<int> he(ne);
   std::vector<double> hfe(ne);
   for (int i = 0; i < ne; ++i) {
@@ -436,6 +503,12 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
     pe::k_het_summary<<<(unsigned)((n + 127) / 128), 128>>>(D, d_edge, d_fe, ne, hb, K, d_A, d_B);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) {   // double-word copies of the summary data for the mixed-precision kernel
+    const long long na = (long long)nb * 30, nbq = (long long)nb * pe::kPairs * 9;
+    pe::k_to_dw4<<<(unsigned)((na + 255) / 256), 256>>>(d_A, na, d_Aw);
+    pe::k_to_dw4<<<(unsigned)((nbq + 255) / 256), 256>>>(d_B, nbq, d_Bw);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(th0);
   cudaFree(coef);
@@ -456,6 +529,8 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
   h->dev.src = d_src;
   h->dev.A = d_A;
   h->dev.Bs = d_B;
+  h->dev.Aw = d_Aw;
+  h->dev.Bw = d_Bw;
   h->dev.ne = ne;
   h->dev.mask = mode_mask;
   *out = h;
