@@ -53,13 +53,13 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
   double iv5 = iv * iv;
   iv5 = iv5 * iv5 * iv;
   double poly = S.P[7];
-  double dpol = 2.0 * S.P[7];
-  double ddpol = 4.0 * S.P[7];
+  double dpol = S.Pd[7];
+  double ddpol = S.Pdd[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);
     dpol = fma(dpol, v, S.Pd[k]);
-    ddpol = fma(ddpol, v, double(k - 5) * S.Pd[k]);
+    ddpol = fma(ddpol, v, S.Pdd[k]);
   }
   const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
@@ -282,11 +282,11 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
   vb += psib * dv * iv + Db * (iv5 * ddpol * iv + S.Q6 * (2.0 + lnv));
   g.M = fma(vb * B.f13, CG.dcm_dM, g.M);
   // coefficient derivatives in q: Psi_q = v^-5 sum dP_k v^k + ln v (dQ5 + dQ6 v), D_q likewise
-  double pq = SG.dP_dq[7], dq = 2.0 * SG.dP_dq[7];
+  double pq = SG.dP_dq[7], dq = SG.dPd_dq[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     pq = fma(pq, v, SG.dP_dq[k]);
-    dq = fma(dq, v, (k - 5) * SG.dP_dq[k]);
+    dq = fma(dq, v, SG.dPd_dq[k]);
   }
   const double psiq = fma(iv5, pq, lnv * fma(SG.dQ6_dq, v, SG.dQ5_dq));
   const double Dq = fma(iv5, dq, fma(SG.dQ6_dq * v, 1.0 + lnv, SG.dQ5_dq));

@@ -99,13 +99,13 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
   double iv5 = iv * iv;
   iv5 = iv5 * iv5 * iv;
   double poly = S.P[7];
-  double dpol = 2.0 * S.P[7];
-  double ddpol = 4.0 * S.P[7];
+  double dpol = S.Pd[7];
+  double ddpol = S.Pdd[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);
     dpol = fma(dpol, v, S.Pd[k]);
-    ddpol = fma(ddpol, v, double(k - 5) * S.Pd[k]);
+    ddpol = fma(ddpol, v, S.Pdd[k]);
   }
   const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
@@ -265,32 +265,35 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
     }
   }
   // ---------------- the offsets' basis: obb[m] = sum_j d0b_j Mo[0][j][m] + d1b_j Mo[1][j][m]
-  double obb[4];
+  df obb[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     df a = zero;
 #pragma unroll
     for (int j = 0; j < 3; ++j) a = dfl_add(a, dfl_add(dfl_mul(d0b[j], mow[5 * j + m]), dfl_mul(d1b[j], mow[15 + 5 * j + m])));
-    obb[m] = df_to(a);
+    obb[m] = a;
   }
-  // ---------------- FP64: mode level (as mode_bwd from here)
+  // ---------------- mode level: the phase cotangent in FP64; the orbit's reverse in double words
+  // (the centre x_c = R (cos a, sin a, 0) and the offsets' basis), t_f's cotangent back in FP64
   const double phb = 2.0 * kPi * df_to(phtb);
   g.ph = fma(phb, 2.0 * C.mfac, g.ph);          // d ph0/d phi_c = m/(2 pi)
   g.tc = fma(-B.f, phb, g.tc);                   // frac(f t_c)
   const double psib = -C.mfac * phb;
-  const double kxcb = -B.f * phb;
-  const double cod = df_to(co), sod = df_to(so);
-  g.k[0] = fma(kxcb, D.R * cod, g.k[0]);
-  g.k[1] = fma(kxcb, D.R * sod, g.k[1]);
-  double cb_ = D.R * kxcb * S.k[0], sb_ = D.R * kxcb * S.k[1];
+  const df kxcb = df_from_bits(-B.f * phb);
+  const df Rk = dfl_mul(D.Rw, kxcb);
+  gw.k[0] = dfl_add(gw.k[0], dfl_mul(Rk, co));
+  gw.k[1] = dfl_add(gw.k[1], dfl_mul(Rk, so));
+  df cb_ = dfl_mul(Rk, kpq[0]), sb_ = dfl_mul(Rk, kpq[1]);
   double tfb;
   if (D.orbit == 0) {
-    cb_ += obb[2] + 2.0 * (cod * obb[0] + sod * obb[1]);
-    sb_ += obb[3] + 2.0 * (cod * obb[1] - sod * obb[0]);
-    tfb = kPi * (cod * sb_ - sod * cb_) * D.rate_ht;
+    // ob = (cos 2a, sin 2a, cos a, sin a)
+    cb_ = dfl_add(cb_, dfl_add(obb[2], df_scale2(dfl_add(dfl_mul(co, obb[0]), dfl_mul(so, obb[1])), 2.0f)));
+    sb_ = dfl_add(sb_, dfl_add(obb[3], df_scale2(dfl_sub(dfl_mul(co, obb[1]), dfl_mul(so, obb[0])), 2.0f)));
+    tfb = kPi * D.rate_ht * df_to(dfl_sub(dfl_mul(co, sb_), dfl_mul(so, cb_)));
   } else {
-    const double c0 = df_to(eg.re), s0 = df_to(eg.im);
-    tfb = kPi * (c0 * obb[1] - s0 * obb[0]) * D.geo_rate_ht + kPi * (cod * sb_ - sod * cb_) * D.rate_ht;
+    // ob = (cos phi_0, sin phi_0, 0, 0)
+    tfb = kPi * D.geo_rate_ht * df_to(dfl_sub(dfl_mul(eg.re, obb[1]), dfl_mul(eg.im, obb[0]))) +
+          kPi * D.rate_ht * df_to(dfl_sub(dfl_mul(co, sb_), dfl_mul(so, cb_)));
   }
   g.tc += tfb;
   const double Db = tfb * C.tffac * B.invf;
@@ -312,11 +315,11 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
   }
   vb += psib * dv * iv + Db * (iv5 * ddpol * iv + S.Q6 * (2.0 + lnv));
   g.M = fma(vb * B.f13, CG.dcm_dM, g.M);
-  double pq = SG.dP_dq[7], dq = 2.0 * SG.dP_dq[7];
+  double pq = SG.dP_dq[7], dq = SG.dPd_dq[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     pq = fma(pq, v, SG.dP_dq[k]);
-    dq = fma(dq, v, (k - 5) * SG.dP_dq[k]);
+    dq = fma(dq, v, SG.dPd_dq[k]);
   }
   const double psiq = fma(iv5, pq, lnv * fma(SG.dQ6_dq, v, SG.dQ5_dq));
   const double Dq = fma(iv5, dq, fma(SG.dQ6_dq * v, 1.0 + lnv, SG.dQ5_dq));

@@ -126,6 +126,7 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   S.P[6] = n * (a6c - 6848.0 / 21.0 * kLn4);             // alpha6 - (6848/21) ln(4 v)
   S.P[7] = n * pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
   for (int k = 0; k < 8; ++k) S.Pd[k] = double(k - 5) * S.P[k];
+  for (int k = 0; k < 8; ++k) S.Pdd[k] = double(k - 5) * S.Pd[k];
   S.Q5 = n * 3.0 * a5c;
   S.Q6 = n * (-6848.0 / 21.0);
   // sky frame
@@ -371,7 +372,7 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   double iv5 = iv * iv;
   iv5 = iv5 * iv5 * iv;
   double poly = S.P[7];
-  double dpol = 2.0 * S.P[7];
+  double dpol = S.Pd[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);

@@ -93,7 +93,7 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   double iv5 = iv * iv;
   iv5 = iv5 * iv5 * iv;
   double poly = S.P[7];
-  double dpol = 2.0 * S.P[7];
+  double dpol = S.Pd[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);

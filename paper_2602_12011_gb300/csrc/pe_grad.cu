@@ -37,6 +37,7 @@ __global__ void k_prep_grad(const double* theta, int B, unsigned mask, DetSet ds
     SampleCoefT<Dn> SD;
     sample_prep_t<Dn>(td, valid, mask, SD);
     for (int k = 0; k < 8; ++k) G.dP_dq[k] = SD.P[k].d[1];
+    for (int k = 0; k < 8; ++k) G.dPd_dq[k] = double(k - 5) * G.dP_dq[k];
     G.dQ5_dq = SD.Q5.d[1];
     G.dQ6_dq = SD.Q6.d[1];
     G.dP3_dc1 = SD.P[3].d[2];

@@ -58,6 +58,7 @@ struct SampleCoefT {
   T tc;
   T P[8];
   T Pd[8];              // (k - 5) P[k]: coefficients of v dPsi_PN/dv
+  T Pdd[8];             // (k - 5)^2 P[k]: coefficients of v d(v dPsi_PN/dv)/dv (reverse sweeps)
   T Q5, Q6;
   T k[3], p[3], q[3];   // propagation direction and polarisation frame
   float2 kw[3];         // k as double words
@@ -90,6 +91,7 @@ struct ModeGrad {
 };
 struct SampleGrad {
   double dP_dq[8], dQ5_dq, dQ6_dq;
+  double dPd_dq[8];     // (k - 5) dP_dq[k]
   double dP3_dc1, dP4_dc1, dP3_dc2, dP4_dc2;
   double dlnA_ddL;           // -1/dL
   double dk[3][3], dp[3][3], dq[3][3];   // [component][lambda, beta, psi]

@@ -109,7 +109,7 @@ __device__ __forceinline__ double psi_of(const SampleCoef& S, double v, double l
   const double iv = 1.0 / v;
   double iv5 = iv * iv;
   iv5 = iv5 * iv5 * iv;
-  double poly = S.P[7], dpol = 2.0 * S.P[7];
+  double poly = S.P[7], dpol = 2.0 * S.P[7];   // P may be a truncated copy (baseline): no Pd
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);
