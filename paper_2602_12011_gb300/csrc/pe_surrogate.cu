@@ -93,8 +93,8 @@ __global__ void k_sur_prep(const double* theta, int B, unsigned mask, SampleCoef
   // baseline: the same phase series truncated after 2.5PN (the 3PN and 3.5PN terms, with the
   // 3PN logarithm, are what the network learns)
   SampleCoef b = a;
-  b.P[6] = 0.0;
-  b.P[7] = 0.0;
+  b.P[6] = b.Pd[6] = b.Pdd[6] = 0.0;
+  b.P[7] = b.Pd[7] = b.Pdd[7] = 0.0;
   b.Q6 = 0.0;
   // the surrogate's per-bin amplitude is the Newtonian power law (2 pi M^2/D) sqrt(eta/3m) x^-7/4;
   // the mode factor |H_lm| travels with the transfer functions, so store amp / |H_lm| here
@@ -109,7 +109,7 @@ __device__ __forceinline__ double psi_of(const SampleCoef& S, double v, double l
   const double iv = 1.0 / v;
   double iv5 = iv * iv;
   iv5 = iv5 * iv5 * iv;
-  double poly = S.P[7], dpol = 2.0 * S.P[7];   // P may be a truncated copy (baseline): no Pd
+  double poly = S.P[7], dpol = 2.0 * S.P[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
     poly = fma(poly, v, S.P[k]);
