@@ -54,7 +54,8 @@ def test_hetero_parity_with_oracle(oracle_mod, Lb, det, mix):
     gh.close()
 
 
-def test_hetero_network_parity(oracle_mod, Lb):
+@pytest.mark.parametrize("mix", [False, True], ids=["fp64", "mixed"])
+def test_hetero_network_parity(oracle_mod, Lb, mix):
     from oracle import hetero as HT
     Ts = (2.0 ** 18, 2.0 ** 17, 2.0 ** 16)
     th0 = np.array([6e5, 3.0, 0.2, 0.5, 12.0, 1.1, 0.3, 4.0, -0.6, 0.4, 0.8 * 2.0 ** 16])
@@ -66,7 +67,7 @@ def test_hetero_network_parity(oracle_mod, Lb):
         e = HT.default_edges(T, k0, nb, th0, W.MODE_ALL, 48)
         ohs.append(HT.Hetero(od, th0, W.MODE_ALL, e))
         gds.append(gd)
-        ghs.append(Lb.Hetero(gd, th0, W.MODE_ALL, edges=e))
+        ghs.append(Lb.Hetero(gd, th0, W.MODE_ALL | (Lb.PE_PREC_MIXED if mix else 0), edges=e))
     th = np.vstack([th0, _near(th0, 6, 7, 1.0)])
     g = Lb.hetero_loglike(ghs, th, dhhh=True)
     for s in range(th.shape[0]):
