@@ -50,6 +50,7 @@ struct HetDev {
 struct HetSet {
   HetDev h[kMaxDet];
   int n;
+  int nemax;   // largest ne of the set (rows of the kernel's ratio table)
 };
 
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
@@ -172,6 +173,42 @@ __global__ void k_to_dw4(const double2* in, long long n, float4* out) {
 }
 
 __device__ __forceinline__ cdf unpack4(float4 q) { return cdf{df_make(q.x, q.y), df_make(q.z, q.w)}; }
+
+// Ratios the mixed kernel keeps as double words stay below this magnitude. Normal ratios are O(1);
+// one far larger comes only from an edge where the reference signal has almost vanished (a tapered
+// end that the sample outlives), and a bin that uses such an edge is contracted in FP64 instead
+// (ratio squares times 1/df^2 stay far inside the FP32 exponent range below it).
+constexpr double kHetDwRatioMax = 16777216.0;   // 2^24
+
+// FP64 contraction of coarse bin b, channel c: (<d|h>, <h|h>) from the ratios ld(edge, md) and the
+// summary data A, B.
+template <class Ld>
+__device__ __forceinline__ void het_bin_fp64(const HetDev& H, int b, int c, Ld ld, double& dh, double& hh) {
+  const double idf = 1.0 / (H.fe[b + 1] - H.fe[b]);
+  double2 r0[kNModes], r1[kNModes];
+  for (int md = 0; md < kNModes; ++md) {
+    const int s0 = H.src[(b * kNModes + md) * 3 + c], s1 = H.src[((b + 1) * kNModes + md) * 3 + c];
+    const double2 ra = s0 >= 0 ? ld(s0, md) : make_double2(0.0, 0.0);
+    const double2 rb = s1 >= 0 ? ld(s1, md) : make_double2(0.0, 0.0);
+    r0[md] = ra;
+    r1[md] = make_double2((rb.x - ra.x) * idf, (rb.y - ra.y) * idf);
+  }
+  dh = 0.0;
+  hh = 0.0;
+  for (int md = 0; md < kNModes; ++md) {
+    const double2 a0 = H.A[(((size_t)b * kNModes + md) * 3 + c) * 2 + 0];
+    const double2 a1 = H.A[(((size_t)b * kNModes + md) * 3 + c) * 2 + 1];
+    dh += cmul(a0, r0[md]).x + cmul(a1, r1[md]).x;
+    for (int m2 = md; m2 < kNModes; ++m2) {
+      const double2* q = H.Bs + (((size_t)b * kPairs + pair_index(md, m2)) * 3 + c) * 3;
+      const double2 t0 = cmul(r0[md], cconj(r0[m2]));
+      const double2 t1 = cadd(cmul(r1[md], cconj(r0[m2])), cmul(r0[md], cconj(r1[m2])));
+      const double2 t2 = cmul(r1[md], cconj(r1[m2]));
+      const double x = cmul(q[0], t0).x + cmul(q[1], t1).x + cmul(q[2], t2).x;
+      hh += (md == m2) ? x : 2.0 * x;
+    }
+  }
+}
 // Re(a b) and Re(a conj(b)) in double words
 __device__ __forceinline__ df re_mul(const cdf& a, const cdf& b) { return dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)); }
 __device__ __forceinline__ cdf mul_conj(const cdf& a, const cdf& b) {
@@ -181,11 +218,13 @@ __device__ __forceinline__ cdf mul_conj(const cdf& a, const cdf& b) {
 // One CTA of kTileBins threads per sample. Dynamic shared memory: [max ne][5][3] double2 ratios.
 // MIX: the signal at the edges by the mixed-precision unit, the ratios kept as double words and
 // the contraction in double words (Aw, Bw); the sums across bins and the block reduction stay
-// FP64.
+// FP64. An edge with a ratio of kHetDwRatioMax or more keeps all its ratios in FP64 (flag byte
+// per edge after the ratios), and every bin that reads it takes the FP64 contraction.
 template <bool MIX>
 __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, const SampleCoef* __restrict__ coef,
                                                            double* logl, double* dhhh) {
   extern __shared__ double2 rsh[];
+  unsigned char* wflag = reinterpret_cast<unsigned char*>(rsh + (size_t)hs.nemax * kNModes * 3);
   __shared__ double pc[kProj];
   __shared__ float2 pcw[MIX ? kProj : 1];
   __shared__ double sh[6][kTileBins / 32];
@@ -216,12 +255,23 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
         mode_brackets_mixed(D, S, H.edge[e], H.mask, o, stabw, pcw);
       else
         mode_brackets(D, S, H.edge[e], H.mask, o, stab, pc);
+      bool wide = false;
+      if constexpr (MIX) {
+        for (int md = 0; md < kNModes; ++md)
+          for (int c = 0; c < 3; ++c) {
+            const int j = (e * kNModes + md) * 3 + c;
+            if (H.src[j] != e) continue;
+            const double2 r = cdiv(o[md][c], H.h0e[j]);
+            wide |= !(fmax(fabs(r.x), fabs(r.y)) < kHetDwRatioMax);   // also true for inf and NaN
+          }
+        wflag[e] = wide ? 1 : 0;
+      }
       for (int md = 0; md < kNModes; ++md)
         for (int c = 0; c < 3; ++c) {
           const int j = (e * kNModes + md) * 3 + c;
           if (H.src[j] != e) continue;
           const double2 r = cdiv(o[md][c], H.h0e[j]);
-          if constexpr (MIX) {
+          if (MIX && !wide) {
             const float2 re = to_dw(r.x), im = to_dw(r.y);
             reinterpret_cast<float4*>(rsh)[j] = make_float4(re.x, re.y, im.x, im.y);
           } else {
@@ -235,6 +285,27 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
       const float4* rw = reinterpret_cast<const float4*>(rsh);
       const cdf zc = {df_make(0.f, 0.f), df_make(0.f, 0.f)};
       for (int b = threadIdx.x; b < H.ne - 1; b += blockDim.x) {
+        bool wide = false;
+        for (int j = 0; j < kNModes * 3; ++j) {
+          const int s0 = H.src[b * kNModes * 3 + j], s1 = H.src[(b + 1) * kNModes * 3 + j];
+          wide |= (s0 >= 0 && wflag[s0]) || (s1 >= 0 && wflag[s1]);
+        }
+        if (wide) {
+#pragma unroll 1
+          for (int c = 0; c < 3; ++c) {
+            auto ld = [&](int e, int md) -> double2 {
+              const int j = (e * kNModes + md) * 3 + c;
+              if (wflag[e]) return rsh[j];
+              const cdf r = unpack4(rw[j]);
+              return make_double2(df_to(r.re), df_to(r.im));
+            };
+            double dh, hh;
+            het_bin_fp64(H, b, c, ld, dh, hh);
+            v[c] += dh;
+            v[3 + c] += hh;
+          }
+          continue;
+        }
         const df idf = to_dw(1.0 / (H.fe[b + 1] - H.fe[b]));
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
@@ -270,31 +341,10 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
       }
     } else
     for (int b = threadIdx.x; b < H.ne - 1; b += blockDim.x) {
-      const double idf = 1.0 / (H.fe[b + 1] - H.fe[b]);
 #pragma unroll 1
       for (int c = 0; c < 3; ++c) {
-        double2 r0[kNModes], r1[kNModes];
-        for (int md = 0; md < kNModes; ++md) {
-          const int s0 = H.src[(b * kNModes + md) * 3 + c], s1 = H.src[((b + 1) * kNModes + md) * 3 + c];
-          const double2 ra = s0 >= 0 ? rsh[(s0 * kNModes + md) * 3 + c] : make_double2(0.0, 0.0);
-          const double2 rb = s1 >= 0 ? rsh[(s1 * kNModes + md) * 3 + c] : make_double2(0.0, 0.0);
-          r0[md] = ra;
-          r1[md] = make_double2((rb.x - ra.x) * idf, (rb.y - ra.y) * idf);
-        }
-        double dh = 0.0, hh = 0.0;
-        for (int md = 0; md < kNModes; ++md) {
-          const double2 a0 = H.A[(((size_t)b * kNModes + md) * 3 + c) * 2 + 0];
-          const double2 a1 = H.A[(((size_t)b * kNModes + md) * 3 + c) * 2 + 1];
-          dh += cmul(a0, r0[md]).x + cmul(a1, r1[md]).x;
-          for (int m2 = md; m2 < kNModes; ++m2) {
-            const double2* q = H.Bs + (((size_t)b * kPairs + pair_index(md, m2)) * 3 + c) * 3;
-            const double2 t0 = cmul(r0[md], cconj(r0[m2]));
-            const double2 t1 = cadd(cmul(r1[md], cconj(r0[m2])), cmul(r0[md], cconj(r1[m2])));
-            const double2 t2 = cmul(r1[md], cconj(r1[m2]));
-            const double x = cmul(q[0], t0).x + cmul(q[1], t1).x + cmul(q[2], t2).x;
-            hh += (md == m2) ? x : 2.0 * x;
-          }
-        }
+        double dh, hh;
+        het_bin_fp64(H, b, c, [&](int e, int md) { return rsh[(e * kNModes + md) * 3 + c]; }, dh, hh);
         v[c] += dh;
         v[3 + c] += hh;
       }
@@ -567,6 +617,7 @@ pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double*
     ds.d[i] = hets[i]->dev.det;
     nemax = std::max(nemax, hets[i]->dev.ne);
   }
+  hs.nemax = nemax;
   auto is_dev = [](const void* p) {
     if (p == nullptr) return false;
     cudaPointerAttributes a;
@@ -598,8 +649,8 @@ pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double*
   if (e == cudaSuccess)
     e = pe::launch_prep(th, B, hets[0]->dev.mask, ds, static_cast<pe::SampleCoef*>(coef), static_cast<int*>(nend),
                         static_cast<int*>(stt), st);
-  const size_t smem = (size_t)nemax * pe::kNModes * 3 * sizeof(double2);
   const bool mix = (hets[0]->dev.mask & PE_PREC_MIXED) != 0u;
+  const size_t smem = (size_t)nemax * pe::kNModes * 3 * sizeof(double2) + (mix ? (size_t)nemax : 0);
   auto kern = mix ? pe::k_het_loglike<true> : pe::k_het_loglike<false>;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
