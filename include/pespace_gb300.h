@@ -157,11 +157,11 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
  * no allocating routine.
  *   theta, out_logl and the optional out_dhhh / out_status must be DEVICE pointers (host buffers
  *   would need staging memory); other arguments and layouts are as for pe_loglike_batch.
- *   Size limit: coefficients (880 bytes per sample) plus one 48-byte partial per tile (128 bins in
- *   FP64, 512 with PE_PREC_MIXED) of every (detector, sample) pair must fit in 32 MiB -- in FP64
- *   about 400 samples on one 2^22 s grid (209,296 bins), about 1,500 on a 2^20 s grid (four times
- *   as many with PE_PREC_MIXED). Larger batches return PE_EINVAL with the
- *   needed size in pe_last_error(); split them.
+ *   Size limit: coefficients (1,024 bytes per sample) plus one 48-byte partial per 128-bin
+ *   sub-tile of every (detector, sample) pair must fit in 32 MiB -- about 400 samples on one
+ *   2^22 s grid (209,296 bins), about 1,500 on a 2^20 s grid, in every precision. Larger batches
+ *   return PE_EINVAL with the needed size in pe_last_error(); split them. The work items take the
+ *   precision's default sub-tile count (no tuned choice is read).
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  *   that device current, so make that first call before any stream capture.
  *   All calls share the one array: calls whose work overlaps on the GPU (other streams, other
@@ -177,22 +177,31 @@ pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet, const doub
  * (detector, sample) pair brings its own grid length and active bin range; all pairs run in one
  * persistent launch over their bin tiles. Refill theta in place and call pe_plan_launch on
  * any stream; results equal pe_loglike_batch's bit for bit.
+ *   The forward kernel's work items are 1, 2, 4 or 8 consecutive 128-bin sub-tiles of one
+ *   (detector, sample) pair; each sub-tile keeps its own partial sum in a fixed reduction order.
  *   autotune = 1: if the tuning cache has no entry for this workload (GPU, SM count, batch size,
- *   mode mask, grids), time the forward kernel's launch variants on the theta present at
- *   creation and store the fastest. The cache is a JSON file at $PE_TUNE_CACHE, else
+ *   mode mask, grids), time the forward kernel's launch choices on the theta present at
+ *   creation (register-budget variant x persistent grid size, then the sub-tiles per work item)
+ *   and store the fastest. The cache is a JSON file at $PE_TUNE_CACHE, else
  *   $XDG_CACHE_HOME/pespace_gb300/tune.json, else ~/.cache/pespace_gb300/tune.json.
- *   Tuning picks only the kernel's register-budget variant and its persistent grid size, never
- *   the tile, so it never changes a result. pe_loglike_batch also uses a cached choice.
- * pe_autotune tunes (and caches) the same choice without building a plan (theta: device). */
+ *   No choice changes a result (every choice keeps the same per-sub-tile partials). pe_loglike_batch
+ *   also uses a cached choice.
+ * pe_plan_info: the plan's choice (subtiles: sub-tiles per work item); tuned_ms 0 for a default.
+ * pe_autotune tunes (and caches) the same choice without building a plan (theta: device).
+ * pe_tune_set records a choice for a workload as the autotuner would (fwd_variant 0..2,
+ *   ctas_per_sm 1..64, subtiles 1, 2, 4 or 8; PE_EINVAL otherwise); later calls and plans for
+ *   that workload use it. */
 typedef struct pe_plan_s* pe_plan;
 pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode_mask, const double* theta_dev,
                          double* out_logl_dev, double* out_dhhh_dev, int32_t* out_status_dev, int autotune,
                          pe_plan* out);
 pe_status pe_plan_launch(pe_plan plan, void* stream);
-pe_status pe_plan_info(pe_plan plan, int* fwd_variant, int* ctas_per_sm, double* tuned_ms);
+pe_status pe_plan_info(pe_plan plan, int* fwd_variant, int* ctas_per_sm, int* subtiles, double* tuned_ms);
 pe_status pe_plan_destroy(pe_plan plan);
 pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev, int B, unsigned mode_mask,
-                      int* out_variant, int* out_ctas_per_sm, double* out_ms);
+                      int* out_variant, int* out_ctas_per_sm, int* out_subtiles, double* out_ms);
+pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_mask, int fwd_variant, int ctas_per_sm,
+                      int subtiles);
 
 /* ---- Learned waveform surrogate (spec growth: MLP on BF16 tensor cores + node spline) ----
  * An MLP 11 -> 256 -> 256 -> 256 -> 2560 (BF16 weights and activations on tensor cores, FP32

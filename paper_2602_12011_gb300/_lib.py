@@ -82,10 +82,12 @@ def lib():
         L.pe_loglike_batch_noalloc.restype = C.c_int
         L.pe_plan_create.argtypes = [_P, C.c_int, C.c_int, C.c_uint, _P, _P, _P, _P, C.c_int, C.POINTER(_P)]
         L.pe_plan_launch.argtypes = [_P, _P]
-        L.pe_plan_info.argtypes = [_P, _P, _P, _P]
+        L.pe_plan_info.argtypes = [_P, _P, _P, _P, _P]
         L.pe_plan_destroy.argtypes = [_P]
-        L.pe_autotune.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P]
-        for name in ("pe_plan_create", "pe_plan_launch", "pe_plan_info", "pe_plan_destroy", "pe_autotune"):
+        L.pe_autotune.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+        L.pe_tune_set.argtypes = [_P, C.c_int, C.c_int, C.c_uint, C.c_int, C.c_int, C.c_int]
+        for name in ("pe_plan_create", "pe_plan_launch", "pe_plan_info", "pe_plan_destroy", "pe_autotune",
+                     "pe_tune_set"):
             getattr(L, name).restype = C.c_int
         L.pe_surrogate_create.argtypes = [C.c_uint64, C.POINTER(_P)]
         L.pe_surrogate_destroy.argtypes = [_P]
@@ -377,9 +379,9 @@ def pe_plan_launch(plan: int, stream=None):
 
 
 def pe_plan_info(plan: int):
-    v, c, ms = C.c_int(), C.c_int(), C.c_double()
-    _check(lib().pe_plan_info(plan, C.addressof(v), C.addressof(c), C.addressof(ms)))
-    return {"fwd_variant": v.value, "ctas_per_sm": c.value, "tuned_ms": ms.value}
+    v, c, r, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+    _check(lib().pe_plan_info(plan, C.addressof(v), C.addressof(c), C.addressof(r), C.addressof(ms)))
+    return {"fwd_variant": v.value, "ctas_per_sm": c.value, "subtiles": r.value, "tuned_ms": ms.value}
 
 
 def pe_plan_destroy(plan: int):
@@ -387,10 +389,15 @@ def pe_plan_destroy(plan: int):
 
 
 def pe_autotune(hs, theta, B: int, mode_mask: int):
-    v, c, ms = C.c_int(), C.c_int(), C.c_double()
+    v, c, r, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
     _check(lib().pe_autotune(_handles(hs), len(hs), _ptr(theta), int(B), int(mode_mask), C.addressof(v),
-                             C.addressof(c), C.addressof(ms)))
-    return {"fwd_variant": v.value, "ctas_per_sm": c.value, "tuned_ms": ms.value}
+                             C.addressof(c), C.addressof(r), C.addressof(ms)))
+    return {"fwd_variant": v.value, "ctas_per_sm": c.value, "subtiles": r.value, "tuned_ms": ms.value}
+
+
+def pe_tune_set(hs, B: int, mode_mask: int, fwd_variant: int, ctas_per_sm: int, subtiles: int):
+    _check(lib().pe_tune_set(_handles(hs), len(hs), int(B), int(mode_mask), int(fwd_variant), int(ctas_per_sm),
+                             int(subtiles)))
 
 
 class Plan:

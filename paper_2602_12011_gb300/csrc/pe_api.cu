@@ -492,7 +492,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   Scratch sc(st);
   const int P = ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kTileBins);
   const double* th = theta;
   if (!is_device_ptr(theta)) {
     double* t = nullptr;
@@ -503,10 +503,14 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   pe::SampleCoef* coef = nullptr;
   int* nend = nullptr;
   long long* off = nullptr;
+  long long* offi = nullptr;
   double* part = nullptr;
+  pe::TuneChoice tc = pe::default_choice(pe::mask_prec(mode_mask));
+  pe::lookup_tuned(ds, B, mode_mask, &tc);
   PE_CUDA(sc.alloc(&coef, B));
   PE_CUDA(sc.alloc(&nend, P));
   PE_CUDA(sc.alloc(&off, P + 1));
+  if (tc.subtiles > 1) PE_CUDA(sc.alloc(&offi, P + 1));
   PE_CUDA(sc.alloc(&part, (size_t)max_tiles * 6));
   const bool h_logl = !is_device_ptr(out_logl);
   const bool h_dhhh = out_dhhh && !is_device_ptr(out_dhhh);
@@ -518,13 +522,11 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (h_dhhh) PE_CUDA(sc.alloc(&dhhh, (size_t)B * ndet * 6));
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep(th, B, mode_mask, ds, coef, nend, stat, st));
-  PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), st));
-  pe::TuneChoice tc = pe::default_choice();
-  pe::lookup_tuned(ds, B, mode_mask, &tc);
+  PE_CUDA(pe::launch_fwd_offsets(nend, P, off, offi, tc.subtiles, st));
   void* prof = nullptr;
   pe::profile_begin(st, &prof);
-  PE_CUDA(pe::launch_loglike_fwd_variant(tc.variant, pe::mask_prec(mode_mask), ds, B, coef, nend, off, part,
-                                         pe::grid_for(tc, max_tiles), st));
+  PE_CUDA(pe::launch_loglike_fwd_variant(tc.variant, pe::mask_prec(mode_mask), ds, B, coef, nend, off, offi,
+                                         tc.subtiles, part, pe::grid_for(tc, max_tiles), st));
   pe::profile_end(st, prof);
   PE_CUDA(pe::launch_reduce(ds, B, off, part, coef, logl, dhhh, st));
   if (h_logl) PE_CUDA(cudaMemcpyAsync(out_logl, logl, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -555,6 +555,36 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[kTileBins /
     }
 }
 
+// Block sum of the six per-thread values of the forward kernels (<d|h>_c, <h|h>_c) through shared
+// memory: every thread stores its six values in red[i][threadIdx.x]; thread t < 96 adds entries
+// g, g + 16, ..., g + 112 of row i = t / 16 (g = t % 16) in that order into red[i][g]; thread i < 6
+// then adds red[i][0..15] in order. About 6 additions per thread against 30 for a shuffle tree per
+// value, and no lane-dependent shuffles. Rows are padded by kRedPad entries so that the six final
+// readers hit different banks. Returns true in threads 0..5, with the block's sum of
+// v[threadIdx.x] in *out.
+constexpr int kRedPad = 2;
+template <class T, class Add>
+__device__ __forceinline__ bool block_sum6(const T v[6], Add add, T (*red)[kTileBins + kRedPad], T* out) {
+  __syncthreads();   // the previous call's final readers are done with red
+#pragma unroll
+  for (int i = 0; i < 6; ++i) red[i][threadIdx.x] = v[i];
+  __syncthreads();
+  if (threadIdx.x < 6 * 16) {
+    const int i = threadIdx.x >> 4, g = threadIdx.x & 15;
+    T s = red[i][g];
+#pragma unroll
+    for (int k = 1; k < kTileBins / 16; ++k) s = add(s, red[i][g + 16 * k]);
+    red[i][g] = s;   // only this thread reads or writes column g of row i in this step
+  }
+  __syncthreads();
+  if (threadIdx.x >= 6) return false;
+  T s = red[threadIdx.x][0];
+#pragma unroll
+  for (int g = 1; g < 16; ++g) s = add(s, red[threadIdx.x][g]);
+  *out = s;
+  return true;
+}
+
 // A/E/T combinations (without Q n_c): B_A = Z' - X', B_E = X' - 2Y' + Z', B_T = X' + Y' + Z'.
 __device__ __forceinline__ void aet_from_xyz(const double2 x[3], double2 o[3]) {
   o[0] = csub(x[2], x[0]);

@@ -19,13 +19,16 @@ constexpr double kEulerGamma = 0.57721566490153286061;
 
 constexpr int kNModes = 5;      // (2,2) (2,1) (3,3) (3,2) (4,4)
 constexpr int kMaxDet = 8;
-constexpr int kTileBins = 128;  // frequency bins per work tile = threads per CTA of the hot kernels
-constexpr int kMixTileBins = 512;  // bins per work tile of the mixed and FP32 likelihood kernels (4 per thread)
+constexpr int kTileBins = 128;  // frequency bins per (sub-)tile = threads per CTA of the hot kernels
 // Arithmetic of the forward path (mode-mask flags PE_PREC_MIXED, PE_PREC_FP32).
 constexpr int kPrecFP64 = 0, kPrecMixed = 1, kPrecFP32 = 2;
-// Bins per work tile of the log-likelihood kernels: the FP64 path keeps one bin per thread (most
-// CTAs for small batches); the others amortise their block reduction over four bins.
-__host__ __device__ constexpr int fwd_tile_bins(int prec) { return prec == kPrecFP64 ? kTileBins : kMixTileBins; }
+// Work items of the log-likelihood kernels are R consecutive 128-bin sub-tiles of one (detector,
+// sample) pair, R in {1, 2, 4, 8} picked by the autotuner. The default (no tuned choice) keeps
+// one sub-tile per item in FP64 (most CTAs for small batches) and four in the other precisions,
+// which amortise their per-item staging over more bins. Each sub-tile keeps its own partial, so R
+// never changes a result.
+constexpr int kFwdMaxSubtiles = 8;
+__host__ __device__ constexpr int fwd_default_subtiles(int prec) { return prec == kPrecFP64 ? 1 : 4; }
 constexpr int kSinTab = 1024;   // entries of the (cos, sin) table used by sincos_turns
 
 // Per-(sample, mode) coefficients (row A1 of the path). With v = (2 pi M f/m)^(1/3):

@@ -297,50 +297,27 @@ __device__ __forceinline__ int find_pair(const long long* off, int P, long long 
 }
 
 // ------------------------------------------------------------------------------------------
-// Rows A2-A7: persistent fused kernel. Work item = one tile of fwd_tile_bins(PREC) bins of one
-// (detector, sample) pair; CTAs stride over the flattened tile list. Each thread owns every
-// kTileBins-th bin of the tile (one bin in FP64, four in the mixed and FP32 paths; coalesced),
-// sums the modes' TDI brackets in registers, forms A/E/T and the weighted products and adds them
-// up; the tile's six sums (<d|h>_c, <h|h>_c) go to part[tile][6]. MINB (resident CTAs per SM requested from
-// the compiler) sets the register budget only; every variant of one precision does the same
-// arithmetic in the same order, so the autotuner's choice never changes a result. PREC selects the
-// all-FP64 unit, the mixed FP64/double-word one (pe_device_mixed.cuh) or the all-FP32 one of the
-// precision study (pe_device_f32.cuh).
+// Rows A2-A7: persistent fused kernel. The work list is every (detector, sample) pair's 128-bin
+// sub-tiles (off: their offsets per pair); a work item is R consecutive sub-tiles of one pair
+// (offi: the items' offsets), and CTAs stride over the items. Per item the CTA forms the pair's
+// projection forms once; per sub-tile each thread owns one bin (coalesced), sums the modes' TDI
+// brackets in registers, forms A/E/T and the weighted products, and the CTA reduces them in a
+// fixed order into part[sub-tile][6] (<d|h>_c, <h|h>_c). The partials are per sub-tile whatever
+// R, MINB (resident CTAs per SM requested from the compiler, which sets the register budget) or
+// the grid, so the autotuner's choices never change a result. PREC selects the all-FP64 unit, the
+// mixed FP64/double-word one (pe_device_mixed.cuh) or the all-FP32 one of the precision study
+// (pe_device_f32.cuh).
 // ------------------------------------------------------------------------------------------
-// Block reduction of NV double words per thread (accurate double-word adds, fixed tree order);
-// result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum_dw(df v[NV], float2 (*sh)[kTileBins / 32]) {
-#pragma unroll
-  for (int i = 0; i < NV; ++i)
-    for (int o = 16; o > 0; o >>= 1) {
-      const df u = df_make(__shfl_down_sync(0xffffffffu, v[i].x, o), __shfl_down_sync(0xffffffffu, v[i].y, o));
-      v[i] = df_add(v[i], u);
-    }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh[i][wid] = v[i];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      df s = sh[i][0];
-      for (int w = 1; w < kTileBins / 32; ++w) s = df_add(s, sh[i][w]);
-      v[i] = s;
-    }
-}
-
 template <int MINB, int PREC>
 __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                                  const int* __restrict__ nend,
-                                                                 const long long* __restrict__ off, double* part) {
-  constexpr int TILE = fwd_tile_bins(PREC);
-  __shared__ double sh[6][kTileBins / 32];
-  __shared__ double pc[kProj];    // the tile's projection forms (proj_coef)
+                                                                 const long long* __restrict__ off,
+                                                                 const long long* __restrict__ offi, int R,
+                                                                 double* part) {
+  __shared__ double red[6][kTileBins + kRedPad];   // block_sum6 staging (as float2 or float rows)
+  __shared__ double pc[kProj];    // the item's projection forms (proj_coef)
   __shared__ float2 pcw[kProj];   // the same as double words (mixed) or floats (.x, FP32)
-  __shared__ SampleF sf;          // the tile's sample coefficients in FP32 (FP32 path)
+  __shared__ SampleF sf;          // the item's sample coefficients in FP32 (FP32 path)
   __shared__ double2 stab[kSinTab];   // the sincos table (as float4 double words in the mixed path)
   if (PREC == kPrecMixed) {
     float4* t4 = reinterpret_cast<float4*>(stab);
@@ -350,11 +327,13 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
   }
   __syncthreads();
   const int P = ds.ndet * B;
-  const long long total = off[P];
+  const long long total = offi[P];
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int p = find_pair(off, P, t);
+    const int p = find_pair(offi, P, t);
     const int I = p / B, s = p - I * B;
-    const int b0 = int(t - off[p]) * TILE + threadIdx.x;
+    const long long j0 = (t - offi[p]) * R;                 // first sub-tile of the item in the pair
+    const long long q0 = off[p] + j0;                       // its index in the partials
+    const long long q1 = min(q0 + R, off[p + 1]);
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
@@ -362,83 +341,71 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
     if constexpr (PREC == kPrecMixed) {
       if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
       __syncthreads();
-      // per bin in double words, times hsc (h) and 1/dg_scale, 1/gg_scale (tables); the tile sums
-      // are scaled back in FP64
-      df v[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) v[i] = df_make(0.f, 0.f);
+      const double ih = S.ihsc;
+      const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
 #pragma unroll 1
-      for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
-        cdf x[3], o[3];
-        bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab), pcw);
-        aet_from_xyz_dw(x, o);
+      for (long long q = q0; q < q1; ++q) {
+        const int b = int(j0 + (q - q0)) * kTileBins + threadIdx.x;
+        // per bin in double words, times hsc (h) and 1/dg_scale, 1/gg_scale (tables); the
+        // sub-tile sums are scaled back in FP64
+        df v[6];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float4 g = D.dgw[c * D.nb + b];
-          v[c] = df_add_s(v[c], df_sub_s(df_mul(df_make(g.x, g.y), o[c].re), df_mul(df_make(g.z, g.w), o[c].im)));
-          const df m2 = df_add_s(df_mul(o[c].re, o[c].re), df_mul(o[c].im, o[c].im));
-          v[3 + c] = df_add_s(v[3 + c], df_mul(D.ggw[c * D.nb + b], m2));
-        }
-      }
-      block_sum_dw<6>(v, reinterpret_cast<float2(*)[kTileBins / 32]>(sh));
-      if (threadIdx.x == 0) {
-        const double ih = S.ihsc;
-        const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
+        for (int i = 0; i < 6; ++i) v[i] = df_make(0.f, 0.f);
+        if (b < ne) {
+          cdf x[3], o[3];
+          bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab), pcw);
+          aet_from_xyz_dw(x, o);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          part[t * 6 + c] = df_to(v[c]) * sd;
-          part[t * 6 + 3 + c] = df_to(v[3 + c]) * sg;
+          for (int c = 0; c < 3; ++c) {
+            const float4 g = D.dgw[c * D.nb + b];
+            v[c] = df_sub_s(df_mul(df_make(g.x, g.y), o[c].re), df_mul(df_make(g.z, g.w), o[c].im));
+            const df m2 = df_add_s(df_mul(o[c].re, o[c].re), df_mul(o[c].im, o[c].im));
+            v[3 + c] = df_mul(D.ggw[c * D.nb + b], m2);
+          }
         }
+        df r;
+        if (block_sum6(v, [](df a, df b) { return dfl_add(a, b); }, reinterpret_cast<float2(*)[kTileBins + kRedPad]>(red), &r))
+          part[q * 6 + threadIdx.x] = df_to(r) * (threadIdx.x < 3 ? sd : sg);
       }
     } else if constexpr (PREC == kPrecFP32) {
       float* pcf = reinterpret_cast<float*>(pcw);
       if (threadIdx.x < kProj) pcf[threadIdx.x] = (float)pc[threadIdx.x];
       if (threadIdx.x == 0) sample_to_f32(S, sf);
       __syncthreads();
-      float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const double ih = S.ihsc;
+      const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
 #pragma unroll 1
-      for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
-        float2 o[3];
-        bin_aet_f32(D, sf, b, o, pcf);
+      for (long long q = q0; q < q1; ++q) {
+        const int b = int(j0 + (q - q0)) * kTileBins + threadIdx.x;
+        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (b < ne) {
+          float2 o[3];
+          bin_aet_f32(D, sf, b, o, pcf);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float2 g = D.dgf[c * D.nb + b];
-          v[c] += g.x * o[c].x - g.y * o[c].y;
-          v[3 + c] += D.ggf[c * D.nb + b] * (o[c].x * o[c].x + o[c].y * o[c].y);
+          for (int c = 0; c < 3; ++c) {
+            const float2 g = D.dgf[c * D.nb + b];
+            v[c] = g.x * o[c].x - g.y * o[c].y;
+            v[3 + c] = D.ggf[c * D.nb + b] * (o[c].x * o[c].x + o[c].y * o[c].y);
+          }
         }
-      }
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-      float* shf = reinterpret_cast<float*>(sh);
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-      __syncthreads();
-      if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < 6; ++i) shf[i * 4 + wid] = v[i];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const double ih = S.ihsc;
-        const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          const float a = ((shf[i * 4] + shf[i * 4 + 1]) + shf[i * 4 + 2]) + shf[i * 4 + 3];
-          part[t * 6 + i] = (double)a * (i < 3 ? sd : sg);
-        }
+        float r;
+        if (block_sum6(v, [](float a, float b) { return a + b; }, reinterpret_cast<float(*)[kTileBins + kRedPad]>(red), &r))
+          part[q * 6 + threadIdx.x] = (double)r * (threadIdx.x < 3 ? sd : sg);
       }
     } else {
-      double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
-      for (int b = b0; b < b0 + TILE && b < ne; b += kTileBins) {
-        double2 x[3], o[3];
-        bin_xyz(D, S, b, x, stab, pc);
-        aet_from_xyz(x, o);
-        accum_bin(D, b, o, v);
+      for (long long q = q0; q < q1; ++q) {
+        const int b = int(j0 + (q - q0)) * kTileBins + threadIdx.x;
+        double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (b < ne) {
+          double2 x[3], o[3];
+          bin_xyz(D, S, b, x, stab, pc);
+          aet_from_xyz(x, o);
+          accum_bin(D, b, o, v);
+        }
+        double r;
+        if (block_sum6(v, [](double a, double b) { return a + b; }, red, &r)) part[q * 6 + threadIdx.x] = r;
       }
-      block_sum<6>(v, sh);
-      if (threadIdx.x == 0)
-#pragma unroll
-        for (int i = 0; i < 6; ++i) part[t * 6 + i] = v[i];
     }
   }
 }
@@ -555,13 +522,19 @@ cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet&
   return cudaGetLastError();
 }
 cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st) {
-  if (tile_bins == kTileBins)
-    k_scan_tiles<kTileBins><<<1, 1024, 0, st>>>(nend, P, off);
-  else if (tile_bins == kMixTileBins)
-    k_scan_tiles<kMixTileBins><<<1, 1024, 0, st>>>(nend, P, off);
-  else
-    return cudaErrorInvalidValue;
+  switch (tile_bins) {
+    case kTileBins: k_scan_tiles<kTileBins><<<1, 1024, 0, st>>>(nend, P, off); break;
+    case 2 * kTileBins: k_scan_tiles<2 * kTileBins><<<1, 1024, 0, st>>>(nend, P, off); break;
+    case 4 * kTileBins: k_scan_tiles<4 * kTileBins><<<1, 1024, 0, st>>>(nend, P, off); break;
+    case 8 * kTileBins: k_scan_tiles<8 * kTileBins><<<1, 1024, 0, st>>>(nend, P, off); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
+}
+cudaError_t launch_fwd_offsets(const int* nend, int P, long long* off, long long* offi, int R, cudaStream_t st) {
+  cudaError_t e = launch_scan_tiles(nend, P, off, kTileBins, st);
+  if (e == cudaSuccess && R > 1) e = launch_scan_tiles(nend, P, offi, R * kTileBins, st);
+  return e;
 }
 cudaError_t launch_dw_tables(const double* f, const double* f13, const double* fm76, const double2* sca,
                              const double2* z, const double2* tab, int nb, double L, float2* fw, float2* aw,
@@ -591,15 +564,15 @@ cudaError_t launch_f32_tables(const double* f, const double* f13, const double* 
   return cudaGetLastError();
 }
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
-                               double* part, int grid, int prec, cudaStream_t st) {
-  return launch_loglike_fwd_variant(kFwdDefaultVariant, prec, ds, B, coef, nend, off, part, grid, st);
+                               const long long* offi, int R, double* part, int grid, int prec, cudaStream_t st) {
+  return launch_loglike_fwd_variant(kFwdDefaultVariant, prec, ds, B, coef, nend, off, offi, R, part, grid, st);
 }
 
 namespace {
 template <int MINB, int PREC>
 cudaError_t fwd_one(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
-                    double* part, int grid, cudaStream_t st) {
-  k_loglike_fwd<MINB, PREC><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, part);
+                    const long long* offi, int R, double* part, int grid, cudaStream_t st) {
+  k_loglike_fwd<MINB, PREC><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, R > 1 ? offi : off, R, part);
   return cudaGetLastError();
 }
 template <int MINB, int PREC>
@@ -614,17 +587,19 @@ int fwd_occ() {
 }  // namespace
 
 cudaError_t launch_loglike_fwd_variant(int variant, int prec, const DetSet& ds, int B, const SampleCoef* coef,
-                                       const int* nend, const long long* off, double* part, int grid, cudaStream_t st) {
+                                       const int* nend, const long long* off, const long long* offi, int R,
+                                       double* part, int grid, cudaStream_t st) {
+  if (R != 1 && R != 2 && R != 4 && R != 8) return cudaErrorInvalidValue;
   switch (variant * 3 + prec) {
-    case 0: return fwd_one<2, kPrecFP64>(ds, B, coef, nend, off, part, grid, st);
-    case 1: return fwd_one<2, kPrecMixed>(ds, B, coef, nend, off, part, grid, st);
-    case 2: return fwd_one<2, kPrecFP32>(ds, B, coef, nend, off, part, grid, st);
-    case 3: return fwd_one<3, kPrecFP64>(ds, B, coef, nend, off, part, grid, st);
-    case 4: return fwd_one<3, kPrecMixed>(ds, B, coef, nend, off, part, grid, st);
-    case 5: return fwd_one<3, kPrecFP32>(ds, B, coef, nend, off, part, grid, st);
-    case 6: return fwd_one<4, kPrecFP64>(ds, B, coef, nend, off, part, grid, st);
-    case 7: return fwd_one<4, kPrecMixed>(ds, B, coef, nend, off, part, grid, st);
-    case 8: return fwd_one<4, kPrecFP32>(ds, B, coef, nend, off, part, grid, st);
+    case 0: return fwd_one<2, kPrecFP64>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 1: return fwd_one<2, kPrecMixed>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 2: return fwd_one<2, kPrecFP32>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 3: return fwd_one<3, kPrecFP64>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 4: return fwd_one<3, kPrecMixed>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 5: return fwd_one<3, kPrecFP32>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 6: return fwd_one<4, kPrecFP64>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 7: return fwd_one<4, kPrecMixed>(ds, B, coef, nend, off, offi, R, part, grid, st);
+    case 8: return fwd_one<4, kPrecFP32>(ds, B, coef, nend, off, offi, R, part, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -17,9 +17,12 @@ cudaError_t launch_data_tables(const double* f, const double2* sca, const double
 cudaError_t launch_sum_parts(const double* part, int n, int w, double* out, cudaStream_t st);
 cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef, int* nend,
                         int* status, cudaStream_t st);
-// tile_bins: kTileBins (FP64 log-likelihood, gradient, Fisher, surrogate kernels) or kMixTileBins
-// (mixed-precision log-likelihood kernel)
+// Tile offsets of the uneven (detector, sample) work list for tiles of tile_bins bins (kTileBins
+// times 1, 2, 4 or 8): off[p] = sum over pairs before p of ceil(nend / tile_bins), off[P] = total.
 cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st);
+// The log-likelihood kernel's offsets: off over 128-bin sub-tiles (partials) and offi over work
+// items of R sub-tiles (not written when R == 1: the kernel then takes off for both).
+cudaError_t launch_fwd_offsets(const int* nend, int P, long long* off, long long* offi, int R, cudaStream_t st);
 inline long long tiles_of(int nb, int tile_bins) { return (nb + tile_bins - 1) / tile_bins; }
 cudaError_t launch_dw_tables(const double* f, const double* f13, const double* fm76, const double2* sca,
                              const double2* z, const double2* tab, int nb, double L, float2* fw, float2* aw,
@@ -33,14 +36,15 @@ cudaError_t launch_dw_data(const double2* dg, const double* gg, int n, double in
 cudaError_t launch_f32_tables(const double* f, const double* f13, const double* fm13, const double* lnf3,
                               const double* fm76, const double2* sca, const double2* z, int nb, float* ff, float* f13f,
                               float* fm13f, float* lnf3f, float* fm76f, float2* scaf, float2* zf, cudaStream_t st);
-// prec: kPrecFP64, kPrecMixed or kPrecFP32 forward kernel
+// prec: kPrecFP64, kPrecMixed or kPrecFP32 forward kernel; R: sub-tiles per work item (1, 2, 4, 8)
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
-                               double* part, int grid, int prec, cudaStream_t st);
+                               const long long* offi, int R, double* part, int grid, int prec, cudaStream_t st);
 // Register-budget variants of the forward kernel (min resident CTAs per SM 2, 3, 4), per precision.
 constexpr int kFwdVariants = 3;
 constexpr int kFwdDefaultVariant = 1;
 cudaError_t launch_loglike_fwd_variant(int variant, int prec, const DetSet& ds, int B, const SampleCoef* coef,
-                                       const int* nend, const long long* off, double* part, int grid, cudaStream_t st);
+                                       const int* nend, const long long* off, const long long* offi, int R,
+                                       double* part, int grid, cudaStream_t st);
 int fwd_variant_min_blocks(int variant);
 int fwd_variant_max_blocks_per_sm(int variant, int prec);
 cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const double* part, const SampleCoef* coef,

@@ -80,14 +80,18 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
   if (!device_ptr(theta) || !device_ptr(out_logl) || (out_dhhh && !device_ptr(out_dhhh)) ||
       (out_status && !device_ptr(out_status)))
     return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: theta and every output must be device pointers");
-  // Scratch layout: coefficients [B], active bins [P], tile offsets [P+1], tile partials [tiles][6].
+  // Scratch layout: coefficients [B], active bins [P], sub-tile offsets [P+1], work-item offsets
+  // [P+1], sub-tile partials [sub-tiles][6]. The work items take the precision's default number of
+  // sub-tiles (no tuned choice is read here).
   const size_t P = (size_t)ndet * B;
+  const int R = pe::fwd_default_subtiles(pe::mask_prec(mode_mask));
   size_t max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (size_t)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (size_t)B * pe::tiles_of(ds.d[i].nb, pe::kTileBins);
   const size_t o_coef = 0;
   const size_t o_nend = align256(o_coef + (size_t)B * sizeof(pe::SampleCoef));
   const size_t o_off = align256(o_nend + P * sizeof(int));
-  const size_t o_part = align256(o_off + (P + 1) * sizeof(long long));
+  const size_t o_offi = align256(o_off + (P + 1) * sizeof(long long));
+  const size_t o_part = align256(o_offi + (P + 1) * sizeof(long long));
   const size_t need = o_part + max_tiles * 6 * sizeof(double);
   if (need > kNoAllocScratchBytes) {
     char msg[320];
@@ -104,6 +108,7 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
   pe::SampleCoef* coef = reinterpret_cast<pe::SampleCoef*>(sc + o_coef);
   int* nend = reinterpret_cast<int*>(sc + o_nend);
   long long* off = reinterpret_cast<long long*>(sc + o_off);
+  long long* offi = reinterpret_cast<long long*>(sc + o_offi);
   double* part = reinterpret_cast<double*>(sc + o_part);
   // Every scratch element a kernel reads is written earlier in the same call (coefficients and
   // active counts by the prep kernel, offsets by the scan, one partial per tile by the forward
@@ -116,9 +121,9 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
     nsm = 1;
   }
   cudaError_t e = pe::launch_prep(theta, B, mode_mask, ds, coef, nend, out_status, st);
-  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), st);
+  if (e == cudaSuccess) e = pe::launch_fwd_offsets(nend, (int)P, off, offi, R, st);
   const size_t g = max_tiles < (size_t)nsm * pe::fwd_blocks_per_sm() ? max_tiles : (size_t)nsm * pe::fwd_blocks_per_sm();
-  if (e == cudaSuccess) e = pe::launch_loglike_fwd(ds, B, coef, nend, off, part, (int)(g > 0 ? g : 1),
+  if (e == cudaSuccess) e = pe::launch_loglike_fwd(ds, B, coef, nend, off, offi, R, part, (int)(g > 0 ? g : 1),
                                                      pe::mask_prec(mode_mask), st);
   if (e == cudaSuccess) e = pe::launch_reduce(ds, B, off, part, coef, out_logl, out_dhhh, st);
   if (e != cudaSuccess) {

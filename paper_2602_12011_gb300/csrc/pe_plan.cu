@@ -1,11 +1,12 @@
 // pe_plan.cu -- uneven-batch execution plans (row G3): the whole batched log-likelihood (prep,
 // tile scan, persistent fused kernel, reduction) over many (detector, sample) pairs with their
 // own grid lengths and active ranges, captured once into a CUDA graph with pre-allocated
-// scratch, plus the project autotuner that picks the forward kernel's register-budget variant and
-// persistent grid size for a workload and caches the choice in a JSON file.
+// scratch, plus the project autotuner that picks the forward kernel's work-item size (128-bin
+// sub-tiles per item), register-budget variant and persistent grid size for a workload and
+// caches the choice in a JSON file.
 //
-// Tuning changes launch parameters only (never the 128-bin tile that fixes the reduction order),
-// so a tuned launch gives bit-identical results to the default one.
+// Every choice keeps one partial per 128-bin sub-tile in the same fixed reduction order, so a
+// tuned launch gives bit-identical results to the default one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +45,9 @@ void mkdirs_for(const std::string& path) {
     if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
 }
 
-// File format: one JSON object, one entry per line:  "key": {"variant": v, "ctas_per_sm": c, "ms": t},
+// File format: one JSON object, one entry per line:
+//   "key": {"variant": v, "ctas_per_sm": c, "subtiles": r, "ms": t},
+// (entries without "subtiles" are from an earlier format and are ignored, so they are re-tuned)
 void load_locked() {
   if (g_loaded) return;
   g_loaded = true;
@@ -60,8 +63,10 @@ void load_locked() {
     if (!q1) continue;
     std::string key(q0 + 1, q1 - q0 - 1);
     TuneChoice c{};
-    if (sscanf(q1 + 1, ": {\"variant\": %d, \"ctas_per_sm\": %d, \"ms\": %lf", &c.variant, &c.ctas_per_sm, &c.ms) == 3 &&
-        c.variant >= 0 && c.variant < kFwdVariants && c.ctas_per_sm >= 1 && c.ctas_per_sm <= 64)
+    if (sscanf(q1 + 1, ": {\"variant\": %d, \"ctas_per_sm\": %d, \"subtiles\": %d, \"ms\": %lf", &c.variant,
+               &c.ctas_per_sm, &c.subtiles, &c.ms) == 4 &&
+        c.variant >= 0 && c.variant < kFwdVariants && c.ctas_per_sm >= 1 && c.ctas_per_sm <= 64 &&
+        (c.subtiles == 1 || c.subtiles == 2 || c.subtiles == 4 || c.subtiles == 8))
       g_cache[key] = c;
   }
   fclose(f);
@@ -77,8 +82,9 @@ void save_locked() {
   fprintf(f, "{\n");
   size_t i = 0;
   for (const auto& kv : g_cache) {
-    fprintf(f, "\"%s\": {\"variant\": %d, \"ctas_per_sm\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(), kv.second.variant,
-            kv.second.ctas_per_sm, kv.second.ms, (++i < g_cache.size()) ? "," : "");
+    fprintf(f, "\"%s\": {\"variant\": %d, \"ctas_per_sm\": %d, \"subtiles\": %d, \"ms\": %.6f}%s\n",
+            kv.first.c_str(), kv.second.variant, kv.second.ctas_per_sm, kv.second.subtiles, kv.second.ms,
+            (++i < g_cache.size()) ? "," : "");
   }
   fprintf(f, "}\n");
   fclose(f);
@@ -125,41 +131,62 @@ bool lookup_tuned(const DetSet& ds, int B, unsigned mask, TuneChoice* out) {
   return true;
 }
 
-TuneChoice default_choice() { return TuneChoice{kFwdDefaultVariant, 8, 0.0}; }
+TuneChoice default_choice(int prec) { return TuneChoice{kFwdDefaultVariant, 8, fwd_default_subtiles(prec), 0.0}; }
 
 int grid_for(const TuneChoice& c, long long max_tiles) {
   const long long g = std::min<long long>(max_tiles, (long long)sm_count_now() * c.ctas_per_sm);
   return (int)std::max<long long>(g, 1);
 }
 
-// Times every (variant, CTAs per SM) candidate of the forward kernel on the prepared work list
-// (coefficients, active counts and tile offsets already on the device) and returns the fastest.
+// Two stages on the prepared work list: every (register-budget variant, CTAs per SM) at the
+// precision's default sub-tiles per item, then every sub-tile count (1, 2, 4, 8) at the best of
+// those. Each candidate: one warm launch, the best of two timed ones.
 cudaError_t autotune_fwd(const DetSet& ds, int B, unsigned mask, const SampleCoef* coef, const int* nend,
-                         const long long* off, double* part, long long max_tiles, cudaStream_t st, TuneChoice* best) {
+                         const long long* off, long long* offi, double* part, long long max_tiles, cudaStream_t st,
+                         TuneChoice* best) {
   static const int kCtas[] = {2, 4, 8, 16};
+  static const int kSub[] = {1, 2, 4, 8};
   const int prec = mask_prec(mask);
+  const int P = ds.ndet * B;
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
   if (e != cudaSuccess) return e;
   if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
-  TuneChoice b{-1, 0, 1e30};
-  for (int v = 0; v < kFwdVariants && e == cudaSuccess; ++v) {
-    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
-      TuneChoice c{v, kCtas[ci], 0.0};
-      const int grid = grid_for(c, max_tiles);
-      if ((e = launch_loglike_fwd_variant(v, prec, ds, B, coef, nend, off, part, grid, st)) != cudaSuccess) break;  // warm
-      float best_ms = 1e30f;
-      for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
-        cudaEventRecord(e0, st);
-        e = launch_loglike_fwd_variant(v, prec, ds, B, coef, nend, off, part, grid, st);
-        cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        best_ms = std::min(best_ms, ms);
-      }
-      if (e == cudaSuccess && best_ms < b.ms) { b = c; b.ms = best_ms; }
+  auto time_one = [&](const TuneChoice& c, float* out_ms) -> cudaError_t {
+    const int grid = grid_for(c, max_tiles);
+    cudaError_t r = cudaSuccess;
+    if (c.subtiles > 1) r = launch_scan_tiles(nend, P, offi, c.subtiles * kTileBins, st);
+    if (r == cudaSuccess)
+      r = launch_loglike_fwd_variant(c.variant, prec, ds, B, coef, nend, off, offi, c.subtiles, part, grid, st);  // warm
+    float bm = 1e30f;
+    for (int k = 0; k < 2 && r == cudaSuccess; ++k) {
+      cudaEventRecord(e0, st);
+      r = launch_loglike_fwd_variant(c.variant, prec, ds, B, coef, nend, off, offi, c.subtiles, part, grid, st);
+      cudaEventRecord(e1, st);
+      if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+      bm = std::min(bm, ms);
     }
+    *out_ms = bm;
+    return r;
+  };
+  TuneChoice b{-1, 0, fwd_default_subtiles(prec), 1e30};
+  for (int v = 0; v < kFwdVariants && e == cudaSuccess; ++v)
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+      TuneChoice c{v, kCtas[ci], fwd_default_subtiles(prec), 0.0};
+      float ms = 0.f;
+      e = time_one(c, &ms);
+      if (e == cudaSuccess && ms < b.ms) { b = c; b.ms = ms; }
+    }
+  const int r0 = b.subtiles;
+  for (int si = 0; si < 4 && e == cudaSuccess; ++si) {
+    if (kSub[si] == r0) continue;
+    TuneChoice c = b;
+    c.subtiles = kSub[si];
+    float ms = 0.f;
+    e = time_one(c, &ms);
+    if (e == cudaSuccess && ms < b.ms) { b = c; b.ms = ms; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -218,10 +245,11 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
     return pe::set_error(PE_EINVAL, "pe_plan_create: theta and outputs must be device pointers");
   const size_t P = (size_t)ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kTileBins);
   const size_t o_nend = a256((size_t)B * sizeof(pe::SampleCoef));
   const size_t o_off = a256(o_nend + P * sizeof(int));
-  const size_t o_part = a256(o_off + (P + 1) * sizeof(long long));
+  const size_t o_offi = a256(o_off + (P + 1) * sizeof(long long));
+  const size_t o_part = a256(o_offi + (P + 1) * sizeof(long long));
   const size_t bytes = o_part + (size_t)max_tiles * 6 * sizeof(double);
   pe_plan_s* pl = new (std::nothrow) pe_plan_s();
   if (!pl) return pe::set_error(PE_ENOMEM, "pe_plan_create: host allocation failed");
@@ -237,15 +265,16 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
   pe::SampleCoef* coef = reinterpret_cast<pe::SampleCoef*>(sc);
   int* nend = reinterpret_cast<int*>(sc + o_nend);
   long long* off = reinterpret_cast<long long*>(sc + o_off);
+  long long* offi = reinterpret_cast<long long*>(sc + o_offi);
   double* part = reinterpret_cast<double*>(sc + o_part);
   cudaStream_t cs = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  pl->choice = pe::default_choice();
+  pl->choice = pe::default_choice(pe::mask_prec(mode_mask));
   if (e == cudaSuccess && !pe::lookup_tuned(ds, B, mode_mask, &pl->choice) && autotune) {
     e = pe::launch_prep(theta_dev, B, mode_mask, ds, coef, nend, nullptr, cs);
-    if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), cs);
+    if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::kTileBins, cs);
     pe::TuneChoice best;
-    if (e == cudaSuccess) e = pe::autotune_fwd(ds, B, mode_mask, coef, nend, off, part, max_tiles, cs, &best);
+    if (e == cudaSuccess) e = pe::autotune_fwd(ds, B, mode_mask, coef, nend, off, offi, part, max_tiles, cs, &best);
     if (e == cudaSuccess) {
       pl->choice = best;
       pe::store_tuned(ds, B, mode_mask, best);
@@ -254,10 +283,10 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t e1 = pe::launch_prep(theta_dev, B, mode_mask, ds, coef, nend, out_status_dev, cs);
-    if (e1 == cudaSuccess) e1 = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), cs);
+    if (e1 == cudaSuccess) e1 = pe::launch_fwd_offsets(nend, (int)P, off, offi, pl->choice.subtiles, cs);
     if (e1 == cudaSuccess)
-      e1 = pe::launch_loglike_fwd_variant(pl->choice.variant, pe::mask_prec(mode_mask), ds, B, coef, nend, off, part,
-                                          pe::grid_for(pl->choice, max_tiles), cs);
+      e1 = pe::launch_loglike_fwd_variant(pl->choice.variant, pe::mask_prec(mode_mask), ds, B, coef, nend, off, offi,
+                                          pl->choice.subtiles, part, pe::grid_for(pl->choice, max_tiles), cs);
     if (e1 == cudaSuccess) e1 = pe::launch_reduce(ds, B, off, part, coef, out_logl_dev, out_dhhh_dev, cs);
     e = cudaStreamEndCapture(cs, &pl->graph);
     if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
@@ -289,16 +318,31 @@ pe_status pe_plan_launch(pe_plan plan, void* stream) {
   return PE_OK;
 }
 
-pe_status pe_plan_info(pe_plan plan, int* fwd_variant, int* ctas_per_sm, double* tuned_ms) {
+pe_status pe_plan_info(pe_plan plan, int* fwd_variant, int* ctas_per_sm, int* subtiles, double* tuned_ms) {
   if (plan == nullptr) return pe::set_error(PE_EINVAL, "pe_plan_info: plan is NULL");
   if (fwd_variant) *fwd_variant = plan->choice.variant;
   if (ctas_per_sm) *ctas_per_sm = plan->choice.ctas_per_sm;
+  if (subtiles) *subtiles = plan->choice.subtiles;
   if (tuned_ms) *tuned_ms = plan->choice.ms;
   return PE_OK;
 }
 
+pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_mask, int fwd_variant, int ctas_per_sm,
+                      int subtiles) {
+  pe::DetSet ds;
+  pe_status s0 = pe::detset_from_handles(dets, ndet, &ds);
+  if (s0 != PE_OK) return s0;
+  if (B < 1 || B > (1 << 20)) return pe::set_error(PE_EINVAL, "pe_tune_set: B outside [1, 2^20]");
+  if (!pe::fwd_mask_ok(mode_mask)) return pe::set_error(PE_EINVAL, "pe_tune_set: bad mode mask");
+  if (fwd_variant < 0 || fwd_variant >= pe::kFwdVariants || ctas_per_sm < 1 || ctas_per_sm > 64 ||
+      (subtiles != 1 && subtiles != 2 && subtiles != 4 && subtiles != 8))
+    return pe::set_error(PE_EINVAL, "pe_tune_set: choice out of range");
+  pe::store_tuned(ds, B, mode_mask, pe::TuneChoice{fwd_variant, ctas_per_sm, subtiles, 0.0});
+  return PE_OK;
+}
+
 pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev, int B, unsigned mode_mask,
-                      int* out_variant, int* out_ctas_per_sm, double* out_ms) {
+                      int* out_variant, int* out_ctas_per_sm, int* out_subtiles, double* out_ms) {
   pe::DetSet ds;
   pe_status s0 = pe::detset_from_handles(dets, ndet, &ds);
   if (s0 != PE_OK) return s0;
@@ -307,10 +351,11 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
   if (!dev_ptr(theta_dev)) return pe::set_error(PE_EINVAL, "pe_autotune: theta must be a device pointer");
   const size_t P = (size_t)ndet * B;
   long long max_tiles = 0;
-  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::fwd_tile_bins(pe::mask_prec(mode_mask)));
+  for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kTileBins);
   const size_t o_nend = a256((size_t)B * sizeof(pe::SampleCoef));
   const size_t o_off = a256(o_nend + P * sizeof(int));
-  const size_t o_part = a256(o_off + (P + 1) * sizeof(long long));
+  const size_t o_offi = a256(o_off + (P + 1) * sizeof(long long));
+  const size_t o_part = a256(o_offi + (P + 1) * sizeof(long long));
   const size_t bytes = o_part + (size_t)max_tiles * 6 * sizeof(double);
   void* scratch = nullptr;
   if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
@@ -321,13 +366,14 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
   pe::SampleCoef* coef = reinterpret_cast<pe::SampleCoef*>(sc);
   int* nend = reinterpret_cast<int*>(sc + o_nend);
   long long* off = reinterpret_cast<long long*>(sc + o_off);
+  long long* offi = reinterpret_cast<long long*>(sc + o_offi);
   double* part = reinterpret_cast<double*>(sc + o_part);
   cudaStream_t cs = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  pe::TuneChoice best = pe::default_choice();
+  pe::TuneChoice best = pe::default_choice(pe::mask_prec(mode_mask));
   if (e == cudaSuccess) e = pe::launch_prep(theta_dev, B, mode_mask, ds, coef, nend, nullptr, cs);
-  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::fwd_tile_bins(pe::mask_prec(mode_mask)), cs);
-  if (e == cudaSuccess) e = pe::autotune_fwd(ds, B, mode_mask, coef, nend, off, part, max_tiles, cs, &best);
+  if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::kTileBins, cs);
+  if (e == cudaSuccess) e = pe::autotune_fwd(ds, B, mode_mask, coef, nend, off, offi, part, max_tiles, cs, &best);
   if (cs) cudaStreamDestroy(cs);
   cudaFree(scratch);
   if (e != cudaSuccess) {
@@ -339,6 +385,7 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
   pe::store_tuned(ds, B, mode_mask, best);
   if (out_variant) *out_variant = best.variant;
   if (out_ctas_per_sm) *out_ctas_per_sm = best.ctas_per_sm;
+  if (out_subtiles) *out_subtiles = best.subtiles;
   if (out_ms) *out_ms = best.ms;
   return PE_OK;
 }

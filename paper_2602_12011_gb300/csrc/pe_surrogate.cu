@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
                                                        const double* __restrict__ hs,
                                                        const int* __restrict__ nend, const long long* __restrict__ off,
                                                        double* part, int mode) {
-  __shared__ double sh[6][kTileBins / 32];
+  __shared__ double red[6][kTileBins + kRedPad];
   __shared__ double pc[kProj];
   __shared__ double ihs[kNModes];
   __shared__ double2 stab[kSinTab];
@@ -446,19 +446,8 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
         }
       }
     }
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-      for (int i = 0; i < 6; ++i) sh[i][wid] = v[i];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-      double a = sh[threadIdx.x][0];
-      for (int w = 1; w < kTileBins / 32; ++w) a += sh[threadIdx.x][w];
-      part[t * 6 + threadIdx.x] = a;
-    }
+    double a;
+    if (block_sum6(v, [](double x, double y) { return x + y; }, red, &a)) part[t * 6 + threadIdx.x] = a;
   }
 }
 

@@ -71,6 +71,43 @@ def test_autotune_changes_no_result(oracle_mod, Lb):
     assert os.path.exists(os.environ["PE_TUNE_CACHE"])
 
 
+@pytest.mark.parametrize("mix", [False, True], ids=["fp64", "mixed"])
+def test_every_tuning_choice_gives_the_same_bits(oracle_mod, Lb, mix):
+    """Work items of 1, 2, 4 and 8 sub-tiles, each register-budget variant and two grid sizes,
+    recorded with pe_tune_set: the direct call and a plan give the same bits for every choice, on
+    a detector network with uneven grids and a ragged tail."""
+    import torch
+    dets = []
+    for det, T in ((W.LISA, 2.0 ** 16), (W.TAIJI, 2.0 ** 15), (W.TIANQIN, 2.0 ** 14)):
+        k0, nb = W.grid(T)
+        d = Lb.Detector(det, T, k0, nb)
+        d.inject(W.theta_injection(2.0 ** 14), W.MODE_ALL, W.normals(nb, 5))
+        dets.append(d)
+    B = 37
+    m = W.MODE_ALL | (Lb.PE_PREC_MIXED if mix else 0)
+    th = W.draw_prior(B, 21, 2.0 ** 14)
+    hs = [d.handle for d in dets]
+    ref = None
+    for r in (1, 2, 4, 8):
+        for v, c in ((0, 16), (1, 2), (2, 8)):
+            Lb.pe_tune_set(hs, B, m, v, c, r)
+            out = Lb.loglike(dets, th, m, dhhh=True)
+            tt = torch.tensor(th, device="cuda")
+            pl = Lb.Plan(dets, B, m, theta=tt, dhhh=True, autotune=False)
+            info = pl.info()
+            assert (info["fwd_variant"], info["ctas_per_sm"], info["subtiles"]) == (v, c, r)
+            pl.launch()
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = out
+            assert np.array_equal(out["logl"], ref["logl"]) and np.array_equal(out["dhhh"], ref["dhhh"])
+            assert np.array_equal(pl.logl.cpu().numpy(), ref["logl"])
+            pl.close()
+    with pytest.raises(Lb.PeError) as e:
+        Lb.pe_tune_set(hs, B, m, 0, 8, 3)
+    assert e.value.status == Lb.PE_EINVAL
+
+
 def test_network_full_size_plan_sampled(oracle_mod, Lb):
     """Detector network at full spans (209,296 + 104,648 + 52,324 bins), B = 4096 in one graph
     launch; a spread of samples is checked against the oracle."""
