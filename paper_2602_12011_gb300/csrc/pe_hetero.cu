@@ -38,7 +38,7 @@ struct HetDev {
   DetDev det;
   const int* edge;       // [ne] fine-bin indices
   const double* fe;      // [ne] edge frequencies
-  const double2* h0e;    // [ne][5][3] reference brackets at the edges
+  const double2* ih0e;   // [ne][5][3] inverses 1/h0 of the reference brackets at the edges (0 where h0 = 0)
   const int* src;        // [ne][5][3] edge whose ratio applies (carry-forward), -1 for none
   const double2* A;      // [ne-1][5][3][2]
   const double2* Bs;     // [ne-1][kPairs][3][3]
@@ -53,10 +53,6 @@ struct HetSet {
   int nemax;   // largest ne of the set (rows of the kernel's ratio table)
 };
 
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  const double den = b.x * b.x + b.y * b.y;
-  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
-}
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
 // Per-mode brackets of one sample at bin b (zero for inactive modes or bins past a mode's end).
@@ -120,6 +116,15 @@ __global__ void k_gather_edges(const double2* hb, int K, const int* edge, int ne
   if (j >= ne * kNModes * 3) return;
   const int i = j / (kNModes * 3), mc = j % (kNModes * 3);
   h0e[j] = hb[(size_t)mc * K + edge[i]];
+}
+
+// h0e -> 1/h0e in place (0 where h0e = 0: such an edge is never a ratio source)
+__global__ void k_invert_edges(double2* h0e, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double2 h = h0e[j];
+  const double den = h.x * h.x + h.y * h.y;
+  h0e[j] = den != 0.0 ? make_double2(h.x / den, -h.y / den) : make_double2(0.0, 0.0);
 }
 
 // Summary data: one thread per (coarse bin, quantity); a sequential sum over the bin's fine bins.
@@ -219,7 +224,7 @@ __device__ __forceinline__ cdf mul_conj(const cdf& a, const cdf& b) {
 // MIX: the signal at the edges by the mixed-precision unit, the ratios kept as double words and
 // the contraction in double words (Aw, Bw); the sums across bins and the block reduction stay
 // FP64. An edge with a ratio of kHetDwRatioMax or more keeps all its ratios in FP64 (flag byte
-// per edge after the ratios), and every bin that reads it takes the FP64 contraction.
+// per edge after the ratios), and every (bin, channel) that reads it takes the FP64 contraction.
 template <bool MIX>
 __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, const SampleCoef* __restrict__ coef,
                                                            double* logl, double* dhhh) {
@@ -255,27 +260,30 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
         mode_brackets_mixed(D, S, H.edge[e], H.mask, o, stabw, pcw);
       else
         mode_brackets(D, S, H.edge[e], H.mask, o, stab, pc);
+      // ratios in place of the brackets; in the mixed kernel, flag the edge if one of them is out
+      // of the double words' range (also for inf and NaN)
       bool wide = false;
-      if constexpr (MIX) {
-        for (int md = 0; md < kNModes; ++md)
-          for (int c = 0; c < 3; ++c) {
-            const int j = (e * kNModes + md) * 3 + c;
-            if (H.src[j] != e) continue;
-            const double2 r = cdiv(o[md][c], H.h0e[j]);
-            wide |= !(fmax(fabs(r.x), fabs(r.y)) < kHetDwRatioMax);   // also true for inf and NaN
-          }
-        wflag[e] = wide ? 1 : 0;
-      }
+#pragma unroll
       for (int md = 0; md < kNModes; ++md)
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           const int j = (e * kNModes + md) * 3 + c;
           if (H.src[j] != e) continue;
-          const double2 r = cdiv(o[md][c], H.h0e[j]);
+          o[md][c] = cmul(o[md][c], H.ih0e[j]);
+          if constexpr (MIX) wide |= !(fmax(fabs(o[md][c].x), fabs(o[md][c].y)) < kHetDwRatioMax);
+        }
+      if constexpr (MIX) wflag[e] = wide ? 1 : 0;
+#pragma unroll
+      for (int md = 0; md < kNModes; ++md)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int j = (e * kNModes + md) * 3 + c;
+          if (H.src[j] != e) continue;
           if (MIX && !wide) {
-            const float2 re = to_dw(r.x), im = to_dw(r.y);
+            const float2 re = to_dw(o[md][c].x), im = to_dw(o[md][c].y);
             reinterpret_cast<float4*>(rsh)[j] = make_float4(re.x, re.y, im.x, im.y);
           } else {
-            rsh[j] = r;
+            rsh[j] = o[md][c];
           }
         }
     }
@@ -285,14 +293,21 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
       const float4* rw = reinterpret_cast<const float4*>(rsh);
       const cdf zc = {df_make(0.f, 0.f), df_make(0.f, 0.f)};
       for (int b = threadIdx.x; b < H.ne - 1; b += blockDim.x) {
-        bool wide = false;
-        for (int j = 0; j < kNModes * 3; ++j) {
-          const int s0 = H.src[b * kNModes * 3 + j], s1 = H.src[(b + 1) * kNModes * 3 + j];
-          wide |= (s0 >= 0 && wflag[s0]) || (s1 >= 0 && wflag[s1]);
-        }
-        if (wide) {
+        const df idf = to_dw(1.0 / (H.fe[b + 1] - H.fe[b]));
 #pragma unroll 1
-          for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 3; ++c) {
+          cdf r0[kNModes], r1[kNModes];
+          bool wide = false;
+#pragma unroll
+          for (int md = 0; md < kNModes; ++md) {
+            const int s0 = H.src[(b * kNModes + md) * 3 + c], s1 = H.src[((b + 1) * kNModes + md) * 3 + c];
+            wide |= (s0 >= 0 && wflag[s0]) || (s1 >= 0 && wflag[s1]);
+            const cdf ra = s0 >= 0 ? unpack4(rw[(s0 * kNModes + md) * 3 + c]) : zc;
+            const cdf rb = s1 >= 0 ? unpack4(rw[(s1 * kNModes + md) * 3 + c]) : zc;
+            r0[md] = ra;
+            r1[md] = cdf{dfl_mul(dfl_sub(rb.re, ra.re), idf), dfl_mul(dfl_sub(rb.im, ra.im), idf)};
+          }
+          if (wide) {   // an edge of this bin keeps FP64 ratios (the double words above are unused)
             auto ld = [&](int e, int md) -> double2 {
               const int j = (e * kNModes + md) * 3 + c;
               if (wflag[e]) return rsh[j];
@@ -303,20 +318,7 @@ __global__ void __launch_bounds__(kTileBins) k_het_loglike(HetSet hs, int B, con
             het_bin_fp64(H, b, c, ld, dh, hh);
             v[c] += dh;
             v[3 + c] += hh;
-          }
-          continue;
-        }
-        const df idf = to_dw(1.0 / (H.fe[b + 1] - H.fe[b]));
-#pragma unroll 1
-        for (int c = 0; c < 3; ++c) {
-          cdf r0[kNModes], r1[kNModes];
-#pragma unroll
-          for (int md = 0; md < kNModes; ++md) {
-            const int s0 = H.src[(b * kNModes + md) * 3 + c], s1 = H.src[((b + 1) * kNModes + md) * 3 + c];
-            const cdf ra = s0 >= 0 ? unpack4(rw[(s0 * kNModes + md) * 3 + c]) : zc;
-            const cdf rb = s1 >= 0 ? unpack4(rw[(s1 * kNModes + md) * 3 + c]) : zc;
-            r0[md] = ra;
-            r1[md] = cdf{dfl_mul(dfl_sub(rb.re, ra.re), idf), dfl_mul(dfl_sub(rb.im, ra.im), idf)};
+            continue;
           }
           df dh = df_make(0.f, 0.f), hh = df_make(0.f, 0.f);
 #pragma unroll
@@ -548,6 +550,10 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
     }
     e = cudaMemcpy(d_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess) {   // the per-sample kernel multiplies by the inverses (no division per ratio)
+    pe::k_invert_edges<<<(ne * 15 + 127) / 128, 128>>>(d_h0e, ne * 15);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     const long long n = (long long)nb * (30 + pe::kPairs * 9);
     pe::k_het_summary<<<(unsigned)((n + 127) / 128), 128>>>(D, d_edge, d_fe, ne, hb, K, d_A, d_B);
@@ -575,7 +581,7 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
   h->dev.det = D;
   h->dev.edge = d_edge;
   h->dev.fe = d_fe;
-  h->dev.h0e = d_h0e;
+  h->dev.ih0e = d_h0e;
   h->dev.src = d_src;
   h->dev.A = d_A;
   h->dev.Bs = d_B;
