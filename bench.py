@@ -38,14 +38,14 @@ MSUN_S = 4.925490947641267e-6
 #   fp64_inst   every FP64-pipe instruction (DFMA, DMUL, DADD, DSETP, F2F, FRND)
 #   fp32_inst   FFMA + FMUL + FADD (the double-word arithmetic of the mixed path)
 UNIT_COUNTS = {
-    "fp64": {"fp64_flops": 408.9, "fp64_inst": 272.5, "fp32_inst": 0.2},
+    "fp64": {"fp64_flops": 399.2, "fp64_inst": 257.9, "fp32_inst": 0.2},
     "mixed": {"fp64_flops": 57.7, "fp64_inst": 44.1, "fp32_inst": 2256.8},
     # FP32 path: fp64_inst counts the FRND and F2F of CUDA's FP32 sincospif/sinf and conversions
-    "fp32": {"fp64_flops": 0.3, "fp64_inst": 10.1, "fp32_inst": 355.8},
+    "fp32": {"fp64_flops": 0.25, "fp64_inst": 9.2, "fp32_inst": 354.4},
 }
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum
 # (profiles/k_loglike_fwd_dram_lisa_hm_T2^22_B1024.md): the per-bin tables, read once per launch
-TRAFFIC = {"fp64": 31.33e6, "mixed": 38.18e6 + 0.85e6, "fp32": None}
+TRAFFIC = {"fp64": 36.47e6 + 0.01e6, "mixed": 38.15e6 + 0.60e6, "fp32": None}
 
 
 def parse():

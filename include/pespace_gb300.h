@@ -157,7 +157,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
  * no allocating routine.
  *   theta, out_logl and the optional out_dhhh / out_status must be DEVICE pointers (host buffers
  *   would need staging memory); other arguments and layouts are as for pe_loglike_batch.
- *   Size limit: coefficients (1,024 bytes per sample) plus one 48-byte partial per 128-bin
+ *   Size limit: coefficients (1,136 bytes per sample) plus one 48-byte partial per 128-bin
  *   sub-tile of every (detector, sample) pair must fit in 32 MiB -- about 400 samples on one
  *   2^22 s grid (209,296 bins), about 1,500 on a 2^20 s grid, in every precision. Larger batches
  *   return PE_EINVAL with the needed size in pe_last_error(); split them. The work items take the

@@ -30,6 +30,7 @@ struct pe_detector_s {
   double* fm13;
   double* lnf3;
   double* fm76;
+  double* fpow;        // [3][nb] f^(-5/6), f^(-1/2), f^(-5/3)
   double2* sca;
   double2* z;
   double2* dg;
@@ -187,6 +188,7 @@ void fill_dev(pe_detector_s* d) {
   }
   D.Rw = host_dw(D.R);
   D.f = d->f; D.f13 = d->f13; D.fm13 = d->fm13; D.lnf3 = d->lnf3; D.fm76 = d->fm76;
+  D.fm56 = d->fpow; D.fm12 = d->fpow + d->nb; D.fm53 = d->fpow + 2 * (size_t)d->nb;
   D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev; D.sct = d->sct;
   D.sctw = d->sctw; D.fw = d->fw; D.aw = d->aw; D.atw = d->atw; D.saw = d->saw; D.caw = d->caw;
   D.zw = d->zw; D.dgw = d->dgw; D.ggw = d->ggw; D.f13w = d->f13w; D.fm76w = d->fm76w;
@@ -260,10 +262,10 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->nb = (int)nbins;
   const size_t nb = (size_t)nbins;
   // double2: sincos table + sca, z (2 nb) + dg (3 nb); float4: double-word sincos table, zw (nb),
-  // dgw (3 nb); doubles: f, f13, fm13, lnf3, fm76 (5 nb) + gg (3 nb) + psd_model (3 nb) + dd (3,
+  // dgw (3 nb); doubles: f, f13, fm13, lnf3, fm76 (5 nb) + fpow (3 nb) + gg (3 nb) + psd_model (3 nb) + dd (3,
   // padded); float2: fw, aw, atw, saw, caw, f13w, fm76w (7 nb) + ggw (3 nb) + scaf, zf (2 nb) +
   // dgf (3 nb); float: five FP32 grid tables (5 nb) + ggf (3 nb)
-  const size_t n_d = 11 * nb + 8, n_d2 = 5 * nb + pe::kSinTab, n_f4 = pe::kSinTab + 4 * nb, n_f2 = 15 * nb,
+  const size_t n_d = 14 * nb + 8, n_d2 = 5 * nb + pe::kSinTab, n_f4 = pe::kSinTab + 4 * nb, n_f2 = 15 * nb,
                n_f = 8 * nb;
   const size_t bytes = n_d2 * sizeof(double2) + n_f4 * sizeof(float4) + n_d * sizeof(double) +
                        n_f2 * sizeof(float2) + n_f * sizeof(float);
@@ -284,6 +286,7 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   d->fm13 = p; p += nb;
   d->lnf3 = p; p += nb;
   d->fm76 = p; p += nb;
+  d->fpow = p; p += 3 * nb;
   d->gg = p; p += 3 * nb;
   d->psd_model = p; p += 3 * nb;
   d->dd_dev = p; p += 8;
@@ -305,8 +308,8 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
   fill_dev(d);
   const double L = det_arm_s(*cfg);
   if ((e = pe::launch_sincos_table(d->sct, 0)) != cudaSuccess ||
-      (e = pe::launch_grid_tables(T_obs, k0, d->nb, L, d->f, d->f13, d->fm13, d->lnf3, d->fm76, d->sca, d->z, 0)) !=
-          cudaSuccess ||
+      (e = pe::launch_grid_tables(T_obs, k0, d->nb, L, d->f, d->f13, d->fm13, d->lnf3, d->fm76, d->fpow, d->sca,
+                                  d->z, 0)) != cudaSuccess ||
       (e = pe::launch_psd_model(d->f, d->nb, L, cfg->oms_m_rtHz, cfg->acc_ms2_rtHz, cfg->psd_shaping, cfg->tdi_gen,
                                 d->psd_model, 0)) != cudaSuccess ||
       (e = pe::launch_dw_tables(d->f, d->f13, d->fm76, d->sca, d->z, d->sct, d->nb, L, d->fw, d->aw, d->atw, d->saw,

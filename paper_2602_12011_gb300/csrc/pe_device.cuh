@@ -30,10 +30,14 @@ __device__ __forceinline__ void sincos_turns(double x, const double2* __restrict
   const double sx = __dadd_rn(x, kRound);
   const double d = __dsub_rn(x, __dsub_rn(sx, kRound));
   const double2 cs = tab[__double2loint(sx) & (kSinTab - 1)];
-  const double t = d * (2.0 * kPi);
-  const double t2 = t * t;
-  const double st = fma(t, t2 * fma(t2, 1.0 / 120.0, -1.0 / 6.0), t);
-  const double ct = fma(t2, fma(t2, 1.0 / 24.0, -0.5), 1.0);
+  // sin(2 pi d) = d (c1 + u (c3 + u c5)) and cos(2 pi d) = 1 + u (c2 + u c4), u = d^2, with
+  // c_n = (-1)^floor(n/2) (2 pi)^n / n! (correctly rounded): the Taylor series in t = 2 pi d with
+  // 2 pi folded into the coefficients
+  constexpr double kS1 = 6.283185307179586, kS3 = -41.34170224039976, kS5 = 81.60524927607506;
+  constexpr double kC2 = -19.739208802178716, kC4 = 64.9393940226683;
+  const double u = d * d;
+  const double st = d * fma(u, fma(u, kS5, kS3), kS1);
+  const double ct = fma(u, fma(u, kC4, kC2), 1.0);
   *s = fma(cs.y, ct, cs.x * st);
   *c = fma(cs.x, ct, -(cs.y * st));
 }
@@ -162,6 +166,9 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
     C.icm = 1.0 / C.cm;
     C.lncm = lncm1 - kLnM3[m];
     C.amp = 2.0 * pi * M * M / D * sqrt(eta / (3.0 * m)) * hmag * (C.icm * C.icm * C.icm / sqrt(C.cm));
+    const T icm2 = C.icm * C.icm;
+    C.icm5 = icm2 * icm2 * C.icm;
+    C.ampp = p == 0 ? C.amp : (p == 1 ? C.amp * C.cm : C.amp * C.cm * C.cm);
     const T ph = m * phic / (2.0 * pi) + (0.125 + argt);
     C.ph0 = ph - rint(ph);
     C.mfac = 0.0 * q + m / (4.0 * pi);
@@ -171,6 +178,7 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
     const double sgn = (l % 2) ? -1.0 : 1.0;
     C.Pp = 0.5 * (yp + sgn * yn);
     C.Pc = 0.5 * (sgn * yn - yp);
+    C.Pc2 = sgn * yn - yp;
     C.fend = double(m) * Fisco;
     C.ftap = 0.9 * double(m) * Fisco;
     C.Ppw = to_dw(val(C.Pp));
@@ -244,9 +252,8 @@ __device__ __forceinline__ double sinc_small(double u) {
 constexpr double kSincPolyA = 0.5;   // bins with a below this take a polynomial
 constexpr double kSincPolyA12 = 0.2;
 constexpr double kSincPolyA8 = 0.05;
-template <int DEG>   // highest power of x kept: 8, 6 or 4
-__device__ __forceinline__ double sinc_poly_n(double u) {
-  const double x = u * u;
+template <int DEG>   // highest power of x kept: 8, 6 or 4; argument x = u^2
+__device__ __forceinline__ double sinc_poly_x(double x) {
   double p = DEG >= 8 ? 1.0 / 355687428096000.0 : (DEG >= 6 ? 1.0 / 6227020800.0 : 1.0 / 362880.0);
   if (DEG >= 8) {
     p = fma(p, x, -1.0 / 1307674368000.0);        // 1/15!
@@ -261,6 +268,8 @@ __device__ __forceinline__ double sinc_poly_n(double u) {
   p = fma(p, x, -1.0 / 6.0);                      // 1/3!
   return fma(p, x, 1.0);
 }
+template <int DEG>
+__device__ __forceinline__ double sinc_poly_n(double u) { return sinc_poly_x<DEG>(u * u); }
 __device__ __forceinline__ double sinc_poly(double u) { return sinc_poly_n<8>(u); }
 // sinc(u) and d sinc/du = u sum_{k>=1} 2k (-1)^k u^(2k-2) / (2k+1)! through the same order as
 // sinc_poly_n<DEG>
@@ -290,8 +299,10 @@ __device__ __forceinline__ void sinc_poly_d(double u, double* sv, double* dv) { 
 //                       n'_l = delta_r - delta_s, link l = (r, s) = (0,1), (1,2), (2,0);
 //   pc[45 + 5 i + m]:   k.delta_i, spacecraft i = 0, 1 (the third-spacecraft phases).
 // Since (k, p, q) is orthonormal, |n'|^2 = (k.n')^2 + (p.n')^2 + (q.n')^2.
-constexpr int kProj = 55;
+//   pc[55], pc[56]:     R k_x, R k_y (the centre's Doppler term k.x_c = R (k_x cos alpha + k_y sin alpha)).
+constexpr int kProj = 57;
 __device__ __forceinline__ double proj_coef(const DetDev& D, const SampleCoef& S, int i) {
+  if (i >= 55) return D.R * S.k[i - 55];
   const int m = i % 5;
   if (i < 45) {
     const int l = i / 15, v = (i / 5) % 3, r = l, s = (l + 1) % 3;
@@ -348,6 +359,9 @@ __device__ __forceinline__ void xyz_final(const XYZAcc& a, double2 z, double2 x[
 struct BinIn {
   double f, f13, fm13, lnf3, fm76, invf;
   double a, sa, ca;    // a = pi f L
+  double a2;           // a^2
+  double hf;           // f / 2
+  int b;               // bin index (for the tables read per unit)
   double aturn;        // a / (2 pi) = f L / 2
   double2 z;           // e^{-2 i a}
   double frc;          // frac(f t_c) computed exactly (turns)
@@ -367,10 +381,8 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
                                          const ModeCoef* C2 = nullptr) {
   // --- waveform and time-frequency map (rows A2, A3)
   const double v = C.cm * B.f13;
-  const double iv = C.icm * B.fm13;
   const double lnv = C.lncm + B.lnf3;
-  double iv5 = iv * iv;
-  iv5 = iv5 * iv5 * iv;
+  const double iv5 = C.icm5 * D.fm53[B.b];   // v^-5 = cm^-5 f^(-5/3)
   double poly = S.P[7];
   double dpol = S.Pd[7];
 #pragma unroll
@@ -378,38 +390,37 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     poly = fma(poly, v, S.P[k]);
     dpol = fma(dpol, v, S.Pd[k]);
   }
-  const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
-  const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));  // v dPsi_PN/dv
-  const double tf = fma(C.tffac * B.invf, dv, S.tc);                   // Eq. eq_tf
-  double w = 1.0;
+  const double q56 = fma(S.Q6, v, S.Q5);
+  const double psi_pn = fma(iv5, poly, lnv * q56);
+  const double dv = fma(iv5, dpol, fma(S.Q6 * v, lnv, q56));   // v dPsi_PN/dv = v^-5 sum_k (k-5) P_k v^k + Q5 + Q6 v (1 + ln v)
+  const double tf = fma(C.tffac * B.invf, dv, S.tc);            // Eq. eq_tf
+  // amp v^p f^(-7/6) = (amp cm^p) f^(-7/6 + p/3), times the Planck taper inside it
+  double amp = C.ampp * (C.p == 0 ? B.fm76 : (C.p == 1 ? D.fm56[B.b] : D.fm12[B.b]));
   if (B.f > C.ftap) {
     const double span = C.fend - C.ftap;
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
-    w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
+    amp *= (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
   }
-  double amp = C.amp * B.fm76 * w;
-  if (C.p >= 1) amp *= v;
-  if (C.p >= 2) amp *= v;
   // --- orbit at t_f (row A4): centre angle and the offsets' basis
   double co, so, ob[4];
   orbit_basis(D, tf, tab, &co, &so, ob);
-  const double kxc = D.R * (S.k[0] * co + S.k[1] * so);
+  const double kxc = fma(pc[55], co, pc[56] * so);   // k.x_c
   const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
   const double phr = ph - rint(ph);
-  // polarisation weights times the amplitude; a paired second mode makes them complex:
-  // Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
-  double2 Ap = make_double2(amp * C.Pp, 0.0), Ac = make_double2(amp * C.Pc, 0.0);
+  // polarisation weights times the amplitude (x weight doubled, see Fx below); a paired second
+  // mode makes them complex: Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
+  double2 Ap = make_double2(amp * C.Pp, 0.0), Ac = make_double2(amp * C.Pc2, 0.0);
   if (C2) {
     const double v2 = v * v;
     const double kr = S.k32.x * v2, ki = S.k32.y * v2;
     Ap = make_double2(amp * fma(kr, C2->Pp, C.Pp), amp * (ki * C2->Pp));
-    Ac = make_double2(amp * fma(kr, C2->Pc, C.Pc), amp * (ki * C2->Pc));
+    Ac = make_double2(amp * fma(kr, C2->Pc2, C.Pc2), amp * (ki * C2->Pc2));
   }
   // mode phase times the third spacecraft's phase e^{i pi f k.delta_t}, one sincos per spacecraft;
   // the offsets sum to zero, so delta_2's phase is minus the other two
   double2 E[3];
   {
-    const double e0 = 0.5 * B.f * dot5(pc + 45, ob), e1 = 0.5 * B.f * dot5(pc + 50, ob);
+    const double e0 = B.hf * dot5(pc + 45, ob), e1 = B.hf * dot5(pc + 50, ob);
     sincos_turns_r(phr + e0, tab, &E[0].y, &E[0].x);
     sincos_turns_r(phr + e1, tab, &E[1].y, &E[1].x);
     sincos_turns_r(phr - (e0 + e1), tab, &E[2].y, &E[2].x);
@@ -436,24 +447,30 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     const double inv = rsqrt(fma(knr[l], knr[l], fma(npr[l], npr[l], nqr[l] * nqr[l])));
     const double kn = knr[l] * inv;
     const double np = npr[l] * inv, nq = nqr[l] * inv;
-    const double Fp = np * np - nq * nq, Fc = 2.0 * np * nq;
-    const double2 gam = C2 ? make_double2(fma(Ap.x, Fp, -Ac.y * Fc), fma(Ap.y, Fp, Ac.x * Fc))
-                           : make_double2(Ap.x * Fp, Ac.x * Fc);
+    // F+ = (n.p)^2 - (n.q)^2, Fx = 2 (n.p)(n.q); the 2 is in Ac (built from 2 Pc)
+    const double Fp = np * np - nq * nq, Fch = np * nq;
+    const double2 gam = C2 ? make_double2(fma(Ap.x, Fp, -Ac.y * Fch), fma(Ap.y, Fp, Ac.x * Fch))
+                           : make_double2(Ap.x * Fp, Ac.x * Fch);
     G[l] = cmul(gam, E[t]);
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (most bins of a massive-binary
     // signal), else from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
-    const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
+    // below a = kSincPolyA: u1^2 = a^2 (1 - kn)^2 = a^2 + a^2 kn (kn - 2) and u2^2 = a^2 + a^2 kn (kn + 2);
+    // where u1 or u2 is small the cancellation error is ~ulp(a^2), far below what sinc resolves
     double sm, spl;
     if (B.a < kSincPolyA8) {
-      sm = sinc_poly_n<4>(u1);
-      spl = sinc_poly_n<4>(u2);
+      const double a2kn = B.a2 * kn;
+      sm = sinc_poly_x<4>(fma(a2kn, kn - 2.0, B.a2));
+      spl = sinc_poly_x<4>(fma(a2kn, kn + 2.0, B.a2));
     } else if (B.a < kSincPolyA12) {
-      sm = sinc_poly_n<6>(u1);
-      spl = sinc_poly_n<6>(u2);
+      const double a2kn = B.a2 * kn;
+      sm = sinc_poly_x<6>(fma(a2kn, kn - 2.0, B.a2));
+      spl = sinc_poly_x<6>(fma(a2kn, kn + 2.0, B.a2));
     } else if (B.a < kSincPolyA) {
-      sm = sinc_poly(u1);
-      spl = sinc_poly(u2);
+      const double a2kn = B.a2 * kn;
+      sm = sinc_poly_x<8>(fma(a2kn, kn - 2.0, B.a2));
+      spl = sinc_poly_x<8>(fma(a2kn, kn + 2.0, B.a2));
     } else {
+      const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
       double sak, cak;
       sincos_turns(B.aturn * kn, tab, &sak, &cak);
       const double s1 = B.sa * cak - B.ca * sak, s2 = B.sa * cak + B.ca * sak;
@@ -489,6 +506,9 @@ __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinI
   B.fm76 = D.fm76[b];
   B.invf = B.fm13 * B.fm13 * B.fm13;
   B.a = kPi * B.f * D.L;
+  B.a2 = B.a * B.a;
+  B.hf = 0.5 * B.f;
+  B.b = b;
   B.aturn = 0.5 * B.f * D.L;
   const double2 sc = D.sca[b];
   B.sa = sc.x; B.ca = sc.y;

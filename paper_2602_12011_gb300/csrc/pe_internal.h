@@ -41,11 +41,14 @@ constexpr int kSinTab = 1024;   // entries of the (cos, sin) table used by sinco
 template <class T>
 struct ModeCoefT {
   T cm, icm, lncm;
+  T icm5;       // icm^5 (v^-5 = icm5 f^(-5/3))
   T amp;
+  T ampp;       // amp cm^p (amp v^p = ampp f^(p/3))
   T ph0;
   T mfac;       // m / (4 pi)
   T tffac;      // m / (12 pi)
   T Pp, Pc;
+  T Pc2;        // 2 Pc (the FP64 unit folds the 2 of Fx = 2 (n.p)(n.q) into it)
   T fend, ftap;
   float2 Ppw, Pcw;   // Pp, Pc as double words (FP32 pairs) for the mixed-precision path
   float2 cmw;        // cm as a double word
@@ -126,6 +129,9 @@ struct DetDev {
   const double* fm13;   // f^(-1/3)
   const double* lnf3;   // ln(f)/3
   const double* fm76;   // f^(-7/6)
+  const double* fm56;   // f^(-5/6) = f^(-7/6 + 1/3)
+  const double* fm12;   // f^(-1/2) = f^(-7/6 + 2/3)
+  const double* fm53;   // f^(-5/3)
   const double2* sca;   // (sin a, cos a), a = pi f L
   const double2* z;     // z = e^{-2 pi i f L}
   const double2* dg;    // [3][nb]: conj(d~_c) w_c Q n_c   (w_c = 4/(S_c T))

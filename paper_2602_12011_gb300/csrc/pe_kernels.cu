@@ -22,10 +22,12 @@
 namespace pe {
 
 // ------------------------------------------------------------------------------------------
-// Row A0: grid tables f, f^(1/3), f^(-1/3), ln(f)/3, f^(-7/6), sincos(pi f L), z = e^{-2 pi i f L}.
+// Row A0: grid tables f, f^(1/3), f^(-1/3), ln(f)/3, f^(-7/6), sincos(pi f L), z = e^{-2 pi i f L},
+// and fpow [3][nb] = f^(-5/6), f^(-1/2), f^(-5/3) (the amplitude powers f^(-7/6 + p/3), p = 1, 2,
+// and v^-5 up to the mode's constant).
 // ------------------------------------------------------------------------------------------
 __global__ void k_grid_tables(double T, long long k0, int nb, double L, double* f, double* f13, double* fm13,
-                              double* lnf3, double* fm76, double2* sca, double2* z) {
+                              double* lnf3, double* fm76, double* fpow, double2* sca, double2* z) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const double fb = double(k0 + b) / T;
@@ -35,6 +37,9 @@ __global__ void k_grid_tables(double T, long long k0, int nb, double L, double* 
   fm13[b] = 1.0 / c;
   lnf3[b] = log(fb) / 3.0;
   fm76[b] = rsqrt(c) / fb;
+  fpow[b] = sqrt(c) / fb;
+  fpow[nb + b] = rsqrt(fb);
+  fpow[2 * nb + b] = 1.0 / (fb * c * c);
   double s, co;
   sincospi(fb * L, &s, &co);
   sca[b] = make_double2(s, co);
@@ -491,8 +496,8 @@ __global__ void k_inject(int nb, double T, const double* psd, const double2* nor
 // Host-callable launch wrappers.
 // ------------------------------------------------------------------------------------------
 cudaError_t launch_grid_tables(double T, long long k0, int nb, double L, double* f, double* f13, double* fm13,
-                               double* lnf3, double* fm76, double2* sca, double2* z, cudaStream_t st) {
-  k_grid_tables<<<(nb + 127) / 128, 128, 0, st>>>(T, k0, nb, L, f, f13, fm13, lnf3, fm76, sca, z);
+                               double* lnf3, double* fm76, double* fpow, double2* sca, double2* z, cudaStream_t st) {
+  k_grid_tables<<<(nb + 127) / 128, 128, 0, st>>>(T, k0, nb, L, f, f13, fm13, lnf3, fm76, fpow, sca, z);
   return cudaGetLastError();
 }
 cudaError_t launch_sincos_table(double2* tab, cudaStream_t st) {

@@ -7,7 +7,7 @@
 namespace pe {
 
 cudaError_t launch_grid_tables(double T, long long k0, int nb, double L, double* f, double* f13, double* fm13,
-                               double* lnf3, double* fm76, double2* sca, double2* z, cudaStream_t st);
+                               double* lnf3, double* fm76, double* fpow, double2* sca, double2* z, cudaStream_t st);
 cudaError_t launch_sincos_table(double2* tab, cudaStream_t st);
 cudaError_t launch_psd_model(const double* f, int nb, double L, double oms, double acc, int shaping, int tdi_gen,
                              double* out, cudaStream_t st);
