@@ -359,8 +359,9 @@ __device__ __forceinline__ void xyz_final(const XYZAcc& a, double2 z, double2 x[
 struct BinIn {
   double f, f13, fm13, lnf3, fm76, invf;
   double a, sa, ca;    // a = pi f L
-  double a2;           // a^2
+  double a2, a2x2;     // a^2, 2 a^2
   double hf;           // f / 2
+  int sdeg;            // sinc polynomial class of the bin: 0, 1, 2 (degree 8, 12, 16 in u), 3 (none)
   int b;               // bin index (for the tables read per unit)
   double aturn;        // a / (2 pi) = f L / 2
   double2 z;           // e^{-2 i a}
@@ -454,21 +455,22 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     G[l] = cmul(gam, E[t]);
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (most bins of a massive-binary
     // signal), else from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
-    // below a = kSincPolyA: u1^2 = a^2 (1 - kn)^2 = a^2 + a^2 kn (kn - 2) and u2^2 = a^2 + a^2 kn (kn + 2);
-    // where u1 or u2 is small the cancellation error is ~ulp(a^2), far below what sinc resolves
+    // below a = kSincPolyA (degree class B.sdeg < 3, chosen once per bin): u1^2 = a^2 (1 - kn)^2 =
+    // a^2 + kn (a^2 kn - 2 a^2) and u2^2 = a^2 + kn (a^2 kn + 2 a^2), two FMAs each; where u1 or u2
+    // is small the cancellation error is ~ulp(a^2), far below what sinc resolves
     double sm, spl;
-    if (B.a < kSincPolyA8) {
-      const double a2kn = B.a2 * kn;
-      sm = sinc_poly_x<4>(fma(a2kn, kn - 2.0, B.a2));
-      spl = sinc_poly_x<4>(fma(a2kn, kn + 2.0, B.a2));
-    } else if (B.a < kSincPolyA12) {
-      const double a2kn = B.a2 * kn;
-      sm = sinc_poly_x<6>(fma(a2kn, kn - 2.0, B.a2));
-      spl = sinc_poly_x<6>(fma(a2kn, kn + 2.0, B.a2));
-    } else if (B.a < kSincPolyA) {
-      const double a2kn = B.a2 * kn;
-      sm = sinc_poly_x<8>(fma(a2kn, kn - 2.0, B.a2));
-      spl = sinc_poly_x<8>(fma(a2kn, kn + 2.0, B.a2));
+    if (B.sdeg < 3) {
+      const double x1 = fma(kn, fma(B.a2, kn, -B.a2x2), B.a2), x2 = fma(kn, fma(B.a2, kn, B.a2x2), B.a2);
+      if (B.sdeg == 0) {
+        sm = sinc_poly_x<4>(x1);
+        spl = sinc_poly_x<4>(x2);
+      } else if (B.sdeg == 1) {
+        sm = sinc_poly_x<6>(x1);
+        spl = sinc_poly_x<6>(x2);
+      } else {
+        sm = sinc_poly_x<8>(x1);
+        spl = sinc_poly_x<8>(x2);
+      }
     } else {
       const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
       double sak, cak;
@@ -507,7 +509,9 @@ __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinI
   B.invf = B.fm13 * B.fm13 * B.fm13;
   B.a = kPi * B.f * D.L;
   B.a2 = B.a * B.a;
+  B.a2x2 = 2.0 * B.a2;
   B.hf = 0.5 * B.f;
+  B.sdeg = B.a < kSincPolyA8 ? 0 : (B.a < kSincPolyA12 ? 1 : (B.a < kSincPolyA ? 2 : 3));
   B.b = b;
   B.aturn = 0.5 * B.f * D.L;
   const double2 sc = D.sca[b];
