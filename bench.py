@@ -39,7 +39,7 @@ MSUN_S = 4.925490947641267e-6
 #   fp32_inst   FFMA + FMUL + FADD (the double-word arithmetic of the mixed path)
 UNIT_COUNTS = {
     "fp64": {"fp64_flops": 402.0, "fp64_inst": 252.3, "fp32_inst": 0.2},
-    "mixed": {"fp64_flops": 57.7, "fp64_inst": 44.1, "fp32_inst": 2256.8},
+    "mixed": {"fp64_flops": 54.9, "fp64_inst": 41.5, "fp32_inst": 2256.8},
     # FP32 path: fp64_inst counts the FRND and F2F of CUDA's FP32 sincospif/sinf and conversions
     "fp32": {"fp64_flops": 0.25, "fp64_inst": 9.2, "fp32_inst": 354.4},
 }

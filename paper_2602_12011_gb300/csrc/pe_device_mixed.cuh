@@ -88,10 +88,8 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
                                                const float2* __restrict__ pcw, const ModeCoef* C2 = nullptr) {
   // --- waveform and time-frequency map (FP64; rows A2, A3)
   const double v = C.cm * B.f13;
-  const double iv = C.icm * B.fm13;
   const double lnv = C.lncm + B.lnf3;
-  double iv5 = iv * iv;
-  iv5 = iv5 * iv5 * iv;
+  const double iv5 = C.icm5 * D.fm53[B.b];   // v^-5 = cm^-5 f^(-5/3)
   double poly = S.P[7];
   double dpol = S.Pd[7];
 #pragma unroll
@@ -99,8 +97,9 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     poly = fma(poly, v, S.P[k]);
     dpol = fma(dpol, v, S.Pd[k]);
   }
-  const double psi_pn = fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
-  const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
+  const double q56 = fma(S.Q6, v, S.Q5);
+  const double psi_pn = fma(iv5, poly, lnv * q56);
+  const double dv = fma(iv5, dpol, fma(S.Q6 * v, lnv, q56));
   const double tf = fma(C.tffac * B.invf, dv, S.tc);
   // amplitude (times hsc) in double words: ampw f^(-7/6) v^p, times the taper where it is below 1
   df A = dfl_mul(C.ampw, W.fm76);

@@ -118,7 +118,8 @@ __global__ void k_gather_edges(const double2* hb, int K, const int* edge, int ne
   h0e[j] = hb[(size_t)mc * K + edge[i]];
 }
 
-// h0e -> 1/h0e in place (0 where h0e = 0: such an edge is never a ratio source)
+// h0e -> 1/h0e in place; 0 where |h0e|^2 is 0 (h0e = 0, never a ratio source, or so small that its
+// square underflows, where the ratio becomes 0 instead of the overflow a division would give)
 __global__ void k_invert_edges(double2* h0e, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
