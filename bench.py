@@ -45,7 +45,7 @@ UNIT_COUNTS = {
 }
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum
 # (profiles/k_loglike_fwd_dram_lisa_hm_T2^22_B1024.md): the per-bin tables, read once per launch
-TRAFFIC = {"fp64": 36.47e6 + 0.01e6, "mixed": 38.15e6 + 0.60e6, "fp32": None}
+TRAFFIC = {"fp64": 36.55e6 + 0.01e6, "mixed": 39.84e6 + 0.74e6, "fp32": None}
 
 
 def parse():
