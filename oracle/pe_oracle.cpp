@@ -25,6 +25,14 @@
 //   * Fisher matrix F_ij = <ds/dtheta_i | ds/dtheta_j> (Sec. 2.2, Eq. eq_ll_fisher and below).
 // Sums over bins use Neumaier-compensated accumulation.
 //
+// Parity unpinned (no check here beyond the transcription itself; the tests pin everything
+// else against closed forms, brute force, energy balance, multipole flux or the paper's
+// identities):
+//   * the phases of the higher-mode factors in Hhat (the factors +-i and the signs of H21, H33,
+//     H44 relative to H22); their magnitudes are pinned by the multipole flux;
+//   * the TianQin normal direction and every noise level (configuration readings); the A/E/T
+//     algebra of psd_aet is pinned.
+//
 // Build: g++ -O2 -std=c++17 -fPIC -shared -fopenmp (no fast-math).
 
 #include <cmath>
@@ -251,6 +259,7 @@ T planck_taper(const Source<T>& s, double f, int m) {
 
 // Leading-order mode factor H_lm(x) of h_lm = 2 M eta x / D sqrt(16 pi/5) H_lm e^{-i m psi}
 // (Blanchet, Living Rev. Relativ. 17, 2 (2014), spherical modes at Newtonian order).
+// Magnitudes pinned by the multipole flux; the phases (+-i, signs) are parity unpinned.
 template <class T>
 Cx<T> Hhat(const Source<T>& s, int l, int m, const T& x) {
   const T eta = s.q / ((1.0 + s.q) * (1.0 + s.q));

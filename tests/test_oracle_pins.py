@@ -213,6 +213,58 @@ def test_spin_orbit_coefficient_in_the_test_mass_limit(oracle_mod):
     assert c[3] == pytest.approx(want, rel=1e-7), (c[3], want)
 
 
+def _spin_energy_balance(q, chi1, chi2):
+    """alpha_3 and alpha_4 of the PN phase with their aligned-spin terms, by energy balance
+    through 2PN (the series algebra of _taylorf2_from_energy_and_flux, numerically). G = c = M = 1,
+    m_1 = q/(1+q), S_i = m_i^2 chi_i along the orbital angular momentum, S = S_1 + S_2,
+    Sigma = S_2/m_2 - S_1/m_1, delta = m_1 - m_2. Circular-orbit energy and flux with their spin
+    parts (Kidder, Phys. Rev. D 52, 821 (1995); Blanchet, Living Rev. Relativ. 17, 2 (2014)):
+      E / (-mu x/2) = 1 + (-3/4 - eta/12) x + (14/3 S + 2 delta Sigma) x^(3/2)
+                      + (-27/8 + 19/8 eta - eta^2/24 + (S_1.S_2 - 3 S_1.L S_2.L) / eta) x^2,
+      F / F_N = 1 + (-1247/336 - 35/12 eta) x + (4 pi - 4 S - 5/4 delta Sigma) x^(3/2)
+                + (-44711/9072 + 9271/504 eta + 65/18 eta^2 + (-103 S_1.S_2 + 289 S_1.L S_2.L) / (48 eta)) x^2.
+    For aligned spins S_1.S_2 = S_1.L S_2.L = eta^2 chi_1 chi_2."""
+    m1, m2 = q / (1 + q), 1 / (1 + q)
+    eta, delta = m1 * m2, m1 - m2
+    S = m1 ** 2 * chi1 + m2 ** 2 * chi2
+    Sig = m2 * chi2 - m1 * chi1
+    ss = eta * chi1 * chi2                      # S_1 S_2 / eta for aligned spins
+    E = {2: -0.5, 4: -0.5 * (-0.75 - eta / 12), 5: -0.5 * (14 / 3 * S + 2 * delta * Sig),
+         6: -0.5 * (-27 / 8 + 19 / 8 * eta - eta ** 2 / 24 + (1 - 3) * ss)}
+    F = {0: 1.0, 2: -1247 / 336 - 35 / 12 * eta, 3: 4 * math.pi - 4 * S - 1.25 * delta * Sig,
+         4: -44711 / 9072 + 9271 / 504 * eta + 65 / 18 * eta ** 2 + (-103 + 289) / 48 * ss}
+    N = 5
+    num = [0.0] * N                             # -(dE/dv) / v
+    for k, c in E.items():
+        num[k - 2] += -k * c
+    Fs = [F.get(k, 0.0) for k in range(N)]
+    inv = [1.0] + [0.0] * (N - 1)               # 1/F as a series
+    for n in range(1, N):
+        inv[n] = -sum(Fs[j] * inv[n - j] for j in range(1, n + 1))
+    g = [sum(num[j] * inv[n - j] for j in range(n + 1)) for n in range(N)]
+    return 40 * g[3] / ((3 - 8) * (3 - 5)), 40 * g[4] / ((4 - 8) * (4 - 5))
+
+
+@pytest.mark.parametrize("q,chi1,chi2", [(1.0, 0.5, -0.3), (3.0, 0.9, 0.2), (8.0, -0.7, 0.6), (1.5, 0.95, 0.95)])
+def test_spin_terms_from_energy_balance(oracle_mod, q, chi1, chi2):
+    """The oracle's alpha_3 (1.5PN spin-orbit, with its eta dependence) and alpha_4 (2PN
+    spin-spin) for comparable masses and aligned spins, against energy balance with the spin parts
+    of the energy and flux (_spin_energy_balance). The oracle keeps exactly these spin orders (no
+    self-spin terms, no higher spin-orbit terms), so only alpha_3 and alpha_4 are compared; their
+    non-spinning parts are pinned on their own above."""
+    eta = q / (1 + q) ** 2
+    th = TH.copy()
+    th[1], th[2], th[3] = q, chi1, chi2
+    vs = np.linspace(0.03, 0.3, 80)
+    y = np.array([oracle_mod.psi_pn(th, v) for v in vs]) * 128 * eta * vs ** 5 / 3
+    B = np.column_stack([vs ** k for k in range(8)] + [vs ** 5 * np.log(vs), vs ** 6 * np.log(vs)])
+    sc = np.abs(B).max(axis=0)
+    c = np.linalg.lstsq(B / sc, y, rcond=None)[0] / sc
+    a3, a4 = _spin_energy_balance(q, chi1, chi2)
+    assert c[3] == pytest.approx(a3, rel=1e-7, abs=1e-6), (c[3], a3)
+    assert c[4] == pytest.approx(a4, rel=1e-7, abs=1e-6), (c[4], a4)
+
+
 def _newtonian_multipole_flux(m1, m2, r, n=64):
     """Energy flux of a Newtonian circular binary (masses m1, m2, separation r; G = c = M = 1),
     split by multipole and by harmonic of the orbital frequency, from the multipole expansion of
