@@ -597,7 +597,9 @@ def main():
             "tuning": tuned,
             "grad": {"value": grad_value, "unit": "grad evals/s", "ms_per_step": sum(gms) / Kg, "steps": Kg,
                      "finite": grad_ok, "mixed": grad_mixed},
-            "gpu_launches": 4 * K,
+            # per step: prep, sub-tile scan (plus the work-item scan when items hold R > 1
+            # sub-tiles), forward, reduce
+            "gpu_launches": (5 if int(tuned.get("subtiles", 1)) > 1 else 4) * K,
             "clocks": clk,
             "results_finite": result_ok}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
