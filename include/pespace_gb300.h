@@ -316,8 +316,10 @@ pe_status pe_fisher_gaussian(const pe_detector* dets, int ndet, const double* th
  *     mode_mask and edges [nedges] (host, strictly increasing, 2 <= nedges <= 640, within the grid).
  *     mode_mask may carry PE_PREC_MIXED: pe_hetero_loglike_batch then evaluates the signal at the
  *     edges with the mixed-precision unit and the per-bin contraction in double words (the
- *     summary data are built in FP64, the sums across bins stay FP64); PE_PREC_FP32 gives
- *     PE_EINVAL. The library owns the result; det must outlive it. Synchronous.
+ *     summary data are built in FP64, the sums across bins stay FP64). An edge where a ratio
+ *     h/h0 reaches 2^24 (a reference that has almost vanished, e.g. past its taper) keeps FP64
+ *     ratios, and the bins that read it are contracted in FP64. PE_PREC_FP32 gives PE_EINVAL.
+ *     The library owns the result; det must outlive it. Synchronous.
  *   pe_hetero_loglike_batch: log L per sample for hets[ndet] (1..8 detectors sharing one mode mask),
  *     theta [B][11], out_logl [B], out_dhhh nullable [B][ndet][3][2], out_status nullable [B] (host or
  *     device each, as pe_loglike_batch). One CTA per sample evaluates all NE edges of every detector.
