@@ -77,6 +77,7 @@ def lib():
         L = C.CDLL(_LIB)
         L.or_sylm.restype = C.c_double
         L.or_sylm.argtypes = [C.c_int, C.c_int, C.c_double]
+        L.or_hhat.argtypes = [C.c_double, C.c_int, C.c_int, C.c_double, _P]
         L.or_psd.argtypes = [C.POINTER(OrConfig), _P, C.c_int64, _P]
         L.or_orbit.argtypes = [C.POINTER(OrConfig), C.c_double, _P]
         L.or_mode.argtypes = [_P, C.c_int, C.c_int, _P, C.c_int64, _P, _P, _P]
@@ -109,6 +110,13 @@ def _f64(a) -> np.ndarray:
 def sylm(l: int, m: int, iota: float) -> float:
     """-2Y_lm(iota, phi=0) from the Wigner-d sum."""
     return lib().or_sylm(l, m, iota)
+
+
+def hhat(q: float, l: int, m: int, x: float) -> complex:
+    """The oracle's leading-order mode factor H_lm(x) for mass ratio q (h_lm ~ H_lm e^{-i m psi})."""
+    out = np.zeros(2)
+    lib().or_hhat(float(q), l, m, float(x), _ptr(out))
+    return complex(out[0], out[1])
 
 
 def psd(det: dict, f) -> np.ndarray:

@@ -26,10 +26,8 @@
 // Sums over bins use Neumaier-compensated accumulation.
 //
 // Parity unpinned (no check here beyond the transcription itself; the tests pin everything
-// else against closed forms, brute force, energy balance, multipole flux or the paper's
-// identities):
-//   * the phases of the higher-mode factors in Hhat (the factors +-i and the signs of H21, H33,
-//     H44 relative to H22); their magnitudes are pinned by the multipole flux;
+// else against closed forms, brute force, energy balance, multipole flux, the 1PN polarisations
+// or the paper's identities):
 //   * the TianQin normal direction and every noise level (configuration readings); the A/E/T
 //     algebra of psd_aet is pinned.
 //
@@ -259,7 +257,7 @@ T planck_taper(const Source<T>& s, double f, int m) {
 
 // Leading-order mode factor H_lm(x) of h_lm = 2 M eta x / D sqrt(16 pi/5) H_lm e^{-i m psi}
 // (Blanchet, Living Rev. Relativ. 17, 2 (2014), spherical modes at Newtonian order).
-// Magnitudes pinned by the multipole flux; the phases (+-i, signs) are parity unpinned.
+// Magnitudes pinned by the multipole flux; the phases (+-i, signs) by the 1PN polarisations.
 template <class T>
 Cx<T> Hhat(const Source<T>& s, int l, int m, const T& x) {
   const T eta = s.q / ((1.0 + s.q) * (1.0 + s.q));
@@ -540,6 +538,15 @@ extern "C" {
 int or_abi_version(void) { return 1; }
 
 double or_sylm(int l, int m, double iota) { return sYlm_m2<double>(l, m, iota); }
+
+// Hhat(l, m, x) for mass ratio q: out = (re, im).
+void or_hhat(double q, int l, int m, double x, double* out) {
+  Source<double> s{};
+  s.q = q;
+  const Cx<double> h = Hhat(s, l, m, x);
+  out[0] = h.re;
+  out[1] = h.im;
+}
 
 void or_psd(const OrConfig* cfg, const double* f, int64_t n, double* out /*[3][n]*/) {
   for (int64_t i = 0; i < n; ++i) {

@@ -265,6 +265,62 @@ def test_spin_terms_from_energy_balance(oracle_mod, q, chi1, chi2):
     assert c[4] == pytest.approx(a4, rel=1e-7, abs=1e-6), (c[4], a4)
 
 
+def _biww_polarizations(iota, q, psi):
+    """(H+ - i Hx) of a circular binary at orders x^0, x^(1/2), x^1, from the 1PN polarisations of
+    Blanchet, Iyer, Will & Wiseman, Class. Quantum Grav. 13, 575 (1996) (as restated in Blanchet,
+    Living Rev. Relativ. 17, 2 (2014)); h+,x = (2 G mu x / (c^2 R)) sum_p x^(p/2) H^(p/2)+,x, psi the
+    orbital phase from the ascending node, Delta = (m1 - m2)/M. The zero-frequency memory term of
+    H+^(0) is left out (it belongs to the m = 0 modes)."""
+    c, s = math.cos(iota), math.sin(iota)
+    nu = q / (1 + q) ** 2
+    D = (q - 1) / (q + 1)
+    hp0 = -(1 + c * c) * np.cos(2 * psi)
+    hx0 = -2 * c * np.sin(2 * psi)
+    hp1 = -s * D * ((5 / 8 + c * c / 8) * np.cos(psi) - (9 / 8 + 9 * c * c / 8) * np.cos(3 * psi))
+    hx1 = s * c * D * (-0.75 * np.sin(psi) + 2.25 * np.sin(3 * psi))
+    hp2 = ((19 / 6 + 1.5 * c * c - c ** 4 / 3 + nu * (-19 / 6 + 11 / 6 * c * c + c ** 4)) * np.cos(2 * psi)
+           - 4 / 3 * s * s * (1 + c * c) * (1 - 3 * nu) * np.cos(4 * psi))
+    hx2 = (c * (17 / 3 - 4 / 3 * c * c + nu * (-13 / 3 + 4 * c * c)) * np.sin(2 * psi)
+           - 8 / 3 * c * s * s * (1 - 3 * nu) * np.sin(4 * psi))
+    return hp0 - 1j * hx0, hp1 - 1j * hx1, hp2 - 1j * hx2
+
+
+@pytest.mark.parametrize("q", [1.5, 3.0, 8.0])
+@pytest.mark.parametrize("iota", [0.3, 1.1, 2.2])
+def test_higher_mode_phases_reproduce_the_1pn_polarisations(oracle_mod, q, iota):
+    """The complex mode factors of the oracle (the +-i of H21 and H33, their relative sign, the
+    signs of H32 and H44), summed as h+ - i hx = sum_lm h_lm -2Y_lm(iota, 0) with
+    h_lm ~ sqrt(16 pi/5) H_lm x^(p/2) e^(-i m psi) and h_(l,-m) = (-1)^l conj(h_lm), against the 1PN
+    polarisations of a circular binary, order by order in x^(1/2). The modes the oracle does not
+    carry but the polarisations contain at these orders are added from Blanchet's review: H31 =
+    i Delta/(12 sqrt(14)) at x^(1/2); H42 = sqrt(5)/63 (1 - 3 nu) and the 1PN term of H22,
+    -107/42 + 55 nu/42, at x^1. The polarisations measure psi from the ascending node; the
+    oracle's phase origin is 3 pi/2 behind it, a convention fixed by the x^0 order up to pi (a
+    shift by pi exchanges the bodies and flips the odd orders, which must not match then)."""
+    nu = q / (1 + q) ** 2
+    D = (q - 1) / (q + 1)
+    k = math.sqrt(16 * math.pi / 5)
+    orders = {0: [(2, 2, oracle_mod.hhat(q, 2, 2, 1.0))],
+              1: [(2, 1, oracle_mod.hhat(q, 2, 1, 1.0)), (3, 3, oracle_mod.hhat(q, 3, 3, 1.0)),
+                  (3, 1, 1j * D / (12 * math.sqrt(14)))],
+              2: [(3, 2, oracle_mod.hhat(q, 3, 2, 1.0)), (4, 4, oracle_mod.hhat(q, 4, 4, 1.0)),
+                  (4, 2, math.sqrt(5) / 63 * (1 - 3 * nu)), (2, 2, -107 / 42 + 55 * nu / 42)]}
+
+    def modes_sum(p, psi):
+        h = np.zeros(psi.shape, dtype=complex)
+        for l, m, H in orders[p]:
+            h += k * (H * np.exp(-1j * m * psi) * oracle_mod.sylm(l, m, iota)
+                      + (-1) ** l * np.conj(H) * np.exp(1j * m * psi) * oracle_mod.sylm(l, -m, iota))
+        return h
+
+    psi = np.linspace(0.0, 2 * math.pi, 64, endpoint=False)
+    ref = _biww_polarizations(iota, q, psi)
+    for p in range(3):
+        assert np.abs(modes_sum(p, psi + 1.5 * math.pi) - ref[p]).max() < 1e-13, p
+    # the other origin allowed by the x^0 order flips the x^(1/2) order (exchanged bodies)
+    assert np.abs(modes_sum(1, psi + 0.5 * math.pi) - ref[1]).max() > 0.1 * np.abs(ref[1]).max()
+
+
 def _newtonian_multipole_flux(m1, m2, r, n=64):
     """Energy flux of a Newtonian circular binary (masses m1, m2, separation r; G = c = M = 1),
     split by multipole and by harmonic of the orbital frequency, from the multipole expansion of
