@@ -54,6 +54,9 @@ def test_null_arguments_are_einval_without_cuda(lib):
     assert b"tdi_gen" in lib.pe_last_error()
     assert lib.pe_loglike_batch(None, 1, None, 1, 1, None, None, None, None) == L.PE_EINVAL
     assert lib.pe_destroy_detector(None) == L.PE_OK
+    # tuning entry points: handle checks come before any device work
+    assert lib.pe_tune_set(None, 1, 1, 0x1F, 0, 8, 1) == L.PE_EINVAL
+    assert lib.pe_autotune(None, 1, None, 1, 0x1F, None, None, None, None) == L.PE_EINVAL
 
 
 def test_product_binding_never_imports_the_oracle():
