@@ -170,7 +170,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
 pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet, const double* theta, int B, unsigned mode_mask,
                                    double* out_logl, double* out_dhhh, int32_t* out_status, void* stream);
 
-/* ---- Uneven-batch plans and the autotuner (spec growth: batched uneven launches) -------
+/* ---- Uneven-batch plans and the autotuner (batched uneven launches) -------------------------
  * A plan is the whole pe_loglike_batch computation for fixed detectors, batch size, mode mask
  * and fixed DEVICE buffers (theta [B][11], out_logl [B], optional out_dhhh [B][ndet][3][2] and
  * out_status [B]), captured once into a CUDA graph with its scratch allocated at creation. Every
@@ -203,7 +203,7 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
 pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_mask, int fwd_variant, int ctas_per_sm,
                       int subtiles);
 
-/* ---- Learned waveform surrogate (spec growth: MLP on BF16 tensor cores + node spline) ----
+/* ---- Learned waveform surrogate (MLP on BF16 tensor cores + node spline) ----------------------
  * An MLP 11 -> 256 -> 256 -> 256 -> 2560 (BF16 weights and activations on tensor cores, FP32
  * accumulation, SiLU) maps theta to, per mode, a phase residual and an amplitude ratio at 256
  * frequency nodes log-spaced from 1e-4 Hz to the mode's taper end m F_isco. The phase residual is

@@ -1,4 +1,4 @@
-// pe_surrogate.cu -- the learned waveform surrogate (spec growth 4): an MLP
+// pe_surrogate.cu -- the learned waveform surrogate: an MLP
 // 11 -> 256 -> 256 -> 256 -> 2560 on BF16 tensor cores (pe_mlp.cu) predicts, per mode, a phase
 // residual and an amplitude ratio at 256 log-spaced frequency nodes; at those nodes the full
 // response is evaluated in FP64 and spline-interpolated onto the grid (the sparse-node idea the
