@@ -485,6 +485,64 @@ def test_planck_taper_edges(oracle_mod):
         assert np.all(np.diff(w) <= 0)
 
 
+def _taper_flatness(w, F1, F2):
+    """Defining properties of the McKechan-Robinson-Sathyaprakash window as a falling edge on
+    [F1, F2]; returns a list of the properties that fail (empty when all hold).
+    - C-infinity flat at both ends: the finite-difference derivatives of orders 1..4, scaled by
+      (F2 - F1)^k, vanish (below 1e-6) at 2 % of the width from either end, and shrink towards it;
+    - faster than any power at the end: the log slope d ln w / d ln(F2 - F) exceeds 0.5 a/delta
+      (> 50 at delta = a/100; a power law delta^p has slope p);
+    - antisymmetric about the midpoint: w(F1 + x) + w(F2 - x) = 1."""
+    a = F2 - F1
+    bad = []
+
+    def deriv(F, k, h):
+        c = [1.0]
+        for _ in range(k):               # binomial central-difference weights of order k
+            c = [x - y for x, y in zip(c + [0.0], [0.0] + c)]
+        pts = [F + (j - k / 2.0) * h for j in range(k + 1)]
+        return sum(cj * w(p) for cj, p in zip(c, pts)) / h ** k
+
+    for k in (1, 2, 3, 4):
+        for end, sgn in ((F1, 1.0), (F2, -1.0)):
+            vals = [abs(deriv(end + sgn * d * a, k, 0.002 * a)) * a ** k for d in (0.04, 0.02)]
+            if not (vals[1] <= 1e-6 and vals[1] <= vals[0]):
+                bad.append("derivative %d at %s: %s" % (k, "F1" if sgn > 0 else "F2", vals))
+    for d in (1e-2, 3e-3):
+        lo, hi = F2 - d * a * 1.01, F2 - d * a / 1.01
+        wl, wh = w(lo), w(hi)
+        slope = (math.log(wl) - math.log(wh)) / (math.log(d * 1.01) - math.log(d / 1.01)) if wl > 0 and wh > 0 else 0.0
+        if not slope > 0.5 / d:
+            bad.append("log slope %.3g at delta %g" % (slope, d))
+    for x in np.linspace(0.05, 0.95, 19):
+        if abs(w(F1 + x * a) + w(F2 - x * a) - 1.0) > 1e-14:
+            bad.append("antisymmetry at %g" % x)
+    return bad
+
+
+def test_planck_taper_is_cinf_flat(oracle_mod):
+    """The window's interior shape (Sec. 2.3 falling edge, read as the McKechan et al. 2010 Planck
+    window): flat to every order at both ends, antisymmetric about the midpoint. A raised-cosine
+    edge and a C^2 smoothstep edge, written here, fail the same checks."""
+    for th0 in (TH, np.r_[3e5, TH[1:]]):
+        M = th0[0] * MSUN_S
+        Fisco = 6 ** -1.5 / (2 * math.pi * M)
+        F1, F2 = 0.9 * Fisco, Fisco
+        for m in (1, 2, 3, 4):
+            assert _taper_flatness(lambda Fo: oracle_mod.taper(th0, Fo * m, m), F1, F2) == []
+
+    def cosine(Fo, F1=0.9, F2=1.0):
+        x = min(max((Fo - F1) / (F2 - F1), 0.0), 1.0)
+        return 0.5 * (1.0 + math.cos(math.pi * x))
+
+    def smoothstep(Fo, F1=0.9, F2=1.0):
+        x = min(max((Fo - F1) / (F2 - F1), 0.0), 1.0)
+        return 1.0 - x ** 3 * (10.0 - 15.0 * x + 6.0 * x * x)
+
+    assert _taper_flatness(cosine, 0.9, 1.0) != []
+    assert _taper_flatness(smoothstep, 0.9, 1.0) != []
+
+
 # -------------------------------------------------------------------------------------------
 # Geometry: sky basis and orbits
 # -------------------------------------------------------------------------------------------
@@ -712,6 +770,71 @@ def test_psd_aet_is_rotation_of_xyz_covariance(oracle_mod):
             # the rotation cancels to O(x^2) in T, so its rounding is relative to S_X
             np.testing.assert_allclose(np.diag(Ca), S[:, i], rtol=1e-12, atol=1e-13 * SX[i] * fac[i])
             assert np.abs(Ca - np.diag(np.diag(Ca))).max() < 1e-13 * SX[i] * fac[i]
+
+
+def _welch_psd(x, dt, nseg):
+    """One-sided PSD of a real series by Welch averaging (Hann window, no overlap):
+    P_k = 2 dt |sum_n w_n x_n e^{-2 pi i k n/N}|^2 / sum_n w_n^2, averaged over segments."""
+    n = x.size // nseg
+    seg = x[:n * nseg].reshape(nseg, n)
+    w = 0.5 - 0.5 * np.cos(2 * math.pi * np.arange(n) / n)
+    X = np.fft.rfft(seg * w, axis=1)
+    return np.fft.rfftfreq(n, dt), 2.0 * dt * np.mean(np.abs(X) ** 2, axis=0) / np.sum(w * w)
+
+
+def _single_link_noise_from_time_series(dt=1.0, n=1 << 23, nseg=2048, seed=20611):
+    """Time-domain definitions of the two noise terms in fractional frequency (Sec. 3.2: test-mass
+    acceleration and optical-metrology (OMS) noise), simulated:
+    - OMS: white displacement noise x(t) of one-sided PSD a_oms^2 [m^2/Hz]; y = (dx/dt)/c, the
+      derivative by a central difference;
+    - acceleration: white acceleration a(t) of one-sided PSD a_acc^2 [m^2 s^-4/Hz]; y = v/c with
+      v(t) = integral of a dt (a running sum).
+    Returns the band frequencies and the averaged periodograms per unit a_oms^2 and a_acc^2, with
+    the discrete operators' transfer functions divided out of the derivative and the running sum
+    (both tend to 1 as f dt -> 0; the band keeps f dt <= 0.02)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    sig = 1.0 / math.sqrt(2.0 * dt)                 # white noise of unit one-sided PSD
+    xd = g.standard_normal(n + 2) * sig
+    y_oms = (xd[2:] - xd[:-2]) / (2.0 * dt) / C_SI
+    acc = g.standard_normal(n) * sig
+    y_acc = np.cumsum(acc) * dt / C_SI
+    f, P_oms = _welch_psd(y_oms, dt, nseg)
+    _, P_acc = _welch_psd(y_acc, dt, nseg)
+    u = 2 * math.pi * f * dt
+    band = (f >= 2e-3) & (f <= 0.02 / dt)
+    P_oms = P_oms[band] / (np.sin(u[band]) / u[band]) ** 2
+    P_acc = P_acc[band] / ((u[band] / 2) / np.sin(u[band] / 2)) ** 2
+    return f[band], P_oms, P_acc
+
+
+def _band_ratios(f, P, S):
+    edges = np.geomspace(f[0], f[-1] * (1 + 1e-9), 7)
+    return np.array([np.mean(P[(f >= lo) & (f < hi)] / S[(f >= lo) & (f < hi)]) for lo, hi in zip(edges[:-1], edges[1:])])
+
+
+def test_psd_unit_conversion_against_time_domain_noise(oracle_mod):
+    """The oracle's single-link OMS and acceleration terms in fractional frequency against averaged
+    periodograms of simulated displacement and acceleration noise converted in the time domain
+    (y = x'/c and y = (1/c) int a dt). The single-link terms are read from the oracle's S_A with the
+    other noise switched off (TDI 1.5, no shaping): S_A = 8 sin^2 x (2 + cos x) S_oms and
+    8 sin^2 x (6 + 4 cos x + 2 cos 2x) S_acc, the A/E/T algebra pinned by the covariance test.
+    The estimate has ~1-2 % statistical error per band (bar 5 %); a dropped 2 pi, a missing 1/c or a wrong
+    power of f, planted in copies written here, fails."""
+    f, P_oms, P_acc = _single_link_noise_from_time_series()
+    base = dict(W.TIANQIN, tdi_gen=15, psd_shaping=0)
+    x = 2 * math.pi * f * base["arm_m"] / C_SI
+    S_oms = oracle_mod.psd(dict(base, oms_m_rtHz=1.0, acc_ms2_rtHz=0.0), f)[0] / (8 * np.sin(x) ** 2 * (2 + np.cos(x)))
+    S_acc = oracle_mod.psd(dict(base, oms_m_rtHz=0.0, acc_ms2_rtHz=1.0), f)[0] / (
+        8 * np.sin(x) ** 2 * (6 + 4 * np.cos(x) + 2 * np.cos(2 * x)))
+    r_oms, r_acc = _band_ratios(f, P_oms, S_oms), _band_ratios(f, P_acc, S_acc)
+    assert np.all(np.abs(r_oms - 1) < 0.05), r_oms
+    assert np.all(np.abs(r_acc - 1) < 0.05), r_acc
+    planted = {"oms without 2 pi": (f / C_SI) ** 2, "oms with f^1": 2 * math.pi * f / C_SI ** 2,
+               "acc without 1/c": 1 / (2 * math.pi * f) ** 2, "acc with f^-1": 1 / (2 * math.pi * f * C_SI ** 2),
+               "acc two-sided": 0.5 / (2 * math.pi * f * C_SI) ** 2}
+    for name, S in planted.items():
+        P = P_oms if name.startswith("oms") else P_acc
+        assert np.any(np.abs(_band_ratios(f, P, S) - 1) > 0.05), name
 
 
 def test_parseval_brute_force_dft(oracle_mod):
