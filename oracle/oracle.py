@@ -90,6 +90,7 @@ def lib():
         L.or_link.argtypes = [C.POINTER(OrConfig), _P, C.c_int, C.c_int, _P, C.c_int64, C.c_int, C.c_int,
                               C.c_double, _P]
         L.or_response.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, _P, C.c_int64, _P]
+        L.or_response_ld.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, _P, C.c_int64, _P]
         L.or_response_xyz.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, _P, C.c_int64, _P]
         L.or_make_data.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, C.c_double, C.c_int64, C.c_int64, _P, _P]
         L.or_loglike.argtypes = [C.POINTER(OrDetector), C.c_int, _P, C.c_uint, _P]
@@ -182,6 +183,15 @@ def response(det: dict, theta, mode_mask: int, f) -> np.ndarray:
     out = np.zeros(3 * 2 * f.size)
     c = config(det)
     lib().or_response(C.byref(c), _ptr(th), mode_mask, _ptr(f), f.size, _ptr(out))
+    return out.view(np.complex128).reshape(3, f.size)
+
+
+def response_ld(det: dict, theta, mode_mask: int, f) -> np.ndarray:
+    """The A/E/T response evaluated in long double (the same template), rounded to complex128."""
+    th, f = _f64(theta), _f64(f)
+    out = np.zeros(3 * 2 * f.size)
+    c = config(det)
+    lib().or_response_ld(C.byref(c), _ptr(th), mode_mask, _ptr(f), f.size, _ptr(out))
     return out.view(np.complex128).reshape(3, f.size)
 
 

@@ -73,6 +73,7 @@ template <class T> struct is_dual { static const bool value = false; };
 template <class T, int N> struct is_dual<Dual<T, N>> { static const bool value = true; };
 
 inline double val(double x) { return x; }
+inline double val(long double x) { return (double)x; }
 template <class T, int N> inline double val(const Dual<T, N>& x) { return val(x.v); }
 
 #define DUAL_T template <class T, int N>
@@ -351,21 +352,25 @@ void sky_basis(const Source<T>& s, T k[3], T ep[3][3], T ec[3][3]) {
 }
 
 // ----------------------------------------------------------------------------------------
-// Orbits: spacecraft position x_i(t), i = 1..3 (index 0..2), in light-seconds.
+// Orbits: spacecraft position x_i(t), i = 1..3 (index 0..2), in light-seconds, as the guiding
+// centre c(t) plus each spacecraft's offset d_i(t), x_i = c + d_i. The link vectors x_r - x_s are
+// formed from the offsets (d_r - d_s): equal in exact arithmetic, and free of the cancellation of
+// the 1 au centre that would otherwise cost ~AU/L ulps in every link vector.
 // ----------------------------------------------------------------------------------------
 template <class T>
-void orbit_pos(const OrConfig& cfg, const T& t, T x[3][3]) {
+void orbit_parts(const OrConfig& cfg, const T& t, T c[3], T d[3][3]) {
   const double L = cfg.arm_m / C_SI;
   if (cfg.orbit == 0) {
     // Rubbo, Cornish & Poujade 2004, Eq. (1)-(3) there: first order in the eccentricity.
     const double R = AU_S;
     const double e = L / (2.0 * std::sqrt(3.0) * R);
     T alpha = cfg.alpha0 + 2.0 * PI * t / YEAR_S;
+    c[0] = R * cos(alpha); c[1] = R * sin(alpha); c[2] = T(0.0);
     for (int i = 0; i < 3; ++i) {
       double b = 2.0 * PI * i / 3.0 + cfg.cartwheel0;
-      x[i][0] = R * cos(alpha) + 0.5 * e * R * (cos(2.0 * alpha - b) - 3.0 * std::cos(b));
-      x[i][1] = R * sin(alpha) + 0.5 * e * R * (sin(2.0 * alpha - b) - 3.0 * std::sin(b));
-      x[i][2] = -std::sqrt(3.0) * e * R * cos(alpha - b);
+      d[i][0] = 0.5 * e * R * (cos(2.0 * alpha - b) - 3.0 * std::cos(b));
+      d[i][1] = 0.5 * e * R * (sin(2.0 * alpha - b) - 3.0 * std::sin(b));
+      d[i][2] = -std::sqrt(3.0) * e * R * cos(alpha - b);
     }
   } else {
     // Earth on a circular 1 au orbit in the ecliptic plus an equilateral triangle of radius
@@ -376,14 +381,21 @@ void orbit_pos(const OrConfig& cfg, const T& t, T x[3][3]) {
     double n[3] = {std::cos(nb) * std::cos(nl), std::cos(nb) * std::sin(nl), std::sin(nb)};
     double e1[3] = {-std::sin(nl), std::cos(nl), 0.0};
     double e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
+    c[0] = R * cos(alpha); c[1] = R * sin(alpha); c[2] = T(0.0);
     for (int i = 0; i < 3; ++i) {
       T ph = 2.0 * PI * t / cfg.geo_period_s + 2.0 * PI * i / 3.0;
       T ci = cos(ph), si = sin(ph);
-      x[i][0] = R * cos(alpha) + r * (ci * e1[0] + si * e2[0]);
-      x[i][1] = R * sin(alpha) + r * (ci * e1[1] + si * e2[1]);
-      x[i][2] = T(0.0) + r * (ci * e1[2] + si * e2[2]);
+      for (int j = 0; j < 3; ++j) d[i][j] = r * (ci * e1[j] + si * e2[j]);
     }
   }
+}
+
+template <class T>
+void orbit_pos(const OrConfig& cfg, const T& t, T x[3][3]) {
+  T c[3], d[3][3];
+  orbit_parts(cfg, t, c, d);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) x[i][j] = c[j] + d[i][j];
 }
 
 template <class T>
@@ -397,25 +409,28 @@ T sinc(const T& x) {
 
 // Single-link FD response of one mode, Eq. eq_fd_resp, link s -> r (1-based r, s):
 //   y~_rs = -i pi f L sinc[pi f L (1 - k.n_rs)] exp{-i pi f [L + k.(x_r + x_s)]} n_rs.h~.n_rs
-// with n_rs = (x_r - x_s)/|x_r - x_s| and positions taken at t_f of the mode.
+// with n_rs = (x_r - x_s)/|x_r - x_s| and positions taken at t_f of the mode. With x = c + d
+// (orbit_parts): x_r - x_s = d_r - d_s, and the phase factor is exp{-i pi f (L + 2 k.c)} times
+// exp{-i pi f k.(d_r + d_s)}; the first factor is the same for every link of the bin.
 template <class T>
-Cx<T> link_response(const OrConfig& cfg, const T k[3], const Cx<T> h[3][3], const T x[3][3], double f,
-                    int r, int s) {
+Cx<T> link_response(const OrConfig& cfg, const T k[3], const Cx<T> h[3][3], const T c[3], const T d[3][3],
+                    double f, int r, int s) {
   const double L = cfg.arm_m / C_SI;
   T n[3];
   T nn(0.0);
-  for (int i = 0; i < 3; ++i) { n[i] = x[r - 1][i] - x[s - 1][i]; nn = nn + n[i] * n[i]; }
+  for (int i = 0; i < 3; ++i) { n[i] = d[r - 1][i] - d[s - 1][i]; nn = nn + n[i] * n[i]; }
   T inv = 1.0 / sqrt(nn);
   for (int i = 0; i < 3; ++i) n[i] = n[i] * inv;
   Cx<T> nhn;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) nhn = nhn + h[i][j] * (n[i] * n[j]);
   T kn = k[0] * n[0] + k[1] * n[1] + k[2] * n[2];
-  T kx = T(0.0);
-  for (int i = 0; i < 3; ++i) kx = kx + k[i] * (x[r - 1][i] + x[s - 1][i]);
+  T kc = k[0] * c[0] + k[1] * c[1] + k[2] * c[2];
+  T kd = T(0.0);
+  for (int i = 0; i < 3; ++i) kd = kd + k[i] * (d[r - 1][i] + d[s - 1][i]);
   T sc = sinc(PI * f * L * (1.0 - kn));
   Cx<T> pre(T(0.0), T(-PI * f * L) * sc);
-  Cx<T> ph = expi(T(-PI * f) * (L + kx));
+  Cx<T> ph = expi(T(-PI * f) * (L + 2.0 * kc)) * expi(T(-PI * f) * kd);
   return (pre * ph) * nhn;
 }
 
@@ -433,15 +448,15 @@ void tdi_xyz_mode(const OrConfig& cfg, const Source<T>& s, int l, int m, double 
   Cx<T> h[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) h[i][j] = H * (Pp * ep[i][j] + Pc * ec[i][j]);
-  T x[3][3];
-  orbit_pos(cfg, tf, x);
+  T c[3], d[3][3];
+  orbit_parts(cfg, tf, c, d);
   const double L = cfg.arm_m / C_SI;
   Cx<double> zd(std::cos(-2.0 * PI * f * L), std::sin(-2.0 * PI * f * L));
   Cx<T> z(T(zd.re), T(zd.im));
   Cx<T> z2 = z * z, z4 = z2 * z2, z6 = z4 * z2;
   Cx<T> one(T(1.0));
   Cx<T> fac = (cfg.tdi_gen == 15) ? (one - z2) : (one - z2 - z4 + z6);
-  auto y = [&](int r, int ss) { return link_response(cfg, k, h, x, f, r, ss); };
+  auto y = [&](int r, int ss) { return link_response(cfg, k, h, c, d, f, r, ss); };
   xyz[0] = fac * (y(1, 3) - y(1, 2) + z * (y(3, 1) - y(2, 1)));
   xyz[1] = fac * (y(2, 1) - y(2, 3) + z * (y(1, 2) - y(3, 2)));
   xyz[2] = fac * (y(3, 2) - y(3, 1) + z * (y(2, 3) - y(1, 3)));
@@ -614,9 +629,9 @@ void or_link(const OrConfig* cfg, const double* theta, int l, int m, const doubl
     mode_h(s, l, m, f[i], &H, &tf);
     Cx<double> h[3][3];
     for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) h[a][b] = H * (Pp * ep[a][b] + Pc * ec[a][b]);
-    double x[3][3];
-    orbit_pos(*cfg, std::isnan(t_fixed) ? tf : t_fixed, x);
-    Cx<double> y = link_response(*cfg, k, h, x, f[i], r, sidx);
+    double c[3], d[3][3];
+    orbit_parts(*cfg, std::isnan(t_fixed) ? tf : t_fixed, c, d);
+    Cx<double> y = link_response(*cfg, k, h, c, d, f[i], r, sidx);
     out[2 * i] = y.re; out[2 * i + 1] = y.im;
   }
 }
@@ -628,6 +643,20 @@ void or_response(const OrConfig* cfg, const double* theta, unsigned mode_mask, c
     Cx<double> aet[3];
     response_aet(*cfg, s, mode_mask, f[i], aet);
     for (int c = 0; c < 3; ++c) { out[(c * n + i) * 2] = aet[c].re; out[(c * n + i) * 2 + 1] = aet[c].im; }
+  }
+}
+
+// The same A/E/T response evaluated in long double (every step of the template above with the
+// scalar type long double): an extended-precision twin that bounds the double oracle's own
+// rounding, used only by the oracle's pins. out [3][n][2] (rounded back to double).
+void or_response_ld(const OrConfig* cfg, const double* theta, unsigned mode_mask, const double* f, int64_t n, double* out) {
+  long double th[11];
+  for (int i = 0; i < 11; ++i) th[i] = theta[i];
+  Source<long double> s = source_from(th);
+  for (int64_t i = 0; i < n; ++i) {
+    Cx<long double> aet[3];
+    response_aet(*cfg, s, mode_mask, f[i], aet);
+    for (int c = 0; c < 3; ++c) { out[(c * n + i) * 2] = (double)aet[c].re; out[(c * n + i) * 2 + 1] = (double)aet[c].im; }
   }
 }
 

@@ -45,12 +45,14 @@ def test_hetero_parity_with_oracle(oracle_mod, Lb, det, mix):
     gh = Lb.Hetero(gd, th0, W.MODE_ALL | (Lb.PE_PREC_MIXED if mix else 0), edges=edges)
     th = np.vstack([th0, _near(th0, 12, 5, 1.0)])
     g = Lb.hetero_loglike([gh], th, dhhh=True)
+    Q = H.floor_terms(oracle_mod, [od], th, W.MODE_ALL)
     for s in range(th.shape[0]):
         r = oh.loglike(th[s])
         sc = 0.5 * r["dd"].sum() + abs(r["dh"].sum()) + 0.5 * r["hh"].sum()
         assert abs(g["logl"][s] - r["logl"]) <= 1e-10 * sc, (s, g["logl"][s], r["logl"])
-        assert np.abs(g["dhhh"][s, 0, :, 0] - r["dh"]).max() <= 1e-10 * sc
-        assert np.abs(g["dhhh"][s, 0, :, 1] - r["hh"]).max() <= 1e-10 * sc
+        H.assert_loglike_parity({"logl": g["logl"][s:s + 1], "dhhh": g["dhhh"][s:s + 1]}, np.array([r["logl"]]),
+                                np.stack([r["dh"], r["hh"]], -1)[None, None], r["dd"], Q[s],
+                                u=H.U_DW if mix else H.U64, name="hetero:%s:%s" % (det["name"], mix))
     gh.close()
 
 
@@ -70,11 +72,14 @@ def test_hetero_network_parity(oracle_mod, Lb, mix):
         ghs.append(Lb.Hetero(gd, th0, W.MODE_ALL | (Lb.PE_PREC_MIXED if mix else 0), edges=e))
     th = np.vstack([th0, _near(th0, 6, 7, 1.0)])
     g = Lb.hetero_loglike(ghs, th, dhhh=True)
+    Q = H.floor_terms(oracle_mod, [o.odet for o in ohs], th, W.MODE_ALL)
     for s in range(th.shape[0]):
         r = HT.loglike_network(ohs, th[s])
         sc = 0.5 * r["dd"].sum() + abs(r["dh"].sum()) + 0.5 * r["hh"].sum()
         assert abs(g["logl"][s] - r["logl"]) <= 1e-10 * sc
-        assert np.abs(g["dhhh"][s, :, :, 0] - r["dh"]).max() <= 1e-10 * sc
+        H.assert_loglike_parity({"logl": g["logl"][s:s + 1], "dhhh": g["dhhh"][s:s + 1]}, np.array([r["logl"]]),
+                                np.stack([r["dh"], r["hh"]], -1)[None], r["dd"], Q[s],
+                                u=H.U_DW if mix else H.U64, name="hetero_network:%s" % mix)
 
 
 def test_hetero_against_exact_likelihood(Lb):

@@ -53,11 +53,10 @@ def test_mixed_signal_per_bin(oracle_mod, Lb, det, mask):
     hm = d.signal(th, mask | MIX)
     h64 = d.signal(th, mask)
     ref = oracle_mod.response(det, th, mask, H.grid_f(T, k0, nb))
-    ae = np.maximum(np.abs(ref[0]), np.abs(ref[1]))
+    phi = H.phase_magnitude(oracle_mod, th, mask, H.grid_f(T, k0, nb))
+    H.assert_signal_parity(hm, ref, "mixed_signal_per_bin:%s:%s:%#x" % (det["name"], det["tdi_gen"], mask), phi,
+                           u=H.U_DW)
     for c in range(3):
-        err = np.abs(hm[c] - ref[c])
-        tol = 1e-9 * np.abs(ref[c]) + 1e-11 * ae + 1e-12 * np.abs(ref[c]).max()
-        assert np.all(err <= tol), (c, np.max(err / (np.abs(ref[c]) + 1e-300)))
         # double words carry ~48-bit significands: a chain of ~100 operations stays near 1e-13 of
         # the single-link terms. At long wavelength (a = pi f L << 1) the TDI channels are O(a^2)
         # times those terms, so rounding in either path shows up amplified by 1/a^2 there.
@@ -84,7 +83,8 @@ def test_mixed_loglike_small_grids(oracle_mod, Lb, T, nbad):
     assert np.all(np.isneginf(g["logl"][bad]))
     good = ~bad
     H.assert_loglike_parity({"logl": g["logl"][good], "dhhh": g["dhhh"][good]}, ll[good], dhhh[good],
-                            _od_dd(oracle_mod, od))
+                            _od_dd(oracle_mod, od), H.floor_terms(oracle_mod, [od], th[good], W.MODE_ALL), u=H.U_DW,
+                            name="mixed")
 
 
 def test_mixed_loglike_edge_grids(oracle_mod, Lb):
@@ -96,7 +96,8 @@ def test_mixed_loglike_edge_grids(oracle_mod, Lb):
         th[1, 0] = 1e5
         g = Lb.loglike([gd], th, W.MODE_ALL | MIX, dhhh=True)
         ll, dhhh = oracle_mod.loglike_batch([od], th, W.MODE_ALL)
-        H.assert_loglike_parity(g, ll, dhhh, _od_dd(oracle_mod, od))
+        H.assert_loglike_parity(g, ll, dhhh, _od_dd(oracle_mod, od), H.floor_terms(oracle_mod, [od], th, W.MODE_ALL),
+                                u=H.U_DW, name="mixed")
 
 
 def test_mixed_single_source_full_grid(oracle_mod, Lb):
@@ -107,7 +108,8 @@ def test_mixed_single_source_full_grid(oracle_mod, Lb):
     th = np.vstack([wl["inj"], wl["inj"] + np.array([1e2, 1e-3, 0, 0, 0.1, 0.01, 0.1, 1e-3, 1e-3, 0.01, 5.0])])
     g = Lb.loglike([gd], th, wl["mode_mask"] | MIX, dhhh=True)
     ll, dhhh = oracle_mod.loglike_batch([od], th, wl["mode_mask"])
-    H.assert_loglike_parity(g, ll, dhhh, _od_dd(oracle_mod, od))
+    H.assert_loglike_parity(g, ll, dhhh, _od_dd(oracle_mod, od), H.floor_terms(oracle_mod, [od], th, wl["mode_mask"]),
+                            u=H.U_DW, name="mixed")
 
 
 def test_mixed_network(oracle_mod, Lb):
@@ -123,7 +125,7 @@ def test_mixed_network(oracle_mod, Lb):
     g = Lb.loglike(gds, th, W.MODE_ALL | MIX, dhhh=True)
     ll, dhhh = oracle_mod.loglike_batch(ods, th, W.MODE_ALL)
     dd = np.array([_od_dd(oracle_mod, od)[0] for od in ods])
-    H.assert_loglike_parity(g, ll, dhhh, dd)
+    H.assert_loglike_parity(g, ll, dhhh, dd, H.floor_terms(oracle_mod, ods, th, W.MODE_ALL), u=H.U_DW, name="mixed")
 
 
 def test_mixed_full_size_sampled(oracle_mod, Lb):
@@ -138,7 +140,8 @@ def test_mixed_full_size_sampled(oracle_mod, Lb):
     order = np.argsort(th[:, 0])
     pick = np.unique(np.r_[order[:3], order[np.linspace(200, 1023, 13).astype(int)]])
     ll, dhhh = oracle_mod.loglike_batch([od], th[pick], wl["mode_mask"])
-    H.assert_loglike_parity({"logl": g["logl"][pick], "dhhh": g["dhhh"][pick]}, ll, dhhh, _od_dd(oracle_mod, od))
+    H.assert_loglike_parity({"logl": g["logl"][pick], "dhhh": g["dhhh"][pick]}, ll, dhhh, _od_dd(oracle_mod, od),
+                            H.floor_terms(oracle_mod, [od], th[pick], wl["mode_mask"]), u=H.U_DW, name="mixed")
     # every sample against the GPU FP64 path, on the same scale
     g64 = Lb.loglike([gd], th, wl["mode_mask"], dhhh=True)
     sc = 0.5 * gd.data_norm().sum() + np.abs(g64["dhhh"][:, 0, :, 0].sum(1)) + 0.5 * g64["dhhh"][:, 0, :, 1].sum(1)

@@ -53,13 +53,8 @@ def test_signal_parity_per_bin(oracle_mod, Lb, det, mask):
     d = Lb.Detector(det, T, k0, nb)
     h = d.signal(th, mask)
     ref = oracle_mod.response(det, th, mask, H.grid_f(T, k0, nb))
-    # T = (X + Y + Z)/sqrt3 cancels to O((fL)^2) of X: its rounding is set by the bin's A/E size
-    # (the oracle differences AU-sized positions, an absolute error ~1e-13 of X per bin)
-    ae = np.maximum(np.abs(ref[0]), np.abs(ref[1]))
-    for c in range(3):
-        err = np.abs(h[c] - ref[c])
-        tol = 1e-9 * np.abs(ref[c]) + 1e-11 * ae + 1e-12 * np.abs(ref[c]).max()
-        assert np.all(err <= tol), (c, np.max(err / (np.abs(ref[c]) + 1e-300)))
+    phi = H.phase_magnitude(oracle_mod, th, mask, H.grid_f(T, k0, nb))
+    H.assert_signal_parity(h, ref, "signal_per_bin:%s:%s:%#x" % (det["name"], det["tdi_gen"], mask), phi)
 
 
 def test_injection_parity(oracle_mod, Lb):
@@ -86,7 +81,7 @@ def test_loglike_single_source_full_grid(oracle_mod, Lb):
     th = np.vstack([wl["inj"], wl["inj"] + np.array([1e2, 1e-3, 0, 0, 0.1, 0.01, 0.1, 1e-3, 1e-3, 0.01, 5.0])])
     g = Lb.loglike([gd], th, wl["mode_mask"], dhhh=True)
     ll, dhhh = oracle_mod.loglike_batch([od], th, wl["mode_mask"])
-    H.assert_loglike_parity(g, ll, dhhh, od_dd(oracle_mod, od))
+    H.assert_loglike_parity(g, ll, dhhh, od_dd(oracle_mod, od), H.floor_terms(oracle_mod, [od], th, wl["mode_mask"]))
     np.testing.assert_allclose(gd.data_norm(), od_dd(oracle_mod, od)[0], rtol=1e-12)
 
 
@@ -114,7 +109,7 @@ def test_loglike_batch_hm_small_grids(oracle_mod, Lb, T, nbad):
     assert np.all(np.isneginf(g["logl"][bad]))
     good = ~bad
     H.assert_loglike_parity({"logl": g["logl"][good], "dhhh": g["dhhh"][good]}, ll[good], dhhh[good],
-                            od_dd(oracle_mod, od))
+                            od_dd(oracle_mod, od), H.floor_terms(oracle_mod, [od], th[good], W.MODE_ALL))
 
 
 def test_loglike_edge_grids(oracle_mod, Lb):
@@ -127,7 +122,7 @@ def test_loglike_edge_grids(oracle_mod, Lb):
         th[1, 0] = 1e5
         g = Lb.loglike([gd], th, W.MODE_ALL, dhhh=True)
         ll, dhhh = oracle_mod.loglike_batch([od], th, W.MODE_ALL)
-        H.assert_loglike_parity(g, ll, dhhh, od_dd(oracle_mod, od))
+        H.assert_loglike_parity(g, ll, dhhh, od_dd(oracle_mod, od), H.floor_terms(oracle_mod, [od], th, W.MODE_ALL))
 
 
 def test_maximum_batch_and_detector_count(oracle_mod, Lb):
@@ -148,7 +143,8 @@ def test_maximum_batch_and_detector_count(oracle_mod, Lb):
     assert np.all(np.isfinite(out))
     pick = np.r_[0, 1, B // 2, B - 1, np.random.Generator(np.random.PCG64(3)).choice(B, 6, replace=False)]
     ll, dhhh = oracle_mod.loglike_batch([od], th[pick], W.MODE_ALL)
-    H.assert_loglike_parity({"logl": out[pick], "dhhh": dh[pick]}, ll, dhhh, od_dd(oracle_mod, od))
+    H.assert_loglike_parity({"logl": out[pick], "dhhh": dh[pick]}, ll, dhhh, od_dd(oracle_mod, od),
+                            H.floor_terms(oracle_mod, [od], th[pick], W.MODE_ALL))
     small = Lb.loglike([gd], th[pick], W.MODE_ALL)
     assert np.array_equal(small["logl"], out[pick])
     with pytest.raises(Lb.PeError) as e:
@@ -168,7 +164,7 @@ def test_maximum_batch_and_detector_count(oracle_mod, Lb):
     g8 = Lb.loglike(gds, th8, W.MODE_ALL, dhhh=True)
     ll8, dhhh8 = oracle_mod.loglike_batch(ods, th8, W.MODE_ALL)
     dd8 = np.array([od_dd(oracle_mod, o) for o in ods])
-    H.assert_loglike_parity(g8, ll8, dhhh8, dd8)
+    H.assert_loglike_parity(g8, ll8, dhhh8, dd8, H.floor_terms(oracle_mod, ods, th8, W.MODE_ALL))
     with pytest.raises(Lb.PeError) as e:
         Lb.loglike(gds + gds[:1], th8, W.MODE_ALL)
     assert e.value.status == Lb.PE_EINVAL
@@ -189,7 +185,7 @@ def test_network_parity(oracle_mod, Lb):
     g = Lb.loglike(gds, th, W.MODE_ALL, dhhh=True)
     ll, dhhh = oracle_mod.loglike_batch(ods, th, W.MODE_ALL)
     dd = np.array([od_dd(oracle_mod, od)[0] for od in ods])
-    H.assert_loglike_parity(g, ll, dhhh, dd)
+    H.assert_loglike_parity(g, ll, dhhh, dd, H.floor_terms(oracle_mod, ods, th, W.MODE_ALL))
 
 
 def test_batch_invariance_bitwise(oracle_mod, Lb):
@@ -258,4 +254,5 @@ def test_full_size_hm_batch_sampled(oracle_mod, Lb):
     order = np.argsort(th[:, 0])
     pick = np.unique(np.r_[order[:3], order[np.linspace(200, 1023, 13).astype(int)]])
     ll, dhhh = oracle_mod.loglike_batch([od], th[pick], wl["mode_mask"])
-    H.assert_loglike_parity({"logl": g["logl"][pick], "dhhh": g["dhhh"][pick]}, ll, dhhh, od_dd(oracle_mod, od))
+    H.assert_loglike_parity({"logl": g["logl"][pick], "dhhh": g["dhhh"][pick]}, ll, dhhh, od_dd(oracle_mod, od),
+                            H.floor_terms(oracle_mod, [od], th[pick], wl["mode_mask"]))

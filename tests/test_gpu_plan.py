@@ -129,5 +129,6 @@ def test_network_full_size_plan_sampled(oracle_mod, Lb):
     pick = np.r_[order[-5:], order[len(order) // 2]]
     ll, ref = oracle_mod.loglike_batch(ods, th[pick], wl["mode_mask"])
     dd = np.array([oracle_mod.loglike([od], th[0], 0)["dd"][0] for od in ods])
-    H.assert_loglike_parity({"logl": logl[pick], "dhhh": dhhh[pick]}, ll, ref, dd)
+    H.assert_loglike_parity({"logl": logl[pick], "dhhh": dhhh[pick]}, ll, ref, dd,
+                            H.floor_terms(oracle_mod, ods, th[pick], wl["mode_mask"]))
     plan.close()

@@ -66,7 +66,9 @@ def test_tdi15_tdi20_likelihood_agree(oracle_mod, Lb, pair, mixed):
     for gen, g in ((15, g15), (20, g20)):
         ll, dhhh = oracle_mod.loglike_batch([out[gen][0]], th[:4], W.MODE_ALL)
         H.assert_loglike_parity({"logl": g["logl"][:4], "dhhh": g["dhhh"][:4]}, ll, dhhh,
-                                np.array([out[gen][1].data_norm()]))
+                                np.array([out[gen][1].data_norm()]),
+                                H.floor_terms(oracle_mod, [out[gen][0]], th[:4], W.MODE_ALL),
+                                u=H.U_DW if mixed else H.U64, name="tdi%d" % gen)
 
 
 def test_tdi15_tdi20_gradient_and_fisher_agree(Lb, pair):

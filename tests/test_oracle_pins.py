@@ -772,6 +772,37 @@ def test_psd_aet_is_rotation_of_xyz_covariance(oracle_mod):
             assert np.abs(Ca - np.diag(np.diag(Ca))).max() < 1e-13 * SX[i] * fac[i]
 
 
+def test_oracle_rounding_against_long_double(oracle_mod):
+    """The oracle's own FP64 rounding, measured against the same template evaluated in long double
+    (or_response_ld), stays inside the rounding floor the GPU parity tests allow (tests/_helpers.py):
+    per bin 1e-10 |h| + 32 u (Phi |h| + max(|A|, |E|) + max |h|) (the GPU bar takes 64), and per
+    channel <h|h> within 1e-10 <h|h> + 2 u sqrt(<h|h> Q) (the GPU bar takes 8x that). On this x86
+    host long double has a 64-bit significand; the check is skipped where long double is double."""
+    from tests import _helpers as H
+    if np.finfo(np.longdouble).nmant < 60:
+        pytest.skip("long double has no extra precision on this platform")
+    T = 2.0 ** 16
+    k0, nb = W.grid(T)
+    f = H.grid_f(T, k0, nb)
+    ths = [np.array([3e5, 2.0, 0.5, 0.3, 25.8, 0.4, 1.3, 1.375, -1.2108, 2.659, 0.8 * T]),
+           np.array([1e5, 7.0, -0.5, 0.9, 5.0, 2.4, 0.3, 4.0, 0.9, 0.6, 0.78 * T])] + list(W.draw_prior(3, 5, T))
+    for det in (W.LISA, W.TIANQIN, dict(W.LISA, tdi_gen=15), W.TAIJI):
+        w = 4.0 / (oracle_mod.psd(det, f) * T)
+        for th in ths:
+            for mask in (0x01, 0x10, 0x1F):
+                a = oracle_mod.response(det, th, mask, f)
+                b = oracle_mod.response_ld(det, th, mask, f)
+                phi = H.phase_magnitude(oracle_mod, th, mask, f)
+                ae = np.maximum(np.abs(b[0]), np.abs(b[1]))
+                for c in range(3):
+                    tol = 1e-10 * np.abs(b[c]) + 32 * H.U64 * (phi * np.abs(b[c]) + ae + np.abs(b[c]).max())
+                    assert np.all(np.abs(a[c] - b[c]) <= tol), (det["name"], th[0], mask, c)
+                hh_a, hh_b = np.sum(w * np.abs(a) ** 2, axis=1), np.sum(w * np.abs(b) ** 2, axis=1)
+                Q = np.sum(w * (ae[None, :] ** 2 + phi[None, :] ** 2 * np.abs(b) ** 2), axis=1)
+                assert np.all(np.abs(hh_a - hh_b) <= 1e-10 * hh_b + 2 * H.U64 * np.sqrt(hh_b * Q)), (
+                    det["name"], th[0], mask, np.abs(hh_a - hh_b) / hh_b)
+
+
 def _welch_psd(x, dt, nseg):
     """One-sided PSD of a real series by Welch averaging (Hann window, no overlap):
     P_k = 2 dt |sum_n w_n x_n e^{-2 pi i k n/N}|^2 / sum_n w_n^2, averaged over segments."""
