@@ -32,6 +32,7 @@
 #include "pe_kernels.h"
 #include "pe_mlp.h"
 #include "pe_surrogate.h"
+#include "pe_fault.h"
 
 namespace pe {
 
@@ -174,8 +175,10 @@ __global__ void k_standardize(float* T, long long n, const float* mean, const fl
   T[i] = (T[i] - mean[c]) / stdv[c];
 }
 
-__global__ void k_gather_rows(const __nv_bfloat16* X, const float* T, const int* idx, int b, __nv_bfloat16* Xb,
-                              float* Tb) {
+// Minibatch rows of the step ctr[0]: rows idx_all[ctr[0] b + r], r < b.
+__global__ void k_gather_rows(const __nv_bfloat16* X, const float* T, const int* idx_all, const int* ctr, int b,
+                              __nv_bfloat16* Xb, float* Tb) {
+  const int* idx = idx_all + (size_t)ctr[0] * b;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < (long long)b * kNin) {
     const int r = (int)(i / kNin), c = (int)(i % kNin);
@@ -497,7 +500,7 @@ struct Layer {
 
 template <class T>
 cudaError_t dalloc(T** p, size_t n) {
-  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T) + 16);
+  return pe::dmalloc(reinterpret_cast<void**>(p), n * sizeof(T) + 16);
 }
 
 }  // namespace
@@ -524,11 +527,22 @@ namespace {
 
 pe_status sfail(pe_status st, const char* msg) { return pe::set_error(st, msg); }
 
+// Status of the tensor-core GEMMs launched since the last check (their barrier waits are bounded
+// and record a code instead of hanging).
+pe_status gemm_status(const char* who) {
+  const int code = pe::umma_take_error();
+  if (code == 0) return PE_OK;
+  char msg[160];
+  snprintf(msg, sizeof(msg), "%s: tensor-core GEMM barrier wait timed out (code %d)", who, code);
+  return sfail(PE_ECUDA, msg);
+}
+
+
 void free_batch(pe_surrogate_s* s) {
   void* ptrs[] = {s->X, s->H[0], s->H[1], s->H[2], s->HT[0], s->HT[1], s->HT[2], s->XT, s->dY, s->dYT, s->dZ,
                   s->dZT, s->Z[0], s->Z[1], s->Z[2], s->Y, s->dYf, s->dH, s->dZf, s->Tb, s->part};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) pe::dfree(p);
   s->X = s->XT = s->dY = s->dYT = s->dZ = s->dZT = nullptr;
   for (int i = 0; i < 3; ++i) { s->H[i] = s->HT[i] = nullptr; s->Z[i] = nullptr; }
   s->Y = s->dYf = s->dH = s->dZf = s->Tb = nullptr;
@@ -582,8 +596,30 @@ cudaError_t mlp_forward(pe_surrogate_s* s, int Bp, cudaStream_t st) {
   return e;
 }
 
-// backward from dY (bf16 + fp32 in s->dY, s->dYf) into every layer's gW, gb
-cudaError_t mlp_backward(pe_surrogate_s* s, int Bp, cudaStream_t st) {
+// Host copy of the intermediates of one forward + backward pass (the elementwise checks of the
+// dense layers): fp32 buffers as they are, bf16 buffers widened to fp32.
+struct MlpTrace {
+  float* host = nullptr;
+  size_t off = 0;
+  cudaError_t err = cudaSuccess;
+  void f32(const float* dev, size_t n) {
+    if (err == cudaSuccess) err = cudaMemcpy(host + off, dev, n * sizeof(float), cudaMemcpyDeviceToHost);
+    off += n;
+  }
+  void b16(const bf16* dev, size_t n) {
+    std::vector<uint16_t> tmp(n);
+    if (err == cudaSuccess) err = cudaMemcpy(tmp.data(), dev, n * sizeof(uint16_t), cudaMemcpyDeviceToHost);
+    for (size_t i = 0; i < n && err == cudaSuccess; ++i) {
+      const uint32_t bits = (uint32_t)tmp[i] << 16;
+      std::memcpy(host + off + i, &bits, sizeof(float));
+    }
+    off += n;
+  }
+};
+
+// backward from dY (bf16 + fp32 in s->dY, s->dYf) into every layer's gW, gb; with a trace, each
+// layer's incoming cotangent dH and its dZ (fp32 and bf16) are copied out as they are formed
+cudaError_t mlp_backward(pe_surrogate_s* s, int Bp, cudaStream_t st, MlpTrace* tr = nullptr) {
   cudaError_t e = pe::transpose_bf16(s->dY, s->dYT, Bp, pe::kNout, st);
   if (e == cudaSuccess) e = pe::transpose_bf16(s->H[2], s->HT[2], Bp, pe::kHid, st);
   // layer 3: gW3 [2560][256] = dY^T H2; gb3 = colsum dY; dH2 = dY W3
@@ -595,6 +631,12 @@ cudaError_t mlp_backward(pe_surrogate_s* s, int Bp, cudaStream_t st) {
     bf16* HinT = (l == 0) ? s->XT : s->HT[l - 1];
     const int nin = (l == 0) ? pe::kNin : pe::kHid;
     e = pe::silu_bwd(s->dH, s->Z[l], s->dZ, s->dZf, (size_t)Bp * pe::kHid, st);
+    if (tr && e == cudaSuccess) {
+      tr->f32(s->dH, (size_t)Bp * pe::kHid);
+      tr->f32(s->dZf, (size_t)Bp * pe::kHid);
+      tr->b16(s->dZ, (size_t)Bp * pe::kHid);
+      e = tr->err;
+    }
     if (e == cudaSuccess) e = pe::transpose_bf16(s->dZ, s->dZT, Bp, pe::kHid, st);
     if (e == cudaSuccess) e = pe::transpose_bf16(Hin, HinT, Bp, nin, st);
     if (e == cudaSuccess) e = pe::gemm_tn(s->dZT, HinT, s->L[l].gW, pe::kHid, nin, Bp, 0, nullptr, nullptr, st);
@@ -642,19 +684,19 @@ pe_status pe_surrogate_create(uint64_t seed, pe_surrogate* out) {
     std::uniform_real_distribution<double> U(-lim, lim);
     std::vector<float> w(nw), z(nw, 0.f), zb(L.out, 0.f);
     for (size_t i = 0; i < nw; ++i) w[i] = (l == 0 && (int)(i % L.in) >= PE_NPARAM) ? 0.f : (float)U(rng);
-    e = cudaMemcpy(L.W, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L.mW, z.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L.vW, z.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L.b, zb.data(), L.out * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L.mb, zb.data(), L.out * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L.vb, zb.data(), L.out * sizeof(float), cudaMemcpyHostToDevice);
+    e = pe::upload(L.W, w.data(), nw * sizeof(float));
+    if (e == cudaSuccess) e = pe::upload(L.mW, z.data(), nw * sizeof(float));
+    if (e == cudaSuccess) e = pe::upload(L.vW, z.data(), nw * sizeof(float));
+    if (e == cudaSuccess) e = pe::upload(L.b, zb.data(), L.out * sizeof(float));
+    if (e == cudaSuccess) e = pe::upload(L.mb, zb.data(), L.out * sizeof(float));
+    if (e == cudaSuccess) e = pe::upload(L.vb, zb.data(), L.out * sizeof(float));
   }
   if (e == cudaSuccess) e = dalloc(&s->mean, pe::kNout);
   if (e == cudaSuccess) e = dalloc(&s->stdv, pe::kNout);
   if (e == cudaSuccess) {
     std::vector<float> zero(pe::kNout, 0.f), one(pe::kNout, 1.f);
-    e = cudaMemcpy(s->mean, zero.data(), pe::kNout * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->stdv, one.data(), pe::kNout * sizeof(float), cudaMemcpyHostToDevice);
+    e = pe::upload(s->mean, zero.data(), pe::kNout * sizeof(float));
+    if (e == cudaSuccess) e = pe::upload(s->stdv, one.data(), pe::kNout * sizeof(float));
   }
   if (e == cudaSuccess) e = refresh_bf16(s, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -662,6 +704,11 @@ pe_status pe_surrogate_create(uint64_t seed, pe_surrogate* out) {
     cudaGetLastError();
     pe_surrogate_destroy(s);
     return sfail(PE_ENOMEM, "pe_surrogate_create: device allocation failed");
+  }
+  if (pe::umma_prepare() != cudaSuccess) {
+    cudaGetLastError();
+    pe_surrogate_destroy(s);
+    return sfail(PE_ECUDA, "pe_surrogate_create: the tensor-core GEMM cannot be set up on this device");
   }
   *out = s;
   return PE_OK;
@@ -675,10 +722,10 @@ pe_status pe_surrogate_destroy(pe_surrogate s) {
     Layer& L = s->L[l];
     void* ptrs[] = {L.W, L.b, L.mW, L.vW, L.mb, L.vb, L.gW, L.gb, L.Wb, L.WTb};
     for (void* p : ptrs)
-      if (p) cudaFree(p);
+      if (p) pe::dfree(p);
   }
-  if (s->mean) cudaFree(s->mean);
-  if (s->stdv) cudaFree(s->stdv);
+  if (s->mean) pe::dfree(s->mean);
+  if (s->stdv) pe::dfree(s->stdv);
   cudaGetLastError();
   delete s;
   return PE_OK;
@@ -707,11 +754,11 @@ pe_status pe_surrogate_targets(const double* theta_dev, int B, float* out_dev) {
     pe::k_sur_prep<<<(B + 63) / 64, 64>>>(theta_dev, B, PE_MODE_ALL, S, S0);
     const long long n = (long long)B * pe::kNModes * pe::kNodes;
     pe::k_targets<<<(unsigned)((n + 255) / 256), 256>>>(theta_dev, B, S, S0, out_dev);
-    e = cudaGetLastError();
+    e = pe::launch_status();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
-  if (S) cudaFree(S);
-  if (S0) cudaFree(S0);
+  if (S) pe::dfree(S);
+  if (S0) pe::dfree(S0);
   if (e != cudaSuccess) { cudaGetLastError(); return sfail(PE_ECUDA, "pe_surrogate_targets failed"); }
   return PE_OK;
 }
@@ -726,13 +773,13 @@ pe_status pe_surrogate_train(pe_surrogate s, const double* theta_train_dev, int 
   int* idx_d = nullptr;
   cudaError_t e = dalloc(&T, nt * pe::kNout);
   if (e == cudaSuccess) e = dalloc(&Xall, nt * pe::kNin);
-  if (e == cudaSuccess) e = dalloc(&idx_d, (size_t)batch);
+  if (e == cudaSuccess) e = dalloc(&idx_d, nt);
   if (e == cudaSuccess) e = ensure_batch(s, batch);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    if (T) cudaFree(T);
-    if (Xall) cudaFree(Xall);
-    if (idx_d) cudaFree(idx_d);
+    if (T) pe::dfree(T);
+    if (Xall) pe::dfree(Xall);
+    if (idx_d) pe::dfree(idx_d);
     return sfail(PE_ENOMEM, "pe_surrogate_train: allocation failed");
   }
   pe_status st = PE_OK;
@@ -747,59 +794,88 @@ pe_status pe_surrogate_train(pe_surrogate s, const double* theta_train_dev, int 
     const long long n = (long long)nt * pe::kNout;
     pe::k_standardize<<<(unsigned)((n + 255) / 256), 256>>>(T, (long long)nt, s->mean, s->stdv);
     pe::k_features<<<(n_train + 127) / 128, 128>>>(theta_train_dev, n_train, n_train, Xall);
-    e = cudaGetLastError();
+    e = pe::launch_status();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) st = sfail(PE_ECUDA, "pe_surrogate_train: target preparation failed");
   }
+  // One training step -- minibatch gather, forward, loss, backward, Adam, bf16 refresh, step
+  // counters -- is captured once as a CUDA graph and replayed for every step: the per-epoch
+  // permutation lives on the device, and the step's schedule (learning rate, Adam bias
+  // corrections, minibatch offset) comes from device counters.
   std::mt19937_64 rng(s->seed ^ 0x9e3779b97f4a7c15ull);
   std::vector<int> perm(nt);
   for (size_t i = 0; i < nt; ++i) perm[i] = (int)i;
   const int steps = n_train / batch;
   const int total_steps = steps * epochs;
+  const long long ng = (long long)batch * pe::kNout;
+  int nblk = 0;
+  int* ctr = nullptr;
+  float* par = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (st == PE_OK) {
+    e = dalloc(&ctr, 4);
+    if (e == cudaSuccess) e = dalloc(&par, 4);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    const int ctr0[4] = {0, 0, s->adam_t, 0};
+    if (e == cudaSuccess) e = pe::upload(ctr, ctr0, sizeof(ctr0));
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t c = pe::train_step_params(ctr, par, lr, total_steps, 0.9f, 0.999f, cs);
+      if (c == cudaSuccess) {
+        pe::k_gather_rows<<<(unsigned)((ng + 255) / 256), 256, 0, cs>>>(Xall, T, idx_d, ctr, batch, s->X, s->Tb);
+        c = pe::launch_status();
+      }
+      if (c == cudaSuccess) c = mlp_forward(s, batch, cs);
+      if (c == cudaSuccess) c = pe::mse(s->Y, s->Tb, s->dYf, s->dY, s->part, (size_t)ng, 1.0f / (float)ng, &nblk, cs);
+      if (c == cudaSuccess) c = mlp_backward(s, batch, cs);
+      for (int l = 0; l < 4 && c == cudaSuccess; ++l) {
+        Layer& L = s->L[l];
+        c = pe::adam(L.W, L.gW, L.mW, L.vW, (size_t)L.in * L.out, par, 0.9f, 0.999f, 1e-8f, cs);
+        if (c == cudaSuccess) c = pe::adam(L.b, L.gb, L.mb, L.vb, L.out, par, 0.9f, 0.999f, 1e-8f, cs);
+      }
+      if (c == cudaSuccess) c = refresh_bf16(s, cs);
+      if (c == cudaSuccess) c = pe::train_step_advance(ctr, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = c;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) st = sfail(PE_ECUDA, "pe_surrogate_train: capturing the training step failed");
+  }
   std::vector<double> hpart;
   double last = 0.0;
-  int gstep = 0;
   for (int ep = 0; ep < epochs && st == PE_OK; ++ep) {
     std::shuffle(perm.begin(), perm.end(), rng);
-    double ep_loss = 0.0;
-    for (int k = 0; k < steps && st == PE_OK; ++k, ++gstep) {
-      e = cudaMemcpy(idx_d, perm.data() + (size_t)k * batch, batch * sizeof(int), cudaMemcpyHostToDevice);
-      const long long ng = (long long)batch * pe::kNout;
-      if (e == cudaSuccess) {
-        pe::k_gather_rows<<<(unsigned)((ng + 255) / 256), 256>>>(Xall, T, idx_d, batch, s->X, s->Tb);
-        e = cudaGetLastError();
-      }
-      if (e == cudaSuccess) e = mlp_forward(s, batch, 0);
-      int nblk = 0;
-      if (e == cudaSuccess)
-        e = pe::mse(s->Y, s->Tb, s->dYf, s->dY, s->part, (size_t)ng, 1.0f / (float)ng, &nblk, 0);
-      if (e == cudaSuccess) e = mlp_backward(s, batch, 0);
-      // cosine learning-rate schedule
-      const double frac = (double)gstep / (double)std::max(1, total_steps - 1);
-      const float lr_t = (float)(lr * (0.02 + 0.98 * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))));
-      ++s->adam_t;
-      for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
-        Layer& L = s->L[l];
-        e = pe::adam(L.W, L.gW, L.mW, L.vW, nullptr, (size_t)L.in * L.out, lr_t, 0.9f, 0.999f, 1e-8f, s->adam_t, 0);
-        if (e == cudaSuccess) e = pe::adam(L.b, L.gb, L.mb, L.vb, nullptr, L.out, lr_t, 0.9f, 0.999f, 1e-8f, s->adam_t, 0);
-      }
-      if (e == cudaSuccess) e = refresh_bf16(s, 0);
-      if (e == cudaSuccess && k == steps - 1) {
-        hpart.resize(nblk);
-        e = cudaMemcpy(hpart.data(), s->part, nblk * sizeof(double), cudaMemcpyDeviceToHost);
-        double sum = 0.0;
-        for (double x : hpart) sum += x;
-        ep_loss = sum / (double)ng;
-      }
-      if (e != cudaSuccess) st = sfail(PE_ECUDA, "pe_surrogate_train: training step failed");
+    e = pe::upload_async(idx_d, perm.data(), nt * sizeof(int), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, sizeof(int), cs);   // step within the epoch
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, cs);
+    // loss of the epoch's last minibatch (its partial sums are left in s->part)
+    hpart.resize(nblk);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hpart.data(), s->part, nblk * sizeof(double), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+      st = sfail(PE_ECUDA, "pe_surrogate_train: training step failed");
+      break;
     }
-    last = ep_loss;
-    if (out_loss_curve) out_loss_curve[ep] = (float)ep_loss;
+    double sum = 0.0;
+    for (double x : hpart) sum += x;
+    last = sum / (double)ng;
+    if (out_loss_curve) out_loss_curve[ep] = (float)last;
   }
-  cudaFree(T);
-  cudaFree(Xall);
-  cudaFree(idx_d);
+  if (st == PE_OK) s->adam_t += total_steps;
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (ctr) pe::dfree(ctr);
+  if (par) pe::dfree(par);
+  if (st == PE_OK && cudaDeviceSynchronize() != cudaSuccess) st = sfail(PE_ECUDA, "pe_surrogate_train: training failed");
+  pe::dfree(T);
+  pe::dfree(Xall);
+  pe::dfree(idx_d);
   if (st != PE_OK) { cudaGetLastError(); return st; }
+  st = gemm_status("pe_surrogate_train");
+  if (st != PE_OK) return st;
   s->trained = 1;
   if (out_final_loss) *out_final_loss = last;
   return PE_OK;
@@ -812,17 +888,17 @@ pe_status pe_surrogate_predict(pe_surrogate s, const double* theta_dev, int B, f
   cudaError_t e = ensure_batch(s, Bp);
   if (e == cudaSuccess) {
     pe::k_features<<<(Bp + 127) / 128, 128>>>(theta_dev, B, Bp, s->X);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess) e = mlp_forward(s, Bp, 0);
   if (e == cudaSuccess) {
     const long long n = (long long)B * pe::kNout;
     pe::k_destd<<<(unsigned)((n + 255) / 256), 256>>>(s->Y, B, s->mean, s->stdv, out_dev);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { cudaGetLastError(); return sfail(PE_ECUDA, "pe_surrogate_predict failed"); }
-  return PE_OK;
+  return gemm_status("pe_surrogate_predict");
 }
 
 // Shared driver of the surrogate log-likelihood (mode 0) and the mismatch study (mode 1).
@@ -842,7 +918,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   auto aalloc = [&](auto** p, size_t n) {
     if (e != cudaSuccess) return;
     void* q = nullptr;
-    e = cudaMallocAsync(&q, n * sizeof(**p) + 16, st);
+    e = pe::dmalloc_async(&q, n * sizeof(**p) + 16, st);
     if (e == cudaSuccess) { bufs.push_back(q); *p = static_cast<std::remove_pointer_t<decltype(p)>>(q); }
   };
   pe::SampleCoef *S = nullptr, *S0 = nullptr;
@@ -865,7 +941,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   if (e == cudaSuccess) {
     // MLP inference (BF16 tensor cores) -> de-standardised node values
     pe::k_features<<<(Bp + 127) / 128, 128, 0, st>>>(theta_dev, B, Bp, s->X);
-    e = cudaGetLastError();
+    e = pe::launch_status();
     if (e == cudaSuccess && s->node_source == 0) e = mlp_forward(s, Bp, st);
   }
   if (e == cudaSuccess) {
@@ -880,7 +956,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     pe::k_node_h<<<(B * pe::kNModes + 127) / 128, 128, 0, st>>>(theta_dev, B, hs);
     const long long nn = (long long)nsys * pe::kNodes;
     pe::k_sur_nodes<<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(ds, B, S, S0, Yd, theta_dev, s->box, nodes);
-    e = cudaGetLastError();
+    e = pe::launch_status();
     // the spline kernel reads the node spacing per system (I, s, md): replicate per detector
     for (int I = 0; I < ndet && e == cudaSuccess; ++I)
       e = cudaMemcpyAsync(hs_sys + (size_t)I * B * pe::kNModes, hs, (size_t)B * pe::kNModes * sizeof(double),
@@ -888,7 +964,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     if (e == cudaSuccess) {
       const long long ns = (long long)nsys * pe::kQ;
       pe::k_spline<<<(unsigned)((ns + 63) / 64), 64, 0, st>>>(nodes, ns, hs_sys, spl, splt);
-      e = cudaGetLastError();
+      e = pe::launch_status();
     }
   }
   if (e == cudaSuccess) e = pe::launch_prep(theta_dev, B, mode_mask, ds, S, nend, nullptr, st);
@@ -900,21 +976,21 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     const long long g = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * 8));
     pe::k_sur_fwd<<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
                                                           part, mode);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess) {
     if (mode == 0) {
       e = pe::launch_reduce(ds, B, off, part, S, out0, nullptr, st);
       if (e == cudaSuccess && used) {
         pe::k_used<<<(B + 127) / 128, 128, 0, st>>>(theta_dev, B, s->box, S, used);
-        e = cudaGetLastError();
+        e = pe::launch_status();
       }
     } else {
       pe::k_mismatch_reduce<<<(B + 127) / 128, 128, 0, st>>>(ndet, B, off, part, S, out0);
-      e = cudaGetLastError();
+      e = pe::launch_status();
     }
   }
-  for (void* p : bufs) cudaFreeAsync(p, st);
+  for (void* p : bufs) pe::dfree_async(p, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     char msg[256];
@@ -940,19 +1016,31 @@ pe_status pe_surrogate_mismatch(pe_surrogate s, pe_detector det, const double* t
 // gradient checks: x [B][64] (fp32, rounded to bf16 on the device), dy [B][2560]; returns the raw
 // (standardised-space) outputs y [B][2560] and the gradients of every layer, concatenated as
 // gW0, gb0, gW1, gb1, gW2, gb2, gW3, gb3 (weights [out][in]). B must be a multiple of 64.
-pe_status pe_surrogate_mlp_debug(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads) {
+static pe_status mlp_debug_impl(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads,
+                                float* trace) {
   if (!s || !x || !dy || !y || !grads || B < 64 || B % 64) return sfail(PE_EINVAL, "pe_surrogate_mlp_debug: bad arguments");
   cudaError_t e = ensure_batch(s, B);
   float* tmp = nullptr;
-  const size_t nx = (size_t)B * pe::kNin, ny = (size_t)B * pe::kNout;
+  const size_t nx = (size_t)B * pe::kNin, ny = (size_t)B * pe::kNout, nh = (size_t)B * pe::kHid;
+  MlpTrace tr;
+  tr.host = trace;
   if (e == cudaSuccess) e = dalloc(&tmp, std::max(nx, ny));
-  if (e == cudaSuccess) e = cudaMemcpy(tmp, x, nx * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pe::upload(tmp, x, nx * sizeof(float));
   if (e == cudaSuccess) e = pe::f32_to_bf16(tmp, s->X, nx, 0);
   if (e == cudaSuccess) e = mlp_forward(s, B, 0);
   if (e == cudaSuccess) e = cudaMemcpy(y, s->Y, ny * sizeof(float), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(s->dYf, dy, ny * sizeof(float), cudaMemcpyHostToDevice);
+  if (trace && e == cudaSuccess) {
+    tr.b16(s->X, nx);
+    for (int l = 0; l < 3; ++l) {
+      tr.f32(s->Z[l], nh);
+      tr.b16(s->H[l], nh);
+    }
+    tr.f32(s->Y, ny);
+    e = tr.err;
+  }
+  if (e == cudaSuccess) e = pe::upload(s->dYf, dy, ny * sizeof(float));
   if (e == cudaSuccess) e = pe::f32_to_bf16(s->dYf, s->dY, ny, 0);
-  if (e == cudaSuccess) e = mlp_backward(s, B, 0);
+  if (e == cudaSuccess) e = mlp_backward(s, B, 0, trace ? &tr : nullptr);
   size_t o = 0;
   for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
     const size_t nw = (size_t)s->L[l].in * s->L[l].out;
@@ -961,9 +1049,20 @@ pe_status pe_surrogate_mlp_debug(pe_surrogate s, const float* x, int B, const fl
     if (e == cudaSuccess) e = cudaMemcpy(grads + o, s->L[l].gb, s->L[l].out * sizeof(float), cudaMemcpyDeviceToHost);
     o += s->L[l].out;
   }
-  if (tmp) cudaFree(tmp);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (tmp) pe::dfree(tmp);
   if (e != cudaSuccess) { cudaGetLastError(); return sfail(PE_ECUDA, "pe_surrogate_mlp_debug failed"); }
-  return PE_OK;
+  return gemm_status("pe_surrogate_mlp_debug");
+}
+
+pe_status pe_surrogate_mlp_debug(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads) {
+  return mlp_debug_impl(s, x, B, dy, y, grads, nullptr);
+}
+
+pe_status pe_surrogate_mlp_trace(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads,
+                                 float* trace) {
+  if (!trace) return sfail(PE_EINVAL, "pe_surrogate_mlp_trace: trace is NULL");
+  return mlp_debug_impl(s, x, B, dy, y, grads, trace);
 }
 
 // Weights and biases as fp32 host arrays, concatenated W0, b0, W1, b1, W2, b2, W3, b3 ([out][in]).
@@ -1054,7 +1153,7 @@ pe_status pe_surrogate_load(pe_surrogate s, const char* path) {
   memcpy(&s->seed, buf.data() + o, 8); o += 8;
   auto dput = [&](float* d, size_t n) -> bool {
     if (o + n * sizeof(float) > buf.size() - 8) return false;
-    const bool ok = cudaMemcpy(d, buf.data() + o, n * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    const bool ok = pe::upload(d, buf.data() + o, n * sizeof(float)) == cudaSuccess;
     o += n * sizeof(float);
     return ok;
   };
