@@ -152,9 +152,14 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
  * point exists for callers that cannot allocate). A sampler embedded in an application that
  * reserves the GPU's memory for its own pool at start-up, or a latency-critical loop that must
  * never enter the allocator, cannot let the library call cudaMalloc/cudaMallocAsync per call.
- * This variant computes exactly what pe_loglike_batch computes, with its scratch in one fixed
- * 32 MiB device array that every GPU loading the library holds until the process exits; it calls
- * no allocating routine.
+ * This variant computes exactly what pe_loglike_batch computes (bit for bit), with its scratch in
+ * one fixed 32 MiB device array; it calls no allocating routine.
+ *   When the array is committed: CUDA loads the module that holds it lazily, on the first use of
+ *   that module on a device -- the first pe_loglike_batch_noalloc call there. That call commits
+ *   the 32 MiB (and can fail with PE_ECUDA if the device has no memory left); the device then holds
+ *   it until the process exits. So make the first call on each device before the application
+ *   reserves the device's memory for its own pool (and before any stream capture); every later
+ *   call allocates nothing.
  *   theta, out_logl and the optional out_dhhh / out_status must be DEVICE pointers (host buffers
  *   would need staging memory); other arguments and layouts are as for pe_loglike_batch.
  *   Size limit: coefficients (1,136 bytes per sample) plus one 48-byte partial per 128-bin
@@ -162,8 +167,9 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
  *   2^22 s grid (209,296 bins), about 1,500 on a 2^20 s grid, in every precision. Larger batches
  *   return PE_EINVAL with the needed size in pe_last_error(); split them. The work items take the
  *   precision's default sub-tile count (no tuned choice is read).
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current, so make that first call before any stream capture.
+ *   Every call looks up the array's device address on the current device (cudaGetSymbolAddress;
+ *   nothing is allocated once the module is loaded, and no address outlives a device reset).
+ *   Device pointers must belong to the current device (PE_EINVAL otherwise).
  *   All calls share the one array: calls whose work overlaps on the GPU (other streams, other
  *   host threads) race on it and give wrong results; serialise them. Every scratch element is
  *   written before it is read within a call, so nothing is cleared between calls. */
@@ -230,6 +236,12 @@ pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_ma
  *     App. A's mismatch without the maximisation over t_c and phi_c); 0 for fallback samples.
  *   pe_surrogate_mlp_debug / pe_surrogate_get_weights: forward + backward of the network on given
  *     inputs and output cotangents, and its weights, for gradient checks.
+ *   pe_surrogate_mlp_trace: pe_surrogate_mlp_debug that also copies every intermediate of the pass
+ *     to the host buffer trace (float32, B * 6464 values; bf16 buffers widened exactly), in this
+ *     order, each [B][n] row-major: X (n = 64, the bf16 input features); for layer l = 0, 1, 2
+ *     Z_l (256, fp32 pre-activation) then H_l (256, bf16 SiLU output); Y (2560, fp32); then for
+ *     l = 2, 1, 0: dH_l (256, fp32 cotangent of H_l), dZ_l (256, fp32) and its bf16 copy (256).
+ *     For elementwise checks of each layer against its own inputs; x, dy, y, grads as above.
  *   pe_surrogate_save / pe_surrogate_load: versioned binary checkpoint (weights, Adam state,
  *     output standardisation, box, seed) with an FNV-1a checksum; PE_EINVAL on a bad file. */
 typedef struct pe_surrogate_s* pe_surrogate;
@@ -246,6 +258,8 @@ pe_status pe_surrogate_loglike_batch(pe_surrogate s, const pe_detector* dets, in
 pe_status pe_surrogate_mismatch(pe_surrogate s, pe_detector det, const double* theta_dev, int B, unsigned mode_mask,
                                 double* out_mismatch_dev, void* stream);
 pe_status pe_surrogate_mlp_debug(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads);
+pe_status pe_surrogate_mlp_trace(pe_surrogate s, const float* x, int B, const float* dy, float* y, float* grads,
+                                 float* trace);
 pe_status pe_surrogate_get_weights(pe_surrogate s, float* out, int64_t* count);
 pe_status pe_surrogate_save(pe_surrogate s, const char* path);
 pe_status pe_surrogate_load(pe_surrogate s, const char* path);
@@ -333,6 +347,14 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
 pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double* theta, int B, double* out_logl,
                                   double* out_dhhh, int32_t* out_status, void* stream);
 pe_status pe_hetero_destroy(pe_hetero h);
+
+/* Bounded host waits. An entry point that returns results into host memory waits for its stream
+ * by polling an event (no blocking synchronise), for at most the limit set here (seconds, default
+ * 600, process-wide). Past the limit it returns PE_ETIMEOUT: the work stays queued on the stream and
+ * the host outputs are valid only once the stream has finished (cudaStreamSynchronize, or a later
+ * wait). No counterpart in the paper. pe_set_wait_limit: PE_EINVAL unless 0 < seconds < inf. */
+pe_status pe_set_wait_limit(double seconds);
+double pe_get_wait_limit(void);
 
 /* Message describing the last failing call on this thread ("" if none). */
 const char* pe_last_error(void);

@@ -65,66 +65,96 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError("libpespace_gb300.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
-        L = C.CDLL(LIB_PATH)
-        L.pe_abi_version.restype = C.c_int
-        L.pe_last_error.restype = C.c_char_p
-        L.pe_create_detector.argtypes = [C.POINTER(DetectorConfig), C.c_double, C.c_int64, C.c_int64, C.POINTER(_P)]
-        L.pe_destroy_detector.argtypes = [_P]
-        L.pe_psd_model.argtypes = [_P, _P]
-        L.pe_set_data_psd.argtypes = [_P, _P, _P, C.c_int]
-        L.pe_data_norm.argtypes = [_P, _P]
-        L.pe_signal_aet.argtypes = [_P, _P, C.c_uint, _P, _P]
-        L.pe_inject.argtypes = [_P, _P, C.c_uint, _P]
-        L.pe_loglike_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
-        L.pe_loglike_grad_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
-        L.pe_fisher.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P]
-        L.pe_loglike_batch_noalloc.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
-        L.pe_loglike_batch_noalloc.restype = C.c_int
-        L.pe_plan_create.argtypes = [_P, C.c_int, C.c_int, C.c_uint, _P, _P, _P, _P, C.c_int, C.POINTER(_P)]
-        L.pe_plan_launch.argtypes = [_P, _P]
-        L.pe_plan_info.argtypes = [_P, _P, _P, _P, _P]
-        L.pe_plan_destroy.argtypes = [_P]
-        L.pe_autotune.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
-        L.pe_tune_set.argtypes = [_P, C.c_int, C.c_int, C.c_uint, C.c_int, C.c_int, C.c_int]
-        for name in ("pe_plan_create", "pe_plan_launch", "pe_plan_info", "pe_plan_destroy", "pe_autotune",
-                     "pe_tune_set"):
-            getattr(L, name).restype = C.c_int
-        L.pe_surrogate_create.argtypes = [C.c_uint64, C.POINTER(_P)]
-        L.pe_surrogate_destroy.argtypes = [_P]
-        L.pe_surrogate_train.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]
-        L.pe_surrogate_set_box.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_double]
-        L.pe_surrogate_set_node_source.argtypes = [_P, C.c_int]
-        L.pe_surrogate_set_node_source.restype = C.c_int
-        L.pe_surrogate_targets.argtypes = [_P, C.c_int, _P]
-        L.pe_surrogate_predict.argtypes = [_P, _P, C.c_int, _P]
-        L.pe_surrogate_loglike_batch.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P]
-        L.pe_surrogate_mismatch.argtypes = [_P, _P, _P, C.c_int, C.c_uint, _P, _P]
-        L.pe_surrogate_mlp_debug.argtypes = [_P, _P, C.c_int, _P, _P, _P]
-        L.pe_surrogate_get_weights.argtypes = [_P, _P, _P]
-        L.pe_surrogate_save.argtypes = [_P, C.c_char_p]
-        L.pe_surrogate_load.argtypes = [_P, C.c_char_p]
-        for name in ("pe_surrogate_create", "pe_surrogate_destroy", "pe_surrogate_train", "pe_surrogate_set_box",
-                     "pe_surrogate_targets", "pe_surrogate_predict", "pe_surrogate_loglike_batch",
-                     "pe_surrogate_mismatch", "pe_surrogate_mlp_debug", "pe_surrogate_get_weights",
-                     "pe_surrogate_save", "pe_surrogate_load"):
-            getattr(L, name).restype = C.c_int
-        L.pe_fisher_gaussian.argtypes = [_P, C.c_int, _P, C.c_uint, _P, C.c_int, _P, C.c_int, _P, _P]
-        L.pe_fisher_gaussian.restype = C.c_int
-        L.pe_hetero_default_edges.argtypes = [C.c_double, C.c_int64, C.c_int64, _P, C.c_uint, C.c_int, _P, _P]
-        L.pe_hetero_create.argtypes = [_P, _P, C.c_uint, _P, C.c_int, C.POINTER(_P)]
-        L.pe_hetero_loglike_batch.argtypes = [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P]
-        L.pe_hetero_destroy.argtypes = [_P]
-        for name in ("pe_hetero_default_edges", "pe_hetero_create", "pe_hetero_loglike_batch", "pe_hetero_destroy"):
-            getattr(L, name).restype = C.c_int
-        L.pe_profile_enable.argtypes = [C.c_int]
-        L.pe_profile_read.argtypes = [_P, _P]
-        L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
-        L.pe_measure_fp32_peak.argtypes = [C.c_double, _P]
-        for name in ("pe_profile_enable", "pe_profile_read", "pe_measure_fp64_peak", "pe_measure_fp32_peak", "pe_create_detector", "pe_destroy_detector", "pe_psd_model", "pe_set_data_psd", "pe_data_norm",
-                     "pe_signal_aet", "pe_inject", "pe_loglike_batch", "pe_loglike_grad_batch", "pe_fisher"):
-            getattr(L, name).restype = C.c_int
-        _lib = L
+        _lib = load(LIB_PATH)
     return _lib
+
+
+def swap_library(cdll):
+    """Route every wrapper of this module through another build of the library (the test build,
+    libpespace_gb300_test.so, loaded with load()); returns the previous handle to restore."""
+    global _lib
+    prev = lib()
+    _lib = cdll
+    return prev
+
+
+def load(path: str):
+    """A ctypes handle of one build of the library with every signature declared."""
+    L = C.CDLL(path)
+    L.pe_abi_version.restype = C.c_int
+    L.pe_last_error.restype = C.c_char_p
+    L.pe_create_detector.argtypes = [C.POINTER(DetectorConfig), C.c_double, C.c_int64, C.c_int64, C.POINTER(_P)]
+    L.pe_destroy_detector.argtypes = [_P]
+    L.pe_psd_model.argtypes = [_P, _P]
+    L.pe_set_data_psd.argtypes = [_P, _P, _P, C.c_int]
+    L.pe_data_norm.argtypes = [_P, _P]
+    L.pe_signal_aet.argtypes = [_P, _P, C.c_uint, _P, _P]
+    L.pe_inject.argtypes = [_P, _P, C.c_uint, _P]
+    L.pe_loglike_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+    L.pe_loglike_grad_batch.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+    L.pe_fisher.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P]
+    L.pe_loglike_batch_noalloc.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+    L.pe_loglike_batch_noalloc.restype = C.c_int
+    L.pe_plan_create.argtypes = [_P, C.c_int, C.c_int, C.c_uint, _P, _P, _P, _P, C.c_int, C.POINTER(_P)]
+    L.pe_plan_launch.argtypes = [_P, _P]
+    L.pe_plan_info.argtypes = [_P, _P, _P, _P, _P]
+    L.pe_plan_destroy.argtypes = [_P]
+    L.pe_autotune.argtypes = [_P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P, _P]
+    L.pe_tune_set.argtypes = [_P, C.c_int, C.c_int, C.c_uint, C.c_int, C.c_int, C.c_int]
+    for name in ("pe_plan_create", "pe_plan_launch", "pe_plan_info", "pe_plan_destroy", "pe_autotune",
+                 "pe_tune_set"):
+        getattr(L, name).restype = C.c_int
+    L.pe_surrogate_create.argtypes = [C.c_uint64, C.POINTER(_P)]
+    L.pe_surrogate_destroy.argtypes = [_P]
+    L.pe_surrogate_train.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]
+    L.pe_surrogate_set_box.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_double]
+    L.pe_surrogate_set_node_source.argtypes = [_P, C.c_int]
+    L.pe_surrogate_set_node_source.restype = C.c_int
+    L.pe_surrogate_targets.argtypes = [_P, C.c_int, _P]
+    L.pe_surrogate_predict.argtypes = [_P, _P, C.c_int, _P]
+    L.pe_surrogate_loglike_batch.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P]
+    L.pe_surrogate_mismatch.argtypes = [_P, _P, _P, C.c_int, C.c_uint, _P, _P]
+    L.pe_set_wait_limit.argtypes = [C.c_double]
+    L.pe_set_wait_limit.restype = C.c_int
+    L.pe_get_wait_limit.argtypes = []
+    L.pe_get_wait_limit.restype = C.c_double
+    L.pe_surrogate_mlp_debug.argtypes = [_P, _P, C.c_int, _P, _P, _P]
+    L.pe_surrogate_mlp_trace.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
+    L.pe_surrogate_get_weights.argtypes = [_P, _P, _P]
+    L.pe_surrogate_save.argtypes = [_P, C.c_char_p]
+    L.pe_surrogate_load.argtypes = [_P, C.c_char_p]
+    for name in ("pe_surrogate_create", "pe_surrogate_destroy", "pe_surrogate_train", "pe_surrogate_set_box",
+                 "pe_surrogate_targets", "pe_surrogate_predict", "pe_surrogate_loglike_batch",
+                 "pe_surrogate_mismatch", "pe_surrogate_mlp_debug", "pe_surrogate_mlp_trace", "pe_surrogate_get_weights",
+                 "pe_surrogate_save", "pe_surrogate_load"):
+        getattr(L, name).restype = C.c_int
+    L.pe_fisher_gaussian.argtypes = [_P, C.c_int, _P, C.c_uint, _P, C.c_int, _P, C.c_int, _P, _P]
+    L.pe_fisher_gaussian.restype = C.c_int
+    L.pe_hetero_default_edges.argtypes = [C.c_double, C.c_int64, C.c_int64, _P, C.c_uint, C.c_int, _P, _P]
+    L.pe_hetero_create.argtypes = [_P, _P, C.c_uint, _P, C.c_int, C.POINTER(_P)]
+    L.pe_hetero_loglike_batch.argtypes = [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P]
+    L.pe_hetero_destroy.argtypes = [_P]
+    for name in ("pe_hetero_default_edges", "pe_hetero_create", "pe_hetero_loglike_batch", "pe_hetero_destroy"):
+        getattr(L, name).restype = C.c_int
+    L.pe_profile_enable.argtypes = [C.c_int]
+    L.pe_profile_read.argtypes = [_P, _P]
+    L.pe_measure_fp64_peak.argtypes = [C.c_double, _P]
+    L.pe_measure_fp32_peak.argtypes = [C.c_double, _P]
+    for name in ("pe_profile_enable", "pe_profile_read", "pe_measure_fp64_peak", "pe_measure_fp32_peak", "pe_create_detector", "pe_destroy_detector", "pe_psd_model", "pe_set_data_psd", "pe_data_norm",
+                 "pe_signal_aet", "pe_inject", "pe_loglike_batch", "pe_loglike_grad_batch", "pe_fisher"):
+        getattr(L, name).restype = C.c_int
+    if hasattr(L, "pe_test_fault_arm"):
+        L.pe_test_fault_arm.argtypes = [C.c_int, C.c_long]
+        L.pe_test_fault_arm.restype = C.c_int
+        for name in ("pe_test_fault_count",):
+            getattr(L, name).argtypes = [C.c_int]
+            getattr(L, name).restype = C.c_long
+        for name in ("pe_test_fault_fired", "pe_test_live_allocations"):
+            getattr(L, name).argtypes = []
+            getattr(L, name).restype = C.c_long
+        L.pe_test_checked_take.argtypes = []
+        L.pe_test_checked_take.restype = C.c_int
+    return L
 
 
 def _check(st: int):
@@ -156,6 +186,14 @@ def _stream(stream):
 
 
 # ---- ABI functions (same names) --------------------------------------------------------------
+def pe_set_wait_limit(seconds: float):
+    _check(lib().pe_set_wait_limit(float(seconds)))
+
+
+def pe_get_wait_limit() -> float:
+    return lib().pe_get_wait_limit()
+
+
 def pe_abi_version() -> int:
     return lib().pe_abi_version()
 
@@ -524,6 +562,27 @@ class Surrogate:
         g = np.zeros_like(self.weights())
         _check(lib().pe_surrogate_mlp_debug(self.handle, x.ctypes.data, B, dy.ctypes.data, y.ctypes.data, g.ctypes.data))
         return y, g
+
+    # sizes of the intermediates pe_surrogate_mlp_trace returns, per row, in order
+    TRACE_LAYOUT = (("X", 64), ("Z0", 256), ("H0", 256), ("Z1", 256), ("H1", 256), ("Z2", 256), ("H2", 256),
+                    ("Y", 2560), ("dH2", 256), ("dZ2", 256), ("dZb2", 256), ("dH1", 256), ("dZ1", 256),
+                    ("dZb1", 256), ("dH0", 256), ("dZ0", 256), ("dZb0", 256))
+
+    def mlp_trace(self, x: np.ndarray, dy: np.ndarray):
+        """mlp_debug plus every intermediate of the pass: returns y, grads and a dict name -> [B][n]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        dy = np.ascontiguousarray(dy, dtype=np.float32)
+        B = x.shape[0]
+        y = np.zeros((B, SUR_NOUT), dtype=np.float32)
+        g = np.zeros_like(self.weights())
+        tr = np.zeros(B * sum(n for _, n in self.TRACE_LAYOUT), dtype=np.float32)
+        _check(lib().pe_surrogate_mlp_trace(self.handle, x.ctypes.data, B, dy.ctypes.data, y.ctypes.data,
+                                            g.ctypes.data, tr.ctypes.data))
+        out, o = {}, 0
+        for name, n in self.TRACE_LAYOUT:
+            out[name] = tr[o:o + B * n].reshape(B, n)
+            o += B * n
+        return y, g, out
 
     def save(self, path: str):
         _check(lib().pe_surrogate_save(self.handle, path.encode()))

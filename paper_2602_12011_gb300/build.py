@@ -34,23 +34,33 @@ def sources() -> list[str]:
 
 def _newest_input() -> float:
     files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    files.append(os.path.join(INCLUDE, "pespace_gb300.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every .cu under csrc/ for sm_103a and link the shared library. Returns its path."""
-    if not force and not ptxas_info and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(LIBDIR, exist_ok=True)
+# The test build: host-side fault injection (PE_FAULT_INJECTION) and the hot kernels' index checks
+# (PE_CHECKED), exported through include/pespace_gb300_test.h. Never the product library.
+TEST_LIB = os.path.join(LIBDIR, "libpespace_gb300_test.so")
+TEST_FLAGS = ["-DPE_FAULT_INJECTION", "-DPE_CHECKED"]
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, variant: str = "product") -> str:
+    """Compile every .cu under csrc/ for sm_103a and link the shared library. Returns its path.
+    variant "test" builds libpespace_gb300_test.so (fault injection and index checks) instead."""
+    lib_path = TEST_LIB if variant == "test" else LIB
+    objdir = os.path.join(LIBDIR, "test") if variant == "test" else LIBDIR
+    extra = TEST_FLAGS if variant == "test" else []
+    if not force and not ptxas_info and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= _newest_input():
+        return lib_path
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(LIBDIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         if ptxas_info:
             cmd += ["-Xptxas", "-v"]
         cmds.append(cmd)
@@ -66,13 +76,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s%s" % (" ".join(link), r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -2,11 +2,17 @@
 // argument validation, pointer-kind handling, stream-ordered scratch and kernel launches.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <chrono>
+#include <thread>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -17,6 +23,7 @@
 #include "pe_measure.h"
 #include "pe_plan.h"
 #include "pespace_gb300.h"
+#include "pe_fault.h"
 
 struct pe_detector_s {
   int device;
@@ -79,14 +86,38 @@ pe_status fail(pe_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(PE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-bool is_device_ptr(const void* p) {
-  if (p == nullptr) return false;
+// Bounded wait for the call's stream before host outputs are read (PE_ETIMEOUT past the limit).
+#define PE_WAIT(st)                                                                                  \
+  do {                                                                                               \
+    cudaError_t e_ = pe::wait_stream(st);                                                            \
+    if (e_ == cudaErrorNotReady)                                                                     \
+      return fail(PE_ETIMEOUT, "stream did not finish within %g s; the work stays queued",          \
+                  pe_get_wait_limit());                                                              \
+    if (e_ != cudaSuccess) return fail(PE_ECUDA, "stream wait failed: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+// Where a caller's buffer lives: host memory (pageable or pinned), memory the current device can
+// use directly (its own device memory, or managed memory), or another device's memory.
+enum PtrKind { kPtrHost = 0, kPtrDevice = 1, kPtrOtherDevice = 2 };
+PtrKind ptr_kind(const void* p) {
+  if (p == nullptr) return kPtrHost;
+  int dev = -1;
   cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return kPtrHost;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return kPtrDevice;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev ? kPtrDevice : kPtrOtherDevice;
+  return kPtrHost;
+}
+bool is_device_ptr(const void* p) { return ptr_kind(p) == kPtrDevice; }
+// PE_EINVAL (with a message) if any of the caller's buffers is another device's memory
+pe_status check_local(const char* who, std::initializer_list<const void*> ptrs) {
+  for (const void* p : ptrs)
+    if (ptr_kind(p) == kPtrOtherDevice)
+      return fail(PE_EINVAL, "%s: a buffer lives on another device than the current one", who);
+  return PE_OK;
 }
 
 std::once_flag g_pool_once;
@@ -109,12 +140,12 @@ struct Scratch {
   std::vector<void*> bufs;
   explicit Scratch(cudaStream_t s) : st(s) {}
   ~Scratch() {
-    for (void* p : bufs) cudaFreeAsync(p, st);
+    for (void* p : bufs) pe::dfree_async(p, st);
   }
   template <class T>
   cudaError_t alloc(T** p, size_t n) {
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, n * sizeof(T) + 16, st);
+    cudaError_t e = pe::dmalloc_async(&q, n * sizeof(T) + 16, st);
     if (e != cudaSuccess) return e;
     bufs.push_back(q);
     *p = static_cast<T*>(q);
@@ -269,8 +300,8 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
                n_f = 8 * nb;
   const size_t bytes = n_d2 * sizeof(double2) + n_f4 * sizeof(float4) + n_d * sizeof(double) +
                        n_f2 * sizeof(float2) + n_f * sizeof(float);
-  cudaError_t e = cudaMalloc(&d->mem, bytes);
-  if (e != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ENOMEM, "cudaMalloc(%zu) failed", bytes); }
+  cudaError_t e = pe::dmalloc(&d->mem, bytes);
+  if (e != cudaSuccess) { cudaGetLastError(); delete d; return fail(PE_ENOMEM, "pe::dmalloc(%zu) failed", bytes); }
   double2* p2 = static_cast<double2*>(d->mem);
   d->sct = p2; p2 += pe::kSinTab;
   d->sca = p2; p2 += nb;
@@ -320,7 +351,7 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
       (e = cudaMemset(d->dd_dev, 0, 3 * sizeof(double))) != cudaSuccess ||
       (e = cudaDeviceSynchronize()) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(d->mem);
+    pe::dfree(d->mem);
     delete d;
     return fail(PE_ECUDA, "detector table set-up failed: %s", cudaGetErrorString(e));
   }
@@ -331,7 +362,7 @@ pe_status pe_create_detector(const pe_detector_config* cfg, double T_obs, int64_
 pe_status pe_destroy_detector(pe_detector det) {
   if (det == nullptr) return PE_OK;
   cudaDeviceSynchronize();
-  cudaFree(det->mem);
+  pe::dfree(det->mem);
   cudaGetLastError();
   delete det;
   return PE_OK;
@@ -355,8 +386,8 @@ static pe_status set_data_device(pe_detector det, const double2* data_dev, const
   double* parts = nullptr;
   int* bad = nullptr;
   const int nblk = (nb + pe::kTileBins - 1) / pe::kTileBins;
-  PE_CUDA(cudaMalloc(&parts, (size_t)nblk * 3 * sizeof(double)));
-  if (cudaMalloc(&bad, sizeof(int)) != cudaSuccess) { cudaFree(parts); return fail(PE_ENOMEM, "cudaMalloc failed"); }
+  PE_CUDA(pe::dmalloc(&parts, (size_t)nblk * 3 * sizeof(double)));
+  if (pe::dmalloc(&bad, sizeof(int)) != cudaSuccess) { pe::dfree(parts); return fail(PE_ENOMEM, "cudaMalloc failed"); }
   cudaMemset(bad, 0, sizeof(int));
   int g = 0;
   const double L = det_arm_s(det->cfg);
@@ -370,7 +401,7 @@ static pe_status set_data_device(pe_detector det, const double2* data_dev, const
   // near their maxima
   double* mxp = nullptr;
   const int n3 = 3 * nb;
-  if (e == cudaSuccess) e = cudaMalloc(&mxp, ((size_t)(n3 + pe::kTileBins - 1) / pe::kTileBins * 2 + 2) * sizeof(double));
+  if (e == cudaSuccess) e = pe::dmalloc(&mxp, ((size_t)(n3 + pe::kTileBins - 1) / pe::kTileBins * 2 + 2) * sizeof(double));
   double mx[2] = {0.0, 0.0};
   if (e == cudaSuccess) {
     double* out = mxp;
@@ -384,9 +415,9 @@ static pe_status set_data_device(pe_detector det, const double2* data_dev, const
                            det->dgf, det->ggf, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (mxp) cudaFree(mxp);
-  cudaFree(parts);
-  cudaFree(bad);
+  if (mxp) pe::dfree(mxp);
+  pe::dfree(parts);
+  pe::dfree(bad);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(PE_ECUDA, "data tables: %s", cudaGetErrorString(e)); }
   if (hbad) { det->has_data = 0; return fail(PE_EINVAL, "PSD has a non-positive or non-finite value"); }
   det->has_data = 1;
@@ -399,18 +430,18 @@ pe_status pe_set_data_psd(pe_detector det, const double* data_aet, const double*
   if (ptr_is_device) return set_data_device(det, reinterpret_cast<const double2*>(data_aet), psd_aet);
   double2* dd = nullptr;
   double* pd = nullptr;
-  PE_CUDA(cudaMalloc(&dd, 3 * nb * sizeof(double2)));
-  if (psd_aet && cudaMalloc(&pd, 3 * nb * sizeof(double)) != cudaSuccess) {
-    cudaFree(dd);
+  PE_CUDA(pe::dmalloc(&dd, 3 * nb * sizeof(double2)));
+  if (psd_aet && pe::dmalloc(&pd, 3 * nb * sizeof(double)) != cudaSuccess) {
+    pe::dfree(dd);
     return fail(PE_ENOMEM, "cudaMalloc failed");
   }
-  cudaError_t e = cudaMemcpy(dd, data_aet, 3 * nb * sizeof(double2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && psd_aet) e = cudaMemcpy(pd, psd_aet, 3 * nb * sizeof(double), cudaMemcpyHostToDevice);
+  cudaError_t e = pe::upload(dd, data_aet, 3 * nb * sizeof(double2));
+  if (e == cudaSuccess && psd_aet) e = pe::upload(pd, psd_aet, 3 * nb * sizeof(double));
   pe_status st = PE_OK;
   if (e != cudaSuccess) st = fail(PE_ECUDA, "upload failed: %s", cudaGetErrorString(e));
   else st = set_data_device(det, dd, pd);
-  cudaFree(dd);
-  if (pd) cudaFree(pd);
+  pe::dfree(dd);
+  if (pd) pe::dfree(pd);
   return st;
 }
 
@@ -430,7 +461,7 @@ static pe_status signal_device(pe_detector det, const double* theta, unsigned mo
     for (int i = 0; i < PE_NPARAM; ++i)
       if (!std::isfinite(theta[i])) return fail(PE_EINVAL, "theta[%d] is not finite", i);
     PE_CUDA(sc.alloc(&th, PE_NPARAM));
-    PE_CUDA(cudaMemcpyAsync(th, theta, PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+    PE_CUDA(pe::upload_async(th, theta, PE_NPARAM * sizeof(double), st));
   }
   pe::DetSet ds;
   memset(&ds, 0, sizeof(ds));
@@ -440,7 +471,7 @@ static pe_status signal_device(pe_detector det, const double* theta, unsigned mo
   PE_CUDA(pe::launch_signal(det->dev, coef, out_dev, pe::mask_prec(mode_mask), st));
   int hs = 0;
   PE_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  PE_CUDA(cudaStreamSynchronize(st));
+  PE_WAIT(st);
   if (hs) return fail(PE_EINVAL, "theta is outside the parameter domain");
   return PE_OK;
 }
@@ -448,17 +479,18 @@ static pe_status signal_device(pe_detector det, const double* theta, unsigned mo
 pe_status pe_signal_aet(pe_detector det, const double* theta, unsigned mode_mask, double* out, void* stream) {
   if (det == nullptr || theta == nullptr || out == nullptr) return fail(PE_EINVAL, "det/theta/out is NULL");
   if (!pe::fwd_mask_ok(mode_mask)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  if (check_local("pe_signal_aet", {theta, out}) != PE_OK) return PE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (is_device_ptr(out)) return signal_device(det, theta, mode_mask, reinterpret_cast<double2*>(out), st);
   double2* tmp = nullptr;
   const size_t n = 3 * (size_t)det->nb;
-  PE_CUDA(cudaMalloc(&tmp, n * sizeof(double2)));
+  PE_CUDA(pe::dmalloc(&tmp, n * sizeof(double2)));
   pe_status s = signal_device(det, theta, mode_mask, tmp, st);
   if (s == PE_OK) {
     cudaError_t e = cudaMemcpy(out, tmp, n * sizeof(double2), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) s = fail(PE_ECUDA, "download failed: %s", cudaGetErrorString(e));
   }
-  cudaFree(tmp);
+  pe::dfree(tmp);
   return s;
 }
 
@@ -468,18 +500,18 @@ pe_status pe_inject(pe_detector det, const double* theta_inj, unsigned mode_mask
   const size_t n = 3 * (size_t)det->nb;
   double2* h = nullptr;
   double2* nd = nullptr;
-  PE_CUDA(cudaMalloc(&h, n * sizeof(double2)));
+  PE_CUDA(pe::dmalloc(&h, n * sizeof(double2)));
   pe_status s = signal_device(det, theta_inj, mode_mask, h, 0);
   if (s == PE_OK && normals) {
-    cudaError_t e = cudaMalloc(&nd, n * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMemcpy(nd, normals, n * sizeof(double2), cudaMemcpyHostToDevice);
+    cudaError_t e = pe::dmalloc(&nd, n * sizeof(double2));
+    if (e == cudaSuccess) e = pe::upload(nd, normals, n * sizeof(double2));
     if (e == cudaSuccess) e = pe::launch_inject(det->nb, det->T, det->psd_model, nd, h, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { cudaGetLastError(); s = fail(PE_ECUDA, "noise injection failed: %s", cudaGetErrorString(e)); }
   }
   if (s == PE_OK) s = set_data_device(det, h, nullptr);
-  cudaFree(h);
-  if (nd) cudaFree(nd);
+  pe::dfree(h);
+  if (nd) pe::dfree(nd);
   return s;
 }
 
@@ -491,6 +523,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (theta == nullptr || out_logl == nullptr) return fail(PE_EINVAL, "theta/out_logl is NULL");
   if (B < 1 || B > (1 << 20)) return fail(PE_EINVAL, "B=%d outside [1, 2^20]", B);
   if (!pe::fwd_mask_ok(mode_mask)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  if (check_local("pe_loglike_batch", {theta, out_logl, out_dhhh, out_status}) != PE_OK) return PE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch sc(st);
   const int P = ndet * B;
@@ -500,7 +533,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (!is_device_ptr(theta)) {
     double* t = nullptr;
     PE_CUDA(sc.alloc(&t, (size_t)B * PE_NPARAM));
-    PE_CUDA(cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+    PE_CUDA(pe::upload_async(t, theta, (size_t)B * PE_NPARAM * sizeof(double), st));
     th = t;
   }
   pe::SampleCoef* coef = nullptr;
@@ -536,7 +569,7 @@ pe_status pe_loglike_batch(const pe_detector* dets, int ndet, const double* thet
   if (h_dhhh)
     PE_CUDA(cudaMemcpyAsync(out_dhhh, dhhh, (size_t)B * ndet * 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (h_stat) PE_CUDA(cudaMemcpyAsync(out_status, stat, (size_t)B * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  if (h_logl || h_dhhh || h_stat) PE_CUDA(cudaStreamSynchronize(st));
+  if (h_logl || h_dhhh || h_stat) PE_WAIT(st);
   return PE_OK;
 }
 
@@ -551,6 +584,7 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
     return fail(PE_EINVAL, "bad mode mask 0x%x (the gradient takes PE_PREC_MIXED, not PE_PREC_FP32)", mode_mask);
   const bool mixed = (mode_mask & PE_PREC_MIXED) != 0;
   mode_mask &= PE_MODE_ALL;
+  if (check_local("pe_loglike_grad_batch", {theta, out_logl, out_grad, out_status}) != PE_OK) return PE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch sc(st);
   const int P = ndet * B;
@@ -560,7 +594,7 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   if (!is_device_ptr(theta)) {
     double* t = nullptr;
     PE_CUDA(sc.alloc(&t, (size_t)B * PE_NPARAM));
-    PE_CUDA(cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+    PE_CUDA(pe::upload_async(t, theta, (size_t)B * PE_NPARAM * sizeof(double), st));
     th = t;
   }
   pe::SampleCoef* coef = nullptr;
@@ -595,7 +629,7 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   if (h_grad)
     PE_CUDA(cudaMemcpyAsync(out_grad, grad, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (h_stat) PE_CUDA(cudaMemcpyAsync(out_status, stat, (size_t)B * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  if (h_logl || h_grad || h_stat) PE_CUDA(cudaStreamSynchronize(st));
+  if (h_logl || h_grad || h_stat) PE_WAIT(st);
   return PE_OK;
 }
 
@@ -607,6 +641,7 @@ pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int 
   if (theta == nullptr || out_F == nullptr) return fail(PE_EINVAL, "theta/out_F is NULL");
   if (B < 1 || B > (1 << 16)) return fail(PE_EINVAL, "B=%d outside [1, 2^16]", B);
   if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return fail(PE_EINVAL, "bad mode mask 0x%x", mode_mask);
+  if (check_local("pe_fisher", {theta, out_F}) != PE_OK) return PE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Scratch sc(st);
   const int P = ndet * B;
@@ -616,7 +651,7 @@ pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int 
   if (!is_device_ptr(theta)) {
     double* t = nullptr;
     PE_CUDA(sc.alloc(&t, (size_t)B * PE_NPARAM));
-    PE_CUDA(cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st));
+    PE_CUDA(pe::upload_async(t, theta, (size_t)B * PE_NPARAM * sizeof(double), st));
     th = t;
   }
   pe::SampleCoef* coef = nullptr;
@@ -643,7 +678,7 @@ pe_status pe_fisher(const pe_detector* dets, int ndet, const double* theta, int 
   PE_CUDA(pe::launch_fisher_reduce(ds, B, off, part, coef, F, st));
   if (h_F) {
     PE_CUDA(cudaMemcpyAsync(out_F, F, (size_t)B * 121 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    PE_CUDA(cudaStreamSynchronize(st));
+    PE_WAIT(st);
   }
   return PE_OK;
 }
@@ -709,6 +744,106 @@ pe_status pe_fisher_gaussian(const pe_detector* dets, int ndet, const double* th
   return PE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+std::atomic<double> g_wait_limit_s{600.0};
+}
+
+#ifdef PE_FAULT_INJECTION
+#include "pespace_gb300_test.h"
+// ---- test build: host-side fault injection and live-allocation count (pe_fault.h)
+namespace {
+std::atomic<int> g_fault_kind{-1};      // armed kind, -1 none
+std::atomic<long> g_fault_nth{0};       // the armed event's index (1-based) among its kind
+std::atomic<long> g_fault_seen[3];      // events of each kind since the last arm
+std::atomic<long> g_fault_fired{0};
+std::atomic<long> g_live{0};
+std::once_flag g_fault_env_once;
+
+void fault_env() {
+  std::call_once(g_fault_env_once, [] {
+    const char* v = getenv("PE_FAULT");
+    if (!v || !*v) return;
+    const char* names[3] = {"alloc", "upload", "launch"};
+    for (int k = 0; k < 3; ++k) {
+      const size_t n = strlen(names[k]);
+      if (strncmp(v, names[k], n) == 0) {
+        long nth = 1;
+        if (v[n] == ':') nth = strtol(v + n + 1, nullptr, 10);
+        g_fault_nth.store(nth > 0 ? nth : 1);
+        g_fault_kind.store(k);
+      }
+    }
+  });
+}
+}  // namespace
+
+namespace pe {
+bool fault_now(int kind) {
+  fault_env();
+  const long n = ++g_fault_seen[kind];
+  if (g_fault_kind.load() == kind && n == g_fault_nth.load()) {
+    ++g_fault_fired;
+    return true;
+  }
+  return false;
+}
+void live_add(long d) { g_live += d; }
+int checked_take_kernels();
+int checked_take_grad();
+}  // namespace pe
+
+extern "C" {
+pe_status pe_test_fault_arm(int kind, long nth) {
+  if (kind < -1 || kind > 2 || nth < 0) return fail(PE_EINVAL, "pe_test_fault_arm: kind in -1..2, nth >= 0");
+  fault_env();   // PE_FAULT is read once, before the arm below replaces it
+  for (auto& c : g_fault_seen) c.store(0);
+  g_fault_fired.store(0);
+  g_fault_kind.store(nth > 0 ? kind : -1);
+  g_fault_nth.store(nth);
+  return PE_OK;
+}
+long pe_test_fault_count(int kind) { return (kind >= 0 && kind <= 2) ? g_fault_seen[kind].load() : -1; }
+long pe_test_fault_fired(void) { return g_fault_fired.load(); }
+long pe_test_live_allocations(void) { return g_live.load(); }
+int pe_test_checked_take(void) {
+  const int a = pe::checked_take_kernels(), b = pe::checked_take_grad();
+  return (a < 0 || b < 0) ? -1 : (a | b);
+}
+}  // extern "C"
+#endif
+
+namespace pe {
+cudaError_t wait_stream(cudaStream_t st) {
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(ev, st);
+  if (e == cudaSuccess) {
+    const double limit = g_wait_limit_s.load();
+    const auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+      e = cudaEventQuery(ev);
+      if (e != cudaErrorNotReady) break;
+      if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit) break;
+      if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+  cudaEventDestroy(ev);
+  if (e == cudaErrorNotReady) cudaGetLastError();
+  return e;
+}
+}  // namespace pe
+
+extern "C" {
+pe_status pe_set_wait_limit(double seconds) {
+  if (!(seconds > 0.0) || !std::isfinite(seconds)) return fail(PE_EINVAL, "wait limit must be positive and finite");
+  g_wait_limit_s.store(seconds);
+  return PE_OK;
+}
+double pe_get_wait_limit(void) { return g_wait_limit_s.load(); }
 }  // extern "C"
 
 namespace pe {

@@ -14,6 +14,7 @@
 #include "pe_adjoint.cuh"
 #include "pe_adjoint_mixed.cuh"
 #include "pe_grad.h"
+#include "pe_fault.h"
 
 namespace pe {
 
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd(DetSet ds, int B, con
   const long long total = off[P];
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair_g(off, P, t);
+    if (!PE_CHK(p >= 0 && p < P && off[p + 1] <= total && nend[p] <= ds.d[p / B].nb, 16)) continue;
     const int I = p / B, s = p - I * B;
     const int b = int(t - off[p]) * kTileBins + threadIdx.x;
     const DetDev& D = ds.d[I];
@@ -235,6 +237,7 @@ __global__ void k_grad_reduce(DetSet ds, int B, const long long* off, const doub
   double L = 0.0;
   for (int I = 0; I < ds.ndet; ++I) {
     const int p = I * B + s;
+    if (!PE_CHK(off[p] >= 0 && off[p + 1] <= off[ds.ndet * B], 32)) continue;
     double v[kGradW];
     for (int i = 0; i < kGradW; ++i) v[i] = 0.0;
     for (long long t = off[p] + lane; t < off[p + 1]; t += 32)
@@ -272,6 +275,7 @@ __global__ void __launch_bounds__(kFisherThreads) k_fisher_fwd(DetSet ds, int B,
   const int tid = threadIdx.x;
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair_g(off, P, t);
+    if (!PE_CHK(p >= 0 && p < P && off[p + 1] <= total && nend[p] <= ds.d[p / B].nb, 64)) continue;
     const int I = p / B, s = p - I * B;
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
@@ -334,6 +338,7 @@ __global__ void k_fisher_reduce(DetSet ds, int B, const long long* off, const do
   double a = 0.0;
   for (int I = 0; I < ds.ndet; ++I) {
     const int p = I * B + s;
+    if (!PE_CHK(off[p] >= 0 && off[p + 1] <= off[ds.ndet * B], 128)) continue;
     for (long long t = off[p]; t < off[p + 1]; ++t) a += part[t * kFisherW + e];
   }
   if (!coef[s].valid) a = 0.0;
@@ -347,7 +352,7 @@ __global__ void k_fisher_reduce(DetSet ds, int B, const long long* off, const do
 cudaError_t launch_prep_grad(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef,
                              SampleGrad* sgrad, int* nend, int* status, cudaStream_t st) {
   k_prep_grad<<<(B + 31) / 32, 32, 0, st>>>(theta, B, mask, ds, coef, sgrad, nend, status);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad, const int* nend,
                             const long long* off, double* part, int grid, bool mixed, cudaStream_t st) {
@@ -355,7 +360,7 @@ cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, con
     k_grad_fwd<true><<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
   else
     k_grad_fwd<false><<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_grad_reduce(const DetSet& ds, int B, const long long* off, const double* part,
                                const SampleCoef* coef, const SampleGrad* sgrad, double* logl, double* grad,
@@ -363,19 +368,22 @@ cudaError_t launch_grad_reduce(const DetSet& ds, int B, const long long* off, co
   const int threads = 128;
   const int grid = int(((long long)B * 32 + threads - 1) / threads);
   k_grad_reduce<<<grid, threads, 0, st>>>(ds, B, off, part, coef, sgrad, logl, grad);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_fisher_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad,
                               const int* nend, const long long* off, double* part, int grid, cudaStream_t st) {
   k_fisher_fwd<<<grid, kFisherThreads, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, const double* part,
                                  const SampleCoef* coef, double* F, cudaStream_t st) {
   k_fisher_reduce<<<B, 96, 0, st>>>(ds, B, off, part, coef, F);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 int grad_partial_width() { return kGradW; }
 int fisher_partial_width() { return kFisherW; }
+
+// Index-check error word of this file's kernels (checked build; 0 otherwise), cleared when read.
+int checked_take_grad() { return pe_checked_take_local(); }
 
 }  // namespace pe

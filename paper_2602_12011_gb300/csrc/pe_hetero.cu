@@ -24,6 +24,7 @@
 #include "pe_internal.h"
 #include "pe_kernels.h"
 #include "pespace_gb300.h"
+#include "pe_fault.h"
 
 namespace pe {
 
@@ -489,7 +490,7 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
   pe_hetero_s* h = new (std::nothrow) pe_hetero_s();
   if (!h) return herr(PE_ENOMEM, "pe_hetero_create: host allocation failed");
   cudaGetDevice(&h->device);
-  if (cudaMalloc(&h->mem, bytes) != cudaSuccess) {
+  if (pe::dmalloc(&h->mem, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return herr(PE_ENOMEM, "pe_hetero_create: device allocation failed");
@@ -513,23 +514,23 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
   pe::SampleCoef* coef = nullptr;
   int* nend = nullptr;
   double2* hb = nullptr;
-  cudaError_t e = cudaMalloc(&th0, PE_NPARAM * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&coef, sizeof(pe::SampleCoef));
-  if (e == cudaSuccess) e = cudaMalloc(&nend, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&hb, (size_t)pe::kNModes * 3 * K * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMemcpy(th0, theta0, PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_edge, he.data(), ne * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_fe, hfe.data(), ne * sizeof(double), cudaMemcpyHostToDevice);
+  cudaError_t e = pe::dmalloc(&th0, PE_NPARAM * sizeof(double));
+  if (e == cudaSuccess) e = pe::dmalloc(&coef, sizeof(pe::SampleCoef));
+  if (e == cudaSuccess) e = pe::dmalloc(&nend, sizeof(int));
+  if (e == cudaSuccess) e = pe::dmalloc(&hb, (size_t)pe::kNModes * 3 * K * sizeof(double2));
+  if (e == cudaSuccess) e = pe::upload(th0, theta0, PE_NPARAM * sizeof(double));
+  if (e == cudaSuccess) e = pe::upload(d_edge, he.data(), ne * sizeof(int));
+  if (e == cudaSuccess) e = pe::upload(d_fe, hfe.data(), ne * sizeof(double));
   if (e == cudaSuccess) e = pe::launch_prep(th0, 1, mode_mask, ds, coef, nend, nullptr, 0);
   if (e == cudaSuccess) {
     pe::k_mode_brackets<<<(K + pe::kTileBins - 1) / pe::kTileBins, pe::kTileBins>>>(D, coef, K, mode_mask, hb);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   // reference brackets at the edges, and the carry-forward sources
   std::vector<double2> h0e((size_t)ne * 15);
   if (e == cudaSuccess) {
     pe::k_gather_edges<<<(ne * 15 + 127) / 128, 128>>>(hb, K, d_edge, ne, d_h0e);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess) e = cudaMemcpy(h0e.data(), d_h0e, h0e.size() * sizeof(double2), cudaMemcpyDeviceToHost);
   std::vector<int> src((size_t)ne * 15, -1);
@@ -549,31 +550,31 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
           src[j] = ok ? i : (i > 0 ? src[j - 15] : -1);
         }
     }
-    e = cudaMemcpy(d_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
+    e = pe::upload(d_src, src.data(), src.size() * sizeof(int));
   }
   if (e == cudaSuccess) {   // the per-sample kernel multiplies by the inverses (no division per ratio)
     pe::k_invert_edges<<<(ne * 15 + 127) / 128, 128>>>(d_h0e, ne * 15);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess) {
     const long long n = (long long)nb * (30 + pe::kPairs * 9);
     pe::k_het_summary<<<(unsigned)((n + 127) / 128), 128>>>(D, d_edge, d_fe, ne, hb, K, d_A, d_B);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess) {   // double-word copies of the summary data for the mixed-precision kernel
     const long long na = (long long)nb * 30, nbq = (long long)nb * pe::kPairs * 9;
     pe::k_to_dw4<<<(unsigned)((na + 255) / 256), 256>>>(d_A, na, d_Aw);
     pe::k_to_dw4<<<(unsigned)((nbq + 255) / 256), 256>>>(d_B, nbq, d_Bw);
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(th0);
-  cudaFree(coef);
-  cudaFree(nend);
-  cudaFree(hb);
+  pe::dfree(th0);
+  pe::dfree(coef);
+  pe::dfree(nend);
+  pe::dfree(hb);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(h->mem);
+    pe::dfree(h->mem);
     delete h;
     char msg[200];
     snprintf(msg, sizeof(msg), "pe_hetero_create: %s", cudaGetErrorString(e));
@@ -597,7 +598,7 @@ pe_status pe_hetero_create(pe_detector det, const double* theta0, unsigned mode_
 pe_status pe_hetero_destroy(pe_hetero h) {
   if (h == nullptr) return PE_OK;
   cudaDeviceSynchronize();
-  cudaFree(h->mem);
+  pe::dfree(h->mem);
   cudaGetLastError();
   delete h;
   return PE_OK;
@@ -636,14 +637,14 @@ pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double*
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** p, size_t n) {
     if (e != cudaSuccess) return;
-    e = cudaMallocAsync(p, n + 16, st);
+    e = pe::dmalloc_async(p, n + 16, st);
     if (e == cudaSuccess) bufs.push_back(*p);
   };
   const double* th = theta;
   if (!is_dev(theta)) {
     void* t = nullptr;
     alloc(&t, (size_t)B * PE_NPARAM * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(t, theta, (size_t)B * PE_NPARAM * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = pe::upload_async(t, theta, (size_t)B * PE_NPARAM * sizeof(double), st);
     th = static_cast<const double*>(t);
   }
   void *coef = nullptr, *nend = nullptr, *ll = out_logl, *dh = out_dhhh, *stt = out_status;
@@ -663,14 +664,15 @@ pe_status pe_hetero_loglike_batch(const pe_hetero* hets, int ndet, const double*
   if (e == cudaSuccess) {
     kern<<<B, pe::kTileBins, smem, st>>>(hs, B, static_cast<const pe::SampleCoef*>(coef), static_cast<double*>(ll),
                                          static_cast<double*>(dh));
-    e = cudaGetLastError();
+    e = pe::launch_status();
   }
   if (e == cudaSuccess && hl) e = cudaMemcpyAsync(out_logl, ll, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && hd)
     e = cudaMemcpyAsync(out_dhhh, dh, (size_t)B * ndet * 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && hsx) e = cudaMemcpyAsync(out_status, stt, (size_t)B * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-  for (void* p : bufs) cudaFreeAsync(p, st);
-  if (e == cudaSuccess && (hl || hd || hsx)) e = cudaStreamSynchronize(st);
+  for (void* p : bufs) pe::dfree_async(p, st);
+  if (e == cudaSuccess && (hl || hd || hsx)) e = pe::wait_stream(st);
+  if (e == cudaErrorNotReady) return herr(PE_ETIMEOUT, "pe_hetero_loglike_batch: stream did not finish within the wait limit");
   if (e != cudaSuccess) {
     cudaGetLastError();
     char msg[200];

@@ -18,6 +18,7 @@
 #include "pe_device_f32.cuh"
 #include "pe_device_mixed.cuh"
 #include "pe_kernels.h"
+#include "pe_fault.h"
 
 namespace pe {
 
@@ -335,12 +336,15 @@ __global__ void __launch_bounds__(kTileBins, MINB) k_loglike_fwd(DetSet ds, int 
   const long long total = offi[P];
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair(offi, P, t);
+    if (!PE_CHK(p >= 0 && p < P, 1)) continue;              // checked build: uniform over the CTA
     const int I = p / B, s = p - I * B;
     const long long j0 = (t - offi[p]) * R;                 // first sub-tile of the item in the pair
     const long long q0 = off[p] + j0;                       // its index in the partials
     const long long q1 = min(q0 + R, off[p + 1]);
+    if (!PE_CHK(q0 >= 0 && q1 <= off[P], 2)) continue;
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
+    if (!PE_CHK(ne <= D.nb, 4)) continue;
     const SampleCoef& S = coef[s];
     proj_prologue(D, S, pc);
     if constexpr (PREC == kPrecMixed) {
@@ -429,6 +433,7 @@ __global__ void k_reduce(DetSet ds, int B, const long long* off, const double* p
   for (int I = 0; I < ndet; ++I) {
     const int p = I * B + s;
     const long long t0 = off[p], t1 = off[p + 1];
+    if (!PE_CHK(t0 >= 0 && t1 <= off[ndet * B], 8)) continue;   // checked build: uniform over the warp
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long t = t0 + lane; t < t1; t += 32)
 #pragma unroll
@@ -498,16 +503,16 @@ __global__ void k_inject(int nb, double T, const double* psd, const double2* nor
 cudaError_t launch_grid_tables(double T, long long k0, int nb, double L, double* f, double* f13, double* fm13,
                                double* lnf3, double* fm76, double* fpow, double2* sca, double2* z, cudaStream_t st) {
   k_grid_tables<<<(nb + 127) / 128, 128, 0, st>>>(T, k0, nb, L, f, f13, fm13, lnf3, fm76, fpow, sca, z);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_sincos_table(double2* tab, cudaStream_t st) {
   k_sincos_table<<<(kSinTab + 127) / 128, 128, 0, st>>>(tab);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_psd_model(const double* f, int nb, double L, double oms, double acc, int shaping, int tdi_gen,
                              double* out, cudaStream_t st) {
   k_psd_model<<<(nb + 127) / 128, 128, 0, st>>>(f, nb, L, oms, acc, shaping, tdi_gen, out);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_data_tables(const double* f, const double2* sca, const double2* z, int nb, double T, double L,
                                int tdi_gen, const double2* data, const double* psd, double2* dg, double* gg,
@@ -515,16 +520,16 @@ cudaError_t launch_data_tables(const double* f, const double2* sca, const double
   const int g = (nb + kTileBins - 1) / kTileBins;
   *nblocks = g;
   k_data_tables<<<g, kTileBins, 0, st>>>(f, sca, z, nb, T, L, tdi_gen, data, psd, dg, gg, dd_part, bad);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_sum_parts(const double* part, int n, int w, double* out, cudaStream_t st) {
   k_sum_parts<<<1, 32, 0, st>>>(part, n, w, out);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_prep(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef, int* nend,
                         int* status, cudaStream_t st) {
   k_prep<<<(B + 63) / 64, 64, 0, st>>>(theta, B, mask, ds, coef, nend, status);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_bins, cudaStream_t st) {
   switch (tile_bins) {
@@ -534,7 +539,7 @@ cudaError_t launch_scan_tiles(const int* nend, int P, long long* off, int tile_b
     case 8 * kTileBins: k_scan_tiles<8 * kTileBins><<<1, 1024, 0, st>>>(nend, P, off); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_fwd_offsets(const int* nend, int P, long long* off, long long* offi, int R, cudaStream_t st) {
   cudaError_t e = launch_scan_tiles(nend, P, off, kTileBins, st);
@@ -548,25 +553,25 @@ cudaError_t launch_dw_tables(const double* f, const double* f13, const double* f
   const int n = nb > kSinTab ? nb : kSinTab;
   k_dw_tables<<<(n + 127) / 128, 128, 0, st>>>(f, f13, fm76, sca, z, tab, nb, L, fw, aw, atw, saw, caw, f13w, fm76w, zw,
                                                tabw);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_table_max(const double2* dg, const double* gg, int n, double* mx_part, double* out, cudaStream_t st) {
   const int g = (n + kTileBins - 1) / kTileBins;
   k_table_max<<<g, kTileBins, 0, st>>>(dg, gg, n, mx_part);
   k_max_parts<<<1, 32, 0, st>>>(mx_part, g, out);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_dw_data(const double2* dg, const double* gg, int n, double inv_dgs, double inv_ggs, float4* dgw,
                            float2* ggw, float2* dgf, float* ggf, cudaStream_t st) {
   k_dw_data<<<(n + 127) / 128, 128, 0, st>>>(dg, gg, n, inv_dgs, inv_ggs, dgw, ggw, dgf, ggf);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_f32_tables(const double* f, const double* f13, const double* fm13, const double* lnf3,
                               const double* fm76, const double2* sca, const double2* z, int nb, float* ff, float* f13f,
                               float* fm13f, float* lnf3f, float* fm76f, float2* scaf, float2* zf, cudaStream_t st) {
   k_f32_tables<<<(nb + 127) / 128, 128, 0, st>>>(f, f13, fm13, lnf3, fm76, sca, z, nb, ff, f13f, fm13f, lnf3f, fm76f,
                                                  scaf, zf);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_loglike_fwd(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
                                const long long* offi, int R, double* part, int grid, int prec, cudaStream_t st) {
@@ -578,7 +583,7 @@ template <int MINB, int PREC>
 cudaError_t fwd_one(const DetSet& ds, int B, const SampleCoef* coef, const int* nend, const long long* off,
                     const long long* offi, int R, double* part, int grid, cudaStream_t st) {
   k_loglike_fwd<MINB, PREC><<<grid, kTileBins, 0, st>>>(ds, B, coef, nend, off, R > 1 ? offi : off, R, part);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 template <int MINB, int PREC>
 int fwd_occ() {
@@ -629,7 +634,7 @@ cudaError_t launch_reduce(const DetSet& ds, int B, const long long* off, const d
   const long long warps = B;
   const int grid = int((warps * 32 + threads - 1) / threads);
   k_reduce<<<grid, threads, 0, st>>>(ds, B, off, part, coef, logl, dhhh);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out, int prec, cudaStream_t st) {
   const int g = (D.nb + kTileBins - 1) / kTileBins;
@@ -639,11 +644,14 @@ cudaError_t launch_signal(const DetDev& D, const SampleCoef* coef, double2* out,
     k_signal<kPrecFP32><<<g, kTileBins, 0, st>>>(D, coef, out);
   else
     k_signal<kPrecFP64><<<g, kTileBins, 0, st>>>(D, coef, out);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
 cudaError_t launch_inject(int nb, double T, const double* psd, const double2* normals, double2* h, cudaStream_t st) {
   k_inject<<<(3 * nb + 127) / 128, 128, 0, st>>>(nb, T, psd, normals, h);
-  return cudaGetLastError();
+  return pe::launch_status();
 }
+
+// Index-check error word of this file's kernels (checked build; 0 otherwise), cleared when read.
+int checked_take_kernels() { return pe_checked_take_local(); }
 
 }  // namespace pe

@@ -67,5 +67,9 @@ int fwd_blocks_per_sm();
 // Defined in pe_api.cu: handle validation and error reporting shared with other entry points.
 pe_status detset_from_handles(const pe_detector* dets, int ndet, DetSet* ds);
 pe_status set_error(pe_status st, const char* msg);
+// Bounded host wait for the work queued so far on st (an event polled with cudaEventQuery until
+// the limit pe_set_wait_limit set): cudaSuccess, cudaErrorNotReady when the limit ran out (the
+// work stays queued), or the stream's error.
+cudaError_t wait_stream(cudaStream_t st);
 
 }  // namespace pe

@@ -22,6 +22,7 @@
 #include "pe_kernels.h"
 #include "pe_plan.h"
 #include "pespace_gb300.h"
+#include "pe_fault.h"
 
 namespace pe {
 namespace {
@@ -256,7 +257,7 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
   pl->ds = ds;
   pl->B = B;
   pl->mask = mode_mask;
-  if (cudaMalloc(&pl->scratch, bytes) != cudaSuccess) {
+  if (pe::dmalloc(&pl->scratch, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete pl;
     return pe::set_error(PE_ENOMEM, "pe_plan_create: scratch allocation failed");
@@ -296,7 +297,7 @@ pe_status pe_plan_create(const pe_detector* dets, int ndet, int B, unsigned mode
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (pl->graph) cudaGraphDestroy(pl->graph);
-    cudaFree(pl->scratch);
+    pe::dfree(pl->scratch);
     delete pl;
     char msg[256];
     snprintf(msg, sizeof(msg), "pe_plan_create: %s", cudaGetErrorString(e));
@@ -358,7 +359,7 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
   const size_t o_part = a256(o_offi + (P + 1) * sizeof(long long));
   const size_t bytes = o_part + (size_t)max_tiles * 6 * sizeof(double);
   void* scratch = nullptr;
-  if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+  if (pe::dmalloc(&scratch, bytes) != cudaSuccess) {
     cudaGetLastError();
     return pe::set_error(PE_ENOMEM, "pe_autotune: scratch allocation failed");
   }
@@ -375,7 +376,7 @@ pe_status pe_autotune(const pe_detector* dets, int ndet, const double* theta_dev
   if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, (int)P, off, pe::kTileBins, cs);
   if (e == cudaSuccess) e = pe::autotune_fwd(ds, B, mode_mask, coef, nend, off, offi, part, max_tiles, cs, &best);
   if (cs) cudaStreamDestroy(cs);
-  cudaFree(scratch);
+  pe::dfree(scratch);
   if (e != cudaSuccess) {
     cudaGetLastError();
     char msg[256];
@@ -395,7 +396,7 @@ pe_status pe_plan_destroy(pe_plan plan) {
   cudaDeviceSynchronize();
   cudaGraphExecDestroy(plan->exec);
   cudaGraphDestroy(plan->graph);
-  cudaFree(plan->scratch);
+  pe::dfree(plan->scratch);
   cudaGetLastError();
   delete plan;
   return PE_OK;

@@ -19,9 +19,9 @@ def lib():
     return L.lib()
 
 
-def declared_functions():
+def declared_functions(header_glob="pespace_gb300.h"):
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in glob.glob(os.path.join(ROOT, "include", header_glob)):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\*?(pe_[A-Za-z0-9_]+)\s*\(", src, re.M):
@@ -39,6 +39,23 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_test_build_exports_its_header_and_the_product_does_not(lib):
+    """include/pespace_gb300_test.h is exported by the test build (fault injection, index checks)
+    alongside the whole product boundary, and by nothing the product library loads."""
+    test_names = declared_functions("pespace_gb300_test.h")
+    assert test_names and all(n.startswith("pe_test_") for n in test_names)
+    tlib = C.CDLL(B.build(variant="test"))
+    assert not [n for n in test_names + declared_functions() if not hasattr(tlib, n)]
+    assert not [n for n in test_names if hasattr(lib, n)]
+    tlib.pe_test_fault_arm.argtypes = [C.c_int, C.c_long]
+    tlib.pe_test_fault_count.argtypes = [C.c_int]
+    tlib.pe_test_fault_count.restype = C.c_long
+    assert tlib.pe_test_fault_arm(3, 1) == L.PE_EINVAL
+    assert tlib.pe_test_fault_arm(0, -1) == L.PE_EINVAL
+    assert tlib.pe_test_fault_arm(-1, 0) == L.PE_OK
+    assert tlib.pe_test_fault_count(7) == -1
 
 
 def test_abi_version(lib):
@@ -95,3 +112,19 @@ def test_hetero_argument_errors_without_cuda(lib):
     assert lib.pe_hetero_create(None, None, 0x1F, None, 0, C.byref(h)) == L.PE_EINVAL
     assert lib.pe_hetero_loglike_batch(None, 1, None, 1, None, None, None, None) == L.PE_EINVAL
     assert lib.pe_hetero_destroy(None) == L.PE_OK
+
+
+def test_wait_limit_without_cuda(lib):
+    """The bounded host wait's limit (PE_ETIMEOUT past it) is set and read without a GPU."""
+    old = L.pe_get_wait_limit()
+    assert old > 0
+    try:
+        L.pe_set_wait_limit(2.5)
+        assert L.pe_get_wait_limit() == 2.5
+        for bad in (0.0, -1.0, float("inf"), float("nan")):
+            with pytest.raises(L.PeError) as e:
+                L.pe_set_wait_limit(bad)
+            assert e.value.status == L.PE_EINVAL
+        assert L.pe_get_wait_limit() == 2.5
+    finally:
+        L.pe_set_wait_limit(old)
