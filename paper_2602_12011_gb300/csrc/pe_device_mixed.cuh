@@ -235,14 +235,17 @@ __device__ __forceinline__ void bin_xyz_mixed(const DetDev& D, const SampleCoef&
 }
 
 // A/E/T combinations (without Q n_c) in double words: B_A = Z' - X', B_E = X' - 2Y' + Z',
-// B_T = X' + Y' + Z'.
+// B_T = X' + Y' + Z'. At long wavelength (a = pi f L << 1) B_T cancels to O(a^3) of the brackets
+// (the six links' O(1) terms sum to zero exactly), so it is summed exactly (df_sum3_exact): a
+// rounded double-word sum would leave an error of ~2^-47 of the brackets, which for the TianQin
+// arm at 1e-4 Hz is ~1e-2 of B_T itself.
 __device__ __forceinline__ void aet_from_xyz_dw(const cdf x[3], cdf o[3]) {
   o[0].re = dfl_sub(x[2].re, x[0].re);
   o[0].im = dfl_sub(x[2].im, x[0].im);
   o[1].re = dfl_sub(dfl_add(x[0].re, x[2].re), df_scale2(x[1].re, 2.0f));
   o[1].im = dfl_sub(dfl_add(x[0].im, x[2].im), df_scale2(x[1].im, 2.0f));
-  o[2].re = dfl_add(dfl_add(x[0].re, x[1].re), x[2].re);
-  o[2].im = dfl_add(dfl_add(x[0].im, x[1].im), x[2].im);
+  o[2].re = df_sum3_exact(x[0].re, x[1].re, x[2].re);
+  o[2].im = df_sum3_exact(x[0].im, x[1].im, x[2].im);
 }
 
 }  // namespace pe

@@ -97,6 +97,23 @@ __device__ __forceinline__ df df_from_bits(double a) {
   return df_make(h, trunc_to_float(__double_as_longlong(a - hd)));
 }
 
+// a + b + c of three double words (normalised or lazy) as a normalised double word whose error is
+// set by the sum itself, not by the operands: the three high words and the three low words are
+// each summed exactly by TwoSum cascades, the high words' residuals join the low words' sum
+// exactly, and only the last, tiny residuals are rounded (below 2^-72 of the operands). For sums
+// that cancel far below their operands, such as the TDI T channel X' + Y' + Z' at long wavelength.
+__device__ __forceinline__ df df_sum3_exact(df a, df b, df c) {
+  const df s1 = two_sum(a.x, b.x);
+  const df s2 = two_sum(s1.x, c.x);          // a.hi + b.hi + c.hi = s2.x + s1.y + s2.y
+  const df t1 = two_sum(a.y, b.y);
+  const df t2 = two_sum(t1.x, c.y);          // a.lo + b.lo + c.lo = t2.x + t1.y + t2.y
+  const df t3 = two_sum(t2.x, s1.y);
+  const df t4 = two_sum(t3.x, s2.y);         // sum = s2.x + t4.x + (t1.y + t2.y + t3.y + t4.y)
+  const float r = __fadd_rn(__fadd_rn(t1.y, t2.y), __fadd_rn(t3.y, t4.y));
+  const df u = two_sum(s2.x, t4.x);
+  return two_sum(u.x, __fadd_rn(u.y, r));
+}
+
 // 1/x: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0) (error delta^2)
 __device__ __forceinline__ df df_rcp(df x) {
   const float y0 = __frcp_rn(x.x);
