@@ -8,10 +8,12 @@
 // allocates its inputs and outputs once, up front, and this entry point then touches no
 // allocator at all.
 //
-// The scratch lives in g_noalloc_scratch below: kNoAllocScratchBytes (32 MiB) on every GPU that
-// loads the library, held until the process exits. Its device address is looked up once per
-// device with cudaGetSymbolAddress (the host-side symbol is only a stand-in, not a device
-// address) by the entry point's first call on that device.
+// The scratch lives in g_noalloc_scratch below: kNoAllocScratchBytes (32 MiB) per device. CUDA
+// loads this file's module lazily, so the array is committed on a device by the first call there,
+// and held until the process exits. Every call looks up its device address with
+// cudaGetSymbolAddress on the current device (the host-side symbol is only a stand-in, not a
+// device address); once the module is loaded the lookup allocates nothing, and no cached address
+// can outlive a device reset.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -24,46 +26,35 @@
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_dev[kMaxDevices] = {};
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// device (or managed) memory of the current device
 bool device_ptr(const void* p) {
   if (p == nullptr) return false;
+  int dev = -1;
   cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device, looked up on every call.
 pe_status scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
     cudaGetLastError();
-    return pe::set_error(PE_ECUDA, "pe_loglike_batch_noalloc: no current CUDA device");
+    char msg[256];
+    snprintf(msg, sizeof(msg), "pe_loglike_batch_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return pe::set_error(PE_ECUDA, msg);
   }
-  if (dev < 0 || dev >= kMaxDevices) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: device index too large");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (g_scratch_dev[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      char msg[256];
-      snprintf(msg, sizeof(msg), "pe_loglike_batch_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return pe::set_error(PE_ECUDA, msg);
-    }
-    g_scratch_dev[dev] = p;
-  }
-  *out = g_scratch_dev[dev];
+  *out = p;
   return PE_OK;
 }
 
@@ -79,7 +70,8 @@ extern "C" pe_status pe_loglike_batch_noalloc(const pe_detector* dets, int ndet,
   if (!pe::fwd_mask_ok(mode_mask)) return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: bad mode mask");
   if (!device_ptr(theta) || !device_ptr(out_logl) || (out_dhhh && !device_ptr(out_dhhh)) ||
       (out_status && !device_ptr(out_status)))
-    return pe::set_error(PE_EINVAL, "pe_loglike_batch_noalloc: theta and every output must be device pointers");
+    return pe::set_error(PE_EINVAL,
+                         "pe_loglike_batch_noalloc: theta and every output must be device pointers of the current device");
   // Scratch layout: coefficients [B], active bins [P], sub-tile offsets [P+1], work-item offsets
   // [P+1], sub-tile partials [sub-tiles][6]. The work items take the precision's default number of
   // sub-tiles (no tuned choice is read here).
