@@ -33,7 +33,7 @@ METRIC = "log-likelihood evals/s (HM, 3 TDI ch, batched) vs plain path; grad eva
 UNIT = "evals/s"
 MSUN_S = 4.925490947641267e-6
 # Work per active (sample, mode, bin) unit of the fused forward kernel, from the ncu SASS counters
-# of one launch on the 64-sample case of this workload (profiles/k_loglike_fwd_*_ncu.md):
+# of one launch on the 64-sample case of this workload:
 #   fp64_flops  DFMA x 2 + DMUL + DADD
 #   fp64_inst   every FP64-pipe instruction (DFMA, DMUL, DADD, DSETP, F2F, FRND)
 #   fp32_inst   FFMA + FMUL + FADD (the double-word arithmetic of the mixed path)
@@ -43,9 +43,27 @@ UNIT_COUNTS = {
     # FP32 path: fp64_inst counts the FRND and F2F of CUDA's FP32 sincospif/sinf and conversions
     "fp32": {"fp64_flops": 0.25, "fp64_inst": 9.2, "fp32_inst": 354.4},
 }
-# DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum
-# (profiles/k_loglike_fwd_dram_lisa_hm_T2^22_B1024.md): the per-bin tables, read once per launch
+# SHA-256 (first 16 hex digits) of the per-bin unit's sources the counts were taken on; the bench
+# marks the counts stale (and warns) when the sources have changed since.
+UNIT_SOURCES = ("pe_device.cuh", "pe_device_mixed.cuh", "pe_device_f32.cuh", "pe_df.cuh", "pe_kernels.cu")
+UNIT_COUNTS_SOURCE_SHA = {"fp64": None, "mixed": None, "fp32": None}
+# DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum:
+# the per-bin tables, read once per launch
 TRAFFIC = {"fp64": 36.55e6 + 0.01e6, "mixed": 39.84e6 + 0.74e6, "fp32": None}
+# Algorithmic work of the method (oracle/flop_model.py: the oracle's own operations, counted on
+# 16 samples of this workload): add/sub/mul/div per active (sample, mode, bin) unit and per active
+# (sample, bin) for the A/E/T and likelihood terms, and math-library calls per unit.
+ALG_MODEL = {"flops_per_unit": 1755.0, "flops_per_bin": 63.0, "math_calls_per_unit": 81.0,
+             "source": "oracle/flop_model.py (plain per-bin formulation, counted with an operation-counting scalar)"}
+
+
+def unit_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in UNIT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_12011_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -83,6 +101,22 @@ def active_units(theta: np.ndarray, T: float, k0: int, nb: int, mode_mask: int) 
             if fe <= f_lo:
                 continue
             tot += min(nb, int(math.ceil(fe * T - 1e-9)) - k0)
+    return tot
+
+
+def active_bins(theta: np.ndarray, T: float, k0: int, nb: int, mode_mask: int) -> int:
+    """Active (sample, bin) pairs: bins below the largest active mode's taper end."""
+    tot = 0
+    f_hi = (k0 + nb - 1) / T
+    for th in theta:
+        M = th[0] * MSUN_S
+        fisco = 6 ** -1.5 / (2 * math.pi * M)
+        fe = 0.0
+        for bit, (l, m) in enumerate(W.MODES):
+            if (mode_mask >> bit) & 1 and not (m % 2 == 1 and th[1] == 1.0):
+                fe = max(fe, m * fisco)
+        fe = min(fe, f_hi + 1.0 / T)
+        tot += max(0, min(nb, int(math.ceil(fe * T - 1e-9)) - k0))
     return tot
 
 
@@ -130,31 +164,51 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(dets_spec, theta, mode_mask, n_samples, noise_seed, inj, inj_mask):
-    """The oracle, as it stands, on the host cores: a bounded sample of the same workload."""
-    from oracle import oracle as O
-    O.build()
+def _oracle_dets(O, dets_spec, inj, inj_mask, noise_seed):
     ods = []
     for det, T, k0, nb in dets_spec:
-        nrm = W.normals(nb, noise_seed)
-        data = O.make_data(det, inj, inj_mask, T, k0, nb, nrm)
+        data = O.make_data(det, inj, inj_mask, T, k0, nb, W.normals(nb, noise_seed))
         psd = O.psd(det, (k0 + np.arange(nb)) / T)
         ods.append(O.Detector(det, T, k0, nb, data, psd))
+    return ods
+
+
+def _timed_oracle(O, ods, theta, mask, nthreads):
+    t0 = time.perf_counter()
+    O.loglike_batch(ods, theta, mask, nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(dets_spec, theta, mode_mask, n_samples, noise_seed, inj, inj_mask):
+    """The oracle, as it stands, on the host cores: bounded samples of the benchmark workload (all
+    cores, and one core as in the paper's CPU comparison), of the single-source plain workload
+    (whole) and of the three-detector network (one core and all cores)."""
+    from oracle import oracle as O
+    O.build()
+    ods = _oracle_dets(O, dets_spec, inj, inj_mask, noise_seed)
     th = theta[:n_samples]
     cores = O.max_threads()
-    t0 = time.perf_counter()
-    O.loglike_batch(ods, th, mode_mask, nthreads=cores)
-    dt = time.perf_counter() - t0
-    # the paper's CPU comparison runs on one core: the same oracle on one thread, a smaller sample
-    n1 = max(1, n_samples // 16)
-    t1 = time.perf_counter()
-    O.loglike_batch(ods, theta[:n1], mode_mask, nthreads=1)
-    dt1 = time.perf_counter() - t1
+    dt = _timed_oracle(O, ods, th, mode_mask, cores)
+    n1 = 16
+    dt1 = _timed_oracle(O, ods, theta[:n1], mode_mask, 1)
+    ws = W.single_22()
+    o1 = _oracle_dets(O, ws["dets"], ws["inj"], ws["inj_mask"], ws["noise_seed"])
+    ds1 = _timed_oracle(O, o1, ws["theta"], ws["mode_mask"], 1)
+    wn = W.network_hm(4096)
+    on = _oracle_dets(O, wn["dets"], wn["inj"], wn["inj_mask"], wn["noise_seed"])
+    dn1 = _timed_oracle(O, on, wn["theta"][:16], wn["mode_mask"], 1)
+    dn = _timed_oracle(O, on, wn["theta"][:64], wn["mode_mask"], cores)
     return {"value": th.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d of the %d-sample batch, all modes, full grid, OpenMP over samples (%.1f s wall)"
                       % (th.shape[0], theta.shape[0], dt),
             "single_core": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
-                            "sample": "first %d samples of the same batch, one thread (%.1f s)" % (n1, dt1)}}
+                            "sample": "first %d samples of the same batch, one thread (%.1f s)" % (n1, dt1)},
+            "single_source": {"value": 1.0 / ds1, "unit": UNIT, "cores": 1, "workload": ws["name"],
+                              "sample": "the whole workload: one sample, (2,2), 52,324 bins (%.2f s)" % ds1},
+            "network": {"value": 64 / dn, "unit": UNIT, "cores": cores, "workload": wn["name"],
+                        "sample": "first 64 of the 4096 samples, OpenMP over samples (%.1f s)" % dn,
+                        "single_core": {"value": 16 / dn1, "unit": UNIT, "cores": 1,
+                                        "sample": "first 16 samples, one thread (%.1f s)" % dn1}}}
 
 
 def run_reference(args, wl):
@@ -195,34 +249,65 @@ def run_reference(args, wl):
 PIPE_PER_CLK = {"fp64": 2.0, "fp32": 128.0}
 
 
-def roofline(prec: str, units: int, launch_s: float, fp64_tflops: float, fp32_tflops: float,
-             n_sm: int = 152, sm_max_mhz: float = 2070.0) -> dict:
+def roofline(prec: str, units: int, launch_s: float, peaks: dict, n_sm: int = 152, sm_max_mhz: float = 2070.0,
+             sm_mhz_run: float = None, bins: int = 0) -> dict:
     """ALU roofline of the fused forward kernel: per pipe, the instructions one launch issues
-    (per-unit count x active units) per second against the pipe's measured FMA-loop rate (and,
-    beside it, the nominal rate from the unit counts and the maximum clock); the binding pipe is
-    the busier one."""
+    (per-unit count x active units) per second against the pipe's measured FMA-loop rate, against
+    the nominal rate at the maximum clock, and against the nominal rate at the median SM clock
+    sampled while the kernel ran; the binding pipe is the busier one. Beside it, the algorithmic
+    view: the oracle-counted work of the method (ALG_MODEL) per second against the FP64 peak."""
     if prec not in UNIT_COUNTS:
         return None
     c = UNIT_COUNTS[prec]
     ups = units / launch_s
     pipes = {}
-    for name, inst, tf in (("fp64", c["fp64_inst"], fp64_tflops), ("fp32", c["fp32_inst"], fp32_tflops)):
-        peak = tf * 1e3 / 2.0   # G FMA instructions/s of the measured loop
+    for name, inst in (("fp64", c["fp64_inst"]), ("fp32", c["fp32_inst"])):
+        loop = peaks[name]
+        peak = loop["tflops"] * 1e3 / 2.0   # G FMA instructions/s of the measured loop
         nominal = PIPE_PER_CLK[name] * n_sm * sm_max_mhz / 1e3
         ach = inst * ups / 1e9
         pipes[name] = {"inst_per_unit": inst, "achieved_ginst_s": ach, "peak_ginst_s": peak, "frac": ach / peak,
+                       "peak_loop_sm_mhz": loop.get("sm_mhz"),
+                       "peak_loop_at_its_clock_frac_nominal": (peak / (PIPE_PER_CLK[name] * n_sm * loop["sm_mhz"] / 1e3)
+                                                               if loop.get("sm_mhz") else None),
                        "peak_nominal_ginst_s": nominal, "frac_nominal": ach / nominal}
+        if sm_mhz_run:
+            pipes[name]["frac_nominal_at_run_clock"] = ach / (PIPE_PER_CLK[name] * n_sm * sm_mhz_run / 1e3)
     bind = max(pipes, key=lambda k: pipes[k]["frac"])
+    sha = unit_sources_sha()
+    alg_tflops = (ALG_MODEL["flops_per_unit"] * units + ALG_MODEL["flops_per_bin"] * bins) / launch_s / 1e12
+    fp64_nominal_tflops = 2 * PIPE_PER_CLK["fp64"] * n_sm * sm_max_mhz / 1e6
     return {"bound": "alu", "pipe": bind, "unit": "Ginst/s", "achieved": pipes[bind]["achieved_ginst_s"],
             "peak": pipes[bind]["peak_ginst_s"], "frac": pipes[bind]["frac"],
-            "peak_kind": "measured FMA loops (FP64 and FP32, 1 s each)",
+            "peak_kind": "measured FMA loops (FP64 and FP32, 1 s each; clocks sampled during them)",
             "peak_nominal": pipes[bind]["peak_nominal_ginst_s"], "frac_nominal": pipes[bind]["frac_nominal"],
             "peak_nominal_kind": "%g inst/clk/SM x %d SMs x %g MHz" % (PIPE_PER_CLK[bind], n_sm, sm_max_mhz),
+            "frac_nominal_at_run_clock": pipes[bind].get("frac_nominal_at_run_clock"), "run_sm_mhz": sm_mhz_run,
             "kernel": "k_loglike_fwd",
-            "launch_ms": launch_s * 1e3, "units_per_launch": units, "units_per_s": ups,
-            "fp64_tflops": c["fp64_flops"] * ups / 1e12, "fp64_tflops_peak": fp64_tflops,
-            "fp64_flops_frac": c["fp64_flops"] * ups / 1e12 / fp64_tflops, "pipes": pipes,
-            "traffic": TRAFFIC[prec], "traffic_gbs": TRAFFIC[prec] / launch_s / 1e9 if TRAFFIC[prec] else None}
+            "launch_ms": launch_s * 1e3, "units_per_launch": units, "bins_per_launch": bins, "units_per_s": ups,
+            "fp64_tflops": c["fp64_flops"] * ups / 1e12, "fp64_tflops_peak": peaks["fp64"]["tflops"],
+            "fp64_flops_frac": c["fp64_flops"] * ups / 1e12 / peaks["fp64"]["tflops"],
+            "alg_flops_per_unit": ALG_MODEL["flops_per_unit"], "alg_flops_per_bin": ALG_MODEL["flops_per_bin"],
+            "alg_tflops": alg_tflops, "alg_frac_nominal": alg_tflops / fp64_nominal_tflops,
+            "alg_note": ("the oracle's plain formulation counted per active unit (%s); a fraction above 1 is work "
+                         "the kernel's factored algebra and tables avoid" % ALG_MODEL["source"]),
+            "unit_counts_source_sha": UNIT_COUNTS_SOURCE_SHA[prec], "unit_sources_sha": sha,
+            "unit_counts_current": UNIT_COUNTS_SOURCE_SHA[prec] == sha,
+            "pipes": pipes,
+            "traffic": TRAFFIC[prec] if UNIT_COUNTS_SOURCE_SHA[prec] == sha else None,
+            "traffic_gbs": TRAFFIC[prec] / launch_s / 1e9 if TRAFFIC[prec] else None}
+
+
+def measure_peaks(L, local_rank: int) -> dict:
+    """The FP64 and FP32 FMA-loop rates (1 s each) with the SM clock sampled during each."""
+    out = {}
+    for name, fn in (("fp64", L.pe_measure_fp64_peak), ("fp32", L.pe_measure_fp32_peak)):
+        cs = ClockSampler()
+        time.sleep(0.2)
+        tf = fn(1.0)
+        clk = cs.stop(local_rank)
+        out[name] = {"tflops": tf, "sm_mhz": clk.get("sm_mhz"), "clock_reasons": clk.get("reasons")}
+    return out
 
 
 def main():
@@ -300,12 +385,19 @@ def main():
     result_ok = bool(torch.isfinite(out_dev).all().item())
 
     units = active_units(theta, T, k0, nb, mask)
+    bins = active_bins(theta, T, k0, nb, mask)
     fwd_avg_s = (fwd_ms / max(fwd_launches, 1)) / 1e3
-    peak64 = L.pe_measure_fp64_peak(1.0)
-    peak32 = L.pe_measure_fp32_peak(1.0)
+    peaks = measure_peaks(L, local_rank)
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    roof = roofline(args.precision, units, fwd_avg_s, peak64, peak32, n_sm, sm_max)
+    roof = roofline(args.precision, units, fwd_avg_s, peaks, n_sm, sm_max, clk.get("sm_mhz"), bins)
+    if roof and not roof["unit_counts_current"]:
+        sys.stderr.write("bench: the per-unit instruction counts were taken on other unit sources (%s, now %s); "
+                         "re-take them with ncu\n" % (roof["unit_counts_source_sha"], roof["unit_sources_sha"]))
+    # every rank's per-sample results in one place (what a sampler's driver needs), outside the
+    # timed region
+    gathered = shard.gather_results(out_dev, world * B, world) if world > 1 else out_dev
+    result_ok = result_ok and bool(torch.isfinite(gathered).all().item())
 
     # ---- precision study (the paper's low-precision option against FP64): the same batch through
     # the other forward path, device-timed the same way; accuracy of its log L against the FP64
@@ -344,8 +436,8 @@ def main():
             absmax = (llo - ll64).abs().max().item()
             study[other] = {"value": B * K / (sum(ems) / 1e3), "ms_per_step": sum(ems) / K, "tuning": tuned_o,
                             "max_rel_dlogl_vs_fp64": rel, "max_abs_dlogl_vs_fp64": absmax, "parity_bar": 1e-10,
-                            "roofline": roofline(other, units, (o_ms / max(o_n, 1)) / 1e3, peak64, peak32,
-                                                 n_sm, sm_max)}
+                            "roofline": roofline(other, units, (o_ms / max(o_n, 1)) / 1e3, peaks, n_sm, sm_max,
+                                                 clk.get("sm_mhz"), bins)}
         study["note"] = ("mixed: FP64 TaylorF2 phase, t_f, turn reductions and tile sums; response "
                          "geometry, TDI, A/E/T and per-bin products in double-word FP32 arithmetic. "
                          "fp32: every step in FP32 (the paper's float32 option); misses the 1e-10 bar")
@@ -385,6 +477,25 @@ def main():
     torch.cuda.synchronize()
     plain_graph_value = n_plain / (e0.elapsed_time(e1) / 1e3)
     plan1.close()
+
+    # ---- the single-source plain workload (LISA, (2,2), T = 2^20 s, 52,324 bins, one parameter
+    # point): one call per evaluation, device-timed over 200 calls
+    ws = W.single_22()
+    det1, T1, k01, nb1 = ws["dets"][0]
+    g1 = L.Detector(det1, T1, k01, nb1)
+    g1.inject(ws["inj"], ws["inj_mask"], W.normals(nb1, ws["noise_seed"]))
+    th1 = torch.tensor(ws["theta"], device="cuda")
+    for _ in range(5):
+        L.pe_loglike_batch([g1.handle], th1, 1, ws["mode_mask"], out1, None, None, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(200):
+        L.pe_loglike_batch([g1.handle], th1, 1, ws["mode_mask"], out1, None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single = {"value": 200 / (e0.elapsed_time(e1) / 1e3), "unit": UNIT, "workload": ws["name"],
+              "calls": 200, "note": "one pe_loglike_batch call (B = 1) per evaluation, device-timed"}
+    g1.close()
 
     # ---- gradient evals/s: hand-written adjoint over the same batch, device-timed
     grad_dev = torch.empty((B, 11), dtype=torch.float64, device="cuda")
@@ -494,10 +605,34 @@ def main():
         tho = W.draw_prior(2048, 2606, T)
         mm = srg.mismatch(gd, torch.tensor(tho, device="cuda"), mask64).cpu().numpy()
         inbox = (tho[:, 0] >= 3e5) & (tho[:, 1] <= 8.0)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        # the same node-spline path without the network (the plain generator's exact node values),
+        # and the plain mixed-precision path, on the same batch
+        srg.set_node_source(1)
+        ms_n = timed(lambda: srg.loglike([gd], tts, mask64))
+        mm_n = srg.mismatch(gd, torch.tensor(tho, device="cuda"), mask64).cpu().numpy()
+        srg.set_node_source(0)
+        ms_mx = timed(lambda: L.pe_loglike_batch(hs, tts, Bs, mask64 | L.PE_PREC_MIXED, outs, None, None, stream))
         sur = {"value": world * Bs / (ms_s / 1e3), "unit": UNIT, "plain_same_batch": world * Bs / (ms_p / 1e3),
                "gain": ms_p / ms_s, "batch": Bs, "used_fraction": float(used.float().mean().item()),
+               "no_network_same_batch": world * Bs / (ms_n / 1e3), "network_over_no_network": ms_n / ms_s,
+               "plain_mixed_same_batch": world * Bs / (ms_mx / 1e3), "network_over_plain_mixed": ms_mx / ms_s,
                "train_s": t_tr, "train_loss": sl, "heldout_pass_1e-3": float(np.mean(mm[inbox] <= 1e-3)),
-               "heldout_in_box": int(inbox.sum())}
+               "heldout_max_mismatch_no_network": float(np.max(mm_n[inbox])),
+               "heldout_in_box": int(inbox.sum()),
+               "note": ("network: MLP node values (3PN/3.5PN phase terms, |H_lm|) + node splines; no_network: "
+                        "the same splines from the plain generator's exact node values; plain: per-bin FP64; "
+                        "plain_mixed: per-bin FP64 phase with double-word geometry (1e-10 parity)")}
         srg.close()
 
     # ---- heterodyned (relative-binning) likelihood, the second workload: 1024 draws in the posterior's
@@ -590,6 +725,7 @@ def main():
                     "d2h_bytes_per_step": int(B * 8)},
             "plain_path": {"value": plain_value, "unit": UNIT, "samples": n_plain,
                            "graph_plan_value": plain_graph_value, "batched_same_samples": batched_same},
+            "single_source": single,
             "fisher": fisher,
             "network": net,
             "surrogate": sur,

@@ -90,6 +90,7 @@ def lib():
         L.or_link.argtypes = [C.POINTER(OrConfig), _P, C.c_int, C.c_int, _P, C.c_int64, C.c_int, C.c_int,
                               C.c_double, _P]
         L.or_response.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, _P, C.c_int64, _P]
+        L.or_op_count.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, _P, C.c_int64, _P, _P, C.c_double, _P]
         L.or_response_ld.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, _P, C.c_int64, _P]
         L.or_response_xyz.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, _P, C.c_int64, _P]
         L.or_make_data.argtypes = [C.POINTER(OrConfig), _P, C.c_uint, C.c_double, C.c_int64, C.c_int64, _P, _P]
@@ -184,6 +185,24 @@ def response(det: dict, theta, mode_mask: int, f) -> np.ndarray:
     c = config(det)
     lib().or_response(C.byref(c), _ptr(th), mode_mask, _ptr(f), f.size, _ptr(out))
     return out.view(np.complex128).reshape(3, f.size)
+
+
+OP_NAMES = ("add", "mul", "div", "sqrt", "sincos", "exp", "log", "cbrt", "pow", "cmp")
+
+
+def op_count(det: dict, theta, mode_mask: int, f, data=None, psd=None, T: float = 1.0) -> dict:
+    """Operations of the oracle's own steps per active (mode, bin) unit, per active bin and per
+    sample (see or_op_count), counted with its operation-counting scalar."""
+    th, f = _f64(theta), _f64(f)
+    out = np.zeros(2 + 3 * len(OP_NAMES))
+    c = config(det)
+    dp = None if data is None else np.ascontiguousarray(np.asarray(data, dtype=np.complex128).reshape(3, f.size))
+    pp = None if psd is None else _f64(psd).reshape(3, f.size)
+    lib().or_op_count(C.byref(c), _ptr(th), mode_mask, _ptr(f), f.size, None if dp is None else _ptr(dp),
+                      None if pp is None else _ptr(pp), float(T), _ptr(out))
+    k = len(OP_NAMES)
+    return {"units": out[0], "bins": out[1], "per_unit": dict(zip(OP_NAMES, out[2:2 + k])),
+            "per_bin": dict(zip(OP_NAMES, out[2 + k:2 + 2 * k])), "per_sample": dict(zip(OP_NAMES, out[2 + 2 * k:]))}
 
 
 def response_ld(det: dict, theta, mode_mask: int, f) -> np.ndarray:

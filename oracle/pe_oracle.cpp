@@ -117,6 +117,44 @@ DUAL_T inline Dual<T, N> pow(const Dual<T, N>& a, double p) {
   T f = pow(a.v, p); return chain(a, f, T(p) * pow(a.v, p - 1.0)); }
 
 // ----------------------------------------------------------------------------------------
+// Operation-counting scalar: a double that counts every arithmetic operation and math-library
+// call made on it (the algorithmic-work model of the method, or_op_count). Single-threaded use.
+// ----------------------------------------------------------------------------------------
+enum { OP_ADD, OP_MUL, OP_DIV, OP_SQRT, OP_SINCOS, OP_EXP, OP_LOG, OP_CBRT, OP_POW, OP_CMP, OP_N };
+static unsigned long long g_ops[OP_N];
+struct Flop {
+  double v;
+  Flop() : v(0.0) {}
+  Flop(double x) : v(x) {}
+};
+inline double val(const Flop& x) { return x.v; }
+inline Flop fop(int k, double r) { ++g_ops[k]; return Flop(r); }
+inline Flop operator+(const Flop& a, const Flop& b) { return fop(OP_ADD, a.v + b.v); }
+inline Flop operator-(const Flop& a, const Flop& b) { return fop(OP_ADD, a.v - b.v); }
+inline Flop operator*(const Flop& a, const Flop& b) { return fop(OP_MUL, a.v * b.v); }
+inline Flop operator/(const Flop& a, const Flop& b) { return fop(OP_DIV, a.v / b.v); }
+inline Flop operator+(const Flop& a, double b) { return fop(OP_ADD, a.v + b); }
+inline Flop operator+(double a, const Flop& b) { return fop(OP_ADD, a + b.v); }
+inline Flop operator-(const Flop& a, double b) { return fop(OP_ADD, a.v - b); }
+inline Flop operator-(double a, const Flop& b) { return fop(OP_ADD, a - b.v); }
+inline Flop operator*(const Flop& a, double b) { return fop(OP_MUL, a.v * b); }
+inline Flop operator*(double a, const Flop& b) { return fop(OP_MUL, a * b.v); }
+inline Flop operator/(const Flop& a, double b) { return fop(OP_DIV, a.v / b); }
+inline Flop operator/(double a, const Flop& b) { return fop(OP_DIV, a / b.v); }
+inline Flop operator-(const Flop& a) { return Flop(-a.v); }
+inline Flop& operator+=(Flop& a, const Flop& b) { a = a + b; return a; }
+inline Flop& operator-=(Flop& a, const Flop& b) { a = a - b; return a; }
+inline Flop& operator*=(Flop& a, const Flop& b) { a = a * b; return a; }
+inline Flop sin(const Flop& a) { return fop(OP_SINCOS, std::sin(a.v)); }
+inline Flop cos(const Flop& a) { return fop(OP_SINCOS, std::cos(a.v)); }
+inline Flop exp(const Flop& a) { return fop(OP_EXP, std::exp(a.v)); }
+inline Flop log(const Flop& a) { return fop(OP_LOG, std::log(a.v)); }
+inline Flop sqrt(const Flop& a) { return fop(OP_SQRT, std::sqrt(a.v)); }
+inline Flop cbrt(const Flop& a) { return fop(OP_CBRT, std::cbrt(a.v)); }
+inline Flop pow(const Flop& a, double p) { return fop(OP_POW, std::pow(a.v, p)); }
+inline Flop fabs(const Flop& a) { return Flop(std::fabs(a.v)); }
+
+// ----------------------------------------------------------------------------------------
 // Complex numbers over T (std::complex is only specified for built-in floating types).
 // ----------------------------------------------------------------------------------------
 template <class T>
@@ -149,6 +187,11 @@ template <> struct Acc<double> {
     s = t;
   }
   double get() const { return s + c; }
+};
+template <> struct Acc<Flop> {
+  Flop s;
+  void add(const Flop& x) { s = s + x; }
+  Flop get() const { return s; }
 };
 template <class T, int N> struct Acc<Dual<T, N>> {
   Acc<T> v; Acc<T> d[N];
@@ -657,6 +700,63 @@ void or_response_ld(const OrConfig* cfg, const double* theta, unsigned mode_mask
     Cx<long double> aet[3];
     response_aet(*cfg, s, mode_mask, f[i], aet);
     for (int c = 0; c < 3; ++c) { out[(c * n + i) * 2] = (double)aet[c].re; out[(c * n + i) * 2 + 1] = (double)aet[c].im; }
+  }
+}
+
+// Algorithmic work of the method, counted on the oracle's own steps with the operation-counting
+// scalar: per active (mode, bin) unit the mode's waveform, t_f, orbit, six links and TDI brackets
+// (tdi_xyz_mode), and per bin with at least one active mode the A/E/T combination and the three
+// channels' likelihood terms (detector_sums' per-bin body); the sample's sky frame once. Inactive
+// (mode, bin) pairs (taper exactly 0) are not counted. data [3][n][2] and psd [3][n] may be NULL
+// (zeros and ones). out: [0] active units, [1] active bins, then OP_N counts per unit, OP_N per
+// bin, OP_N per sample (add/sub, mul, div, sqrt, sin or cos, exp, log, cbrt, pow, comparisons).
+void or_op_count(const OrConfig* cfg, const double* theta, unsigned mode_mask, const double* f, int64_t n,
+                 const double* data, const double* psd, double T_obs, double* out) {
+  Flop th[11];
+  for (int i = 0; i < 11; ++i) th[i] = Flop(theta[i]);
+  Source<Flop> s = source_from(th);
+  unsigned long long unit[OP_N] = {0}, bin[OP_N] = {0}, samp[OP_N] = {0};
+  double n_units = 0.0, n_bins = 0.0;
+  for (int k = 0; k < OP_N; ++k) g_ops[k] = 0;
+  Flop kv[3], ep[3][3], ec[3][3];
+  sky_basis(s, kv, ep, ec);
+  for (int k = 0; k < OP_N; ++k) samp[k] = g_ops[k];
+  for (int64_t i = 0; i < n; ++i) {
+    Cx<Flop> X, Y, Z;
+    bool any = false;
+    for (int md = 0; md < 5; ++md) {
+      if (!(mode_mask & (1u << md))) continue;
+      for (int k = 0; k < OP_N; ++k) g_ops[k] = 0;
+      Cx<Flop> xyz[3];
+      tdi_xyz_mode(*cfg, s, MODE_L[md], MODE_M[md], f[i], kv, ep, ec, xyz);
+      const bool active = val(xyz[0].re) != 0.0 || val(xyz[0].im) != 0.0 || val(xyz[1].re) != 0.0 ||
+                          val(xyz[1].im) != 0.0 || val(xyz[2].re) != 0.0 || val(xyz[2].im) != 0.0;
+      if (!active) continue;
+      any = true;
+      n_units += 1.0;
+      for (int k = 0; k < OP_N; ++k) unit[k] += g_ops[k];
+      X = X + xyz[0]; Y = Y + xyz[1]; Z = Z + xyz[2];
+    }
+    if (!any) continue;
+    for (int k = 0; k < OP_N; ++k) g_ops[k] = 0;
+    const Flop r2(1.0 / std::sqrt(2.0)), r6(1.0 / std::sqrt(6.0)), r3(1.0 / std::sqrt(3.0));
+    Cx<Flop> aet[3] = {(Z - X) * r2, (X - Y * Flop(2.0) + Z) * r6, (X + Y + Z) * r3};
+    Acc<Flop> adh, ahh;
+    for (int c = 0; c < 3; ++c) {
+      const Flop w = Flop(4.0) / (Flop(psd ? psd[c * n + i] : 1.0) * T_obs);
+      Cx<Flop> d(Flop(data ? data[(c * n + i) * 2] : 0.0), Flop(data ? data[(c * n + i) * 2 + 1] : 0.0));
+      adh.add(w * (conj(d) * aet[c]).re);
+      ahh.add(w * norm2(aet[c]));
+    }
+    n_bins += 1.0;
+    for (int k = 0; k < OP_N; ++k) bin[k] += g_ops[k];
+  }
+  out[0] = n_units;
+  out[1] = n_bins;
+  for (int k = 0; k < OP_N; ++k) {
+    out[2 + k] = n_units > 0 ? (double)unit[k] / n_units : 0.0;
+    out[2 + OP_N + k] = n_bins > 0 ? (double)bin[k] / n_bins : 0.0;
+    out[2 + 2 * OP_N + k] = (double)samp[k];
   }
 }
 

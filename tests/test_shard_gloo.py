@@ -1,5 +1,7 @@
 """Host logic of the multi-rank path with world_size 2 on the gloo backend (CPU): contiguous
-shards of independent samples, the gather of per-sample results, and the max-over-ranks timing."""
+shards of independent samples, each rank evaluating the log-likelihood of its own shard (the
+oracle's, on a tiny grid, standing in for one GPU's batched call), the gather of the per-sample
+results, and the max-over-ranks timing."""
 import os
 import socket
 
@@ -29,6 +31,25 @@ def _free_port():
     return p
 
 
+def _problem(n):
+    from oracle import oracle as O
+    from paper_2602_12011_gb300 import workloads as W
+    T = 2.0 ** 12
+    k0, nb = W.grid(T)
+    inj = W.theta_injection(T)
+    f = (k0 + np.arange(nb)) / T
+    od = O.Detector(W.LISA, T, k0, nb, O.make_data(W.LISA, inj, W.MODE_ALL, T, k0, nb, W.normals(nb, 4)),
+                    O.psd(W.LISA, f))
+    return O, od, W.draw_prior(n, 5, T), W.MODE_ALL
+
+
+def _rank_loglike(rank, world, n):
+    """log L of this rank's contiguous shard only."""
+    O, od, theta, mask = _problem(n)
+    lo, hi = shard.shard_bounds(n, rank, world)
+    return O.loglike_batch([od], theta[lo:hi], mask, nthreads=1)[0]
+
+
 def _worker(rank, world, port, n, q):
     import torch
     import torch.distributed as dist
@@ -36,12 +57,8 @@ def _worker(rank, world, port, n, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        from paper_2602_12011_gb300 import workloads as W
-        theta = torch.tensor(W.draw_prior(n, 5, 2.0 ** 20))
-        lo, hi = shard.shard_bounds(n, rank, world)
-        # stand-in per-sample result of this rank's shard (independent of the other rank's)
-        local = theta[lo:hi, 0] * 1e-6 + theta[lo:hi, 10] * 1e-3
-        full = shard.gather_results(local, n, world)
+        ll_local = _rank_loglike(rank, world, n)
+        full = shard.gather_results(torch.tensor(ll_local), n, world)
         t = shard.max_over_ranks(0.5 + rank)
         if rank == 0:
             q.put((full.numpy(), t))
@@ -51,7 +68,6 @@ def _worker(rank, world, port, n, q):
 
 def test_gather_and_max_timing_world2_gloo():
     import torch.multiprocessing as mp
-    from paper_2602_12011_gb300 import workloads as W
     n, world = 101, 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -63,6 +79,6 @@ def test_gather_and_max_timing_world2_gloo():
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    theta = W.draw_prior(n, 5, 2.0 ** 20)
-    np.testing.assert_array_equal(full, theta[:, 0] * 1e-6 + theta[:, 10] * 1e-3)
+    O, od, theta, mask = _problem(n)
+    np.testing.assert_array_equal(full, O.loglike_batch([od], theta, mask, nthreads=1)[0])
     assert t == 1.5
