@@ -38,18 +38,18 @@ MSUN_S = 4.925490947641267e-6
 #   fp64_inst   every FP64-pipe instruction (DFMA, DMUL, DADD, DSETP, F2F, FRND)
 #   fp32_inst   FFMA + FMUL + FADD (the double-word arithmetic of the mixed path)
 UNIT_COUNTS = {
-    "fp64": {"fp64_flops": 402.0, "fp64_inst": 252.3, "fp32_inst": 0.2},
-    "mixed": {"fp64_flops": 54.9, "fp64_inst": 41.5, "fp32_inst": 2256.8},
+    "fp64": {"fp64_flops": 402.0, "fp64_inst": 252.1, "fp32_inst": 0.2},
+    "mixed": {"fp64_flops": 55.9, "fp64_inst": 42.2, "fp32_inst": 2281.3},
     # FP32 path: fp64_inst counts the FRND and F2F of CUDA's FP32 sincospif/sinf and conversions
-    "fp32": {"fp64_flops": 0.25, "fp64_inst": 9.2, "fp32_inst": 354.4},
+    "fp32": {"fp64_flops": 0.47, "fp64_inst": 9.9, "fp32_inst": 354.4},
 }
 # SHA-256 (first 16 hex digits) of the per-bin unit's sources the counts were taken on; the bench
 # marks the counts stale (and warns) when the sources have changed since.
 UNIT_SOURCES = ("pe_device.cuh", "pe_device_mixed.cuh", "pe_device_f32.cuh", "pe_df.cuh", "pe_kernels.cu")
-UNIT_COUNTS_SOURCE_SHA = {"fp64": None, "mixed": None, "fp32": None}
+UNIT_COUNTS_SOURCE_SHA = {"fp64": "88ed2cfdca2eaddf", "mixed": "88ed2cfdca2eaddf", "fp32": "88ed2cfdca2eaddf"}
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum:
 # the per-bin tables, read once per launch
-TRAFFIC = {"fp64": 36.55e6 + 0.01e6, "mixed": 39.84e6 + 0.74e6, "fp32": None}
+TRAFFIC = {"fp64": 36.47e6 + 0.01e6, "mixed": 40.00e6 + 1.01e6, "fp32": None}
 # Algorithmic work of the method (oracle/flop_model.py: the oracle's own operations, counted on
 # 16 samples of this workload): add/sub/mul/div per active (sample, mode, bin) unit and per active
 # (sample, bin) for the A/E/T and likelihood terms, and math-library calls per unit.
