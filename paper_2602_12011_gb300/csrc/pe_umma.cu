@@ -12,7 +12,10 @@
 //                   descriptors; tcgen05.commit frees the stage ("empty" barrier) once its MMAs are
 //                   done, and a last commit signals the accumulator ("accum" barrier);
 //   warps 0-3       epilogue: warp w reads TMEM lanes 32w..32w+31 (tile rows), 16 fp32 columns per
-//                   tcgen05.ld, adds the bias, applies SiLU, stores fp32 C and bf16 H.
+//                   tcgen05.ld, adds the bias (staged in shared memory), applies SiLU, and writes
+//                   fp32 C and bf16 H into the (by then idle) operand stages in the 128-byte swizzled
+//                   layout of TMA; one thread then stores the tile with cp.async.bulk.tensor (rows
+//                   past M are clipped by the tensor map).
 // Every wait on a barrier is bounded (about one second of %globaltimer); on a timeout the kernel
 // records an error code, drains its own TMA copies and MMAs (again bounded), frees its TMEM and
 // returns, and the host reads the code (umma_take_error).
@@ -93,6 +96,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(src))
+               : "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle layout that
 // TMA's SWIZZLE_128B writes: rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte
 // offset), tile base 1024-byte aligned. Fields: start address >> 4 in bits 0-13, leading byte
@@ -143,9 +152,10 @@ __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z));
 // epi 0: C = acc; 1: Z = acc + bias -> C and SiLU(Z) -> Hout (bf16); 2: C = acc + bias
 template <int BN>
 __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                   const __grid_constant__ CUtensorMap tmB, float* __restrict__ C,
-                                                   int M, int N, int K, int epi, const float* __restrict__ bias,
-                                                   __nv_bfloat16* __restrict__ Hout) {
+                                                   const __grid_constant__ CUtensorMap tmB,
+                                                   const __grid_constant__ CUtensorMap tmC,
+                                                   const __grid_constant__ CUtensorMap tmH, int M, int N, int K,
+                                                   int epi, const float* __restrict__ bias) {
   using Lay = Layout<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -158,6 +168,7 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   __shared__ int s_fail;
   __shared__ int s_armed[STAGES];       // TMA copies issued per stage
   __shared__ int s_taken[STAGES];       // ... and consumed by the MMA issuer
+  __shared__ float s_bias[BN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -174,6 +185,7 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  if (threadIdx.x < BN) s_bias[threadIdx.x] = (epi >= 1) ? bias[n0 + threadIdx.x] : 0.f;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                  "r"((uint32_t)BN)
@@ -227,7 +239,7 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   }
   __syncwarp();
 
-  // ---- epilogue: TMEM -> registers -> bias / SiLU -> global
+  // ---- epilogue: TMEM -> registers -> bias / SiLU -> shared (TMA layout) -> TMA store
   const bool ready = mbar_wait(accum, 0);
   if (!ready && lane == 0) {
     atomicCAS(&g_umma_error, 0, 3);
@@ -236,29 +248,43 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const __grid_constant__ CUten
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   if (!s_fail) {
-    const int row = m0 + warp * 32 + lane;
+    // every MMA has completed, so the operand stages are free: C tile as BN/32 boxes of 32 fp32
+    // columns x 128 rows, then H as BN/64 boxes of 64 bf16 columns x 128 rows, 16 KB each, rows of
+    // 128 bytes whose 16-byte chunks sit at chunk ^ (row & 7) (TMA's 128-byte swizzle)
+    uint8_t* sC = base;
+    uint8_t* sH = base + (BN / 32) * 16384;
+    const int r = warp * 32 + lane;           // tile row of this thread = its TMEM lane
+    const int sw = r & 7;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      const int col = n0 + c0;
-      if (row < M && col < N) {
-        if (epi >= 1) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += bias[col + i];
-        }
-        float4* cp = reinterpret_cast<float4*>(C + (size_t)row * N + col);
+      for (int i = 0; i < 16; ++i) v[i] += s_bias[c0 + i];
+      uint8_t* crow = sC + (c0 / 32) * 16384 + r * 128;
+      const int k0 = (c0 % 32) / 4;           // first 16-byte chunk of these 16 columns in the row
 #pragma unroll
-        for (int i = 0; i < 4; ++i) cp[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-        if (epi == 1) {
-          __nv_bfloat162 h[8];
+      for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<float4*>(crow + (((k0 + j) ^ sw) << 4)) =
+            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+      if (epi == 1) {
+        __nv_bfloat162 h[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(silu(v[2 * i]), silu(v[2 * i + 1]));
-          uint4* hp = reinterpret_cast<uint4*>(Hout + (size_t)row * N + col);
-          hp[0] = *reinterpret_cast<uint4*>(&h[0]);
-          hp[1] = *reinterpret_cast<uint4*>(&h[4]);
-        }
+        for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(silu(v[2 * i]), silu(v[2 * i + 1]));
+        uint8_t* hrow = sH + (c0 / 64) * 16384 + r * 128;
+        const int kh = (c0 % 64) / 8;         // 16 bf16 = 2 chunks
+        *reinterpret_cast<uint4*>(hrow + (((kh + 0) ^ sw) << 4)) = *reinterpret_cast<uint4*>(&h[0]);
+        *reinterpret_cast<uint4*>(hrow + (((kh + 1) ^ sw) << 4)) = *reinterpret_cast<uint4*>(&h[4]);
       }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> TMA reads
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int g = 0; g < BN / 32; ++g) tma_store_2d(&tmC, n0 + 32 * g, m0, sC + g * 16384);
+      if (epi == 1)
+        for (int g = 0; g < BN / 64; ++g) tma_store_2d(&tmH, n0 + 64 * g, m0, sH + g * 16384);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // shared memory read out
     }
   } else if (threadIdx.x == 0) {
     // drain: every TMA copy issued but never consumed must land before the CTA's shared memory goes
@@ -289,16 +315,18 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// rows x K bf16, K contiguous; box 64 (K) x box_rows, 128-byte swizzle, zero fill out of range
-static bool make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int K, int box_rows) {
+// rows x cols row-major (cols contiguous), box box_cols x box_rows, 128-byte swizzle (box_cols x
+// element size = 128 bytes), zero fill for loads out of range (stores are clipped there)
+static bool make_map(CUtensorMap* map, const void* ptr, CUtensorMapDataType type, int elem_bytes, int rows, int cols,
+                     int box_cols, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * elem_bytes};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return fn(map, type, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -310,10 +338,18 @@ static cudaError_t set_smem_attr() {
 template <int BN>
 static cudaError_t launch(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, int M, int N, int K, int epi,
                           const float* bias, __nv_bfloat16* Hout, cudaStream_t st) {
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, A, M, K, BM) || !make_map(&mb, Bt, N, K, BN)) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb, mc, mh;
+  const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  if (!make_map(&ma, A, bf, 2, M, K, BK, BM) || !make_map(&mb, Bt, bf, 2, N, K, BK, BN) ||
+      !make_map(&mc, C, f32, 4, M, N, 32, BM))
+    return cudaErrorInvalidValue;
+  if (epi == 1) {
+    if (!make_map(&mh, Hout, bf, 2, M, N, 64, BM)) return cudaErrorInvalidValue;
+  } else {
+    mh = mc;   // not read
+  }
   dim3 grid((unsigned)(N / BN), (unsigned)((M + BM - 1) / BM));
-  k_umma_gemm<BN><<<grid, 128, Layout<BN>::kDyn, st>>>(ma, mb, C, M, N, K, epi, bias, Hout);
+  k_umma_gemm<BN><<<grid, 128, Layout<BN>::kDyn, st>>>(ma, mb, mc, mh, M, N, K, epi, bias);
   return pe::launch_status();
 }
 
@@ -323,7 +359,11 @@ cudaError_t gemm_tn(const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C, i
                     const float* bias, __nv_bfloat16* Hout, cudaStream_t st) {
   // TMA: 16-byte aligned bases and row strides; whole 64-wide K blocks; N a multiple of the tile
   if (M <= 0 || N <= 0 || K <= 0 || K % umma::BK || N % 64) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt)) & 15) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt) | reinterpret_cast<uintptr_t>(C) |
+       reinterpret_cast<uintptr_t>(Hout)) & 15)
+    return cudaErrorInvalidValue;
+  if (epi == 1 && Hout == nullptr) return cudaErrorInvalidValue;
+  if (epi >= 1 && bias == nullptr) return cudaErrorInvalidValue;
   if (N % 128 == 0) return umma::launch<128>(A, Bt, C, M, N, K, epi, bias, Hout, st);
   return umma::launch<64>(A, Bt, C, M, N, K, epi, bias, Hout, st);
 }
