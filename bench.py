@@ -621,18 +621,37 @@ def main():
         srg.set_node_source(1)
         ms_n = timed(lambda: srg.loglike([gd], tts, mask64))
         mm_n = srg.mismatch(gd, torch.tensor(tho, device="cuda"), mask64).cpu().numpy()
+        ms_nx = timed(lambda: srg.loglike([gd], tts, mask64 | L.PE_PREC_MIXED))
         srg.set_node_source(0)
         ms_mx = timed(lambda: L.pe_loglike_batch(hs, tts, Bs, mask64 | L.PE_PREC_MIXED, outs, None, None, stream))
+        # the surrogate path in mixed precision (out-of-box samples on the mixed plain unit, in-box
+        # ones with the spline phase's sincos and the transfer functions on the FP32 pipe), and its
+        # deviation from the FP64 surrogate path on the likelihood's scale
+        ms_sx = timed(lambda: srg.loglike([gd], tts, mask64 | L.PE_PREC_MIXED))
+        ll_s64, _ = srg.loglike([gd], tts, mask64)
+        ll_smx, _ = srg.loglike([gd], tts, mask64 | L.PE_PREC_MIXED)
+        dhs = torch.empty((Bs, 1, 3, 2), dtype=torch.float64, device="cuda")
+        L.pe_loglike_batch(hs, tts, Bs, mask64, outs, dhs, None, stream)
+        torch.cuda.synchronize()
+        scale_s = (0.5 * float(gd.data_norm().sum()) + dhs[:, :, :, 0].sum(dim=(1, 2)).abs()
+                   + 0.5 * dhs[:, :, :, 1].sum(dim=(1, 2)))
+        dev_sx = ((ll_smx - ll_s64).abs() / scale_s).max().item()
         sur = {"value": world * Bs / (ms_s / 1e3), "unit": UNIT, "plain_same_batch": world * Bs / (ms_p / 1e3),
                "gain": ms_p / ms_s, "batch": Bs, "used_fraction": float(used.float().mean().item()),
                "no_network_same_batch": world * Bs / (ms_n / 1e3), "network_over_no_network": ms_n / ms_s,
                "plain_mixed_same_batch": world * Bs / (ms_mx / 1e3), "network_over_plain_mixed": ms_mx / ms_s,
+               "network_mixed_same_batch": world * Bs / (ms_sx / 1e3),
+               "no_network_mixed_same_batch": world * Bs / (ms_nx / 1e3),
+               "network_mixed_over_plain_mixed": ms_mx / ms_sx,
+               "network_mixed_max_rel_dlogl_vs_network_fp64": dev_sx,
                "train_s": t_tr, "train_loss": sl, "heldout_pass_1e-3": float(np.mean(mm[inbox] <= 1e-3)),
                "heldout_max_mismatch_no_network": float(np.max(mm_n[inbox])),
                "heldout_in_box": int(inbox.sum()),
                "note": ("network: MLP node values (3PN/3.5PN phase terms, |H_lm|) + node splines; no_network: "
                         "the same splines from the plain generator's exact node values; plain: per-bin FP64; "
-                        "plain_mixed: per-bin FP64 phase with double-word geometry (1e-10 parity)")}
+                        "plain_mixed: per-bin FP64 phase with double-word geometry (1e-10 parity); *_mixed: "
+                        "the surrogate path with PE_PREC_MIXED (fallbacks on the mixed plain unit, in-box spline "
+                        "sincos and transfer functions in FP32, double-word A/E/T and products)")}
         srg.close()
 
     # ---- heterodyned (relative-binning) likelihood, the second workload: 1024 draws in the posterior's

@@ -231,9 +231,14 @@ pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_ma
  *     [B][5][2][256] (fp32, device) for theta [B][11] (device).
  *   pe_surrogate_loglike_batch: log L per sample through the surrogate path (device pointers);
  *     out_used_dev (nullable) = 1 where the surrogate was used, 0 where the plain path was.
+ *     mode_mask may carry PE_PREC_MIXED: out-of-box samples then take the mixed-precision plain
+ *     path (as pe_loglike_batch with the flag) and in-box samples evaluate the spline phase in
+ *     FP64, its sine and cosine and the transfer functions on the FP32 pipe; A/E/T and the
+ *     weighted per-bin products of both are double words. PE_PREC_FP32 gives PE_EINVAL.
  *   pe_surrogate_mismatch: 1 - <h_s|h_p>/sqrt(<h_s|h_s><h_p|h_p>) between the surrogate and the
  *     plain A/E/T signals on one detector (noise-weighted inner product, Eq. eq_inner_product;
  *     App. A's mismatch without the maximisation over t_c and phi_c); 0 for fallback samples.
+ *     FP64 only: a precision flag in mode_mask gives PE_EINVAL.
  *   pe_surrogate_mlp_debug / pe_surrogate_get_weights: forward + backward of the network on given
  *     inputs and output cotangents, and its weights, for gradient checks.
  *   pe_surrogate_mlp_trace: pe_surrogate_mlp_debug that also copies every intermediate of the pass

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "pe_device.cuh"
+#include "pe_device_mixed.cuh"
 #include "pe_kernels.h"
 #include "pe_mlp.h"
 #include "pe_surrogate.h"
@@ -371,6 +372,46 @@ __device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, dou
   }
 }
 
+// mode_bin_sur with the sincos on the FP32 pipe: the FP64 spline phase is reduced exactly to a
+// fraction of a turn r in [-1/2, 1/2] (FP64), r goes to a float by truncation on the integer pipe
+// (relative error < 2^-23; GB300 runs F2F on its FP64 pipe) and sin, cos of 2 pi r come from CUDA's
+// sincospif, ~1 ulp of 1 -- the accuracy of the FP32 transfer functions it multiplies. The
+// amplitude is formed in FP32: ampf = a_lm hsc (per tile), fm76 = f^(-7/6) (the high word of its
+// double-word table), and the taper weight (FP64 as in mode_bin_sur, only where f > ftap).
+// u0 = ln f - ln kFmin; frc = frac(f t_c) (FP64, per bin).
+__device__ __forceinline__ void mode_bin_sur_mix(const ModeCoef& C, float ampf, double f, float fm76, double u0,
+                                                 double frc, const double* cf, const float* cft, double h, double ih,
+                                                 float2 acc[3]) {
+  const double uj = u0 * ih;
+  int j = (int)floor(uj);
+  j = j < 0 ? 0 : (j > kNodes - 2 ? kNodes - 2 : j);
+  const double t = (uj - j) * h;
+  const double* c0 = cf + (size_t)j * 4;
+  const double ph = fma(fma(fma(c0[3], t, c0[2]), t, c0[1]), t, c0[0]) - frc;
+  const float rr = trunc_to_float(__double_as_longlong(ph - rint(ph)));
+  const float tf = trunc_to_float(__double_as_longlong(t));
+  float val[kQ - 1];
+#pragma unroll
+  for (int k = 0; k < kQ - 1; ++k) {
+    const float4 c = *reinterpret_cast<const float4*>(cft + ((size_t)k * (kNodes - 1) + j) * 4);
+    val[k] = fmaf(fmaf(fmaf(c.w, tf, c.z), tf, c.y), tf, c.x);
+  }
+  float amp = ampf * fm76;
+  if (f > C.ftap) {
+    const double span = C.fend - C.ftap;
+    const double zt = span / (C.fend - f) - span / (f - C.ftap);
+    amp = (zt > 700.0) ? 0.f : amp * trunc_to_float(__double_as_longlong(1.0 / (1.0 + exp(zt))));
+  }
+  float sph, cph;
+  sincospif(2.0f * rr, &sph, &cph);
+  const float hr = amp * cph, hi = amp * sph;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c].x = fmaf(hr, val[2 * c], fmaf(-hi, val[2 * c + 1], acc[c].x));
+    acc[c].y = fmaf(hr, val[2 * c + 1], fmaf(hi, val[2 * c], acc[c].y));
+  }
+}
+
 __device__ __forceinline__ int find_pair_s(const long long* off, int P, long long t) {
   int lo = 0, hi = P;
   while (hi - lo > 1) {
@@ -384,6 +425,11 @@ __device__ __forceinline__ int find_pair_s(const long long* off, int P, long lon
 // one bin per thread, the same order of the sums). mode 0: surrogate path (in-box
 // samples) or plain path (others), partials [tile][6] as the plain kernel. mode 1: mismatch sums
 // of the surrogate against the plain signal, partials [tile][6] = (<s|p>, <s|s>, <p|p>, 0, 0, 0).
+// MIX (mode 0 only): the mixed-precision variant. Out-of-box samples take the mixed plain unit
+// (bin_xyz_mixed, as k_loglike_fwd with PE_PREC_MIXED); in-box samples take mode_bin_sur_mix; both
+// then form A/E/T and the weighted products in double words and sum each tile in double words
+// (k_loglike_fwd's mixed tail), scaled back to FP64 per tile.
+template <bool MIX>
 __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                        const SampleCoef* __restrict__ coefN,
                                                        const double* __restrict__ theta, SurBox bx,
@@ -391,11 +437,18 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
                                                        const double* __restrict__ hs,
                                                        const int* __restrict__ nend, const long long* __restrict__ off,
                                                        double* part, int mode) {
-  __shared__ double red[6][kTileBins + kRedPad];
+  __shared__ double red[6][kTileBins + kRedPad];   // block_sum6 staging (float2 rows when MIX)
   __shared__ double pc[kProj];
+  __shared__ float2 pcw[kProj];                    // the projection forms as double words (MIX)
   __shared__ double ihs[kNModes];
-  __shared__ double2 stab[kSinTab];
-  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  __shared__ float ampf[kNModes];                  // a_lm hsc in FP32 (MIX)
+  __shared__ double2 stab[kSinTab];                // as float4 double words when MIX
+  if (MIX) {
+    float4* t4 = reinterpret_cast<float4*>(stab);
+    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) t4[i] = ds.d[0].sctw[i];
+  } else {
+    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  }
   __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
@@ -407,50 +460,97 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
     proj_prologue(D, S, pc);
-    if (threadIdx.x < kNModes) ihs[threadIdx.x] = 1.0 / hs[(size_t)s * kNModes + threadIdx.x];
+    if (threadIdx.x < kNModes) {
+      ihs[threadIdx.x] = 1.0 / hs[(size_t)s * kNModes + threadIdx.x];
+      if (MIX) ampf[threadIdx.x] = (float)(coefN[s].md[threadIdx.x].amp * S.hsc);
+    }
+    if (MIX && threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
     __syncthreads();
     const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll 1
-    for (int b = b0; b < b0 + kTileBins && b < ne; b += kTileBins) {
-      BinIn Bn;
-      load_bin(D, b, S.tc, Bn);
-      float2 xs[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-      XYZAcc xpa;
-      xyz_zero(xpa);
-      const double u = 3.0 * Bn.lnf3;
-      if (sur) {
-#pragma unroll 1
-        for (int md = 0; md < kNModes; ++md) {
-          const ModeCoef& C = S.md[md];
-          if (!C.active || !(Bn.f < C.fend)) continue;
-          const size_t sys = ((size_t)I * B + s) * kNModes + md;
-          mode_bin_sur(C, coefN[s].md[md].amp, S.hsc, Bn, u, spl + sys * kQ * (kNodes - 1) * 4,
-                       splt + sys * (kQ - 1) * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], ihs[md], xs, stab);
-        }
-      }
-      if (!sur || mode == 1) bin_modes(D, S, Bn, xpa, stab, pc);   // the plain path, as k_loglike_fwd
-      double2 xp[3], xsd[3];
-      xyz_final(xpa, Bn.z, xp);
+    if constexpr (MIX) {
+      df v[6];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) xsd[c] = make_double2((double)xs[c].x * S.ihsc, (double)xs[c].y * S.ihsc);
-      double2 os[3], op[3];
-      aet_from_xyz(sur ? xsd : xp, os);
-      if (mode == 0) {
-        accum_bin(D, b, os, v);
-      } else {
-        aet_from_xyz(xp, op);
+      for (int i = 0; i < 6; ++i) v[i] = df_make(0.f, 0.f);
+      const int b = b0;
+      if (b < ne) {
+        cdf x[3], o[3];
+        if (sur) {
+          const double f = D.f[b];
+          const double u0 = 3.0 * D.lnf3[b] - kLnFmin;
+          const float fm76 = D.fm76w[b].x;
+          const double pr = f * S.tc;                       // frac(f t_c) as load_bin
+          const double frc = (pr - rint(pr)) + fma(f, S.tc, -pr);
+          float2 xs[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll 1
+          for (int md = 0; md < kNModes; ++md) {
+            const ModeCoef& C = S.md[md];
+            if (!C.active || !(f < C.fend)) continue;
+            const size_t sys = ((size_t)I * B + s) * kNModes + md;
+            mode_bin_sur_mix(C, ampf[md], f, fm76, u0, frc, spl + sys * kQ * (kNodes - 1) * 4,
+                             splt + sys * (kQ - 1) * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], ihs[md], xs);
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) x[c] = cdf{df_make(xs[c].x, 0.f), df_make(xs[c].y, 0.f)};
+        } else {
+          bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab), pcw);
+        }
+        aet_from_xyz_dw(x, o);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double w = D.gg[c * D.nb + b];
-          v[0] += w * (os[c].x * op[c].x + os[c].y * op[c].y);
-          v[1] += w * (os[c].x * os[c].x + os[c].y * os[c].y);
-          v[2] += w * (op[c].x * op[c].x + op[c].y * op[c].y);
+          const float4 g = D.dgw[c * D.nb + b];
+          v[c] = df_sub_s(df_mul(df_make(g.x, g.y), o[c].re), df_mul(df_make(g.z, g.w), o[c].im));
+          const df m2 = df_add_s(df_mul(o[c].re, o[c].re), df_mul(o[c].im, o[c].im));
+          v[3 + c] = df_mul(D.ggw[c * D.nb + b], m2);
         }
       }
+      const double ih = S.ihsc;
+      const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
+      df r;
+      if (block_sum6(v, [](df a, df b) { return dfl_add(a, b); }, reinterpret_cast<float2(*)[kTileBins + kRedPad]>(red), &r))
+        part[t * 6 + threadIdx.x] = df_to(r) * (threadIdx.x < 3 ? sd : sg);
+    } else {
+      double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 1
+      for (int b = b0; b < b0 + kTileBins && b < ne; b += kTileBins) {
+        BinIn Bn;
+        load_bin(D, b, S.tc, Bn);
+        float2 xs[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        XYZAcc xpa;
+        xyz_zero(xpa);
+        const double u = 3.0 * Bn.lnf3;
+        if (sur) {
+#pragma unroll 1
+          for (int md = 0; md < kNModes; ++md) {
+            const ModeCoef& C = S.md[md];
+            if (!C.active || !(Bn.f < C.fend)) continue;
+            const size_t sys = ((size_t)I * B + s) * kNModes + md;
+            mode_bin_sur(C, coefN[s].md[md].amp, S.hsc, Bn, u, spl + sys * kQ * (kNodes - 1) * 4,
+                         splt + sys * (kQ - 1) * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], ihs[md], xs, stab);
+          }
+        }
+        if (!sur || mode == 1) bin_modes(D, S, Bn, xpa, stab, pc);   // the plain path, as k_loglike_fwd
+        double2 xp[3], xsd[3];
+        xyz_final(xpa, Bn.z, xp);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xsd[c] = make_double2((double)xs[c].x * S.ihsc, (double)xs[c].y * S.ihsc);
+        double2 os[3], op[3];
+        aet_from_xyz(sur ? xsd : xp, os);
+        if (mode == 0) {
+          accum_bin(D, b, os, v);
+        } else {
+          aet_from_xyz(xp, op);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double w = D.gg[c * D.nb + b];
+            v[0] += w * (os[c].x * op[c].x + os[c].y * op[c].y);
+            v[1] += w * (os[c].x * os[c].x + os[c].y * os[c].y);
+            v[2] += w * (op[c].x * op[c].x + op[c].y * op[c].y);
+          }
+        }
+      }
+      double a;
+      if (block_sum6(v, [](double x, double y) { return x + y; }, red, &a)) part[t * 6 + threadIdx.x] = a;
     }
-    double a;
-    if (block_sum6(v, [](double x, double y) { return x + y; }, red, &a)) part[t * 6 + threadIdx.x] = a;
   }
 }
 
@@ -908,7 +1008,11 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   pe_status s0 = pe::detset_from_handles(dets, ndet, &ds);
   if (s0 != PE_OK) return s0;
   if (B < 1 || B > (1 << 20) || !theta_dev || !out0) return sfail(PE_EINVAL, "surrogate: bad arguments");
-  if (mode_mask == 0 || (mode_mask & ~PE_MODE_ALL)) return sfail(PE_EINVAL, "surrogate: bad mode mask");
+  const bool mix = (mode_mask & PE_PREC_MIXED) != 0;
+  if ((mode_mask & PE_MODE_ALL) == 0 || (mode_mask & ~(PE_MODE_ALL | PE_PREC_MIXED)))
+    return sfail(PE_EINVAL, "surrogate: bad mode mask");
+  if (mix && mode != 0) return sfail(PE_EINVAL, "surrogate: the mismatch study is FP64 only");
+  mode_mask &= PE_MODE_ALL;
   const int P = ndet * B;
   long long max_tiles = 0;
   for (int i = 0; i < ndet; ++i) max_tiles += (long long)B * pe::tiles_of(ds.d[i].nb, pe::kTileBins);
@@ -974,8 +1078,12 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long g = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * 8));
-    pe::k_sur_fwd<<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
-                                                          part, mode);
+    if (mix)
+      pe::k_sur_fwd<true><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend,
+                                                                 off, part, mode);
+    else
+      pe::k_sur_fwd<false><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend,
+                                                                  off, part, mode);
     e = pe::launch_status();
   }
   if (e == cudaSuccess) {

@@ -142,10 +142,13 @@ def _mlp_layers_check(Lb, s, B):
             assert np.linalg.norm(a - b) / np.linalg.norm(b) < 5e-3
 
 
-def test_node_spline_path_matches_oracle(oracle_mod, Lb):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_node_spline_path_matches_oracle(oracle_mod, Lb, prec):
     """With the plain generator's own node values (no network), the node-spline log-likelihood
-    agrees with the oracle to the spline's accuracy."""
+    agrees with the oracle to the spline's accuracy, in FP64 and in mixed precision (where the
+    spline phase's sine and cosine are FP32, ~1 ulp of 1, as the FP32 transfer functions)."""
     import torch
+    flag = Lb.PE_PREC_MIXED if prec == "mixed" else 0
     T = 2.0 ** 20
     k0, nb = W.grid(T)
     inj = np.array([2e6, 3.0, 0.5, 0.3, 25.8, 0.4, 1.3, 1.375, -1.2108, 2.659, 0.8 * T])
@@ -156,13 +159,14 @@ def test_node_spline_path_matches_oracle(oracle_mod, Lb):
     th = np.vstack([inj, W.draw_prior(6, 31, T)])
     th[1:, 0] = np.linspace(5e5, 9e6, 6)
     th[1:, 1] = np.minimum(th[1:, 1], 8.0)
-    ll, used = s.loglike([gd], torch.tensor(th, device="cuda"), W.MODE_ALL)
+    ll, used = s.loglike([gd], torch.tensor(th, device="cuda"), W.MODE_ALL | flag)
     ll = ll.cpu().numpy()
     assert np.all(used.cpu().numpy() == 1)
     ref, dhhh = oracle_mod.loglike_batch([od], th, W.MODE_ALL)
     dd = od_dd = oracle_mod.loglike([od], inj, 0)["dd"].sum()
     for i in range(th.shape[0]):
         scale = 0.5 * dd + abs(dhhh[i, :, :, 0].sum()) + 0.5 * dhhh[i, :, :, 1].sum()
+        H.record_margin("surrogate:node_spline_%s" % prec, abs(ll[i] - ref[i]) / (1e-6 * scale))
         assert abs(ll[i] - ref[i]) <= 1e-6 * scale, (i, ll[i], ref[i])
     s.close()
 
@@ -180,17 +184,33 @@ def test_heldout_mismatch_acceptance(Lb, lisa22, trained):
     assert frac >= 0.99, (frac, np.quantile(mm[inbox], [0.5, 0.99]))
 
 
-def test_fallback_is_the_plain_path_bitwise(Lb, lisa22, trained):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fallback_is_the_plain_path_bitwise(Lb, lisa22, trained, prec):
+    """Out-of-box samples give the plain path's log L bit for bit, in each precision (the same
+    unit, the same per-tile partials and the same fixed-order reduction)."""
     import torch
+    flag = Lb.PE_PREC_MIXED if prec == "mixed" else 0
     th = W.draw_prior(64, 2607, T22)
     th[::2, 1] = 9.5                                   # outside the box (q > 8)
     th[1::4, 0] = 2e5                                  # outside the box (light)
     tt = torch.tensor(th, device="cuda")
-    ll, used = trained.loglike([lisa22], tt, W.MODE_ALL)
-    ref = Lb.loglike([lisa22], th, W.MODE_ALL)["logl"]
+    ll, used = trained.loglike([lisa22], tt, W.MODE_ALL | flag)
+    ref = Lb.loglike([lisa22], th, W.MODE_ALL | flag)["logl"]
     out = (th[:, 1] > 8.0) | (th[:, 0] < 3e5)
     assert np.array_equal(used.cpu().numpy(), (~out).astype(np.int32))
     assert np.array_equal(ll.cpu().numpy()[out], ref[out])
+
+
+def test_precision_flags_that_the_surrogate_rejects(Lb, lisa22, trained):
+    """The mismatch study is FP64 only, and the all-FP32 option is not a surrogate path."""
+    import torch
+    tt = torch.tensor(W.draw_prior(4, 2610, T22), device="cuda")
+    for call in (lambda: trained.mismatch(lisa22, tt, W.MODE_ALL | Lb.PE_PREC_MIXED),
+                 lambda: trained.loglike([lisa22], tt, W.MODE_ALL | Lb.PE_PREC_FP32),
+                 lambda: trained.loglike([lisa22], tt, Lb.PE_PREC_MIXED)):
+        with pytest.raises(Lb.PeError) as e:
+            call()
+        assert e.value.status == Lb.PE_EINVAL
 
 
 def test_network_against_the_paths_without_it(Lb, lisa22, trained):
@@ -199,11 +219,13 @@ def test_network_against_the_paths_without_it(Lb, lisa22, trained):
       network     MLP node values (3PN/3.5PN phase terms, |H_lm|) -> node splines -> response;
       no network  the same node splines from the plain generator's exact node values;
       plain FP64  the per-bin path (1e-10 parity);
-      plain mixed the per-bin path with double-word geometry (1e-10 parity).
+      plain mixed the per-bin path with double-word geometry (1e-10 parity);
+      network mixed / no network mixed: the spline path with PE_PREC_MIXED.
     The spline path beats the plain FP64 path (> 1.3x) with or without the network. The network
     buys nothing over exact node values here: TaylorF2 is analytic, so the exact node values cost
     about what the MLP inference does, and they are exact (mismatch from the splines alone). The
-    mixed per-bin path is faster than both at full parity (the ratios are recorded)."""
+    mixed spline path stays within 1e-6 of the likelihood's scale of the FP64 spline path and is
+    faster than it; its ratio to the plain mixed path is recorded."""
     import torch
     th = W.draw_prior(1024, 2608, T22)
     th[:, 1] = np.minimum(th[:, 1], 8.0)
@@ -235,13 +257,33 @@ def test_network_against_the_paths_without_it(Lb, lisa22, trained):
         mm_exact = trained.mismatch(lisa22, tt, W.MODE_ALL).cpu().numpy()
     finally:
         trained.set_node_source(0)
-    print("plain %.2f ms, mixed %.2f ms, network %.2f ms, no network %.2f ms" % (t_plain, t_mixed, t_net, t_exact))
+    mx = W.MODE_ALL | Lb.PE_PREC_MIXED
+    t_net_mx = med(lambda: trained.loglike([lisa22], tt, mx))
+    trained.set_node_source(1)
+    try:
+        t_exact_mx = med(lambda: trained.loglike([lisa22], tt, mx))
+    finally:
+        trained.set_node_source(0)
+    ll64 = trained.loglike([lisa22], tt, W.MODE_ALL)[0].cpu().numpy()
+    llmx = trained.loglike([lisa22], tt, mx)[0].cpu().numpy()
+    dh = Lb.loglike([lisa22], tt, W.MODE_ALL, dhhh=True)["dhhh"].cpu().numpy()
+    scale = 0.5 * lisa22.data_norm().sum() + np.abs(dh[..., 0].sum(axis=(1, 2))) + 0.5 * dh[..., 1].sum(axis=(1, 2))
+    dev = np.max(np.abs(llmx - ll64) / scale)
+    print("plain %.2f ms, mixed %.2f ms, network %.2f ms, no network %.2f ms, network mixed %.2f ms, "
+          "no network mixed %.2f ms, mixed vs fp64 spline path %.2e of the scale"
+          % (t_plain, t_mixed, t_net, t_exact, t_net_mx, t_exact_mx, dev))
     H.record_margin("surrogate:network_over_no_network_speed", t_exact / t_net)
     H.record_margin("surrogate:network_over_plain_fp64_speed", t_plain / t_net)
     H.record_margin("surrogate:network_over_plain_mixed_speed", t_mixed / t_net)
+    H.record_margin("surrogate:network_mixed_over_plain_mixed_speed", t_mixed / t_net_mx)
+    H.record_margin("surrogate:network_mixed_over_network_fp64_speed", t_net / t_net_mx)
+    H.record_margin("surrogate:no_network_mixed_over_plain_mixed_speed", t_mixed / t_exact_mx)
+    H.record_margin("surrogate:mixed_vs_fp64_spline_dev_over_1e-6", dev / 1e-6)
     assert np.mean(mm_net <= 1e-3) >= 0.99
     assert np.max(mm_exact) <= 1e-5
     assert t_plain / t_net > 1.3 and t_plain / t_exact > 1.3
+    assert dev <= 1e-6
+    assert t_net_mx < t_net
 
 
 def test_checkpoint_roundtrip_and_corruption(Lb, trained, tmp_path):
