@@ -45,13 +45,15 @@ extern "C" {
 #define PE_MODE_ALL 0x1Fu
 /* Precision flag, OR-ed into the mode_mask of the forward entry points (pe_loglike_batch,
  * pe_loglike_batch_noalloc, pe_plan_create, pe_autotune, pe_signal_aet). Without it every step
- * runs in FP64. With it the TaylorF2 phase, t_f, the reduction of the phase and orbital angles
- * to a fraction of a turn and every sum stay FP64, while the response geometry (orbit offsets,
- * link vectors, projections, sincs, third-spacecraft phases, TDI brackets) runs on the FP32 pipe
- * in double-word arithmetic (~48-bit significands, ~1e-14 relative). It agrees with the FP64 path
- * to far below the 1e-10 parity bar but not bit for bit; each precision is bitwise
- * batch-invariant by itself. The gradient, Fisher and surrogate entry points are FP64 only and
- * reject the flag. */
+ * runs in FP64. With it the TaylorF2 phase, its reduction to a fraction of a turn and every sum
+ * across tiles stay FP64, while t_f, the orbit angles and the response geometry (orbit offsets,
+ * link vectors, projections, sincs, third-spacecraft phases, TDI brackets) run on the FP32 pipe
+ * in double-word arithmetic (~48-bit significands, ~1e-14 relative; t_f and the orbit angles in
+ * FP64 where t_f lies more than 2^23 s, heliocentric, or 2^21 s, geocentric, from the origin).
+ * It agrees with the FP64 path to far below the 1e-10 parity bar but not bit for bit; each
+ * precision is bitwise batch-invariant by itself. pe_loglike_grad_batch, pe_hetero_create and
+ * pe_surrogate_loglike_batch also take the flag (see there); pe_fisher and
+ * pe_surrogate_mismatch are FP64 only and reject it. */
 #define PE_PREC_MIXED 0x100u
 /* Precision flag for the precision study, OR-ed into the same mode masks (not with PE_PREC_MIXED):
  * every step in FP32, including the TaylorF2 phase, t_f and frac(f t_c) -- the paper's float32

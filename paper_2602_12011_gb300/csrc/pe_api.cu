@@ -218,6 +218,13 @@ void fill_dev(pe_detector_s* d) {
     }
   }
   D.Rw = host_dw(D.R);
+  D.ratew = host_dw(D.rate_t);
+  D.alpha0w = host_dw(D.alpha0_t);
+  D.geo_ratew = host_dw(D.geo_rate_t);
+  // double-word t_f carries ~6e-14 relative error (a dozen rounded operations); below 2^23 s the
+  // heliocentric angle (1 turn a year) and below 2^21 s the geocentric one (1 turn in ~4 days) stay
+  // within ~1e-13 turn of their FP64 values; beyond, the unit forms them in FP64
+  D.tfw_max = (c.orbit == PE_ORBIT_HELIO) ? 8388608.0f : 2097152.0f;
   D.f = d->f; D.f13 = d->f13; D.fm13 = d->fm13; D.lnf3 = d->lnf3; D.fm76 = d->fm76;
   D.fm56 = d->fpow; D.fm12 = d->fpow + d->nb; D.fm53 = d->fpow + 2 * (size_t)d->nb;
   D.sca = d->sca; D.z = d->z; D.dg = d->dg; D.gg = d->gg; D.dd = d->dd_dev; D.sct = d->sct;

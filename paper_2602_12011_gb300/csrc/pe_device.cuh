@@ -143,6 +143,9 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   const T v[3] = {-(sb * cl), -(sb * sl), cb};
   for (int i = 0; i < 3; ++i) { S.p[i] = cp * u[i] + sp * v[i]; S.q[i] = -(sp * u[i]) + cp * v[i]; }
   for (int i = 0; i < 3; ++i) S.kw[i] = to_dw(val(S.k[i]));
+  for (int k = 0; k < 8; ++k) S.Pdw[k] = to_dw(val(S.Pd[k]));
+  S.Q6w = to_dw(val(S.Q6));
+  S.tcw = to_dw(val(S.tc));
   // modes: (2 pi M / m)^(1/3) = (2 pi M)^(1/3) m^(-1/3) and its log from one cube root and one
   // log per sample; the spin-weighted harmonics share the sines and cosines of iota and iota/2
   const T Fisco = 1.0 / (k6Pow15 * 2.0 * pi * M);
@@ -183,6 +186,7 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
     C.ftap = 0.9 * double(m) * Fisco;
     C.Ppw = to_dw(val(C.Pp));
     C.Pcw = to_dw(val(C.Pc));
+    C.tffacw = to_dw(val(C.tffac));
     C.p = p;
     C.active = (valid && (mask & (1u << md)) && val(hmag) != 0.0) ? 1 : 0;
   }
@@ -356,6 +360,10 @@ __device__ __forceinline__ void xyz_final(const XYZAcc& a, double2 z, double2 x[
 }
 
 // Per-bin inputs shared by all modes of one bin.
+// a < b for non-negative doubles by the order of their bit patterns: an integer compare, exact
+// (GB300 runs the double compare DSETP on its narrow FP64 pipe)
+__device__ __forceinline__ bool dlt_pos(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+
 struct BinIn {
   double f, f13, fm13, lnf3, fm76, invf;
   double a, sa, ca;    // a = pi f L

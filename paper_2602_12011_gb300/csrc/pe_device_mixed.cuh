@@ -1,9 +1,10 @@
 // pe_device_mixed.cuh -- the (sample, mode, bin) unit of mode_bin (pe_device.cuh) with the
 // response geometry on the FP32 pipe in double-word arithmetic (pe_df.cuh, ~1e-14 relative).
 // GB300 issues FP32 at 64x its FP64 rate, so the FP64 pipe keeps only what needs FP64's range
-// and 53-bit precision: the TaylorF2 phase (up to ~1e6 rad) and t_f, the exact reduction of the
-// phase and the orbital angle to a fraction of a turn, and the likelihood accumulation across tiles.
-// Everything else -- the sines and cosines of the orbit, phase, third-spacecraft and sinc
+// and 53-bit precision: the TaylorF2 phase (up to ~1e6 rad), its exact reduction to a fraction of
+// a turn, t_f where it lies far (more than 2^23 s, heliocentric, or 2^21 s, geocentric) from the
+// origin, and the likelihood accumulation across tiles. Everything else -- t_f and the orbit
+// angles, the sines and cosines of the orbit, phase, third-spacecraft and sinc
 // arguments, the projections k.n, n.e+.n, n.ex.n of the link vectors (per-tile linear forms in the
 // orbit basis, converted to double words once per tile), the
 // sincs, the mode tensor factors, the TDI brackets, the A/E/T combinations and the PSD-weighted
@@ -35,9 +36,9 @@ __device__ __forceinline__ void mix_final(const MixAcc& a, const cdf& z, cdf x[3
   }
 }
 
-// Per-bin double words: f, a = pi f L, a / (2 pi), sin a, cos a, f^(1/3), f^(-7/6).
+// Per-bin double words: f, a = pi f L, a / (2 pi), sin a, cos a, f^(1/3), f^(-7/6), 1/f.
 struct BinW {
-  df f, a, at, sa, ca, f13, fm76;
+  df f, a, at, sa, ca, f13, fm76, invf;
 };
 __device__ __forceinline__ void load_bin_w(const DetDev& D, int b, BinW& W) {
   W.f = D.fw[b];
@@ -47,6 +48,7 @@ __device__ __forceinline__ void load_bin_w(const DetDev& D, int b, BinW& W) {
   W.at = D.atw[b];
   W.sa = D.saw[b];
   W.ca = D.caw[b];
+  W.invf = df_rcp(W.f);
 }
 
 // sinc(u) for |u| < 1e-3: 1 + u^2 (-1/6 + u^2/120) (the u^2/120 term enters the low word of -1/6;
@@ -86,29 +88,47 @@ __device__ __forceinline__ df frac_dw(double x) { return df_from_bits(x - rint(x
 __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
                                                const BinW& W, MixAcc& acc, const float4* __restrict__ tab,
                                                const float2* __restrict__ pcw, const ModeCoef* C2 = nullptr) {
-  // --- waveform and time-frequency map (FP64; rows A2, A3)
+  // --- waveform (row A2): the phase in FP64
   const double v = C.cm * B.f13;
   const double lnv = C.lncm + B.lnf3;
   const double iv5 = C.icm5 * D.fm53[B.b];   // v^-5 = cm^-5 f^(-5/3)
   double poly = S.P[7];
-  double dpol = S.Pd[7];
 #pragma unroll
-  for (int k = 6; k >= 0; --k) {
-    poly = fma(poly, v, S.P[k]);
-    dpol = fma(dpol, v, S.Pd[k]);
-  }
+  for (int k = 6; k >= 0; --k) poly = fma(poly, v, S.P[k]);
   const double q56 = fma(S.Q6, v, S.Q5);
   const double psi_pn = fma(iv5, poly, lnv * q56);
-  const double dv = fma(iv5, dpol, fma(S.Q6 * v, lnv, q56));
-  const double tf = fma(C.tffac * B.invf, dv, S.tc);
+  // time-frequency map (row A3): t_f = t_c + (m / 12 pi) f^-1 v dPsi/dv with
+  // v dPsi/dv = v^-5 sum_k Pd_k v^k + Q6 v ln v + q56, in double words. t_f only places the orbit,
+  // so what matters is the error of the orbit angles alpha = alpha0 + t_f / yr (turns) and, for a
+  // geocentric orbit, t_f / P_geo: while |t_f| < D.tfw_max they stay within ~1e-13 turn of their
+  // FP64 values; beyond (the lowest frequencies of light systems) t_f and the angles are formed
+  // in FP64 and reduced exactly there.
+  const df vw = dfl_mul(C.cmw, W.f13);
+  df dpol = S.Pdw[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) dpol = dfl_add(dfl_mul(dpol, vw), S.Pdw[k]);
+  const df dv = dfl_add(dfl_mul(df_from_bits(iv5), dpol),
+                        dfl_add(dfl_mul(dfl_mul(S.Q6w, vw), df_from_bits(lnv)), df_from_bits(q56)));
+  const df tf = dfl_add(S.tcw, dfl_mul(dfl_mul(C.tffacw, W.invf), dv));
+  df alpha, geo;   // orbit angles in turns (df_cis_turns reduces them exactly)
+  if (fabsf(tf.x) < D.tfw_max) {
+    alpha = dfl_add(dfl_mul(tf, D.ratew), D.alpha0w);
+    geo = dfl_mul(tf, D.geo_ratew);
+  } else {
+    double dpol64 = S.Pd[7];
+#pragma unroll 1
+    for (int k = 6; k >= 0; --k) dpol64 = fma(dpol64, v, S.Pd[k]);
+    const double tf64 = fma(C.tffac * B.invf, fma(iv5, dpol64, fma(S.Q6 * v, lnv, q56)), S.tc);
+    alpha = frac_dw(fma(tf64, D.rate_t, D.alpha0_t));
+    geo = frac_dw(tf64 * D.geo_rate_t);
+  }
   // amplitude (times hsc) in double words: ampw f^(-7/6) v^p, times the taper where it is below 1
   df A = dfl_mul(C.ampw, W.fm76);
   if (C.p >= 1) {
-    const df vw = dfl_mul(C.cmw, W.f13);
     A = dfl_mul(A, vw);
     if (C.p >= 2) A = dfl_mul(A, vw);
   }
-  if (B.f > C.ftap) {
+  if (dlt_pos(C.ftap, B.f)) {
     const double span = C.fend - C.ftap;
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
     A = dfl_mul(A, df_from_bits((zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt))));
@@ -117,14 +137,14 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
   // Pp + kappa Pp2, Pc + kappa Pc2, kappa = k32 v^2
   cdf Ap = {dfl_mul(A, C.Ppw), df_make(0.f, 0.f)}, Ac = {dfl_mul(A, C.Pcw), df_make(0.f, 0.f)};
   if (C2) {
-    const df vw = dfl_mul(C.cmw, W.f13);
     const df v2 = dfl_mul(vw, vw);
     const df kr = dfl_mul(S.k32w[0], v2), ki = dfl_mul(S.k32w[1], v2);
     Ap = cdf{dfl_mul(A, dfl_add(C.Ppw, dfl_mul(kr, C2->Ppw))), dfl_mul(A, dfl_mul(ki, C2->Ppw))};
     Ac = cdf{dfl_mul(A, dfl_add(C.Pcw, dfl_mul(kr, C2->Pcw))), dfl_mul(A, dfl_mul(ki, C2->Pcw))};
   }
-  // --- orbital angle alpha(t_f) (row A4), centre Doppler f k.x_c, x_c = R (cos a, sin a, 0)
-  const cdf eo = df_cis_turns(frac_dw(fma(tf, D.rate_t, D.alpha0_t)), tab);
+  // --- orbital angle alpha(t_f) (row A4), centre Doppler f k.x_c, x_c = R (cos a, sin a, 0);
+  // df_cis_turns reduces the angle in turns exactly
+  const cdf eo = df_cis_turns(alpha, tab);
   const df co = eo.re, so = eo.im;
   const df kxc = dfl_mul(D.Rw, dfl_add(dfl_mul(S.kw[0], co), dfl_mul(S.kw[1], so)));
   // mode phase: the FP64 part reduced to a fraction of a turn, minus f k.x_c in double words
@@ -137,7 +157,7 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     ob[2] = co;
     ob[3] = so;
   } else {
-    const cdf e0 = df_cis_turns(frac_dw(tf * D.geo_rate_t), tab);
+    const cdf e0 = df_cis_turns(geo, tab);
     ob[0] = e0.re;
     ob[1] = e0.im;
     ob[2] = ob[3] = df_make(0.f, 0.f);
@@ -183,7 +203,7 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
     // sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     const df akn = dfl_mul(W.a, kn);
     const df u1 = dfl_sub(W.a, akn), u2 = dfl_add(W.a, akn);
-    if (B.a < kSincPolyA) {
+    if (dlt_pos(B.a, kSincPolyA)) {
       smv[l] = df_sinc_poly(u1);
       spv[l] = df_sinc_poly(u2);
     } else {
@@ -227,7 +247,7 @@ __device__ __forceinline__ void bin_xyz_mixed(const DetDev& D, const SampleCoef&
   for (int md = 0; md < kNModes; ++md) {
     if (md == 3 && S.pair32) continue;
     const ModeCoef& C = S.md[md];
-    if (!C.active || !(B.f < C.fend)) continue;
+    if (!C.active || !dlt_pos(B.f, C.fend)) continue;
     mode_bin_mixed(D, S, C, B, W, a, tab, pcw, (md == 0 && S.pair32) ? &S.md[3] : nullptr);
   }
   const float4 zz = D.zw[b];

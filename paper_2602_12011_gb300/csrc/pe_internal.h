@@ -53,6 +53,7 @@ struct ModeCoefT {
   float2 Ppw, Pcw;   // Pp, Pc as double words (FP32 pairs) for the mixed-precision path
   float2 cmw;        // cm as a double word
   float2 ampw;       // amp times the sample's hsc as a double word
+  float2 tffacw;     // tffac as a double word
   int p;        // power of v in |H_lm|: 0 (22), 1 (21, 33), 2 (32, 44)
   int active;   // 1 if the mode is in the mask and its amplitude is non-zero
 };
@@ -68,6 +69,8 @@ struct SampleCoefT {
   T Q5, Q6;
   T k[3], p[3], q[3];   // propagation direction and polarisation frame
   float2 kw[3];         // k as double words
+  float2 Pdw[8];        // Pd, Q6 and tc as double words (the mixed path's t_f)
+  float2 Q6w, tcw;
   double hsc, ihsc;     // power of two near 1/amp of the (2,2) mode and its inverse: the mixed-
                         // precision path carries amplitudes times hsc, keeping them far from the
                         // FP32 range limits
@@ -168,6 +171,8 @@ struct DetDev {
   // (cos phi_0, sin phi_0, 0, 0) (geocentric, constant term 0)
   double Mo[3][3][5];
   float2 Rw;            // R as a double word
+  float2 ratew, alpha0w, geo_ratew;   // rate_t, alpha0_t, geo_rate_t as double words
+  float tfw_max;        // |t_f| below which the mixed unit forms t_f and the orbit angles in double words
   // Q = TDI factor(z) (-i a) e^{-i a}; n_A = 1/sqrt2, n_E = 1/sqrt6, n_T = 1/sqrt3
 };
 
