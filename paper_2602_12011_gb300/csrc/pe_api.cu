@@ -218,6 +218,9 @@ void fill_dev(pe_detector_s* d) {
     }
   }
   D.Rw = host_dw(D.R);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int m = 0; m < 5; ++m) D.Mof[i][j][m] = static_cast<float>(D.Mo[i][j][m]);
   D.ratew = host_dw(D.rate_t);
   D.alpha0w = host_dw(D.alpha0_t);
   D.geo_ratew = host_dw(D.geo_rate_t);

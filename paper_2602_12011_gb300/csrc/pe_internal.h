@@ -170,6 +170,7 @@ struct DetDev {
   // orbit basis b = (cos 2alpha, sin 2alpha, cos alpha, sin alpha) (heliocentric) or
   // (cos phi_0, sin phi_0, 0, 0) (geocentric, constant term 0)
   double Mo[3][3][5];
+  float Mof[3][3][5];   // the same in FP32 (the mixed surrogate's node geometry)
   float2 Rw;            // R as a double word
   float2 ratew, alpha0w, geo_ratew;   // rate_t, alpha0_t, geo_rate_t as double words
   float tfw_max;        // |t_f| below which the mixed unit forms t_f and the orbit angles in double words

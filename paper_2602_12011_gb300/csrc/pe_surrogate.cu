@@ -196,10 +196,83 @@ __device__ __forceinline__ bool in_box(const double* t, const SurBox& bx) {
   return t[0] >= bx.mlo && t[0] <= bx.mhi && t[1] <= bx.qmax && fabs(t[2]) <= bx.chimax && fabs(t[3]) <= bx.chimax;
 }
 
+// FP32 link transfer functions of one node (the mixed path): T_X, T_Y, T_Z per unit mode amplitude,
+// the same algebra as below with every quantity a float. The transfer functions are O(1) sums of
+// O(1) link terms (the TDI factor, which vanishes at low frequency, is in the data tables), so
+// FP32 leaves them ~1e-7 relative -- what their FP32 spline coefficients keep anyway.
+// c, s: cos, sin of the orbit angle (heliocentric basis) or of the geocentric phase.
+__device__ __forceinline__ void node_links_f32(const DetDev& D, const SampleCoef& Sa, const ModeCoef& C, float ff,
+                                               float c, float s, float2 T[3]) {
+  float b[4];
+  if (D.orbit == 0) {
+    b[0] = c * c - s * s;
+    b[1] = 2.f * s * c;
+    b[2] = c;
+    b[3] = s;
+  } else {
+    b[0] = c;
+    b[1] = s;
+    b[2] = b[3] = 0.f;
+  }
+  float dl[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      dl[i][j] = fmaf(D.Mof[i][j][0], b[0], fmaf(D.Mof[i][j][1], b[1], fmaf(D.Mof[i][j][2], b[2],
+                      fmaf(D.Mof[i][j][3], b[3], D.Mof[i][j][4]))));
+  const float k[3] = {Sa.kw[0].x, Sa.kw[1].x, Sa.kw[2].x};
+  float p[3], qv[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    p[i] = trunc_to_float(__double_as_longlong(Sa.p[i]));
+    qv[i] = trunc_to_float(__double_as_longlong(Sa.q[i]));
+  }
+  const float Pp = C.Ppw.x, Pc = C.Pcw.x;
+  float sa, ca;
+  sincospif(ff * D.Lf, &sa, &ca);   // a = pi f L
+  const float2 z = make_float2(ca * ca - sa * sa, -2.f * sa * ca);   // e^{-2 i a}
+  const float a = 3.14159265f * ff * D.Lf;
+  float2 G[3], U[3], V[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const int rr = l, ss = (l + 1) % 3, tt = (l + 2) % 3;
+    float n0 = dl[rr][0] - dl[ss][0], n1 = dl[rr][1] - dl[ss][1], n2 = dl[rr][2] - dl[ss][2];
+    const float inv = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+    n0 *= inv; n1 *= inv; n2 *= inv;
+    const float kn = k[0] * n0 + k[1] * n1 + k[2] * n2;
+    const float np = p[0] * n0 + p[1] * n1 + p[2] * n2;
+    const float nq = qv[0] * n0 + qv[1] * n1 + qv[2] * n2;
+    const float gr = Pp * (np * np - nq * nq), gi = Pc * 2.f * np * nq;
+    const float kd = k[0] * dl[tt][0] + k[1] * dl[tt][1] + k[2] * dl[tt][2];
+    float se, ce;
+    sincospif(ff * kd, &se, &ce);   // pi f k.delta_t
+    G[l] = make_float2(ce * gr - se * gi, ce * gi + se * gr);
+    const float u1 = a * (1.f - kn), u2 = a * (1.f + kn);
+    const float sm = fabsf(u1) < 1e-3f ? fmaf(-u1 * u1, 1.f / 6.f, 1.f) : sinf(u1) / u1;
+    const float sp = fabsf(u2) < 1e-3f ? fmaf(-u2 * u2, 1.f / 6.f, 1.f) : sinf(u2) / u2;
+    U[l] = make_float2(fmaf(z.x, sp, sm), z.y * sp);
+    V[l] = make_float2(fmaf(z.x, sm, sp), z.y * sm);
+  }
+  auto cm = [](float2 x, float2 y) { return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
+  auto cs = [](float2 x, float2 y) { return make_float2(x.x - y.x, x.y - y.y); };
+  T[0] = cs(cm(G[2], V[2]), cm(G[0], U[0]));
+  T[1] = cs(cm(G[0], V[0]), cm(G[1], U[1]));
+  T[2] = cs(cm(G[1], V[1]), cm(G[2], U[2]));
+}
+
 // Per (detector I, sample s, mode md, node j): the 7 spline quantities.
-// Y: de-standardised MLP outputs [Bpad][kNout]; nodes out: [I][s][md][q][j].
+// Y: de-standardised MLP outputs [Bpad][kNout]; hs, nv: the mode's node spacing h and (v, ln v) at
+// the first node (k_node_h); nodes out: [I][s][md][q][j]. Node j sits at f_j = kFmin e^{j h}, so
+// v_j = v_0 e^{j h/3} and ln v_j = ln v_0 + j h/3 (one exponential per node); the sines and cosines
+// go through the library's table sincos in turns, sin(a -+ a k.n) is formed from sin a, cos a and
+// one sincos of a k.n, and the pair of sincs shares one reciprocal.
+// MIX: the phase, t_f, the orbit angle and the centre Doppler term stay FP64 as above; the link
+// transfer functions are FP32 (node_links_f32), and quantities 1..6 are written as floats into the
+// first half of their rows (k_spline's mixed path reads them so).
+template <bool MIX>
 __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleCoef* S0, const float* Y,
-                            const double* theta, SurBox bx, double* nodes) {
+                            const double* theta, SurBox bx, const double* hs, const double2* nv, double* nodes) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)ds.ndet * B * kNModes * kNodes;
   if (i >= total) return;
@@ -216,33 +289,53 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
   }
   const DetDev& D = ds.d[I];
   const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
-  const double M = theta[(size_t)s * PE_NPARAM] * kMsunS;
-  const double h = node_h(M, mm);
-  const double f = kFmin * exp(j * h);
-  const double v = cbrt(2.0 * kPi * M * f / mm);
-  const double lnv = log(v);
+  const double h = hs[(size_t)s * kNModes + md];
+  const double2 v0 = nv[(size_t)s * kNModes + md];
+  const double jh3 = j * h * (1.0 / 3.0);
+  const double e3 = exp(jh3);
+  const double f = kFmin * (e3 * e3 * e3);
+  const double invf = 1.0 / f;
+  const double v = v0.x * e3;
+  const double lnv = v0.y + jh3;
   double D0;
   const double psi0 = psi_of(S0[s], v, lnv, &D0);
-  const float* y = Y + (size_t)s * kNout;
-  const double r = y[(md * 2 + 0) * kNodes + j];
-  const double amp_ratio = y[(md * 2 + 1) * kNodes + j];
+  const float* y = Y + (size_t)s * kNout + (md * 2) * kNodes;
+  const double r = y[j];
+  const double amp_ratio = y[kNodes + j];
   // residual derivative in u = ln f by node differences (one-sided at the ends)
   double drdu;
-  if (j == 0) drdu = (-3.0 * r + 4.0 * y[(md * 2) * kNodes + 1] - y[(md * 2) * kNodes + 2]) / (2.0 * h);
-  else if (j == kNodes - 1)
-    drdu = (3.0 * r - 4.0 * y[(md * 2) * kNodes + kNodes - 2] + y[(md * 2) * kNodes + kNodes - 3]) / (2.0 * h);
-  else drdu = (y[(md * 2) * kNodes + j + 1] - y[(md * 2) * kNodes + j - 1]) / (2.0 * h);
-  const double tf = Sa.tc + C.tffac / f * D0 + drdu / (2.0 * kPi * f);
+  if (j == 0) drdu = -3.0 * r + 4.0 * y[1] - y[2];
+  else if (j == kNodes - 1) drdu = 3.0 * r - 4.0 * y[kNodes - 2] + y[kNodes - 3];
+  else drdu = y[j + 1] - y[j - 1];
+  drdu *= 0.5 / h;
+  const double tf = fma(invf, fma(C.tffac, D0, drdu * (0.5 / kPi)), Sa.tc);
+  if constexpr (MIX) {
+    double so, co;
+    sincos_turns(fma(tf, D.rate_t, D.alpha0_t), D.sct, &so, &co);
+    const double kxc = D.R * (Sa.k[0] * co + Sa.k[1] * so);
+    q[0] = C.ph0 - (0.5 * mm * psi0 + r) * (0.5 / kPi) - f * kxc;
+    if (D.orbit != 0) sincos_turns(tf * D.geo_rate_t, D.sct, &so, &co);
+    float2 T[3];
+    node_links_f32(D, Sa, C, trunc_to_float(__double_as_longlong(f)), trunc_to_float(__double_as_longlong(co)),
+                   trunc_to_float(__double_as_longlong(so)), T);
+    const float ar = y[kNodes + j];
+    double* row0 = q - j;   // this system's row of quantity 0
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      reinterpret_cast<float*>(row0 + (1 + 2 * c) * kNodes)[j] = T[c].x * ar;
+      reinterpret_cast<float*>(row0 + (2 + 2 * c) * kNodes)[j] = T[c].y * ar;
+    }
+    return;
+  }
   double xc[3], dl[3][3];
   orbit_offsets(D, tf, xc, dl, D.sct);
   const double kxc = Sa.k[0] * xc[0] + Sa.k[1] * xc[1] + Sa.k[2] * xc[2];
-  const double phi = C.ph0 - (0.5 * mm * psi0 + r) / (2.0 * kPi) - f * kxc;
-  // link transfer functions per unit mode amplitude at the node frequency
+  const double phi = C.ph0 - (0.5 * mm * psi0 + r) * (0.5 / kPi) - f * kxc;
+  // link transfer functions per unit mode amplitude at the node frequency; a = pi f L
+  const double at = 0.5 * f * D.L;   // a in turns
   double sa, ca;
-  sincospi(f * D.L, &sa, &ca);
-  double s2, c2;
-  sincospi(2.0 * f * D.L, &s2, &c2);
-  const double2 z = make_double2(c2, -s2);
+  sincos_turns(at, D.sct, &sa, &ca);
+  const double2 z = make_double2(ca * ca - sa * sa, -2.0 * sa * ca);   // e^{-2 i a}
   const double a = kPi * f * D.L;
   double2 G[3], U[3], V[3];
   for (int l = 0; l < 3; ++l) {
@@ -256,11 +349,22 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
     const double2 gam = make_double2(C.Pp * (np * np - nq * nq), C.Pc * 2.0 * np * nq);
     const double kd = Sa.k[0] * dl[tt][0] + Sa.k[1] * dl[tt][1] + Sa.k[2] * dl[tt][2];
     double se, ce;
-    sincospi(f * kd, &se, &ce);
+    sincos_turns(0.5 * f * kd, D.sct, &se, &ce);   // pi f k.delta_t
     G[l] = cmul(make_double2(ce, se), gam);
     const double u1 = a * (1.0 - kn), u2 = a * (1.0 + kn);
-    const double sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : sin(u1) / u1;
-    const double spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : sin(u2) / u2;
+    double sk, ck;
+    sincos_turns(at * kn, D.sct, &sk, &ck);        // a k.n
+    const double s1 = fma(sa, ck, -(ca * sk)), s2 = fma(sa, ck, ca * sk);
+    const bool small1 = fabs(u1) < 1e-3, small2 = fabs(u2) < 1e-3;
+    double sm, spl;
+    if (!small1 && !small2) {
+      const double ru = 1.0 / (u1 * u2);
+      sm = s1 * u2 * ru;
+      spl = s2 * u1 * ru;
+    } else {
+      sm = small1 ? sinc_small(u1) : s1 / u1;
+      spl = small2 ? sinc_small(u2) : s2 / u2;
+    }
     U[l] = make_double2(fma(z.x, spl, sm), z.y * spl);
     V[l] = make_double2(fma(z.x, sm, spl), z.y * sm);
   }
@@ -277,61 +381,200 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
 }
 
 // Not-a-knot cubic spline on the uniform nodes u_j = u_0 + j h of one quantity; writes, per
-// interval j, (a, b, c, d) of y(u_j + t) = a + b t + c t^2 + d t^3 in place over coef[j][4].
+// interval j, (a, b, c, d) of y(u_j + t) = a + b t + c t^2 + d t^3 over coef[j][4].
 // With uniform spacing the not-a-knot conditions give M_1 = r_1/6, M_{N-2} = r_{N-2}/6
-// (r_j = 6 (y_{j+1} - 2 y_j + y_{j-1})/h^2); the interior (1, 4, 1) system is solved by Thomas.
+// (r_j = 6 (y_{j+1} - 2 y_j + y_{j-1})/h^2); the interior (1, 4, 1) system j = 2 .. N-3 is solved
+// by the Thomas algorithm, whose pivots c'_j = 1/(4 - c'_{j-1}), c'_2 = 1/4, are the same for every
+// system (a compile-time table). Both sweeps are first-order affine recurrences,
+// d'_j = c'_j (r_j - d'_{j-1}) and M_j = d'_j - c'_j M_{j+1}, so one warp solves a system: each lane
+// composes the maps of 8 consecutive rows, a shuffle scan composes the lanes' maps, and each lane
+// then runs its rows from its prefix (|c'_j| <= 1/4 + ..., ~0.27, so the composed maps only shrink).
 // coef_t: FP32 copies of quantities 1..6 (the transfer functions), [system][6][kNodes - 1][4].
-__global__ void k_spline(const double* nodes, long long nsys, const double* hs, double* coef, float* coef_t) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nsys) return;
-  const double* y = nodes + i * kNodes;
-  double* cf = coef + i * (kNodes - 1) * 4;
+struct ThomasPivots {
+  double c[kNodes];
+};
+constexpr ThomasPivots thomas_pivots() {
+  ThomasPivots t{};
+  double prev = 0.0;
+  for (int j = 2; j <= kNodes - 3; ++j) {
+    t.c[j] = 1.0 / (4.0 - prev);
+    prev = t.c[j];
+  }
+  return t;
+}
+__constant__ ThomasPivots kThomas = thomas_pivots();
+
+constexpr int kSplineWarps = 4;   // systems per CTA, one warp each
+constexpr int kSplineNP = kNodes + kNodes / 8;   // padded length of the shared arrays
+// shared arrays are indexed through pad(j) = j + j/8: in the sweeps lane L reads rows 8L + k, and
+// the padding spreads the 32 lanes' rows over distinct banks
+__device__ __forceinline__ int spad(int j) { return j + (j >> 3); }
+
+// The second derivatives M_j of one system, by one warp, in arithmetic R (double, or float for the
+// FP32 transfer-function splines of the mixed path): yy the node values and piv the pivots
+// (padded, shared), M the result (padded, shared).
+template <class R>
+__device__ __forceinline__ void spline_solve_warp(const R* yy, const R* piv, R* M, R ih2, int lane) {
+  constexpr int N = kNodes, lo = 2, hi = N - 3, RW = 8;   // RW rows per lane: 32 x 8 >= hi - lo + 1
+  const R M1 = ih2 * (yy[spad(2)] - R(2) * yy[spad(1)] + yy[spad(0)]) / R(6);
+  const R MN2 = ih2 * (yy[spad(N - 1)] - R(2) * yy[spad(N - 2)] + yy[spad(N - 3)]) / R(6);
+  // forward sweep: this lane's rows j0 .. j0 + RW - 1 (rows beyond hi are identity maps)
+  const int j0 = lo + RW * lane;
+  R rr[RW];
+  R A = R(1), Bc = R(0);   // composed map d -> A d + Bc of this lane's rows
+#pragma unroll
+  for (int k = 0; k < RW; ++k) {
+    const int j = j0 + k;
+    if (j <= hi) {
+      R r = ih2 * (yy[spad(j + 1)] - R(2) * yy[spad(j)] + yy[spad(j - 1)]);
+      if (j == lo) r -= M1;
+      if (j == hi) r -= MN2;
+      rr[k] = r;
+      const R c = piv[spad(j)];
+      A = -c * A;
+      Bc = c * (r - Bc);
+    }
+  }
+  // inclusive scan of the maps over the lanes (lane L after lanes < L), then the input of this
+  // lane's first row is the composition of the lanes before it applied to d'_{lo-1} = 0
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const R Ap = __shfl_up_sync(0xffffffffu, A, off), Bp = __shfl_up_sync(0xffffffffu, Bc, off);
+    if (lane >= off) {
+      Bc = fma(A, Bp, Bc);
+      A = A * Ap;
+    }
+  }
+  R d = __shfl_up_sync(0xffffffffu, Bc, 1);
+  if (lane == 0) d = R(0);
+  R dd[RW];
+#pragma unroll
+  for (int k = 0; k < RW; ++k) {
+    const int j = j0 + k;
+    if (j <= hi) d = (rr[k] - d) * piv[spad(j)];
+    dd[k] = d;
+  }
+  // back substitution M_j = d'_j - c'_j M_{j+1} from M_{hi+1} = 0: this lane's rows top down,
+  // composed over the lanes above it
+  A = R(1);
+  Bc = R(0);
+#pragma unroll
+  for (int k = RW - 1; k >= 0; --k) {
+    const int j = j0 + k;
+    if (j <= hi) {
+      const R c = piv[spad(j)];
+      Bc = fma(-c, Bc, dd[k]);
+      A = -c * A;
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const R Ap = __shfl_down_sync(0xffffffffu, A, off), Bp = __shfl_down_sync(0xffffffffu, Bc, off);
+    if (lane + off < 32) {
+      Bc = fma(A, Bp, Bc);
+      A = A * Ap;
+    }
+  }
+  R m = __shfl_down_sync(0xffffffffu, Bc, 1);
+  if (lane == 31) m = R(0);
+#pragma unroll
+  for (int k = RW - 1; k >= 0; --k) {
+    const int j = j0 + k;
+    if (j <= hi) {
+      m = fma(-piv[spad(j)], m, dd[k]);
+      M[spad(j)] = m;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    M[spad(1)] = M1;
+    M[spad(N - 2)] = MN2;
+    M[spad(0)] = R(2) * M1 - M[spad(2)];
+    M[spad(N - 1)] = R(2) * MN2 - M[spad(N - 3)];
+  }
+  __syncwarp();
+}
+
+// mixed: the phase (quantity 0) is written as double words, (c0, c1) and (c2, c3) as two float4 per
+// interval in the same 32 bytes (the mixed-precision unit's form), and the transfer functions
+// (quantities 1..6, used only through their FP32 copies) are solved in FP32 and written to coef_t
+// alone.
+__global__ void __launch_bounds__(32 * kSplineWarps) k_spline(const double* nodes, long long nsys, const double* hs,
+                                                               double* coef, float* coef_t, int mixed) {
+  constexpr int N = kNodes;
+  __shared__ double ys[kSplineWarps][kSplineNP], Ms[kSplineWarps][kSplineNP];
+  __shared__ double piv[kSplineNP];   // the pivots in shared memory: the lanes read different rows at once
+  __shared__ float pivf[kSplineNP];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    piv[spad(j)] = kThomas.c[j];
+    pivf[spad(j)] = (float)kThomas.c[j];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long i = (long long)blockIdx.x * kSplineWarps + w;
+  if (i >= nsys) return;                                  // whole warps leave together
+  const double* y = nodes + i * N;
+  double* cf = coef + i * (N - 1) * 4;
   const int q = (int)(i % kQ);
-  float* ct = q > 0 ? coef_t + ((i / kQ) * (kQ - 1) + (q - 1)) * (kNodes - 1) * 4 : nullptr;
+  float* ct = q > 0 ? coef_t + ((i / kQ) * (kQ - 1) + (q - 1)) * (N - 1) * 4 : nullptr;
   const double h = hs[i / kQ];
   if (!(h > 0.0)) {
-    for (int j = 0; j < kNodes - 1; ++j) cf[4 * j] = cf[4 * j + 1] = cf[4 * j + 2] = cf[4 * j + 3] = 0.0;
-    if (ct)
-      for (int j = 0; j < 4 * (kNodes - 1); ++j) ct[j] = 0.f;
+    for (int j = lane; j < 4 * (N - 1); j += 32) {
+      if (!(mixed && q > 0)) cf[j] = 0.0;
+      if (ct) ct[j] = 0.f;
+    }
     return;
   }
-  constexpr int N = kNodes;
-  double Mv[N];
-  double cp[N];
-  const double ih2 = 6.0 / (h * h);
-  Mv[1] = ih2 * (y[2] - 2.0 * y[1] + y[0]) / 6.0;
-  Mv[N - 2] = ih2 * (y[N - 1] - 2.0 * y[N - 2] + y[N - 3]) / 6.0;
-  // interior rows j = 2 .. N-3: M_{j-1} + 4 M_j + M_{j+1} = r_j, with M_1, M_{N-2} known
-  const int lo = 2, hi = N - 3;
-  double dprev = 0.0;
-  for (int j = lo; j <= hi; ++j) {
-    double rj = ih2 * (y[j + 1] - 2.0 * y[j] + y[j - 1]);
-    if (j == lo) rj -= Mv[1];
-    if (j == hi) rj -= Mv[N - 2];
-    const double denom = 4.0 - (j == lo ? 0.0 : cp[j - 1]);
-    cp[j] = 1.0 / denom;
-    dprev = (rj - (j == lo ? 0.0 : dprev)) / denom;
-    Mv[j] = dprev;  // holds d'_j for now
+  if (mixed && q > 0) {
+    float* yy = reinterpret_cast<float*>(ys[w]);
+    float* M = reinterpret_cast<float*>(Ms[w]);
+    const float* yf = reinterpret_cast<const float*>(y);   // k_sur_nodes<true> wrote floats
+    for (int j = lane; j < N; j += 32) yy[spad(j)] = yf[j];
+    __syncwarp();
+    const float hf = (float)h;
+    spline_solve_warp<float>(yy, pivf, M, 6.f / (hf * hf), lane);
+    const float ih = 1.f / hf, h6 = hf * (1.f / 6.f), ih6 = ih * (1.f / 6.f);
+    for (int j = lane; j < N - 1; j += 32) {
+      const float y0 = yy[spad(j)], y1 = yy[spad(j + 1)], m0 = M[spad(j)], m1 = M[spad(j + 1)];
+      *reinterpret_cast<float4*>(ct + 4 * j) =
+          make_float4(y0, (y1 - y0) * ih - h6 * (2.f * m0 + m1), 0.5f * m0, (m1 - m0) * ih6);
+    }
+    return;
   }
-  for (int j = hi - 1; j >= lo; --j) Mv[j] -= cp[j] * Mv[j + 1];
-  Mv[0] = 2.0 * Mv[1] - Mv[2];
-  Mv[N - 1] = 2.0 * Mv[N - 2] - Mv[N - 3];
-  for (int j = 0; j < N - 1; ++j) {
-    cf[4 * j + 0] = y[j];
-    cf[4 * j + 1] = (y[j + 1] - y[j]) / h - h * (2.0 * Mv[j] + Mv[j + 1]) / 6.0;
-    cf[4 * j + 2] = 0.5 * Mv[j];
-    cf[4 * j + 3] = (Mv[j + 1] - Mv[j]) / (6.0 * h);
-    if (ct)
-      for (int k = 0; k < 4; ++k) ct[4 * j + k] = (float)cf[4 * j + k];
+  double* yy = ys[w];
+  double* M = Ms[w];
+  for (int j = lane; j < N; j += 32) yy[spad(j)] = y[j];
+  __syncwarp();
+  spline_solve_warp<double>(yy, piv, M, 6.0 / (h * h), lane);
+  const double ih = 1.0 / h, h6 = h * (1.0 / 6.0), ih6 = ih * (1.0 / 6.0);
+  for (int j = lane; j < N - 1; j += 32) {
+    const double y0 = yy[spad(j)], y1 = yy[spad(j + 1)], m0 = M[spad(j)], m1 = M[spad(j + 1)];
+    const double c0 = y0;
+    const double c1 = (y1 - y0) * ih - h6 * (2.0 * m0 + m1);
+    const double c2 = 0.5 * m0;
+    const double c3 = (m1 - m0) * ih6;
+    if (q == 0 && mixed) {
+      const float2 w0 = to_dw(c0), w1 = to_dw(c1), w2 = to_dw(c2), w3 = to_dw(c3);
+      float4* cw = reinterpret_cast<float4*>(cf + 4 * j);
+      cw[0] = make_float4(w0.x, w0.y, w1.x, w1.y);
+      cw[1] = make_float4(w2.x, w2.y, w3.x, w3.y);
+    } else {
+      *reinterpret_cast<double4*>(cf + 4 * j) = make_double4(c0, c1, c2, c3);
+    }
+    if (ct) *reinterpret_cast<float4*>(ct + 4 * j) = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
   }
 }
 
-__global__ void k_node_h(const double* theta, int B, double* hs) {
+// Per (sample, mode): the node spacing h in ln f and (v, ln v) at the first node f = kFmin.
+__global__ void k_node_h(const double* theta, int B, double* hs, double2* nv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * kNModes) return;
   const int s = i / kNModes, md = i % kNModes;
   const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
-  hs[i] = node_h(theta[(size_t)s * PE_NPARAM] * kMsunS, mm);
+  const double M = theta[(size_t)s * PE_NPARAM] * kMsunS;
+  hs[i] = node_h(M, mm);
+  const double v = cbrt(2.0 * kPi * M * kFmin / mm);
+  nv[i] = make_double2(v, log(v));
 }
 
 // Spline evaluation of one mode at one bin: adds hsc H T_X, hsc H T_Y, hsc H T_Z to acc. The phase
@@ -372,24 +615,31 @@ __device__ __forceinline__ void mode_bin_sur(const ModeCoef& C, double ampN, dou
   }
 }
 
-// mode_bin_sur with the sincos on the FP32 pipe: the FP64 spline phase is reduced exactly to a
-// fraction of a turn r in [-1/2, 1/2] (FP64), r goes to a float by truncation on the integer pipe
-// (relative error < 2^-23; GB300 runs F2F on its FP64 pipe) and sin, cos of 2 pi r come from CUDA's
-// sincospif, ~1 ulp of 1 -- the accuracy of the FP32 transfer functions it multiplies. The
-// amplitude is formed in FP32: ampf = a_lm hsc (per tile), fm76 = f^(-7/6) (the high word of its
-// double-word table), and the taper weight (FP64 as in mode_bin_sur, only where f > ftap).
-// u0 = ln f - ln kFmin; frc = frac(f t_c) (FP64, per bin).
-__device__ __forceinline__ void mode_bin_sur_mix(const ModeCoef& C, float ampf, double f, float fm76, double u0,
-                                                 double frc, const double* cf, const float* cft, double h, double ih,
+// mode_bin_sur on the FP32 pipe. The phase spline (up to ~1e5 turns) is evaluated in double words
+// from its double-word coefficients (k_spline with phase_dw), at t = u0 - j h in double words
+// (relative error ~1e-14, ~1e-9 turn at the largest phases), minus frac(f t_c); the result is
+// reduced exactly to a fraction of a turn in [-1/2, 1/2] (hi - rint(hi), exact in FP32, plus lo),
+// and sin, cos of 2 pi r come from CUDA's sincospif, ~1 ulp of 1 -- the accuracy of the FP32
+// transfer functions they multiply. The segment j is located in FP32: a bin within rounding of a
+// node may take the neighbouring segment, whose cubic agrees there to the spline's C2 continuity.
+// The amplitude is FP32: ampf = a_lm hsc (per tile), fm76 = f^(-7/6) (the high word of its
+// double-word table), and the taper weight 1/(1 + e^z) where f > ftap, with the distances to the
+// taper's ends taken in FP64 (exact) and z, e^z in FP32 (relative error ~1e-6 of the weight).
+// u0w = ln f - ln kFmin and frcw = frac(f t_c) as double words (per bin); hw, ihf: the mode's node
+// spacing as a double word and 1/h in FP32 (per tile).
+__device__ __forceinline__ void mode_bin_sur_mix(const ModeCoef& C, float ampf, double f, float fm76, df u0w,
+                                                 df frcw, const double* cf, const float* cft, df hw, float ihf,
                                                  float2 acc[3]) {
-  const double uj = u0 * ih;
-  int j = (int)floor(uj);
+  int j = (int)floorf(u0w.x * ihf);
   j = j < 0 ? 0 : (j > kNodes - 2 ? kNodes - 2 : j);
-  const double t = (uj - j) * h;
-  const double* c0 = cf + (size_t)j * 4;
-  const double ph = fma(fma(fma(c0[3], t, c0[2]), t, c0[1]), t, c0[0]) - frc;
-  const float rr = trunc_to_float(__double_as_longlong(ph - rint(ph)));
-  const float tf = trunc_to_float(__double_as_longlong(t));
+  const df t = dfl_sub(u0w, dfl_mulf(hw, (float)j));
+  const float4* cw = reinterpret_cast<const float4*>(cf) + 2 * j;
+  const float4 c01 = cw[0], c23 = cw[1];
+  df ph = dfl_add(df_make(c23.x, c23.y), dfl_mul(df_make(c23.z, c23.w), t));
+  ph = dfl_add(df_make(c01.z, c01.w), dfl_mul(ph, t));
+  ph = dfl_sub(dfl_add(df_make(c01.x, c01.y), dfl_mul(ph, t)), frcw);
+  const float rr = __fadd_rn(__fsub_rn(ph.x, rintf(ph.x)), ph.y);
+  const float tf = t.x;
   float val[kQ - 1];
 #pragma unroll
   for (int k = 0; k < kQ - 1; ++k) {
@@ -397,10 +647,11 @@ __device__ __forceinline__ void mode_bin_sur_mix(const ModeCoef& C, float ampf, 
     val[k] = fmaf(fmaf(fmaf(c.w, tf, c.z), tf, c.y), tf, c.x);
   }
   float amp = ampf * fm76;
-  if (f > C.ftap) {
-    const double span = C.fend - C.ftap;
-    const double zt = span / (C.fend - f) - span / (f - C.ftap);
-    amp = (zt > 700.0) ? 0.f : amp * trunc_to_float(__double_as_longlong(1.0 / (1.0 + exp(zt))));
+  if (dlt_pos(C.ftap, f)) {
+    const float span = trunc_to_float(__double_as_longlong(C.fend - C.ftap));
+    const float zt = __fdividef(span, trunc_to_float(__double_as_longlong(C.fend - f))) -
+                     __fdividef(span, trunc_to_float(__double_as_longlong(f - C.ftap)));
+    amp = (zt > 80.f) ? 0.f : amp / (1.f + __expf(zt));
   }
   float sph, cph;
   sincospif(2.0f * rr, &sph, &cph);
@@ -422,51 +673,67 @@ __device__ __forceinline__ int find_pair_s(const long long* off, int P, long lon
 }
 
 // Persistent kernel over the same tile list as the FP64 k_loglike_fwd (kTileBins bins per tile,
-// one bin per thread, the same order of the sums). mode 0: surrogate path (in-box
-// samples) or plain path (others), partials [tile][6] as the plain kernel. mode 1: mismatch sums
+// one bin per thread, the same order of the sums). KIND 0 (FP64), mode 0: surrogate path (in-box
+// samples) or plain path (others), partials [tile][6] as the plain kernel; mode 1: mismatch sums
 // of the surrogate against the plain signal, partials [tile][6] = (<s|p>, <s|s>, <p|p>, 0, 0, 0).
-// MIX (mode 0 only): the mixed-precision variant. Out-of-box samples take the mixed plain unit
-// (bin_xyz_mixed, as k_loglike_fwd with PE_PREC_MIXED); in-box samples take mode_bin_sur_mix; both
-// then form A/E/T and the weighted products in double words and sum each tile in double words
-// (k_loglike_fwd's mixed tail), scaled back to FP64 per tile.
-template <bool MIX>
+// KIND 1 and 2, the mixed-precision variant (mode 0), split over two launches that each take their
+// own tiles: KIND 1 the in-box samples' tiles (mode_bin_sur_mix, a light unit with few registers
+// and no tables in shared memory), KIND 2 the out-of-box samples' tiles (the mixed plain unit
+// bin_xyz_mixed, as k_loglike_fwd with PE_PREC_MIXED). Both form A/E/T and the weighted products
+// in double words and sum each tile in double words (k_loglike_fwd's mixed tail), scaled back to
+// FP64 per tile, so a tile's partial does not depend on the split.
+template <int KIND>
 __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                        const SampleCoef* __restrict__ coefN,
                                                        const double* __restrict__ theta, SurBox bx,
                                                        const double* __restrict__ spl, const float* __restrict__ splt,
                                                        const double* __restrict__ hs,
                                                        const int* __restrict__ nend, const long long* __restrict__ off,
-                                                       double* part, int mode) {
+                                                       const long long* __restrict__ offk, double* part, int mode) {
+  constexpr bool MIX = KIND != 0;
+  constexpr bool PLAIN = KIND != 1;                // runs the plain unit: needs the tables
   __shared__ double red[6][kTileBins + kRedPad];   // block_sum6 staging (float2 rows when MIX)
-  __shared__ double pc[kProj];
-  __shared__ float2 pcw[kProj];                    // the projection forms as double words (MIX)
+  __shared__ double pc[PLAIN ? kProj : 1];
+  __shared__ float2 pcw[KIND == 2 ? kProj : 1];    // the projection forms as double words
   __shared__ double ihs[kNModes];
-  __shared__ float ampf[kNModes];                  // a_lm hsc in FP32 (MIX)
-  __shared__ double2 stab[kSinTab];                // as float4 double words when MIX
-  if (MIX) {
+  __shared__ float ampf[kNModes];                  // a_lm hsc in FP32 (KIND 1)
+  __shared__ float2 hsw[kNModes];                  // node spacing h as a double word (KIND 1)
+  __shared__ float ihsf[kNModes];                  // 1/h in FP32 (KIND 1)
+  __shared__ double2 stab[PLAIN ? kSinTab : 1];    // as float4 double words when MIX
+  if (KIND == 2) {
     float4* t4 = reinterpret_cast<float4*>(stab);
     for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) t4[i] = ds.d[0].sctw[i];
-  } else {
+  } else if (KIND == 0) {
     for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
   }
   __syncthreads();
+  // the tiles this kind walks: KIND 0 all of them (offk = off), KIND 1 and 2 those of their own
+  // pairs (offk: the scan of the pairs' tile counts with the other kind's set to 0); a tile's
+  // partial keeps its place in the full list, off[p] + its index in the pair
   const int P = ds.ndet * B;
-  const long long total = off[P];
-  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int p = find_pair_s(off, P, t);
+  const long long total = offk[P];
+  for (long long tk = blockIdx.x; tk < total; tk += gridDim.x) {
+    const int p = find_pair_s(offk, P, tk);
     const int I = p / B, s = p - I * B;
-    const int b0 = int(t - off[p]) * kTileBins + threadIdx.x;
+    const long long t = off[p] + (tk - offk[p]);
+    const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
+    const int b0 = int(tk - offk[p]) * kTileBins + threadIdx.x;
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
-    proj_prologue(D, S, pc);
+    if (PLAIN) proj_prologue(D, S, pc);
+    else __syncthreads();   // the previous tile's readers of the shared per-tile values are done
     if (threadIdx.x < kNModes) {
       ihs[threadIdx.x] = 1.0 / hs[(size_t)s * kNModes + threadIdx.x];
-      if (MIX) ampf[threadIdx.x] = (float)(coefN[s].md[threadIdx.x].amp * S.hsc);
+      if (KIND == 1) {
+        const double hm = hs[(size_t)s * kNModes + threadIdx.x];
+        ampf[threadIdx.x] = (float)(coefN[s].md[threadIdx.x].amp * S.hsc);
+        hsw[threadIdx.x] = to_dw(hm);
+        ihsf[threadIdx.x] = (float)ihs[threadIdx.x];
+      }
     }
-    if (MIX && threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+    if (KIND == 2 && threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
     __syncthreads();
-    const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
     if constexpr (MIX) {
       df v[6];
 #pragma unroll
@@ -474,20 +741,20 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
       const int b = b0;
       if (b < ne) {
         cdf x[3], o[3];
-        if (sur) {
+        if constexpr (KIND == 1) {
           const double f = D.f[b];
-          const double u0 = 3.0 * D.lnf3[b] - kLnFmin;
+          const df u0w = df_from_bits(fma(3.0, D.lnf3[b], -kLnFmin));
           const float fm76 = D.fm76w[b].x;
           const double pr = f * S.tc;                       // frac(f t_c) as load_bin
-          const double frc = (pr - rint(pr)) + fma(f, S.tc, -pr);
+          const df frcw = df_from_bits((pr - rint(pr)) + fma(f, S.tc, -pr));
           float2 xs[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll 1
           for (int md = 0; md < kNModes; ++md) {
             const ModeCoef& C = S.md[md];
-            if (!C.active || !(f < C.fend)) continue;
+            if (!C.active || !dlt_pos(f, C.fend)) continue;
             const size_t sys = ((size_t)I * B + s) * kNModes + md;
-            mode_bin_sur_mix(C, ampf[md], f, fm76, u0, frc, spl + sys * kQ * (kNodes - 1) * 4,
-                             splt + sys * (kQ - 1) * (kNodes - 1) * 4, hs[(size_t)s * kNModes + md], ihs[md], xs);
+            mode_bin_sur_mix(C, ampf[md], f, fm76, u0w, frcw, spl + sys * kQ * (kNodes - 1) * 4,
+                             splt + sys * (kQ - 1) * (kNodes - 1) * 4, hsw[md], ihsf[md], xs);
           }
 #pragma unroll
           for (int c = 0; c < 3; ++c) x[c] = cdf{df_make(xs[c].x, 0.f), df_make(xs[c].y, 0.f)};
@@ -568,6 +835,15 @@ __global__ void k_mismatch_reduce(int ndet, int B, const long long* off, const d
     }
   }
   mm[s] = (coef[s].valid && b > 0.0 && c > 0.0) ? 1.0 - a / sqrt(b * c) : NAN;
+}
+
+// Tile counts of the in-box pairs (nin) and of the others (nout), from the pairs' active bins.
+__global__ void k_split_nend(const double* theta, int ndet, int B, SurBox bx, const int* nend, int* nin, int* nout) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ndet * B) return;
+  const bool sur = in_box(theta + (size_t)(p % B) * PE_NPARAM, bx);
+  nin[p] = sur ? nend[p] : 0;
+  nout[p] = sur ? 0 : nend[p];
 }
 
 __global__ void k_used(const double* theta, int B, SurBox bx, const SampleCoef* coef, int32_t* used) {
@@ -1029,18 +1305,28 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   int* nend = nullptr;
   long long* off = nullptr;
   double *part = nullptr, *nodes = nullptr, *spl = nullptr, *hs = nullptr, *hs_sys = nullptr;
+  double2* nv = nullptr;
   float *Yd = nullptr, *splt = nullptr;
   const size_t nsys = (size_t)ndet * B * pe::kNModes;
   aalloc(&S, B);
   aalloc(&S0, B);
   aalloc(&nend, P);
   aalloc(&off, P + 1);
+  int *nin = nullptr, *nout = nullptr;
+  long long *offin = nullptr, *offout = nullptr;
+  if (mix) {
+    aalloc(&nin, P);
+    aalloc(&nout, P);
+    aalloc(&offin, P + 1);
+    aalloc(&offout, P + 1);
+  }
   aalloc(&part, (size_t)max_tiles * 6);
   aalloc(&nodes, nsys * pe::kQ * pe::kNodes);
   aalloc(&spl, nsys * pe::kQ * (pe::kNodes - 1) * 4);
   aalloc(&splt, nsys * (pe::kQ - 1) * (pe::kNodes - 1) * 4);
   aalloc(&hs, (size_t)B * pe::kNModes);
   aalloc(&hs_sys, nsys);
+  aalloc(&nv, (size_t)B * pe::kNModes);
   aalloc(&Yd, (size_t)B * pe::kNout);
   if (e == cudaSuccess) {
     // MLP inference (BF16 tensor cores) -> de-standardised node values
@@ -1057,9 +1343,14 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
       const long long nt = (long long)B * pe::kNModes * pe::kNodes;
       pe::k_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(theta_dev, B, S, S0, Yd);
     }
-    pe::k_node_h<<<(B * pe::kNModes + 127) / 128, 128, 0, st>>>(theta_dev, B, hs);
+    pe::k_node_h<<<(B * pe::kNModes + 127) / 128, 128, 0, st>>>(theta_dev, B, hs, nv);
     const long long nn = (long long)nsys * pe::kNodes;
-    pe::k_sur_nodes<<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(ds, B, S, S0, Yd, theta_dev, s->box, nodes);
+    if (mix)
+      pe::k_sur_nodes<true><<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(ds, B, S, S0, Yd, theta_dev, s->box, hs,
+                                                                          nv, nodes);
+    else
+      pe::k_sur_nodes<false><<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(ds, B, S, S0, Yd, theta_dev, s->box, hs,
+                                                                           nv, nodes);
     e = pe::launch_status();
     // the spline kernel reads the node spacing per system (I, s, md): replicate per detector
     for (int I = 0; I < ndet && e == cudaSuccess; ++I)
@@ -1067,23 +1358,35 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
                           cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) {
       const long long ns = (long long)nsys * pe::kQ;
-      pe::k_spline<<<(unsigned)((ns + 63) / 64), 64, 0, st>>>(nodes, ns, hs_sys, spl, splt);
+      pe::k_spline<<<(unsigned)((ns + pe::kSplineWarps - 1) / pe::kSplineWarps), 32 * pe::kSplineWarps, 0, st>>>(
+          nodes, ns, hs_sys, spl, splt, mix ? 1 : 0);
       e = pe::launch_status();
     }
   }
   if (e == cudaSuccess) e = pe::launch_prep(theta_dev, B, mode_mask, ds, S, nend, nullptr, st);
   if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, P, off, pe::kTileBins, st);
+  if (e == cudaSuccess && mix) {
+    pe::k_split_nend<<<(P + 127) / 128, 128, 0, st>>>(theta_dev, ndet, B, s->box, nend, nin, nout);
+    e = pe::launch_status();
+    if (e == cudaSuccess) e = pe::launch_scan_tiles(nin, P, offin, pe::kTileBins, st);
+    if (e == cudaSuccess) e = pe::launch_scan_tiles(nout, P, offout, pe::kTileBins, st);
+  }
   if (e == cudaSuccess) {
     int nsm = 1, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long g = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * 8));
-    if (mix)
-      pe::k_sur_fwd<true><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend,
-                                                                 off, part, mode);
-    else
-      pe::k_sur_fwd<false><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend,
-                                                                  off, part, mode);
+    if (mix) {
+      pe::k_sur_fwd<1><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
+                                                              offin, part, mode);
+      e = pe::launch_status();
+      if (e == cudaSuccess)
+        pe::k_sur_fwd<2><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend,
+                                                                off, offout, part, mode);
+    } else {
+      pe::k_sur_fwd<0><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
+                                                              off, part, mode);
+    }
     e = pe::launch_status();
   }
   if (e == cudaSuccess) {
