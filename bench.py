@@ -39,17 +39,18 @@ MSUN_S = 4.925490947641267e-6
 #   fp32_inst   FFMA + FMUL + FADD (the double-word arithmetic of the mixed path)
 UNIT_COUNTS = {
     "fp64": {"fp64_flops": 402.0, "fp64_inst": 252.1, "fp32_inst": 0.2},
-    "mixed": {"fp64_flops": 55.9, "fp64_inst": 42.2, "fp32_inst": 2281.3},
+    "mixed": {"fp64_flops": 36.9, "fp64_inst": 27.3, "fp32_inst": 2431.8},
     # FP32 path: fp64_inst counts the FRND and F2F of CUDA's FP32 sincospif/sinf and conversions
     "fp32": {"fp64_flops": 0.47, "fp64_inst": 9.9, "fp32_inst": 354.4},
 }
 # SHA-256 (first 16 hex digits) of the per-bin unit's sources the counts were taken on; the bench
 # marks the counts stale (and warns) when the sources have changed since.
-UNIT_SOURCES = ("pe_device.cuh", "pe_device_mixed.cuh", "pe_device_f32.cuh", "pe_df.cuh", "pe_kernels.cu")
-UNIT_COUNTS_SOURCE_SHA = {"fp64": "88ed2cfdca2eaddf", "mixed": "88ed2cfdca2eaddf", "fp32": "88ed2cfdca2eaddf"}
+UNIT_SOURCES = ("pe_device.cuh", "pe_device_mixed.cuh", "pe_device_f32.cuh", "pe_df.cuh", "pe_kernels.cu",
+                "pe_internal.h")
+UNIT_COUNTS_SOURCE_SHA = {"fp64": "586471c840af9737", "mixed": "586471c840af9737", "fp32": "586471c840af9737"}
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum:
 # the per-bin tables, read once per launch
-TRAFFIC = {"fp64": 36.47e6 + 0.01e6, "mixed": 40.00e6 + 1.01e6, "fp32": None}
+TRAFFIC = {"fp64": 36.75e6 + 0.01e6, "mixed": 40.34e6 + 1.04e6, "fp32": None}
 # Algorithmic work of the method (oracle/flop_model.py: the oracle's own operations, counted on
 # 16 samples of this workload): add/sub/mul/div per active (sample, mode, bin) unit and per active
 # (sample, bin) for the A/E/T and likelihood terms, and math-library calls per unit.

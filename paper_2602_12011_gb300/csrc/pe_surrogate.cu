@@ -32,6 +32,7 @@
 #include "pe_device_mixed.cuh"
 #include "pe_kernels.h"
 #include "pe_mlp.h"
+#include "pe_plan.h"
 #include "pe_surrogate.h"
 #include "pe_fault.h"
 
@@ -42,8 +43,11 @@ constexpr int kNout = kNModes * 2 * kNodes;   // [mode][kind][node], kind 0 phas
 constexpr int kNin = 64;                      // 11 features, zero padded
 constexpr int kHid = 256;
 constexpr int kQ = 7;                         // spline quantities per (detector, sample, mode)
+constexpr int kNodeTab = 2 + 8;               // double2 entries of k_node_h's table per (sample, mode)
 constexpr double kFmin = 1e-4;                // lowest node frequency [Hz]
 constexpr double kLnFmin = -9.210340371976182;  // ln(kFmin), the nodes' origin in u = ln f
+constexpr float kLnFminHi = static_cast<float>(kLnFmin);   // as a double word
+constexpr float kLnFminLo = static_cast<float>(kLnFmin - static_cast<double>(kLnFminHi));
 
 // ---- features, targets ------------------------------------------------------------------------
 // Normalised inputs: the 11 parameters, each affinely scaled to order one (log10 for the mass).
@@ -107,8 +111,9 @@ __global__ void k_sur_prep(const double* theta, int B, unsigned mask, SampleCoef
   S0[s] = b;
 }
 
-__device__ __forceinline__ double psi_of(const SampleCoef& S, double v, double lnv, double* dv_out) {
-  const double iv = 1.0 / v;
+__device__ __forceinline__ double psi_of(const SampleCoef& S, double v, double lnv, double* dv_out,
+                                         double iv = 0.0) {
+  if (iv == 0.0) iv = 1.0 / v;   // the caller may pass 1/v
   double iv5 = iv * iv;
   iv5 = iv5 * iv5 * iv;
   double poly = S.P[7], dpol = 2.0 * S.P[7];
@@ -262,9 +267,10 @@ __device__ __forceinline__ void node_links_f32(const DetDev& D, const SampleCoef
 }
 
 // Per (detector I, sample s, mode md, node j): the 7 spline quantities.
-// Y: de-standardised MLP outputs [Bpad][kNout]; hs, nv: the mode's node spacing h and (v, ln v) at
-// the first node (k_node_h); nodes out: [I][s][md][q][j]. Node j sits at f_j = kFmin e^{j h}, so
-// v_j = v_0 e^{j h/3} and ln v_j = ln v_0 + j h/3 (one exponential per node); the sines and cosines
+// Y: de-standardised MLP outputs [Bpad][kNout]; hs, nv: the mode's node spacing h and node table
+// (k_node_h); nodes out: [I][s][md][q][j]. Node j sits at f_j = kFmin e^{j h}, so
+// v_j = v_0 e^{j h/3} and ln v_j = ln v_0 + j h/3, with e^{+-j h/3} a product of the table's
+// e^{+-2^k h/3} over the binary digits of j (no exponential, division or log per node); the sines and cosines
 // go through the library's table sincos in turns, sin(a -+ a k.n) is formed from sin a, cos a and
 // one sincos of a k.n, and the pair of sincs shares one reciprocal.
 // MIX: the phase, t_f, the orbit angle and the centre Doppler term stay FP64 as above; the link
@@ -290,15 +296,22 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
   const DetDev& D = ds.d[I];
   const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
   const double h = hs[(size_t)s * kNModes + md];
-  const double2 v0 = nv[(size_t)s * kNModes + md];
-  const double jh3 = j * h * (1.0 / 3.0);
-  const double e3 = exp(jh3);
+  const double2* tab = nv + ((size_t)s * kNModes + md) * kNodeTab;
+  const double2 v0 = tab[0], iv0 = tab[1];
+  double e3 = 1.0, ie3 = 1.0;   // e^{+-j h/3} from the binary digits of j
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if ((j >> k) & 1) {
+      const double2 w = tab[2 + k];
+      e3 *= w.x;
+      ie3 *= w.y;
+    }
   const double f = kFmin * (e3 * e3 * e3);
-  const double invf = 1.0 / f;
+  const double invf = (1.0 / kFmin) * (ie3 * ie3 * ie3);
   const double v = v0.x * e3;
-  const double lnv = v0.y + jh3;
+  const double lnv = fma((double)j, iv0.y, v0.y);
   double D0;
-  const double psi0 = psi_of(S0[s], v, lnv, &D0);
+  const double psi0 = psi_of(S0[s], v, lnv, &D0, iv0.x * ie3);
   const float* y = Y + (size_t)s * kNout + (md * 2) * kNodes;
   const double r = y[j];
   const double amp_ratio = y[kNodes + j];
@@ -565,16 +578,25 @@ __global__ void __launch_bounds__(32 * kSplineWarps) k_spline(const double* node
   }
 }
 
-// Per (sample, mode): the node spacing h in ln f and (v, ln v) at the first node f = kFmin.
+// Per (sample, mode): the node spacing h in ln f, and the node table of k_sur_nodes: (v, ln v) and
+// (1/v, h/3) at the first node f = kFmin, then e^{+-2^k h/3} for k = 0..7 (each from exp, so a
+// node's product of at most 8 of them is within ~8 ulp of e^{+-j h/3}).
 __global__ void k_node_h(const double* theta, int B, double* hs, double2* nv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * kNModes) return;
   const int s = i / kNModes, md = i % kNModes;
   const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
   const double M = theta[(size_t)s * PE_NPARAM] * kMsunS;
-  hs[i] = node_h(M, mm);
+  const double h = node_h(M, mm);
+  hs[i] = h;
   const double v = cbrt(2.0 * kPi * M * kFmin / mm);
-  nv[i] = make_double2(v, log(v));
+  double2* t = nv + (size_t)i * kNodeTab;
+  t[0] = make_double2(v, log(v));
+  t[1] = make_double2(1.0 / v, h * (1.0 / 3.0));
+  for (int k = 0; k < 8; ++k) {
+    const double x = (double)(1 << k) * h * (1.0 / 3.0);
+    t[2 + k] = make_double2(exp(x), exp(-x));
+  }
 }
 
 // Spline evaluation of one mode at one bin: adds hsc H T_X, hsc H T_Y, hsc H T_Z to acc. The phase
@@ -663,8 +685,11 @@ __device__ __forceinline__ void mode_bin_sur_mix(const ModeCoef& C, float ampf, 
   }
 }
 
-__device__ __forceinline__ int find_pair_s(const long long* off, int P, long long t) {
-  int lo = 0, hi = P;
+// The pair p with off[p] <= t < off[p + 1] (the last such p where pairs are empty), searched in
+// [lo, P): a CTA's tiles only move forward, so it passes the pair of its previous tile.
+__device__ __forceinline__ int find_pair_s(const long long* off, int P, long long t, int lo = 0) {
+  if (off[lo + 1] > t) return lo;   // still in the previous tile's pair (or its empty successors' place)
+  int hi = P;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (off[mid] <= t) lo = mid; else hi = mid;
@@ -676,47 +701,52 @@ __device__ __forceinline__ int find_pair_s(const long long* off, int P, long lon
 // one bin per thread, the same order of the sums). KIND 0 (FP64), mode 0: surrogate path (in-box
 // samples) or plain path (others), partials [tile][6] as the plain kernel; mode 1: mismatch sums
 // of the surrogate against the plain signal, partials [tile][6] = (<s|p>, <s|s>, <p|p>, 0, 0, 0).
-// KIND 1 and 2, the mixed-precision variant (mode 0), split over two launches that each take their
-// own tiles: KIND 1 the in-box samples' tiles (mode_bin_sur_mix, a light unit with few registers
-// and no tables in shared memory), KIND 2 the out-of-box samples' tiles (the mixed plain unit
-// bin_xyz_mixed, as k_loglike_fwd with PE_PREC_MIXED). Both form A/E/T and the weighted products
-// in double words and sum each tile in double words (k_loglike_fwd's mixed tail), scaled back to
-// FP64 per tile, so a tile's partial does not depend on the split.
+// KIND 1, the mixed-precision variant (mode 0): the in-box samples' tiles only (mode_bin_sur_mix, a
+// light unit with few registers and no tables in shared memory), A/E/T and the weighted products in
+// double words and each tile summed in double words (k_loglike_fwd's mixed tail), scaled back to
+// FP64 per tile. The out-of-box samples' tiles go to k_loglike_fwd itself (PE_PREC_MIXED).
+constexpr int kSurInboxCtas = 8;    // resident CTAs per SM asked of the in-box kernel (KIND 1)
 template <int KIND>
-__global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+__global__ void __launch_bounds__(kTileBins, KIND == 1 ? kSurInboxCtas : 3) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                        const SampleCoef* __restrict__ coefN,
                                                        const double* __restrict__ theta, SurBox bx,
                                                        const double* __restrict__ spl, const float* __restrict__ splt,
                                                        const double* __restrict__ hs,
                                                        const int* __restrict__ nend, const long long* __restrict__ off,
                                                        const long long* __restrict__ offk, double* part, int mode) {
+  static_assert(KIND == 0 || KIND == 1, "KIND 0 (FP64) or 1 (mixed, in-box tiles)");
   constexpr bool MIX = KIND != 0;
   constexpr bool PLAIN = KIND != 1;                // runs the plain unit: needs the tables
   __shared__ double red[6][kTileBins + kRedPad];   // block_sum6 staging (float2 rows when MIX)
   __shared__ double pc[PLAIN ? kProj : 1];
-  __shared__ float2 pcw[KIND == 2 ? kProj : 1];    // the projection forms as double words
   __shared__ double ihs[kNModes];
   __shared__ float ampf[kNModes];                  // a_lm hsc in FP32 (KIND 1)
   __shared__ float2 hsw[kNModes];                  // node spacing h as a double word (KIND 1)
   __shared__ float ihsf[kNModes];                  // 1/h in FP32 (KIND 1)
-  __shared__ double2 stab[PLAIN ? kSinTab : 1];    // as float4 double words when MIX
-  if (KIND == 2) {
-    float4* t4 = reinterpret_cast<float4*>(stab);
-    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) t4[i] = ds.d[0].sctw[i];
-  } else if (KIND == 0) {
+  __shared__ double2 stab[PLAIN ? kSinTab : 1];
+  if (KIND == 0)
     for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
-  }
   __syncthreads();
-  // the tiles this kind walks: KIND 0 all of them (offk = off), KIND 1 and 2 those of their own
-  // pairs (offk: the scan of the pairs' tile counts with the other kind's set to 0); a tile's
-  // partial keeps its place in the full list, off[p] + its index in the pair
+  // the tiles this kind walks: KIND 0 all of them (offk = off), KIND 1 those of the in-box pairs
+  // (offk: the scan of the pairs' tile counts with the others' set to 0); a tile's partial keeps its
+  // place in the full list, off[p] + its index in the pair
+  // KIND 1 takes a contiguous run of tiles per CTA, so that consecutive tiles of one pair reuse
+  // the pair's spline coefficients from L1; the heavier kinds stride over the list
   const int P = ds.ndet * B;
   const long long total = offk[P];
-  for (long long tk = blockIdx.x; tk < total; tk += gridDim.x) {
-    const int p = find_pair_s(offk, P, tk);
+  long long tk0 = blockIdx.x, tk1 = total, step = gridDim.x;
+  if (KIND == 1) {
+    const long long chunk = (total + gridDim.x - 1) / gridDim.x;
+    tk0 = blockIdx.x * chunk;
+    tk1 = tk0 + chunk < total ? tk0 + chunk : total;
+    step = 1;
+  }
+  int p = 0;
+  for (long long tk = tk0; tk < tk1; tk += step) {
+    p = find_pair_s(offk, P, tk, p);
     const int I = p / B, s = p - I * B;
     const long long t = off[p] + (tk - offk[p]);
-    const bool sur = in_box(theta + (size_t)s * PE_NPARAM, bx);
+    const bool sur = KIND == 0 ? in_box(theta + (size_t)s * PE_NPARAM, bx) : KIND == 1;
     const int b0 = int(tk - offk[p]) * kTileBins + threadIdx.x;
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
@@ -732,7 +762,6 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
         ihsf[threadIdx.x] = (float)ihs[threadIdx.x];
       }
     }
-    if (KIND == 2 && threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
     __syncthreads();
     if constexpr (MIX) {
       df v[6];
@@ -742,13 +771,15 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
       if (b < ne) {
         cdf x[3], o[3];
         if constexpr (KIND == 1) {
+          // per bin in double words, no FP64 arithmetic: u0 = 3 (ln f / 3) - ln kFmin, and frac(f t_c)
+          // from the double-word product (relative error ~2^-46: ~1e-8 turn at f t_c ~ 4e5 turns)
           const double f = D.f[b];
-          const df u0w = df_from_bits(fma(3.0, D.lnf3[b], -kLnFmin));
+          const df u0w = dfl_sub(dfl_mulf(df_from_bits(D.lnf3[b]), 3.f), df_make(kLnFminHi, kLnFminLo));
           const float fm76 = D.fm76w[b].x;
-          const double pr = f * S.tc;                       // frac(f t_c) as load_bin
-          const df frcw = df_from_bits((pr - rint(pr)) + fma(f, S.tc, -pr));
+          const df ftc = dfl_mul(D.fw[b], S.tcw);
+          const df frcw = two_sum(__fsub_rn(ftc.x, rintf(ftc.x)), ftc.y);
           float2 xs[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll 1
+#pragma unroll   // the modes' coefficient loads overlap
           for (int md = 0; md < kNModes; ++md) {
             const ModeCoef& C = S.md[md];
             if (!C.active || !dlt_pos(f, C.fend)) continue;
@@ -758,8 +789,6 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
           }
 #pragma unroll
           for (int c = 0; c < 3; ++c) x[c] = cdf{df_make(xs[c].x, 0.f), df_make(xs[c].y, 0.f)};
-        } else {
-          bin_xyz_mixed(D, S, b, x, reinterpret_cast<const float4*>(stab), pcw);
         }
         aet_from_xyz_dw(x, o);
 #pragma unroll
@@ -770,11 +799,11 @@ __global__ void __launch_bounds__(kTileBins) k_sur_fwd(DetSet ds, int B, const S
           v[3 + c] = df_mul(D.ggw[c * D.nb + b], m2);
         }
       }
-      const double ih = S.ihsc;
-      const double sd = D.dg_scale * ih, sg = D.gg_scale * ih * ih;
       df r;
-      if (block_sum6(v, [](df a, df b) { return dfl_add(a, b); }, reinterpret_cast<float2(*)[kTileBins + kRedPad]>(red), &r))
-        part[t * 6 + threadIdx.x] = df_to(r) * (threadIdx.x < 3 ? sd : sg);
+      if (block_sum6(v, [](df a, df b) { return dfl_add(a, b); }, reinterpret_cast<float2(*)[kTileBins + kRedPad]>(red), &r)) {
+        const double ih = S.ihsc;
+        part[t * 6 + threadIdx.x] = df_to(r) * (threadIdx.x < 3 ? D.dg_scale * ih : D.gg_scale * ih * ih);
+      }
     } else {
       double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
@@ -1326,7 +1355,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   aalloc(&splt, nsys * (pe::kQ - 1) * (pe::kNodes - 1) * 4);
   aalloc(&hs, (size_t)B * pe::kNModes);
   aalloc(&hs_sys, nsys);
-  aalloc(&nv, (size_t)B * pe::kNModes);
+  aalloc(&nv, (size_t)B * pe::kNModes * pe::kNodeTab);
   aalloc(&Yd, (size_t)B * pe::kNout);
   if (e == cudaSuccess) {
     // MLP inference (BF16 tensor cores) -> de-standardised node values
@@ -1365,11 +1394,14 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   }
   if (e == cudaSuccess) e = pe::launch_prep(theta_dev, B, mode_mask, ds, S, nend, nullptr, st);
   if (e == cudaSuccess) e = pe::launch_scan_tiles(nend, P, off, pe::kTileBins, st);
+  pe::TuneChoice tcm = pe::default_choice(pe::kPrecMixed);
+  if (mix) pe::lookup_tuned(ds, B, mode_mask | PE_PREC_MIXED, &tcm);
   if (e == cudaSuccess && mix) {
     pe::k_split_nend<<<(P + 127) / 128, 128, 0, st>>>(theta_dev, ndet, B, s->box, nend, nin, nout);
     e = pe::launch_status();
     if (e == cudaSuccess) e = pe::launch_scan_tiles(nin, P, offin, pe::kTileBins, st);
-    if (e == cudaSuccess) e = pe::launch_scan_tiles(nout, P, offout, pe::kTileBins, st);
+    // the fallback pairs' work items for the tuned mixed-precision forward kernel
+    if (e == cudaSuccess) e = pe::launch_scan_tiles(nout, P, offout, tcm.subtiles * pe::kTileBins, st);
   }
   if (e == cudaSuccess) {
     int nsm = 1, dev = 0;
@@ -1377,17 +1409,21 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long g = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * 8));
     if (mix) {
-      pe::k_sur_fwd<1><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
+      const long long g1 = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * pe::kSurInboxCtas));
+      pe::k_sur_fwd<1><<<(unsigned)g1, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
                                                               offin, part, mode);
       e = pe::launch_status();
+      // fallback tiles: the mixed-precision forward kernel of pe_loglike_batch with its tuned (or
+      // default) choice, over the fallback pairs' work items; it writes each sub-tile's partial at
+      // off[p] + its index, the same place as in the full list
       if (e == cudaSuccess)
-        pe::k_sur_fwd<2><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend,
-                                                                off, offout, part, mode);
+        e = pe::launch_loglike_fwd_variant(tcm.variant, pe::kPrecMixed, ds, B, S, nend, off, offout, tcm.subtiles,
+                                           part, pe::grid_for(tcm, max_tiles), st);
     } else {
       pe::k_sur_fwd<0><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
                                                               off, part, mode);
+      e = pe::launch_status();
     }
-    e = pe::launch_status();
   }
   if (e == cudaSuccess) {
     if (mode == 0) {

@@ -221,11 +221,12 @@ def test_network_against_the_paths_without_it(Lb, lisa22, trained):
       plain FP64  the per-bin path (1e-10 parity);
       plain mixed the per-bin path with double-word geometry (1e-10 parity);
       network mixed / no network mixed: the spline path with PE_PREC_MIXED.
-    The spline path beats the plain FP64 path (> 1.3x) with or without the network. The network
-    buys nothing over exact node values here: TaylorF2 is analytic, so the exact node values cost
-    about what the MLP inference does, and they are exact (mismatch from the splines alone). The
-    mixed spline path stays within 1e-6 of the likelihood's scale of the FP64 spline path and is
-    faster than it; its ratio to the plain mixed path is recorded."""
+    The spline path beats the plain FP64 path (> 1.3x) with or without the network. In FP64 the
+    network buys little over exact node values (TaylorF2 is analytic, so its FP64 node values cost
+    about what the MLP inference does); in the mixed path, where the per-bin work has left the FP64
+    pipe, the exact node values' FP64 evaluation is a visible share and the BF16 network beats it
+    (> 1.15x; measured ~1.4x). The mixed spline path stays within 1e-6 of the likelihood's scale
+    of the FP64 spline path and beats the plain mixed path at full parity (> 2x; measured ~4x)."""
     import torch
     th = W.draw_prior(1024, 2608, T22)
     th[:, 1] = np.minimum(th[:, 1], 8.0)
@@ -284,6 +285,8 @@ def test_network_against_the_paths_without_it(Lb, lisa22, trained):
     assert t_plain / t_net > 1.3 and t_plain / t_exact > 1.3
     assert dev <= 1e-6
     assert t_net_mx < t_net
+    assert t_mixed / t_net_mx > 2.0
+    assert t_exact_mx / t_net_mx > 1.15
 
 
 def test_checkpoint_roundtrip_and_corruption(Lb, trained, tmp_path):
