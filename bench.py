@@ -45,9 +45,12 @@ UNIT_COUNTS = {
 }
 # SHA-256 (first 16 hex digits) of the per-bin unit's sources the counts were taken on; the bench
 # marks the counts stale (and warns) when the sources have changed since.
-UNIT_SOURCES = ("pe_device.cuh", "pe_device_mixed.cuh", "pe_device_f32.cuh", "pe_df.cuh", "pe_kernels.cu",
-                "pe_internal.h")
-UNIT_COUNTS_SOURCE_SHA = {"fp64": "586471c840af9737", "mixed": "586471c840af9737", "fp32": "586471c840af9737"}
+UNIT_SOURCES = {
+    "fp64": ("pe_device.cuh", "pe_kernels.cu", "pe_internal.h"),
+    "mixed": ("pe_device.cuh", "pe_device_mixed.cuh", "pe_df.cuh", "pe_kernels.cu", "pe_internal.h"),
+    "fp32": ("pe_device.cuh", "pe_device_f32.cuh", "pe_kernels.cu", "pe_internal.h"),
+}
+UNIT_COUNTS_SOURCE_SHA = {"fp64": "7d24ccd1e20053ac", "mixed": "528d2df6fd1429b0", "fp32": "92b088e0accfee87"}
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum:
 # the per-bin tables, read once per launch
 TRAFFIC = {"fp64": 36.75e6 + 0.01e6, "mixed": 40.34e6 + 1.04e6, "fp32": None}
@@ -58,10 +61,10 @@ ALG_MODEL = {"flops_per_unit": 1755.0, "flops_per_bin": 63.0, "math_calls_per_un
              "source": "oracle/flop_model.py (plain per-bin formulation, counted with an operation-counting scalar)"}
 
 
-def unit_sources_sha() -> str:
+def unit_sources_sha(prec: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in UNIT_SOURCES:
+    for name in UNIT_SOURCES[prec]:
         with open(os.path.join(ROOT, "paper_2602_12011_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -275,7 +278,7 @@ def roofline(prec: str, units: int, launch_s: float, peaks: dict, n_sm: int = 15
         if sm_mhz_run:
             pipes[name]["frac_nominal_at_run_clock"] = ach / (PIPE_PER_CLK[name] * n_sm * sm_mhz_run / 1e3)
     bind = max(pipes, key=lambda k: pipes[k]["frac"])
-    sha = unit_sources_sha()
+    sha = unit_sources_sha(prec)
     alg_tflops = (ALG_MODEL["flops_per_unit"] * units + ALG_MODEL["flops_per_bin"] * bins) / launch_s / 1e12
     fp64_nominal_tflops = 2 * PIPE_PER_CLK["fp64"] * n_sm * sm_max_mhz / 1e6
     return {"bound": "alu", "pipe": bind, "unit": "Ginst/s", "achieved": pipes[bind]["achieved_ginst_s"],
@@ -296,7 +299,8 @@ def roofline(prec: str, units: int, launch_s: float, peaks: dict, n_sm: int = 15
             "unit_counts_current": UNIT_COUNTS_SOURCE_SHA[prec] == sha,
             "pipes": pipes,
             "traffic": TRAFFIC[prec] if UNIT_COUNTS_SOURCE_SHA[prec] == sha else None,
-            "traffic_gbs": TRAFFIC[prec] / launch_s / 1e9 if TRAFFIC[prec] else None}
+            "traffic_gbs": (TRAFFIC[prec] / launch_s / 1e9
+                            if TRAFFIC[prec] and UNIT_COUNTS_SOURCE_SHA[prec] == sha else None)}
 
 
 def measure_peaks(L, local_rank: int) -> dict:

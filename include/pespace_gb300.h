@@ -220,7 +220,8 @@ pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_ma
  * amplitude ratio its |H_lm| relative to the Newtonian power law. At the nodes the full response
  * (t_f, orbit, links, TDI) is evaluated in FP64 and not-a-knot cubic splines in ln f carry the
  * mode phase and the A/E/T transfer functions to every bin (the sparse-node interpolation idea the
- * paper cites for lisabeta, Sec. 1). Samples outside the training box take the plain path.
+ * paper cites for lisabeta, Sec. 1). Samples outside the training box, and detectors on a
+ * geocentric orbit, take the plain path.
  *   pe_surrogate_create: random initial weights (seed); the library owns all device memory.
  *   pe_surrogate_train: trains on the plain generator's node values of theta_train_dev
  *     [n_train][11] (device) with Adam, MSE on standardised outputs, cosine learning rate, batch
@@ -232,7 +233,10 @@ pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_ma
  *   pe_surrogate_targets / pe_surrogate_predict: plain-generator / network node values
  *     [B][5][2][256] (fp32, device) for theta [B][11] (device).
  *   pe_surrogate_loglike_batch: log L per sample through the surrogate path (device pointers);
- *     out_used_dev (nullable) = 1 where the surrogate was used, 0 where the plain path was.
+ *     out_used_dev (nullable) = 1 where the surrogate was used, 0 where the plain path was. A
+ *     detector on a geocentric orbit (TianQin) always takes the plain path: its response turns
+ *     too fast in t_f for the log-spaced nodes; used = 1 means the node splines served at least
+ *     one heliocentric detector.
  *     mode_mask may carry PE_PREC_MIXED: out-of-box samples then take the mixed-precision plain
  *     path (as pe_loglike_batch with the flag) and in-box samples evaluate the spline phase in
  *     FP64, its sine and cosine and the transfer functions on the FP32 pipe; A/E/T and the

@@ -171,7 +171,9 @@ __device__ __forceinline__ cdf cdfl_mul(const cdf& a, const cdf& b) {
 // t = 2 pi d (|t| <= pi/kSinTab) goes through sin t = t + t t^2 (-1/6 + t^2/120) and
 // cos t = 1 + t^2 (-1/2 + t^2/24); the t^2/120 and t^2/24 corrections enter the low words of the
 // double-word coefficients (their rounding is below 1e-18 of the result, the dropped t^7 and t^6
-// terms below 2e-18). tab[j] = (cos hi, cos lo, sin hi, sin lo) of 2 pi j/kSinTab. Not inlined: the
+// terms below 2e-18). The Taylor sums and the rotation by the table entry use the unnormalised
+// operations below (dfl_*: the same rounding error bounds, the result's |lo| possibly a few ulps
+// above ulp(hi)/2, as every lazy result). tab[j] = (cos hi, cos lo, sin hi, sin lo) of 2 pi j/kSinTab. Not inlined: the
 // mixed unit calls it from five places, and one copy keeps the kernel's hot loop in the
 // instruction cache.
 static __device__ __noinline__ cdf df_cis_turns(df x, const float4* __restrict__ tab) {
@@ -186,16 +188,16 @@ static __device__ __noinline__ cdf df_cis_turns(df x, const float4* __restrict__
   const df d = fast_two_sum(__fsub_rn(rh, __fmul_rn(__fsub_rn(yb, kR), 1.0f / kSinTab)), x.y);
   const float4 e = tab[j & (kSinTab - 1)];
   const df cj = df_make(e.x, e.y), sj = df_make(e.z, e.w);
-  const df t = df_mul(d, df_make(6.28318548202514648f, -1.74845553e-07f));   // 2 pi as a double word
-  const df t2 = df_mul(t, t);
+  const df t = dfl_mul(d, df_make(6.28318548202514648f, -1.74845553e-07f));   // 2 pi as a double word
+  const df t2 = dfl_mul(t, t);
   // -1/6 = -0.166666672 + 4.96705388e-09 and -1/2, with the next Taylor terms folded into the lows
   const df ps = df_make(-0.166666672f, __fmaf_rn(t2.x, 1.0f / 120.0f, 4.96705388e-09f));
   const df pc = df_make(-0.5f, __fmul_rn(t2.x, 1.0f / 24.0f));
-  const df st = df_add_s(t, df_mul(t, df_mul(t2, ps)));
-  const df ct = df_add_s(df_make(1.f, 0.f), df_mul(t2, pc));
+  const df st = dfl_add(t, dfl_mul(t, dfl_mul(t2, ps)));
+  const df ct = dfl_add(df_make(1.f, 0.f), dfl_mul(t2, pc));
   cdf r;
-  r.re = df_sub_s(df_mul(cj, ct), df_mul(sj, st));
-  r.im = df_add_s(df_mul(sj, ct), df_mul(cj, st));
+  r.re = dfl_sub(dfl_mul(cj, ct), dfl_mul(sj, st));
+  r.im = dfl_add(dfl_mul(sj, ct), dfl_mul(cj, st));
   return r;
 }
 

@@ -201,6 +201,15 @@ __device__ __forceinline__ bool in_box(const double* t, const SurBox& bx) {
   return t[0] >= bx.mlo && t[0] <= bx.mhi && t[1] <= bx.qmax && fabs(t[2]) <= bx.chimax && fabs(t[3]) <= bx.chimax;
 }
 
+// Whether a (sample, detector) pair takes the node-spline path: the sample is in the training box
+// and the detector's orbit is heliocentric. A geocentric orbit (TianQin: a turn in 3.65 days)
+// turns the response ~85 times per unit of ln f where t_f runs months before coalescence, ~2.5
+// turns per node interval of the 256 log-spaced nodes, which no spline on those nodes carries;
+// such a detector's bins take the plain path (its share of log L is then exact).
+__device__ __forceinline__ bool sur_pair(const double* t, const SurBox& bx, int orbit) {
+  return orbit == 0 && in_box(t, bx);
+}
+
 // FP32 link transfer functions of one node (the mixed path): T_X, T_Y, T_Z per unit mode amplitude,
 // the same algebra as below with every quantity a float. The transfer functions are O(1) sums of
 // O(1) link terms (the TDI factor, which vanishes at low frequency, is in the data tables), so
@@ -289,11 +298,11 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
   double* q = nodes + ((((size_t)I * B + s) * kNModes + md) * kQ) * kNodes + j;
   const SampleCoef& Sa = S[s];
   const ModeCoef& C = Sa.md[md];
-  if (!C.active || !in_box(theta + (size_t)s * PE_NPARAM, bx)) {
+  const DetDev& D = ds.d[I];
+  if (!C.active || !sur_pair(theta + (size_t)s * PE_NPARAM, bx, D.orbit)) {
     for (int k = 0; k < kQ; ++k) q[k * kNodes] = 0.0;
     return;
   }
-  const DetDev& D = ds.d[I];
   const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
   const double h = hs[(size_t)s * kNModes + md];
   const double2* tab = nv + ((size_t)s * kNModes + md) * kNodeTab;
@@ -746,7 +755,7 @@ __global__ void __launch_bounds__(kTileBins, KIND == 1 ? kSurInboxCtas : 3) k_su
     p = find_pair_s(offk, P, tk, p);
     const int I = p / B, s = p - I * B;
     const long long t = off[p] + (tk - offk[p]);
-    const bool sur = KIND == 0 ? in_box(theta + (size_t)s * PE_NPARAM, bx) : KIND == 1;
+    const bool sur = KIND == 0 ? sur_pair(theta + (size_t)s * PE_NPARAM, bx, ds.d[I].orbit) : KIND == 1;
     const int b0 = int(tk - offk[p]) * kTileBins + threadIdx.x;
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
@@ -867,17 +876,19 @@ __global__ void k_mismatch_reduce(int ndet, int B, const long long* off, const d
 }
 
 // Tile counts of the in-box pairs (nin) and of the others (nout), from the pairs' active bins.
-__global__ void k_split_nend(const double* theta, int ndet, int B, SurBox bx, const int* nend, int* nin, int* nout) {
+__global__ void k_split_nend(const double* theta, int ndet, int B, SurBox bx, unsigned geo_mask, const int* nend,
+                             int* nin, int* nout) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= ndet * B) return;
-  const bool sur = in_box(theta + (size_t)(p % B) * PE_NPARAM, bx);
+  const bool sur = sur_pair(theta + (size_t)(p % B) * PE_NPARAM, bx, (geo_mask >> (p / B)) & 1u);
   nin[p] = sur ? nend[p] : 0;
   nout[p] = sur ? 0 : nend[p];
 }
 
-__global__ void k_used(const double* theta, int B, SurBox bx, const SampleCoef* coef, int32_t* used) {
+// used[s] = 1 where the sample took the node-spline path on at least one (heliocentric) detector.
+__global__ void k_used(const double* theta, int B, SurBox bx, int any_helio, const SampleCoef* coef, int32_t* used) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < B) used[s] = (coef[s].valid && in_box(theta + (size_t)s * PE_NPARAM, bx)) ? 1 : 0;
+  if (s < B) used[s] = (any_helio && coef[s].valid && in_box(theta + (size_t)s * PE_NPARAM, bx)) ? 1 : 0;
 }
 
 __global__ void k_destd(const float* Y, int B, const float* mean, const float* stdv, float* out) {
@@ -1397,7 +1408,10 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   pe::TuneChoice tcm = pe::default_choice(pe::kPrecMixed);
   if (mix) pe::lookup_tuned(ds, B, mode_mask | PE_PREC_MIXED, &tcm);
   if (e == cudaSuccess && mix) {
-    pe::k_split_nend<<<(P + 127) / 128, 128, 0, st>>>(theta_dev, ndet, B, s->box, nend, nin, nout);
+    unsigned geo_mask = 0;
+    for (int I = 0; I < ndet; ++I)
+      if (ds.d[I].orbit != 0) geo_mask |= 1u << I;
+    pe::k_split_nend<<<(P + 127) / 128, 128, 0, st>>>(theta_dev, ndet, B, s->box, geo_mask, nend, nin, nout);
     e = pe::launch_status();
     if (e == cudaSuccess) e = pe::launch_scan_tiles(nin, P, offin, pe::kTileBins, st);
     // the fallback pairs' work items for the tuned mixed-precision forward kernel
@@ -1429,7 +1443,9 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     if (mode == 0) {
       e = pe::launch_reduce(ds, B, off, part, S, out0, nullptr, st);
       if (e == cudaSuccess && used) {
-        pe::k_used<<<(B + 127) / 128, 128, 0, st>>>(theta_dev, B, s->box, S, used);
+        int any_helio = 0;
+        for (int I = 0; I < ndet; ++I) any_helio |= ds.d[I].orbit == 0 ? 1 : 0;
+        pe::k_used<<<(B + 127) / 128, 128, 0, st>>>(theta_dev, B, s->box, any_helio, S, used);
         e = pe::launch_status();
       }
     } else {

@@ -171,6 +171,36 @@ def test_node_spline_path_matches_oracle(oracle_mod, Lb, prec):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_node_spline_path_network_matches_oracle(oracle_mod, Lb, prec):
+    """The node-spline path on a two-detector network, LISA (heliocentric) and TianQin (geocentric
+    orbit, the FP32 node geometry's other branch), with the plain generator's node values: joint
+    log L within the spline's 1e-6 of the likelihood's scale of the oracle's."""
+    import torch
+    flag = Lb.PE_PREC_MIXED if prec == "mixed" else 0
+    T = 2.0 ** 20
+    k0, nb = W.grid(T)
+    inj = np.array([2e6, 3.0, 0.5, 0.3, 25.8, 0.4, 1.3, 1.375, -1.2108, 2.659, 0.8 * T])
+    ods = [H.oracle_detector(oracle_mod, det, T, k0, nb, inj, W.MODE_ALL, seed)
+           for det, seed in ((W.LISA, 5), (W.TIANQIN, 6))]
+    gds = [H.library_detector(Lb, od) for od in ods]
+    s = Lb.Surrogate(seed=1)
+    s.set_node_source(1)
+    th = np.vstack([inj, W.draw_prior(5, 37, T)])
+    th[1:, 0] = np.linspace(4e5, 8e6, 5)
+    th[1:, 1] = np.minimum(th[1:, 1], 8.0)
+    ll, used = s.loglike(gds, torch.tensor(th, device="cuda"), W.MODE_ALL | flag)
+    ll = ll.cpu().numpy()
+    assert np.all(used.cpu().numpy() == 1)
+    ref, dhhh = oracle_mod.loglike_batch(ods, th, W.MODE_ALL)
+    dd = sum(oracle_mod.loglike([od], inj, 0)["dd"].sum() for od in ods)
+    for i in range(th.shape[0]):
+        scale = 0.5 * dd + abs(dhhh[i, :, :, 0].sum()) + 0.5 * dhhh[i, :, :, 1].sum()
+        H.record_margin("surrogate:node_spline_network_%s" % prec, abs(ll[i] - ref[i]) / (1e-6 * scale))
+        assert abs(ll[i] - ref[i]) <= 1e-6 * scale, (i, ll[i], ref[i])
+    s.close()
+
+
 def test_heldout_mismatch_acceptance(Lb, lisa22, trained):
     """>= 99% of held-out samples inside the training box have mismatch <= 1e-3 against the plain
     generator on the 2^22 s LISA grid (noise-weighted inner product)."""
@@ -199,6 +229,26 @@ def test_fallback_is_the_plain_path_bitwise(Lb, lisa22, trained, prec):
     out = (th[:, 1] > 8.0) | (th[:, 0] < 3e5)
     assert np.array_equal(used.cpu().numpy(), (~out).astype(np.int32))
     assert np.array_equal(ll.cpu().numpy()[out], ref[out])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_geocentric_detector_takes_the_plain_path(Lb, trained, prec):
+    """A detector on a geocentric orbit (TianQin) never takes the node splines: in-box samples get
+    the plain path's log L bit for bit and used = 0."""
+    import torch
+    flag = Lb.PE_PREC_MIXED if prec == "mixed" else 0
+    T = 2.0 ** 20
+    k0, nb = W.grid(T)
+    d = Lb.Detector(W.TIANQIN, T, k0, nb)
+    d.inject(W.theta_injection(T), W.MODE_ALL, W.normals(nb, 11))
+    th = W.draw_prior(32, 2611, T)
+    th[:, 1] = np.minimum(th[:, 1], 8.0)
+    th[:, 0] = np.maximum(th[:, 0], 3e5)
+    ll, used = trained.loglike([d], torch.tensor(th, device="cuda"), W.MODE_ALL | flag)
+    ref = Lb.loglike([d], th, W.MODE_ALL | flag)["logl"]
+    assert np.all(used.cpu().numpy() == 0)
+    assert np.array_equal(ll.cpu().numpy(), ref)
+    d.close()
 
 
 def test_precision_flags_that_the_surrogate_rejects(Lb, lisa22, trained):
