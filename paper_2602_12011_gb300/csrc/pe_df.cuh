@@ -114,20 +114,6 @@ __device__ __forceinline__ df df_sum3_exact(df a, df b, df c) {
   return two_sum(u.x, __fadd_rn(u.y, r));
 }
 
-// 1/x: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0) (error delta^2)
-__device__ __forceinline__ df df_rcp(df x) {
-  const float y0 = __frcp_rn(x.x);
-  const df e = df_sub(df_make(1.f, 0.f), df_mulf(x, y0));
-  return df_add(df_make(y0, 0.f), df_mulf(e, y0));
-}
-// 1/sqrt(x), x > 0: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0^2)/2
-// (relative error (3/2) delta^2 for a seed error delta <= u, plus the DW rounding)
-__device__ __forceinline__ df df_rsqrt(df x) {
-  const float y0 = __frsqrt_rn(x.x);
-  const df xy2 = df_mulf(df_mulf(x, y0), y0);
-  const df e = df_sub(df_make(1.f, 0.f), xy2);
-  return df_add(df_make(y0, 0.f), df_mulf(df_scale2(e, 0.5f), y0));
-}
 
 // Unnormalised ("lazy") variants for the long chains of the mixed-precision units. dfl_add is
 // df_add_s without its closing Fast2Sum: the same rounded quantities, so the same absolute error
@@ -149,6 +135,23 @@ __device__ __forceinline__ df dfl_mul(df x, df y) {
 __device__ __forceinline__ df dfl_mulf(df x, float y) {
   const float ch = __fmul_rn(x.x, y);
   return df_make(ch, __fmaf_rn(x.y, y, __fmaf_rn(x.x, y, -ch)));
+}
+// 1/x: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0) (error delta^2).
+// The step runs on the unnormalised operations: 1 - x y0 is exact in its high word (Sterbenz) and
+// only ~u in size, so the lazy pairs lose nothing that the step keeps.
+__device__ __forceinline__ df df_rcp(df x) {
+  const float y0 = __frcp_rn(x.x);
+  const df e = dfl_sub(df_make(1.f, 0.f), dfl_mulf(x, y0));
+  return dfl_add(df_make(y0, 0.f), dfl_mulf(e, y0));
+}
+// 1/sqrt(x), x > 0: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0^2)/2
+// (relative error (3/2) delta^2 for a seed error delta <= u, plus the DW rounding); unnormalised
+// operations as df_rcp.
+__device__ __forceinline__ df df_rsqrt(df x) {
+  const float y0 = __frsqrt_rn(x.x);
+  const df xy2 = dfl_mulf(dfl_mulf(x, y0), y0);
+  const df e = dfl_sub(df_make(1.f, 0.f), xy2);
+  return dfl_add(df_make(y0, 0.f), dfl_mulf(df_scale2(e, 0.5f), y0));
 }
 
 // complex DW numbers as pairs (re, im)
