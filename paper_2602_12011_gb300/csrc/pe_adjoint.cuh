@@ -31,7 +31,7 @@ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {  // a * conj
 
 // d sinc(u)/du with the same small-argument series as sinc_small
 __device__ __forceinline__ double dsinc(double u, double cosu, double sincu) {
-  if (fabs(u) < 1e-3) {
+  if (dlt_pos(fabs(u), 1e-3)) {
     const double u2 = u * u;
     return u * (-1.0 / 3.0 + u2 / 30.0 - u2 * u2 / 840.0);
   }
@@ -65,7 +65,7 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
   const double tf = fma(C.tffac * B.invf, dv, S.tc);
   double w = 1.0, zt = 0.0;
-  const bool tap = B.f > C.ftap;
+  const bool tap = dlt_pos(C.ftap, B.f);
   if (tap) {
     const double span = C.fend - C.ftap;
     zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
@@ -155,13 +155,13 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
     const double2 G = cmul(K, E);
     const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
     double sm, spl, dsm, dspl;   // sinc(u1), sinc(u2) and their derivatives
-    if (B.a < kSincPolyA8) {
+    if (dlt_pos(B.a, kSincPolyA8)) {
       sinc_poly_d_n<4>(u1, &sm, &dsm);
       sinc_poly_d_n<4>(u2, &spl, &dspl);
-    } else if (B.a < kSincPolyA12) {
+    } else if (dlt_pos(B.a, kSincPolyA12)) {
       sinc_poly_d_n<6>(u1, &sm, &dsm);
       sinc_poly_d_n<6>(u2, &spl, &dspl);
-    } else if (B.a < kSincPolyA) {
+    } else if (dlt_pos(B.a, kSincPolyA)) {
       sinc_poly_d(u1, &sm, &dsm);
       sinc_poly_d(u2, &spl, &dspl);
     } else {
@@ -169,13 +169,14 @@ __device__ __forceinline__ void mode_bwd(const DetDev& D, const SampleCoef& S, c
       sincos_turns(B.aturn * kn, tab, &sak, &cak);
       const double s1 = B.sa * cak - B.ca * sak, s2u = B.sa * cak + B.ca * sak;
       const double c1u = B.ca * cak + B.sa * sak, c2u = B.ca * cak - B.sa * sak;
-      if (fabs(u1) >= 1e-3 && fabs(u2) >= 1e-3) {
+      const bool small1 = dlt_pos(fabs(u1), 1e-3), small2 = dlt_pos(fabs(u2), 1e-3);
+      if (!small1 && !small2) {
         const double rr = 1.0 / (u1 * u2);
         sm = s1 * u2 * rr;
         spl = s2u * u1 * rr;
       } else {
-        sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
-        spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2u / u2;
+        sm = small1 ? sinc_small(u1) : s1 / u1;
+        spl = small2 ? sinc_small(u2) : s2u / u2;
       }
       dsm = dsinc(u1, c1u, sm);
       dspl = dsinc(u2, c2u, spl);

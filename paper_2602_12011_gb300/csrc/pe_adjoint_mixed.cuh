@@ -111,7 +111,7 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
   const double dv = fma(iv5, dpol, fma(S.Q6 * v, 1.0 + lnv, S.Q5));
   const double tf = fma(C.tffac * B.invf, dv, S.tc);
   double w = 1.0, zt = 0.0;
-  const bool tap = B.f > C.ftap;
+  const bool tap = dlt_pos(C.ftap, B.f);
   if (tap) {
     const double span = C.fend - C.ftap;
     zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
@@ -198,7 +198,7 @@ __device__ __forceinline__ void mode_bwd_mixed(const DetDev& D, const SampleCoef
     const df akn = dfl_mul(W.a, kn);
     const df u1 = dfl_sub(W.a, akn), u2 = dfl_add(W.a, akn);
     df sm, spl, dsm, dspl;   // sinc(u1), sinc(u2) and their derivatives
-    if (B.a < kSincPolyA) {
+    if (dlt_pos(B.a, kSincPolyA)) {
       const df2 r1 = df_sinc_poly_d(u1), r2 = df_sinc_poly_d(u2);
       sm = r1.v;
       dsm = r1.d;

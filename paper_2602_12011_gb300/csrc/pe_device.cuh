@@ -405,7 +405,7 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   const double tf = fma(C.tffac * B.invf, dv, S.tc);            // Eq. eq_tf
   // amp v^p f^(-7/6) = (amp cm^p) f^(-7/6 + p/3), times the Planck taper inside it
   double amp = C.ampp * (C.p == 0 ? B.fm76 : (C.p == 1 ? D.fm56[B.b] : D.fm12[B.b]));
-  if (B.f > C.ftap) {
+  if (dlt_pos(C.ftap, B.f)) {
     const double span = C.fend - C.ftap;
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
     amp *= (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
@@ -484,13 +484,14 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
       double sak, cak;
       sincos_turns(B.aturn * kn, tab, &sak, &cak);
       const double s1 = B.sa * cak - B.ca * sak, s2 = B.sa * cak + B.ca * sak;
-      if (fabs(u1) >= 1e-3 && fabs(u2) >= 1e-3) {
+      const bool small1 = dlt_pos(fabs(u1), 1e-3), small2 = dlt_pos(fabs(u2), 1e-3);
+      if (!small1 && !small2) {
         const double rr = 1.0 / (u1 * u2);
         sm = s1 * u2 * rr;
         spl = s2 * u1 * rr;
       } else {
-        sm = (fabs(u1) < 1e-3) ? sinc_small(u1) : s1 / u1;
-        spl = (fabs(u2) < 1e-3) ? sinc_small(u2) : s2 / u2;
+        sm = small1 ? sinc_small(u1) : s1 / u1;
+        spl = small2 ? sinc_small(u2) : s2 / u2;
       }
     }
     smv[l] = sm;
@@ -519,7 +520,7 @@ __device__ __forceinline__ void load_bin(const DetDev& D, int b, double tc, BinI
   B.a2 = B.a * B.a;
   B.a2x2 = 2.0 * B.a2;
   B.hf = 0.5 * B.f;
-  B.sdeg = B.a < kSincPolyA8 ? 0 : (B.a < kSincPolyA12 ? 1 : (B.a < kSincPolyA ? 2 : 3));
+  B.sdeg = dlt_pos(B.a, kSincPolyA8) ? 0 : (dlt_pos(B.a, kSincPolyA12) ? 1 : (dlt_pos(B.a, kSincPolyA) ? 2 : 3));
   B.b = b;
   B.aturn = 0.5 * B.f * D.L;
   const double2 sc = D.sca[b];
@@ -539,7 +540,7 @@ __device__ __forceinline__ void bin_modes(const DetDev& D, const SampleCoef& S, 
   for (int md = 0; md < kNModes; ++md) {
     if (md == 3 && S.pair32) continue;
     const ModeCoef& C = S.md[md];
-    if (!C.active || !(B.f < C.fend)) continue;
+    if (!C.active || !dlt_pos(B.f, C.fend)) continue;
     mode_bin(D, S, C, B, a, tab, pc, (md == 0 && S.pair32) ? &S.md[3] : nullptr);
   }
 }
