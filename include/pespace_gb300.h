@@ -228,7 +228,7 @@ pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_ma
  *     % 64 == 0; out_loss_curve (host, nullable) receives the last minibatch loss of each epoch.
  *   pe_surrogate_set_node_source: 0 (default) the network's node values; 1 the plain generator's
  *     own node values (the same spline path without the network, for comparison).
- *   pe_surrogate_set_box: the training box (defaults 3e5-1e7 Msun, q <= 8, |chi| <= 0.99: where
+ *   pe_surrogate_set_box: the training box (defaults 1e5-1e7 Msun, q <= 8, |chi| <= 0.99: where
  *     the held-out mismatch of the trained network stays <= 1e-3).
  *   pe_surrogate_targets / pe_surrogate_predict: plain-generator / network node values
  *     [B][5][2][256] (fp32, device) for theta [B][11] (device).

@@ -48,6 +48,11 @@ constexpr double kFmin = 1e-4;                // lowest node frequency [Hz]
 constexpr double kLnFmin = -9.210340371976182;  // ln(kFmin), the nodes' origin in u = ln f
 constexpr float kLnFminHi = static_cast<float>(kLnFmin);   // as a double word
 constexpr float kLnFminLo = static_cast<float>(kLnFmin - static_cast<double>(kLnFminHi));
+constexpr float kFminHi = static_cast<float>(kFmin);       // kFmin as a double word
+constexpr float kFminLo = static_cast<float>(kFmin - static_cast<double>(kFminHi));
+constexpr double kInv2Pi = 0.5 / kPi;                      // 1/(2 pi) as a double word
+constexpr float kInv2PiHi = static_cast<float>(kInv2Pi);
+constexpr float kInv2PiLo = static_cast<float>(kInv2Pi - static_cast<double>(kInv2PiHi));
 
 // ---- features, targets ------------------------------------------------------------------------
 // Normalised inputs: the 11 parameters, each affinely scaled to order one (log10 for the mass).
@@ -102,6 +107,7 @@ __global__ void k_sur_prep(const double* theta, int B, unsigned mask, SampleCoef
   b.P[6] = b.Pd[6] = b.Pdd[6] = 0.0;
   b.P[7] = b.Pd[7] = b.Pdd[7] = 0.0;
   b.Q6 = 0.0;
+  b.Pdw[6] = b.Pdw[7] = b.Q6w = make_float2(0.f, 0.f);
   // the surrogate's per-bin amplitude is the Newtonian power law (2 pi M^2/D) sqrt(eta/3m) x^-7/4;
   // the mode factor |H_lm| travels with the transfer functions, so store amp / |H_lm| here
   for (int md = 0; md < kNModes; ++md) {
@@ -307,6 +313,58 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
   const double h = hs[(size_t)s * kNModes + md];
   const double2* tab = nv + ((size_t)s * kNModes + md) * kNodeTab;
   const double2 v0 = tab[0], iv0 = tab[1];
+  const float* y = Y + (size_t)s * kNout + (md * 2) * kNodes;
+  if constexpr (MIX) {
+    // The node phase, t_f, the orbit angle and the centre Doppler term in double words (relative
+    // error ~1e-14: ~1e-9 turn at the phase's 1e5 turns, far below the spline's own error); the
+    // residual's derivative in FP32 (it only corrects t_f); the link transfer functions in FP32.
+    df e3 = df_make(1.f, 0.f), ie3 = e3;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if ((j >> k) & 1) {
+        const double2 w = tab[2 + k];
+        e3 = dfl_mul(e3, df_from_bits(w.x));
+        ie3 = dfl_mul(ie3, df_from_bits(w.y));
+      }
+    const df f = dfl_mul(dfl_mul(dfl_mul(e3, e3), e3), df_make(kFminHi, kFminLo));
+    const df invf = dfl_mulf(dfl_mul(dfl_mul(ie3, ie3), ie3), 1.0f / kFminHi);   // 1/kFmin = 1e4, exact
+    const df v = dfl_mul(df_from_bits(v0.x), e3), iv = dfl_mul(df_from_bits(iv0.x), ie3);
+    const df lnv = dfl_add(df_from_bits(v0.y), dfl_mulf(df_from_bits(iv0.y), (float)j));
+    const SampleCoef& Sb = S0[s];
+    df poly = df_from_bits(Sb.P[7]), dpol = Sb.Pdw[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) {
+      poly = dfl_add(dfl_mul(poly, v), df_from_bits(Sb.P[k]));
+      dpol = dfl_add(dfl_mul(dpol, v), Sb.Pdw[k]);
+    }
+    const df iv2 = dfl_mul(iv, iv);
+    const df iv5 = dfl_mul(dfl_mul(iv2, iv2), iv);
+    const df q5 = df_from_bits(Sb.Q5), q6v = dfl_mul(Sb.Q6w, v);
+    const df D0 = dfl_add(dfl_mul(iv5, dpol), dfl_add(dfl_mul(q6v, dfl_add(df_make(1.f, 0.f), lnv)), q5));
+    const df psi0 = dfl_add(dfl_mul(iv5, poly), dfl_mul(lnv, dfl_add(q6v, q5)));
+    const float r = y[j];
+    float dr;
+    if (j == 0) dr = fmaf(-3.f, r, fmaf(4.f, y[1], -y[2]));
+    else if (j == kNodes - 1) dr = fmaf(3.f, r, fmaf(-4.f, y[kNodes - 2], y[kNodes - 3]));
+    else dr = y[j + 1] - y[j - 1];
+    const float drdu = dr * (0.5f / trunc_to_float(__double_as_longlong(h)));
+    const df inv2pi = df_make(kInv2PiHi, kInv2PiLo);
+    const df tf = dfl_add(Sa.tcw, dfl_mul(invf, dfl_add(dfl_mul(C.tffacw, D0), dfl_mulf(inv2pi, drdu))));
+    const cdf eo = df_cis_turns(dfl_add(dfl_mul(tf, D.ratew), D.alpha0w), D.sctw);
+    const df kxc = dfl_mul(D.Rw, dfl_add(dfl_mul(Sa.kw[0], eo.re), dfl_mul(Sa.kw[1], eo.im)));
+    const df ph = dfl_mul(dfl_add(dfl_mulf(psi0, 0.5f * mm), df_make(r, 0.f)), inv2pi);
+    q[0] = df_to(dfl_sub(dfl_sub(df_from_bits(C.ph0), ph), dfl_mul(f, kxc)));
+    float2 T[3];
+    node_links_f32(D, Sa, C, f.x, eo.re.x, eo.im.x, T);   // heliocentric (geocentric nodes are skipped)
+    const float ar = y[kNodes + j];
+    double* row0 = q - j;   // this system's row of quantity 0
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      reinterpret_cast<float*>(row0 + (1 + 2 * c) * kNodes)[j] = T[c].x * ar;
+      reinterpret_cast<float*>(row0 + (2 + 2 * c) * kNodes)[j] = T[c].y * ar;
+    }
+    return;
+  }
   double e3 = 1.0, ie3 = 1.0;   // e^{+-j h/3} from the binary digits of j
 #pragma unroll
   for (int k = 0; k < 8; ++k)
@@ -321,7 +379,6 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
   const double lnv = fma((double)j, iv0.y, v0.y);
   double D0;
   const double psi0 = psi_of(S0[s], v, lnv, &D0, iv0.x * ie3);
-  const float* y = Y + (size_t)s * kNout + (md * 2) * kNodes;
   const double r = y[j];
   const double amp_ratio = y[kNodes + j];
   // residual derivative in u = ln f by node differences (one-sided at the ends)
@@ -331,24 +388,6 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
   else drdu = y[j + 1] - y[j - 1];
   drdu *= 0.5 / h;
   const double tf = fma(invf, fma(C.tffac, D0, drdu * (0.5 / kPi)), Sa.tc);
-  if constexpr (MIX) {
-    double so, co;
-    sincos_turns(fma(tf, D.rate_t, D.alpha0_t), D.sct, &so, &co);
-    const double kxc = D.R * (Sa.k[0] * co + Sa.k[1] * so);
-    q[0] = C.ph0 - (0.5 * mm * psi0 + r) * (0.5 / kPi) - f * kxc;
-    if (D.orbit != 0) sincos_turns(tf * D.geo_rate_t, D.sct, &so, &co);
-    float2 T[3];
-    node_links_f32(D, Sa, C, trunc_to_float(__double_as_longlong(f)), trunc_to_float(__double_as_longlong(co)),
-                   trunc_to_float(__double_as_longlong(so)), T);
-    const float ar = y[kNodes + j];
-    double* row0 = q - j;   // this system's row of quantity 0
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      reinterpret_cast<float*>(row0 + (1 + 2 * c) * kNodes)[j] = T[c].x * ar;
-      reinterpret_cast<float*>(row0 + (2 + 2 * c) * kNodes)[j] = T[c].y * ar;
-    }
-    return;
-  }
   double xc[3], dl[3][3];
   orbit_offsets(D, tf, xc, dl, D.sct);
   const double kxc = Sa.k[0] * xc[0] + Sa.k[1] * xc[1] + Sa.k[2] * xc[2];
@@ -925,7 +964,7 @@ struct pe_surrogate_s {
   Layer L[4];
   float* mean = nullptr;
   float* stdv = nullptr;
-  pe::SurBox box{3e5, 1e7, 8.0, 0.99};
+  pe::SurBox box{1e5, 1e7, 8.0, 0.99};
   int node_source = 0;   // 0: the network; 1: the plain generator at the nodes (no network)
   int trained = 0;
   int adam_t = 0;

@@ -14,6 +14,7 @@ from tests import _helpers as H
 pytestmark = pytest.mark.gpu
 
 T22 = 2.0 ** 22
+BOX_MLO = 1e5   # the default training box: Mtot in [1e5, 1e7] Msun, q <= 8, |chi| <= 0.99
 
 
 @pytest.fixture(scope="module")
@@ -207,7 +208,7 @@ def test_heldout_mismatch_acceptance(Lb, lisa22, trained):
     import torch
     th = W.draw_prior(2048, 2606, T22)
     mm = trained.mismatch(lisa22, torch.tensor(th, device="cuda"), W.MODE_ALL).cpu().numpy()
-    inbox = (th[:, 0] >= 3e5) & (th[:, 1] <= 8.0)
+    inbox = (th[:, 0] >= BOX_MLO) & (th[:, 1] <= 8.0)
     assert inbox.mean() > 0.7
     assert np.all(mm[~inbox] == 0.0)                 # fallback samples are the plain signal
     frac = np.mean(mm[inbox] <= 1e-3)
@@ -222,11 +223,11 @@ def test_fallback_is_the_plain_path_bitwise(Lb, lisa22, trained, prec):
     flag = Lb.PE_PREC_MIXED if prec == "mixed" else 0
     th = W.draw_prior(64, 2607, T22)
     th[::2, 1] = 9.5                                   # outside the box (q > 8)
-    th[1::4, 0] = 2e5                                  # outside the box (light)
+    th[1::4, 2] = 0.995                                # outside the box (|chi_1| > 0.99)
     tt = torch.tensor(th, device="cuda")
     ll, used = trained.loglike([lisa22], tt, W.MODE_ALL | flag)
     ref = Lb.loglike([lisa22], th, W.MODE_ALL | flag)["logl"]
-    out = (th[:, 1] > 8.0) | (th[:, 0] < 3e5)
+    out = (th[:, 1] > 8.0) | (np.abs(th[:, 2]) > 0.99)
     assert np.array_equal(used.cpu().numpy(), (~out).astype(np.int32))
     assert np.array_equal(ll.cpu().numpy()[out], ref[out])
 
