@@ -609,7 +609,7 @@ def main():
         ms_p = e0.elapsed_time(e1)
         tho = W.draw_prior(2048, 2606, T)
         mm = srg.mismatch(gd, torch.tensor(tho, device="cuda"), mask64).cpu().numpy()
-        inbox = (tho[:, 0] >= 1e5) & (tho[:, 1] <= 8.0)   # the default training box
+        inbox = (tho[:, 0] >= 1e5) & (tho[:, 1] <= 10.0)   # the default box of the spline path
 
         def timed(fn):
             fn()

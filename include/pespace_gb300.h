@@ -228,8 +228,11 @@ pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_ma
  *     % 64 == 0; out_loss_curve (host, nullable) receives the last minibatch loss of each epoch.
  *   pe_surrogate_set_node_source: 0 (default) the network's node values; 1 the plain generator's
  *     own node values (the same spline path without the network, for comparison).
- *   pe_surrogate_set_box: the training box (defaults 1e5-1e7 Msun, q <= 8, |chi| <= 0.99: where
- *     the held-out mismatch of the trained network stays <= 1e-3).
+ *   pe_surrogate_set_box: the box of the node-spline path (defaults 1e5-1e7 Msun, q <= 10,
+ *     |chi| <= 0.99: the prior's range); samples outside it take the plain path.
+ *   pe_surrogate_set_network_qmax: the largest mass ratio whose node values come from the network
+ *     (default 8: where the held-out mismatch of the trained network stays <= 1e-3); in-box samples
+ *     above it take the plain generator's own node values on the same spline path. q_net >= 1.
  *   pe_surrogate_targets / pe_surrogate_predict: plain-generator / network node values
  *     [B][5][2][256] (fp32, device) for theta [B][11] (device).
  *   pe_surrogate_loglike_batch: log L per sample through the surrogate path (device pointers);
@@ -254,7 +257,8 @@ pe_status pe_tune_set(const pe_detector* dets, int ndet, int B, unsigned mode_ma
  *     l = 2, 1, 0: dH_l (256, fp32 cotangent of H_l), dZ_l (256, fp32) and its bf16 copy (256).
  *     For elementwise checks of each layer against its own inputs; x, dy, y, grads as above.
  *   pe_surrogate_save / pe_surrogate_load: versioned binary checkpoint (weights, Adam state,
- *     output standardisation, box, seed) with an FNV-1a checksum; PE_EINVAL on a bad file. */
+ *     output standardisation, box and network bound, seed) with an FNV-1a checksum; PE_EINVAL on a
+ *     bad file. */
 typedef struct pe_surrogate_s* pe_surrogate;
 pe_status pe_surrogate_create(uint64_t seed, pe_surrogate* out);
 pe_status pe_surrogate_destroy(pe_surrogate s);
@@ -262,6 +266,7 @@ pe_status pe_surrogate_train(pe_surrogate s, const double* theta_train_dev, int 
                              double lr, double* out_final_loss, float* out_loss_curve);
 pe_status pe_surrogate_set_box(pe_surrogate s, double mtot_lo, double mtot_hi, double q_max, double chi_max);
 pe_status pe_surrogate_set_node_source(pe_surrogate s, int source);
+pe_status pe_surrogate_set_network_qmax(pe_surrogate s, double q_net);
 pe_status pe_surrogate_targets(const double* theta_dev, int B, float* out_dev);
 pe_status pe_surrogate_predict(pe_surrogate s, const double* theta_dev, int B, float* out_dev);
 pe_status pe_surrogate_loglike_batch(pe_surrogate s, const pe_detector* dets, int ndet, const double* theta_dev, int B,

@@ -110,6 +110,8 @@ def load(path: str):
     L.pe_surrogate_set_box.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_double]
     L.pe_surrogate_set_node_source.argtypes = [_P, C.c_int]
     L.pe_surrogate_set_node_source.restype = C.c_int
+    L.pe_surrogate_set_network_qmax.argtypes = [_P, C.c_double]
+    L.pe_surrogate_set_network_qmax.restype = C.c_int
     L.pe_surrogate_targets.argtypes = [_P, C.c_int, _P]
     L.pe_surrogate_predict.argtypes = [_P, _P, C.c_int, _P]
     L.pe_surrogate_loglike_batch.argtypes = [_P, _P, C.c_int, _P, C.c_int, C.c_uint, _P, _P, _P]
@@ -499,6 +501,10 @@ class Surrogate:
 
     def set_box(self, mtot_lo: float, mtot_hi: float, q_max: float = 10.0, chi_max: float = 0.99):
         _check(lib().pe_surrogate_set_box(self.handle, float(mtot_lo), float(mtot_hi), float(q_max), float(chi_max)))
+
+    def set_network_qmax(self, q_net: float):
+        """Largest mass ratio whose node values come from the network (exact node values above)."""
+        _check(lib().pe_surrogate_set_network_qmax(self.handle, float(q_net)))
 
     def set_node_source(self, source: int):
         """0: network node values (default); 1: plain generator's node values (no network)."""

@@ -132,14 +132,17 @@ __device__ __forceinline__ double psi_of(const SampleCoef& S, double v, double l
   return fma(iv5, poly, lnv * fma(S.Q6, v, S.Q5));
 }
 
-// Plain-generator node values (raw): out[s][(md*2 + kind)*kNodes + j].
-__global__ void k_targets(const double* theta, int B, const SampleCoef* S, const SampleCoef* S0, float* out) {
+// Plain-generator node values (raw): out[s][(md*2 + kind)*kNodes + j], for the samples whose mass
+// ratio exceeds q_above (all of them for q_above < 1; the others' rows are left as they are).
+__global__ void k_targets(const double* theta, int B, const SampleCoef* S, const SampleCoef* S0, float* out,
+                          double q_above) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)B * kNModes * kNodes) return;
   const int j = (int)(i % kNodes);
   const int md = (int)((i / kNodes) % kNModes);
   const int s = (int)(i / ((long long)kNodes * kNModes));
   const double* t = theta + (size_t)s * PE_NPARAM;
+  if (!(t[1] > q_above)) return;
   const int mm = (md == 0) ? 2 : (md == 1) ? 1 : (md == 2) ? 3 : (md == 3) ? 2 : 4;
   const double M = t[0] * kMsunS;
   const double f = kFmin * exp(j * node_h(M, mm));
@@ -964,7 +967,7 @@ struct pe_surrogate_s {
   Layer L[4];
   float* mean = nullptr;
   float* stdv = nullptr;
-  pe::SurBox box{1e5, 1e7, 8.0, 0.99};
+  pe::SurBox box{1e5, 1e7, 10.0, 0.99, 8.0};
   int node_source = 0;   // 0: the network; 1: the plain generator at the nodes (no network)
   int trained = 0;
   int adam_t = 0;
@@ -1196,7 +1199,13 @@ pe_status pe_surrogate_set_box(pe_surrogate s, double mtot_lo, double mtot_hi, d
   if (!s) return sfail(PE_EINVAL, "pe_surrogate_set_box: NULL handle");
   if (!(mtot_lo > 0.0 && mtot_hi >= mtot_lo && q_max >= 1.0 && chi_max >= 0.0 && chi_max < 1.0))
     return sfail(PE_EINVAL, "pe_surrogate_set_box: bad box");
-  s->box = pe::SurBox{mtot_lo, mtot_hi, q_max, chi_max};
+  s->box = pe::SurBox{mtot_lo, mtot_hi, q_max, chi_max, s->box.qnet};
+  return PE_OK;
+}
+
+pe_status pe_surrogate_set_network_qmax(pe_surrogate s, double q_net) {
+  if (!s || !(q_net >= 1.0)) return sfail(PE_EINVAL, "pe_surrogate_set_network_qmax: bad arguments");
+  s->box.qnet = q_net;
   return PE_OK;
 }
 
@@ -1208,7 +1217,7 @@ pe_status pe_surrogate_targets(const double* theta_dev, int B, float* out_dev) {
   if (e == cudaSuccess) {
     pe::k_sur_prep<<<(B + 63) / 64, 64>>>(theta_dev, B, PE_MODE_ALL, S, S0);
     const long long n = (long long)B * pe::kNModes * pe::kNodes;
-    pe::k_targets<<<(unsigned)((n + 255) / 256), 256>>>(theta_dev, B, S, S0, out_dev);
+    pe::k_targets<<<(unsigned)((n + 255) / 256), 256>>>(theta_dev, B, S, S0, out_dev, 0.0);
     e = pe::launch_status();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -1416,11 +1425,15 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   if (e == cudaSuccess) {
     const long long n = (long long)B * pe::kNout;
     pe::k_sur_prep<<<(B + 63) / 64, 64, 0, st>>>(theta_dev, B, mode_mask, S, S0);
+    // node values: the network's, with the plain generator's own above the network's mass-ratio
+    // bound (or everywhere for node source 1)
+    const long long nt = (long long)B * pe::kNModes * pe::kNodes;
     if (s->node_source == 0) {
       pe::k_destd<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->Y, B, s->mean, s->stdv, Yd);
+      if (s->box.qnet < s->box.qmax)
+        pe::k_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(theta_dev, B, S, S0, Yd, s->box.qnet);
     } else {
-      const long long nt = (long long)B * pe::kNModes * pe::kNodes;
-      pe::k_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(theta_dev, B, S, S0, Yd);
+      pe::k_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(theta_dev, B, S, S0, Yd, 0.0);
     }
     pe::k_node_h<<<(B * pe::kNModes + 127) / 128, 128, 0, st>>>(theta_dev, B, hs, nv);
     const long long nn = (long long)nsys * pe::kNodes;
@@ -1599,7 +1612,7 @@ pe_status pe_surrogate_save(pe_surrogate s, const char* path) {
   std::vector<unsigned char> buf;
   auto put = [&](const void* p, size_t n) { buf.insert(buf.end(), (const unsigned char*)p, (const unsigned char*)p + n); };
   put("PESURR01", 8);
-  const uint32_t ver = 1, dims[5] = {pe::kNin, pe::kHid, pe::kHid, pe::kHid, pe::kNout};
+  const uint32_t ver = 2, dims[5] = {pe::kNin, pe::kHid, pe::kHid, pe::kHid, pe::kNout};   // 2: SurBox.qnet
   put(&ver, 4);
   put(dims, sizeof(dims));
   put(&s->box, sizeof(s->box));
@@ -1649,7 +1662,7 @@ pe_status pe_surrogate_load(pe_surrogate s, const char* path) {
   memcpy(&ver, buf.data() + o, 4); o += 4;
   memcpy(dims, buf.data() + o, sizeof(dims)); o += sizeof(dims);
   const uint32_t want[5] = {pe::kNin, pe::kHid, pe::kHid, pe::kHid, pe::kNout};
-  if (ver != 1 || memcmp(dims, want, sizeof(dims)) != 0) return sfail(PE_EINVAL, "pe_surrogate_load: version/shape mismatch");
+  if (ver != 2 || memcmp(dims, want, sizeof(dims)) != 0) return sfail(PE_EINVAL, "pe_surrogate_load: version/shape mismatch");
   memcpy(&s->box, buf.data() + o, sizeof(s->box)); o += sizeof(s->box);
   memcpy(&s->adam_t, buf.data() + o, 4); o += 4;
   memcpy(&s->seed, buf.data() + o, 8); o += 8;

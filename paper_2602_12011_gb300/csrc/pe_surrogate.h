@@ -9,6 +9,7 @@ struct SurBox {
   double mlo, mhi;   // total mass range [Msun]
   double qmax;       // largest mass ratio
   double chimax;     // largest |chi_i|
+  double qnet;       // largest mass ratio whose node values come from the network (exact above)
 };
 
 }  // namespace pe

@@ -14,7 +14,9 @@ from tests import _helpers as H
 pytestmark = pytest.mark.gpu
 
 T22 = 2.0 ** 22
-BOX_MLO = 1e5   # the default training box: Mtot in [1e5, 1e7] Msun, q <= 8, |chi| <= 0.99
+# the default box of the spline path: Mtot in [1e5, 1e7] Msun, q <= 10, |chi| <= 0.99 (the prior's
+# range), with the network's node values up to q = 8 and the plain generator's above
+BOX_MLO, BOX_QMAX, NET_QMAX = 1e5, 10.0, 8.0
 
 
 @pytest.fixture(scope="module")
@@ -208,7 +210,7 @@ def test_heldout_mismatch_acceptance(Lb, lisa22, trained):
     import torch
     th = W.draw_prior(2048, 2606, T22)
     mm = trained.mismatch(lisa22, torch.tensor(th, device="cuda"), W.MODE_ALL).cpu().numpy()
-    inbox = (th[:, 0] >= BOX_MLO) & (th[:, 1] <= 8.0)
+    inbox = (th[:, 0] >= BOX_MLO) & (th[:, 1] <= BOX_QMAX)
     assert inbox.mean() > 0.7
     assert np.all(mm[~inbox] == 0.0)                 # fallback samples are the plain signal
     frac = np.mean(mm[inbox] <= 1e-3)
@@ -222,14 +224,37 @@ def test_fallback_is_the_plain_path_bitwise(Lb, lisa22, trained, prec):
     import torch
     flag = Lb.PE_PREC_MIXED if prec == "mixed" else 0
     th = W.draw_prior(64, 2607, T22)
-    th[::2, 1] = 9.5                                   # outside the box (q > 8)
+    th[::2, 1] = 10.5                                  # outside the box (q > 10)
     th[1::4, 2] = 0.995                                # outside the box (|chi_1| > 0.99)
     tt = torch.tensor(th, device="cuda")
     ll, used = trained.loglike([lisa22], tt, W.MODE_ALL | flag)
     ref = Lb.loglike([lisa22], th, W.MODE_ALL | flag)["logl"]
-    out = (th[:, 1] > 8.0) | (np.abs(th[:, 2]) > 0.99)
+    out = (th[:, 1] > BOX_QMAX) | (np.abs(th[:, 2]) > 0.99)
     assert np.array_equal(used.cpu().numpy(), (~out).astype(np.int32))
     assert np.array_equal(ll.cpu().numpy()[out], ref[out])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_exact_node_values_above_the_network_bound(Lb, lisa22, trained, prec):
+    """In-box samples above the network's mass-ratio bound (q > 8) take the plain generator's own
+    node values on the spline path: their log L equals the no-network path's bit for bit, while
+    the samples below the bound differ from it (network node values)."""
+    import torch
+    flag = Lb.PE_PREC_MIXED if prec == "mixed" else 0
+    th = W.draw_prior(64, 2612, T22)
+    th[::2, 1] = np.linspace(8.2, 9.9, 32)             # above the network's bound
+    th[1::2, 1] = np.minimum(th[1::2, 1], 7.5)         # below it
+    tt = torch.tensor(th, device="cuda")
+    ll, used = trained.loglike([lisa22], tt, W.MODE_ALL | flag)
+    trained.set_node_source(1)
+    try:
+        ll_exact, _ = trained.loglike([lisa22], tt, W.MODE_ALL | flag)
+    finally:
+        trained.set_node_source(0)
+    ll, ll_exact = ll.cpu().numpy(), ll_exact.cpu().numpy()
+    assert np.all(used.cpu().numpy() == 1)
+    assert np.array_equal(ll[::2], ll_exact[::2])
+    assert np.all(ll[1::2] != ll_exact[1::2])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
