@@ -144,6 +144,8 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
   for (int i = 0; i < 3; ++i) { S.p[i] = cp * u[i] + sp * v[i]; S.q[i] = -(sp * u[i]) + cp * v[i]; }
   for (int i = 0; i < 3; ++i) S.kw[i] = to_dw(val(S.k[i]));
   for (int k = 0; k < 8; ++k) S.Pdw[k] = to_dw(val(S.Pd[k]));
+  for (int k = 0; k < 8; ++k) S.Pw[k] = to_dw(val(S.P[k]));
+  S.Q5w = to_dw(val(S.Q5));
   S.Q6w = to_dw(val(S.Q6));
   S.tcw = to_dw(val(S.tc));
   // modes: (2 pi M / m)^(1/3) = (2 pi M)^(1/3) m^(-1/3) and its log from one cube root and one
@@ -187,6 +189,7 @@ __device__ inline void sample_prep_t(const T* th, bool valid, unsigned mask, Sam
     C.Ppw = to_dw(val(C.Pp));
     C.Pcw = to_dw(val(C.Pc));
     C.tffacw = to_dw(val(C.tffac));
+    C.ph0w = to_dw(val(C.ph0));
     C.p = p;
     C.active = (valid && (mask & (1u << md)) && val(hmag) != 0.0) ? 1 : 0;
   }

@@ -54,6 +54,7 @@ struct ModeCoefT {
   float2 cmw;        // cm as a double word
   float2 ampw;       // amp times the sample's hsc as a double word
   float2 tffacw;     // tffac as a double word
+  float2 ph0w;       // ph0 as a double word
   int p;        // power of v in |H_lm|: 0 (22), 1 (21, 33), 2 (32, 44)
   int active;   // 1 if the mode is in the mask and its amplitude is non-zero
 };
@@ -71,6 +72,7 @@ struct SampleCoefT {
   float2 kw[3];         // k as double words
   float2 Pdw[8];        // Pd, Q6 and tc as double words (the mixed path's t_f)
   float2 Q6w, tcw;
+  float2 Pw[8], Q5w;    // P and Q5 as double words (the mixed surrogate's node phase)
   double hsc, ihsc;     // power of two near 1/amp of the (2,2) mode and its inverse: the mixed-
                         // precision path carries amplitudes times hsc, keeping them far from the
                         // FP32 range limits

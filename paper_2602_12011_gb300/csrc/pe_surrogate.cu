@@ -107,7 +107,7 @@ __global__ void k_sur_prep(const double* theta, int B, unsigned mask, SampleCoef
   b.P[6] = b.Pd[6] = b.Pdd[6] = 0.0;
   b.P[7] = b.Pd[7] = b.Pdd[7] = 0.0;
   b.Q6 = 0.0;
-  b.Pdw[6] = b.Pdw[7] = b.Q6w = make_float2(0.f, 0.f);
+  b.Pdw[6] = b.Pdw[7] = b.Pw[6] = b.Pw[7] = b.Q6w = make_float2(0.f, 0.f);
   // the surrogate's per-bin amplitude is the Newtonian power law (2 pi M^2/D) sqrt(eta/3m) x^-7/4;
   // the mode factor |H_lm| travels with the transfer functions, so store amp / |H_lm| here
   for (int md = 0; md < kNModes; ++md) {
@@ -296,7 +296,8 @@ __device__ __forceinline__ void node_links_f32(const DetDev& D, const SampleCoef
 // first half of their rows (k_spline's mixed path reads them so).
 template <bool MIX>
 __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleCoef* S0, const float* Y,
-                            const double* theta, SurBox bx, const double* hs, const double2* nv, double* nodes) {
+                            const double* theta, SurBox bx, const double* hs, const double2* nv,
+                            const float4* __restrict__ nvw, double* nodes) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)ds.ndet * B * kNModes * kNodes;
   if (i >= total) return;
@@ -321,28 +322,30 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
     // The node phase, t_f, the orbit angle and the centre Doppler term in double words (relative
     // error ~1e-14: ~1e-9 turn at the phase's 1e5 turns, far below the spline's own error); the
     // residual's derivative in FP32 (it only corrects t_f); the link transfer functions in FP32.
+    const float4* tw = nvw + ((size_t)s * kNModes + md) * kNodeTab;
     df e3 = df_make(1.f, 0.f), ie3 = e3;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       if ((j >> k) & 1) {
-        const double2 w = tab[2 + k];
-        e3 = dfl_mul(e3, df_from_bits(w.x));
-        ie3 = dfl_mul(ie3, df_from_bits(w.y));
+        const float4 w = tw[2 + k];
+        e3 = dfl_mul(e3, df_make(w.x, w.y));
+        ie3 = dfl_mul(ie3, df_make(w.z, w.w));
       }
+    const float4 t0 = tw[0], t1 = tw[1];   // (v, ln v), (1/v, h/3) at the first node
     const df f = dfl_mul(dfl_mul(dfl_mul(e3, e3), e3), df_make(kFminHi, kFminLo));
     const df invf = dfl_mulf(dfl_mul(dfl_mul(ie3, ie3), ie3), 1.0f / kFminHi);   // 1/kFmin = 1e4, exact
-    const df v = dfl_mul(df_from_bits(v0.x), e3), iv = dfl_mul(df_from_bits(iv0.x), ie3);
-    const df lnv = dfl_add(df_from_bits(v0.y), dfl_mulf(df_from_bits(iv0.y), (float)j));
+    const df v = dfl_mul(df_make(t0.x, t0.y), e3), iv = dfl_mul(df_make(t1.x, t1.y), ie3);
+    const df lnv = dfl_add(df_make(t0.z, t0.w), dfl_mulf(df_make(t1.z, t1.w), (float)j));
     const SampleCoef& Sb = S0[s];
-    df poly = df_from_bits(Sb.P[7]), dpol = Sb.Pdw[7];
+    df poly = Sb.Pw[7], dpol = Sb.Pdw[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) {
-      poly = dfl_add(dfl_mul(poly, v), df_from_bits(Sb.P[k]));
+      poly = dfl_add(dfl_mul(poly, v), Sb.Pw[k]);
       dpol = dfl_add(dfl_mul(dpol, v), Sb.Pdw[k]);
     }
     const df iv2 = dfl_mul(iv, iv);
     const df iv5 = dfl_mul(dfl_mul(iv2, iv2), iv);
-    const df q5 = df_from_bits(Sb.Q5), q6v = dfl_mul(Sb.Q6w, v);
+    const df q5 = Sb.Q5w, q6v = dfl_mul(Sb.Q6w, v);
     const df D0 = dfl_add(dfl_mul(iv5, dpol), dfl_add(dfl_mul(q6v, dfl_add(df_make(1.f, 0.f), lnv)), q5));
     const df psi0 = dfl_add(dfl_mul(iv5, poly), dfl_mul(lnv, dfl_add(q6v, q5)));
     const float r = y[j];
@@ -356,7 +359,7 @@ __global__ void k_sur_nodes(DetSet ds, int B, const SampleCoef* S, const SampleC
     const cdf eo = df_cis_turns(dfl_add(dfl_mul(tf, D.ratew), D.alpha0w), D.sctw);
     const df kxc = dfl_mul(D.Rw, dfl_add(dfl_mul(Sa.kw[0], eo.re), dfl_mul(Sa.kw[1], eo.im)));
     const df ph = dfl_mul(dfl_add(dfl_mulf(psi0, 0.5f * mm), df_make(r, 0.f)), inv2pi);
-    q[0] = df_to(dfl_sub(dfl_sub(df_from_bits(C.ph0), ph), dfl_mul(f, kxc)));
+    reinterpret_cast<df*>(q - j)[j] = dfl_sub(dfl_sub(C.ph0w, ph), dfl_mul(f, kxc));   // a double word
     float2 T[3];
     node_links_f32(D, Sa, C, f.x, eo.re.x, eo.im.x, T);   // heliocentric (geocentric nodes are skipped)
     const float ar = y[kNodes + j];
@@ -559,19 +562,110 @@ __device__ __forceinline__ void spline_solve_warp(const R* yy, const R* piv, R* 
   __syncwarp();
 }
 
-// mixed: the phase (quantity 0) is written as double words, (c0, c1) and (c2, c3) as two float4 per
-// interval in the same 32 bytes (the mixed-precision unit's form), and the transfer functions
-// (quantities 1..6, used only through their FP32 copies) are solved in FP32 and written to coef_t
-// alone.
+// spline_solve_warp in double words (the mixed path's phase spline): yy the node values, piv the
+// pivots as double words, M the result (padded, shared); k6 = 1/h^2. The same sweeps and scans,
+// every operation an unnormalised double-word one (~1e-14 relative: ~1e-9 turn at 1e5 turns).
+__device__ __forceinline__ df shfl_up_dw(df x, int off) {
+  return df_make(__shfl_up_sync(0xffffffffu, x.x, off), __shfl_up_sync(0xffffffffu, x.y, off));
+}
+__device__ __forceinline__ df shfl_down_dw(df x, int off) {
+  return df_make(__shfl_down_sync(0xffffffffu, x.x, off), __shfl_down_sync(0xffffffffu, x.y, off));
+}
+__device__ __forceinline__ df second_diff_dw(const df* yy, int j) {
+  return dfl_add(dfl_sub(yy[spad(j + 1)], df_scale2(yy[spad(j)], 2.f)), yy[spad(j - 1)]);
+}
+__device__ __forceinline__ void spline_solve_warp_dw(const df* yy, const df* piv, df* M, df k6, int lane) {
+  constexpr int N = kNodes, lo = 2, hi = N - 3, RW = 8;
+  const df zero = df_make(0.f, 0.f), one = df_make(1.f, 0.f);
+  const df M1 = dfl_mul(k6, second_diff_dw(yy, 1));
+  const df MN2 = dfl_mul(k6, second_diff_dw(yy, N - 2));
+  const int j0 = lo + RW * lane;
+  df rr[RW];
+  df A = one, Bc = zero;
+#pragma unroll
+  for (int k = 0; k < RW; ++k) {
+    const int j = j0 + k;
+    if (j <= hi) {
+      df r = dfl_mulf(dfl_mul(k6, second_diff_dw(yy, j)), 6.f);
+      if (j == lo) r = dfl_sub(r, M1);
+      if (j == hi) r = dfl_sub(r, MN2);
+      rr[k] = r;
+      const df c = piv[spad(j)];
+      A = df_neg(dfl_mul(c, A));
+      Bc = dfl_mul(c, dfl_sub(r, Bc));
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const df Ap = shfl_up_dw(A, off), Bp = shfl_up_dw(Bc, off);
+    if (lane >= off) {
+      Bc = dfl_add(dfl_mul(A, Bp), Bc);
+      A = dfl_mul(A, Ap);
+    }
+  }
+  df d = shfl_up_dw(Bc, 1);
+  if (lane == 0) d = zero;
+  df dd[RW];
+#pragma unroll
+  for (int k = 0; k < RW; ++k) {
+    const int j = j0 + k;
+    if (j <= hi) d = dfl_mul(dfl_sub(rr[k], d), piv[spad(j)]);
+    dd[k] = d;
+  }
+  A = one;
+  Bc = zero;
+#pragma unroll
+  for (int k = RW - 1; k >= 0; --k) {
+    const int j = j0 + k;
+    if (j <= hi) {
+      const df c = piv[spad(j)];
+      Bc = dfl_sub(dd[k], dfl_mul(c, Bc));
+      A = df_neg(dfl_mul(c, A));
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const df Ap = shfl_down_dw(A, off), Bp = shfl_down_dw(Bc, off);
+    if (lane + off < 32) {
+      Bc = dfl_add(dfl_mul(A, Bp), Bc);
+      A = dfl_mul(A, Ap);
+    }
+  }
+  df m = shfl_down_dw(Bc, 1);
+  if (lane == 31) m = zero;
+#pragma unroll
+  for (int k = RW - 1; k >= 0; --k) {
+    const int j = j0 + k;
+    if (j <= hi) {
+      m = dfl_sub(dd[k], dfl_mul(piv[spad(j)], m));
+      M[spad(j)] = m;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    M[spad(1)] = M1;
+    M[spad(N - 2)] = MN2;
+    M[spad(0)] = dfl_sub(df_scale2(M1, 2.f), M[spad(2)]);
+    M[spad(N - 1)] = dfl_sub(df_scale2(MN2, 2.f), M[spad(N - 3)]);
+  }
+  __syncwarp();
+}
+
+// mixed: the phase (quantity 0, double-word node values from k_sur_nodes<true>) is solved in double
+// words and written as (c0, c1) and (c2, c3), two float4 per interval in the same 32 bytes (the
+// mixed-precision unit's form), and the transfer functions (quantities 1..6, used only through
+// their FP32 copies) are solved in FP32 and written to coef_t alone.
 __global__ void __launch_bounds__(32 * kSplineWarps) k_spline(const double* nodes, long long nsys, const double* hs,
                                                                double* coef, float* coef_t, int mixed) {
   constexpr int N = kNodes;
   __shared__ double ys[kSplineWarps][kSplineNP], Ms[kSplineWarps][kSplineNP];
   __shared__ double piv[kSplineNP];   // the pivots in shared memory: the lanes read different rows at once
   __shared__ float pivf[kSplineNP];
+  __shared__ float2 pivw[kSplineNP];
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     piv[spad(j)] = kThomas.c[j];
     pivf[spad(j)] = (float)kThomas.c[j];
+    pivw[spad(j)] = to_dw(kThomas.c[j]);
   }
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -605,6 +699,26 @@ __global__ void __launch_bounds__(32 * kSplineWarps) k_spline(const double* node
     }
     return;
   }
+  if (mixed) {   // the phase, as double words (k_sur_nodes<true> wrote them), no FP64 arithmetic
+    df* yy = reinterpret_cast<df*>(ys[w]);
+    df* M = reinterpret_cast<df*>(Ms[w]);
+    const df* yw = reinterpret_cast<const df*>(y);
+    for (int j = lane; j < N; j += 32) yy[spad(j)] = yw[j];
+    __syncwarp();
+    const df hw = to_dw(h), ihw = to_dw(1.0 / h);
+    spline_solve_warp_dw(yy, pivw, M, dfl_mul(ihw, ihw), lane);
+    const df h6 = dfl_mulf(hw, 1.f / 6.f), ih6 = dfl_mulf(ihw, 1.f / 6.f);
+    for (int j = lane; j < N - 1; j += 32) {
+      const df y0 = yy[spad(j)], y1 = yy[spad(j + 1)], m0 = M[spad(j)], m1 = M[spad(j + 1)];
+      const df c1 = dfl_sub(dfl_mul(dfl_sub(y1, y0), ihw), dfl_mul(h6, dfl_add(df_scale2(m0, 2.f), m1)));
+      const df c2 = df_scale2(m0, 0.5f);
+      const df c3 = dfl_mul(dfl_sub(m1, m0), ih6);
+      float4* cw = reinterpret_cast<float4*>(cf + 4 * j);
+      cw[0] = make_float4(y0.x, y0.y, c1.x, c1.y);
+      cw[1] = make_float4(c2.x, c2.y, c3.x, c3.y);
+    }
+    return;
+  }
   double* yy = ys[w];
   double* M = Ms[w];
   for (int j = lane; j < N; j += 32) yy[spad(j)] = y[j];
@@ -617,14 +731,7 @@ __global__ void __launch_bounds__(32 * kSplineWarps) k_spline(const double* node
     const double c1 = (y1 - y0) * ih - h6 * (2.0 * m0 + m1);
     const double c2 = 0.5 * m0;
     const double c3 = (m1 - m0) * ih6;
-    if (q == 0 && mixed) {
-      const float2 w0 = to_dw(c0), w1 = to_dw(c1), w2 = to_dw(c2), w3 = to_dw(c3);
-      float4* cw = reinterpret_cast<float4*>(cf + 4 * j);
-      cw[0] = make_float4(w0.x, w0.y, w1.x, w1.y);
-      cw[1] = make_float4(w2.x, w2.y, w3.x, w3.y);
-    } else {
-      *reinterpret_cast<double4*>(cf + 4 * j) = make_double4(c0, c1, c2, c3);
-    }
+    *reinterpret_cast<double4*>(cf + 4 * j) = make_double4(c0, c1, c2, c3);
     if (ct) *reinterpret_cast<float4*>(ct + 4 * j) = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
   }
 }
@@ -632,7 +739,7 @@ __global__ void __launch_bounds__(32 * kSplineWarps) k_spline(const double* node
 // Per (sample, mode): the node spacing h in ln f, and the node table of k_sur_nodes: (v, ln v) and
 // (1/v, h/3) at the first node f = kFmin, then e^{+-2^k h/3} for k = 0..7 (each from exp, so a
 // node's product of at most 8 of them is within ~8 ulp of e^{+-j h/3}).
-__global__ void k_node_h(const double* theta, int B, double* hs, double2* nv) {
+__global__ void k_node_h(const double* theta, int B, double* hs, double2* nv, float4* nvw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * kNModes) return;
   const int s = i / kNModes, md = i % kNModes;
@@ -647,6 +754,12 @@ __global__ void k_node_h(const double* theta, int B, double* hs, double2* nv) {
   for (int k = 0; k < 8; ++k) {
     const double x = (double)(1 << k) * h * (1.0 / 3.0);
     t[2 + k] = make_double2(exp(x), exp(-x));
+  }
+  // the same entries as double words (hi, lo of .x, hi, lo of .y) for the mixed node kernel
+  float4* tw = nvw + (size_t)i * kNodeTab;
+  for (int k = 0; k < kNodeTab; ++k) {
+    const float2 a = to_dw(t[k].x), b = to_dw(t[k].y);
+    tw[k] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
@@ -1394,6 +1507,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   long long* off = nullptr;
   double *part = nullptr, *nodes = nullptr, *spl = nullptr, *hs = nullptr, *hs_sys = nullptr;
   double2* nv = nullptr;
+  float4* nvw = nullptr;
   float *Yd = nullptr, *splt = nullptr;
   const size_t nsys = (size_t)ndet * B * pe::kNModes;
   aalloc(&S, B);
@@ -1415,6 +1529,7 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
   aalloc(&hs, (size_t)B * pe::kNModes);
   aalloc(&hs_sys, nsys);
   aalloc(&nv, (size_t)B * pe::kNModes * pe::kNodeTab);
+  aalloc(&nvw, (size_t)B * pe::kNModes * pe::kNodeTab);
   aalloc(&Yd, (size_t)B * pe::kNout);
   if (e == cudaSuccess) {
     // MLP inference (BF16 tensor cores) -> de-standardised node values
@@ -1435,14 +1550,14 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     } else {
       pe::k_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(theta_dev, B, S, S0, Yd, 0.0);
     }
-    pe::k_node_h<<<(B * pe::kNModes + 127) / 128, 128, 0, st>>>(theta_dev, B, hs, nv);
+    pe::k_node_h<<<(B * pe::kNModes + 127) / 128, 128, 0, st>>>(theta_dev, B, hs, nv, nvw);
     const long long nn = (long long)nsys * pe::kNodes;
     if (mix)
       pe::k_sur_nodes<true><<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(ds, B, S, S0, Yd, theta_dev, s->box, hs,
-                                                                          nv, nodes);
+                                                                          nv, nvw, nodes);
     else
       pe::k_sur_nodes<false><<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(ds, B, S, S0, Yd, theta_dev, s->box, hs,
-                                                                           nv, nodes);
+                                                                           nv, nvw, nodes);
     e = pe::launch_status();
     // the spline kernel reads the node spacing per system (I, s, md): replicate per detector
     for (int I = 0; I < ndet && e == cudaSuccess; ++I)
