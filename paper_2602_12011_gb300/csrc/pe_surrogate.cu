@@ -862,113 +862,43 @@ __device__ __forceinline__ int find_pair_s(const long long* off, int P, long lon
 }
 
 // Persistent kernel over the same tile list as the FP64 k_loglike_fwd (kTileBins bins per tile,
-// one bin per thread, the same order of the sums). KIND 0 (FP64), mode 0: surrogate path (in-box
-// samples) or plain path (others), partials [tile][6] as the plain kernel; mode 1: mismatch sums
-// of the surrogate against the plain signal, partials [tile][6] = (<s|p>, <s|s>, <p|p>, 0, 0, 0).
-// KIND 1, the mixed-precision variant (mode 0): the in-box samples' tiles only (mode_bin_sur_mix, a
-// light unit with few registers and no tables in shared memory), A/E/T and the weighted products in
-// double words and each tile summed in double words (k_loglike_fwd's mixed tail), scaled back to
-// FP64 per tile. The out-of-box samples' tiles go to k_loglike_fwd itself (PE_PREC_MIXED).
-constexpr int kSurInboxCtas = 8;    // resident CTAs per SM asked of the in-box kernel (KIND 1)
-template <int KIND>
-__global__ void __launch_bounds__(kTileBins, KIND == 1 ? kSurInboxCtas : 3) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
-                                                       const SampleCoef* __restrict__ coefN,
-                                                       const double* __restrict__ theta, SurBox bx,
-                                                       const double* __restrict__ spl, const float* __restrict__ splt,
-                                                       const double* __restrict__ hs,
-                                                       const int* __restrict__ nend, const long long* __restrict__ off,
-                                                       const long long* __restrict__ offk, double* part, int mode) {
-  static_assert(KIND == 0 || KIND == 1, "KIND 0 (FP64) or 1 (mixed, in-box tiles)");
-  constexpr bool MIX = KIND != 0;
-  constexpr bool PLAIN = KIND != 1;                // runs the plain unit: needs the tables
-  __shared__ double red[6][kTileBins + kRedPad];   // block_sum6 staging (float2 rows when MIX)
-  __shared__ double pc[PLAIN ? kProj : 1];
+// one bin per thread, the same order of the sums), FP64 unit. mode 0: surrogate path (in-box
+// samples on heliocentric detectors) or plain path (the others), partials [tile][6] as the plain
+// kernel; mode 1: mismatch sums of the surrogate against the plain signal, partials [tile][6] =
+// (<s|p>, <s|s>, <p|p>, 0, 0, 0). The mixed-precision variant is k_sur_inbox (in-box tiles) plus
+// k_loglike_fwd itself (the other tiles).
+constexpr int kSurInboxCtas = 8;    // resident CTAs per SM asked of the in-box kernel (k_sur_inbox)
+// consecutive tiles (bins per thread) k_sur_inbox takes at a time; measured on 1024 in-box samples,
+// whole call: 1 tile 1.16 ms, 2 tiles 1.29 ms (64 registers, 8 CTAs per SM), 1.45 ms (6 CTAs per SM)
+constexpr int kSurInboxBins = 1;
+__global__ void __launch_bounds__(kTileBins, 3) k_sur_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+                                                        const SampleCoef* __restrict__ coefN,
+                                                        const double* __restrict__ theta, SurBox bx,
+                                                        const double* __restrict__ spl, const float* __restrict__ splt,
+                                                        const double* __restrict__ hs,
+                                                        const int* __restrict__ nend, const long long* __restrict__ off,
+                                                        double* part, int mode) {
+  __shared__ double red[6][kTileBins + kRedPad];   // block_sum6 staging
+  __shared__ double pc[kProj];
   __shared__ double ihs[kNModes];
-  __shared__ float ampf[kNModes];                  // a_lm hsc in FP32 (KIND 1)
-  __shared__ float2 hsw[kNModes];                  // node spacing h as a double word (KIND 1)
-  __shared__ float ihsf[kNModes];                  // 1/h in FP32 (KIND 1)
-  __shared__ double2 stab[PLAIN ? kSinTab : 1];
-  if (KIND == 0)
-    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  __shared__ double2 stab[kSinTab];
+  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
   __syncthreads();
-  // the tiles this kind walks: KIND 0 all of them (offk = off), KIND 1 those of the in-box pairs
-  // (offk: the scan of the pairs' tile counts with the others' set to 0); a tile's partial keeps its
-  // place in the full list, off[p] + its index in the pair
-  // KIND 1 takes a contiguous run of tiles per CTA, so that consecutive tiles of one pair reuse
-  // the pair's spline coefficients from L1; the heavier kinds stride over the list
   const int P = ds.ndet * B;
-  const long long total = offk[P];
-  long long tk0 = blockIdx.x, tk1 = total, step = gridDim.x;
-  if (KIND == 1) {
-    const long long chunk = (total + gridDim.x - 1) / gridDim.x;
-    tk0 = blockIdx.x * chunk;
-    tk1 = tk0 + chunk < total ? tk0 + chunk : total;
-    step = 1;
-  }
+  const long long total = off[P];
   int p = 0;
-  for (long long tk = tk0; tk < tk1; tk += step) {
-    p = find_pair_s(offk, P, tk, p);
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    p = find_pair_s(off, P, t, p);
     const int I = p / B, s = p - I * B;
-    const long long t = off[p] + (tk - offk[p]);
-    const bool sur = KIND == 0 ? sur_pair(theta + (size_t)s * PE_NPARAM, bx, ds.d[I].orbit) : KIND == 1;
-    const int b0 = int(tk - offk[p]) * kTileBins + threadIdx.x;
+    const bool sur = sur_pair(theta + (size_t)s * PE_NPARAM, bx, ds.d[I].orbit);
+    const int b0 = int(t - off[p]) * kTileBins + threadIdx.x;
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
-    if (PLAIN) proj_prologue(D, S, pc);
-    else __syncthreads();   // the previous tile's readers of the shared per-tile values are done
-    if (threadIdx.x < kNModes) {
-      ihs[threadIdx.x] = 1.0 / hs[(size_t)s * kNModes + threadIdx.x];
-      if (KIND == 1) {
-        const double hm = hs[(size_t)s * kNModes + threadIdx.x];
-        ampf[threadIdx.x] = (float)(coefN[s].md[threadIdx.x].amp * S.hsc);
-        hsw[threadIdx.x] = to_dw(hm);
-        ihsf[threadIdx.x] = (float)ihs[threadIdx.x];
-      }
-    }
+    proj_prologue(D, S, pc);
+    if (threadIdx.x < kNModes) ihs[threadIdx.x] = 1.0 / hs[(size_t)s * kNModes + threadIdx.x];
     __syncthreads();
-    if constexpr (MIX) {
-      df v[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) v[i] = df_make(0.f, 0.f);
-      const int b = b0;
-      if (b < ne) {
-        cdf x[3], o[3];
-        if constexpr (KIND == 1) {
-          // per bin in double words, no FP64 arithmetic: u0 = 3 (ln f / 3) - ln kFmin, and frac(f t_c)
-          // from the double-word product (relative error ~2^-46: ~1e-8 turn at f t_c ~ 4e5 turns)
-          const double f = D.f[b];
-          const df u0w = dfl_sub(dfl_mulf(df_from_bits(D.lnf3[b]), 3.f), df_make(kLnFminHi, kLnFminLo));
-          const float fm76 = D.fm76w[b].x;
-          const df ftc = dfl_mul(D.fw[b], S.tcw);
-          const df frcw = two_sum(__fsub_rn(ftc.x, rintf(ftc.x)), ftc.y);
-          float2 xs[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll   // the modes' coefficient loads overlap
-          for (int md = 0; md < kNModes; ++md) {
-            const ModeCoef& C = S.md[md];
-            if (!C.active || !dlt_pos(f, C.fend)) continue;
-            const size_t sys = ((size_t)I * B + s) * kNModes + md;
-            mode_bin_sur_mix(C, ampf[md], f, fm76, u0w, frcw, spl + sys * kQ * (kNodes - 1) * 4,
-                             splt + sys * (kQ - 1) * (kNodes - 1) * 4, hsw[md], ihsf[md], xs);
-          }
-#pragma unroll
-          for (int c = 0; c < 3; ++c) x[c] = cdf{df_make(xs[c].x, 0.f), df_make(xs[c].y, 0.f)};
-        }
-        aet_from_xyz_dw(x, o);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float4 g = D.dgw[c * D.nb + b];
-          v[c] = df_sub_s(df_mul(df_make(g.x, g.y), o[c].re), df_mul(df_make(g.z, g.w), o[c].im));
-          const df m2 = df_add_s(df_mul(o[c].re, o[c].re), df_mul(o[c].im, o[c].im));
-          v[3 + c] = df_mul(D.ggw[c * D.nb + b], m2);
-        }
-      }
-      df r;
-      if (block_sum6(v, [](df a, df b) { return dfl_add(a, b); }, reinterpret_cast<float2(*)[kTileBins + kRedPad]>(red), &r)) {
-        const double ih = S.ihsc;
-        part[t * 6 + threadIdx.x] = df_to(r) * (threadIdx.x < 3 ? D.dg_scale * ih : D.gg_scale * ih * ih);
-      }
-    } else {
+    {
       double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
       for (int b = b0; b < b0 + kTileBins && b < ne; b += kTileBins) {
@@ -1011,6 +941,109 @@ __global__ void __launch_bounds__(kTileBins, KIND == 1 ? kSurInboxCtas : 3) k_su
       double a;
       if (block_sum6(v, [](double x, double y) { return x + y; }, red, &a)) part[t * 6 + threadIdx.x] = a;
     }
+  }
+}
+
+// The mixed-precision surrogate's in-box tiles (mode 0): mode_bin_sur_mix per (mode, bin), A/E/T
+// and the weighted products in double words, each 128-bin tile summed in double words (the tail of
+// k_loglike_fwd's mixed path) and scaled back to FP64 into its own partial. A CTA walks a contiguous
+// run of the in-box tile list (offk), so that consecutive tiles of a pair reuse its spline
+// coefficients from L1, and takes NB consecutive tiles of one pair at a time: each thread then
+// carries NB independent bins through one mode loop (their coefficient loads and arithmetic
+// overlap), and each tile still gets its own partial in the same fixed order.
+template <int NB>
+__global__ void __launch_bounds__(kTileBins, kSurInboxCtas) k_sur_inbox(DetSet ds, int B,
+                                                                     const SampleCoef* __restrict__ coef,
+                                                                     const SampleCoef* __restrict__ coefN,
+                                                                     const double* __restrict__ spl,
+                                                                     const float* __restrict__ splt,
+                                                                     const double* __restrict__ hs,
+                                                                     const int* __restrict__ nend,
+                                                                     const long long* __restrict__ off,
+                                                                     const long long* __restrict__ offk, double* part) {
+  __shared__ float2 red[6][kTileBins + kRedPad];   // block_sum6 staging
+  __shared__ float ampf[kNModes];                  // a_lm hsc in FP32
+  __shared__ float2 hsw[kNModes];                  // node spacing h as a double word
+  __shared__ float ihsf[kNModes];                  // 1/h in FP32
+  const int P = ds.ndet * B;
+  const long long total = offk[P];
+  const long long chunk = (total + gridDim.x - 1) / gridDim.x;
+  const long long tk0 = blockIdx.x * chunk;
+  const long long tk1 = tk0 + chunk < total ? tk0 + chunk : total;
+  int p = 0;
+  for (long long tk = tk0; tk < tk1;) {
+    p = find_pair_s(offk, P, tk, p);
+    const long long tend = offk[p + 1] < tk1 ? offk[p + 1] : tk1;   // this pair's tiles in the run
+    const int nt = (NB == 2 && tk + 1 < tend) ? 2 : 1;                // uniform over the CTA
+    const int I = p / B, s = p - I * B;
+    const int ne = nend[p];
+    const DetDev& D = ds.d[I];
+    const SampleCoef& S = coef[s];
+    __syncthreads();   // the previous tiles' readers of the shared per-tile values are done
+    if (threadIdx.x < kNModes) {
+      const double hm = hs[(size_t)s * kNModes + threadIdx.x];
+      ampf[threadIdx.x] = (float)(coefN[s].md[threadIdx.x].amp * S.hsc);
+      hsw[threadIdx.x] = to_dw(hm);
+      ihsf[threadIdx.x] = (float)(1.0 / hm);
+    }
+    __syncthreads();
+    // per bin in double words, no FP64 arithmetic: u0 = 3 (ln f / 3) - ln kFmin, and frac(f t_c)
+    // from the double-word product (relative error ~2^-46: ~1e-8 turn at f t_c ~ 4e5 turns)
+    int bb[NB];
+    double f[NB];
+    df u0w[NB], frcw[NB];
+    float fm76[NB];
+    float2 xs[NB][3];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      bb[k] = int(tk - offk[p] + k) * kTileBins + threadIdx.x;
+      const int b = (k < nt && bb[k] < ne) ? bb[k] : 0;
+      f[k] = (k < nt && bb[k] < ne) ? D.f[b] : 0.0;   // 0 keeps an absent bin out of every mode
+      u0w[k] = dfl_sub(dfl_mulf(df_from_bits(D.lnf3[b]), 3.f), df_make(kLnFminHi, kLnFminLo));
+      fm76[k] = D.fm76w[b].x;
+      const df ftc = dfl_mul(D.fw[b], S.tcw);
+      frcw[k] = two_sum(__fsub_rn(ftc.x, rintf(ftc.x)), ftc.y);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xs[k][c] = make_float2(0.f, 0.f);
+    }
+#pragma unroll   // the modes' (and the bins') coefficient loads overlap
+    for (int md = 0; md < kNModes; ++md) {
+      const ModeCoef& C = S.md[md];
+      if (!C.active) continue;
+      const size_t sys = ((size_t)I * B + s) * kNModes + md;
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (dlt_pos(0.0, f[k]) && dlt_pos(f[k], C.fend))
+          mode_bin_sur_mix(C, ampf[md], f[k], fm76[k], u0w[k], frcw[k], spl + sys * kQ * (kNodes - 1) * 4,
+                           splt + sys * (kQ - 1) * (kNodes - 1) * 4, hsw[md], ihsf[md], xs[k]);
+    }
+    const double ih = S.ihsc;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      if (k >= nt) break;   // uniform
+      df v[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] = df_make(0.f, 0.f);
+      const int b = bb[k];
+      if (b < ne) {
+        cdf x[3], o[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[c] = cdf{df_make(xs[k][c].x, 0.f), df_make(xs[k][c].y, 0.f)};
+        aet_from_xyz_dw(x, o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float4 g = D.dgw[c * D.nb + b];
+          v[c] = df_sub_s(df_mul(df_make(g.x, g.y), o[c].re), df_mul(df_make(g.z, g.w), o[c].im));
+          const df m2 = df_add_s(df_mul(o[c].re, o[c].re), df_mul(o[c].im, o[c].im));
+          v[3 + c] = df_mul(D.ggw[c * D.nb + b], m2);
+        }
+      }
+      df r;
+      if (block_sum6(v, [](df a, df b) { return dfl_add(a, b); }, red, &r))
+        part[(off[p] + (tk - offk[p]) + k) * 6 + threadIdx.x] =
+            df_to(r) * (threadIdx.x < 3 ? D.dg_scale * ih : D.gg_scale * ih * ih);
+    }
+    tk += nt;
   }
 }
 
@@ -1591,8 +1624,8 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
     const long long g = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * 8));
     if (mix) {
       const long long g1 = std::max<long long>(1, std::min<long long>(max_tiles, (long long)nsm * pe::kSurInboxCtas));
-      pe::k_sur_fwd<1><<<(unsigned)g1, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
-                                                              offin, part, mode);
+      pe::k_sur_inbox<pe::kSurInboxBins><<<(unsigned)g1, pe::kTileBins, 0, st>>>(ds, B, S, S0, spl, splt, hs, nend,
+                                                                                off, offin, part);
       e = pe::launch_status();
       // fallback tiles: the mixed-precision forward kernel of pe_loglike_batch with its tuned (or
       // default) choice, over the fallback pairs' work items; it writes each sub-tile's partial at
@@ -1601,8 +1634,8 @@ static pe_status sur_run(pe_surrogate s, const pe_detector* dets, int ndet, cons
         e = pe::launch_loglike_fwd_variant(tcm.variant, pe::kPrecMixed, ds, B, S, nend, off, offout, tcm.subtiles,
                                            part, pe::grid_for(tcm, max_tiles), st);
     } else {
-      pe::k_sur_fwd<0><<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
-                                                              off, part, mode);
+      pe::k_sur_fwd<<<(unsigned)g, pe::kTileBins, 0, st>>>(ds, B, S, S0, theta_dev, s->box, spl, splt, hs, nend, off,
+                                                           part, mode);
       e = pe::launch_status();
     }
   }
