@@ -1,0 +1,435 @@
+// pe_adjoint_tape.cuh -- FP64 gradient (row G1, arXiv:2602.12011 Sec. 2.2-2.3) of one (sample,
+// mode, bin) unit with a tape: the forward pass evaluates the unit exactly as the likelihood's
+// forward kernel does (mode_bin: the geometry as projections of the unnormalised link vectors on
+// the sample's frame, linear forms in the orbit basis) and also writes the values its reverse
+// sweep needs into a per-thread tape; the reverse sweep reads them back instead of recomputing the
+// mode.
+//
+// Why a tape pays on this part: the FP64 pipe retires two operations per SM cycle, 64 times fewer
+// than the FP32 pipe, so a value read back from memory costs a small fraction of its
+// recomputation. A 128-thread CTA's tape (its 128 bins, up to four unit modes: 148 KB) lives in
+// global memory, one region per resident CTA (~45 MB on 152 SMs, L2-resident), so that two CTAs
+// per SM keep two warps per scheduler issuing to the FP64 pipe; one CTA per SM with the tape in
+// shared memory left the pipe waiting on its own dependent instructions a quarter of the time.
+//
+// The reverse sweep pulls the bracket cotangents back to the projections' values, then
+//   (a) to the orbit basis, the orbit angle and t_f, through the forms' coefficients pc, and
+//   (b) to the coefficients pc themselves (linear in the sky frame k, p, q): the cotangent of
+//       coefficient m of a form is the sum over the tile's (bin, mode) entries of the form's
+//       cotangent times basis element m. That contraction runs once per tile over the tape, and
+//       its 42 sums are mapped to k, p, q through the offsets' forms Mo.
+#pragma once
+#include "pe_adjoint.cuh"
+
+namespace pe {
+
+// Tape of one unit mode: field f of thread i at tape[(slot * kTapeF + f) * kTileBins + i] of the
+// CTA's region (coalesced: consecutive threads, consecutive addresses).
+// Slots: (2,2) with a paired (3,2), or an unpaired (3,2) (the two exclude each other); (2,1);
+// (3,3); (4,4).
+constexpr int kTapeSlots = 4;
+enum : int {
+  kTco = 0, kTso = 1,     // cos, sin of the centre's orbit angle
+  kTob0 = 2, kTob1 = 3,   // orbit basis b0, b1 (b2, b3 = cos, sin heliocentric; 0 geocentric)
+  kTE = 4,                // e^{2 pi i (phase + theta_t)}, t = 0..2: (re, im) at kTE + 2 t
+  kTamp0 = 10,            // amplitude before the taper
+  kTw = 11,               // taper weight
+  kTdv = 12,              // v dPsi_PN/dv
+  kTL = 13,               // link l: kTL + 8 l + {0 kn, 1 np, 2 nq, 3 1/|n'|, 4 s-, 5 s+, 6 ds-/dkn, 7 ds+/dkn}
+  kTapeF = 37,
+  kTfb = 13,              // after the reverse sweep: the nine form cotangents (over the link fields)
+};
+constexpr int kTapeDoubles = kTapeSlots * kTapeF * kTileBins;   // per CTA
+// Tape slot of mode md (an unpaired (3,2) only occurs with (2,2) inactive).
+__device__ __forceinline__ int tape_slot(int md) { return md == 4 ? 3 : (md == 3 ? 0 : md); }
+// Pairs of the contraction: 30 link-form coefficients (forms 0..5 = k, p, q projections of links
+// 0 and 1; coefficients m = 0..4), 10 spacecraft-offset coefficients (forms 6, 7) and the two of
+// the centre's Doppler term k.x_c = pc55 cos + pc56 sin.
+constexpr int kTapeSums = 42;
+
+// q(x) with d sinc(u)/du = u q(u^2): the derivative of sinc_poly_x<DEG>'s series term by term,
+// q(x) = sum_{k=1..DEG} (-1)^k 2k x^(k-1) / (2k+1)!
+template <int DEG>
+__device__ __forceinline__ double dsinc_poly_x(double x) {
+  double q = DEG >= 8 ? 16.0 / 355687428096000.0 : (DEG >= 6 ? 12.0 / 6227020800.0 : 8.0 / 362880.0);
+  if (DEG >= 8) {
+    q = fma(q, x, -14.0 / 1307674368000.0);
+    q = fma(q, x, 12.0 / 6227020800.0);
+  }
+  if (DEG >= 6) {
+    q = fma(q, x, -10.0 / 39916800.0);
+    q = fma(q, x, 8.0 / 362880.0);
+  }
+  q = fma(q, x, -6.0 / 5040.0);
+  q = fma(q, x, 4.0 / 120.0);
+  return fma(q, x, -2.0 / 6.0);
+}
+
+// Forward pass of one unit: mode_bin's arithmetic (same operations, same order) plus the tape.
+// tp points at this thread's column of the mode's slot.
+__device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
+                                              XYZAcc& acc, const double2* __restrict__ tab,
+                                              const double* __restrict__ pc, const ModeCoef* C2, double* tp) {
+  const double v = C.cm * B.f13;
+  const double lnv = C.lncm + B.lnf3;
+  const double iv5 = C.icm5 * D.fm53[B.b];
+  double poly = S.P[7];
+  double dpol = S.Pd[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) {
+    poly = fma(poly, v, S.P[k]);
+    dpol = fma(dpol, v, S.Pd[k]);
+  }
+  const double q56 = fma(S.Q6, v, S.Q5);
+  const double psi_pn = fma(iv5, poly, lnv * q56);
+  const double dv = fma(iv5, dpol, fma(S.Q6 * v, lnv, q56));
+  const double tf = fma(C.tffac * B.invf, dv, S.tc);
+  const double amp0 = C.ampp * (C.p == 0 ? B.fm76 : (C.p == 1 ? D.fm56[B.b] : D.fm12[B.b]));
+  double w = 1.0;
+  if (dlt_pos(C.ftap, B.f)) {
+    const double span = C.fend - C.ftap;
+    const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
+    w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
+  }
+  const double amp = amp0 * w;
+  double co, so, ob[4];
+  orbit_basis(D, tf, tab, &co, &so, ob);
+  const double kxc = fma(pc[55], co, pc[56] * so);
+  const double ph = fma(-C.mfac, psi_pn, C.ph0 - B.frc) - B.f * kxc;
+  const double phr = ph - rint(ph);
+  double2 Ap = make_double2(amp * C.Pp, 0.0), Ac = make_double2(amp * C.Pc2, 0.0);
+  if (C2) {
+    const double v2 = v * v;
+    const double kr = S.k32.x * v2, ki = S.k32.y * v2;
+    Ap = make_double2(amp * fma(kr, C2->Pp, C.Pp), amp * (ki * C2->Pp));
+    Ac = make_double2(amp * fma(kr, C2->Pc2, C.Pc2), amp * (ki * C2->Pc2));
+  }
+  double2 E[3];
+  {
+    const double e0 = B.hf * dot5(pc + 45, ob), e1 = B.hf * dot5(pc + 50, ob);
+    sincos_turns_r(phr + e0, tab, &E[0].y, &E[0].x);
+    sincos_turns_r(phr + e1, tab, &E[1].y, &E[1].x);
+    sincos_turns_r(phr - (e0 + e1), tab, &E[2].y, &E[2].x);
+  }
+  tp[kTco * kTileBins] = co;
+  tp[kTso * kTileBins] = so;
+  tp[kTob0 * kTileBins] = ob[0];
+  tp[kTob1 * kTileBins] = ob[1];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    tp[(kTE + 2 * t) * kTileBins] = E[t].x;
+    tp[(kTE + 2 * t + 1) * kTileBins] = E[t].y;
+  }
+  tp[kTamp0 * kTileBins] = amp0;
+  tp[kTw * kTileBins] = w;
+  tp[kTdv * kTileBins] = dv;
+  double knr[3], npr[3], nqr[3];
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    knr[l] = dot5(pc + 15 * l, ob);
+    npr[l] = dot5(pc + 15 * l + 5, ob);
+    nqr[l] = dot5(pc + 15 * l + 10, ob);
+  }
+  knr[2] = -(knr[0] + knr[1]);
+  npr[2] = -(npr[0] + npr[1]);
+  nqr[2] = -(nqr[0] + nqr[1]);
+  double2 G[3];
+  double smv[3], spv[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const int t = (l + 2) % 3;
+    const double inv = rsqrt(fma(knr[l], knr[l], fma(npr[l], npr[l], nqr[l] * nqr[l])));
+    const double kn = knr[l] * inv;
+    const double np = npr[l] * inv, nq = nqr[l] * inv;
+    const double Fp = np * np - nq * nq, Fch = np * nq;
+    const double2 gam = C2 ? make_double2(fma(Ap.x, Fp, -Ac.y * Fch), fma(Ap.y, Fp, Ac.x * Fch))
+                           : make_double2(Ap.x * Fp, Ac.x * Fch);
+    G[l] = cmul(gam, E[t]);
+    // sincs and their derivatives in kn: u1 = a (1 - kn), u2 = a (1 + kn), so
+    // d s-/dkn = -a sinc'(u1) = (a^2 kn - a^2) q(u1^2) and d s+/dkn = (a^2 kn + a^2) q(u2^2) on the
+    // polynomial branch
+    double sm, spl, dsm, dspl;
+    if (B.sdeg < 3) {
+      const double x1 = fma(kn, fma(B.a2, kn, -B.a2x2), B.a2), x2 = fma(kn, fma(B.a2, kn, B.a2x2), B.a2);
+      const double w1 = fma(B.a2, kn, -B.a2), w2 = fma(B.a2, kn, B.a2);
+      if (B.sdeg == 0) {
+        sm = sinc_poly_x<4>(x1);
+        spl = sinc_poly_x<4>(x2);
+        dsm = w1 * dsinc_poly_x<4>(x1);
+        dspl = w2 * dsinc_poly_x<4>(x2);
+      } else if (B.sdeg == 1) {
+        sm = sinc_poly_x<6>(x1);
+        spl = sinc_poly_x<6>(x2);
+        dsm = w1 * dsinc_poly_x<6>(x1);
+        dspl = w2 * dsinc_poly_x<6>(x2);
+      } else {
+        sm = sinc_poly_x<8>(x1);
+        spl = sinc_poly_x<8>(x2);
+        dsm = w1 * dsinc_poly_x<8>(x1);
+        dspl = w2 * dsinc_poly_x<8>(x2);
+      }
+    } else {
+      const double u1 = B.a * (1.0 - kn), u2 = B.a * (1.0 + kn);
+      double sak, cak;
+      sincos_turns(B.aturn * kn, tab, &sak, &cak);
+      const double s1 = B.sa * cak - B.ca * sak, s2 = B.sa * cak + B.ca * sak;
+      const double c1u = B.ca * cak + B.sa * sak, c2u = B.ca * cak - B.sa * sak;
+      const bool small1 = dlt_pos(fabs(u1), 1e-3), small2 = dlt_pos(fabs(u2), 1e-3);
+      if (!small1 && !small2) {
+        const double rr = 1.0 / (u1 * u2);
+        sm = s1 * u2 * rr;
+        spl = s2 * u1 * rr;
+      } else {
+        sm = small1 ? sinc_small(u1) : s1 / u1;
+        spl = small2 ? sinc_small(u2) : s2 / u2;
+      }
+      dsm = -B.a * dsinc(u1, c1u, sm);
+      dspl = B.a * dsinc(u2, c2u, spl);
+    }
+    smv[l] = sm;
+    spv[l] = spl;
+    double* tl = tp + (kTL + 8 * l) * kTileBins;
+    tl[0] = kn;
+    tl[kTileBins] = np;
+    tl[2 * kTileBins] = nq;
+    tl[3 * kTileBins] = inv;
+    tl[4 * kTileBins] = sm;
+    tl[5 * kTileBins] = spl;
+    tl[6 * kTileBins] = dsm;
+    tl[7 * kTileBins] = dspl;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lp = (c + 2) % 3, lu = c;
+    acc.P[c].x = fma(G[lp].x, spv[lp], fma(-G[lu].x, smv[lu], acc.P[c].x));
+    acc.P[c].y = fma(G[lp].y, spv[lp], fma(-G[lu].y, smv[lu], acc.P[c].y));
+    acc.Q[c].x = fma(G[lp].x, smv[lp], fma(-G[lu].x, spv[lu], acc.Q[c].x));
+    acc.Q[c].y = fma(G[lp].y, smv[lp], fma(-G[lu].y, spv[lu], acc.Q[c].y));
+  }
+}
+
+// Reverse sweep of one unit from its tape. sX, sY, sZ: cotangents of the bin's brackets X', Y',
+// Z'. Accumulates the theta components reached per unit (Mtot, q, chi1, chi2, dL, iota, phi_c,
+// t_c) into g and writes the nine form cotangents to the slot's kTfb fields: links 0 and 1's
+// (k, p, q) projections, the two spacecraft-offset phases and the centre's Doppler term.
+__device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef& S, const SampleGrad& SG, int md,
+                                              const BinIn& B, double2 sX, double2 sY, double2 sZ, GradAcc& g,
+                                              const double* __restrict__ pc, double* tp, int md2) {
+  const ModeCoef& C = S.md[md];
+  const ModeGrad& CG = SG.md[md];
+  const double v = C.cm * B.f13;
+  const double iv = C.icm * B.fm13;
+  const double lnv = C.lncm + B.lnf3;
+  const double iv5 = C.icm5 * D.fm53[B.b];
+  const double amp0 = tp[kTamp0 * kTileBins], w = tp[kTw * kTileBins];
+  const double amp = amp0 * w;
+  // polarisation weights without the amplitude: ap = Pp + kappa Pp', ac = 2 Pc + kappa 2 Pc'
+  double2 kap = make_double2(0.0, 0.0);
+  double Pp2 = 0.0, Pc22 = 0.0;
+  if (md2 >= 0) {
+    kap = make_double2(S.k32.x * v * v, S.k32.y * v * v);
+    Pp2 = S.md[md2].Pp;
+    Pc22 = S.md[md2].Pc2;
+  }
+  const double2 ap = make_double2(fma(kap.x, Pp2, C.Pp), kap.y * Pp2);
+  const double2 ac = make_double2(fma(kap.x, Pc22, C.Pc2), kap.y * Pc22);
+  const double2 Ap = make_double2(amp * ap.x, amp * ap.y), Ac = make_double2(amp * ac.x, amp * ac.y);
+  double2 Apb = make_double2(0.0, 0.0), Acb = make_double2(0.0, 0.0);
+  double thb[3];                    // cotangents of the spacecraft angles 2 pi (phase + theta_t)
+  double krb[3], prb[3], qrb[3];    // cotangents of the unnormalised projections, per link
+  // seeds: pair 0 = (1,2): X' has -G U, Y' has +G V; pair 1 = (2,3): Y' -G U, Z' +G V;
+  //        pair 2 = (3,1): Z' -G U, X' +G V.
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const int t = (l + 2) % 3;
+    double2 Su, Sv;
+    if (l == 0) { Su = make_double2(-sX.x, -sX.y); Sv = sY; }
+    else if (l == 1) { Su = make_double2(-sY.x, -sY.y); Sv = sZ; }
+    else { Su = make_double2(-sZ.x, -sZ.y); Sv = sX; }
+    const double* tl = tp + (kTL + 8 * l) * kTileBins;
+    const double kn = tl[0], np = tl[kTileBins], nq = tl[2 * kTileBins], inv = tl[3 * kTileBins];
+    const double sm = tl[4 * kTileBins], spl = tl[5 * kTileBins];
+    const double dsm = tl[6 * kTileBins], dspl = tl[7 * kTileBins];
+    const double2 E = make_double2(tp[(kTE + 2 * t) * kTileBins], tp[(kTE + 2 * t + 1) * kTileBins]);
+    const double Fp = np * np - nq * nq, Fch = np * nq;
+    const double2 gam = make_double2(fma(Ap.x, Fp, -Ac.y * Fch), fma(Ap.y, Fp, Ac.x * Fch));
+    const double2 G = cmul(gam, E);
+    const double2 U = make_double2(fma(B.z.x, spl, sm), B.z.y * spl);
+    const double2 V = make_double2(fma(B.z.x, sm, spl), B.z.y * sm);
+    const double2 Gb = cadd(cconjmul(Su, U), cconjmul(Sv, V));
+    const double2 Ub = cconjmul(Su, G);
+    const double2 Vb = cconjmul(Sv, G);
+    const double smb = Ub.x + Vb.x * B.z.x + Vb.y * B.z.y;
+    const double splb = Ub.x * B.z.x + Ub.y * B.z.y + Vb.x;
+    const double knb = fma(smb, dsm, splb * dspl);
+    const double2 gamb = cconjmul(Gb, E);
+    const double2 Eb = cconjmul(Gb, gam);
+    thb[t] = E.x * Eb.y - E.y * Eb.x;
+    // gam = Fp Ap + i Fch Ac
+    Apb = make_double2(fma(gamb.x, Fp, Apb.x), fma(gamb.y, Fp, Apb.y));
+    Acb = make_double2(fma(gamb.y, Fch, Acb.x), fma(-gamb.x, Fch, Acb.y));
+    const double Fpb = fma(gamb.x, Ap.x, gamb.y * Ap.y), Fchb = fma(gamb.y, Ac.x, -gamb.x * Ac.y);
+    const double npb = fma(2.0 * np, Fpb, nq * Fchb);
+    const double nqb = fma(-2.0 * nq, Fpb, np * Fchb);
+    // (kn, np, nq) = (knr, npr, nqr) / |n'|
+    const double dot = fma(knb, kn, fma(npb, np, nqb * nq));
+    krb[l] = inv * fma(-kn, dot, knb);
+    prb[l] = inv * fma(-np, dot, npb);
+    qrb[l] = inv * fma(-nq, dot, nqb);
+  }
+  // link 2's projections are minus the sum of links 0 and 1's
+  double fb[9];
+  fb[0] = krb[0] - krb[2]; fb[1] = prb[0] - prb[2]; fb[2] = qrb[0] - qrb[2];
+  fb[3] = krb[1] - krb[2]; fb[4] = prb[1] - prb[2]; fb[5] = qrb[1] - qrb[2];
+  // spacecraft angles 2 pi (phr + e_t), e_2 = -(e_0 + e_1), e_t = (f/2) (form 6 + t)
+  const double phb = 2.0 * kPi * (thb[0] + thb[1] + thb[2]);   // cotangent of the phase (turns)
+  fb[6] = kPi * B.f * (thb[0] - thb[2]);
+  fb[7] = kPi * B.f * (thb[1] - thb[2]);
+  const double kxcb = -B.f * phb;
+  fb[8] = kxcb;
+  // orbit basis through the forms' coefficients
+  double obb[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    double a = fb[7] * pc[50 + m];
+    a = fma(fb[6], pc[45 + m], a);
+#pragma unroll
+    for (int f = 5; f >= 0; --f) a = fma(fb[f], pc[5 * f + m], a);
+    obb[m] = a;
+  }
+  const double co = tp[kTco * kTileBins], so = tp[kTso * kTileBins];
+  double tfb;
+  if (D.orbit == 0) {
+    // b = (cos 2a, sin 2a, cos a, sin a)
+    const double cob = fma(2.0 * co, obb[0], fma(2.0 * so, obb[1], fma(kxcb, pc[55], obb[2])));
+    const double sob = fma(-2.0 * so, obb[0], fma(2.0 * co, obb[1], fma(kxcb, pc[56], obb[3])));
+    tfb = kPi * D.rate_ht * (co * sob - so * cob);
+  } else {
+    // b = (cos phi_0, sin phi_0, 0, 0); the centre keeps its heliocentric angle
+    const double c0 = tp[kTob0 * kTileBins], s0 = tp[kTob1 * kTileBins];
+    const double cob = kxcb * pc[55], sob = kxcb * pc[56];
+    tfb = kPi * D.geo_rate_ht * (c0 * obb[1] - s0 * obb[0]) + kPi * D.rate_ht * (co * sob - so * cob);
+  }
+#pragma unroll
+  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = fb[f];
+  // ---------------- mode level
+  g.ph = fma(phb, 2.0 * C.mfac, g.ph);          // d ph0/d phi_c = m/(2 pi)
+  g.tc = fma(-B.f, phb, g.tc);                   // frac(f t_c)
+  const double psib = -C.mfac * phb;
+  g.tc += tfb;                                   // t_f = t_c + (m/(12 pi f)) D(v)
+  const double Db = tfb * C.tffac * B.invf;
+  double vb = 0.0;
+  if (dlt_pos(0.0, amp)) {
+    const double ampb = fma(Apb.x, ap.x, fma(Apb.y, ap.y, fma(Acb.x, ac.x, Acb.y * ac.y)));
+    const double lnAb = ampb * amp;
+    g.M = fma(lnAb, CG.dlnA_dM, g.M);
+    g.q = fma(lnAb, CG.dlnA_dq, g.q);
+    g.dL = fma(lnAb, SG.dlnA_ddL, g.dL);
+    vb = lnAb * double(C.p) * iv;
+    if (dlt_pos(C.ftap, B.f)) {
+      const double wb = ampb * amp0;
+      const double zb = -wb * w * (1.0 - w);
+      const double fe = C.fend, ft = C.ftap, A = fe - ft;
+      const double dz = 0.1 / (fe - B.f) - A / ((fe - B.f) * (fe - B.f)) - 0.1 / (B.f - ft) -
+                        0.9 * A / ((B.f - ft) * (B.f - ft));
+      g.M = fma(zb * dz, CG.dfend_dM, g.M);
+    }
+  }
+  double ddpol = S.Pdd[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) ddpol = fma(ddpol, v, S.Pdd[k]);
+  // Psi_PN(v), D(v): dPsi/dv = D/v, dD/dv = v^-5 ddpol / v + Q6 (2 + ln v)
+  const double dv = tp[kTdv * kTileBins];
+  vb += psib * dv * iv + Db * (iv5 * ddpol * iv + S.Q6 * (2.0 + lnv));
+  g.M = fma(vb * B.f13, CG.dcm_dM, g.M);
+  double pq = SG.dP_dq[7], dq = SG.dPd_dq[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) {
+    pq = fma(pq, v, SG.dP_dq[k]);
+    dq = fma(dq, v, SG.dPd_dq[k]);
+  }
+  const double psiq = fma(iv5, pq, lnv * fma(SG.dQ6_dq, v, SG.dQ5_dq));
+  const double Dq = fma(iv5, dq, fma(SG.dQ6_dq * v, 1.0 + lnv, SG.dQ5_dq));
+  g.q += psib * psiq + Db * Dq;
+  const double iv2 = iv * iv;
+  g.c1 += psib * (SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv) - Db * (2.0 * SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv);
+  g.c2 += psib * (SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv) - Db * (2.0 * SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv);
+  // polarisation weights: cotangents of ap, ac are amp Apb, amp Acb; ac carries 2 Pc
+  const double2 apb = make_double2(amp * Apb.x, amp * Apb.y), acb = make_double2(amp * Acb.x, amp * Acb.y);
+  g.io += apb.x * CG.dPp_di + 2.0 * acb.x * CG.dPc_di;
+  if (md2 >= 0) {
+    const ModeGrad& CG2 = SG.md[md2];
+    g.io += (apb.x * kap.x + apb.y * kap.y) * CG2.dPp_di + 2.0 * (acb.x * kap.x + acb.y * kap.y) * CG2.dPc_di;
+    const double2 kb = make_double2(apb.x * Pp2 + acb.x * Pc22, apb.y * Pp2 + acb.y * Pc22);   // kappa-bar
+    // kappa = k32 v^2; only ln(amp2 / amp1) varies with theta (M, q), see mode_bwd
+    const double lnrb = v * v * (kb.x * S.k32.x + kb.y * S.k32.y);
+    g.M = fma(lnrb, CG2.dlnA_dM - CG.dlnA_dM, g.M);
+    g.q = fma(lnrb, CG2.dlnA_dq - CG.dlnA_dq, g.q);
+    const double vkb = 2.0 * lnrb / v;
+    g.M = fma(vkb * B.f13, CG.dcm_dM, g.M);
+  }
+}
+
+// Zeroes the contraction fields (form cotangents and basis) of a slot no unit used at this bin.
+__device__ __forceinline__ void tape_clear(double* tp) {
+  tp[kTco * kTileBins] = 0.0;
+  tp[kTso * kTileBins] = 0.0;
+  tp[kTob0 * kTileBins] = 0.0;
+  tp[kTob1 * kTileBins] = 0.0;
+#pragma unroll
+  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = 0.0;
+}
+
+// One of the 42 contraction sums over entries [e0, e1) of the tile's tape (entry e = slot * 128 +
+// thread): sum j pairs a form's cotangent with one basis element (j < 30: link forms, coefficient
+// j % 5; 30..39: spacecraft forms; 40, 41: the centre term's cos, sin). Each sum starts at entry
+// e0 + j (neighbouring lanes read neighbouring threads' columns) and runs in a fixed order.
+__device__ __forceinline__ double tape_sum(const double* tape, int j, int e0, int e1, bool geo) {
+  int f, m;
+  if (j < 30) { f = j / 5; m = j % 5; }
+  else if (j < 40) { f = 6 + (j - 30) / 5; m = (j - 30) % 5; }
+  else { f = 8; m = j - 38; }          // cos, sin: the centre's angle in either orbit
+  if (j < 40 && geo && (m == 2 || m == 3)) return 0.0;
+  const int bf = m == 0 ? kTob0 : (m == 1 ? kTob1 : (m == 2 ? kTco : kTso));
+  const int len = e1 - e0;
+  const int st = j % len;
+  // four interleaved partial sums (a fixed order) keep four independent FMA chains in flight
+  auto term = [&](int i, double a) {
+    int e = st + i;
+    e = e0 + (e >= len ? e - len : e);
+    const int slot = e >> 7, th = e & (kTileBins - 1);
+    const double* col = tape + slot * kTapeF * kTileBins + th;
+    const double fv = col[(kTfb + f) * kTileBins];
+    return (m == 4) ? a + fv : fma(fv, col[bf * kTileBins], a);
+  };
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int i = 0;
+  for (; i + 4 <= len; i += 4) {
+    a0 = term(i, a0);
+    a1 = term(i + 1, a1);
+    a2 = term(i + 2, a2);
+    a3 = term(i + 3, a3);
+  }
+  for (; i < len; ++i) a0 = term(i, a0);
+  const double r = (a0 + a1) + (a2 + a3);
+  return r;
+}
+
+// Maps the contraction sums (cotangents of the coefficients pc) to the sky frame: component c of
+// k (vec 0), p (1) or q (2). pc[15 l + 5 vec + m] = w_vec . (Mo[l] - Mo[l+1])[., m] (links 0, 1),
+// pc[45 + 5 e + m] = k . Mo[e][., m], pc55 = R k_x, pc56 = R k_y.
+__device__ __forceinline__ double tape_to_frame(const DetDev& D, const double* pcb, int vec, int c) {
+  double a = 0.0;
+#pragma unroll 1
+  for (int l = 0; l < 2; ++l)
+    for (int m = 0; m < 5; ++m) a = fma(pcb[15 * l + 5 * vec + m], D.Mo[l][c][m] - D.Mo[l + 1][c][m], a);
+  if (vec == 0) {
+#pragma unroll 1
+    for (int e = 0; e < 2; ++e)
+      for (int m = 0; m < 5; ++m) a = fma(pcb[30 + 5 * e + m], D.Mo[e][c][m], a);
+    if (c < 2) a = fma(pcb[40 + c], D.R, a);
+  }
+  return a;
+}
+
+}  // namespace pe

@@ -3,8 +3,12 @@
 // Sec. 2.3), built on the hand-written reverse sweep in pe_adjoint.cuh:
 //   k_prep_grad     per-sample coefficients (values) plus their derivatives in theta, the
 //                   latter by device dual numbers over the 11 parameters
-//   k_grad_fwd      persistent: per bin the forward mode sum, the cotangents of the A/E/T
-//                   sums dL/dB_c = conj(dg_c) - gg_c B_c, then one reverse sweep per mode
+//   k_grad_fwd_tape FP64, persistent, two 128-thread CTAs per SM: per bin the forward mode sum
+//                   writing each unit's tape (the CTA's region of global memory), the cotangents of the A/E/T
+//                   sums dL/dB_c = conj(dg_c) - gg_c B_c, one reverse sweep per mode from the
+//                   tape, and per tile the contraction of the form cotangents (pe_adjoint_tape.cuh)
+//   k_grad_fwd_mixed mixed precision, persistent: per bin the forward mode sum, the cotangents,
+//                   then one reverse sweep per mode that recomputes the mode
 //   k_grad_reduce   fixed-order per-sample sums of the tile partials -> logL, grad[11]
 //   k_fisher_fwd    per bin six reverse sweeps (Re/Im of X', Y', Z') -> Jacobian J, then
 //                   F += sum_c gg_c (J_Re B_c^T J_Re B_c + J_Im B_c^T J_Im B_c)
@@ -13,6 +17,7 @@
 
 #include "pe_adjoint.cuh"
 #include "pe_adjoint_mixed.cuh"
+#include "pe_adjoint_tape.cuh"
 #include "pe_grad.h"
 #include "pe_fault.h"
 
@@ -108,24 +113,21 @@ __device__ __forceinline__ void bracket_cotangents(const DetDev& D, int b, const
   *sZ = make_double2(bb[0].x + bb[1].x + bb[2].x, bb[0].y + bb[1].y + bb[2].y);
 }
 
-// MIX: the bin's forward mode sum (the brackets the cotangents need) by the mixed-precision unit
-// (FP64 phase, t_f and turn reductions; double-word geometry), returned to FP64, and the reverse
-// sweeps by mode_bwd_mixed; the cotangents of the A/E/T sums and every accumulation are FP64.
-template <bool MIX>
-__global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd(DetSet ds, int B, const SampleCoef* __restrict__ coef,
-                                                        const SampleGrad* __restrict__ sgrad,
-                                                        const int* __restrict__ nend,
-                                                        const long long* __restrict__ off, double* part) {
+// Mixed-precision gradient: the bin's forward mode sum (the brackets the cotangents need) by the
+// mixed-precision unit (FP64 phase, t_f and turn reductions; double-word geometry), returned to
+// FP64, and the reverse sweeps by mode_bwd_mixed, which recompute each mode; the cotangents of the
+// A/E/T sums and every accumulation are FP64.
+__global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd_mixed(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+                                                              const SampleGrad* __restrict__ sgrad,
+                                                              const int* __restrict__ nend,
+                                                              const long long* __restrict__ off, double* part) {
   __shared__ double sh[kGradW][kTileBins / 32];
-  __shared__ double2 stab[kSinTab];
-  __shared__ float4 stabw[MIX ? kSinTab : 1];
+  __shared__ float4 stabw[kSinTab];
   __shared__ double pc[kProj];
-  __shared__ float2 pcw[MIX ? kProj : 1];
-  __shared__ float2 mow[MIX ? 30 : 1];   // DetDev::Mo[0..1] as double words
-  __shared__ float2 kpq[MIX ? 9 : 1];    // the sample's k, p, q as double words
-  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
-  if constexpr (MIX)
-    for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stabw[i] = ds.d[0].sctw[i];
+  __shared__ float2 pcw[kProj];
+  __shared__ float2 mow[30];   // DetDev::Mo[0..1] as double words
+  __shared__ float2 kpq[9];    // the sample's k, p, q as double words
+  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stabw[i] = ds.d[0].sctw[i];
   __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
@@ -136,19 +138,17 @@ __global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd(DetSet ds, int B, con
     const int b = int(t - off[p]) * kTileBins + threadIdx.x;
     const DetDev& D = ds.d[I];
     proj_prologue(D, coef[s], pc);
-    if constexpr (MIX) {
-      if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
-      if (threadIdx.x >= kProj && threadIdx.x < kProj + 30) {
-        const int i = threadIdx.x - kProj;
-        mow[i] = to_dw(D.Mo[i / 15][(i / 5) % 3][i % 5]);
-      }
-      if (threadIdx.x >= kProj + 30 && threadIdx.x < kProj + 39) {
-        const int i = threadIdx.x - kProj - 30;
-        const SampleCoef& S = coef[s];
-        kpq[i] = to_dw(i < 3 ? S.k[i] : (i < 6 ? S.p[i - 3] : S.q[i - 6]));
-      }
-      __syncthreads();
+    if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+    if (threadIdx.x >= kProj && threadIdx.x < kProj + 30) {
+      const int i = threadIdx.x - kProj;
+      mow[i] = to_dw(D.Mo[i / 15][(i / 5) % 3][i % 5]);
     }
+    if (threadIdx.x >= kProj + 30 && threadIdx.x < kProj + 39) {
+      const int i = threadIdx.x - kProj - 30;
+      const SampleCoef& S = coef[s];
+      kpq[i] = to_dw(i < 3 ? S.k[i] : (i < 6 ? S.p[i - 3] : S.q[i - 6]));
+    }
+    __syncthreads();
     double v[kGradW];
 #pragma unroll
     for (int i = 0; i < kGradW; ++i) v[i] = 0.0;
@@ -158,25 +158,18 @@ __global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd(DetSet ds, int B, con
       BinIn Bn;
       load_bin(D, b, S.tc, Bn);
       double2 o[3];
-      if constexpr (MIX) {
+      {
         cdf x[3], od[3];
         bin_xyz_mixed(D, S, b, x, stabw, pcw);
         aet_from_xyz_dw(x, od);
 #pragma unroll
         for (int c = 0; c < 3; ++c) o[c] = make_double2(df_to(od[c].re) * S.ihsc, df_to(od[c].im) * S.ihsc);
-      } else {
-        XYZAcc xa;
-        xyz_zero(xa);
-        bin_modes(D, S, Bn, xa, stab, pc);
-        double2 x[3];
-        xyz_final(xa, Bn.z, x);
-        aet_from_xyz(x, o);
       }
       double2 sX, sY, sZ;
       bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
       GradAcc g;
       gacc_zero(g);
-      if constexpr (MIX) {
+      {
         BinW W;
         load_bin_w(D, b, W);
         const float4 zz = D.zw[b];
@@ -195,13 +188,6 @@ __global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd(DetSet ds, int B, con
                            (md == 0 && S.pair32) ? 3 : -1);
         }
         gaccw_flush(gw, g);
-      } else {
-#pragma unroll 1
-        for (int md = 0; md < kNModes; ++md) {
-          if (md == 3 && S.pair32) continue;
-          if (S.md[md].active && Bn.f < S.md[md].fend)
-            mode_bwd(D, S, SG, md, Bn, sX, sY, sZ, g, stab, (md == 0 && S.pair32) ? 3 : -1);
-        }
       }
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
 #pragma unroll
@@ -221,6 +207,103 @@ __global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd(DetSet ds, int B, con
       double a = sh[threadIdx.x][0];
       for (int w = 1; w < kTileBins / 32; ++w) a += sh[threadIdx.x][w];
       part[t * kGradW + threadIdx.x] = a;
+    }
+  }
+}
+
+// FP64 gradient with a tape. Per tile: the forward mode sum writes each unit's tape, the bracket
+// cotangents follow from the mode sum, the reverse sweeps read the tape and leave the form
+// cotangents in it, and the CTA contracts them with the orbit basis (42 sums over the tile's
+// 512 (bin, slot) entries, three threads per sum) and maps the sums to the sky frame. The 23
+// partials per tile are those of the recomputing kernel.
+constexpr int kGradV = 14;   // per-thread partials reduced by shuffles: dh[3], hh[3], M q c1 c2 dL io ph tc
+__global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+                                                             const SampleGrad* __restrict__ sgrad,
+                                                             const int* __restrict__ nend,
+                                                             const long long* __restrict__ off, double* part,
+                                                             double* tape_all) {
+  double* tape = tape_all + (size_t)blockIdx.x * kTapeDoubles;   // [kTapeSlots][kTapeF][kTileBins]
+  __shared__ double sh[kGradV][kTileBins / 32];
+  __shared__ double2 stab[kSinTab];
+  __shared__ double pc[kProj];
+  __shared__ double sums[3][kTapeSums];
+  for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
+  __syncthreads();
+  const int P = ds.ndet * B;
+  const long long total = off[P];
+  double* tcol = tape + threadIdx.x;
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int p = find_pair_g(off, P, t);
+    if (!PE_CHK(p >= 0 && p < P && off[p + 1] <= total && nend[p] <= ds.d[p / B].nb, 16)) continue;
+    const int I = p / B, s = p - I * B;
+    const int b = int(t - off[p]) * kTileBins + threadIdx.x;
+    const DetDev& D = ds.d[I];
+    proj_prologue(D, coef[s], pc);
+    double v[kGradV];
+#pragma unroll
+    for (int i = 0; i < kGradV; ++i) v[i] = 0.0;
+    unsigned used = 0;
+    if (b < nend[p]) {
+      const SampleCoef& S = coef[s];
+      const SampleGrad& SG = sgrad[s];
+      BinIn Bn;
+      load_bin(D, b, S.tc, Bn);
+      XYZAcc xa;
+      xyz_zero(xa);
+#pragma unroll 1
+      for (int md = 0; md < kNModes; ++md) {
+        if (md == 3 && S.pair32) continue;
+        const ModeCoef& C = S.md[md];
+        if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
+        const int sl = tape_slot(md);
+        mode_fwd_tape(D, S, C, Bn, xa, stab, pc, (md == 0 && S.pair32) ? &S.md[3] : nullptr,
+                      tcol + sl * kTapeF * kTileBins);
+        used |= 1u << sl;
+      }
+      double2 x[3], o[3];
+      xyz_final(xa, Bn.z, x);
+      aet_from_xyz(x, o);
+      double2 sX, sY, sZ;
+      bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
+      GradAcc g;
+      gacc_zero(g);
+#pragma unroll 1
+      for (int md = 0; md < kNModes; ++md) {
+        if (md == 3 && S.pair32) continue;
+        const ModeCoef& C = S.md[md];
+        if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
+        mode_bwd_tape(D, S, SG, md, Bn, sX, sY, sZ, g, pc, tcol + tape_slot(md) * kTapeF * kTileBins,
+                      (md == 0 && S.pair32) ? 3 : -1);
+      }
+      v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
+    }
+#pragma unroll 1
+    for (int sl = 0; sl < kTapeSlots; ++sl)
+      if (!(used & (1u << sl))) tape_clear(tcol + sl * kTapeF * kTileBins);
+#pragma unroll
+    for (int i = 0; i < kGradV; ++i)
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < kGradV; ++i) sh[i][wid] = v[i];
+    constexpr int kEnt = kTapeSlots * kTileBins;
+    if (threadIdx.x < 3 * kTapeSums) {
+      const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
+      const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
+      sums[q][j] = tape_sum(tape, j, e0, e1, D.orbit != 0);
+    }
+    __syncthreads();
+    if (threadIdx.x < kGradV) {
+      double a = sh[threadIdx.x][0];
+      for (int w = 1; w < kTileBins / 32; ++w) a += sh[threadIdx.x][w];
+      part[t * kGradW + threadIdx.x] = a;
+    } else if (threadIdx.x < kGradW) {
+      const int k = threadIdx.x - kGradV;
+      double pcb[kTapeSums];
+      for (int j = 0; j < kTapeSums; ++j) pcb[j] = sums[0][j] + sums[1][j] + sums[2][j];
+      part[t * kGradW + threadIdx.x] = tape_to_frame(D, pcb, k / 3, k % 3);
     }
   }
 }
@@ -355,11 +438,11 @@ cudaError_t launch_prep_grad(const double* theta, int B, unsigned mask, const De
   return pe::launch_status();
 }
 cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad, const int* nend,
-                            const long long* off, double* part, int grid, bool mixed, cudaStream_t st) {
+                            const long long* off, double* part, int grid, bool mixed, double* tape, cudaStream_t st) {
   if (mixed)
-    k_grad_fwd<true><<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
+    k_grad_fwd_mixed<<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
   else
-    k_grad_fwd<false><<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
+    k_grad_fwd_tape<<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part, tape);
   return pe::launch_status();
 }
 cudaError_t launch_grad_reduce(const DetSet& ds, int B, const long long* off, const double* part,
@@ -381,6 +464,8 @@ cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, 
   return pe::launch_status();
 }
 int grad_partial_width() { return kGradW; }
+int grad_tape_ctas_per_sm() { return 2; }
+size_t grad_tape_doubles_per_cta() { return (size_t)kTapeDoubles; }
 int fisher_partial_width() { return kFisherW; }
 
 // Index-check error word of this file's kernels (checked build; 0 otherwise), cleared when read.

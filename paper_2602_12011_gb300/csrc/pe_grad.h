@@ -9,7 +9,8 @@ namespace pe {
 cudaError_t launch_prep_grad(const double* theta, int B, unsigned mask, const DetSet& ds, SampleCoef* coef,
                              SampleGrad* sgrad, int* nend, int* status, cudaStream_t st);
 cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad, const int* nend,
-                            const long long* off, double* part, int grid, bool mixed, cudaStream_t st);
+                            const long long* off, double* part, int grid, bool mixed, double* tape,
+                            cudaStream_t st);
 cudaError_t launch_grad_reduce(const DetSet& ds, int B, const long long* off, const double* part,
                                const SampleCoef* coef, const SampleGrad* sgrad, double* logl, double* grad,
                                cudaStream_t st);
@@ -18,6 +19,10 @@ cudaError_t launch_fisher_fwd(const DetSet& ds, int B, const SampleCoef* coef, c
 cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, const double* part,
                                  const SampleCoef* coef, double* F, cudaStream_t st);
 int grad_partial_width();
+// FP64 gradient: resident CTAs per SM of its persistent kernel, and the doubles of tape each CTA
+// of its grid needs (launch_grad_fwd's tape holds grid x that many; unused in mixed precision)
+int grad_tape_ctas_per_sm();
+size_t grad_tape_doubles_per_cta();
 int fisher_partial_width();
 
 }  // namespace pe
