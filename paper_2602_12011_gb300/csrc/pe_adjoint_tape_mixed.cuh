@@ -1,0 +1,404 @@
+// pe_adjoint_tape_mixed.cuh -- the tape gradient of pe_adjoint_tape.cuh in mixed precision
+// (PE_PREC_MIXED; row G1, arXiv:2602.12011 Sec. 2.2-2.3). The forward pass is the mixed-precision
+// unit (mode_bin_mixed: FP64 TaylorF2 phase and its exact turn reduction; double-word t_f,
+// geometry, sincs and TDI brackets, same operations in the same order) writing the double words
+// its reverse needs to the tape; the reverse sweep runs in double words from the tape, and only
+// the phase and t_f cotangents and the PN chain rule at the mode level return to FP64. The
+// per-tile contraction of the form cotangents with the orbit basis runs in double words too.
+//
+// The tape has the FP64 tape's layout (pe_adjoint_tape.cuh) with every field a double word
+// (8 bytes, as a double): kTamp0 holds the amplitude times hsc before the taper, kTw after it.
+#pragma once
+#include "pe_adjoint_mixed.cuh"
+#include "pe_adjoint_tape.cuh"
+
+namespace pe {
+
+// Forward pass of one unit: mode_bin_mixed plus the tape and the sincs' derivatives in k.n.
+__device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const SampleCoef& S, const ModeCoef& C,
+                                                    const BinIn& B, const BinW& W, MixAcc& acc,
+                                                    const float4* __restrict__ tab, const float2* __restrict__ pcw,
+                                                    const ModeCoef* C2, df* tp) {
+  const double v = C.cm * B.f13;
+  const double lnv = C.lncm + B.lnf3;
+  const double iv5 = C.icm5 * D.fm53[B.b];
+  double poly = S.P[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) poly = fma(poly, v, S.P[k]);
+  const double q56 = fma(S.Q6, v, S.Q5);
+  const double psi_pn = fma(iv5, poly, lnv * q56);
+  const df vw = dfl_mul(C.cmw, W.f13);
+  df dpol = S.Pdw[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) dpol = dfl_add(dfl_mul(dpol, vw), S.Pdw[k]);
+  const df dv = dfl_add(dfl_mul(df_from_bits(iv5), dpol),
+                        dfl_add(dfl_mul(dfl_mul(S.Q6w, vw), df_from_bits(lnv)), df_from_bits(q56)));
+  const df tf = dfl_add(S.tcw, dfl_mul(dfl_mul(C.tffacw, W.invf), dv));
+  df alpha, geo;
+  if (fabsf(tf.x) < D.tfw_max) {
+    alpha = dfl_add(dfl_mul(tf, D.ratew), D.alpha0w);
+    geo = dfl_mul(tf, D.geo_ratew);
+  } else {
+    double dpol64 = S.Pd[7];
+#pragma unroll 1
+    for (int k = 6; k >= 0; --k) dpol64 = fma(dpol64, v, S.Pd[k]);
+    const double tf64 = fma(C.tffac * B.invf, fma(iv5, dpol64, fma(S.Q6 * v, lnv, q56)), S.tc);
+    alpha = frac_dw(fma(tf64, D.rate_t, D.alpha0_t));
+    geo = frac_dw(tf64 * D.geo_rate_t);
+  }
+  df A = dfl_mul(C.ampw, W.fm76);
+  if (C.p >= 1) {
+    A = dfl_mul(A, vw);
+    if (C.p >= 2) A = dfl_mul(A, vw);
+  }
+  tp[kTamp0 * kTileBins] = A;
+  if (dlt_pos(C.ftap, B.f)) {
+    const double span = C.fend - C.ftap;
+    const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
+    A = dfl_mul(A, df_from_bits((zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt))));
+  }
+  tp[kTw * kTileBins] = A;
+  tp[kTdv * kTileBins] = dv;
+  cdf Ap = {dfl_mul(A, C.Ppw), df_make(0.f, 0.f)}, Ac = {dfl_mul(A, C.Pcw), df_make(0.f, 0.f)};
+  if (C2) {
+    const df v2 = dfl_mul(vw, vw);
+    const df kr = dfl_mul(S.k32w[0], v2), ki = dfl_mul(S.k32w[1], v2);
+    Ap = cdf{dfl_mul(A, dfl_add(C.Ppw, dfl_mul(kr, C2->Ppw))), dfl_mul(A, dfl_mul(ki, C2->Ppw))};
+    Ac = cdf{dfl_mul(A, dfl_add(C.Pcw, dfl_mul(kr, C2->Pcw))), dfl_mul(A, dfl_mul(ki, C2->Pcw))};
+  }
+  const cdf eo = df_cis_turns(alpha, tab);
+  const df co = eo.re, so = eo.im;
+  const df kxc = dfl_mul(D.Rw, dfl_add(dfl_mul(S.kw[0], co), dfl_mul(S.kw[1], so)));
+  const df pf = dfl_sub(frac_dw(fma(-C.mfac, psi_pn, C.ph0 - B.frc)), dfl_mul(W.f, kxc));
+  df ob[4];
+  if (D.orbit == 0) {
+    ob[0] = dfl_sub(dfl_mul(co, co), dfl_mul(so, so));
+    ob[1] = df_scale2(dfl_mul(so, co), 2.0f);
+    ob[2] = co;
+    ob[3] = so;
+  } else {
+    const cdf e0 = df_cis_turns(geo, tab);
+    ob[0] = e0.re;
+    ob[1] = e0.im;
+    ob[2] = ob[3] = df_make(0.f, 0.f);
+  }
+  tp[kTco * kTileBins] = co;
+  tp[kTso * kTileBins] = so;
+  tp[kTob0 * kTileBins] = ob[0];
+  tp[kTob1 * kTileBins] = ob[1];
+  const df e0 = df_scale2(dfl_mul(W.f, dw_dot5(pcw + 45, ob)), 0.5f);
+  const df e1 = df_scale2(dfl_mul(W.f, dw_dot5(pcw + 50, ob)), 0.5f);
+  const df e01 = dfl_add(e0, e1);
+  cdf G[3];
+  df smv[3], spv[3];
+  df sk = df_make(0.f, 0.f), sp = sk, sq = sk;
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    df knr, npr, nqr;
+    if (l < 2) {
+      knr = dw_dot5(pcw + 15 * l, ob);
+      npr = dw_dot5(pcw + 15 * l + 5, ob);
+      nqr = dw_dot5(pcw + 15 * l + 10, ob);
+      sk = dfl_add(sk, knr);
+      sp = dfl_add(sp, npr);
+      sq = dfl_add(sq, nqr);
+    } else {
+      knr = df_make(-sk.x, -sk.y);
+      npr = df_make(-sp.x, -sp.y);
+      nqr = df_make(-sq.x, -sq.y);
+    }
+    const df inv = df_rsqrt(dfl_add(dfl_mul(knr, knr), dfl_add(dfl_mul(npr, npr), dfl_mul(nqr, nqr))));
+    const df kn = dfl_mul(knr, inv);
+    const df np = dfl_mul(npr, inv);
+    const df nq = dfl_mul(nqr, inv);
+    const df Fp = dfl_sub(dfl_mul(np, np), dfl_mul(nq, nq));
+    const df Fc = df_scale2(dfl_mul(np, nq), 2.0f);
+    const cdf gam = C2 ? cdf{dfl_sub(dfl_mul(Ap.re, Fp), dfl_mul(Ac.im, Fc)), dfl_add(dfl_mul(Ap.im, Fp), dfl_mul(Ac.re, Fc))}
+                       : cdf{dfl_mul(Ap.re, Fp), dfl_mul(Ac.re, Fc)};
+    const int t = (l == 0) ? 2 : l - 1;   // third spacecraft
+    const cdf Et = df_cis_turns(l == 0 ? dfl_sub(pf, e01) : dfl_add(pf, l == 1 ? e0 : e1), tab);
+    tp[(kTE + 2 * t) * kTileBins] = Et.re;
+    tp[(kTE + 2 * t + 1) * kTileBins] = Et.im;
+    G[l] = cdfl_mul(gam, Et);
+    // sincs, and their derivatives in kn: d s-/dkn = -a sinc'(u1), d s+/dkn = a sinc'(u2)
+    const df akn = dfl_mul(W.a, kn);
+    const df u1 = dfl_sub(W.a, akn), u2 = dfl_add(W.a, akn);
+    df dsm, dspl;
+    if (dlt_pos(B.a, kSincPolyA)) {
+      const df2 r1 = df_sinc_poly_d(u1), r2 = df_sinc_poly_d(u2);
+      smv[l] = r1.v;
+      spv[l] = r2.v;
+      dsm = r1.d;
+      dspl = r2.d;
+    } else {
+      const cdf ea = df_cis_turns(dfl_mul(W.at, kn), tab);
+      const df sak = ea.im, cak = ea.re;
+      const df x1 = dfl_mul(W.sa, cak), x2 = dfl_mul(W.ca, sak);
+      const df s1 = dfl_sub(x1, x2), s2 = dfl_add(x1, x2);
+      const df y1 = dfl_mul(W.ca, cak), y2 = dfl_mul(W.sa, sak);
+      const df c1 = dfl_add(y1, y2), c2 = dfl_sub(y1, y2);   // cos u1, cos u2
+      const bool small1 = fabsf(u1.x) < 1e-3f, small2 = fabsf(u2.x) < 1e-3f;
+      if (!small1 && !small2) {
+        const df rr = df_rcp(dfl_mul(u1, u2));
+        smv[l] = dfl_mul(dfl_mul(s1, u2), rr);
+        spv[l] = dfl_mul(dfl_mul(s2, u1), rr);
+        dsm = dfl_mul(dfl_sub(c1, smv[l]), dfl_mul(u2, rr));
+        dspl = dfl_mul(dfl_sub(c2, spv[l]), dfl_mul(u1, rr));
+      } else {
+        if (small1) {
+          smv[l] = df_sinc_small(u1);
+          dsm = df_dsinc_small(u1);
+        } else {
+          const df r1 = df_rcp(u1);
+          smv[l] = dfl_mul(s1, r1);
+          dsm = dfl_mul(dfl_sub(c1, smv[l]), r1);
+        }
+        if (small2) {
+          spv[l] = df_sinc_small(u2);
+          dspl = df_dsinc_small(u2);
+        } else {
+          const df r2 = df_rcp(u2);
+          spv[l] = dfl_mul(s2, r2);
+          dspl = dfl_mul(dfl_sub(c2, spv[l]), r2);
+        }
+      }
+    }
+    df* tl = tp + (kTL + 8 * l) * kTileBins;
+    tl[0] = kn;
+    tl[kTileBins] = np;
+    tl[2 * kTileBins] = nq;
+    tl[3 * kTileBins] = inv;
+    tl[4 * kTileBins] = smv[l];
+    tl[5 * kTileBins] = spv[l];
+    tl[6 * kTileBins] = df_neg(dfl_mul(W.a, dsm));
+    tl[7 * kTileBins] = dfl_mul(W.a, dspl);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lp = (c + 2) % 3, lu = c;
+    acc.Pr[c] = dfl_add(acc.Pr[c], dfl_sub(dfl_mul(G[lp].re, spv[lp]), dfl_mul(G[lu].re, smv[lu])));
+    acc.Pi[c] = dfl_add(acc.Pi[c], dfl_sub(dfl_mul(G[lp].im, spv[lp]), dfl_mul(G[lu].im, smv[lu])));
+    acc.Qr[c] = dfl_add(acc.Qr[c], dfl_sub(dfl_mul(G[lp].re, smv[lp]), dfl_mul(G[lu].re, spv[lu])));
+    acc.Qi[c] = dfl_add(acc.Qi[c], dfl_sub(dfl_mul(G[lp].im, smv[lp]), dfl_mul(G[lu].im, spv[lu])));
+  }
+}
+
+// Reverse sweep of one unit from its double-word tape. sX, sY, sZ: the bracket cotangents times
+// ihsc; zw: the bin's z. Accumulates the theta components reached per unit into g (FP64) and writes
+// the nine form cotangents (double words) to the slot's kTfb fields, as mode_bwd_tape.
+__device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const SampleCoef& S, const SampleGrad& SG,
+                                                    int md, const BinIn& B, const BinW& W, const cdf& zw,
+                                                    const cdf& sX, const cdf& sY, const cdf& sZ, GradAcc& g,
+                                                    const float2* __restrict__ pcw, df* tp, int md2) {
+  const ModeCoef& C = S.md[md];
+  const ModeGrad& CG = SG.md[md];
+  const df zero = df_make(0.f, 0.f);
+  const df A0 = tp[kTamp0 * kTileBins], A = tp[kTw * kTileBins];
+  // polarisation weights without the amplitude, as the forward pass forms them
+  const df vw = dfl_mul(C.cmw, W.f13);
+  cdf ap = {C.Ppw, zero}, ac = {C.Pcw, zero};
+  if (md2 >= 0) {
+    const df v2 = dfl_mul(vw, vw);
+    const df kr = dfl_mul(S.k32w[0], v2), ki = dfl_mul(S.k32w[1], v2);
+    const ModeCoef& C2 = S.md[md2];
+    ap = cdf{dfl_add(C.Ppw, dfl_mul(kr, C2.Ppw)), dfl_mul(ki, C2.Ppw)};
+    ac = cdf{dfl_add(C.Pcw, dfl_mul(kr, C2.Pcw)), dfl_mul(ki, C2.Pcw)};
+  }
+  const cdf Ap = {dfl_mul(A, ap.re), dfl_mul(A, ap.im)}, Ac = {dfl_mul(A, ac.re), dfl_mul(A, ac.im)};
+  cdf Apb = {zero, zero}, Acb = {zero, zero};
+  df th0b = zero, th1b = zero, th2b = zero;            // spacecraft-angle cotangents (radians)
+  df f0k = zero, f0p = zero, f0q = zero, f1k = zero, f1p = zero, f1q = zero;   // link forms 0..5
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    const cdf& su = (l == 0) ? sX : (l == 1 ? sY : sZ);
+    const cdf& Sv = (l == 0) ? sY : (l == 1 ? sZ : sX);
+    const cdf Su = {df_neg(su.re), df_neg(su.im)};
+    const int t = (l == 0) ? 2 : l - 1;
+    const df* tl = tp + (kTL + 8 * l) * kTileBins;
+    const df kn = tl[0], np = tl[kTileBins], nq = tl[2 * kTileBins], inv = tl[3 * kTileBins];
+    const df sm = tl[4 * kTileBins], spl = tl[5 * kTileBins];
+    const df dsm = tl[6 * kTileBins], dspl = tl[7 * kTileBins];
+    const cdf E = {tp[(kTE + 2 * t) * kTileBins], tp[(kTE + 2 * t + 1) * kTileBins]};
+    const df Fp = dfl_sub(dfl_mul(np, np), dfl_mul(nq, nq));
+    const df Fc = df_scale2(dfl_mul(np, nq), 2.0f);
+    const cdf gam = (md2 >= 0) ? cdf{dfl_sub(dfl_mul(Ap.re, Fp), dfl_mul(Ac.im, Fc)),
+                                     dfl_add(dfl_mul(Ap.im, Fp), dfl_mul(Ac.re, Fc))}
+                               : cdf{dfl_mul(Ap.re, Fp), dfl_mul(Ac.re, Fc)};
+    const cdf G = cdf_mul_s(gam, E);
+    const cdf U = {dfl_add(dfl_mul(zw.re, spl), sm), dfl_mul(zw.im, spl)};
+    const cdf V = {dfl_add(dfl_mul(zw.re, sm), spl), dfl_mul(zw.im, sm)};
+    const cdf Gb = cdf_add_s(cdf_mul_conj(Su, U), cdf_mul_conj(Sv, V));
+    const cdf Ub = cdf_mul_conj(Su, G), Vb = cdf_mul_conj(Sv, G);
+    const df smb = dfl_add(Ub.re, dfl_add(dfl_mul(Vb.re, zw.re), dfl_mul(Vb.im, zw.im)));
+    const df splb = dfl_add(dfl_add(dfl_mul(Ub.re, zw.re), dfl_mul(Ub.im, zw.im)), Vb.re);
+    const df knb = dfl_add(dfl_mul(smb, dsm), dfl_mul(splb, dspl));
+    const cdf gamb = cdf_mul_conj(Gb, E), Eb = cdf_mul_conj(Gb, gam);
+    const df thb = dfl_sub(dfl_mul(E.re, Eb.im), dfl_mul(E.im, Eb.re));
+    if (t == 0) th0b = dfl_add(th0b, thb);
+    else if (t == 1) th1b = dfl_add(th1b, thb);
+    else th2b = dfl_add(th2b, thb);
+    // gam = Fp Ap + i Fc Ac
+    Apb = cdf{dfl_add(Apb.re, dfl_mul(gamb.re, Fp)), dfl_add(Apb.im, dfl_mul(gamb.im, Fp))};
+    Acb = cdf{dfl_add(Acb.re, dfl_mul(gamb.im, Fc)), dfl_sub(Acb.im, dfl_mul(gamb.re, Fc))};
+    const df Fpb = dfl_add(dfl_mul(gamb.re, Ap.re), dfl_mul(gamb.im, Ap.im));
+    const df Fcb = dfl_sub(dfl_mul(gamb.im, Ac.re), dfl_mul(gamb.re, Ac.im));
+    const df npb = df_scale2(dfl_add(dfl_mul(np, Fpb), dfl_mul(nq, Fcb)), 2.0f);
+    const df nqb = df_scale2(dfl_sub(dfl_mul(np, Fcb), dfl_mul(nq, Fpb)), 2.0f);
+    // (kn, np, nq) = (knr, npr, nqr) / |n'|
+    const df dot = dfl_add(dfl_mul(knb, kn), dfl_add(dfl_mul(npb, np), dfl_mul(nqb, nq)));
+    const df rk = dfl_mul(inv, dfl_sub(knb, dfl_mul(kn, dot)));
+    const df rp = dfl_mul(inv, dfl_sub(npb, dfl_mul(np, dot)));
+    const df rq = dfl_mul(inv, dfl_sub(nqb, dfl_mul(nq, dot)));
+    // link 2's projections are minus the sum of links 0 and 1's
+    if (l != 1) {
+      const df sk = l == 0 ? rk : df_neg(rk), sp = l == 0 ? rp : df_neg(rp), sq = l == 0 ? rq : df_neg(rq);
+      f0k = dfl_add(f0k, sk); f0p = dfl_add(f0p, sp); f0q = dfl_add(f0q, sq);
+    }
+    if (l != 0) {
+      const df sk = l == 1 ? rk : df_neg(rk), sp = l == 1 ? rp : df_neg(rp), sq = l == 1 ? rq : df_neg(rq);
+      f1k = dfl_add(f1k, sk); f1p = dfl_add(f1p, sp); f1q = dfl_add(f1q, sq);
+    }
+  }
+  // spacecraft angles 2 pi (pf + e_t), e_2 = -(e_0 + e_1), e_t = (f/2) (form 6 + t)
+  const double phb = 2.0 * kPi * df_to(dfl_add(dfl_add(th0b, th1b), th2b));   // phase cotangent (turns)
+  const df pif = dfl_mul(W.f, df_make(3.1415927f, -8.742278e-08f));            // pi f
+  df fb[9];
+  fb[0] = f0k; fb[1] = f0p; fb[2] = f0q; fb[3] = f1k; fb[4] = f1p; fb[5] = f1q;
+  fb[6] = dfl_mul(pif, dfl_sub(th0b, th2b));
+  fb[7] = dfl_mul(pif, dfl_sub(th1b, th2b));
+  const df kxcb = df_from_bits(-B.f * phb);
+  fb[8] = kxcb;
+  df obb[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    df a = dfl_add(dfl_mul(fb[6], pcw[45 + m]), dfl_mul(fb[7], pcw[50 + m]));
+#pragma unroll
+    for (int f = 0; f < 6; ++f) a = dfl_add(a, dfl_mul(fb[f], pcw[5 * f + m]));
+    obb[m] = a;
+  }
+  const df co = tp[kTco * kTileBins], so = tp[kTso * kTileBins];
+  double tfb;
+  if (D.orbit == 0) {
+    const df cob = dfl_add(dfl_add(obb[2], dfl_mul(kxcb, pcw[55])),
+                           df_scale2(dfl_add(dfl_mul(co, obb[0]), dfl_mul(so, obb[1])), 2.0f));
+    const df sob = dfl_add(dfl_add(obb[3], dfl_mul(kxcb, pcw[56])),
+                           df_scale2(dfl_sub(dfl_mul(co, obb[1]), dfl_mul(so, obb[0])), 2.0f));
+    tfb = kPi * D.rate_ht * df_to(dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob)));
+  } else {
+    const df c0 = tp[kTob0 * kTileBins], s0 = tp[kTob1 * kTileBins];
+    const df cob = dfl_mul(kxcb, pcw[55]), sob = dfl_mul(kxcb, pcw[56]);
+    tfb = kPi * D.geo_rate_ht * df_to(dfl_sub(dfl_mul(c0, obb[1]), dfl_mul(s0, obb[0]))) +
+          kPi * D.rate_ht * df_to(dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob)));
+  }
+#pragma unroll
+  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = fb[f];
+  // ---------------- mode level (FP64)
+  const double v = C.cm * B.f13;
+  const double iv = C.icm * B.fm13;
+  const double lnv = C.lncm + B.lnf3;
+  const double iv5 = C.icm5 * D.fm53[B.b];
+  g.ph = fma(phb, 2.0 * C.mfac, g.ph);          // d ph0/d phi_c = m/(2 pi)
+  g.tc = fma(-B.f, phb, g.tc);                   // frac(f t_c)
+  const double psib = -C.mfac * phb;
+  g.tc += tfb;                                   // t_f = t_c + (m/(12 pi f)) D(v)
+  const double Db = tfb * C.tffac * B.invf;
+  double vb = 0.0;
+  if (A.x != 0.0f) {
+    // cotangent of the amplitude (times ihsc), then of ln amp
+    const df ampb = dfl_add(dfl_add(dfl_mul(Apb.re, ap.re), dfl_mul(Apb.im, ap.im)),
+                            dfl_add(dfl_mul(Acb.re, ac.re), dfl_mul(Acb.im, ac.im)));
+    const double lnAb = df_to(dfl_mul(ampb, A));
+    g.M = fma(lnAb, CG.dlnA_dM, g.M);
+    g.q = fma(lnAb, CG.dlnA_dq, g.q);
+    g.dL = fma(lnAb, SG.dlnA_ddL, g.dL);
+    vb = lnAb * double(C.p) * iv;
+    if (dlt_pos(C.ftap, B.f)) {
+      const double span = C.fend - C.ftap;
+      const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
+      const double w = (zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt));
+      const double wb = df_to(dfl_mul(ampb, A0));
+      const double zb = -wb * w * (1.0 - w);
+      const double fe = C.fend, ft = C.ftap, As = fe - ft;
+      const double dz = 0.1 / (fe - B.f) - As / ((fe - B.f) * (fe - B.f)) - 0.1 / (B.f - ft) -
+                        0.9 * As / ((B.f - ft) * (B.f - ft));
+      g.M = fma(zb * dz, CG.dfend_dM, g.M);
+    }
+  }
+  double ddpol = S.Pdd[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) ddpol = fma(ddpol, v, S.Pdd[k]);
+  const double dv = df_to(tp[kTdv * kTileBins]);
+  vb += psib * dv * iv + Db * (iv5 * ddpol * iv + S.Q6 * (2.0 + lnv));
+  g.M = fma(vb * B.f13, CG.dcm_dM, g.M);
+  double pq = SG.dP_dq[7], dq = SG.dPd_dq[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) {
+    pq = fma(pq, v, SG.dP_dq[k]);
+    dq = fma(dq, v, SG.dPd_dq[k]);
+  }
+  const double psiq = fma(iv5, pq, lnv * fma(SG.dQ6_dq, v, SG.dQ5_dq));
+  const double Dq = fma(iv5, dq, fma(SG.dQ6_dq * v, 1.0 + lnv, SG.dQ5_dq));
+  g.q += psib * psiq + Db * Dq;
+  const double iv2 = iv * iv;
+  g.c1 += psib * (SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv) - Db * (2.0 * SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv);
+  g.c2 += psib * (SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv) - Db * (2.0 * SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv);
+  // polarisation weights: cotangents of ap, ac are A Apb, A Acb (true scale)
+  const double apbx = df_to(dfl_mul(A, Apb.re)), acbx = df_to(dfl_mul(A, Acb.re));
+  g.io += apbx * CG.dPp_di + acbx * CG.dPc_di;
+  if (md2 >= 0) {
+    const ModeGrad& CG2 = SG.md[md2];
+    const double apby = df_to(dfl_mul(A, Apb.im)), acby = df_to(dfl_mul(A, Acb.im));
+    const double Pp2 = S.md[md2].Pp, Pc2 = S.md[md2].Pc;
+    const double2 kap = make_double2(S.k32.x * v * v, S.k32.y * v * v);
+    g.io += (apbx * kap.x + apby * kap.y) * CG2.dPp_di + (acbx * kap.x + acby * kap.y) * CG2.dPc_di;
+    const double2 kb = make_double2(apbx * Pp2 + acbx * Pc2, apby * Pp2 + acby * Pc2);   // kappa-bar
+    const double lnrb = v * v * (kb.x * S.k32.x + kb.y * S.k32.y);
+    g.M = fma(lnrb, CG2.dlnA_dM - CG.dlnA_dM, g.M);
+    g.q = fma(lnrb, CG2.dlnA_dq - CG.dlnA_dq, g.q);
+    const double vkb = 2.0 * lnrb / v;
+    g.M = fma(vkb * B.f13, CG.dcm_dM, g.M);
+  }
+}
+
+// Zeroes the contraction fields of a slot no unit used at this bin (double-word tape).
+__device__ __forceinline__ void tape_clear_dw(df* tp) {
+  const df z = df_make(0.f, 0.f);
+  tp[kTco * kTileBins] = z;
+  tp[kTso * kTileBins] = z;
+  tp[kTob0 * kTileBins] = z;
+  tp[kTob1 * kTileBins] = z;
+#pragma unroll
+  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = z;
+}
+
+// tape_sum on the double-word tape, in double words; the result returns to FP64.
+__device__ __forceinline__ double tape_sum_dw(const df* tape, int j, int e0, int e1, bool geo) {
+  int f, m;
+  if (j < 30) { f = j / 5; m = j % 5; }
+  else if (j < 40) { f = 6 + (j - 30) / 5; m = (j - 30) % 5; }
+  else { f = 8; m = j - 38; }
+  if (j < 40 && geo && (m == 2 || m == 3)) return 0.0;
+  const int bf = m == 0 ? kTob0 : (m == 1 ? kTob1 : (m == 2 ? kTco : kTso));
+  const int len = e1 - e0;
+  const int st = j % len;
+  auto term = [&](int i, df a) {
+    int e = st + i;
+    e = e0 + (e >= len ? e - len : e);
+    const int slot = e >> 7, th = e & (kTileBins - 1);
+    const df* col = tape + slot * kTapeF * kTileBins + th;
+    const df fv = col[(kTfb + f) * kTileBins];
+    return (m == 4) ? dfl_add(a, fv) : dfl_add(a, dfl_mul(fv, col[bf * kTileBins]));
+  };
+  df a0 = df_make(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+  int i = 0;
+  for (; i + 4 <= len; i += 4) {
+    a0 = term(i, a0);
+    a1 = term(i + 1, a1);
+    a2 = term(i + 2, a2);
+    a3 = term(i + 3, a3);
+  }
+  for (; i < len; ++i) a0 = term(i, a0);
+  return df_to(dfl_add(dfl_add(a0, a1), dfl_add(a2, a3)));
+}
+
+}  // namespace pe

@@ -629,12 +629,11 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep_grad(th, B, mode_mask, ds, coef, sg, nend, stat, st));
   PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::kTileBins, st));
-  // FP64: a persistent grid of two CTAs per SM, each with its tape region; mixed: as the forward
-  const long long g = std::max<long long>(
-      1, std::min<long long>(max_tiles, (long long)sm_count() *
-                                            (mixed ? pe::fwd_blocks_per_sm() : pe::grad_tape_ctas_per_sm())));
+  // a persistent grid of two CTAs per SM, each with its tape region
+  const long long g =
+      std::max<long long>(1, std::min<long long>(max_tiles, (long long)sm_count() * pe::grad_tape_ctas_per_sm()));
   double* tape = nullptr;
-  if (!mixed) PE_CUDA(sc.alloc(&tape, (size_t)g * pe::grad_tape_doubles_per_cta()));
+  PE_CUDA(sc.alloc(&tape, (size_t)g * pe::grad_tape_doubles_per_cta()));
   void* prof = nullptr;
   pe::profile_begin(st, &prof);
   PE_CUDA(pe::launch_grad_fwd(ds, B, coef, sg, nend, off, part, (int)g, mixed, tape, st));

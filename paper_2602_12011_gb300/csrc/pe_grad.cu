@@ -7,8 +7,8 @@
 //                   writing each unit's tape (the CTA's region of global memory), the cotangents of the A/E/T
 //                   sums dL/dB_c = conj(dg_c) - gg_c B_c, one reverse sweep per mode from the
 //                   tape, and per tile the contraction of the form cotangents (pe_adjoint_tape.cuh)
-//   k_grad_fwd_mixed mixed precision, persistent: per bin the forward mode sum, the cotangents,
-//                   then one reverse sweep per mode that recomputes the mode
+//   k_grad_fwd_mixed the same in mixed precision with a double-word tape
+//                   (pe_adjoint_tape_mixed.cuh)
 //   k_grad_reduce   fixed-order per-sample sums of the tile partials -> logL, grad[11]
 //   k_fisher_fwd    per bin six reverse sweeps (Re/Im of X', Y', Z') -> Jacobian J, then
 //                   F += sum_c gg_c (J_Re B_c^T J_Re B_c + J_Im B_c^T J_Im B_c)
@@ -18,12 +18,14 @@
 #include "pe_adjoint.cuh"
 #include "pe_adjoint_mixed.cuh"
 #include "pe_adjoint_tape.cuh"
+#include "pe_adjoint_tape_mixed.cuh"
 #include "pe_grad.h"
 #include "pe_fault.h"
 
 namespace pe {
 
 constexpr int kGradW = 23;   // per-tile partials: dh[3], hh[3], M q c1 c2 dL io ph tc, k[3] p[3] q[3]
+constexpr int kGradV = 14;   // of which reduced by shuffles: dh[3], hh[3], M q c1 c2 dL io ph tc
 constexpr int kFisherW = 66; // unique entries of the symmetric 11 x 11 matrix
 constexpr int kFisherThreads = 32;
 
@@ -113,24 +115,26 @@ __device__ __forceinline__ void bracket_cotangents(const DetDev& D, int b, const
   *sZ = make_double2(bb[0].x + bb[1].x + bb[2].x, bb[0].y + bb[1].y + bb[2].y);
 }
 
-// Mixed-precision gradient: the bin's forward mode sum (the brackets the cotangents need) by the
-// mixed-precision unit (FP64 phase, t_f and turn reductions; double-word geometry), returned to
-// FP64, and the reverse sweeps by mode_bwd_mixed, which recompute each mode; the cotangents of the
-// A/E/T sums and every accumulation are FP64.
-__global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd_mixed(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+// Mixed-precision gradient with a double-word tape (pe_adjoint_tape_mixed.cuh): per tile the
+// mixed-precision forward mode sum writes each unit's tape, the bracket cotangents are formed in
+// FP64 from the mode sum, the reverse sweeps read the tape, and the CTA contracts the form
+// cotangents in double words. The 23 partials per tile are the FP64 kernel's.
+__global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                               const SampleGrad* __restrict__ sgrad,
                                                               const int* __restrict__ nend,
-                                                              const long long* __restrict__ off, double* part) {
-  __shared__ double sh[kGradW][kTileBins / 32];
+                                                              const long long* __restrict__ off, double* part,
+                                                              double* tape_all) {
+  df* tape = reinterpret_cast<df*>(tape_all + (size_t)blockIdx.x * kTapeDoubles);
+  __shared__ double sh[kGradV][kTileBins / 32];
   __shared__ float4 stabw[kSinTab];
   __shared__ double pc[kProj];
   __shared__ float2 pcw[kProj];
-  __shared__ float2 mow[30];   // DetDev::Mo[0..1] as double words
-  __shared__ float2 kpq[9];    // the sample's k, p, q as double words
+  __shared__ double sums[3][kTapeSums];
   for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stabw[i] = ds.d[0].sctw[i];
   __syncthreads();
   const int P = ds.ndet * B;
   const long long total = off[P];
+  df* tcol = tape + threadIdx.x;
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair_g(off, P, t);
     if (!PE_CHK(p >= 0 && p < P && off[p + 1] <= total && nend[p] <= ds.d[p / B].nb, 16)) continue;
@@ -139,74 +143,83 @@ __global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd_mixed(DetSet ds, int 
     const DetDev& D = ds.d[I];
     proj_prologue(D, coef[s], pc);
     if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
-    if (threadIdx.x >= kProj && threadIdx.x < kProj + 30) {
-      const int i = threadIdx.x - kProj;
-      mow[i] = to_dw(D.Mo[i / 15][(i / 5) % 3][i % 5]);
-    }
-    if (threadIdx.x >= kProj + 30 && threadIdx.x < kProj + 39) {
-      const int i = threadIdx.x - kProj - 30;
-      const SampleCoef& S = coef[s];
-      kpq[i] = to_dw(i < 3 ? S.k[i] : (i < 6 ? S.p[i - 3] : S.q[i - 6]));
-    }
     __syncthreads();
-    double v[kGradW];
+    double v[kGradV];
 #pragma unroll
-    for (int i = 0; i < kGradW; ++i) v[i] = 0.0;
+    for (int i = 0; i < kGradV; ++i) v[i] = 0.0;
+    unsigned used = 0;
     if (b < nend[p]) {
       const SampleCoef& S = coef[s];
       const SampleGrad& SG = sgrad[s];
       BinIn Bn;
       load_bin(D, b, S.tc, Bn);
-      double2 o[3];
-      {
-        cdf x[3], od[3];
-        bin_xyz_mixed(D, S, b, x, stabw, pcw);
-        aet_from_xyz_dw(x, od);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[c] = make_double2(df_to(od[c].re) * S.ihsc, df_to(od[c].im) * S.ihsc);
+      BinW W;
+      load_bin_w(D, b, W);
+      const float4 zz = D.zw[b];
+      const cdf zw = {df_make(zz.x, zz.y), df_make(zz.z, zz.w)};
+      MixAcc xa;
+      mix_zero(xa);
+#pragma unroll 1
+      for (int md = 0; md < kNModes; ++md) {
+        if (md == 3 && S.pair32) continue;
+        const ModeCoef& C = S.md[md];
+        if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
+        const int sl = tape_slot(md);
+        mode_fwd_tape_mixed(D, S, C, Bn, W, xa, stabw, pcw, (md == 0 && S.pair32) ? &S.md[3] : nullptr,
+                            tcol + sl * kTapeF * kTileBins);
+        used |= 1u << sl;
       }
+      cdf x[3], od[3];
+      mix_final(xa, zw, x);
+      aet_from_xyz_dw(x, od);
+      double2 o[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) o[c] = make_double2(df_to(od[c].re) * S.ihsc, df_to(od[c].im) * S.ihsc);
       double2 sX, sY, sZ;
       bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
+      const double ih = S.ihsc;
+      const cdf wX = {df_from_bits(sX.x * ih), df_from_bits(sX.y * ih)};
+      const cdf wY = {df_from_bits(sY.x * ih), df_from_bits(sY.y * ih)};
+      const cdf wZ = {df_from_bits(sZ.x * ih), df_from_bits(sZ.y * ih)};
       GradAcc g;
       gacc_zero(g);
-      {
-        BinW W;
-        load_bin_w(D, b, W);
-        const float4 zz = D.zw[b];
-        const cdf zw = {df_make(zz.x, zz.y), df_make(zz.z, zz.w)};
-        const double ih = S.ihsc;
-        const cdf wX = {df_from_bits(sX.x * ih), df_from_bits(sX.y * ih)};
-        const cdf wY = {df_from_bits(sY.x * ih), df_from_bits(sY.y * ih)};
-        const cdf wZ = {df_from_bits(sZ.x * ih), df_from_bits(sZ.y * ih)};
-        GradAccW gw;
-        gaccw_zero(gw);
 #pragma unroll 1
-        for (int md = 0; md < kNModes; ++md) {
-          if (md == 3 && S.pair32) continue;
-          if (S.md[md].active && Bn.f < S.md[md].fend)
-            mode_bwd_mixed(D, S, SG, md, Bn, W, zw, wX, wY, wZ, g, gw, stabw, kpq, mow,
-                           (md == 0 && S.pair32) ? 3 : -1);
-        }
-        gaccw_flush(gw, g);
+      for (int md = 0; md < kNModes; ++md) {
+        if (md == 3 && S.pair32) continue;
+        const ModeCoef& C = S.md[md];
+        if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
+        mode_bwd_tape_mixed(D, S, SG, md, Bn, W, zw, wX, wY, wZ, g, pcw, tcol + tape_slot(md) * kTapeF * kTileBins,
+                            (md == 0 && S.pair32) ? 3 : -1);
       }
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { v[14 + i] = g.k[i]; v[17 + i] = g.p[i]; v[20 + i] = g.qv[i]; }
     }
-    // fixed-order block reduction
+#pragma unroll 1
+    for (int sl = 0; sl < kTapeSlots; ++sl)
+      if (!(used & (1u << sl))) tape_clear_dw(tcol + sl * kTapeF * kTileBins);
 #pragma unroll
-    for (int i = 0; i < kGradW; ++i)
+    for (int i = 0; i < kGradV; ++i)
       for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0)
 #pragma unroll
-      for (int i = 0; i < kGradW; ++i) sh[i][wid] = v[i];
+      for (int i = 0; i < kGradV; ++i) sh[i][wid] = v[i];
+    constexpr int kEnt = kTapeSlots * kTileBins;
+    if (threadIdx.x < 3 * kTapeSums) {
+      const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
+      const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
+      sums[q][j] = tape_sum_dw(tape, j, e0, e1, D.orbit != 0);
+    }
     __syncthreads();
-    if (threadIdx.x < kGradW) {
+    if (threadIdx.x < kGradV) {
       double a = sh[threadIdx.x][0];
       for (int w = 1; w < kTileBins / 32; ++w) a += sh[threadIdx.x][w];
       part[t * kGradW + threadIdx.x] = a;
+    } else if (threadIdx.x < kGradW) {
+      const int k = threadIdx.x - kGradV;
+      double pcb[kTapeSums];
+      for (int j = 0; j < kTapeSums; ++j) pcb[j] = sums[0][j] + sums[1][j] + sums[2][j];
+      part[t * kGradW + threadIdx.x] = tape_to_frame(D, pcb, k / 3, k % 3);
     }
   }
 }
@@ -216,7 +229,6 @@ __global__ void __launch_bounds__(kTileBins, 1) k_grad_fwd_mixed(DetSet ds, int 
 // cotangents in it, and the CTA contracts them with the orbit basis (42 sums over the tile's
 // 512 (bin, slot) entries, three threads per sum) and maps the sums to the sky frame. The 23
 // partials per tile are those of the recomputing kernel.
-constexpr int kGradV = 14;   // per-thread partials reduced by shuffles: dh[3], hh[3], M q c1 c2 dL io ph tc
 __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                              const SampleGrad* __restrict__ sgrad,
                                                              const int* __restrict__ nend,
@@ -440,7 +452,7 @@ cudaError_t launch_prep_grad(const double* theta, int B, unsigned mask, const De
 cudaError_t launch_grad_fwd(const DetSet& ds, int B, const SampleCoef* coef, const SampleGrad* sgrad, const int* nend,
                             const long long* off, double* part, int grid, bool mixed, double* tape, cudaStream_t st) {
   if (mixed)
-    k_grad_fwd_mixed<<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part);
+    k_grad_fwd_mixed<<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part, tape);
   else
     k_grad_fwd_tape<<<grid, kTileBins, 0, st>>>(ds, B, coef, sgrad, nend, off, part, tape);
   return pe::launch_status();

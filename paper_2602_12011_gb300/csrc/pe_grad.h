@@ -19,8 +19,8 @@ cudaError_t launch_fisher_fwd(const DetSet& ds, int B, const SampleCoef* coef, c
 cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, const double* part,
                                  const SampleCoef* coef, double* F, cudaStream_t st);
 int grad_partial_width();
-// FP64 gradient: resident CTAs per SM of its persistent kernel, and the doubles of tape each CTA
-// of its grid needs (launch_grad_fwd's tape holds grid x that many; unused in mixed precision)
+// Gradient: resident CTAs per SM of its persistent kernels, and the doubles of tape each CTA of
+// the grid needs (launch_grad_fwd's tape holds grid x that many)
 int grad_tape_ctas_per_sm();
 size_t grad_tape_doubles_per_cta();
 int fisher_partial_width();
