@@ -90,10 +90,10 @@ def test_grad_single_modes_and_tdi15(oracle_mod, Lb):
 
 def test_grad_mixed_precision_forward_pass(oracle_mod, Lb):
     """PE_PREC_MIXED on the gradient: each bin's forward mode sum (log L and the cotangents) comes
-    from the mixed-precision unit, and the reverse sweeps run with double-word geometry
-    (mode_bwd_tape_mixed, from a double-word tape). The oracle bars are the FP64 gradient's, on LISA (taper region included)
-    and TianQin (geocentric orbit); the result also stays within 1e-11 of the scale of the FP64
-    call's log L and gradient. PE_PREC_FP32 is refused."""
+    from the mixed-precision unit, and the reverse sweeps run with double-word geometry from a
+    double-word tape (mode_bwd_tape_mixed). The oracle bars are the FP64 gradient's, on LISA
+    (taper region included) and TianQin (geocentric orbit); the result also stays within 1e-11 of
+    the scale of the FP64 call's log L and gradient. PE_PREC_FP32 is refused."""
     T = 2.0 ** 17
     inj = _inj(T)
     ods, gds = _setup(oracle_mod, Lb, [(W.LISA, T)], inj)
