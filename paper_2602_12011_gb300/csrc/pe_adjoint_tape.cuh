@@ -208,12 +208,30 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
   }
 }
 
-// Reverse sweep of one unit from its tape. sX, sY, sZ: cotangents of the bin's brackets X', Y',
-// Z'. Accumulates the theta components reached per unit (Mtot, q, chi1, chi2, dL, iota, phi_c,
-// t_c) into g and writes the nine form cotangents to the slot's kTfb fields: links 0 and 1's
-// (k, p, q) projections, the two spacecraft-offset phases and the centre's Doppler term.
+// The bracket cotangents of one bin in the form the link sweeps use. Link l contributes
+// -G U to one bracket (cotangent sU) and +G V to the next (cotangent sV), U = s- + z s+,
+// V = s+ + z s-; with Su = -sU, Sv = sV: Gb = s- P_l + s+ Q_l, d/ds- = Re(G conj P_l),
+// d/ds+ = Re(G conj Q_l), where P_l = Su + Sv conj z and Q_l = Su conj z + Sv depend on the bin
+// only. Pairs: link 0 = (1,2): X' -G U, Y' +G V; link 1 = (2,3): Y', Z'; link 2 = (3,1): Z', X'.
+// Writes P_l, Q_l to pq[(2 l) * kTileBins], pq[(2 l + 1) * kTileBins].
+__device__ __forceinline__ void link_seeds(double2 sX, double2 sY, double2 sZ, double2 z, double2* pq) {
+  const double2 zc = make_double2(z.x, -z.y);
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const double2 su = (l == 0) ? sX : (l == 1 ? sY : sZ);
+    const double2 Sv = (l == 0) ? sY : (l == 1 ? sZ : sX);
+    const double2 Su = make_double2(-su.x, -su.y);
+    pq[2 * l * kTileBins] = cadd(Su, cmul(Sv, zc));
+    pq[(2 * l + 1) * kTileBins] = cadd(cmul(Su, zc), Sv);
+  }
+}
+
+// Reverse sweep of one unit from its tape. seeds: the bin's link seeds (link_seeds). Accumulates the
+// theta components reached per unit (Mtot, q, chi1, chi2, dL, iota, phi_c, t_c) into g and writes
+// the nine form cotangents to the slot's kTfb fields: links 0 and 1's (k, p, q) projections, the
+// two spacecraft-offset phases and the centre's Doppler term.
 __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef& S, const SampleGrad& SG, int md,
-                                              const BinIn& B, double2 sX, double2 sY, double2 sZ, GradAcc& g,
+                                              const BinIn& B, const double2* __restrict__ seeds, GradAcc& g,
                                               const double* __restrict__ pc, double* tp, int md2) {
   const ModeCoef& C = S.md[md];
   const ModeGrad& CG = SG.md[md];
@@ -237,15 +255,10 @@ __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef&
   double2 Apb = make_double2(0.0, 0.0), Acb = make_double2(0.0, 0.0);
   double thb[3];                    // cotangents of the spacecraft angles 2 pi (phase + theta_t)
   double krb[3], prb[3], qrb[3];    // cotangents of the unnormalised projections, per link
-  // seeds: pair 0 = (1,2): X' has -G U, Y' has +G V; pair 1 = (2,3): Y' -G U, Z' +G V;
-  //        pair 2 = (3,1): Z' -G U, X' +G V.
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int t = (l + 2) % 3;
-    double2 Su, Sv;
-    if (l == 0) { Su = make_double2(-sX.x, -sX.y); Sv = sY; }
-    else if (l == 1) { Su = make_double2(-sY.x, -sY.y); Sv = sZ; }
-    else { Su = make_double2(-sZ.x, -sZ.y); Sv = sX; }
+    const double2 P = seeds[2 * l * kTileBins], Q = seeds[(2 * l + 1) * kTileBins];
     const double* tl = tp + (kTL + 8 * l) * kTileBins;
     const double kn = tl[0], np = tl[kTileBins], nq = tl[2 * kTileBins], inv = tl[3 * kTileBins];
     const double sm = tl[4 * kTileBins], spl = tl[5 * kTileBins];
@@ -254,17 +267,12 @@ __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef&
     const double Fp = np * np - nq * nq, Fch = np * nq;
     const double2 gam = make_double2(fma(Ap.x, Fp, -Ac.y * Fch), fma(Ap.y, Fp, Ac.x * Fch));
     const double2 G = cmul(gam, E);
-    const double2 U = make_double2(fma(B.z.x, spl, sm), B.z.y * spl);
-    const double2 V = make_double2(fma(B.z.x, sm, spl), B.z.y * sm);
-    const double2 Gb = cadd(cconjmul(Su, U), cconjmul(Sv, V));
-    const double2 Ub = cconjmul(Su, G);
-    const double2 Vb = cconjmul(Sv, G);
-    const double smb = Ub.x + Vb.x * B.z.x + Vb.y * B.z.y;
-    const double splb = Ub.x * B.z.x + Ub.y * B.z.y + Vb.x;
+    const double2 Gb = make_double2(fma(sm, P.x, spl * Q.x), fma(sm, P.y, spl * Q.y));
+    const double smb = fma(G.x, P.x, G.y * P.y);
+    const double splb = fma(G.x, Q.x, G.y * Q.y);
     const double knb = fma(smb, dsm, splb * dspl);
     const double2 gamb = cconjmul(Gb, E);
-    const double2 Eb = cconjmul(Gb, gam);
-    thb[t] = E.x * Eb.y - E.y * Eb.x;
+    thb[t] = fma(Gb.y, G.x, -Gb.x * G.y);   // Im(Gb conj G): the angle's cotangent (G = gam E)
     // gam = Fp Ap + i Fch Ac
     Apb = make_double2(fma(gamb.x, Fp, Apb.x), fma(gamb.y, Fp, Apb.y));
     Acb = make_double2(fma(gamb.y, Fch, Acb.x), fma(-gamb.x, Fch, Acb.y));

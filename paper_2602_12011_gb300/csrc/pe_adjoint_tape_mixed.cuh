@@ -183,12 +183,26 @@ __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const Sampl
   }
 }
 
-// Reverse sweep of one unit from its double-word tape. sX, sY, sZ: the bracket cotangents times
-// ihsc; zw: the bin's z. Accumulates the theta components reached per unit into g (FP64) and writes
-// the nine form cotangents (double words) to the slot's kTfb fields, as mode_bwd_tape.
+// link_seeds in double words: sX, sY, sZ are the bracket cotangents times ihsc, zw the bin's z.
+__device__ __forceinline__ void link_seeds_dw(const cdf& sX, const cdf& sY, const cdf& sZ, const cdf& zw, cdf* seeds) {
+  const cdf zc = {zw.re, df_neg(zw.im)};
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const cdf& su = (l == 0) ? sX : (l == 1 ? sY : sZ);
+    const cdf& Sv = (l == 0) ? sY : (l == 1 ? sZ : sX);
+    const cdf Su = {df_neg(su.re), df_neg(su.im)};
+    const cdf a = cdfl_mul(Sv, zc), b = cdfl_mul(Su, zc);
+    seeds[2 * l * kTileBins] = cdf{dfl_add(Su.re, a.re), dfl_add(Su.im, a.im)};
+    seeds[(2 * l + 1) * kTileBins] = cdf{dfl_add(b.re, Sv.re), dfl_add(b.im, Sv.im)};
+  }
+}
+
+// Reverse sweep of one unit from its double-word tape. seeds: the bin's link seeds
+// (link_seeds_dw). Accumulates the theta components reached per unit into g (FP64) and writes the
+// nine form cotangents (double words) to the slot's kTfb fields, as mode_bwd_tape.
 __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const SampleCoef& S, const SampleGrad& SG,
-                                                    int md, const BinIn& B, const BinW& W, const cdf& zw,
-                                                    const cdf& sX, const cdf& sY, const cdf& sZ, GradAcc& g,
+                                                    int md, const BinIn& B, const BinW& W,
+                                                    const cdf* __restrict__ seeds, GradAcc& g,
                                                     const float2* __restrict__ pcw, df* tp, int md2) {
   const ModeCoef& C = S.md[md];
   const ModeGrad& CG = SG.md[md];
@@ -210,10 +224,8 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
   df f0k = zero, f0p = zero, f0q = zero, f1k = zero, f1p = zero, f1q = zero;   // link forms 0..5
 #pragma unroll 1
   for (int l = 0; l < 3; ++l) {
-    const cdf& su = (l == 0) ? sX : (l == 1 ? sY : sZ);
-    const cdf& Sv = (l == 0) ? sY : (l == 1 ? sZ : sX);
-    const cdf Su = {df_neg(su.re), df_neg(su.im)};
     const int t = (l == 0) ? 2 : l - 1;
+    const cdf P = seeds[2 * l * kTileBins], Q = seeds[(2 * l + 1) * kTileBins];
     const df* tl = tp + (kTL + 8 * l) * kTileBins;
     const df kn = tl[0], np = tl[kTileBins], nq = tl[2 * kTileBins], inv = tl[3 * kTileBins];
     const df sm = tl[4 * kTileBins], spl = tl[5 * kTileBins];
@@ -225,15 +237,12 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
                                      dfl_add(dfl_mul(Ap.im, Fp), dfl_mul(Ac.re, Fc))}
                                : cdf{dfl_mul(Ap.re, Fp), dfl_mul(Ac.re, Fc)};
     const cdf G = cdf_mul_s(gam, E);
-    const cdf U = {dfl_add(dfl_mul(zw.re, spl), sm), dfl_mul(zw.im, spl)};
-    const cdf V = {dfl_add(dfl_mul(zw.re, sm), spl), dfl_mul(zw.im, sm)};
-    const cdf Gb = cdf_add_s(cdf_mul_conj(Su, U), cdf_mul_conj(Sv, V));
-    const cdf Ub = cdf_mul_conj(Su, G), Vb = cdf_mul_conj(Sv, G);
-    const df smb = dfl_add(Ub.re, dfl_add(dfl_mul(Vb.re, zw.re), dfl_mul(Vb.im, zw.im)));
-    const df splb = dfl_add(dfl_add(dfl_mul(Ub.re, zw.re), dfl_mul(Ub.im, zw.im)), Vb.re);
+    const cdf Gb = {dfl_add(dfl_mul(sm, P.re), dfl_mul(spl, Q.re)), dfl_add(dfl_mul(sm, P.im), dfl_mul(spl, Q.im))};
+    const df smb = dfl_add(dfl_mul(G.re, P.re), dfl_mul(G.im, P.im));
+    const df splb = dfl_add(dfl_mul(G.re, Q.re), dfl_mul(G.im, Q.im));
     const df knb = dfl_add(dfl_mul(smb, dsm), dfl_mul(splb, dspl));
-    const cdf gamb = cdf_mul_conj(Gb, E), Eb = cdf_mul_conj(Gb, gam);
-    const df thb = dfl_sub(dfl_mul(E.re, Eb.im), dfl_mul(E.im, Eb.re));
+    const cdf gamb = cdf_mul_conj(Gb, E);
+    const df thb = dfl_sub(dfl_mul(Gb.im, G.re), dfl_mul(Gb.re, G.im));   // Im(Gb conj G)
     if (t == 0) th0b = dfl_add(th0b, thb);
     else if (t == 1) th1b = dfl_add(th1b, thb);
     else th2b = dfl_add(th2b, thb);

@@ -115,6 +115,31 @@ __device__ __forceinline__ void bracket_cotangents(const DetDev& D, int b, const
   *sZ = make_double2(bb[0].x + bb[1].x + bb[2].x, bb[0].y + bb[1].y + bb[2].y);
 }
 
+// Block sum of the kGradV per-thread partials, already stored in red[i][threadIdx.x], through
+// shared memory in a fixed order (block_sum6's scheme for 14 rows): thread t < 112 adds entries
+// g, g + 8, ..., g + 120 of row i = t / 8 (g = t % 8) into red[i][g]; thread i < 14 then adds
+// red[i][0..7] and returns the row's sum (other threads return 0). About 1,800 FP64 additions per
+// tile against ~9,000 for a shuffle tree over all lanes. The caller stores the partials and holds
+// the barrier before them.
+__device__ __forceinline__ double grad_block_sum(double (*red)[kTileBins + kRedPad]) {
+  __syncthreads();
+  if (threadIdx.x < kGradV * 8) {
+    const int i = threadIdx.x >> 3, g = threadIdx.x & 7;
+    double s = red[i][g];
+#pragma unroll
+    for (int k = 1; k < kTileBins / 8; ++k) s += red[i][g + 8 * k];
+    red[i][g] = s;   // only this thread touches column g of row i in this step
+  }
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < kGradV) {
+    s = red[threadIdx.x][0];
+#pragma unroll
+    for (int g = 1; g < 8; ++g) s += red[threadIdx.x][g];
+  }
+  return s;
+}
+
 // Mixed-precision gradient with a double-word tape (pe_adjoint_tape_mixed.cuh): per tile the
 // mixed-precision forward mode sum writes each unit's tape, the bracket cotangents are formed in
 // FP64 from the mode sum, the reverse sweeps read the tape, and the CTA contracts the form
@@ -125,8 +150,9 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int 
                                                               const long long* __restrict__ off, double* part,
                                                               double* tape_all) {
   df* tape = reinterpret_cast<df*>(tape_all + (size_t)blockIdx.x * kTapeDoubles);
-  __shared__ double sh[kGradV][kTileBins / 32];
+  __shared__ double red[kGradV][kTileBins + kRedPad];
   __shared__ float4 stabw[kSinTab];
+  __shared__ cdf lseed[6][kTileBins];   // each thread's link seeds P_l, Q_l (own column)
   __shared__ double pc[kProj];
   __shared__ float2 pcw[kProj];
   __shared__ double sums[3][kTapeSums];
@@ -181,6 +207,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int 
       const cdf wX = {df_from_bits(sX.x * ih), df_from_bits(sX.y * ih)};
       const cdf wY = {df_from_bits(sY.x * ih), df_from_bits(sY.y * ih)};
       const cdf wZ = {df_from_bits(sZ.x * ih), df_from_bits(sZ.y * ih)};
+      link_seeds_dw(wX, wY, wZ, zw, &lseed[0][threadIdx.x]);
       GradAcc g;
       gacc_zero(g);
 #pragma unroll 1
@@ -188,32 +215,25 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int 
         if (md == 3 && S.pair32) continue;
         const ModeCoef& C = S.md[md];
         if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
-        mode_bwd_tape_mixed(D, S, SG, md, Bn, W, zw, wX, wY, wZ, g, pcw, tcol + tape_slot(md) * kTapeF * kTileBins,
-                            (md == 0 && S.pair32) ? 3 : -1);
+        mode_bwd_tape_mixed(D, S, SG, md, Bn, W, &lseed[0][threadIdx.x], g, pcw,
+                            tcol + tape_slot(md) * kTapeF * kTileBins, (md == 0 && S.pair32) ? 3 : -1);
       }
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
     }
 #pragma unroll 1
     for (int sl = 0; sl < kTapeSlots; ++sl)
       if (!(used & (1u << sl))) tape_clear_dw(tcol + sl * kTapeF * kTileBins);
+    __syncthreads();   // the tape is complete; the previous tile's readers of red are done
 #pragma unroll
-    for (int i = 0; i < kGradV; ++i)
-      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-      for (int i = 0; i < kGradV; ++i) sh[i][wid] = v[i];
+    for (int i = 0; i < kGradV; ++i) red[i][threadIdx.x] = v[i];
     constexpr int kEnt = kTapeSlots * kTileBins;
     if (threadIdx.x < 3 * kTapeSums) {
       const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
       const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
       sums[q][j] = tape_sum_dw(tape, j, e0, e1, D.orbit != 0);
     }
-    __syncthreads();
+    const double a = grad_block_sum(red);
     if (threadIdx.x < kGradV) {
-      double a = sh[threadIdx.x][0];
-      for (int w = 1; w < kTileBins / 32; ++w) a += sh[threadIdx.x][w];
       part[t * kGradW + threadIdx.x] = a;
     } else if (threadIdx.x < kGradW) {
       const int k = threadIdx.x - kGradV;
@@ -235,8 +255,9 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
                                                              const long long* __restrict__ off, double* part,
                                                              double* tape_all) {
   double* tape = tape_all + (size_t)blockIdx.x * kTapeDoubles;   // [kTapeSlots][kTapeF][kTileBins]
-  __shared__ double sh[kGradV][kTileBins / 32];
+  __shared__ double red[kGradV][kTileBins + kRedPad];
   __shared__ double2 stab[kSinTab];
+  __shared__ double2 lseed[6][kTileBins];   // each thread's link seeds P_l, Q_l (own column)
   __shared__ double pc[kProj];
   __shared__ double sums[3][kTapeSums];
   for (int i = threadIdx.x; i < kSinTab; i += blockDim.x) stab[i] = ds.d[0].sct[i];
@@ -277,6 +298,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
       aet_from_xyz(x, o);
       double2 sX, sY, sZ;
       bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
+      link_seeds(sX, sY, sZ, Bn.z, &lseed[0][threadIdx.x]);
       GradAcc g;
       gacc_zero(g);
 #pragma unroll 1
@@ -284,32 +306,25 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
         if (md == 3 && S.pair32) continue;
         const ModeCoef& C = S.md[md];
         if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
-        mode_bwd_tape(D, S, SG, md, Bn, sX, sY, sZ, g, pc, tcol + tape_slot(md) * kTapeF * kTileBins,
-                      (md == 0 && S.pair32) ? 3 : -1);
+        mode_bwd_tape(D, S, SG, md, Bn, &lseed[0][threadIdx.x], g, pc,
+                      tcol + tape_slot(md) * kTapeF * kTileBins, (md == 0 && S.pair32) ? 3 : -1);
       }
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
     }
 #pragma unroll 1
     for (int sl = 0; sl < kTapeSlots; ++sl)
       if (!(used & (1u << sl))) tape_clear(tcol + sl * kTapeF * kTileBins);
+    __syncthreads();   // the tape is complete; the previous tile's readers of red are done
 #pragma unroll
-    for (int i = 0; i < kGradV; ++i)
-      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-      for (int i = 0; i < kGradV; ++i) sh[i][wid] = v[i];
+    for (int i = 0; i < kGradV; ++i) red[i][threadIdx.x] = v[i];
     constexpr int kEnt = kTapeSlots * kTileBins;
     if (threadIdx.x < 3 * kTapeSums) {
       const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
       const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
       sums[q][j] = tape_sum(tape, j, e0, e1, D.orbit != 0);
     }
-    __syncthreads();
+    const double a = grad_block_sum(red);
     if (threadIdx.x < kGradV) {
-      double a = sh[threadIdx.x][0];
-      for (int w = 1; w < kTileBins / 32; ++w) a += sh[threadIdx.x][w];
       part[t * kGradW + threadIdx.x] = a;
     } else if (threadIdx.x < kGradW) {
       const int k = threadIdx.x - kGradV;
