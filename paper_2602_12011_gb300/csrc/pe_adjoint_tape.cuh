@@ -208,21 +208,30 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
   }
 }
 
-// The bracket cotangents of one bin in the form the link sweeps use. Link l contributes
-// -G U to one bracket (cotangent sU) and +G V to the next (cotangent sV), U = s- + z s+,
-// V = s+ + z s-; with Su = -sU, Sv = sV: Gb = s- P_l + s+ Q_l, d/ds- = Re(G conj P_l),
-// d/ds+ = Re(G conj Q_l), where P_l = Su + Sv conj z and Q_l = Su conj z + Sv depend on the bin
-// only. Pairs: link 0 = (1,2): X' -G U, Y' +G V; link 1 = (2,3): Y', Z'; link 2 = (3,1): Z', X'.
+// The seeds of the link sweeps of one bin. Link l contributes -G U to one bracket (cotangent
+// sU) and +G V to the next (cotangent sV), U = s- + z s+, V = s+ + z s-; with Su = -sU:
+// Gb = s- P_l + s+ Q_l, d/ds- = Re(G conj P_l), d/ds+ = Re(G conj Q_l), where
+// P_l = Su + sV conj z and Q_l = Su conj z + sV depend on the bin only. Pairs: link 0 = (1,2):
+// X' and Y'; link 1 = (2,3): Y', Z'; link 2 = (3,1): Z', X'. From the A/E/T cotangents bb
+// (sX = -bA + bE + bT, sY = -2 bE + bT, sZ = bA + bE + bT) the differences sV - sU are bA - 3 bE,
+// bA + 3 bE and -2 bA: the T cotangent, which dwarfs the others at long wavelength (the T
+// channel's noise falls as a^4), cancels exactly, and with conj z - 1 = -2 sin a (sin a - i cos a)
+// P_l = (sV - sU) + sV (conj z - 1), Q_l = (sV - sU) - sU (conj z - 1). sa, ca: sin a, cos a.
 // Writes P_l, Q_l to pq[(2 l) * kTileBins], pq[(2 l + 1) * kTileBins].
-__device__ __forceinline__ void link_seeds(double2 sX, double2 sY, double2 sZ, double2 z, double2* pq) {
-  const double2 zc = make_double2(z.x, -z.y);
+__device__ __forceinline__ void link_seeds(const double2 bb[3], double sa, double ca, double2* pq) {
+  const double2 sX = make_double2(-bb[0].x + bb[1].x + bb[2].x, -bb[0].y + bb[1].y + bb[2].y);
+  const double2 sY = make_double2(-2.0 * bb[1].x + bb[2].x, -2.0 * bb[1].y + bb[2].y);
+  const double2 sZ = make_double2(bb[0].x + bb[1].x + bb[2].x, bb[0].y + bb[1].y + bb[2].y);
+  const double2 zm = make_double2(-2.0 * sa * sa, 2.0 * sa * ca);
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const double2 su = (l == 0) ? sX : (l == 1 ? sY : sZ);
-    const double2 Sv = (l == 0) ? sY : (l == 1 ? sZ : sX);
-    const double2 Su = make_double2(-su.x, -su.y);
-    pq[2 * l * kTileBins] = cadd(Su, cmul(Sv, zc));
-    pq[(2 * l + 1) * kTileBins] = cadd(cmul(Su, zc), Sv);
+    const double2 sU = (l == 0) ? sX : (l == 1 ? sY : sZ);
+    const double2 sV = (l == 0) ? sY : (l == 1 ? sZ : sX);
+    const double2 d = (l == 0) ? make_double2(bb[0].x - 3.0 * bb[1].x, bb[0].y - 3.0 * bb[1].y)
+                    : (l == 1) ? make_double2(bb[0].x + 3.0 * bb[1].x, bb[0].y + 3.0 * bb[1].y)
+                               : make_double2(-2.0 * bb[0].x, -2.0 * bb[0].y);
+    pq[2 * l * kTileBins] = cadd(d, cmul(sV, zm));
+    pq[(2 * l + 1) * kTileBins] = csub(d, cmul(sU, zm));
   }
 }
 

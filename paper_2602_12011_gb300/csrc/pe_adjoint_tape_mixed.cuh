@@ -183,26 +183,100 @@ __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const Sampl
   }
 }
 
-// link_seeds in double words: sX, sY, sZ are the bracket cotangents times ihsc, zw the bin's z.
-__device__ __forceinline__ void link_seeds_dw(const cdf& sX, const cdf& sY, const cdf& sZ, const cdf& zw, cdf* seeds) {
-  const cdf zc = {zw.re, df_neg(zw.im)};
+// Double-word copies of what the mode-level chain rule reads: the sample's PN coefficients and
+// their derivatives, the orbit rates, and per mode the PN factors and the derivatives of the
+// amplitude, v-scale and polarisation weights. Formed once per tile (one sample per tile) by
+// chain_fill; the mixed reverse sweep then runs its chain rule on the FP32 pipe.
+struct ChainW {
+  df Pdd[8], dPq[8], dPdq[8];
+  df Q6, dQ5q, dQ6q, dP3c1, dP4c1, dP3c2, dP4c2, dlnAdL;
+  df rate, geo_rate;   // pi rate_ht, pi geo_rate_ht (turns of the orbit angles per second, times 2 pi)
+  df mfac2[kNModes], mfac[kNModes], tffac[kNModes], lncm[kNModes];
+  df dlnAdM[kNModes], dlnAdq[kNModes], dcmdM[kNModes], dPpdi[kNModes], dPcdi[kNModes];
+};
+constexpr int kChainW = (int)(sizeof(ChainW) / sizeof(df));
+__device__ __forceinline__ double chain_value(const DetDev& D, const SampleCoef& S, const SampleGrad& SG, int i) {
+  if (i < 8) return S.Pdd[i];
+  if (i < 16) return SG.dP_dq[i - 8];
+  if (i < 24) return SG.dPd_dq[i - 16];
+  switch (i) {
+    case 24: return S.Q6;
+    case 25: return SG.dQ5_dq;
+    case 26: return SG.dQ6_dq;
+    case 27: return SG.dP3_dc1;
+    case 28: return SG.dP4_dc1;
+    case 29: return SG.dP3_dc2;
+    case 30: return SG.dP4_dc2;
+    case 31: return SG.dlnA_ddL;
+    case 32: return kPi * D.rate_ht;
+    case 33: return kPi * D.geo_rate_ht;
+    default: break;
+  }
+  const int k = (i - 34) / kNModes, md = (i - 34) % kNModes;
+  const ModeCoef& C = S.md[md];
+  const ModeGrad& G = SG.md[md];
+  switch (k) {
+    case 0: return 2.0 * C.mfac;
+    case 1: return C.mfac;
+    case 2: return C.tffac;
+    case 3: return C.lncm;
+    case 4: return G.dlnA_dM;
+    case 5: return G.dlnA_dq;
+    case 6: return G.dcm_dM;
+    case 7: return G.dPp_di;
+    default: return G.dPc_di;
+  }
+}
+// Every thread of the CTA calls this between barriers; entry i is formed by thread i.
+__device__ __forceinline__ void chain_fill(const DetDev& D, const SampleCoef& S, const SampleGrad& SG, ChainW* cw) {
+  if (threadIdx.x < kChainW) reinterpret_cast<df*>(cw)[threadIdx.x] = to_dw(chain_value(D, S, SG, threadIdx.x));
+}
+// Double-word accumulators of the theta components reached per unit (a bin's modes), converted to
+// FP64 once per bin.
+struct GradAccDW {
+  df M, q, c1, c2, dL, io, ph, tc;
+};
+__device__ __forceinline__ void gaccdw_zero(GradAccDW& a) {
+  a.M = a.q = a.c1 = a.c2 = a.dL = a.io = a.ph = a.tc = df_make(0.f, 0.f);
+}
+__device__ __forceinline__ void gaccdw_flush(const GradAccDW& a, GradAcc& g) {
+  g.M += df_to(a.M); g.q += df_to(a.q); g.c1 += df_to(a.c1); g.c2 += df_to(a.c2);
+  g.dL += df_to(a.dL); g.io += df_to(a.io); g.ph += df_to(a.ph); g.tc += df_to(a.tc);
+}
+
+// link_seeds in double words: bw are the A/E/T cotangents times ihsc, sa, ca the bin's sin a,
+// cos a (the T cotangent cancels from the differences exactly, as there).
+__device__ __forceinline__ void link_seeds_dw(const cdf bw[3], const df& sa, const df& ca, cdf* seeds) {
+  const cdf& bA = bw[0];
+  const cdf& bE = bw[1];
+  const cdf& bT = bw[2];
+  const cdf sX = {dfl_add(dfl_sub(bE.re, bA.re), bT.re), dfl_add(dfl_sub(bE.im, bA.im), bT.im)};
+  const cdf sY = {dfl_sub(bT.re, df_scale2(bE.re, 2.0f)), dfl_sub(bT.im, df_scale2(bE.im, 2.0f))};
+  const cdf sZ = {dfl_add(dfl_add(bA.re, bE.re), bT.re), dfl_add(dfl_add(bA.im, bE.im), bT.im)};
+  const df s2 = df_scale2(sa, 2.0f);
+  const cdf zm = {df_neg(dfl_mul(s2, sa)), dfl_mul(s2, ca)};
+  const df e3r = dfl_mul(bE.re, df_make(3.f, 0.f)), e3i = dfl_mul(bE.im, df_make(3.f, 0.f));
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const cdf& su = (l == 0) ? sX : (l == 1 ? sY : sZ);
-    const cdf& Sv = (l == 0) ? sY : (l == 1 ? sZ : sX);
-    const cdf Su = {df_neg(su.re), df_neg(su.im)};
-    const cdf a = cdfl_mul(Sv, zc), b = cdfl_mul(Su, zc);
-    seeds[2 * l * kTileBins] = cdf{dfl_add(Su.re, a.re), dfl_add(Su.im, a.im)};
-    seeds[(2 * l + 1) * kTileBins] = cdf{dfl_add(b.re, Sv.re), dfl_add(b.im, Sv.im)};
+    const cdf& sU = (l == 0) ? sX : (l == 1 ? sY : sZ);
+    const cdf& sV = (l == 0) ? sY : (l == 1 ? sZ : sX);
+    const cdf d = (l == 0) ? cdf{dfl_sub(bA.re, e3r), dfl_sub(bA.im, e3i)}
+                : (l == 1) ? cdf{dfl_add(bA.re, e3r), dfl_add(bA.im, e3i)}
+                           : cdf{df_scale2(bA.re, -2.0f), df_scale2(bA.im, -2.0f)};
+    const cdf a = cdfl_mul(sV, zm), c = cdfl_mul(sU, zm);
+    seeds[2 * l * kTileBins] = cdf{dfl_add(d.re, a.re), dfl_add(d.im, a.im)};
+    seeds[(2 * l + 1) * kTileBins] = cdf{dfl_sub(d.re, c.re), dfl_sub(d.im, c.im)};
   }
 }
 
 // Reverse sweep of one unit from its double-word tape. seeds: the bin's link seeds
-// (link_seeds_dw). Accumulates the theta components reached per unit into g (FP64) and writes the
-// nine form cotangents (double words) to the slot's kTfb fields, as mode_bwd_tape.
+// (link_seeds_dw); cw: the tile's ChainW; lnf3: ln(f)/3 of the bin as a double word. Accumulates
+// the theta components reached per unit into gw (double words; the taper's rare term into g) and
+// writes the nine form cotangents (double words) to the slot's kTfb fields, as mode_bwd_tape.
 __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const SampleCoef& S, const SampleGrad& SG,
                                                     int md, const BinIn& B, const BinW& W,
-                                                    const cdf* __restrict__ seeds, GradAcc& g,
+                                                    const cdf* __restrict__ seeds, const ChainW& cw, df lnf3,
+                                                    GradAccDW& gw, GradAcc& g,
                                                     const float2* __restrict__ pcw, df* tp, int md2) {
   const ModeCoef& C = S.md[md];
   const ModeGrad& CG = SG.md[md];
@@ -269,13 +343,13 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
     }
   }
   // spacecraft angles 2 pi (pf + e_t), e_2 = -(e_0 + e_1), e_t = (f/2) (form 6 + t)
-  const double phb = 2.0 * kPi * df_to(dfl_add(dfl_add(th0b, th1b), th2b));   // phase cotangent (turns)
+  const df phb = dfl_mul(dfl_add(dfl_add(th0b, th1b), th2b), df_make(6.28318548f, -1.74845553e-07f));   // turns
   const df pif = dfl_mul(W.f, df_make(3.1415927f, -8.742278e-08f));            // pi f
   df fb[9];
   fb[0] = f0k; fb[1] = f0p; fb[2] = f0q; fb[3] = f1k; fb[4] = f1p; fb[5] = f1q;
   fb[6] = dfl_mul(pif, dfl_sub(th0b, th2b));
   fb[7] = dfl_mul(pif, dfl_sub(th1b, th2b));
-  const df kxcb = df_from_bits(-B.f * phb);
+  const df kxcb = df_neg(dfl_mul(W.f, phb));
   fb[8] = kxcb;
   df obb[4];
 #pragma unroll
@@ -286,41 +360,40 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
     obb[m] = a;
   }
   const df co = tp[kTco * kTileBins], so = tp[kTso * kTileBins];
-  double tfb;
+  df tfb;
   if (D.orbit == 0) {
     const df cob = dfl_add(dfl_add(obb[2], dfl_mul(kxcb, pcw[55])),
                            df_scale2(dfl_add(dfl_mul(co, obb[0]), dfl_mul(so, obb[1])), 2.0f));
     const df sob = dfl_add(dfl_add(obb[3], dfl_mul(kxcb, pcw[56])),
                            df_scale2(dfl_sub(dfl_mul(co, obb[1]), dfl_mul(so, obb[0])), 2.0f));
-    tfb = kPi * D.rate_ht * df_to(dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob)));
+    tfb = dfl_mul(cw.rate, dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob)));
   } else {
     const df c0 = tp[kTob0 * kTileBins], s0 = tp[kTob1 * kTileBins];
     const df cob = dfl_mul(kxcb, pcw[55]), sob = dfl_mul(kxcb, pcw[56]);
-    tfb = kPi * D.geo_rate_ht * df_to(dfl_sub(dfl_mul(c0, obb[1]), dfl_mul(s0, obb[0]))) +
-          kPi * D.rate_ht * df_to(dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob)));
+    tfb = dfl_add(dfl_mul(cw.geo_rate, dfl_sub(dfl_mul(c0, obb[1]), dfl_mul(s0, obb[0]))),
+                  dfl_mul(cw.rate, dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob))));
   }
 #pragma unroll
   for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = fb[f];
-  // ---------------- mode level (FP64)
-  const double v = C.cm * B.f13;
-  const double iv = C.icm * B.fm13;
-  const double lnv = C.lncm + B.lnf3;
-  const double iv5 = C.icm5 * D.fm53[B.b];
-  g.ph = fma(phb, 2.0 * C.mfac, g.ph);          // d ph0/d phi_c = m/(2 pi)
-  g.tc = fma(-B.f, phb, g.tc);                   // frac(f t_c)
-  const double psib = -C.mfac * phb;
-  g.tc += tfb;                                   // t_f = t_c + (m/(12 pi f)) D(v)
-  const double Db = tfb * C.tffac * B.invf;
-  double vb = 0.0;
+  // ---------------- mode level, in double words (the taper's rare term in FP64)
+  const df iv = df_rcp(vw);
+  const df lnv = dfl_add(cw.lncm[md], lnf3);
+  const df iv2 = dfl_mul(iv, iv);
+  const df iv5 = dfl_mul(dfl_mul(iv2, iv2), iv);
+  gw.ph = dfl_add(gw.ph, dfl_mul(phb, cw.mfac2[md]));   // d ph0/d phi_c = m/(2 pi)
+  gw.tc = dfl_add(gw.tc, dfl_sub(tfb, dfl_mul(W.f, phb)));   // t_f = t_c + ..., frac(f t_c)
+  const df psib = df_neg(dfl_mul(cw.mfac[md], phb));
+  const df Db = dfl_mul(dfl_mul(tfb, cw.tffac[md]), W.invf);
+  df vb = df_make(0.f, 0.f);
   if (A.x != 0.0f) {
     // cotangent of the amplitude (times ihsc), then of ln amp
     const df ampb = dfl_add(dfl_add(dfl_mul(Apb.re, ap.re), dfl_mul(Apb.im, ap.im)),
                             dfl_add(dfl_mul(Acb.re, ac.re), dfl_mul(Acb.im, ac.im)));
-    const double lnAb = df_to(dfl_mul(ampb, A));
-    g.M = fma(lnAb, CG.dlnA_dM, g.M);
-    g.q = fma(lnAb, CG.dlnA_dq, g.q);
-    g.dL = fma(lnAb, SG.dlnA_ddL, g.dL);
-    vb = lnAb * double(C.p) * iv;
+    const df lnAb = dfl_mul(ampb, A);
+    gw.M = dfl_add(gw.M, dfl_mul(lnAb, cw.dlnAdM[md]));
+    gw.q = dfl_add(gw.q, dfl_mul(lnAb, cw.dlnAdq[md]));
+    gw.dL = dfl_add(gw.dL, dfl_mul(lnAb, cw.dlnAdL));
+    vb = dfl_mul(dfl_mulf(lnAb, (float)C.p), iv);
     if (dlt_pos(C.ftap, B.f)) {
       const double span = C.fend - C.ftap;
       const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
@@ -333,39 +406,48 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
       g.M = fma(zb * dz, CG.dfend_dM, g.M);
     }
   }
-  double ddpol = S.Pdd[7];
+  // Psi_PN(v), D(v): dPsi/dv = D/v, dD/dv = v^-5 ddpol / v + Q6 (2 + ln v)
+  df ddpol = cw.Pdd[7];
 #pragma unroll
-  for (int k = 6; k >= 0; --k) ddpol = fma(ddpol, v, S.Pdd[k]);
-  const double dv = df_to(tp[kTdv * kTileBins]);
-  vb += psib * dv * iv + Db * (iv5 * ddpol * iv + S.Q6 * (2.0 + lnv));
-  g.M = fma(vb * B.f13, CG.dcm_dM, g.M);
-  double pq = SG.dP_dq[7], dq = SG.dPd_dq[7];
+  for (int k = 6; k >= 0; --k) ddpol = dfl_add(dfl_mul(ddpol, vw), cw.Pdd[k]);
+  const df dv = tp[kTdv * kTileBins];
+  const df dDdv = dfl_add(dfl_mul(dfl_mul(iv5, ddpol), iv), dfl_mul(cw.Q6, dfl_add(df_make(2.f, 0.f), lnv)));
+  vb = dfl_add(vb, dfl_add(dfl_mul(dfl_mul(psib, dv), iv), dfl_mul(Db, dDdv)));
+  gw.M = dfl_add(gw.M, dfl_mul(dfl_mul(vb, W.f13), cw.dcmdM[md]));
+  // coefficient derivatives in q: Psi_q = v^-5 sum dP_k v^k + ln v (dQ5 + dQ6 v), D_q likewise
+  df pq = cw.dPq[7], dq = cw.dPdq[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) {
-    pq = fma(pq, v, SG.dP_dq[k]);
-    dq = fma(dq, v, SG.dPd_dq[k]);
+    pq = dfl_add(dfl_mul(pq, vw), cw.dPq[k]);
+    dq = dfl_add(dfl_mul(dq, vw), cw.dPdq[k]);
   }
-  const double psiq = fma(iv5, pq, lnv * fma(SG.dQ6_dq, v, SG.dQ5_dq));
-  const double Dq = fma(iv5, dq, fma(SG.dQ6_dq * v, 1.0 + lnv, SG.dQ5_dq));
-  g.q += psib * psiq + Db * Dq;
-  const double iv2 = iv * iv;
-  g.c1 += psib * (SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv) - Db * (2.0 * SG.dP3_dc1 * iv2 + SG.dP4_dc1 * iv);
-  g.c2 += psib * (SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv) - Db * (2.0 * SG.dP3_dc2 * iv2 + SG.dP4_dc2 * iv);
+  const df q6v = dfl_mul(cw.dQ6q, vw);
+  const df psiq = dfl_add(dfl_mul(iv5, pq), dfl_mul(lnv, dfl_add(q6v, cw.dQ5q)));
+  const df Dq = dfl_add(dfl_mul(iv5, dq), dfl_add(dfl_mul(q6v, dfl_add(df_make(1.f, 0.f), lnv)), cw.dQ5q));
+  gw.q = dfl_add(gw.q, dfl_add(dfl_mul(psib, psiq), dfl_mul(Db, Dq)));
+  // chi1, chi2 enter P3 (spin-orbit) and P4 (spin-spin): Psi += dP3 v^-2 + dP4 v^-1
+  const df pD2 = df_scale2(Db, 2.0f);
+  const df t1 = dfl_sub(psib, pD2), t2 = dfl_sub(psib, Db);   // psib - 2 Db (v^-2), psib - Db (v^-1)
+  gw.c1 = dfl_add(gw.c1, dfl_add(dfl_mul(dfl_mul(cw.dP3c1, iv2), t1), dfl_mul(dfl_mul(cw.dP4c1, iv), t2)));
+  gw.c2 = dfl_add(gw.c2, dfl_add(dfl_mul(dfl_mul(cw.dP3c2, iv2), t1), dfl_mul(dfl_mul(cw.dP4c2, iv), t2)));
   // polarisation weights: cotangents of ap, ac are A Apb, A Acb (true scale)
-  const double apbx = df_to(dfl_mul(A, Apb.re)), acbx = df_to(dfl_mul(A, Acb.re));
-  g.io += apbx * CG.dPp_di + acbx * CG.dPc_di;
+  const df apbx = dfl_mul(A, Apb.re), acbx = dfl_mul(A, Acb.re);
+  gw.io = dfl_add(gw.io, dfl_add(dfl_mul(apbx, cw.dPpdi[md]), dfl_mul(acbx, cw.dPcdi[md])));
   if (md2 >= 0) {
-    const ModeGrad& CG2 = SG.md[md2];
-    const double apby = df_to(dfl_mul(A, Apb.im)), acby = df_to(dfl_mul(A, Acb.im));
-    const double Pp2 = S.md[md2].Pp, Pc2 = S.md[md2].Pc;
-    const double2 kap = make_double2(S.k32.x * v * v, S.k32.y * v * v);
-    g.io += (apbx * kap.x + apby * kap.y) * CG2.dPp_di + (acbx * kap.x + acby * kap.y) * CG2.dPc_di;
-    const double2 kb = make_double2(apbx * Pp2 + acbx * Pc2, apby * Pp2 + acby * Pc2);   // kappa-bar
-    const double lnrb = v * v * (kb.x * S.k32.x + kb.y * S.k32.y);
-    g.M = fma(lnrb, CG2.dlnA_dM - CG.dlnA_dM, g.M);
-    g.q = fma(lnrb, CG2.dlnA_dq - CG.dlnA_dq, g.q);
-    const double vkb = 2.0 * lnrb / v;
-    g.M = fma(vkb * B.f13, CG.dcm_dM, g.M);
+    const df apby = dfl_mul(A, Apb.im), acby = dfl_mul(A, Acb.im);
+    const df v2 = dfl_mul(vw, vw);
+    const cdf kap = {dfl_mul(S.k32w[0], v2), dfl_mul(S.k32w[1], v2)};
+    const ModeCoef& C2 = S.md[md2];
+    gw.io = dfl_add(gw.io, dfl_add(dfl_mul(dfl_add(dfl_mul(apbx, kap.re), dfl_mul(apby, kap.im)), cw.dPpdi[md2]),
+                                   dfl_mul(dfl_add(dfl_mul(acbx, kap.re), dfl_mul(acby, kap.im)), cw.dPcdi[md2])));
+    const cdf kb = {dfl_add(dfl_mul(apbx, C2.Ppw), dfl_mul(acbx, C2.Pcw)),
+                    dfl_add(dfl_mul(apby, C2.Ppw), dfl_mul(acby, C2.Pcw))};   // kappa-bar
+    // kappa = k32 v^2; only ln(amp2 / amp1) varies with theta (M, q)
+    const df lnrb = dfl_mul(v2, dfl_add(dfl_mul(kb.re, S.k32w[0]), dfl_mul(kb.im, S.k32w[1])));
+    gw.M = dfl_add(gw.M, dfl_mul(lnrb, dfl_sub(cw.dlnAdM[md2], cw.dlnAdM[md])));
+    gw.q = dfl_add(gw.q, dfl_mul(lnrb, dfl_sub(cw.dlnAdq[md2], cw.dlnAdq[md])));
+    // d kappa / d v = 2 kappa / v
+    gw.M = dfl_add(gw.M, dfl_mul(dfl_mul(df_scale2(dfl_mul(lnrb, iv), 2.0f), W.f13), cw.dcmdM[md]));
   }
 }
 

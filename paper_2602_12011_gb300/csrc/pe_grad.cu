@@ -96,12 +96,12 @@ __device__ __forceinline__ int find_pair_g(const long long* off, int P, long lon
   return lo;
 }
 
-// Cotangents of the three brackets from the per-channel sums of one bin:
-//   L_c = Re(dg_c B_c) - gg_c |B_c|^2 / 2  =>  Bbar_c = (dg.x - gg B.x, -dg.y - gg B.y),
-//   B_A = Z' - X', B_E = X' - 2Y' + Z', B_T = X' + Y' + Z'.
-__device__ __forceinline__ void bracket_cotangents(const DetDev& D, int b, const double2 o[3], double v6[6],
-                                                   double2* sX, double2* sY, double2* sZ) {
-  double2 bb[3];
+// Cotangents of the A/E/T sums of one bin, and the bin's likelihood terms:
+//   L_c = Re(dg_c B_c) - gg_c |B_c|^2 / 2  =>  Bbar_c = (dg.x - gg B.x, -dg.y - gg B.y).
+// (The brackets' cotangents follow from B_A = Z' - X', B_E = X' - 2Y' + Z', B_T = X' + Y' + Z';
+// link_seeds forms what the link sweeps need from them.)
+__device__ __forceinline__ void aet_cotangents(const DetDev& D, int b, const double2 o[3], double v6[6],
+                                               double2 bb[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const double2 g = D.dg[c * D.nb + b];
@@ -110,9 +110,6 @@ __device__ __forceinline__ void bracket_cotangents(const DetDev& D, int b, const
     v6[3 + c] += w * (o[c].x * o[c].x + o[c].y * o[c].y);
     bb[c] = make_double2(g.x - w * o[c].x, -g.y - w * o[c].y);
   }
-  *sX = make_double2(-bb[0].x + bb[1].x + bb[2].x, -bb[0].y + bb[1].y + bb[2].y);
-  *sY = make_double2(-2.0 * bb[1].x + bb[2].x, -2.0 * bb[1].y + bb[2].y);
-  *sZ = make_double2(bb[0].x + bb[1].x + bb[2].x, bb[0].y + bb[1].y + bb[2].y);
 }
 
 // Block sum of the kGradV per-thread partials, already stored in red[i][threadIdx.x], through
@@ -142,8 +139,9 @@ __device__ __forceinline__ double grad_block_sum(double (*red)[kTileBins + kRedP
 
 // Mixed-precision gradient with a double-word tape (pe_adjoint_tape_mixed.cuh): per tile the
 // mixed-precision forward mode sum writes each unit's tape, the bracket cotangents are formed in
-// FP64 from the mode sum, the reverse sweeps read the tape, and the CTA contracts the form
-// cotangents in double words. The 23 partials per tile are the FP64 kernel's.
+// FP64 from the mode sum, the reverse sweeps read the tape and run in double words (their theta
+// components return to FP64 once per bin), and the CTA contracts the form cotangents in double
+// words. The 23 partials per tile are the FP64 kernel's.
 __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                               const SampleGrad* __restrict__ sgrad,
                                                               const int* __restrict__ nend,
@@ -153,6 +151,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int 
   __shared__ double red[kGradV][kTileBins + kRedPad];
   __shared__ float4 stabw[kSinTab];
   __shared__ cdf lseed[6][kTileBins];   // each thread's link seeds P_l, Q_l (own column)
+  __shared__ ChainW cw;                  // the tile's chain-rule coefficients as double words
   __shared__ double pc[kProj];
   __shared__ float2 pcw[kProj];
   __shared__ double sums[3][kTapeSums];
@@ -169,6 +168,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int 
     const DetDev& D = ds.d[I];
     proj_prologue(D, coef[s], pc);
     if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
+    chain_fill(D, coef[s], sgrad[s], &cw);
     __syncthreads();
     double v[kGradV];
 #pragma unroll
@@ -201,23 +201,27 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int 
       double2 o[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) o[c] = make_double2(df_to(od[c].re) * S.ihsc, df_to(od[c].im) * S.ihsc);
-      double2 sX, sY, sZ;
-      bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
+      double2 bb[3];
+      aet_cotangents(D, b, o, v, bb);
       const double ih = S.ihsc;
-      const cdf wX = {df_from_bits(sX.x * ih), df_from_bits(sX.y * ih)};
-      const cdf wY = {df_from_bits(sY.x * ih), df_from_bits(sY.y * ih)};
-      const cdf wZ = {df_from_bits(sZ.x * ih), df_from_bits(sZ.y * ih)};
-      link_seeds_dw(wX, wY, wZ, zw, &lseed[0][threadIdx.x]);
+      cdf bw[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) bw[c] = cdf{df_from_bits(bb[c].x * ih), df_from_bits(bb[c].y * ih)};
+      link_seeds_dw(bw, W.sa, W.ca, &lseed[0][threadIdx.x]);
+      const df lnf3 = df_from_bits(Bn.lnf3);
       GradAcc g;
       gacc_zero(g);
+      GradAccDW gw;
+      gaccdw_zero(gw);
 #pragma unroll 1
       for (int md = 0; md < kNModes; ++md) {
         if (md == 3 && S.pair32) continue;
         const ModeCoef& C = S.md[md];
         if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
-        mode_bwd_tape_mixed(D, S, SG, md, Bn, W, &lseed[0][threadIdx.x], g, pcw,
+        mode_bwd_tape_mixed(D, S, SG, md, Bn, W, &lseed[0][threadIdx.x], cw, lnf3, gw, g, pcw,
                             tcol + tape_slot(md) * kTapeF * kTileBins, (md == 0 && S.pair32) ? 3 : -1);
       }
+      gaccdw_flush(gw, g);
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
     }
 #pragma unroll 1
@@ -296,9 +300,9 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
       double2 x[3], o[3];
       xyz_final(xa, Bn.z, x);
       aet_from_xyz(x, o);
-      double2 sX, sY, sZ;
-      bracket_cotangents(D, b, o, v, &sX, &sY, &sZ);
-      link_seeds(sX, sY, sZ, Bn.z, &lseed[0][threadIdx.x]);
+      double2 bb[3];
+      aet_cotangents(D, b, o, v, bb);
+      link_seeds(bb, Bn.sa, Bn.ca, &lseed[0][threadIdx.x]);
       GradAcc g;
       gacc_zero(g);
 #pragma unroll 1
