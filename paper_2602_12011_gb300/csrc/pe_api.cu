@@ -629,9 +629,9 @@ pe_status pe_loglike_grad_batch(const pe_detector* dets, int ndet, const double*
   if (h_stat) PE_CUDA(sc.alloc(&stat, B));
   PE_CUDA(pe::launch_prep_grad(th, B, mode_mask, ds, coef, sg, nend, stat, st));
   PE_CUDA(pe::launch_scan_tiles(nend, P, off, pe::kTileBins, st));
-  // a persistent grid of two CTAs per SM, each with its tape region
-  const long long g =
-      std::max<long long>(1, std::min<long long>(max_tiles, (long long)sm_count() * pe::grad_tape_ctas_per_sm()));
+  // a persistent grid of the kernel's resident CTAs per SM, each with its tape region
+  const long long g = std::max<long long>(
+      1, std::min<long long>(max_tiles, (long long)sm_count() * pe::grad_tape_ctas_per_sm(mixed)));
   double* tape = nullptr;
   PE_CUDA(sc.alloc(&tape, (size_t)g * pe::grad_tape_doubles_per_cta()));
   void* prof = nullptr;

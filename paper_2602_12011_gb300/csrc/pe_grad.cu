@@ -3,7 +3,7 @@
 // Sec. 2.3), built on the hand-written reverse sweep in pe_adjoint.cuh:
 //   k_prep_grad     per-sample coefficients (values) plus their derivatives in theta, the
 //                   latter by device dual numbers over the 11 parameters
-//   k_grad_fwd_tape FP64, persistent, two 128-thread CTAs per SM: per bin the forward mode sum
+//   k_grad_fwd_tape FP64, persistent, two 128-thread CTAs per SM (mixed: three): per bin the forward mode sum
 //                   writing each unit's tape (the CTA's region of global memory), the cotangents of the A/E/T
 //                   sums dL/dB_c = conj(dg_c) - gg_c B_c, one reverse sweep per mode from the
 //                   tape, and per tile the contraction of the form cotangents (pe_adjoint_tape.cuh)
@@ -142,7 +142,7 @@ __device__ __forceinline__ double grad_block_sum(double (*red)[kTileBins + kRedP
 // FP64 from the mode sum, the reverse sweeps read the tape and run in double words (their theta
 // components return to FP64 once per bin), and the CTA contracts the form cotangents in double
 // words. The 23 partials per tile are the FP64 kernel's.
-__global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_mixed(DetSet ds, int B, const SampleCoef* __restrict__ coef,
+__global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int B, const SampleCoef* __restrict__ coef,
                                                               const SampleGrad* __restrict__ sgrad,
                                                               const int* __restrict__ nend,
                                                               const long long* __restrict__ off, double* part,
@@ -495,7 +495,10 @@ cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, 
   return pe::launch_status();
 }
 int grad_partial_width() { return kGradW; }
-int grad_tape_ctas_per_sm() { return 2; }
+// FP64: two CTAs per SM (252 registers, no spills); mixed: three (168 registers, a few hundred
+// bytes of spills), which its latency-bound sweep prefers (33.6k against 30.9k grad evals/s with
+// two, 33.0k with four)
+int grad_tape_ctas_per_sm(bool mixed) { return mixed ? 3 : 2; }
 size_t grad_tape_doubles_per_cta() { return (size_t)kTapeDoubles; }
 int fisher_partial_width() { return kFisherW; }
 

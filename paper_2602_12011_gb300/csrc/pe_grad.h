@@ -21,7 +21,7 @@ cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, 
 int grad_partial_width();
 // Gradient: resident CTAs per SM of its persistent kernels, and the doubles of tape each CTA of
 // the grid needs (launch_grad_fwd's tape holds grid x that many)
-int grad_tape_ctas_per_sm();
+int grad_tape_ctas_per_sm(bool mixed);
 size_t grad_tape_doubles_per_cta();
 int fisher_partial_width();
 
