@@ -14,11 +14,33 @@
 
 namespace pe {
 
+// Tape accesses with an L2 eviction-priority hint: the tape's lines are written and read back
+// within one tile, while the per-bin tables stream past them, so they are marked to be evicted
+// last (createpolicy.fractional.L2::evict_last; a hint only, no lasting state).
+__device__ __forceinline__ unsigned long long tape_l2_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void tst(df* a, df v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(__cvta_generic_to_global(a)), "f"(v.x),
+               "f"(v.y), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ df tld(const df* a, unsigned long long pol) {
+  df v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(v.x), "=f"(v.y)
+               : "l"(__cvta_generic_to_global(a)), "l"(pol)
+               : "memory");
+  return v;
+}
+
 // Forward pass of one unit: mode_bin_mixed plus the tape and the sincs' derivatives in k.n.
 __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const SampleCoef& S, const ModeCoef& C,
                                                     const BinIn& B, const BinW& W, MixAcc& acc,
                                                     const float4* __restrict__ tab, const float2* __restrict__ pcw,
-                                                    const ModeCoef* C2, df* tp) {
+                                                    const ModeCoef* C2, df* tp, unsigned long long pol) {
   const double v = C.cm * B.f13;
   const double lnv = C.lncm + B.lnf3;
   const double iv5 = C.icm5 * D.fm53[B.b];
@@ -51,14 +73,14 @@ __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const Sampl
     A = dfl_mul(A, vw);
     if (C.p >= 2) A = dfl_mul(A, vw);
   }
-  tp[kTamp0 * kTileBins] = A;
+  tst(tp + (kTamp0 * kTileBins), A, pol);
   if (dlt_pos(C.ftap, B.f)) {
     const double span = C.fend - C.ftap;
     const double zt = span / (C.fend - B.f) - span / (B.f - C.ftap);
     A = dfl_mul(A, df_from_bits((zt > 700.0) ? 0.0 : 1.0 / (1.0 + exp(zt))));
   }
-  tp[kTw * kTileBins] = A;
-  tp[kTdv * kTileBins] = dv;
+  tst(tp + (kTw * kTileBins), A, pol);
+  tst(tp + (kTdv * kTileBins), dv, pol);
   cdf Ap = {dfl_mul(A, C.Ppw), df_make(0.f, 0.f)}, Ac = {dfl_mul(A, C.Pcw), df_make(0.f, 0.f)};
   if (C2) {
     const df v2 = dfl_mul(vw, vw);
@@ -82,10 +104,10 @@ __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const Sampl
     ob[1] = e0.im;
     ob[2] = ob[3] = df_make(0.f, 0.f);
   }
-  tp[kTco * kTileBins] = co;
-  tp[kTso * kTileBins] = so;
-  tp[kTob0 * kTileBins] = ob[0];
-  tp[kTob1 * kTileBins] = ob[1];
+  tst(tp + (kTco * kTileBins), co, pol);
+  tst(tp + (kTso * kTileBins), so, pol);
+  tst(tp + (kTob0 * kTileBins), ob[0], pol);
+  tst(tp + (kTob1 * kTileBins), ob[1], pol);
   const df e0 = df_scale2(dfl_mul(W.f, dw_dot5(pcw + 45, ob)), 0.5f);
   const df e1 = df_scale2(dfl_mul(W.f, dw_dot5(pcw + 50, ob)), 0.5f);
   const df e01 = dfl_add(e0, e1);
@@ -117,8 +139,8 @@ __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const Sampl
                        : cdf{dfl_mul(Ap.re, Fp), dfl_mul(Ac.re, Fc)};
     const int t = (l == 0) ? 2 : l - 1;   // third spacecraft
     const cdf Et = df_cis_turns(l == 0 ? dfl_sub(pf, e01) : dfl_add(pf, l == 1 ? e0 : e1), tab);
-    tp[(kTE + 2 * t) * kTileBins] = Et.re;
-    tp[(kTE + 2 * t + 1) * kTileBins] = Et.im;
+    tst(tp + ((kTE + 2 * t) * kTileBins), Et.re, pol);
+    tst(tp + ((kTE + 2 * t + 1) * kTileBins), Et.im, pol);
     G[l] = cdfl_mul(gam, Et);
     // sincs, and their derivatives in kn: d s-/dkn = -a sinc'(u1), d s+/dkn = a sinc'(u2)
     const df akn = dfl_mul(W.a, kn);
@@ -164,14 +186,14 @@ __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const Sampl
       }
     }
     df* tl = tp + (kTL + 8 * l) * kTileBins;
-    tl[0] = kn;
-    tl[kTileBins] = np;
-    tl[2 * kTileBins] = nq;
-    tl[3 * kTileBins] = inv;
-    tl[4 * kTileBins] = smv[l];
-    tl[5 * kTileBins] = spv[l];
-    tl[6 * kTileBins] = df_neg(dfl_mul(W.a, dsm));
-    tl[7 * kTileBins] = dfl_mul(W.a, dspl);
+    tst(tl + (0), kn, pol);
+    tst(tl + (kTileBins), np, pol);
+    tst(tl + (2 * kTileBins), nq, pol);
+    tst(tl + (3 * kTileBins), inv, pol);
+    tst(tl + (4 * kTileBins), smv[l], pol);
+    tst(tl + (5 * kTileBins), spv[l], pol);
+    tst(tl + (6 * kTileBins), df_neg(dfl_mul(W.a, dsm)), pol);
+    tst(tl + (7 * kTileBins), dfl_mul(W.a, dspl), pol);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -277,11 +299,12 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
                                                     int md, const BinIn& B, const BinW& W,
                                                     const cdf* __restrict__ seeds, const ChainW& cw, df lnf3,
                                                     GradAccDW& gw, GradAcc& g,
-                                                    const float2* __restrict__ pcw, df* tp, int md2) {
+                                                    const float2* __restrict__ pcw, df* tp, int md2,
+                                                    unsigned long long pol) {
   const ModeCoef& C = S.md[md];
   const ModeGrad& CG = SG.md[md];
   const df zero = df_make(0.f, 0.f);
-  const df A0 = tp[kTamp0 * kTileBins], A = tp[kTw * kTileBins];
+  const df A0 = tld(tp + (kTamp0 * kTileBins), pol), A = tld(tp + (kTw * kTileBins), pol);
   // polarisation weights without the amplitude, as the forward pass forms them
   const df vw = dfl_mul(C.cmw, W.f13);
   cdf ap = {C.Ppw, zero}, ac = {C.Pcw, zero};
@@ -301,10 +324,11 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
     const int t = (l == 0) ? 2 : l - 1;
     const cdf P = seeds[2 * l * kTileBins], Q = seeds[(2 * l + 1) * kTileBins];
     const df* tl = tp + (kTL + 8 * l) * kTileBins;
-    const df kn = tl[0], np = tl[kTileBins], nq = tl[2 * kTileBins], inv = tl[3 * kTileBins];
-    const df sm = tl[4 * kTileBins], spl = tl[5 * kTileBins];
-    const df dsm = tl[6 * kTileBins], dspl = tl[7 * kTileBins];
-    const cdf E = {tp[(kTE + 2 * t) * kTileBins], tp[(kTE + 2 * t + 1) * kTileBins]};
+    const df kn = tld(tl, pol), np = tld(tl + kTileBins, pol);
+    const df nq = tld(tl + 2 * kTileBins, pol), inv = tld(tl + 3 * kTileBins, pol);
+    const df sm = tld(tl + (4 * kTileBins), pol), spl = tld(tl + (5 * kTileBins), pol);
+    const df dsm = tld(tl + (6 * kTileBins), pol), dspl = tld(tl + (7 * kTileBins), pol);
+    const cdf E = {tld(tp + ((kTE + 2 * t) * kTileBins), pol), tld(tp + ((kTE + 2 * t + 1) * kTileBins), pol)};
     const df Fp = dfl_sub(dfl_mul(np, np), dfl_mul(nq, nq));
     const df Fc = df_scale2(dfl_mul(np, nq), 2.0f);
     const cdf gam = (md2 >= 0) ? cdf{dfl_sub(dfl_mul(Ap.re, Fp), dfl_mul(Ac.im, Fc)),
@@ -359,7 +383,7 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
     for (int f = 0; f < 6; ++f) a = dfl_add(a, dfl_mul(fb[f], pcw[5 * f + m]));
     obb[m] = a;
   }
-  const df co = tp[kTco * kTileBins], so = tp[kTso * kTileBins];
+  const df co = tld(tp + (kTco * kTileBins), pol), so = tld(tp + (kTso * kTileBins), pol);
   df tfb;
   if (D.orbit == 0) {
     const df cob = dfl_add(dfl_add(obb[2], dfl_mul(kxcb, pcw[55])),
@@ -368,13 +392,13 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
                            df_scale2(dfl_sub(dfl_mul(co, obb[1]), dfl_mul(so, obb[0])), 2.0f));
     tfb = dfl_mul(cw.rate, dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob)));
   } else {
-    const df c0 = tp[kTob0 * kTileBins], s0 = tp[kTob1 * kTileBins];
+    const df c0 = tld(tp + (kTob0 * kTileBins), pol), s0 = tld(tp + (kTob1 * kTileBins), pol);
     const df cob = dfl_mul(kxcb, pcw[55]), sob = dfl_mul(kxcb, pcw[56]);
     tfb = dfl_add(dfl_mul(cw.geo_rate, dfl_sub(dfl_mul(c0, obb[1]), dfl_mul(s0, obb[0]))),
                   dfl_mul(cw.rate, dfl_sub(dfl_mul(co, sob), dfl_mul(so, cob))));
   }
 #pragma unroll
-  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = fb[f];
+  for (int f = 0; f < 9; ++f) tst(tp + ((kTfb + f) * kTileBins), fb[f], pol);
   // ---------------- mode level, in double words (the taper's rare term in FP64)
   const df iv = df_rcp(vw);
   const df lnv = dfl_add(cw.lncm[md], lnf3);
@@ -410,7 +434,7 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
   df ddpol = cw.Pdd[7];
 #pragma unroll
   for (int k = 6; k >= 0; --k) ddpol = dfl_add(dfl_mul(ddpol, vw), cw.Pdd[k]);
-  const df dv = tp[kTdv * kTileBins];
+  const df dv = tld(tp + (kTdv * kTileBins), pol);
   const df dDdv = dfl_add(dfl_mul(dfl_mul(iv5, ddpol), iv), dfl_mul(cw.Q6, dfl_add(df_make(2.f, 0.f), lnv)));
   vb = dfl_add(vb, dfl_add(dfl_mul(dfl_mul(psib, dv), iv), dfl_mul(Db, dDdv)));
   gw.M = dfl_add(gw.M, dfl_mul(dfl_mul(vb, W.f13), cw.dcmdM[md]));
@@ -452,18 +476,19 @@ __device__ __forceinline__ void mode_bwd_tape_mixed(const DetDev& D, const Sampl
 }
 
 // Zeroes the contraction fields of a slot no unit used at this bin (double-word tape).
-__device__ __forceinline__ void tape_clear_dw(df* tp) {
+__device__ __forceinline__ void tape_clear_dw(df* tp, unsigned long long pol) {
   const df z = df_make(0.f, 0.f);
-  tp[kTco * kTileBins] = z;
-  tp[kTso * kTileBins] = z;
-  tp[kTob0 * kTileBins] = z;
-  tp[kTob1 * kTileBins] = z;
+  tst(tp + (kTco * kTileBins), z, pol);
+  tst(tp + (kTso * kTileBins), z, pol);
+  tst(tp + (kTob0 * kTileBins), z, pol);
+  tst(tp + (kTob1 * kTileBins), z, pol);
 #pragma unroll
-  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = z;
+  for (int f = 0; f < 9; ++f) tst(tp + ((kTfb + f) * kTileBins), z, pol);
 }
 
 // tape_sum on the double-word tape, in double words; the result returns to FP64.
-__device__ __forceinline__ double tape_sum_dw(const df* tape, int j, int e0, int e1, bool geo) {
+__device__ __forceinline__ double tape_sum_dw(const df* tape, int j, int e0, int e1, bool geo,
+                                              unsigned long long pol) {
   int f, m;
   if (j < 30) { f = j / 5; m = j % 5; }
   else if (j < 40) { f = 6 + (j - 30) / 5; m = (j - 30) % 5; }
@@ -477,8 +502,8 @@ __device__ __forceinline__ double tape_sum_dw(const df* tape, int j, int e0, int
     e = e0 + (e >= len ? e - len : e);
     const int slot = e >> 7, th = e & (kTileBins - 1);
     const df* col = tape + slot * kTapeF * kTileBins + th;
-    const df fv = col[(kTfb + f) * kTileBins];
-    return (m == 4) ? dfl_add(a, fv) : dfl_add(a, dfl_mul(fv, col[bf * kTileBins]));
+    const df fv = tld(col + ((kTfb + f) * kTileBins), pol);
+    return (m == 4) ? dfl_add(a, fv) : dfl_add(a, dfl_mul(fv, tld(col + (bf * kTileBins), pol)));
   };
   df a0 = df_make(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
   int i = 0;

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int 
   const int P = ds.ndet * B;
   const long long total = off[P];
   df* tcol = tape + threadIdx.x;
+  const unsigned long long pol = tape_l2_policy();
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair_g(off, P, t);
     if (!PE_CHK(p >= 0 && p < P && off[p + 1] <= total && nend[p] <= ds.d[p / B].nb, 16)) continue;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int 
         if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
         const int sl = tape_slot(md);
         mode_fwd_tape_mixed(D, S, C, Bn, W, xa, stabw, pcw, (md == 0 && S.pair32) ? &S.md[3] : nullptr,
-                            tcol + sl * kTapeF * kTileBins);
+                            tcol + sl * kTapeF * kTileBins, pol);
         used |= 1u << sl;
       }
       cdf x[3], od[3];
@@ -219,14 +220,14 @@ __global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int 
         const ModeCoef& C = S.md[md];
         if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
         mode_bwd_tape_mixed(D, S, SG, md, Bn, W, &lseed[0][threadIdx.x], cw, lnf3, gw, g, pcw,
-                            tcol + tape_slot(md) * kTapeF * kTileBins, (md == 0 && S.pair32) ? 3 : -1);
+                            tcol + tape_slot(md) * kTapeF * kTileBins, (md == 0 && S.pair32) ? 3 : -1, pol);
       }
       gaccdw_flush(gw, g);
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
     }
 #pragma unroll 1
     for (int sl = 0; sl < kTapeSlots; ++sl)
-      if (!(used & (1u << sl))) tape_clear_dw(tcol + sl * kTapeF * kTileBins);
+      if (!(used & (1u << sl))) tape_clear_dw(tcol + sl * kTapeF * kTileBins, pol);
     __syncthreads();   // the tape is complete; the previous tile's readers of red are done
 #pragma unroll
     for (int i = 0; i < kGradV; ++i) red[i][threadIdx.x] = v[i];
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int 
     if (threadIdx.x < 3 * kTapeSums) {
       const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
       const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
-      sums[q][j] = tape_sum_dw(tape, j, e0, e1, D.orbit != 0);
+      sums[q][j] = tape_sum_dw(tape, j, e0, e1, D.orbit != 0, pol);
     }
     const double a = grad_block_sum(red);
     if (threadIdx.x < kGradV) {
