@@ -47,6 +47,25 @@ __device__ __forceinline__ int tape_slot(int md) { return md == 4 ? 3 : (md == 3
 // the centre's Doppler term k.x_c = pc55 cos + pc56 sin.
 constexpr int kTapeSums = 42;
 
+// Tape accesses with an L2 eviction-priority hint: the tape's lines are written and read back
+// within one tile, while the per-bin tables stream past them, so they are marked to be evicted
+// last (createpolicy.fractional.L2::evict_last; a hint only, no lasting state).
+__device__ __forceinline__ unsigned long long tape_l2_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void tst(double* a, double v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(__cvta_generic_to_global(a)), "d"(v), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ double tld(const double* a, unsigned long long pol) {
+  double v;
+  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(__cvta_generic_to_global(a)), "l"(pol)
+               : "memory");
+  return v;
+}
+
 // q(x) with d sinc(u)/du = u q(u^2): the derivative of sinc_poly_x<DEG>'s series term by term,
 // q(x) = sum_{k=1..DEG} (-1)^k 2k x^(k-1) / (2k+1)!
 template <int DEG>
@@ -69,7 +88,8 @@ __device__ __forceinline__ double dsinc_poly_x(double x) {
 // tp points at this thread's column of the mode's slot.
 __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef& S, const ModeCoef& C, const BinIn& B,
                                               XYZAcc& acc, const double2* __restrict__ tab,
-                                              const double* __restrict__ pc, const ModeCoef* C2, double* tp) {
+                                              const double* __restrict__ pc, const ModeCoef* C2, double* tp,
+                                              unsigned long long pol) {
   const double v = C.cm * B.f13;
   const double lnv = C.lncm + B.lnf3;
   const double iv5 = C.icm5 * D.fm53[B.b];
@@ -111,18 +131,18 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
     sincos_turns_r(phr + e1, tab, &E[1].y, &E[1].x);
     sincos_turns_r(phr - (e0 + e1), tab, &E[2].y, &E[2].x);
   }
-  tp[kTco * kTileBins] = co;
-  tp[kTso * kTileBins] = so;
-  tp[kTob0 * kTileBins] = ob[0];
-  tp[kTob1 * kTileBins] = ob[1];
+  tst(tp + (kTco * kTileBins), co, pol);
+  tst(tp + (kTso * kTileBins), so, pol);
+  tst(tp + (kTob0 * kTileBins), ob[0], pol);
+  tst(tp + (kTob1 * kTileBins), ob[1], pol);
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    tp[(kTE + 2 * t) * kTileBins] = E[t].x;
-    tp[(kTE + 2 * t + 1) * kTileBins] = E[t].y;
+    tst(tp + ((kTE + 2 * t) * kTileBins), E[t].x, pol);
+    tst(tp + ((kTE + 2 * t + 1) * kTileBins), E[t].y, pol);
   }
-  tp[kTamp0 * kTileBins] = amp0;
-  tp[kTw * kTileBins] = w;
-  tp[kTdv * kTileBins] = dv;
+  tst(tp + (kTamp0 * kTileBins), amp0, pol);
+  tst(tp + (kTw * kTileBins), w, pol);
+  tst(tp + (kTdv * kTileBins), dv, pol);
   double knr[3], npr[3], nqr[3];
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
@@ -189,14 +209,14 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
     smv[l] = sm;
     spv[l] = spl;
     double* tl = tp + (kTL + 8 * l) * kTileBins;
-    tl[0] = kn;
-    tl[kTileBins] = np;
-    tl[2 * kTileBins] = nq;
-    tl[3 * kTileBins] = inv;
-    tl[4 * kTileBins] = sm;
-    tl[5 * kTileBins] = spl;
-    tl[6 * kTileBins] = dsm;
-    tl[7 * kTileBins] = dspl;
+    tst(tl + (0), kn, pol);
+    tst(tl + (kTileBins), np, pol);
+    tst(tl + (2 * kTileBins), nq, pol);
+    tst(tl + (3 * kTileBins), inv, pol);
+    tst(tl + (4 * kTileBins), sm, pol);
+    tst(tl + (5 * kTileBins), spl, pol);
+    tst(tl + (6 * kTileBins), dsm, pol);
+    tst(tl + (7 * kTileBins), dspl, pol);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -241,14 +261,15 @@ __device__ __forceinline__ void link_seeds(const double2 bb[3], double sa, doubl
 // two spacecraft-offset phases and the centre's Doppler term.
 __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef& S, const SampleGrad& SG, int md,
                                               const BinIn& B, const double2* __restrict__ seeds, GradAcc& g,
-                                              const double* __restrict__ pc, double* tp, int md2) {
+                                              const double* __restrict__ pc, double* tp, int md2,
+                                              unsigned long long pol) {
   const ModeCoef& C = S.md[md];
   const ModeGrad& CG = SG.md[md];
   const double v = C.cm * B.f13;
   const double iv = C.icm * B.fm13;
   const double lnv = C.lncm + B.lnf3;
   const double iv5 = C.icm5 * D.fm53[B.b];
-  const double amp0 = tp[kTamp0 * kTileBins], w = tp[kTw * kTileBins];
+  const double amp0 = tld(tp + (kTamp0 * kTileBins), pol), w = tld(tp + (kTw * kTileBins), pol);
   const double amp = amp0 * w;
   // polarisation weights without the amplitude: ap = Pp + kappa Pp', ac = 2 Pc + kappa 2 Pc'
   double2 kap = make_double2(0.0, 0.0);
@@ -269,10 +290,10 @@ __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef&
     const int t = (l + 2) % 3;
     const double2 P = seeds[2 * l * kTileBins], Q = seeds[(2 * l + 1) * kTileBins];
     const double* tl = tp + (kTL + 8 * l) * kTileBins;
-    const double kn = tl[0], np = tl[kTileBins], nq = tl[2 * kTileBins], inv = tl[3 * kTileBins];
-    const double sm = tl[4 * kTileBins], spl = tl[5 * kTileBins];
-    const double dsm = tl[6 * kTileBins], dspl = tl[7 * kTileBins];
-    const double2 E = make_double2(tp[(kTE + 2 * t) * kTileBins], tp[(kTE + 2 * t + 1) * kTileBins]);
+    const double kn = tld(tl + (0), pol), np = tld(tl + (kTileBins), pol), nq = tld(tl + (2 * kTileBins), pol), inv = tld(tl + (3 * kTileBins), pol);
+    const double sm = tld(tl + (4 * kTileBins), pol), spl = tld(tl + (5 * kTileBins), pol);
+    const double dsm = tld(tl + (6 * kTileBins), pol), dspl = tld(tl + (7 * kTileBins), pol);
+    const double2 E = make_double2(tld(tp + ((kTE + 2 * t) * kTileBins), pol), tld(tp + ((kTE + 2 * t + 1) * kTileBins), pol));
     const double Fp = np * np - nq * nq, Fch = np * nq;
     const double2 gam = make_double2(fma(Ap.x, Fp, -Ac.y * Fch), fma(Ap.y, Fp, Ac.x * Fch));
     const double2 G = cmul(gam, E);
@@ -314,7 +335,7 @@ __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef&
     for (int f = 5; f >= 0; --f) a = fma(fb[f], pc[5 * f + m], a);
     obb[m] = a;
   }
-  const double co = tp[kTco * kTileBins], so = tp[kTso * kTileBins];
+  const double co = tld(tp + (kTco * kTileBins), pol), so = tld(tp + (kTso * kTileBins), pol);
   double tfb;
   if (D.orbit == 0) {
     // b = (cos 2a, sin 2a, cos a, sin a)
@@ -323,12 +344,12 @@ __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef&
     tfb = kPi * D.rate_ht * (co * sob - so * cob);
   } else {
     // b = (cos phi_0, sin phi_0, 0, 0); the centre keeps its heliocentric angle
-    const double c0 = tp[kTob0 * kTileBins], s0 = tp[kTob1 * kTileBins];
+    const double c0 = tld(tp + (kTob0 * kTileBins), pol), s0 = tld(tp + (kTob1 * kTileBins), pol);
     const double cob = kxcb * pc[55], sob = kxcb * pc[56];
     tfb = kPi * D.geo_rate_ht * (c0 * obb[1] - s0 * obb[0]) + kPi * D.rate_ht * (co * sob - so * cob);
   }
 #pragma unroll
-  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = fb[f];
+  for (int f = 0; f < 9; ++f) tst(tp + ((kTfb + f) * kTileBins), fb[f], pol);
   // ---------------- mode level
   g.ph = fma(phb, 2.0 * C.mfac, g.ph);          // d ph0/d phi_c = m/(2 pi)
   g.tc = fma(-B.f, phb, g.tc);                   // frac(f t_c)
@@ -356,7 +377,7 @@ __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef&
 #pragma unroll
   for (int k = 6; k >= 0; --k) ddpol = fma(ddpol, v, S.Pdd[k]);
   // Psi_PN(v), D(v): dPsi/dv = D/v, dD/dv = v^-5 ddpol / v + Q6 (2 + ln v)
-  const double dv = tp[kTdv * kTileBins];
+  const double dv = tld(tp + (kTdv * kTileBins), pol);
   vb += psib * dv * iv + Db * (iv5 * ddpol * iv + S.Q6 * (2.0 + lnv));
   g.M = fma(vb * B.f13, CG.dcm_dM, g.M);
   double pq = SG.dP_dq[7], dq = SG.dPd_dq[7];
@@ -388,20 +409,21 @@ __device__ __forceinline__ void mode_bwd_tape(const DetDev& D, const SampleCoef&
 }
 
 // Zeroes the contraction fields (form cotangents and basis) of a slot no unit used at this bin.
-__device__ __forceinline__ void tape_clear(double* tp) {
-  tp[kTco * kTileBins] = 0.0;
-  tp[kTso * kTileBins] = 0.0;
-  tp[kTob0 * kTileBins] = 0.0;
-  tp[kTob1 * kTileBins] = 0.0;
+__device__ __forceinline__ void tape_clear(double* tp, unsigned long long pol) {
+  tst(tp + (kTco * kTileBins), 0.0, pol);
+  tst(tp + (kTso * kTileBins), 0.0, pol);
+  tst(tp + (kTob0 * kTileBins), 0.0, pol);
+  tst(tp + (kTob1 * kTileBins), 0.0, pol);
 #pragma unroll
-  for (int f = 0; f < 9; ++f) tp[(kTfb + f) * kTileBins] = 0.0;
+  for (int f = 0; f < 9; ++f) tst(tp + ((kTfb + f) * kTileBins), 0.0, pol);
 }
 
 // One of the 42 contraction sums over entries [e0, e1) of the tile's tape (entry e = slot * 128 +
 // thread): sum j pairs a form's cotangent with one basis element (j < 30: link forms, coefficient
 // j % 5; 30..39: spacecraft forms; 40, 41: the centre term's cos, sin). Each sum starts at entry
 // e0 + j (neighbouring lanes read neighbouring threads' columns) and runs in a fixed order.
-__device__ __forceinline__ double tape_sum(const double* tape, int j, int e0, int e1, bool geo) {
+__device__ __forceinline__ double tape_sum(const double* tape, int j, int e0, int e1, bool geo,
+                                           unsigned long long pol) {
   int f, m;
   if (j < 30) { f = j / 5; m = j % 5; }
   else if (j < 40) { f = 6 + (j - 30) / 5; m = (j - 30) % 5; }
@@ -416,8 +438,8 @@ __device__ __forceinline__ double tape_sum(const double* tape, int j, int e0, in
     e = e0 + (e >= len ? e - len : e);
     const int slot = e >> 7, th = e & (kTileBins - 1);
     const double* col = tape + slot * kTapeF * kTileBins + th;
-    const double fv = col[(kTfb + f) * kTileBins];
-    return (m == 4) ? a + fv : fma(fv, col[bf * kTileBins], a);
+    const double fv = tld(col + ((kTfb + f) * kTileBins), pol);
+    return (m == 4) ? a + fv : fma(fv, tld(col + (bf * kTileBins), pol), a);
   };
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int i = 0;

@@ -14,14 +14,7 @@
 
 namespace pe {
 
-// Tape accesses with an L2 eviction-priority hint: the tape's lines are written and read back
-// within one tile, while the per-bin tables stream past them, so they are marked to be evicted
-// last (createpolicy.fractional.L2::evict_last; a hint only, no lasting state).
-__device__ __forceinline__ unsigned long long tape_l2_policy() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
+// The same hinted accesses for double-word fields (tape_l2_policy, pe_adjoint_tape.cuh).
 __device__ __forceinline__ void tst(df* a, df v, unsigned long long pol) {
   asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(__cvta_generic_to_global(a)), "f"(v.x),
                "f"(v.y), "l"(pol)

@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
   const int P = ds.ndet * B;
   const long long total = off[P];
   double* tcol = tape + threadIdx.x;
+  const unsigned long long pol = tape_l2_policy();
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int p = find_pair_g(off, P, t);
     if (!PE_CHK(p >= 0 && p < P && off[p + 1] <= total && nend[p] <= ds.d[p / B].nb, 16)) continue;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
         if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
         const int sl = tape_slot(md);
         mode_fwd_tape(D, S, C, Bn, xa, stab, pc, (md == 0 && S.pair32) ? &S.md[3] : nullptr,
-                      tcol + sl * kTapeF * kTileBins);
+                      tcol + sl * kTapeF * kTileBins, pol);
         used |= 1u << sl;
       }
       double2 x[3], o[3];
@@ -312,13 +313,13 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
         const ModeCoef& C = S.md[md];
         if (!C.active || !dlt_pos(Bn.f, C.fend)) continue;
         mode_bwd_tape(D, S, SG, md, Bn, &lseed[0][threadIdx.x], g, pc,
-                      tcol + tape_slot(md) * kTapeF * kTileBins, (md == 0 && S.pair32) ? 3 : -1);
+                      tcol + tape_slot(md) * kTapeF * kTileBins, (md == 0 && S.pair32) ? 3 : -1, pol);
       }
       v[6] = g.M; v[7] = g.q; v[8] = g.c1; v[9] = g.c2; v[10] = g.dL; v[11] = g.io; v[12] = g.ph; v[13] = g.tc;
     }
 #pragma unroll 1
     for (int sl = 0; sl < kTapeSlots; ++sl)
-      if (!(used & (1u << sl))) tape_clear(tcol + sl * kTapeF * kTileBins);
+      if (!(used & (1u << sl))) tape_clear(tcol + sl * kTapeF * kTileBins, pol);
     __syncthreads();   // the tape is complete; the previous tile's readers of red are done
 #pragma unroll
     for (int i = 0; i < kGradV; ++i) red[i][threadIdx.x] = v[i];
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
     if (threadIdx.x < 3 * kTapeSums) {
       const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
       const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
-      sums[q][j] = tape_sum(tape, j, e0, e1, D.orbit != 0);
+      sums[q][j] = tape_sum(tape, j, e0, e1, D.orbit != 0, pol);
     }
     const double a = grad_block_sum(red);
     if (threadIdx.x < kGradV) {
@@ -496,9 +497,9 @@ cudaError_t launch_fisher_reduce(const DetSet& ds, int B, const long long* off, 
   return pe::launch_status();
 }
 int grad_partial_width() { return kGradW; }
-// FP64: two CTAs per SM (252 registers, no spills); mixed: three (168 registers, a few hundred
-// bytes of spills), which its latency-bound sweep prefers (33.6k against 30.9k grad evals/s with
-// two, 33.0k with four)
+// FP64: two CTAs per SM (230 registers, no spills; three, at 168 registers, ran 0.4 % slower);
+// mixed: three (168 registers, a few hundred bytes of spills), which its latency-bound sweep
+// prefers (33.6k against 30.9k grad evals/s with two, 33.0k with four)
 int grad_tape_ctas_per_sm(bool mixed) { return mixed ? 3 : 2; }
 size_t grad_tape_doubles_per_cta() { return (size_t)kTapeDoubles; }
 int fisher_partial_width() { return kFisherW; }
