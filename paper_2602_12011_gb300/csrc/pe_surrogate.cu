@@ -951,6 +951,30 @@ __global__ void __launch_bounds__(kTileBins, 3) k_sur_fwd(DetSet ds, int B, cons
 // coefficients from L1, and takes NB consecutive tiles of one pair at a time: each thread then
 // carries NB independent bins through one mode loop (their coefficient loads and arithmetic
 // overlap), and each tile still gets its own partial in the same fixed order.
+// block_sum6's fixed-order sum of six double words per thread with two barriers instead of
+// three: consecutive tiles alternate between two staging buffers, so a tile's writes cannot meet
+// the previous tile's final readers (those finish before the next tile's first barrier, and the
+// buffer they read is written again only a tile later).
+__device__ __forceinline__ bool tile_sum6(const df v[6], float2 (*red)[kTileBins + kRedPad], df* out) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) red[i][threadIdx.x] = v[i];
+  __syncthreads();
+  if (threadIdx.x < 6 * 16) {
+    const int i = threadIdx.x >> 4, g = threadIdx.x & 15;
+    df s = red[i][g];
+#pragma unroll
+    for (int k = 1; k < kTileBins / 16; ++k) s = dfl_add(s, red[i][g + 16 * k]);
+    red[i][g] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 6) return false;
+  df s = red[threadIdx.x][0];
+#pragma unroll
+  for (int g = 1; g < 16; ++g) s = dfl_add(s, red[threadIdx.x][g]);
+  *out = s;
+  return true;
+}
+
 template <int NB>
 __global__ void __launch_bounds__(kTileBins, kSurInboxCtas) k_sur_inbox(DetSet ds, int B,
                                                                      const SampleCoef* __restrict__ coef,
@@ -961,7 +985,7 @@ __global__ void __launch_bounds__(kTileBins, kSurInboxCtas) k_sur_inbox(DetSet d
                                                                      const int* __restrict__ nend,
                                                                      const long long* __restrict__ off,
                                                                      const long long* __restrict__ offk, double* part) {
-  __shared__ float2 red[6][kTileBins + kRedPad];   // block_sum6 staging
+  __shared__ float2 red[2][6][kTileBins + kRedPad];   // tile sums' staging, alternating per tile
   __shared__ float ampf[kNModes];                  // a_lm hsc in FP32
   __shared__ float2 hsw[kNModes];                  // node spacing h as a double word
   __shared__ float ihsf[kNModes];                  // 1/h in FP32
@@ -970,7 +994,7 @@ __global__ void __launch_bounds__(kTileBins, kSurInboxCtas) k_sur_inbox(DetSet d
   const long long chunk = (total + gridDim.x - 1) / gridDim.x;
   const long long tk0 = blockIdx.x * chunk;
   const long long tk1 = tk0 + chunk < total ? tk0 + chunk : total;
-  int p = 0;
+  int p = 0, pcur = -1, buf = 0;
   for (long long tk = tk0; tk < tk1;) {
     p = find_pair_s(offk, P, tk, p);
     const long long tend = offk[p + 1] < tk1 ? offk[p + 1] : tk1;   // this pair's tiles in the run
@@ -979,14 +1003,17 @@ __global__ void __launch_bounds__(kTileBins, kSurInboxCtas) k_sur_inbox(DetSet d
     const int ne = nend[p];
     const DetDev& D = ds.d[I];
     const SampleCoef& S = coef[s];
-    __syncthreads();   // the previous tiles' readers of the shared per-tile values are done
-    if (threadIdx.x < kNModes) {
-      const double hm = hs[(size_t)s * kNModes + threadIdx.x];
-      ampf[threadIdx.x] = (float)(coefN[s].md[threadIdx.x].amp * S.hsc);
-      hsw[threadIdx.x] = to_dw(hm);
-      ihsf[threadIdx.x] = (float)(1.0 / hm);
+    if (p != pcur) {     // the pair's per-sample values, staged once per run of its tiles
+      __syncthreads();   // the previous pair's readers are done
+      if (threadIdx.x < kNModes) {
+        const double hm = hs[(size_t)s * kNModes + threadIdx.x];
+        ampf[threadIdx.x] = (float)(coefN[s].md[threadIdx.x].amp * S.hsc);
+        hsw[threadIdx.x] = to_dw(hm);
+        ihsf[threadIdx.x] = (float)(1.0 / hm);
+      }
+      __syncthreads();
+      pcur = p;
     }
-    __syncthreads();
     // per bin in double words, no FP64 arithmetic: u0 = 3 (ln f / 3) - ln kFmin, and frac(f t_c)
     // from the double-word product (relative error ~2^-46: ~1e-8 turn at f t_c ~ 4e5 turns)
     int bb[NB];
@@ -1039,9 +1066,10 @@ __global__ void __launch_bounds__(kTileBins, kSurInboxCtas) k_sur_inbox(DetSet d
         }
       }
       df r;
-      if (block_sum6(v, [](df a, df b) { return dfl_add(a, b); }, red, &r))
+      if (tile_sum6(v, red[buf], &r))
         part[(off[p] + (tk - offk[p]) + k) * 6 + threadIdx.x] =
             df_to(r) * (threadIdx.x < 3 ? D.dg_scale * ih : D.gg_scale * ih * ih);
+      buf ^= 1;
     }
     tk += nt;
   }
