@@ -8,9 +8,10 @@
 // Why a tape pays on this part: the FP64 pipe retires two operations per SM cycle, 64 times fewer
 // than the FP32 pipe, so a value read back from memory costs a small fraction of its
 // recomputation. A 128-thread CTA's tape (its 128 bins, up to four unit modes: 148 KB) lives in
-// global memory, one region per resident CTA (~45 MB on 152 SMs, L2-resident), so that two CTAs
-// per SM keep two warps per scheduler issuing to the FP64 pipe; one CTA per SM with the tape in
-// shared memory left the pipe waiting on its own dependent instructions a quarter of the time.
+// global memory, one region per resident CTA (46 MB for two CTAs on each of 152 SMs), held in L2
+// by an evict-last hint on its accesses, so that two CTAs per SM keep two warps per scheduler
+// issuing to the FP64 pipe; one CTA per SM with the tape in shared memory left the pipe waiting
+// on its own dependent instructions a quarter of the time.
 //
 // The reverse sweep pulls the bracket cotangents back to the projections' values, then
 //   (a) to the orbit basis, the orbit angle and t_f, through the forms' coefficients pc, and
