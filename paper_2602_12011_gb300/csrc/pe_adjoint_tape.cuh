@@ -41,6 +41,9 @@ enum : int {
   kTfb = 13,              // after the reverse sweep: the nine form cotangents (over the link fields)
 };
 constexpr int kTapeDoubles = kTapeSlots * kTapeF * kTileBins;   // per CTA
+static_assert(kTL + 8 * 3 == kTapeF, "three links of eight fields close the unit's fields");
+static_assert(kTfb + 9 <= kTapeF && kTfb > kTdv, "the form cotangents overwrite only link fields");
+static_assert(kTileBins == 128, "tape_sum splits an entry index with a 7-bit shift");
 // Tape slot of mode md (an unpaired (3,2) only occurs with (2,2) inactive).
 __device__ __forceinline__ int tape_slot(int md) { return md == 4 ? 3 : (md == 3 ? 0 : md); }
 // Pairs of the contraction: 30 link-form coefficients (forms 0..5 = k, p, q projections of links
