@@ -157,8 +157,6 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
   knr[2] = -(knr[0] + knr[1]);
   npr[2] = -(npr[0] + npr[1]);
   nqr[2] = -(nqr[0] + nqr[1]);
-  double2 G[3];
-  double smv[3], spv[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int t = (l + 2) % 3;
@@ -168,7 +166,7 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
     const double Fp = np * np - nq * nq, Fch = np * nq;
     const double2 gam = C2 ? make_double2(fma(Ap.x, Fp, -Ac.y * Fch), fma(Ap.y, Fp, Ac.x * Fch))
                            : make_double2(Ap.x * Fp, Ac.x * Fch);
-    G[l] = cmul(gam, E[t]);
+    const double2 G = cmul(gam, E[t]);
     // sincs and their derivatives in kn: u1 = a (1 - kn), u2 = a (1 + kn), so
     // d s-/dkn = -a sinc'(u1) = (a^2 kn - a^2) q(u1^2) and d s+/dkn = (a^2 kn + a^2) q(u2^2) on the
     // polynomial branch
@@ -210,8 +208,10 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
       dsm = -B.a * dsinc(u1, c1u, sm);
       dspl = B.a * dsinc(u2, c2u, spl);
     }
-    smv[l] = sm;
-    spv[l] = spl;
+    acc.S[l].x = fma(G.x, spl, acc.S[l].x);
+    acc.S[l].y = fma(G.y, spl, acc.S[l].y);
+    acc.M[l].x = fma(G.x, sm, acc.M[l].x);
+    acc.M[l].y = fma(G.y, sm, acc.M[l].y);
     double* tl = tp + (kTL + 8 * l) * kTileBins;
     tst(tl + (0), kn, pol);
     tst(tl + (kTileBins), np, pol);
@@ -221,14 +221,6 @@ __device__ __forceinline__ void mode_fwd_tape(const DetDev& D, const SampleCoef&
     tst(tl + (5 * kTileBins), spl, pol);
     tst(tl + (6 * kTileBins), dsm, pol);
     tst(tl + (7 * kTileBins), dspl, pol);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int lp = (c + 2) % 3, lu = c;
-    acc.P[c].x = fma(G[lp].x, spv[lp], fma(-G[lu].x, smv[lu], acc.P[c].x));
-    acc.P[c].y = fma(G[lp].y, spv[lp], fma(-G[lu].y, smv[lu], acc.P[c].y));
-    acc.Q[c].x = fma(G[lp].x, smv[lp], fma(-G[lu].x, spv[lu], acc.Q[c].x));
-    acc.Q[c].y = fma(G[lp].y, smv[lp], fma(-G[lu].y, spv[lu], acc.Q[c].y));
   }
 }
 

@@ -189,13 +189,13 @@ __device__ __forceinline__ void mode_fwd_tape_mixed(const DetDev& D, const Sampl
     tst(tl + (7 * kTileBins), dfl_mul(W.a, dspl), pol);
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int lp = (c + 2) % 3, lu = c;
-    acc.Pr[c] = dfl_add(acc.Pr[c], dfl_sub(dfl_mul(G[lp].re, spv[lp]), dfl_mul(G[lu].re, smv[lu])));
-    acc.Pi[c] = dfl_add(acc.Pi[c], dfl_sub(dfl_mul(G[lp].im, spv[lp]), dfl_mul(G[lu].im, smv[lu])));
-    acc.Qr[c] = dfl_add(acc.Qr[c], dfl_sub(dfl_mul(G[lp].re, smv[lp]), dfl_mul(G[lu].re, spv[lu])));
-    acc.Qi[c] = dfl_add(acc.Qi[c], dfl_sub(dfl_mul(G[lp].im, smv[lp]), dfl_mul(G[lu].im, spv[lu])));
+  for (int l = 0; l < 3; ++l) {
+    acc.Sr[l] = dfl_add(acc.Sr[l], dfl_mul(G[l].re, spv[l]));
+    acc.Si[l] = dfl_add(acc.Si[l], dfl_mul(G[l].im, spv[l]));
+    acc.Mr[l] = dfl_add(acc.Mr[l], dfl_mul(G[l].re, smv[l]));
+    acc.Mi[l] = dfl_add(acc.Mi[l], dfl_mul(G[l].im, smv[l]));
   }
+
 }
 
 // Double-word copies of what the mode-level chain rule reads: the sample's PN coefficients and

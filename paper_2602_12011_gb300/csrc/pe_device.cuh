@@ -348,18 +348,24 @@ __device__ __forceinline__ void orbit_basis(const DetDev& D, double t, const dou
   }
 }
 
-// Mode-summed TDI brackets of one bin, kept as X' = P_X + z Q_X (and Y', Z' alike): z depends on
-// the bin only, so it is applied once after the mode sum (xyz_final).
+// Mode-summed link products of one bin: S_l = sum over modes of G_l s+_l and M_l = sum of G_l s-_l,
+// for the links l = 0 (1,2), 1 (2,3), 2 (3,1). The TDI brackets follow once per bin (xyz_final):
+// X' = P_X + z Q_X (and Y', Z' alike) with P_c = S_{c+2} - M_c and Q_c = M_{c+2} - S_c (link
+// indices mod 3); z depends on the bin only. Each unit adds four products per link, once each,
+// where summing into the brackets would add each product into two of them.
 struct XYZAcc {
-  double2 P[3], Q[3];
+  double2 S[3], M[3];
 };
 __device__ __forceinline__ void xyz_zero(XYZAcc& a) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) a.P[i] = a.Q[i] = make_double2(0.0, 0.0);
+  for (int i = 0; i < 3; ++i) a.S[i] = a.M[i] = make_double2(0.0, 0.0);
 }
 __device__ __forceinline__ void xyz_final(const XYZAcc& a, double2 z, double2 x[3]) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) x[i] = cadd(a.P[i], cmul(z, a.Q[i]));
+  for (int c = 0; c < 3; ++c) {
+    const int lp = (c + 2) % 3;
+    x[c] = cadd(csub(a.S[lp], a.M[c]), cmul(z, csub(a.M[lp], a.S[c])));
+  }
 }
 
 // Per-bin inputs shared by all modes of one bin.
@@ -450,8 +456,6 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
   knr[2] = -(knr[0] + knr[1]);
   npr[2] = -(npr[0] + npr[1]);
   nqr[2] = -(nqr[0] + nqr[1]);
-  double2 G[3];
-  double smv[3], spv[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int t = (l + 2) % 3;
@@ -463,7 +467,7 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
     const double Fp = np * np - nq * nq, Fch = np * nq;
     const double2 gam = C2 ? make_double2(fma(Ap.x, Fp, -Ac.y * Fch), fma(Ap.y, Fp, Ac.x * Fch))
                            : make_double2(Ap.x * Fp, Ac.x * Fch);
-    G[l] = cmul(gam, E[t]);
+    const double2 G = cmul(gam, E[t]);
     // sinc(a(1 -+ kn)): Taylor polynomial while a < kSincPolyA (most bins of a massive-binary
     // signal), else from sin(a -+ a kn) = sin a cos(a kn) -+ cos a sin(a kn)
     // below a = kSincPolyA (degree class B.sdeg < 3, chosen once per bin): u1^2 = a^2 (1 - kn)^2 =
@@ -497,18 +501,11 @@ __device__ __forceinline__ void mode_bin(const DetDev& D, const SampleCoef& S, c
         spl = small2 ? sinc_small(u2) : s2 / u2;
       }
     }
-    smv[l] = sm;
-    spv[l] = spl;
-  }
-  // --- TDI brackets (row A6); l index: 0 = (1,2), 1 = (2,3), 2 = (3,1); bracket c uses
-  // links lp = (c + 2) % 3 (V term) and lu = c (U term)
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int lp = (c + 2) % 3, lu = c;
-    acc.P[c].x = fma(G[lp].x, spv[lp], fma(-G[lu].x, smv[lu], acc.P[c].x));
-    acc.P[c].y = fma(G[lp].y, spv[lp], fma(-G[lu].y, smv[lu], acc.P[c].y));
-    acc.Q[c].x = fma(G[lp].x, smv[lp], fma(-G[lu].x, spv[lu], acc.Q[c].x));
-    acc.Q[c].y = fma(G[lp].y, smv[lp], fma(-G[lu].y, spv[lu], acc.Q[c].y));
+    // --- the link's products for the TDI brackets (row A6; see XYZAcc)
+    acc.S[l].x = fma(G.x, spl, acc.S[l].x);
+    acc.S[l].y = fma(G.y, spl, acc.S[l].y);
+    acc.M[l].x = fma(G.x, sm, acc.M[l].x);
+    acc.M[l].y = fma(G.y, sm, acc.M[l].y);
   }
 }
 

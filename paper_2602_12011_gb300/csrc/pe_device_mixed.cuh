@@ -19,20 +19,24 @@
 
 namespace pe {
 
+// Mode-summed link products of one bin in double words (times hsc), as XYZAcc: S_l = sum G_l s+_l,
+// M_l = sum G_l s-_l.
 struct MixAcc {
-  df Pr[3], Pi[3], Qr[3], Qi[3];
+  df Sr[3], Si[3], Mr[3], Mi[3];
 };
 __device__ __forceinline__ void mix_zero(MixAcc& a) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) a.Pr[i] = a.Pi[i] = a.Qr[i] = a.Qi[i] = df_make(0.f, 0.f);
+  for (int i = 0; i < 3; ++i) a.Sr[i] = a.Si[i] = a.Mr[i] = a.Mi[i] = df_make(0.f, 0.f);
 }
-// X' = P + z Q (times hsc), double words
+// X' = P + z Q with P_c = S_{c+2} - M_c, Q_c = M_{c+2} - S_c (times hsc), double words
 __device__ __forceinline__ void mix_final(const MixAcc& a, const cdf& z, cdf x[3]) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const cdf zq = cdfl_mul(z, cdf{a.Qr[i], a.Qi[i]});
-    x[i].re = dfl_add(a.Pr[i], zq.re);
-    x[i].im = dfl_add(a.Pi[i], zq.im);
+  for (int c = 0; c < 3; ++c) {
+    const int lp = (c + 2) % 3;
+    const cdf q = {dfl_sub(a.Mr[lp], a.Sr[c]), dfl_sub(a.Mi[lp], a.Si[c])};
+    const cdf zq = cdfl_mul(z, q);
+    x[c].re = dfl_add(dfl_sub(a.Sr[lp], a.Mr[c]), zq.re);
+    x[c].im = dfl_add(dfl_sub(a.Si[lp], a.Mi[c]), zq.im);
   }
 }
 
@@ -222,14 +226,13 @@ __device__ __forceinline__ void mode_bin_mixed(const DetDev& D, const SampleCoef
       }
     }
   }
-  // --- TDI brackets (row A6): P_c += G_lp s+_lp - G_lu s-_lu, Q_c += G_lp s-_lp - G_lu s+_lu
+  // --- the links' products for the TDI brackets (row A6; see MixAcc)
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int lp = (c + 2) % 3, lu = c;
-    acc.Pr[c] = dfl_add(acc.Pr[c], dfl_sub(dfl_mul(G[lp].re, spv[lp]), dfl_mul(G[lu].re, smv[lu])));
-    acc.Pi[c] = dfl_add(acc.Pi[c], dfl_sub(dfl_mul(G[lp].im, spv[lp]), dfl_mul(G[lu].im, smv[lu])));
-    acc.Qr[c] = dfl_add(acc.Qr[c], dfl_sub(dfl_mul(G[lp].re, smv[lp]), dfl_mul(G[lu].re, spv[lu])));
-    acc.Qi[c] = dfl_add(acc.Qi[c], dfl_sub(dfl_mul(G[lp].im, smv[lp]), dfl_mul(G[lu].im, spv[lu])));
+  for (int l = 0; l < 3; ++l) {
+    acc.Sr[l] = dfl_add(acc.Sr[l], dfl_mul(G[l].re, spv[l]));
+    acc.Si[l] = dfl_add(acc.Si[l], dfl_mul(G[l].im, spv[l]));
+    acc.Mr[l] = dfl_add(acc.Mr[l], dfl_mul(G[l].re, smv[l]));
+    acc.Mi[l] = dfl_add(acc.Mi[l], dfl_mul(G[l].im, smv[l]));
   }
 }
 
