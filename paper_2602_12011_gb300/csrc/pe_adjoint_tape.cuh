@@ -418,7 +418,9 @@ __device__ __forceinline__ void tape_clear(double* tp, unsigned long long pol) {
 // thread): sum j pairs a form's cotangent with one basis element (j < 30: link forms, coefficient
 // j % 5; 30..39: spacecraft forms; 40, 41: the centre term's cos, sin). Each sum starts at entry
 // e0 + j (neighbouring lanes read neighbouring threads' columns) and runs in a fixed order.
-__device__ __forceinline__ double tape_sum(const double* tape, int j, int e0, int e1, bool geo,
+// act: the tile's active slots, two bits each in order (entry e is in slot (act >> 2 (e >> 7)) & 3):
+// slots no unit of the tile used hold only zeros and are skipped.
+__device__ __forceinline__ double tape_sum(const double* tape, int j, int e0, int e1, bool geo, unsigned act,
                                            unsigned long long pol) {
   int f, m;
   if (j < 30) { f = j / 5; m = j % 5; }
@@ -427,12 +429,13 @@ __device__ __forceinline__ double tape_sum(const double* tape, int j, int e0, in
   if (j < 40 && geo && (m == 2 || m == 3)) return 0.0;
   const int bf = m == 0 ? kTob0 : (m == 1 ? kTob1 : (m == 2 ? kTco : kTso));
   const int len = e1 - e0;
+  if (len <= 0) return 0.0;
   const int st = j % len;
   // four interleaved partial sums (a fixed order) keep four independent FMA chains in flight
   auto term = [&](int i, double a) {
     int e = st + i;
     e = e0 + (e >= len ? e - len : e);
-    const int slot = e >> 7, th = e & (kTileBins - 1);
+    const int slot = (act >> (2 * (e >> 7))) & 3, th = e & (kTileBins - 1);
     const double* col = tape + slot * kTapeF * kTileBins + th;
     const double fv = tld(col + ((kTfb + f) * kTileBins), pol);
     return (m == 4) ? a + fv : fma(fv, tld(col + (bf * kTileBins), pol), a);

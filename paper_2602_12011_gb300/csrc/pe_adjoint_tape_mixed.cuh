@@ -480,7 +480,7 @@ __device__ __forceinline__ void tape_clear_dw(df* tp, unsigned long long pol) {
 }
 
 // tape_sum on the double-word tape, in double words; the result returns to FP64.
-__device__ __forceinline__ double tape_sum_dw(const df* tape, int j, int e0, int e1, bool geo,
+__device__ __forceinline__ double tape_sum_dw(const df* tape, int j, int e0, int e1, bool geo, unsigned act,
                                               unsigned long long pol) {
   int f, m;
   if (j < 30) { f = j / 5; m = j % 5; }
@@ -489,11 +489,12 @@ __device__ __forceinline__ double tape_sum_dw(const df* tape, int j, int e0, int
   if (j < 40 && geo && (m == 2 || m == 3)) return 0.0;
   const int bf = m == 0 ? kTob0 : (m == 1 ? kTob1 : (m == 2 ? kTco : kTso));
   const int len = e1 - e0;
+  if (len <= 0) return 0.0;
   const int st = j % len;
   auto term = [&](int i, df a) {
     int e = st + i;
     e = e0 + (e >= len ? e - len : e);
-    const int slot = e >> 7, th = e & (kTileBins - 1);
+    const int slot = (act >> (2 * (e >> 7))) & 3, th = e & (kTileBins - 1);
     const df* col = tape + slot * kTapeF * kTileBins + th;
     const df fv = tld(col + ((kTfb + f) * kTileBins), pol);
     return (m == 4) ? dfl_add(a, fv) : dfl_add(a, dfl_mul(fv, tld(col + (bf * kTileBins), pol)));

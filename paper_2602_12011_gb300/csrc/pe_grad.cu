@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int 
                                                               double* tape_all) {
   df* tape = reinterpret_cast<df*>(tape_all + (size_t)blockIdx.x * kTapeDoubles);
   __shared__ double red[kGradV][kTileBins + kRedPad];
+  __shared__ unsigned tile_used;   // the slots some unit of the tile used
   __shared__ float4 stabw[kSinTab];
   __shared__ cdf lseed[6][kTileBins];   // each thread's link seeds P_l, Q_l (own column)
   __shared__ ChainW cw;                  // the tile's chain-rule coefficients as double words
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int 
     const int I = p / B, s = p - I * B;
     const int b = int(t - off[p]) * kTileBins + threadIdx.x;
     const DetDev& D = ds.d[I];
+    if (threadIdx.x == 0) tile_used = 0u;   // the previous tile's readers passed two barriers since
     proj_prologue(D, coef[s], pc);
     if (threadIdx.x < kProj) pcw[threadIdx.x] = to_dw(pc[threadIdx.x]);
     chain_fill(D, coef[s], sgrad[s], &cw);
@@ -228,14 +230,25 @@ __global__ void __launch_bounds__(kTileBins, 3) k_grad_fwd_mixed(DetSet ds, int 
 #pragma unroll 1
     for (int sl = 0; sl < kTapeSlots; ++sl)
       if (!(used & (1u << sl))) tape_clear_dw(tcol + sl * kTapeF * kTileBins, pol);
+    {
+      const unsigned wu = __reduce_or_sync(0xffffffffu, used);
+      if ((threadIdx.x & 31) == 0 && wu) atomicOr(&tile_used, wu);
+    }
     __syncthreads();   // the tape is complete; the previous tile's readers of red are done
 #pragma unroll
     for (int i = 0; i < kGradV; ++i) red[i][threadIdx.x] = v[i];
-    constexpr int kEnt = kTapeSlots * kTileBins;
+    // the contraction walks only the slots some unit of the tile used
+    const unsigned tu = tile_used;
+    unsigned act = 0;
+    int nact = 0;
+#pragma unroll
+    for (int sl = 0; sl < kTapeSlots; ++sl)
+      if ((tu >> sl) & 1u) act |= unsigned(sl) << (2 * nact++);
+    const int ent = nact * kTileBins;
     if (threadIdx.x < 3 * kTapeSums) {
       const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
-      const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
-      sums[q][j] = tape_sum_dw(tape, j, e0, e1, D.orbit != 0, pol);
+      const int e0 = q * ent / 3, e1 = (q + 1) * ent / 3;
+      sums[q][j] = tape_sum_dw(tape, j, e0, e1, D.orbit != 0, act, pol);
     }
     const double a = grad_block_sum(red);
     if (threadIdx.x < kGradV) {
@@ -261,6 +274,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
                                                              double* tape_all) {
   double* tape = tape_all + (size_t)blockIdx.x * kTapeDoubles;   // [kTapeSlots][kTapeF][kTileBins]
   __shared__ double red[kGradV][kTileBins + kRedPad];
+  __shared__ unsigned tile_used;   // the slots some unit of the tile used
   __shared__ double2 stab[kSinTab];
   __shared__ double2 lseed[6][kTileBins];   // each thread's link seeds P_l, Q_l (own column)
   __shared__ double pc[kProj];
@@ -277,6 +291,7 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
     const int I = p / B, s = p - I * B;
     const int b = int(t - off[p]) * kTileBins + threadIdx.x;
     const DetDev& D = ds.d[I];
+    if (threadIdx.x == 0) tile_used = 0u;   // the previous tile's readers passed two barriers since
     proj_prologue(D, coef[s], pc);
     double v[kGradV];
 #pragma unroll
@@ -320,14 +335,25 @@ __global__ void __launch_bounds__(kTileBins, 2) k_grad_fwd_tape(DetSet ds, int B
 #pragma unroll 1
     for (int sl = 0; sl < kTapeSlots; ++sl)
       if (!(used & (1u << sl))) tape_clear(tcol + sl * kTapeF * kTileBins, pol);
+    {
+      const unsigned wu = __reduce_or_sync(0xffffffffu, used);
+      if ((threadIdx.x & 31) == 0 && wu) atomicOr(&tile_used, wu);
+    }
     __syncthreads();   // the tape is complete; the previous tile's readers of red are done
 #pragma unroll
     for (int i = 0; i < kGradV; ++i) red[i][threadIdx.x] = v[i];
-    constexpr int kEnt = kTapeSlots * kTileBins;
+    // the contraction walks only the slots some unit of the tile used
+    const unsigned tu = tile_used;
+    unsigned act = 0;
+    int nact = 0;
+#pragma unroll
+    for (int sl = 0; sl < kTapeSlots; ++sl)
+      if ((tu >> sl) & 1u) act |= unsigned(sl) << (2 * nact++);
+    const int ent = nact * kTileBins;
     if (threadIdx.x < 3 * kTapeSums) {
       const int j = threadIdx.x % kTapeSums, q = threadIdx.x / kTapeSums;
-      const int e0 = q * kEnt / 3, e1 = (q + 1) * kEnt / 3;
-      sums[q][j] = tape_sum(tape, j, e0, e1, D.orbit != 0, pol);
+      const int e0 = q * ent / 3, e1 = (q + 1) * ent / 3;
+      sums[q][j] = tape_sum(tape, j, e0, e1, D.orbit != 0, act, pol);
     }
     const double a = grad_block_sum(red);
     if (threadIdx.x < kGradV) {
