@@ -24,7 +24,8 @@ __device__ __forceinline__ cdf cdf_mul_s(const cdf& a, const cdf& b) {
 // sinc(u) and d sinc/du for |u| <= 1 in double words. With x = u^2: sinc = 1 + x P(x) (the series of
 // df_sinc_poly) and d sinc/du = 2 u Q(x), Q(x) = sum_k k c_k x^(k-1), c_k = (-1)^k / (2k+1)!:
 // Q = c1 + x (2 c2 + x (3 c3 + x (4 c4 + x T))), T = 5 c5 + x (6 c6 + x (7 c7 + x 8 c8)) in float
-// (|T| < 1.3e-7); the first dropped term, 9 c9 x^8, is below 7.5e-17.
+// (|T| < 1.3e-7); the first dropped term, 9 c9 x^8, is below 7.5e-17. As in df_sinc_poly, each
+// Horner step adds a term smaller than its constant (ordered adds).
 struct df2 {
   df v, d;
 };
@@ -35,10 +36,10 @@ static __device__ __noinline__ df2 df_sinc_poly_d(df u) {
   float T = __fmaf_rn(x.x, 2.2491659e-14f, -5.3530145e-12f);
   T = __fmaf_rn(T, x.x, 9.635426e-10f);
   T = __fmaf_rn(T, x.x, -1.2526054e-07f);
-  df q = dfl_add(df_make(1.10229275e-05f, 1.5174285e-13f), dfl_mulf(x, T));   // 4 c4
-  q = dfl_add(df_make(-0.0005952381f, 2.2728706e-11f), dfl_mul(x, q));          // 3 c3
-  q = dfl_add(df_make(0.016666668f, -8.692344e-10f), dfl_mul(x, q));            // 2 c2
-  q = dfl_add(df_make(-0.16666667f, 4.967054e-09f), dfl_mul(x, q));             // c1
+  df q = dfl_add_o(df_make(1.10229275e-05f, 1.5174285e-13f), dfl_mulf(x, T));   // 4 c4
+  q = dfl_add_o(df_make(-0.0005952381f, 2.2728706e-11f), dfl_mul(x, q));          // 3 c3
+  q = dfl_add_o(df_make(0.016666668f, -8.692344e-10f), dfl_mul(x, q));            // 2 c2
+  q = dfl_add_o(df_make(-0.16666667f, 4.967054e-09f), dfl_mul(x, q));             // c1
   r.d = df_scale2(dfl_mul(u, q), 2.0f);
   return r;
 }

@@ -60,24 +60,25 @@ __device__ __forceinline__ void load_bin_w(const DetDev& D, int b, BinW& W) {
 __device__ __forceinline__ df df_sinc_small(df u) {
   const df u2 = dfl_mul(u, u);
   const df p = df_make(-0.166666672f, __fmaf_rn(u2.x, 1.0f / 120.0f, 4.96705388e-09f));
-  return dfl_add(df_make(1.f, 0.f), dfl_mul(u2, p));
+  return dfl_add_o(df_make(1.f, 0.f), dfl_mul(u2, p));
 }
 
 // p[0..3] . b + p[4] in double words (the projection forms of DetDev::Mo, see proj_coef)
 // sinc(u) for |u| <= 1 in double words: 1 + x (c1 + x (c2 + x (c3 + x (c4 + x T)))), x = u^2,
 // c_k = (-1)^k / (2k+1)! as double words; the tail T = c5 + x (c6 + x (c7 + x c8)) is below
 // 2.5e-8 and is evaluated in float (its rounding stays below 1e-14 of the result); the first
-// dropped term is below 1/19! = 8.2e-18.
+// dropped term is below 1/19! = 8.2e-18. With x <= 1 each Horner step adds a term at least six
+// times smaller than its constant, so the steps take the ordered add.
 __device__ __forceinline__ df df_sinc_poly(df u) {
   const df x = dfl_mul(u, u);
   float T = __fmaf_rn(x.x, 1.0f / 355687428096000.0f, -1.0f / 1307674368000.0f);
   T = __fmaf_rn(T, x.x, 1.0f / 6227020800.0f);
   T = __fmaf_rn(T, x.x, -1.0f / 39916800.0f);
-  df p = dfl_add(df_make(2.75573188e-06f, 3.79357122e-14f), dfl_mulf(x, T));       // 1/9!
-  p = dfl_add(df_make(-0.000198412701f, 2.72559687e-12f), dfl_mul(x, p));           // -1/7!
-  p = dfl_add(df_make(0.00833333377f, -4.34617203e-10f), dfl_mul(x, p));            // 1/5!
-  p = dfl_add(df_make(-0.166666672f, 4.96705388e-09f), dfl_mul(x, p));              // -1/3!
-  return dfl_add(df_make(1.f, 0.f), dfl_mul(x, p));
+  df p = dfl_add_o(df_make(2.75573188e-06f, 3.79357122e-14f), dfl_mulf(x, T));       // 1/9!
+  p = dfl_add_o(df_make(-0.000198412701f, 2.72559687e-12f), dfl_mul(x, p));           // -1/7!
+  p = dfl_add_o(df_make(0.00833333377f, -4.34617203e-10f), dfl_mul(x, p));            // 1/5!
+  p = dfl_add_o(df_make(-0.166666672f, 4.96705388e-09f), dfl_mul(x, p));              // -1/3!
+  return dfl_add_o(df_make(1.f, 0.f), dfl_mul(x, p));
 }
 
 __device__ __forceinline__ df dw_dot5(const float2* p, const df b[4]) {

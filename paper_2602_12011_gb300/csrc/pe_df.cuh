@@ -126,6 +126,14 @@ __device__ __forceinline__ df dfl_add(df x, df y) {
   return df_make(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
 }
 __device__ __forceinline__ df dfl_sub(df x, df y) { return dfl_add(x, make_float2(-y.x, -y.y)); }
+// dfl_add for operands ordered by size, |x.hi| >= |y.hi| (or x.hi = 0): under that ordering Fast2Sum
+// returns the same rounded sum and the same exact error as TwoSum, in three additions instead of
+// six, so the result is dfl_add's bit for bit. For the Taylor and Horner steps and the Newton
+// corrections, where the ordering follows from the magnitudes of the terms.
+__device__ __forceinline__ df dfl_add_o(df x, df y) {
+  const df s = fast_two_sum(x.x, y.x);
+  return df_make(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
 __device__ __forceinline__ df dfl_mul(df x, df y) {
   const float ch = __fmul_rn(x.x, y.x);
   const float cl1 = __fmaf_rn(x.x, y.x, -ch);
@@ -142,7 +150,7 @@ __device__ __forceinline__ df dfl_mulf(df x, float y) {
 __device__ __forceinline__ df df_rcp(df x) {
   const float y0 = __frcp_rn(x.x);
   const df e = dfl_sub(df_make(1.f, 0.f), dfl_mulf(x, y0));
-  return dfl_add(df_make(y0, 0.f), dfl_mulf(e, y0));
+  return dfl_add_o(df_make(y0, 0.f), dfl_mulf(e, y0));
 }
 // 1/sqrt(x), x > 0: correctly rounded float seed, one Newton step in DW: y = y0 + y0 (1 - x y0^2)/2
 // (relative error (3/2) delta^2 for a seed error delta <= u, plus the DW rounding); unnormalised
@@ -151,7 +159,7 @@ __device__ __forceinline__ df df_rsqrt(df x) {
   const float y0 = __frsqrt_rn(x.x);
   const df xy2 = dfl_mulf(dfl_mulf(x, y0), y0);
   const df e = dfl_sub(df_make(1.f, 0.f), xy2);
-  return dfl_add(df_make(y0, 0.f), dfl_mulf(df_scale2(e, 0.5f), y0));
+  return dfl_add_o(df_make(y0, 0.f), dfl_mulf(df_scale2(e, 0.5f), y0));
 }
 
 // complex DW numbers as pairs (re, im)
@@ -196,8 +204,8 @@ static __device__ __noinline__ cdf df_cis_turns(df x, const float4* __restrict__
   // -1/6 = -0.166666672 + 4.96705388e-09 and -1/2, with the next Taylor terms folded into the lows
   const df ps = df_make(-0.166666672f, __fmaf_rn(t2.x, 1.0f / 120.0f, 4.96705388e-09f));
   const df pc = df_make(-0.5f, __fmul_rn(t2.x, 1.0f / 24.0f));
-  const df st = dfl_add(t, dfl_mul(t, dfl_mul(t2, ps)));
-  const df ct = dfl_add(df_make(1.f, 0.f), dfl_mul(t2, pc));
+  const df st = dfl_add_o(t, dfl_mul(t, dfl_mul(t2, ps)));   // |t^3/6| < |t|
+  const df ct = dfl_add_o(df_make(1.f, 0.f), dfl_mul(t2, pc));  // |t^2/2| < 1
   cdf r;
   r.re = dfl_sub(dfl_mul(cj, ct), dfl_mul(sj, st));
   r.im = dfl_add(dfl_mul(sj, ct), dfl_mul(cj, st));
