@@ -40,7 +40,7 @@ MSUN_S = 4.925490947641267e-6
 UNIT_COUNTS = {
     "fp64": {"fp64_flops": 386.2, "fp64_inst": 243.4, "fp32_inst": 0.2},
     # mixed: the MINB 4 (128-register) variant, the autotuner's usual pick for the mixed path
-    "mixed": {"fp64_flops": 39.7, "fp64_inst": 29.6, "fp32_inst": 2156.7},
+    "mixed": {"fp64_flops": 41.2, "fp64_inst": 31.1, "fp32_inst": 2054.6},
     # FP32 path: fp64_inst counts the FRND and F2F of CUDA's FP32 sincospif/sinf and conversions
     "fp32": {"fp64_flops": 0.3, "fp64_inst": 8.9, "fp32_inst": 354.4},
 }
@@ -51,10 +51,10 @@ UNIT_SOURCES = {
     "mixed": ("pe_device.cuh", "pe_device_mixed.cuh", "pe_df.cuh", "pe_kernels.cu", "pe_internal.h"),
     "fp32": ("pe_device.cuh", "pe_device_f32.cuh", "pe_kernels.cu", "pe_internal.h"),
 }
-UNIT_COUNTS_SOURCE_SHA = {"fp64": "292696e716174956", "mixed": "3ec3250ebdbaf22c", "fp32": "5ceb52c2077064e4"}
+UNIT_COUNTS_SOURCE_SHA = {"fp64": "292696e716174956", "mixed": "7c7bef97e00bebcd", "fp32": "5ceb52c2077064e4"}
 # DRAM bytes (read + write) of one full-size launch (B = 1024), ncu dram__bytes_{read,write}.sum:
 # the per-bin tables, read once per launch
-TRAFFIC = {"fp64": 36.62e6 + 0.01e6, "mixed": 40.39e6 + 1.16e6, "fp32": None}
+TRAFFIC = {"fp64": 36.62e6 + 0.01e6, "mixed": 40.42e6 + 1.06e6, "fp32": None}
 # Algorithmic work of the method (oracle/flop_model.py: the oracle's own operations, counted on
 # 16 samples of this workload): add/sub/mul/div per active (sample, mode, bin) unit and per active
 # (sample, bin) for the A/E/T and likelihood terms, and math-library calls per unit.
